@@ -1,0 +1,9 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This package holds no arithmetic of the method: it only lays out structured P1 meshes
+(triangles and tetrahedra) of a box domain Omega with its interaction layer, with an
+optional seeded vertex jitter, and describes the workloads (horizon, mollifier width,
+refinement levels, kernel, manufactured solution) the tests and the benchmark run.
+"""
+from .mesh import Mesh, structured_mesh, splitmix64_unit  # noqa: F401
+from .configs import WORKLOADS, Workload, workload_mesh  # noqa: F401

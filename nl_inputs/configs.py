@@ -1,0 +1,83 @@
+"""Workload descriptions: the shapes and parameters of the paper's tests and of the
+benchmark configurations, as plain data.
+
+Every mesh is a structured P1 mesh of a box Omega with an interaction layer of
+ceil((delta + eps)/h) whole cells, so the mollified kernel (support radius delta + eps)
+never reaches past the meshed region from a point of Omega.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, replace
+
+from .mesh import Mesh, structured_mesh
+
+KERNEL_CONST = 0
+KERNEL_GAUSS = 1
+
+MS_LINEAR = 0
+MS_QUADRATIC = 1
+MS_CUBIC = 2
+MS_QUARTIC = 3
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    dim: int
+    cells: tuple
+    h: float
+    lo: tuple
+    delta: float
+    eps: float
+    L_max: int
+    L_min: int = 1
+    kernel: int = KERNEL_CONST
+    ms: int = MS_QUADRATIC
+    jitter: float = 0.0
+    seed: int = 0
+    layer_cells: int = 0  # 0: ceil((delta + eps)/h); otherwise the given number of cells
+
+    @property
+    def layer(self) -> int:
+        if self.layer_cells:
+            return int(self.layer_cells)
+        return int(math.ceil((self.delta + self.eps) / self.h - 1e-9))
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def _unit_box(name, dim, n, delta, eps, L_max, **kw) -> Workload:
+    return Workload(name=name, dim=dim, cells=(n,) * dim, h=1.0 / n, lo=(0.0,) * dim,
+                    delta=delta, eps=eps, L_max=L_max, **kw)
+
+
+def table2_tri(ml: int) -> Workload:
+    """Sec. 6, Table 2: Omega = [-0.6, 0.6] x [-0.4, 0.4], h = 0.1 (1/2)^(ml-2),
+    delta = 0.2, eps = 0.0125 (2/3)^(ml-2), L_min = 1, L_max = 3, u = x^3 + y^3.  The layer
+    Gamma is meshed delta wide (Sec. 2, eq. interaction-domain), 2^(ml-1) cells."""
+    s = 2 ** (ml - 2)
+    return Workload(name=f"table2_tri_ml{ml}", dim=2, cells=(12 * s, 8 * s), h=0.1 / s,
+                    lo=(-0.6, -0.4), delta=0.2, eps=0.0125 * (2.0 / 3.0) ** (ml - 2), L_max=3,
+                    ms=MS_CUBIC, layer_cells=2 * s)
+
+
+_H2 = 1.0 / 256.0
+WORKLOADS = {
+    # 2D, h = 1/16, delta = 0.1, eps = delta/10, 3 levels, u = x^2 + y^2
+    "c1_2d": _unit_box("c1_2d", 2, 16, 0.1, 0.01, 3),
+    # 2D at scale, h = 1/256, delta = 4h, eps in {delta/5, delta/20}, 4 levels, jitter 0.1h
+    "c2_2d": _unit_box("c2_2d", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1),
+    "c2_2d_eps20": _unit_box("c2_2d_eps20", 2, 256, 4 * _H2, 4 * _H2 / 20, 4, jitter=0.1),
+    "c2_2d_gauss": _unit_box("c2_2d_gauss", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1,
+                             kernel=KERNEL_GAUSS),
+    # 3D, h = 1/16, delta = 0.125, eps = delta/10, 2 levels, u = x^2 + y^2 + z^2
+    "c3_3d": _unit_box("c3_3d", 3, 16, 0.125, 0.0125, 2),
+    # 3D, h = 1/32, delta = 3h, eps = delta/10, 2 levels
+    "c4_3d": _unit_box("c4_3d", 3, 32, 3.0 / 32, 0.3 / 32, 2),
+}
+
+
+def workload_mesh(w: Workload) -> Mesh:
+    return structured_mesh(w.dim, w.cells, w.h, w.lo, w.layer, jitter=w.jitter, seed=w.seed)

@@ -1,0 +1,123 @@
+"""Structured P1 meshes of Omega = [lo, lo + cells*h] with an interaction layer.
+
+Layout (the same on both sides of every parity test):
+
+* vertices are numbered lexicographically, x fastest: v = i + (nx+1)*(j + (ny+1)*k),
+  where i, j, k count grid lines from the outer corner of the layer;
+* ``coords`` is SoA, shape (dim, n_vert), float64;
+* cells are numbered lexicographically, x fastest; each square is cut along its
+  "/" diagonal into (v00, v10, v11) and (v00, v11, v01); each cube is cut into the six
+  Kuhn tetrahedra (v000, v000+e_a, v000+e_a+e_b, v111) for the permutations (a, b, c)
+  of the axes in lexicographic order; ``conn`` has shape (n_elem, dim+1), int32;
+* an element belongs to Omega when its cell does; a vertex is a degree of freedom
+  ("free") when it lies strictly inside Omega (grid index strictly between the Omega
+  faces), so the vertices on the boundary of Omega belong to the volume constraint;
+* optional jitter moves every vertex that lies neither on the boundary of Omega nor on
+  the outer boundary of the layer by ``jitter * h * (2u - 1)`` per coordinate, with u the
+  splitmix64 counter generator of :func:`splitmix64_unit`.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64_unit(seed: int, counter: np.ndarray) -> np.ndarray:
+    """Uniform doubles in [0, 1) from splitmix64 (Steele, Lea, Flood 2014) at position
+    ``seed + (counter + 1) * golden``: z ^= z>>30; z *= M1; z ^= z>>27; z *= M2; z ^= z>>31;
+    u = (z >> 11) * 2^-53."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (counter.astype(np.uint64) + np.uint64(1)) * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+@dataclass
+class Mesh:
+    dim: int
+    coords: np.ndarray  # (dim, n_vert) float64, SoA
+    conn: np.ndarray  # (n_elem, dim+1) int32
+    elem_in_omega: np.ndarray  # (n_elem,) uint8
+    node_free: np.ndarray  # (n_vert,) uint8
+    h: float
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_vert(self) -> int:
+        return int(self.coords.shape[1])
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.conn.shape[0])
+
+    def points(self) -> np.ndarray:
+        """(n_vert, dim) copy of the coordinates."""
+        return np.ascontiguousarray(self.coords.T)
+
+
+def structured_mesh(dim: int, cells, h: float, lo, layer: int, jitter: float = 0.0,
+                    seed: int = 0) -> Mesh:
+    """Mesh of Omega = prod_k [lo_k, lo_k + cells_k*h] plus ``layer`` cells on every side."""
+    if dim not in (2, 3):
+        raise ValueError("dim must be 2 or 3")
+    cells = [int(c) for c in (cells if np.iterable(cells) else [cells] * dim)]
+    lo = [float(v) for v in (lo if np.iterable(lo) else [lo] * dim)]
+    if len(cells) != dim or len(lo) != dim or layer < 0 or min(cells) < 1:
+        raise ValueError("bad mesh description")
+    nc = [c + 2 * layer for c in cells]  # cells per axis including the layer
+    nl = [c + 1 for c in nc]  # grid lines per axis
+    n_vert = int(np.prod(nl))
+    # grid index of every vertex, x fastest
+    idx = np.indices(nl[::-1]).reshape(dim, -1)[::-1]  # idx[k] = index along axis k
+    coords = np.empty((dim, n_vert), dtype=np.float64)
+    for k in range(dim):
+        coords[k] = lo[k] + (idx[k] - layer).astype(np.float64) * h
+    faces = [(0, layer, layer + cells[k], nc[k]) for k in range(dim)]
+    on_face = np.zeros(n_vert, dtype=bool)
+    inside = np.ones(n_vert, dtype=bool)
+    for k in range(dim):
+        on_face |= np.isin(idx[k], faces[k])
+        inside &= (idx[k] > layer) & (idx[k] < layer + cells[k])
+    if jitter != 0.0:
+        vid = np.arange(n_vert, dtype=np.int64)
+        move = ~on_face
+        for k in range(dim):
+            u = splitmix64_unit(seed, vid * 4 + k)
+            off = (jitter * h) * (2.0 * u - 1.0)
+            coords[k] = np.where(move, coords[k] + off, coords[k])
+    # elements
+    cidx = np.indices(nc[::-1]).reshape(dim, -1)[::-1]  # cell index per axis, x fastest
+    n_cells = cidx.shape[1]
+    stride = [int(np.prod(nl[:k])) for k in range(dim)]
+    base = sum(cidx[k] * stride[k] for k in range(dim))
+    in_omega = np.ones(n_cells, dtype=bool)
+    for k in range(dim):
+        in_omega &= (cidx[k] >= layer) & (cidx[k] < layer + cells[k])
+    if dim == 2:
+        v00 = base
+        v10 = base + stride[0]
+        v01 = base + stride[1]
+        v11 = base + stride[0] + stride[1]
+        tris = [(v00, v10, v11), (v00, v11, v01)]
+        conn = np.stack([np.stack(t, axis=1) for t in tris], axis=1).reshape(-1, 3)
+        per_cell = 2
+    else:
+        tets = []
+        for perm in itertools.permutations(range(3)):
+            a = base + stride[perm[0]]
+            b = a + stride[perm[1]]
+            tets.append((base, a, b, base + stride[0] + stride[1] + stride[2]))
+        conn = np.stack([np.stack(t, axis=1) for t in tets], axis=1).reshape(-1, 4)
+        per_cell = 6
+    elem_in_omega = np.repeat(in_omega, per_cell).astype(np.uint8)
+    return Mesh(dim=dim, coords=coords, conn=np.ascontiguousarray(conn.astype(np.int32)),
+                elem_in_omega=elem_in_omega, node_free=inside.astype(np.uint8), h=float(h),
+                meta=dict(cells=cells, lo=lo, layer=layer, jitter=jitter, seed=seed))

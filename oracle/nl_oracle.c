@@ -1,0 +1,940 @@
+/* nl_oracle.c -- plain FP64 CPU oracle for the mollified nonlocal FE assembly of
+ * Aulisa, Capodaglio, Chierici, D'Elia, "Efficient quadrature rules for finite
+ * element discretizations of nonlocal equations" (arXiv 2101.08825).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py load this library; the product path
+ * never does.  It is deliberately slow and literal: every step follows the paper's
+ * definitions in the paper's order and notation, in FP64, compiled with
+ * -ffp-contract=off.  It shares no code with the CUDA library.
+ *
+ * Pins (tests/test_oracle_*.py): xi and mu against their closed-form properties,
+ * C_{delta,eps} against an independent radial quadrature, the simplex rules against
+ * exact monomial integrals, the box distances against exact point-set distances,
+ * fully-interior pairs against closed-form local matrices, transition pairs against
+ * brute-force uniform quadrature, zero row sums, exact symmetry at L_max = 1,
+ * L_eps u = Laplace(u) on quadratics, and the printed Table 2 (TRI, linear) errors.
+ */
+#include "nl_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------------------
+ * Sec. 3, eq. (mollifier).  The printed argument of xi reads ((delta-eps) - r)/eps,
+ * which gives mu = xi(-1) = 0 at r = delta-eps and a negative second moment; the
+ * reading used here is (delta - r)/eps, for which mu is C^4, equals 1 at r = delta-eps
+ * and 0 at r = delta+eps, and reproduces the printed C_{delta,eps} of Sec. 6. */
+double or_xi(double s) {
+  double s2 = s * s;
+  double s3 = s2 * s;
+  double s5 = s3 * s2;
+  double s7 = s5 * s2;
+  double s9 = s7 * s2;
+  return (128.0 + 315.0 * s - 420.0 * s3 + 378.0 * s5 - 180.0 * s7 + 35.0 * s9) / 256.0;
+}
+
+double or_mu(double r, double delta, double eps) {
+  if (r < delta - eps) return 1.0;
+  if (r > delta + eps) return 0.0;
+  return or_xi((delta - r) / eps);
+}
+
+/* Sec. 3, eq. (gamma): gamma = C eta(|x-y|) 1(y in B_delta(x)).  eta = 1 in every test of
+ * the paper (Sec. 6); the truncated Gaussian exp(-r^2/delta^2) is the second radial
+ * profile of the workloads. */
+double or_eta(int kernel, double r, double delta) {
+  if (kernel == OR_KERNEL_GAUSS) return exp(-(r * r) / (delta * delta));
+  return 1.0;
+}
+
+/* n-point Gauss-Legendre nodes and weights on [-1, 1]: roots of P_n by Newton's method on
+ * the three-term recurrence, w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2). */
+int or_gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; i++) {
+    double z = cos(OR_PI * (i + 0.75) / (n + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; it++) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; k++) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  return 0;
+}
+
+/* int_a^b r^q eta(r) mu(r) dr by 60-point Gauss-Legendre on [0, delta-eps] (mu = 1) and
+ * [delta-eps, delta+eps] (mu = xi), where the integrand is smooth. */
+static double radial_integral(int q, int kernel, double delta, double eps) {
+  enum { NG = 60 };
+  double gx[NG], gw[NG];
+  or_gauss_legendre(NG, gx, gw);
+  double pieces[3] = {0.0, delta - eps, delta + eps};
+  double total = 0.0;
+  for (int s = 0; s < 2; s++) {
+    double a = pieces[s], b = pieces[s + 1];
+    double half = 0.5 * (b - a), mid = 0.5 * (b + a);
+    for (int i = 0; i < NG; i++) {
+      double r = mid + half * gx[i];
+      double rq = 1.0;
+      for (int k = 0; k < q; k++) rq *= r;
+      total += half * gw[i] * rq * or_eta(kernel, r, delta) * or_mu(r, delta, eps);
+    }
+  }
+  return total;
+}
+
+/* int_{R^n} z_1^p gamma_eps(|z|) dz, p in {2, 4}, for gamma_eps = C eta mu (Sec. 3, eq.
+ * approx-kernel).  In polar form: int z_1^2 f = (1/n) |S^{n-1}| int r^{n+1} f dr and
+ * int z_1^4 f = 3/(n(n+2)) |S^{n-1}| int r^{n+3} f dr, |S^1| = 2 pi, |S^2| = 4 pi. */
+double or_kernel_moment(int dim, int kernel, double delta, double eps, double C, int p) {
+  double sphere = (dim == 2) ? 2.0 * OR_PI : 4.0 * OR_PI;
+  if (p == 2) return C * sphere / dim * radial_integral(dim + 1, kernel, delta, eps);
+  if (p == 4) return C * sphere * 3.0 / (dim * (dim + 2.0)) * radial_integral(dim + 3, kernel, delta, eps);
+  return NAN;
+}
+
+/* Sec. 6: the scaling constants.  kappa (undefined in the paper) is read as 1. */
+double or_kernel_constant(int dim, int kernel, double delta, double eps) {
+  if (kernel == OR_KERNEL_CONST) {
+    double t = eps / delta;
+    double t2 = t * t;
+    double t4 = t2 * t2;
+    if (dim == 2) {
+      double c_delta = 4.0 / (OR_PI * delta * delta * delta * delta);
+      return c_delta / (1.0 + 6.0 / 11.0 * t2 + 3.0 / 143.0 * t4);
+    }
+    double c_delta = 15.0 / (4.0 * OR_PI * delta * delta * delta * delta * delta);
+    return c_delta / (1.0 + 10.0 / 11.0 * t2 + 15.0 / 143.0 * t4);
+  }
+  /* L_eps u = Laplace(u) for quadratic u  <=>  int z_1^2 gamma_eps dz = 1. */
+  return 1.0 / or_kernel_moment(dim, kernel, delta, eps, 1.0, 2);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Degree-5 symmetric simplex rules (Sec. 6: the 7-point rule for triangles; the
+ * 14-point tetrahedral rule of the 3D workloads).  Each rule is a union of symmetry
+ * orbits of barycentric points; the unknowns (orbit weights and parameters) solve the
+ * moment equations sum_q w_q lambda^alpha(q) = n! alpha! / (|alpha| + n)! for a set of
+ * monomials spanning the symmetric polynomials of degree <= 5. */
+
+/* The moment equations are solved in long double (80-bit on x86-64, 128-bit on
+ * aarch64) and the result is rounded to double, so the tables are correct to the last
+ * bit or so on both machines. */
+typedef long double ld;
+
+/* Fills the distinct permutations of an orbit; returns how many. */
+static int orbit_points(int dim, int type, ld a, ld pts[][4]) {
+  if (dim == 2) {
+    if (type == 0) { /* centroid */
+      pts[0][0] = pts[0][1] = pts[0][2] = 1.0L / 3.0L;
+      return 1;
+    }
+    ld b = 1.0L - 2.0L * a; /* (a, a, b) */
+    ld base[3][3] = {{a, a, b}, {a, b, a}, {b, a, a}};
+    for (int i = 0; i < 3; i++)
+      for (int k = 0; k < 3; k++) pts[i][k] = base[i][k];
+    return 3;
+  }
+  if (type == 1) { /* (a, a, a, 1-3a) */
+    ld b = 1.0L - 3.0L * a;
+    for (int i = 0; i < 4; i++)
+      for (int k = 0; k < 4; k++) pts[i][k] = (k == 3 - i) ? b : a;
+    return 4;
+  }
+  /* type 2: (a, a, 1/2-a, 1/2-a) */
+  ld b = 0.5L - a;
+  int n = 0;
+  for (int i = 0; i < 4; i++)
+    for (int j = i + 1; j < 4; j++) {
+      for (int k = 0; k < 4; k++) pts[n][k] = (k == i || k == j) ? a : b;
+      n++;
+    }
+  return 6;
+}
+
+static ld factorial(int n) {
+  ld f = 1.0L;
+  for (int i = 2; i <= n; i++) f *= i;
+  return f;
+}
+
+/* Moment test functions: lambda_1^k (k = 0, 2, 3, 4, 5) and, in 3D, lambda_1^2 lambda_2^2. */
+static const int tri_alpha[5][3] = {{0, 0, 0}, {2, 0, 0}, {3, 0, 0}, {4, 0, 0}, {5, 0, 0}};
+static const int tet_alpha[6][4] = {{0, 0, 0, 0}, {2, 0, 0, 0}, {3, 0, 0, 0},
+                                    {4, 0, 0, 0}, {5, 0, 0, 0}, {2, 2, 0, 0}};
+
+static ld mono(int dim, const int* alpha, const ld* lam) {
+  ld v = 1.0L;
+  for (int k = 0; k <= dim; k++)
+    for (int e = 0; e < alpha[k]; e++) v *= lam[k];
+  return v;
+}
+
+static ld mono_exact(int dim, const int* alpha) {
+  int s = 0;
+  ld num = factorial(dim);
+  for (int k = 0; k <= dim; k++) {
+    s += alpha[k];
+    num *= factorial(alpha[k]);
+  }
+  return num / factorial(s + dim);
+}
+
+/* Rule layout: 2D unknowns u = (w0, w1, a1, w2, a2) for orbits (centroid, S21(a1),
+ * S21(a2)); 3D u = (w1, a, w2, b, w3, c) for orbits (S31(a), S31(b), S22(c)). */
+static int rule_points(int dim, const ld* u, ld pts[][4], ld* w) {
+  ld tmp[8][4];
+  int n = 0;
+  for (int o = 0; o < 3; o++) {
+    int type;
+    ld wt, par;
+    if (dim == 2) {
+      type = (o == 0) ? 0 : 1;
+      wt = (o == 0) ? u[0] : u[2 * o - 1];
+      par = (o == 0) ? 0.0L : u[2 * o];
+    } else {
+      type = (o < 2) ? 1 : 2;
+      wt = u[2 * o];
+      par = u[2 * o + 1];
+    }
+    int c = orbit_points(dim, type, par, tmp);
+    for (int i = 0; i < c; i++) {
+      for (int k = 0; k < 4; k++) pts[n][k] = tmp[i][k];
+      w[n] = wt;
+      n++;
+    }
+  }
+  return n;
+}
+
+static void rule_residual(int dim, const ld* u, ld* res) {
+  ld pts[16][4], w[16];
+  int n = rule_points(dim, u, pts, w);
+  int neq = (dim == 2) ? 5 : 6;
+  for (int j = 0; j < neq; j++) {
+    const int* alpha = (dim == 2) ? tri_alpha[j] : tet_alpha[j];
+    ld s = 0.0L;
+    for (int q = 0; q < n; q++) s += w[q] * mono(dim, alpha, pts[q]);
+    res[j] = s - mono_exact(dim, alpha);
+  }
+}
+
+static int dense_solve_ld(int n, ld* A, ld* b) {
+  for (int k = 0; k < n; k++) {
+    int piv = k;
+    for (int i = k + 1; i < n; i++)
+      if (fabsl(A[i * n + k]) > fabsl(A[piv * n + k])) piv = i;
+    if (A[piv * n + k] == 0.0L) return -1;
+    for (int j = 0; j < n; j++) {
+      ld t = A[k * n + j];
+      A[k * n + j] = A[piv * n + j];
+      A[piv * n + j] = t;
+    }
+    ld t = b[k];
+    b[k] = b[piv];
+    b[piv] = t;
+    for (int i = k + 1; i < n; i++) {
+      ld f = A[i * n + k] / A[k * n + k];
+      for (int j = k; j < n; j++) A[i * n + j] -= f * A[k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    ld s = b[i];
+    for (int j = i + 1; j < n; j++) s -= A[i * n + j] * b[j];
+    b[i] = s / A[i * n + i];
+  }
+  return 0;
+}
+
+int or_quad_rule(int dim, double* bary, double* w) {
+  /* Starting points near the positive interior solution; Newton's method with a
+   * central-difference Jacobian then solves the moment equations. */
+  ld u[6];
+  int nu;
+  if (dim == 2) {
+    ld u0[5] = {0.22L, 0.13L, 0.10L, 0.13L, 0.47L};
+    memcpy(u, u0, sizeof u0);
+    nu = 5;
+  } else if (dim == 3) {
+    ld u0[6] = {0.07L, 0.09L, 0.11L, 0.31L, 0.04L, 0.045L};
+    memcpy(u, u0, sizeof u0);
+    nu = 6;
+  } else {
+    return -1;
+  }
+  ld res[6], rp[6], rm[6], J[36];
+  for (int it = 0; it < 60; it++) {
+    rule_residual(dim, u, res);
+    for (int c = 0; c < nu; c++) {
+      ld save = u[c], hstep = 1e-9L;
+      u[c] = save + hstep;
+      rule_residual(dim, u, rp);
+      u[c] = save - hstep;
+      rule_residual(dim, u, rm);
+      u[c] = save;
+      for (int j = 0; j < nu; j++) J[j * nu + c] = (rp[j] - rm[j]) / (2.0L * hstep);
+    }
+    for (int j = 0; j < nu; j++) res[j] = -res[j];
+    if (dense_solve_ld(nu, J, res) != 0) return -1;
+    for (int c = 0; c < nu; c++) u[c] += res[c];
+  }
+  rule_residual(dim, u, res);
+  ld nr = 0.0L;
+  for (int j = 0; j < nu; j++) nr += fabsl(res[j]);
+  if (!(nr < 1e-17L)) return -1;
+  ld pts[16][4], ww[16];
+  int n = rule_points(dim, u, pts, ww);
+  for (int q = 0; q < n; q++) {
+    if (!(ww[q] > 0.0L)) return -1;
+    for (int k = 0; k <= dim; k++) {
+      if (!(pts[q][k] > 0.0L && pts[q][k] < 1.0L)) return -1;
+      bary[q * (dim + 1) + k] = (double)pts[q][k];
+    }
+    w[q] = (double)ww[q];
+  }
+  return n;
+}
+
+/* Dense Gaussian elimination with partial pivoting; solves A x = b in place (b -> x). */
+static int dense_solve(int n, double* A, double* b) {
+  for (int k = 0; k < n; k++) {
+    int piv = k;
+    for (int i = k + 1; i < n; i++)
+      if (fabs(A[(size_t)i * n + k]) > fabs(A[(size_t)piv * n + k])) piv = i;
+    if (A[(size_t)piv * n + k] == 0.0) return -1;
+    if (piv != k) {
+      for (int j = 0; j < n; j++) {
+        double t = A[(size_t)k * n + j];
+        A[(size_t)k * n + j] = A[(size_t)piv * n + j];
+        A[(size_t)piv * n + j] = t;
+      }
+      double t = b[k];
+      b[k] = b[piv];
+      b[piv] = t;
+    }
+    for (int i = k + 1; i < n; i++) {
+      double f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      if (f == 0.0) continue;
+      for (int j = k; j < n; j++) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    double s = b[i];
+    for (int j = i + 1; j < n; j++) s -= A[(size_t)i * n + j] * b[j];
+    b[i] = s / A[(size_t)i * n + i];
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Sec. 5.1: approximate distances between the bounding boxes of E_l (lo1, hi1) and
+ * E_m (lo2, hi2): d1^k = x^k_min - y^k_max, d2^k = y^k_min - x^k_max. */
+double or_aprx_max_dist(int dim, const double* lo1, const double* hi1, const double* lo2,
+                        const double* hi2) {
+  double s = 0.0;
+  for (int k = 0; k < dim; k++) { /* eq. (maxdist) */
+    double d1 = lo1[k] - hi2[k];
+    double d2 = lo2[k] - hi1[k];
+    double a = d1 * d1, b = d2 * d2;
+    s += (a > b) ? a : b;
+  }
+  return sqrt(s);
+}
+
+double or_aprx_min_dist(int dim, const double* lo1, const double* hi1, const double* lo2,
+                        const double* hi2) {
+  double m = 0.0;
+  for (int k = 0; k < dim; k++) { /* eq. (mindist) */
+    double d1 = lo1[k] - hi2[k];
+    double d2 = lo2[k] - hi1[k];
+    double t = (d1 > d2) ? d1 : d2;
+    if (t > m) m = t;
+  }
+  return m;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Mesh helpers. */
+static void elem_verts(const or_mesh* M, int64_t e, double V[4][3]) {
+  int nv = M->dim + 1;
+  for (int a = 0; a < nv; a++) {
+    int64_t v = M->conn[e * nv + a];
+    for (int k = 0; k < 3; k++) V[a][k] = (k < M->dim) ? M->coords[k * M->n_vert + v] : 0.0;
+  }
+}
+
+static void verts_bbox(int dim, const double V[4][3], double* lo, double* hi) {
+  for (int k = 0; k < dim; k++) {
+    lo[k] = V[0][k];
+    hi[k] = V[0][k];
+    for (int a = 1; a <= dim; a++) {
+      if (V[a][k] < lo[k]) lo[k] = V[a][k];
+      if (V[a][k] > hi[k]) hi[k] = V[a][k];
+    }
+  }
+}
+
+/* |det[v1-v0, ..., vn-v0]| / n! */
+static double simplex_volume(int dim, const double V[4][3]) {
+  if (dim == 2) {
+    double a = V[1][0] - V[0][0], b = V[2][0] - V[0][0];
+    double c = V[1][1] - V[0][1], d = V[2][1] - V[0][1];
+    return fabs(a * d - b * c) / 2.0;
+  }
+  double m[3][3];
+  for (int i = 0; i < 3; i++)
+    for (int k = 0; k < 3; k++) m[k][i] = V[i + 1][k] - V[0][k];
+  double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+               m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+               m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+  return fabs(det) / 6.0;
+}
+
+/* P1 basis of the simplex V at x: the barycentric coordinates, from Cramer's rule on
+ * sum_{a>=1} lambda_a (v_a - v_0) = x - v_0. */
+static void barycentric(int dim, const double V[4][3], const double* x, double* lam) {
+  if (dim == 2) {
+    double a = V[1][0] - V[0][0], b = V[2][0] - V[0][0];
+    double c = V[1][1] - V[0][1], d = V[2][1] - V[0][1];
+    double rx = x[0] - V[0][0], ry = x[1] - V[0][1];
+    double det = a * d - b * c;
+    lam[1] = (rx * d - b * ry) / det;
+    lam[2] = (a * ry - rx * c) / det;
+    lam[0] = 1.0 - lam[1] - lam[2];
+    return;
+  }
+  double m[3][3], r[3];
+  for (int i = 0; i < 3; i++) {
+    for (int k = 0; k < 3; k++) m[k][i] = V[i + 1][k] - V[0][k];
+    r[i] = x[i] - V[0][i];
+  }
+  double det = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+               m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+               m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+  for (int c = 0; c < 3; c++) {
+    double mc[3][3];
+    for (int i = 0; i < 3; i++)
+      for (int k = 0; k < 3; k++) mc[i][k] = (k == c) ? r[i] : m[i][k];
+    double dc = mc[0][0] * (mc[1][1] * mc[2][2] - mc[1][2] * mc[2][1]) -
+                mc[0][1] * (mc[1][0] * mc[2][2] - mc[1][2] * mc[2][0]) +
+                mc[0][2] * (mc[1][0] * mc[2][1] - mc[1][1] * mc[2][0]);
+    lam[c + 1] = dc / det;
+  }
+  lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+}
+
+static void midpoint(const double* a, const double* b, double* out) {
+  for (int k = 0; k < 3; k++) out[k] = (a[k] + b[k]) * 0.5;
+}
+
+/* Midpoint refinement into 2^N children (Sec. 5).  Triangle: the three corner triangles
+ * and the middle one.  Tetrahedron: Bey's rule, interior octahedron cut along the
+ * diagonal x02-x13. */
+static void split(int dim, const double V[4][3], double C[8][4][3]) {
+  if (dim == 2) {
+    double m01[3], m02[3], m12[3];
+    midpoint(V[0], V[1], m01);
+    midpoint(V[0], V[2], m02);
+    midpoint(V[1], V[2], m12);
+    const double* ch[4][3] = {{V[0], m01, m02}, {m01, V[1], m12}, {m02, m12, V[2]}, {m01, m12, m02}};
+    for (int c = 0; c < 4; c++)
+      for (int a = 0; a < 3; a++)
+        for (int k = 0; k < 3; k++) C[c][a][k] = ch[c][a][k];
+    return;
+  }
+  double x01[3], x02[3], x03[3], x12[3], x13[3], x23[3];
+  midpoint(V[0], V[1], x01);
+  midpoint(V[0], V[2], x02);
+  midpoint(V[0], V[3], x03);
+  midpoint(V[1], V[2], x12);
+  midpoint(V[1], V[3], x13);
+  midpoint(V[2], V[3], x23);
+  const double* ch[8][4] = {{V[0], x01, x02, x03}, {x01, V[1], x12, x13}, {x02, x12, V[2], x23},
+                            {x03, x13, x23, V[3]}, {x01, x02, x03, x13}, {x01, x02, x12, x13},
+                            {x02, x03, x13, x23},  {x02, x12, x13, x23}};
+  for (int c = 0; c < 8; c++)
+    for (int a = 0; a < 4; a++)
+      for (int k = 0; k < 3; k++) C[c][a][k] = ch[c][a][k];
+}
+
+/* ------------------------------------------------------------------------------------
+ * Eq. (k_l): the element pairs. */
+int64_t or_pairs(const or_mesh* M, double delta, double eps, int64_t* pair_off, int32_t* pair_l,
+                 int64_t cap) {
+  int dim = M->dim;
+  int64_t n = M->n_elem;
+  double* lo = (double*)malloc(sizeof(double) * 3 * n);
+  double* hi = (double*)malloc(sizeof(double) * 3 * n);
+  if (!lo || !hi) {
+    free(lo);
+    free(hi);
+    return -1;
+  }
+  for (int64_t e = 0; e < n; e++) {
+    double V[4][3];
+    elem_verts(M, e, V);
+    verts_bbox(dim, V, lo + 3 * e, hi + 3 * e);
+  }
+  double reach = delta + eps;
+  int64_t cnt = 0;
+  for (int64_t m = 0; m < n; m++) {
+    pair_off[m] = cnt;
+    for (int64_t l = 0; l < n; l++) {
+      if (or_aprx_min_dist(dim, lo + 3 * l, hi + 3 * l, lo + 3 * m, hi + 3 * m) < reach) {
+        if (cnt < cap) pair_l[cnt] = (int32_t)l;
+        cnt++;
+      }
+    }
+  }
+  pair_off[n] = cnt;
+  free(lo);
+  free(hi);
+  return cnt;
+}
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* The entries (i, j) that Eqs. (J21Nr), (J22Nr) can touch: i a node of m, j a node of m or
+ * of l, (m, l) in J (l = m is in J, so the nodes of m are included). */
+int64_t or_csr(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l, int64_t* row_ptr,
+               int32_t* col, int64_t cap) {
+  int nv = M->dim + 1;
+  int64_t nV = M->n_vert, nE = M->n_elem;
+  /* node -> elements */
+  int64_t* deg = (int64_t*)calloc(nV + 1, sizeof(int64_t));
+  int64_t* n2e = (int64_t*)malloc(sizeof(int64_t) * nE * nv + 1);
+  int64_t* fillp = (int64_t*)malloc(sizeof(int64_t) * (nV + 1));
+  int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * nV);
+  int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * nV);
+  if (!deg || !n2e || !fillp || !mark || !buf) {
+    free(deg), free(n2e), free(fillp), free(mark), free(buf);
+    return -1;
+  }
+  for (int64_t e = 0; e < nE; e++)
+    for (int a = 0; a < nv; a++) deg[M->conn[e * nv + a] + 1]++;
+  for (int64_t v = 0; v < nV; v++) deg[v + 1] += deg[v];
+  for (int64_t v = 0; v <= nV; v++) fillp[v] = deg[v];
+  for (int64_t e = 0; e < nE; e++)
+    for (int a = 0; a < nv; a++) n2e[fillp[M->conn[e * nv + a]]++] = e;
+  for (int64_t v = 0; v < nV; v++) mark[v] = -1;
+  int64_t nnz = 0;
+  for (int64_t i = 0; i < nV; i++) {
+    row_ptr[i] = nnz;
+    int64_t cnt = 0;
+    for (int64_t t = deg[i]; t < deg[i + 1]; t++) {
+      int64_t m = n2e[t];
+      for (int64_t p = pair_off[m]; p < pair_off[m + 1]; p++) {
+        int64_t l = pair_l[p];
+        for (int c = 0; c < nv; c++) {
+          int32_t j = M->conn[l * nv + c];
+          if (mark[j] != i) {
+            mark[j] = i;
+            buf[cnt++] = j;
+          }
+        }
+      }
+    }
+    qsort(buf, (size_t)cnt, sizeof(int32_t), cmp_i32);
+    if (col && nnz + cnt <= cap) memcpy(col + nnz, buf, sizeof(int32_t) * cnt);
+    nnz += cnt;
+  }
+  row_ptr[nV] = nnz;
+  free(deg), free(n2e), free(fillp), free(mark), free(buf);
+  return nnz;
+}
+
+static double* csr_entry(const int64_t* row_ptr, const int32_t* col, double* values, int64_t i,
+                         int32_t j) {
+  int64_t lo = row_ptr[i], hi = row_ptr[i + 1] - 1;
+  while (lo <= hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (col[mid] == j) return values + mid;
+    if (col[mid] < j) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return NULL;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Sec. 5: Algorithm 1 and the element sums (J21Nr), (J22Nr). */
+typedef struct {
+  const or_mesh* M;
+  const or_params* P;
+  int dim, nv, nq;
+  double qb[16][4], qw[16];
+  const double* lo; /* element boxes (3 per element) */
+  const double* hi;
+  int64_t l;
+  double Vl[4][3];
+  const int64_t* row_ptr;
+  const int32_t* col;
+  double* values;
+  or_stats* st;
+  int error;
+} actx;
+
+/* Integration(E', J'): for every m in J', Q2 on the sub-element E' (outer variable x, test
+ * functions of l) and Q1 on E_m (inner variable y).  Adds
+ *   2 A^22_ij : 2 sum w_x w_y gamma_eps(x,y) phi^m_i(y) phi^m_j(y)     (eq. J22Nr)
+ *   2 A^21_ij : -2 sum w_x w_y gamma_eps(x,y) phi^m_i(y) phi^l_j(x)    (eq. J21Nr; the minus
+ *              sign of eq. J21 is restored, it is missing in the discrete version)
+ * The finite sum over (x, m, y) is accumulated per m into the local blocks S (i, j in m)
+ * and X (i in m, j in l) before it is added to A. */
+static void integration(actx* c, const double E[4][3], const int32_t* J, int64_t nJ) {
+  int dim = c->dim, nv = c->nv, nq = c->nq;
+  const or_params* P = c->P;
+  double vol = simplex_volume(dim, E);
+  double xq[16][3], wx[16], phil[16][4];
+  for (int q = 0; q < nq; q++) {
+    for (int k = 0; k < 3; k++) {
+      double s = 0.0;
+      for (int v = 0; v < nv; v++) s += c->qb[q][v] * E[v][k];
+      xq[q][k] = s;
+    }
+    wx[q] = c->qw[q] * vol;
+    barycentric(dim, c->Vl, xq[q], phil[q]);
+  }
+  for (int64_t t = 0; t < nJ; t++) {
+    int64_t m = J[t];
+    double Vm[4][3];
+    elem_verts(c->M, m, Vm);
+    double volm = simplex_volume(dim, Vm);
+    double S[4][4] = {{0}}, X[4][4] = {{0}};
+    for (int q = 0; q < nq; q++) {
+      for (int p = 0; p < nq; p++) {
+        double y[3];
+        for (int k = 0; k < 3; k++) {
+          double s = 0.0;
+          for (int v = 0; v < nv; v++) s += c->qb[p][v] * Vm[v][k];
+          y[k] = s;
+        }
+        double wy = c->qw[p] * volm;
+        double r2 = 0.0;
+        for (int k = 0; k < dim; k++) r2 += (xq[q][k] - y[k]) * (xq[q][k] - y[k]);
+        double r = sqrt(r2);
+        double G = wx[q] * wy * P->C * or_eta(P->kernel, r, P->delta) * or_mu(r, P->delta, P->eps);
+        c->st->n_point_pairs++;
+        if (r >= P->delta - P->eps && r <= P->delta + P->eps) c->st->n_band_pairs++;
+        for (int a = 0; a < nv; a++) {
+          double phia = c->qb[p][a]; /* phi^m_a(y_p): barycentric coordinate of y_p in E_m */
+          for (int b = 0; b < nv; b++) S[a][b] += G * phia * c->qb[p][b];
+          for (int d = 0; d < nv; d++) X[a][d] += G * phia * phil[q][d];
+        }
+      }
+    }
+    c->st->n_integrations++;
+    for (int a = 0; a < nv; a++) {
+      int64_t i = c->M->conn[m * nv + a];
+      for (int b = 0; b < nv; b++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * nv + b]);
+        if (!e) {
+          c->error = 1;
+          continue;
+        }
+        *e += 2.0 * S[a][b];
+      }
+      for (int d = 0; d < nv; d++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * nv + d]);
+        if (!e) {
+          c->error = 1;
+          continue;
+        }
+        *e -= 2.0 * X[a][d];
+      }
+    }
+  }
+}
+
+/* Algorithm 1, Adaptive Integration(L_min, L_max, L_cur, E_l, J_l). */
+static void adaptive_integration(actx* c, int L_cur, const double E[4][3], const int32_t* J,
+                                 int64_t nJ) {
+  const or_params* P = c->P;
+  int dim = c->dim;
+  int nchild = (dim == 2) ? 4 : 8;
+  if (L_cur < P->L_min) {
+    double C[8][4][3];
+    split(dim, E, C);
+    for (int i = 0; i < nchild; i++) adaptive_integration(c, L_cur + 1, C[i], J, nJ);
+    return;
+  }
+  if (L_cur == P->L_max) {
+    integration(c, E, J, nJ);
+    return;
+  }
+  int32_t* Jint = (int32_t*)malloc(sizeof(int32_t) * (nJ + 1));
+  int32_t* Jref = (int32_t*)malloc(sizeof(int32_t) * (nJ + 1));
+  if (!Jint || !Jref) {
+    free(Jint), free(Jref);
+    c->error = 1;
+    return;
+  }
+  int64_t nint = 0, nref = 0;
+  double lo[3], hi[3];
+  verts_bbox(dim, E, lo, hi);
+  for (int64_t t = 0; t < nJ; t++) {
+    int64_t m = J[t];
+    if (or_aprx_max_dist(dim, lo, hi, c->lo + 3 * m, c->hi + 3 * m) < P->delta - P->eps)
+      Jint[nint++] = (int32_t)m;
+    else if (or_aprx_min_dist(dim, lo, hi, c->lo + 3 * m, c->hi + 3 * m) < P->delta + P->eps)
+      Jref[nref++] = (int32_t)m;
+  }
+  if (nint > 0) integration(c, E, Jint, nint);
+  if (nref > 0) {
+    double C[8][4][3];
+    split(dim, E, C);
+    for (int i = 0; i < nchild; i++) adaptive_integration(c, L_cur + 1, C[i], Jref, nref);
+  }
+  free(Jint);
+  free(Jref);
+}
+
+int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l,
+                const or_params* P, const int64_t* row_ptr, const int32_t* col, double* values,
+                const uint8_t* m_mask, or_stats* stats) {
+  int dim = M->dim, nv = dim + 1;
+  int64_t nE = M->n_elem, nV = M->n_vert;
+  if (dim != 2 && dim != 3) return -1;
+  if (!(P->eps > 0.0 && P->eps < P->delta) || P->L_min < 1 || P->L_max < P->L_min) return -1;
+  actx c;
+  memset(&c, 0, sizeof c);
+  c.M = M;
+  c.P = P;
+  c.dim = dim;
+  c.nv = nv;
+  double bary[64], w[16];
+  c.nq = or_quad_rule(dim, bary, w);
+  if (c.nq <= 0) return -1;
+  for (int q = 0; q < c.nq; q++) {
+    for (int v = 0; v < nv; v++) c.qb[q][v] = bary[q * nv + v];
+    c.qw[q] = w[q];
+  }
+  double* lo = (double*)malloc(sizeof(double) * 3 * nE);
+  double* hi = (double*)malloc(sizeof(double) * 3 * nE);
+  /* J_l: the transpose of the m-major pair lists, restricted to the selected m. */
+  int64_t* toff = (int64_t*)calloc(nE + 1, sizeof(int64_t));
+  int64_t* fillp = (int64_t*)malloc(sizeof(int64_t) * (nE + 1));
+  int64_t np = pair_off[nE];
+  int32_t* tm = (int32_t*)malloc(sizeof(int32_t) * (np + 1));
+  if (!lo || !hi || !toff || !fillp || !tm) {
+    free(lo), free(hi), free(toff), free(fillp), free(tm);
+    return -1;
+  }
+  for (int64_t e = 0; e < nE; e++) {
+    double V[4][3];
+    elem_verts(M, e, V);
+    verts_bbox(dim, V, lo + 3 * e, hi + 3 * e);
+  }
+  for (int64_t m = 0; m < nE; m++) {
+    if (m_mask && !m_mask[m]) continue;
+    for (int64_t p = pair_off[m]; p < pair_off[m + 1]; p++) toff[pair_l[p] + 1]++;
+  }
+  for (int64_t l = 0; l < nE; l++) toff[l + 1] += toff[l];
+  for (int64_t l = 0; l <= nE; l++) fillp[l] = toff[l];
+  for (int64_t m = 0; m < nE; m++) { /* m ascending, so every J_l is sorted */
+    if (m_mask && !m_mask[m]) continue;
+    for (int64_t p = pair_off[m]; p < pair_off[m + 1]; p++) tm[fillp[pair_l[p]]++] = (int32_t)m;
+  }
+  c.lo = lo;
+  c.hi = hi;
+  c.row_ptr = row_ptr;
+  c.col = col;
+  c.values = values;
+  or_stats local;
+  memset(&local, 0, sizeof local);
+  c.st = &local;
+  memset(values, 0, sizeof(double) * row_ptr[nV]);
+  for (int64_t l = 0; l < nE; l++) {
+    int64_t nJ = toff[l + 1] - toff[l];
+    if (nJ == 0) continue;
+    c.l = l;
+    elem_verts(M, l, c.Vl);
+    adaptive_integration(&c, 1, c.Vl, tm + toff[l], nJ);
+  }
+  if (stats) *stats = local;
+  free(lo), free(hi), free(toff), free(fillp), free(tm);
+  return c.error ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Manufactured solutions (Sec. 6) and f = -L_eps u (Sec. 2, eq. L).  For u = sum_k p(x_k),
+ * a Taylor expansion of p(x_k + z_k) - p(x_k) and the radial symmetry of gamma_eps (odd
+ * moments vanish) give L_eps u = sum_k [p''(x_k) M2 + p''''(x_k) M4 / 12] with
+ * M2 = int z_1^2 gamma_eps, M4 = int z_1^4 gamma_eps, wherever B_{delta+eps}(x) lies
+ * inside the mesh. */
+double or_ms_u(int ms, int dim, const double* x) {
+  double s = (ms == OR_MS_LINEAR) ? 1.0 : 0.0;
+  for (int k = 0; k < dim; k++) {
+    double t = x[k];
+    switch (ms) {
+      case OR_MS_LINEAR: s += t; break;
+      case OR_MS_QUADRATIC: s += t * t; break;
+      case OR_MS_CUBIC: s += t * t * t; break;
+      case OR_MS_QUARTIC: s += t * t * t * t; break;
+      default: return NAN;
+    }
+  }
+  return s;
+}
+
+double or_ms_f(int ms, int dim, const double* x, int kernel, double delta, double eps, double C) {
+  double M2 = or_kernel_moment(dim, kernel, delta, eps, C, 2);
+  double M4 = or_kernel_moment(dim, kernel, delta, eps, C, 4);
+  double Lu = 0.0;
+  for (int k = 0; k < dim; k++) {
+    double t = x[k], p2 = 0.0, p4 = 0.0;
+    switch (ms) {
+      case OR_MS_LINEAR: break;
+      case OR_MS_QUADRATIC: p2 = 2.0; break;
+      case OR_MS_CUBIC: p2 = 6.0 * t; break;
+      case OR_MS_QUARTIC: p2 = 12.0 * t * t; p4 = 24.0; break;
+      default: return NAN;
+    }
+    Lu += p2 * M2 + p4 * M4 / 12.0;
+  }
+  return -Lu;
+}
+
+/* Sec. 2, eqs. (A-F) and (weak-homo), Sec. 4: F_i = int_Omega f phi_i (degree-5 rule on
+ * every element of Omega), then the lifting u = w + g~ moves the constrained columns to
+ * the right-hand side: F~_i = F_i - sum_{k not free} A_ik g(x_k). */
+int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const double* values,
+           int ms, int kernel, double delta, double eps, double C, double* F) {
+  int dim = M->dim, nv = dim + 1;
+  double bary[64], w[16];
+  int nq = or_quad_rule(dim, bary, w);
+  if (nq <= 0) return -1;
+  for (int64_t i = 0; i < M->n_vert; i++) F[i] = 0.0;
+  for (int64_t e = 0; e < M->n_elem; e++) {
+    if (!M->elem_in_omega[e]) continue;
+    double V[4][3];
+    elem_verts(M, e, V);
+    double vol = simplex_volume(dim, V);
+    for (int q = 0; q < nq; q++) {
+      double x[3];
+      for (int k = 0; k < 3; k++) {
+        double s = 0.0;
+        for (int v = 0; v < nv; v++) s += bary[q * nv + v] * V[v][k];
+        x[k] = s;
+      }
+      double f = or_ms_f(ms, dim, x, kernel, delta, eps, C);
+      for (int a = 0; a < nv; a++) {
+        int64_t i = M->conn[e * nv + a];
+        if (M->node_free[i]) F[i] += w[q] * vol * f * bary[q * nv + a];
+      }
+    }
+  }
+  for (int64_t i = 0; i < M->n_vert; i++) {
+    if (!M->node_free[i]) continue;
+    for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; t++) {
+      int64_t j = col[t];
+      if (M->node_free[j]) continue;
+      double xj[3] = {0, 0, 0};
+      for (int k = 0; k < dim; k++) xj[k] = M->coords[k * M->n_vert + j];
+      F[i] -= values[t] * or_ms_u(ms, dim, xj);
+    }
+  }
+  return 0;
+}
+
+int or_solve_dense(const or_mesh* M, const int64_t* row_ptr, const int32_t* col,
+                   const double* values, const double* F, int ms, double* u_h) {
+  int64_t nV = M->n_vert;
+  int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * nV);
+  if (!idx) return -1;
+  int64_t nf = 0;
+  for (int64_t i = 0; i < nV; i++) idx[i] = M->node_free[i] ? nf++ : -1;
+  if (nf > 20000) {
+    free(idx);
+    return -1;
+  }
+  double* A = (double*)calloc((size_t)(nf * nf + 1), sizeof(double));
+  double* b = (double*)malloc(sizeof(double) * (nf + 1));
+  if (!A || !b) {
+    free(idx), free(A), free(b);
+    return -1;
+  }
+  for (int64_t i = 0; i < nV; i++) {
+    if (idx[i] < 0) continue;
+    b[idx[i]] = F[i];
+    for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; t++)
+      if (idx[col[t]] >= 0) A[idx[i] * nf + idx[col[t]]] = values[t];
+  }
+  int rc = dense_solve((int)nf, A, b);
+  for (int64_t i = 0; i < nV; i++) {
+    if (idx[i] >= 0) {
+      u_h[i] = b[idx[i]];
+    } else {
+      double x[3] = {0, 0, 0};
+      for (int k = 0; k < M->dim; k++) x[k] = M->coords[k * nV + i];
+      u_h[i] = or_ms_u(ms, M->dim, x);
+    }
+  }
+  free(idx), free(A), free(b);
+  return rc;
+}
+
+/* ||u - u_h||_{L2}: each element is split twice by midpoints and the degree-5 rule is
+ * applied on every piece. */
+static double err_on(int dim, const double V[4][3], const double* nodal, const double bary[][4],
+                     const double* w, int nq, int ms, const double Vroot[4][3], int depth) {
+  if (depth > 0) {
+    double C[8][4][3];
+    split(dim, V, C);
+    double s = 0.0;
+    for (int i = 0; i < ((dim == 2) ? 4 : 8); i++)
+      s += err_on(dim, C[i], nodal, bary, w, nq, ms, Vroot, depth - 1);
+    return s;
+  }
+  double vol = simplex_volume(dim, V), s = 0.0;
+  for (int q = 0; q < nq; q++) {
+    double x[3];
+    for (int k = 0; k < 3; k++) {
+      double t = 0.0;
+      for (int v = 0; v <= dim; v++) t += bary[q][v] * V[v][k];
+      x[k] = t;
+    }
+    double lam[4];
+    barycentric(dim, Vroot, x, lam);
+    double uh = 0.0;
+    for (int a = 0; a <= dim; a++) uh += lam[a] * nodal[a];
+    double d = or_ms_u(ms, dim, x) - uh;
+    s += w[q] * vol * d * d;
+  }
+  return s;
+}
+
+double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) {
+  int dim = M->dim, nv = dim + 1;
+  double b[64], w[16], bary[16][4];
+  int nq = or_quad_rule(dim, b, w);
+  if (nq <= 0) return NAN;
+  for (int q = 0; q < nq; q++)
+    for (int v = 0; v < nv; v++) bary[q][v] = b[q * nv + v];
+  double s = 0.0;
+  for (int64_t e = 0; e < M->n_elem; e++) {
+    if (omega_only && !M->elem_in_omega[e]) continue;
+    double V[4][3], nodal[4];
+    elem_verts(M, e, V);
+    for (int a = 0; a < nv; a++) nodal[a] = u_h[M->conn[e * nv + a]];
+    s += err_on(dim, V, nodal, (const double(*)[4])bary, w, nq, ms, V, 2);
+  }
+  return sqrt(s);
+}
