@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the nonlocal assembly + solve hot path on one GB300 (or N replicas).
+
+One step = the whole path on the 2D workload at scale (Omega = (0,1)^2, h = 1/256,
+141,512 P1 triangles with the layer, delta = 4h, eps = delta/5, L_max = 4, constant kernel,
+vertices jittered by up to 0.1h, seed 0): element-pair search and CSR pattern, Algorithm 1
+assembly, right-hand side with lifting (u = x^2 + y^2, f = -4) and BiCGStab solve to 1e-10,
+with the mesh resident on the device.  The headline runs the FP32 point-pair path with the
+solve in FP32 inside FP64 iterative refinement ("mixed"); the same step in FP64 is measured
+next to it with the solution error of both against the manufactured solution.
+
+Output: one JSON line (rank 0).  --impl reference times the plain CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("element pairs/s & quad-pt pairs/s, mixed vs FP64 at equal error; "
+          "p50/p99 solve ms")
+WORKLOAD = "c2_2d"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--profile", action="store_true",
+                    help="one pair build and one FP32 and one FP64 assembly of the 2D workload "
+                         "at h=1/128 (a small case for ncu), then exit")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing -------------------------------------------------------------------
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks ----------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.idx = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---- workload --------------------------------------------------------------------------------
+
+def workload(name):
+    from nl_inputs import WORKLOADS, workload_mesh
+    w = WORKLOADS[name]
+    mesh = workload_mesh(w)
+    return w, mesh
+
+
+def u_exact(mesh):
+    return (mesh.coords ** 2).sum(axis=0)  # u = x^2 + y^2 (+ z^2)
+
+
+def l2_err_omega(mesh, u_h, rule):
+    """||u - u_h||_{L2(Omega)} with the degree-5 rule per element (u = sum x_k^2)."""
+    b, w = rule
+    P = mesh.points()
+    conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
+    V = P[conn]  # (ne, nv, dim)
+    if mesh.dim == 2:
+        vol = 0.5 * np.abs((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1]) -
+                           (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
+    else:
+        vol = np.abs(np.linalg.det(V[:, 1:] - V[:, :1])) / 6.0
+    X = np.einsum("qv,evk->eqk", b, V)
+    uh = np.einsum("qv,ev->eq", b, u_h[conn])
+    d = (X ** 2).sum(-1) - uh
+    return float(math.sqrt(np.sum(vol[:, None] * w[None, :] * d * d)))
+
+
+# ---- our implementation ----------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2101_08825_gb300 import nl
+    from paper_2101_08825_gb300.build import build
+
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build()
+    barrier(world)
+    nl.lib()
+    stream = torch.cuda.current_stream()
+    w, mesh = workload(args.workload)
+    delta, eps, L_max = w.delta, w.eps, w.L_max
+    g = u_exact(mesh)
+    f_const = -2.0 * mesh.dim
+    rule = nl.nl_quad_rule(mesh.dim)
+    flush = torch.empty(int(256 * 2 ** 20) // 4, dtype=torch.float32, device="cuda")
+
+    dmesh = nl.mesh_from(mesh)
+
+    def step(prec, keep=False):
+        p = nl.nl_pairs_build(dmesh, delta, eps)
+        A, st = nl.nl_assemble(dmesh, p, delta, eps, L_max, precision=prec)
+        b = nl.nl_rhs(dmesh, A, g, f_const=f_const)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        u, it, rr, _ = nl.nl_solve(A, b, g, solver=1, rtol=1e-10, max_iter=20000,
+                                   precision=nl.NL_PREC_FP32 if prec != nl.NL_PREC_FP64 else nl.NL_PREC_FP64)
+        t1.record(stream)
+        t1.synchronize()
+        res = dict(st=st, u=u, it=it, rr=rr, solve_ms=t0.elapsed_time(t1))
+        if keep:
+            res["A"] = A.export()
+        return res
+
+    def timed(prec, steps, warmup):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize()
+        times, solve_ms, kern_ms, last = [], [], [], None
+        launches0 = nl.lib().nl_launch_count()
+        for _ in range(steps):
+            flush.zero_()  # L2 flush (256 MB > 129 MB L2) between steps, outside the timing
+            barrier(world)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step(prec)
+            e1.record(stream)
+            e1.synchronize()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            solve_ms.append(last["solve_ms"])
+            kern_ms.append(last["st"].ms_assemble)
+        launches = nl.lib().nl_launch_count() - launches0
+        return times, solve_ms, kern_ms, last, launches
+
+    # mixed headline (timed with clock sampling)
+    clk = ClockSampler(local)
+    clk.start()
+    times, solve_ms, kern_ms, last, launches = timed(nl.NL_PREC_FP32, args.steps, args.warmup)
+    clocks = clk.stop()
+    ms = statistics.mean(times)
+    ms_max = allmax(world, ms)
+    st = last["st"]
+    n_pairs, n_pp = st.n_pairs, st.n_point_pairs
+    value = world * n_pairs / (ms_max / 1e3)
+    err_mixed = l2_err_omega(mesh, last["u"], rule)
+
+    # FP64 path, same step
+    t64, s64, k64, last64, _ = timed(nl.NL_PREC_FP64, max(1, args.fp64_steps), 1)
+    ms64 = statistics.mean(t64)
+    err64 = l2_err_omega(mesh, last64["u"], rule)
+
+    # matrix difference mixed vs FP64 (one extra untimed assembly each)
+    r32 = step(nl.NL_PREC_FP32, keep=True)["A"]
+    r64 = step(nl.NL_PREC_FP64, keep=True)["A"]
+    a_rel = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
+
+    # roofline of the dominant kernel (FP32 assembly kernel): algorithmic flops per launch
+    kern_avg = statistics.mean(kern_ms)
+    flops = roofline_flops(mesh.dim, st)
+    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
+    achieved = flops / (kern_avg / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 1),
+            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
+            "kernel": "k_quad<2,float,0>", "flops_per_launch": flops,
+            "kernel_ms_avg": round(kern_avg, 3)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "element pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{w.name}: 2D unit square, h=1/256, {mesh.n_elem} P1 triangles "
+                               f"(131072 in Omega), delta=4h, eps=delta/5, L_max=4, constant kernel, "
+                               f"jitter 0.1h seed 0; u=x^2+y^2; BiCGStab to 1e-10",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "working set > L2 and a 256 MB L2 flush between steps"},
+        "quad_pt_pairs_per_s": round(world * n_pp / (ms_max / 1e3), 1),
+        "assembly_kernel": {"ms": round(kern_avg, 3),
+                            "element_pairs_per_s": round(n_pairs / (kern_avg / 1e3), 1),
+                            "quad_pt_pairs_per_s": round(n_pp / (kern_avg / 1e3), 1)},
+        "counts": {"element_pairs": n_pairs, "quad_pt_pairs": n_pp, "items": st.n_items,
+                   "fp64_rechecks": st.n_exact_checks},
+        "fp64": {"dtype": "f64", "ms_per_step": round(ms64, 3),
+                 "value": round(world * n_pairs / (ms64 / 1e3), 1),
+                 "assembly_kernel_ms": round(statistics.mean(k64), 3),
+                 "l2_err_omega": err64},
+        "mixed": {"l2_err_omega": err_mixed, "A_rel_frobenius_vs_fp64": a_rel,
+                  "solve_iters": last["it"], "speedup_vs_fp64": round(ms64 / ms, 2)},
+        "solve_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
+                     "p99": round(float(np.percentile(solve_ms, 99)), 3)},
+        "roofline": roof,
+        "gpu_launches": int(launches / max(1, args.steps)),
+        "clocks": clocks,
+    }
+    if not args.no_e2e:
+        out["e2e"] = e2e_ours(args, mesh, w, g, f_const, stream, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(mesh, w, seconds=15.0)
+    return out
+
+
+def roofline_flops(dim, st):
+    """Algorithmic FP32 flops of one assembly launch (FMA = 2): per evaluated point pair the
+    squared distance (2D 5, 3D 8), the weight product (1) and the accumulation into g and the
+    dim barycentric moments (1 + 2*dim); per outer point of a mu = 1 item of the constant
+    kernel the same accumulation once (1 + 2*dim) for all inner points."""
+    ev = getattr(st, "n_eval_point_pairs", 0) or 0
+    un = getattr(st, "n_uniform_points", 0) or 0
+    if ev == 0 and un == 0:
+        ev = st.n_point_pairs
+    per_pp = (5 if dim == 2 else 8) + 1 + 1 + 2 * dim
+    return float(ev * per_pp + un * (1 + 2 * dim))
+
+
+def e2e_ours(args, mesh, w, g, f_const, stream, world):
+    """Public-API step from pinned host buffers: mesh upload, pairs, assembly, right-hand
+    side, solve and the solution read back, all inside the timed region."""
+    import torch
+    from paper_2101_08825_gb300 import nl
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    coords, conn = pinned(mesh.coords), pinned(mesh.conn)
+    eio, nf, gp = pinned(mesh.elem_in_omega), pinned(mesh.node_free), pinned(g)
+    times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dm = nl.nl_mesh_create(mesh.dim, coords, conn, eio, nf)
+        p = nl.nl_pairs_build(dm, w.delta, w.eps)
+        A, st = nl.nl_assemble(dm, p, w.delta, w.eps, w.L_max, precision=nl.NL_PREC_FP32)
+        b = nl.nl_rhs(dm, A, gp, f_const=f_const)
+        u, it, rr, _ = nl.nl_solve(A, b, gp, solver=1, rtol=1e-10, max_iter=20000,
+                                   precision=nl.NL_PREC_FP32)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+        n_pairs = st.n_pairs
+    ms = allmax(world, statistics.mean(times))
+    h2d = coords.nbytes + conn.nbytes + eio.nbytes + nf.nbytes + 2 * gp.nbytes
+    d2h = u.nbytes
+    return {"value": round(world * n_pairs / (ms / 1e3), 1), "unit": "element pairs/s",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
+
+
+# ---- the oracle on a bounded sample ------------------------------------------------------------
+
+def oracle_sample(mesh, w, n_m, seed=0):
+    """Times the oracle's pair search, pattern and Algorithm 1 assembly for the rows of n_m
+    seeded inner elements of the workload; returns (pairs, point pairs, seconds)."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    mask = np.zeros(mesh.n_elem, np.uint8)
+    mask[rng.choice(mesh.n_elem, size=n_m, replace=False)] = 1
+    om = O.OMesh(mesh)
+    t0 = time.perf_counter()
+    off, pl = O.pairs(om, w.delta, w.eps, m_mask=mask)
+    rp, col = O.csr(om, off, pl)
+    vals, st = O.assemble(om, off, pl, rp, col, w.delta, w.eps, w.L_max, w.L_min, w.kernel,
+                          m_mask=mask)
+    dt = time.perf_counter() - t0
+    return len(pl), st.n_point_pairs, dt
+
+
+def cpu_baseline(mesh, w, seconds=15.0):
+    import oracle as O
+    O.build()
+    n_p, n_pp, dt = oracle_sample(mesh, w, 8)
+    n_m = int(max(8, min(mesh.n_elem, 8 * seconds / max(dt, 1e-3))))
+    n_p, n_pp, dt = oracle_sample(mesh, w, n_m, seed=1)
+    return {"value": round(n_p / dt, 1), "unit": "element pairs/s", "cores": 1, "kind": "oracle",
+            "sample": f"pairs, pattern and Algorithm-1 assembly of the rows of {n_m} seeded "
+                      f"inner elements of the workload ({n_p} element pairs, {n_pp} quad-pt "
+                      f"pairs, {dt:.1f} s single-threaded FP64)",
+            "quad_pt_pairs_per_s": round(n_pp / dt, 1)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle as O
+    O.build()
+    w, mesh = workload(args.workload)
+    n_p, n_pp, dt = oracle_sample(mesh, w, 4)
+    n_m = int(max(4, min(mesh.n_elem, 4 * 6.0 / max(dt, 1e-3))))  # ~6 s per step
+    for _ in range(args.warmup):
+        oracle_sample(mesh, w, max(4, n_m // 8), seed=99)
+    times, pairs = [], []
+    for k in range(args.steps):
+        n_p, n_pp, dt = oracle_sample(mesh, w, n_m, seed=k)
+        times.append(dt)
+        pairs.append(n_p)
+    value = sum(pairs) / sum(times)
+    sample = (f"each step: pairs, pattern and Algorithm-1 assembly of the rows of {n_m} seeded "
+              f"inner elements of {w.name}")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1),
+            "unit": "element pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "parallelism": "single CPU core"},
+            "cpu_baseline": {"value": round(value, 1), "unit": "element pairs/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": "element pairs/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_profile_case():
+    import torch
+    from paper_2101_08825_gb300 import nl
+    from paper_2101_08825_gb300.build import build
+    build()
+    w, mesh = workload("c2_2d_h128")
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, w.delta, w.eps)
+    for prec in (nl.NL_PREC_FP32, nl.NL_PREC_FP64):
+        A, st = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, precision=prec)
+        print(json.dumps({"profile_case": w.name, "precision": prec, "pairs": st.n_pairs,
+                          "point_pairs": st.n_point_pairs, "kernel_ms": st.ms_assemble}))
+    torch.cuda.synchronize()
+
+
+def main():
+    args = parse()
+    if args.profile:
+        run_profile_case()
+        return
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/* nl.h -- C ABI of the GB300 library for finite-element assembly of the mollified
+ * nonlocal diffusion operator of Aulisa, Capodaglio, Chierici, D'Elia, "Efficient
+ * quadrature rules for finite element discretizations of nonlocal equations"
+ * (arXiv 2101.08825), and for the volume-constrained Poisson problem built on it.
+ *
+ * Problem (Sec. 2, eqs. L, poisson, A-F): Omega open and bounded, Gamma the interaction
+ * layer of points within delta of Omega, gamma(x,y) = C eta(|x-y|) 1(|x-y| <= delta)
+ * (eq. gamma).  Sec. 3 (eqs. approx-kernel, mollifier) replaces the indicator by the
+ * C^4 mollifier mu_{delta,eps}(r) = 1 (r < delta-eps), xi((delta-r)/eps) (band),
+ * 0 (r > delta+eps).  Sec. 4 (eq. Aij-support2) defines the P1 stiffness matrix
+ * A_ij = int int (phi_i(x)-phi_i(y))(phi_j(x)-phi_j(y)) gamma_eps(x,y) dy dx, which
+ * Sec. 5 (Corollary 1, eqs. J21Nr, J22Nr) computes as 2 A^21 + 2 A^22: an inner
+ * Gauss rule on element m (rows: the nodes of m) and an outer rule on element l that
+ * Algorithm 1 refines adaptively per (l, m) pair with the box distances of Sec. 5.1.
+ *
+ * Conventions for every entry point:
+ *   - the return value is an nl_status; nothing aborts or throws across the ABI, and on
+ *     failure nl_last_error() returns a message for the calling thread;
+ *   - handles are opaque and owned by the library; destroy them with their *_destroy;
+ *   - host arrays passed in are owned by the caller and are copied before return;
+ *     host arrays passed out are caller-allocated with the documented size;
+ *   - every handle binds the CUDA stream given at mesh creation (NULL = legacy default
+ *     stream); work is enqueued on it and the calls that return host data synchronise it;
+ *   - device memory comes from the allocator installed by nl_set_allocator
+ *     (default: cudaMallocAsync / cudaFreeAsync on the handle's stream).
+ */
+#ifndef NL_H
+#define NL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NL_OK = 0,
+  NL_EINVAL = 1,     /* invalid argument (message in nl_last_error) */
+  NL_ENOMEM = 2,     /* a device or host allocation failed */
+  NL_ECUDA = 3,      /* a CUDA runtime call failed */
+  NL_ENOTCONV = 4,   /* the iterative solver hit max_iter before rtol */
+  NL_ETIMEOUT = 5,   /* a bounded wait ran out */
+  NL_EBUSY = 6,      /* the result is not ready yet (nl_serve_poll) */
+  NL_EINTERNAL = 7   /* a device-side capacity or consistency check failed */
+} nl_status;
+
+typedef enum {
+  NL_KERNEL_CONST = 0,      /* eta = 1 (Sec. 6) */
+  NL_KERNEL_TRUNC_GAUSS = 1 /* eta = exp(-r^2/delta^2) */
+} nl_kernel_kind;
+
+typedef enum {
+  NL_PREC_FP64 = 0,       /* every point pair and every accumulation in FP64 */
+  NL_PREC_MIXED_TF32 = 1, /* gamma_eps in FP32; cross-term contraction on the tensor cores
+                             (TF32 with a split-precision correction, FP32 accumulation) */
+  NL_PREC_MIXED_BF16 = 2, /* as MIXED_TF32 with BF16 operands split in three parts */
+  NL_PREC_FP32 = 3        /* gamma_eps and the per-pair local sums in FP32 on the ALUs */
+} nl_precision;
+
+/* Kernel gamma_eps = C eta mu_{delta,eps}.  Requires 0 < eps < delta (Sec. 3).
+ * C_override = 0 selects C_{delta,eps}: for NL_KERNEL_CONST the closed form of Sec. 6
+ * with kappa = 1, otherwise the value that makes int z_1^2 gamma_eps dz = 1 (so that
+ * L_eps u = Laplace(u) for quadratic u, the property Sec. 6 uses to fix the constant). */
+typedef struct {
+  double delta, eps;
+  double kappa;      /* multiplies C; 0 is read as 1 */
+  int kernel;        /* nl_kernel_kind */
+  double C_override; /* > 0: use this C instead */
+} nl_kernel_params;
+
+/* Algorithm 1 levels, 1 <= L_min <= L_max <= 12 (2D) or 9 (3D).  rule must be 0: the
+ * degree-5 7-point triangle rule (Sec. 6) and the degree-5 14-point tetrahedral rule. */
+typedef struct {
+  int L_min, L_max;
+  int rule;
+} nl_quad_params;
+
+/* Work counters of one assembly. */
+typedef struct {
+  int64_t n_pairs;        /* element pairs |J| */
+  int64_t n_point_pairs;  /* (outer, inner) point pairs of Algorithm 1 */
+  int64_t n_items;        /* (sub-element, m) integrations of Algorithm 1 */
+  int64_t n_exact_checks; /* classifications decided by the FP64 fallback */
+  double ms_assemble;     /* device time of the assembly kernels (CUDA events) */
+  int64_t n_eval_point_pairs; /* point pairs evaluated one by one (the others are either
+                                 beyond delta+eps, or have mu = 1 with a constant kernel and
+                                 are summed once per outer point) */
+  int64_t n_uniform_points;   /* outer points summed once for all inner points (mu = 1,
+                                 constant kernel) */
+} nl_assemble_stats;
+
+typedef struct nl_mesh nl_mesh;
+typedef struct nl_pairs nl_pairs;
+typedef struct nl_matrix nl_matrix;
+typedef struct nl_vector nl_vector;
+typedef struct nl_server nl_server;
+
+/* Allocator hooks: alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, bytes, stream, ctx).  Pass NULLs to restore the default.  Not thread-safe
+ * against concurrent calls; install it before creating handles. */
+typedef void* (*nl_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*nl_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+nl_status nl_set_allocator(nl_alloc_fn alloc, nl_free_fn free_fn, void* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* nl_last_error(void);
+/* Library version string. */
+const char* nl_version(void);
+/* Number of CUDA kernels this library has launched in this process (all threads). */
+int64_t nl_launch_count(void);
+
+/* Mesh of Omega U Gamma (Sec. 4: a triangulation T_h, here P1 triangles (dim 2) or
+ * tetrahedra (dim 3)).
+ *   coords        host, SoA: coords[k*n_vert + v], k < dim (FP64)
+ *   conn          host, (dim+1)*n_elem vertex indices, element-major
+ *   elem_in_omega host, n_elem flags: 1 = element of Omega, 0 = of Gamma
+ *   node_free     host, n_vert flags: 1 = degree of freedom (inside Omega), 0 = value
+ *                 prescribed by the volume constraint u = g (eq. poisson)
+ * Errors: NL_EINVAL for dim not 2/3, empty or >2^31-1 vertices, an index out of range,
+ * a non-finite coordinate or a degenerate element (zero volume). */
+nl_status nl_mesh_create(int dim, int64_t n_vert, const double* coords, int64_t n_elem,
+                         const int32_t* conn, const uint8_t* elem_in_omega,
+                         const uint8_t* node_free, void* cuda_stream, nl_mesh** out);
+
+/* Structured mesh of Omega = prod_k [lo_k, lo_k + cells_k h] with `layer` cells of Gamma on
+ * every side.  Vertices are numbered lexicographically (x fastest) over the grid lines
+ * counted from the outer corner; cells likewise.  Each square (v00 v10 v01 v11) becomes the
+ * triangles (v00, v10, v11), (v00, v11, v01); each cube the 6 Kuhn tetrahedra
+ * (v000, v000+e_a, v000+e_a+e_b, v111) for the axis permutations (a, b, c) in
+ * lexicographic order.  Vertices off the boundary of Omega and off the outer boundary move
+ * by (jitter*h)*(2u-1) per axis, u = splitmix64 output at counter 4*vertex+axis for the
+ * given seed, mapped to [0,1) by its top 53 bits.  cells and lo have dim entries. */
+nl_status nl_mesh_create_box(int dim, const int32_t* cells, double h, const double* lo,
+                             int32_t layer, double jitter, uint64_t seed, void* cuda_stream,
+                             nl_mesh** out);
+nl_status nl_mesh_info(const nl_mesh* mesh, int* dim, int64_t* n_vert, int64_t* n_elem);
+/* Copies the mesh back (host buffers of the sizes of nl_mesh_create; any may be NULL). */
+nl_status nl_mesh_export(const nl_mesh* mesh, double* coords, int32_t* conn,
+                         uint8_t* elem_in_omega, uint8_t* node_free);
+void nl_mesh_destroy(nl_mesh* mesh);
+
+/* Element pairs and sparsity pattern (Sec. 5, eq. k_l; Sec. 5.1 eq. mindist):
+ *   J = {(m, l) : aprx-min-dist(E_l, E_m) < delta + eps}, bounding boxes of the vertices,
+ * stored m-major with l ascending, and the CSR pattern of A: row i (every node) holds the
+ * nodes of every l with (m, l) in J and i a node of m, columns ascending.
+ * Errors: NL_EINVAL unless 0 < eps < delta; NL_EINTERNAL if a neighbourhood exceeds the
+ * builder's shared-memory capacity (more than 49152 pairs for one element or 8192
+ * columns in one row). */
+nl_status nl_pairs_build(nl_mesh* mesh, double delta, double eps, nl_pairs** out);
+nl_status nl_pairs_info(const nl_pairs* pairs, int64_t* n_pairs, int64_t* nnz);
+/* Host copies: pair_off[n_elem+1], pair_l[n_pairs], row_ptr[n_vert+1], col[nnz]; any may
+ * be NULL. */
+nl_status nl_pairs_export(const nl_pairs* pairs, int64_t* pair_off, int32_t* pair_l,
+                          int64_t* row_ptr, int32_t* col);
+void nl_pairs_destroy(nl_pairs* pairs);
+
+/* Stiffness matrix values on the pattern of `pairs` (Sec. 5: Corollary 1, eqs. J21Nr and
+ * J22Nr with Algorithm 1), computed in the given precision.  The int/ref/drop decisions
+ * of Algorithm 1 are bit-identical to a plain FP64 evaluation of eqs. maxdist/mindist on
+ * the sub-element vertices obtained by repeated (a+b)*0.5 midpoints (triangles: corner
+ * children then the middle one; tetrahedra: Bey's rule with the x02-x13 diagonal), in
+ * every precision.  stats may be NULL.  *A is created (or, if *A is a matrix of the same
+ * pattern, overwritten). */
+nl_status nl_assemble(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_params* kp,
+                      const nl_quad_params* qp, nl_precision precision, nl_matrix** A,
+                      nl_assemble_stats* stats);
+/* Host copy of the nnz values (CSR order of the pattern). */
+nl_status nl_matrix_export(const nl_matrix* A, double* values);
+/* Device pointer to the values (valid until nl_matrix_destroy). */
+nl_status nl_matrix_device_values(const nl_matrix* A, double** values);
+void nl_matrix_destroy(nl_matrix* A);
+
+/* Right-hand side with lifting (Sec. 2, eqs. A-F and weak-homo):
+ *   F_i = int_Omega f phi_i for free i, f = f_const + the P1 interpolant of f_nodes
+ *         (f_nodes may be NULL), integrated with the degree-5 rule per element of Omega;
+ *   F~_i = F_i - sum_{k not free} A_ik g_k;  F~_i = 0 for constrained i.
+ * f_nodes, g_nodes: host, n_vert values (g_nodes is read at constrained nodes only). */
+nl_status nl_rhs(nl_mesh* mesh, nl_matrix* A, const double* f_nodes, double f_const,
+                 const double* g_nodes, nl_vector** rhs);
+nl_status nl_vector_export(const nl_vector* v, double* values);
+void nl_vector_destroy(nl_vector* v);
+
+/* Solves A_{free,free} W = F~_free (A is nonsymmetric at quadrature-error level when
+ * L_max > 1, Sec. 5): solver 0 = CG, 1 = BiCGStab.  precision NL_PREC_FP64 runs the Krylov
+ * method in FP64; any other value runs it in FP32 inside FP64 iterative refinement
+ * (residuals r = F~ - A u in FP64).  Stops when ||F~ - A u|| <= rtol ||F~|| (free rows)
+ * or after max_iter iterations (total inner iterations).  u_out: host, n_vert values (free
+ * nodes: W; constrained nodes: g).  iters, final_rel_res may be NULL.
+ * Errors: NL_ENOTCONV when max_iter ran out (u_out still written). */
+nl_status nl_solve(nl_matrix* A, const nl_vector* rhs, const double* g_nodes, int solver,
+                   double rtol, int max_iter, nl_precision precision, double* u_out,
+                   int* iters, double* final_rel_res);
+
+/* ---- host-side tables (no device work; usable without a GPU) ------------------------- */
+/* The degree-5 simplex rule used by the kernels: bary[npts*(dim+1)], w[npts] (sum 1).
+ * Returns the number of points, or -1. */
+int nl_quad_rule(int dim, double* bary, double* w);
+/* C_{delta,eps} as nl_assemble uses it (kappa = 1, no override). */
+double nl_kernel_constant(int dim, int kernel, double delta, double eps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -70,6 +70,7 @@ WORKLOADS = {
     # 2D at scale, h = 1/256, delta = 4h, eps in {delta/5, delta/20}, 4 levels, jitter 0.1h
     "c2_2d": _unit_box("c2_2d", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1),
     "c2_2d_eps20": _unit_box("c2_2d_eps20", 2, 256, 4 * _H2, 4 * _H2 / 20, 4, jitter=0.1),
+    "c2_2d_h128": _unit_box("c2_2d_h128", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1),
     "c2_2d_gauss": _unit_box("c2_2d_gauss", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1,
                              kernel=KERNEL_GAUSS),
     # 3D, h = 1/16, delta = 0.125, eps = delta/10, 2 levels, u = x^2 + y^2 + z^2

@@ -76,7 +76,7 @@ def lib():
         L.or_aprx_min_dist.restype = d
         L.or_aprx_min_dist.argtypes = [i, p, p, p, p]
         L.or_pairs.restype = i64
-        L.or_pairs.argtypes = [ctypes.POINTER(_Mesh), d, d, p, p, i64]
+        L.or_pairs.argtypes = [ctypes.POINTER(_Mesh), d, d, p, p, i64, p]
         L.or_csr.restype = i64
         L.or_csr.argtypes = [ctypes.POINTER(_Mesh), p, p, p, p, i64]
         L.or_assemble.argtypes = [ctypes.POINTER(_Mesh), p, p, ctypes.POINTER(_Params), p, p, p,
@@ -167,15 +167,18 @@ def aprx_min_dist(lo1, hi1, lo2, hi2) -> float:
 
 # ---- pairs, pattern, assembly --------------------------------------------------------
 
-def pairs(mesh, delta: float, eps: float):
-    """m-major element pairs: (pair_off (n_elem+1,), pair_l) with l ascending."""
+def pairs(mesh, delta: float, eps: float, m_mask=None):
+    """m-major element pairs: (pair_off (n_elem+1,), pair_l) with l ascending; with m_mask
+    only the lists of the selected inner elements m are filled."""
     om = _om(mesh)
     n = om.conn.shape[0]
     off = np.zeros(n + 1, dtype=np.int64)
-    cap = max(1024, 64 * n)
+    mm = None if m_mask is None else np.ascontiguousarray(m_mask, dtype=np.uint8)
+    cap = max(1024, (64 * n) if mm is None else 1024 * (int(mm.sum()) + 1))
     while True:
         pl = np.zeros(cap, dtype=np.int32)
-        cnt = lib().or_pairs(ctypes.byref(om.c), delta, eps, _ptr(off), _ptr(pl), cap)
+        cnt = lib().or_pairs(ctypes.byref(om.c), delta, eps, _ptr(off), _ptr(pl), cap,
+                             None if mm is None else _ptr(mm))
         if cnt < 0:
             raise RuntimeError("or_pairs failed")
         if cnt <= cap:

@@ -475,7 +475,7 @@ static void split(int dim, const double V[4][3], double C[8][4][3]) {
 /* ------------------------------------------------------------------------------------
  * Eq. (k_l): the element pairs. */
 int64_t or_pairs(const or_mesh* M, double delta, double eps, int64_t* pair_off, int32_t* pair_l,
-                 int64_t cap) {
+                 int64_t cap, const uint8_t* m_mask) {
   int dim = M->dim;
   int64_t n = M->n_elem;
   double* lo = (double*)malloc(sizeof(double) * 3 * n);
@@ -494,6 +494,7 @@ int64_t or_pairs(const or_mesh* M, double delta, double eps, int64_t* pair_off, 
   int64_t cnt = 0;
   for (int64_t m = 0; m < n; m++) {
     pair_off[m] = cnt;
+    if (m_mask && !m_mask[m]) continue;
     for (int64_t l = 0; l < n; l++) {
       if (or_aprx_min_dist(dim, lo + 3 * l, hi + 3 * l, lo + 3 * m, hi + 3 * m) < reach) {
         if (cnt < cap) pair_l[cnt] = (int32_t)l;

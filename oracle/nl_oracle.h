@@ -74,10 +74,11 @@ double or_aprx_min_dist(int dim, const double* lo1, const double* hi1, const dou
                         const double* hi2);
 
 /* Eq. (k_l): J = {(m, l) : aprx-min-dist(E_l, E_m) < delta + eps}, m-major, l ascending.
- * pair_off has n_elem+1 entries; pair_l has room for cap entries.  Returns the number of
- * pairs (which may exceed cap: then call again with a larger buffer), or -1 on error. */
+ * pair_off has n_elem+1 entries; pair_l has room for cap entries.  m_mask (nullable) keeps
+ * only the lists of the selected m (the others are empty).  Returns the number of pairs
+ * (which may exceed cap: then call again with a larger buffer), or -1 on error. */
 int64_t or_pairs(const or_mesh* M, double delta, double eps, int64_t* pair_off, int32_t* pair_l,
-                 int64_t cap);
+                 int64_t cap, const uint8_t* m_mask);
 
 /* Sparsity of A: row i holds the nodes of every l with (m, l) in J and i a node of m.
  * Returns nnz (row_ptr filled; col filled when cap >= nnz), or -1 on error. */

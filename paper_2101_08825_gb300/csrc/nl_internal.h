@@ -1,0 +1,158 @@
+// nl_internal.h -- internal declarations of the GB300 nonlocal-assembly library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/nl.h"
+
+namespace nlx {
+
+// ---- errors --------------------------------------------------------------------------
+nl_status fail(nl_status st, const char* fmt, ...);
+nl_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define NL_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return ::nlx::cuda_fail(_e, #call); \
+  } while (0)
+
+#define NL_TRY(call)                  \
+  do {                                \
+    nl_status _s = (call);            \
+    if (_s != NL_OK) return _s;       \
+  } while (0)
+
+// ---- kernel launch counter (every launch site wraps its grid size in NL_CNT) ----------
+void count_launch();
+long long launch_count();
+#define NL_CNT(grid) (::nlx::count_launch(), (grid))
+
+// ---- device memory ---------------------------------------------------------------------
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, size_t bytes, cudaStream_t s);
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  nl_status alloc(size_t count, cudaStream_t stream) {
+    release();
+    s = stream;
+    n = count;
+    if (count == 0) return NL_OK;
+    p = static_cast<T*>(dev_alloc(count * sizeof(T), stream));
+    if (!p) {
+      n = 0;
+      return fail(NL_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+    }
+    return NL_OK;
+  }
+  void release() {
+    if (p) dev_free(p, n * sizeof(T), s);
+    p = nullptr;
+    n = 0;
+  }
+  T* release_ownership() {
+    T* q = p;
+    p = nullptr;
+    n = 0;
+    return q;
+  }
+};
+
+// ---- quadrature rules and kernel constants (host) --------------------------------------
+struct Rule {
+  int n = 0;
+  double bary[16][4] = {};
+  double w[16] = {};
+};
+const Rule& rule(int dim);  // degree-5 simplex rule; weights sum to 1
+double kernel_constant(int dim, int kernel, double delta, double eps);
+
+// Uploads the rule tables to the current device once.
+nl_status ensure_device_tables();
+
+// ---- kernels shared between translation units -------------------------------------------
+// Exclusive scan of n int64 counts into out[0..n] (out[n] = total), on stream s.
+nl_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+nl_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+}  // namespace nlx
+
+// ---- handles -------------------------------------------------------------------------------
+struct nl_mesh {
+  std::atomic<int> refs{1};
+  int dim = 0;
+  int64_t n_vert = 0, n_elem = 0;
+  cudaStream_t stream = nullptr;
+  double* coords = nullptr;        // [dim][n_vert]
+  int32_t* conn = nullptr;         // [n_elem][dim+1]
+  uint8_t* elem_in_omega = nullptr;
+  uint8_t* node_free = nullptr;
+  double* evert = nullptr;         // [n_elem][dim+1][dim] vertex coordinates per element
+  double* blo = nullptr;           // [n_elem][dim] bounding boxes
+  double* bhi = nullptr;
+  double* vol = nullptr;           // [n_elem]
+  double* jinv = nullptr;          // [n_elem][dim][dim]: lambda_{1..dim} = jinv (x - v0)
+  int64_t* n2e_off = nullptr;      // [n_vert+1] node -> elements
+  int32_t* n2e = nullptr;          // [(dim+1) n_elem]
+  double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};
+  double max_ext = 0.0;            // largest bounding-box side of an element
+  size_t bytes = 0;
+};
+
+struct nl_pairs {
+  std::atomic<int> refs{1};
+  nl_mesh* mesh = nullptr;
+  double delta = 0.0, eps = 0.0;
+  int64_t n_pairs = 0, nnz = 0;
+  int64_t* pair_off = nullptr;  // [n_elem+1]
+  int32_t* pair_l = nullptr;    // [n_pairs]
+  int64_t* row_ptr = nullptr;   // [n_vert+1]
+  int32_t* col = nullptr;       // [nnz]
+  int32_t max_pairs_per_elem = 0;
+  int32_t max_row_nnz = 0;
+  size_t bytes = 0;
+};
+
+struct nl_matrix {
+  nl_pairs* pairs = nullptr;  // holds a reference
+  double* values = nullptr;   // [nnz]
+  cudaStream_t stream = nullptr;
+};
+
+struct nl_vector {
+  nl_mesh* mesh = nullptr;  // holds a reference
+  double* v = nullptr;      // [n_vert]
+  int64_t n = 0;
+  cudaStream_t stream = nullptr;
+};
+
+namespace nlx {
+void mesh_release(nl_mesh* m);
+void pairs_release(nl_pairs* p);
+// Builds the pair lists and the CSR pattern (nl_pairs.cu).
+nl_status build_pairs(nl_mesh* m, double delta, double eps, nl_pairs* out);
+// Runs the assembly kernels (nl_quad.cu); values must hold nnz doubles.
+nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                          const nl_quad_params* qp, nl_precision prec, double* values,
+                          nl_assemble_stats* st);
+// Right-hand side and solver kernels (nl_solve.cu).
+nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_const,
+                     const double* g_nodes, double* F);
+nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes, int solver,
+                       double rtol, int max_iter, nl_precision prec, double* u_out, int* iters,
+                       double* rel_res);
+}  // namespace nlx

@@ -1,0 +1,317 @@
+"""ctypes binding of libnl.so (include/nl.h): argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all computation runs in
+the library's CUDA kernels.  There is no fallback: if libnl.so is missing or fails to load,
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnl.so")
+HEADER = os.path.join(HERE, "..", "include", "nl.h")
+
+NL_OK, NL_EINVAL, NL_ENOMEM, NL_ECUDA, NL_ENOTCONV, NL_ETIMEOUT, NL_EBUSY, NL_EINTERNAL = range(8)
+STATUS_NAMES = ["NL_OK", "NL_EINVAL", "NL_ENOMEM", "NL_ECUDA", "NL_ENOTCONV", "NL_ETIMEOUT",
+                "NL_EBUSY", "NL_EINTERNAL"]
+NL_KERNEL_CONST, NL_KERNEL_TRUNC_GAUSS = 0, 1
+NL_PREC_FP64, NL_PREC_MIXED_TF32, NL_PREC_MIXED_BF16, NL_PREC_FP32 = 0, 1, 2, 3
+
+
+class NLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class KernelParams(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("eps", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("kernel", ctypes.c_int), ("C_override", ctypes.c_double)]
+
+
+class QuadParams(ctypes.Structure):
+    _fields_ = [("L_min", ctypes.c_int), ("L_max", ctypes.c_int), ("rule", ctypes.c_int)]
+
+
+class AssembleStats(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int64), ("n_point_pairs", ctypes.c_int64),
+                ("n_items", ctypes.c_int64), ("n_exact_checks", ctypes.c_int64),
+                ("ms_assemble", ctypes.c_double), ("n_eval_point_pairs", ctypes.c_int64),
+                ("n_uniform_points", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libnl.so (built by __graft_entry__.build() / paper_2101_08825_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    p, i, i64, d, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "nl_set_allocator": (st, [p, p, p]),
+        "nl_last_error": (ctypes.c_char_p, []),
+        "nl_version": (ctypes.c_char_p, []),
+        "nl_launch_count": (i64, []),
+        "nl_mesh_create": (st, [i, i64, p, i64, p, p, p, p, pp]),
+        "nl_mesh_create_box": (st, [i, p, d, p, ctypes.c_int32, d, ctypes.c_uint64, p, pp]),
+        "nl_mesh_info": (st, [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                              ctypes.POINTER(ctypes.c_int64)]),
+        "nl_mesh_export": (st, [p, p, p, p, p]),
+        "nl_mesh_destroy": (None, [p]),
+        "nl_pairs_build": (st, [p, d, d, pp]),
+        "nl_pairs_info": (st, [p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "nl_pairs_export": (st, [p, p, p, p, p]),
+        "nl_pairs_destroy": (None, [p]),
+        "nl_assemble": (st, [p, p, ctypes.POINTER(KernelParams), ctypes.POINTER(QuadParams), i, pp,
+                             ctypes.POINTER(AssembleStats)]),
+        "nl_matrix_export": (st, [p, p]),
+        "nl_matrix_device_values": (st, [p, pp]),
+        "nl_matrix_destroy": (None, [p]),
+        "nl_rhs": (st, [p, p, p, d, p, pp]),
+        "nl_vector_export": (st, [p, p]),
+        "nl_vector_destroy": (None, [p]),
+        "nl_solve": (st, [p, p, p, i, d, i, i, p, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_double)]),
+        "nl_quad_rule": (i, [i, p, p]),
+        "nl_kernel_constant": (d, [i, i, d, d]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in include/nl.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(nl_[a-z0-9_]+)\s*\(", text)
+    typedef_fns = set(re.findall(r"\(\*\s*(nl_[a-z0-9_]+)\)", text))
+    return sorted(set(n for n in names if n not in typedef_fns))
+
+
+def _check(status: int, what: str = ""):
+    if status != NL_OK:
+        raise NLError(status, (what + ": " if what else "") + lib().nl_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def current_stream():
+    """The torch current CUDA stream handle (0 = legacy default stream when unavailable)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+# ---- handles -----------------------------------------------------------------------------
+
+class _Handle:
+    _destroy = ""
+
+    def __init__(self, h):
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            getattr(lib(), self._destroy)(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Mesh(_Handle):
+    _destroy = "nl_mesh_destroy"
+
+    def info(self):
+        dim, nv, ne = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nl_mesh_info(self.h, ctypes.byref(dim), ctypes.byref(nv), ctypes.byref(ne)))
+        return dim.value, nv.value, ne.value
+
+    def export(self):
+        dim, nv, ne = self.info()
+        coords = np.zeros(dim * nv)
+        conn = np.zeros(ne * (dim + 1), dtype=np.int32)
+        eio = np.zeros(ne, dtype=np.uint8)
+        nf = np.zeros(nv, dtype=np.uint8)
+        _check(lib().nl_mesh_export(self.h, _ptr(coords), _ptr(conn), _ptr(eio), _ptr(nf)))
+        return coords.reshape(dim, nv), conn.reshape(ne, dim + 1), eio, nf
+
+
+class Pairs(_Handle):
+    _destroy = "nl_pairs_destroy"
+
+    def info(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().nl_pairs_info(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def export(self, n_elem: int, n_vert: int):
+        n_pairs, nnz = self.info()
+        off = np.zeros(n_elem + 1, dtype=np.int64)
+        pl = np.zeros(max(n_pairs, 1), dtype=np.int32)
+        rp = np.zeros(n_vert + 1, dtype=np.int64)
+        col = np.zeros(max(nnz, 1), dtype=np.int32)
+        _check(lib().nl_pairs_export(self.h, _ptr(off), _ptr(pl), _ptr(rp), _ptr(col)))
+        return off, pl[:n_pairs], rp, col[:nnz]
+
+
+class Matrix(_Handle):
+    _destroy = "nl_matrix_destroy"
+
+    def __init__(self, h, nnz):
+        super().__init__(h)
+        self.nnz = nnz
+
+    def export(self):
+        v = np.zeros(max(self.nnz, 1))
+        _check(lib().nl_matrix_export(self.h, _ptr(v)))
+        return v[: self.nnz]
+
+    def device_values(self) -> int:
+        p = ctypes.c_void_p()
+        _check(lib().nl_matrix_device_values(self.h, ctypes.byref(p)))
+        return p.value
+
+
+class Vector(_Handle):
+    _destroy = "nl_vector_destroy"
+
+    def __init__(self, h, n):
+        super().__init__(h)
+        self.n = n
+
+    def export(self):
+        v = np.zeros(self.n)
+        _check(lib().nl_vector_export(self.h, _ptr(v)))
+        return v
+
+
+# ---- entry points ---------------------------------------------------------------------------
+
+def nl_mesh_create(dim, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
+    coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(dim, -1)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, dim + 1)
+    eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
+    nf = np.ascontiguousarray(node_free, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib().nl_mesh_create(dim, coords.shape[1], _ptr(coords), conn.shape[0], _ptr(conn),
+                                _ptr(eio), _ptr(nf), stream if stream is not None else current_stream(),
+                                ctypes.byref(h)), "nl_mesh_create")
+    return Mesh(h)
+
+
+def mesh_from(mesh, stream=None) -> Mesh:
+    """Uploads an nl_inputs.Mesh."""
+    return nl_mesh_create(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
+
+
+def nl_mesh_create_box(dim, cells, h, lo, layer, jitter=0.0, seed=0, stream=None) -> Mesh:
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().nl_mesh_create_box(dim, _ptr(cells), float(h), _ptr(lo), int(layer), float(jitter),
+                                    int(seed), stream if stream is not None else current_stream(),
+                                    ctypes.byref(out)), "nl_mesh_create_box")
+    return Mesh(out)
+
+
+def nl_pairs_build(mesh: Mesh, delta: float, eps: float) -> Pairs:
+    out = ctypes.c_void_p()
+    _check(lib().nl_pairs_build(mesh.h, float(delta), float(eps), ctypes.byref(out)), "nl_pairs_build")
+    return Pairs(out)
+
+
+def nl_assemble(mesh: Mesh, pairs: Pairs, delta, eps, L_max, L_min=1, kernel=NL_KERNEL_CONST,
+                precision=NL_PREC_FP64, C_override=0.0, kappa=0.0, into: Matrix | None = None):
+    kp = KernelParams(float(delta), float(eps), float(kappa), int(kernel), float(C_override))
+    qp = QuadParams(int(L_min), int(L_max), 0)
+    st = AssembleStats()
+    h = ctypes.c_void_p(into.h.value if into is not None else None)
+    _check(lib().nl_assemble(mesh.h, pairs.h, ctypes.byref(kp), ctypes.byref(qp), int(precision),
+                             ctypes.byref(h), ctypes.byref(st)), "nl_assemble")
+    if into is not None:
+        return into, st
+    return Matrix(h, pairs.info()[1]), st
+
+
+def nl_rhs(mesh: Mesh, A: Matrix, g_nodes, f_const=0.0, f_nodes=None) -> Vector:
+    g = np.ascontiguousarray(g_nodes, dtype=np.float64)
+    fn = None if f_nodes is None else np.ascontiguousarray(f_nodes, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().nl_rhs(mesh.h, A.h, None if fn is None else _ptr(fn), float(f_const), _ptr(g),
+                        ctypes.byref(out)), "nl_rhs")
+    return Vector(out, len(g))
+
+
+def nl_solve(A: Matrix, rhs: Vector, g_nodes, solver=1, rtol=1e-12, max_iter=10000,
+             precision=NL_PREC_FP64, check=True):
+    g = np.ascontiguousarray(g_nodes, dtype=np.float64)
+    u = np.zeros(len(g))
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    s = lib().nl_solve(A.h, rhs.h, _ptr(g), int(solver), float(rtol), int(max_iter), int(precision),
+                       _ptr(u), ctypes.byref(it), ctypes.byref(rr))
+    if check:
+        _check(s, "nl_solve")
+    return u, it.value, rr.value, s
+
+
+def nl_quad_rule(dim: int):
+    b = np.zeros(64)
+    w = np.zeros(16)
+    n = lib().nl_quad_rule(dim, _ptr(b), _ptr(w))
+    if n <= 0:
+        raise NLError(NL_EINTERNAL, "nl_quad_rule failed")
+    return b[: n * (dim + 1)].reshape(n, dim + 1).copy(), w[:n].copy()
+
+
+def nl_kernel_constant(dim, kernel, delta, eps) -> float:
+    return lib().nl_kernel_constant(dim, kernel, delta, eps)
+
+
+@dataclass
+class Problem:
+    """Mesh, pairs and matrix of one assembled problem, kept on the device."""
+    mesh: Mesh
+    pairs: Pairs
+    A: Matrix
+    stats: AssembleStats
+
+
+def assemble_problem(mesh_in, delta, eps, L_max, L_min=1, kernel=NL_KERNEL_CONST,
+                     precision=NL_PREC_FP64) -> Problem:
+    m = mesh_from(mesh_in)
+    p = nl_pairs_build(m, delta, eps)
+    A, st = nl_assemble(m, p, delta, eps, L_max, L_min, kernel, precision)
+    return Problem(m, p, A, st)
