@@ -254,9 +254,13 @@ def run_ours(args, rank, world, local):
     r64 = step(nl.NL_PREC_FP64, keep=True)["A"]
     a_rel = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
 
-    # roofline of the dominant kernel (FP32 assembly kernel): algorithmic flops per launch
+    # roofline of the dominant kernel (FP32 assembly kernel): algorithmic flops per launch;
+    # the band count comes from one extra untimed launch with NL_QUAD_COUNT_BAND
     kern_avg = statistics.mean(kern_ms)
-    flops = roofline_flops(mesh.dim, st)
+    pb = nl.nl_pairs_build(dmesh, delta, eps)
+    _, stb = nl.nl_assemble(dmesh, pb, delta, eps, L_max, precision=nl.NL_PREC_FP32,
+                            count_band=True)
+    flops = roofline_flops(mesh.dim, stb)
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
     achieved = flops / (kern_avg / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 1),
@@ -279,7 +283,10 @@ def run_ours(args, rank, world, local):
                             "element_pairs_per_s": round(n_pairs / (kern_avg / 1e3), 1),
                             "quad_pt_pairs_per_s": round(n_pp / (kern_avg / 1e3), 1)},
         "counts": {"element_pairs": n_pairs, "quad_pt_pairs": n_pp, "items": st.n_items,
-                   "fp64_rechecks": st.n_exact_checks},
+                   "fp64_rechecks": st.n_exact_checks,
+                   "evaluated_point_pairs": stb.n_eval_point_pairs,
+                   "band_point_pairs": stb.n_band_point_pairs,
+                   "closed_form_items": stb.n_closed_items},
         "fp64": {"dtype": "f64", "ms_per_step": round(ms64, 3),
                  "value": round(world * n_pairs / (ms64 / 1e3), 1),
                  "assembly_kernel_ms": round(statistics.mean(k64), 3),
@@ -300,16 +307,15 @@ def run_ours(args, rank, world, local):
 
 
 def roofline_flops(dim, st):
-    """Algorithmic FP32 flops of one assembly launch (FMA = 2): per evaluated point pair the
-    squared distance (2D 5, 3D 8), the weight product (1) and the accumulation into g and the
-    dim barycentric moments (1 + 2*dim); per outer point of a mu = 1 item of the constant
-    kernel the same accumulation once (1 + 2*dim) for all inner points."""
-    ev = getattr(st, "n_eval_point_pairs", 0) or 0
-    un = getattr(st, "n_uniform_points", 0) or 0
-    if ev == 0 and un == 0:
-        ev = st.n_point_pairs
+    """Algorithmic FP32 flops of one assembly launch (FMA = 2).  Per point pair evaluated one
+    by one: the squared distance (2D 5, 3D 8), the weight product (1) and the accumulation
+    into g and the dim barycentric moments (1 + 2*dim); per band point pair additionally
+    r = r2*rsqrt(r2) (1), s = (delta - r)/eps (2) and xi(s) by Horner (12).  Sub-elements
+    summed in closed form and the per-item set-up are not counted."""
+    ev = max(0, int(getattr(st, "n_eval_point_pairs", 0) or 0))
+    band = max(0, int(getattr(st, "n_band_point_pairs", 0) or 0))
     per_pp = (5 if dim == 2 else 8) + 1 + 1 + 2 * dim
-    return float(ev * per_pp + un * (1 + 2 * dim))
+    return float(ev * per_pp + band * 15)
 
 
 def e2e_ours(args, mesh, w, g, f_const, stream, world):

@@ -69,8 +69,11 @@ typedef struct {
   double C_override; /* > 0: use this C instead */
 } nl_kernel_params;
 
-/* Algorithm 1 levels, 1 <= L_min <= L_max <= 12 (2D) or 9 (3D).  rule must be 0: the
- * degree-5 7-point triangle rule (Sec. 6) and the degree-5 14-point tetrahedral rule. */
+/* Algorithm 1 levels, 1 <= L_min <= L_max <= 12 (2D) or 9 (3D).  rule: 0 = the degree-5
+ * 7-point triangle rule (Sec. 6) and the degree-5 14-point tetrahedral rule, optionally OR
+ * NL_QUAD_COUNT_BAND to count the point pairs in the mollifier band (a measurement aid; it
+ * adds an integer add per evaluated point pair). */
+#define NL_QUAD_COUNT_BAND 0x100
 typedef struct {
   int L_min, L_max;
   int rule;
@@ -83,11 +86,13 @@ typedef struct {
   int64_t n_items;        /* (sub-element, m) integrations of Algorithm 1 */
   int64_t n_exact_checks; /* classifications decided by the FP64 fallback */
   double ms_assemble;     /* device time of the assembly kernels (CUDA events) */
-  int64_t n_eval_point_pairs; /* point pairs evaluated one by one (the others are either
-                                 beyond delta+eps, or have mu = 1 with a constant kernel and
-                                 are summed once per outer point) */
-  int64_t n_uniform_points;   /* outer points summed once for all inner points (mu = 1,
-                                 constant kernel) */
+  int64_t n_eval_point_pairs; /* point pairs evaluated one by one; the others belong to
+                                 sub-elements beyond delta+eps (mu = 0) or, with the
+                                 constant kernel, to sub-elements with mu = 1, whose outer
+                                 sums have the closed form C |E'| [1, lambda(centroid)] */
+  int64_t n_closed_items;     /* sub-elements summed in closed form (mu = 1, constant kernel) */
+  int64_t n_band_point_pairs; /* evaluated point pairs with delta-eps <= r <= delta+eps, when
+                                 NL_QUAD_COUNT_BAND was given; -1 otherwise */
 } nl_assemble_stats;
 
 typedef struct nl_mesh nl_mesh;

@@ -72,7 +72,7 @@ struct QParams {
   int* err;
   double delta, dme, dpe, C, inv_eps, inv_delta2;
   float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe;
-  int L_min, L_max, scap;
+  int L_min, L_max, scap, count_band;
   double B[14][4];
   double W[14];
 };
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
   R gself[NYL];
 #pragma unroll
   for (int i = 0; i < NYL; i++) gself[i] = 0;
-  unsigned long long st_items = 0, st_exact = 0, st_eval = 0, st_unif = 0;
+  unsigned long long st_items = 0, st_exact = 0, st_eval = 0, st_unif = 0, st_band = 0;
   int err = 0;
 
   int64_t cur_m = -1;
@@ -490,8 +490,7 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
         const R* iv = wm.iv + (size_t)kind * NVC * IMAX;
         const R* iw = wm.iw + kind * IMAX;
         const int n_x = n_it * NQ;
-        if (kind == KIND_INT && KERN == NL_KERNEL_CONST) st_unif += n_x;
-        else st_eval += (unsigned long long)n_x * NQ;
+        st_eval += (unsigned long long)n_x * NQ;
         for (int base = 0; base < n_x; base += G::XPI) {
           int o = base + xl;
           bool valid = o < n_x;
@@ -514,28 +513,49 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
             for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - vl0[c]);
             lam[r] = s;
           }
-          if (kind == KIND_INT && KERN == NL_KERNEL_CONST) {
-            ug += wcx;
 #pragma unroll
-            for (int k = 0; k < D; k++) uh[k] += wcx * lam[k];
-          } else {
+          for (int i = 0; i < NYL; i++) {
+            R r2 = 0;
 #pragma unroll
-            for (int i = 0; i < NYL; i++) {
-              R r2 = 0;
-#pragma unroll
-              for (int k = 0; k < D; k++) {
-                R d = x[k] - y[i][k];
-                r2 += d * d;
-              }
-              R g = wcx;
-              if (kind == KIND_FINAL) g *= mollifier(P, r2);
-              if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
-              gp[i] += g;
-#pragma unroll
-              for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
+            for (int k = 0; k < D; k++) {
+              R d = x[k] - y[i][k];
+              r2 += d * d;
             }
+            R g = wcx;
+            if (kind == KIND_FINAL) {
+              g *= mollifier(P, r2);
+              if (P.count_band) st_band += (r2 >= P.fdme2 && r2 <= P.fdpe2 && valid) ? 1 : 0;
+            }
+            if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
+            gp[i] += g;
+#pragma unroll
+            for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
           }
         }
+      };
+
+      // A sub-element with max-dist < delta - eps has mu = 1 at every point pair; with the
+      // constant kernel its outer sum is sum_q w_q C [1, lambda^l(x_q)] = C |E'| [1,
+      // lambda^l(centroid)], because the degree-5 rule integrates linear functions exactly.
+      auto closed_int = [&](const R (&V)[NV][D], int level) {
+        R cen[D];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          R s = 0;
+#pragma unroll
+          for (int a = 0; a < NV; a++) s += V[a][k];
+          cen[k] = s * (R)(1.0 / NV);
+        }
+        R wv = (R)(P.C * ldexp(vol_l, -D * (level - 1)));
+        ug += wv;
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+          R s = 0;
+#pragma unroll
+          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - vl0[c]);
+          uh[r] += wv * s;
+        }
+        st_unif++;
       };
 
       // ---- Algorithm 1 for this pair ----------------------------------------------------------
@@ -559,6 +579,8 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
             for (int t = 0; t < NVC; t++) wm.rv[t * P.scap] = V0[t / D][t % D];
             wm.rc[0] = code0;
             wm.ctl[0] = 1;
+          } else if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
+            closed_int(V0, 1);
           } else if (act == ACT_INT || act == ACT_FINAL) {
             int kind = act == ACT_INT ? KIND_INT : KIND_FINAL;
             R* iv = wm.iv + (size_t)kind * NVC * IMAX;
@@ -615,6 +637,11 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
         }
         __syncwarp();
         if (active) act = classify(V, code);
+        if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
+          closed_int(V, (int)(code >> LEVEL_SHIFT));
+          st_items++;
+          act = ACT_DROP;
+        }
         // append items and push refined sub-elements
         const unsigned m_int = __ballot_sync(0xffffffffu, act == ACT_INT);
         const unsigned m_fin = __ballot_sync(0xffffffffu, act == ACT_FINAL);
@@ -656,11 +683,15 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
       __syncwarp();
       // ---- end of pair: fold, reduce, scatter the cross block --------------------------------
 #pragma unroll
-      for (int i = 0; i < NYL; i++) {
-        gp[i] += ug;
+      for (int o = 16; o > 0; o >>= 1) {
+        ug += shfl_xor(ug, o);
 #pragma unroll
-        for (int k = 0; k < D; k++) hp[k][i] += uh[k];
+        for (int k = 0; k < D; k++) uh[k] += shfl_xor(uh[k], o);
+      }
+#pragma unroll
+      for (int i = 0; i < NYL; i++) {
         gself[i] += gp[i];
+        if (xl == 0) gself[i] += ug;  // once per group of lanes that share these inner points
       }
 #pragma unroll
       for (int i = 0; i < NYL; i++) {
@@ -674,9 +705,9 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
 #pragma unroll
           for (int k = 0; k < D; k++) ak[k] += shfl_xor(ak[k], o);
         }
-        gp[i] = a0;
+        gp[i] = a0 + ug;
 #pragma unroll
-        for (int k = 0; k < D; k++) hp[k][i] = ak[k];
+        for (int k = 0; k < D; k++) hp[k][i] = ak[k] + uh[k];
       }
       {
         // X[a][c] = vol_m sum_y W B_a(y) H_c(y), H_0 = g - sum_k h_k, H_c = h_{c-1}
@@ -716,6 +747,8 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
   for (int o = 16; o > 0; o >>= 1) {
     st_items += __shfl_xor_sync(0xffffffffu, st_items, o);
     st_exact += __shfl_xor_sync(0xffffffffu, st_exact, o);
+    st_unif += __shfl_xor_sync(0xffffffffu, st_unif, o);
+    st_band += __shfl_xor_sync(0xffffffffu, st_band, o);
     err |= __shfl_xor_sync(0xffffffffu, err, o);
   }
   if (lane == 0) {
@@ -723,6 +756,7 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
     atomicAdd(&P.stats[2], st_exact);
     atomicAdd(&P.stats[3], st_eval);
     atomicAdd(&P.stats[4], st_unif);
+    atomicAdd(&P.stats[5], st_band);
     if (err) atomicOr(P.err, err);
   }
 }
@@ -762,7 +796,7 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   const int lmax_cap = D == 2 ? 12 : 9;
   if (qp->L_min < 1 || qp->L_max < qp->L_min || qp->L_max > lmax_cap)
     return fail(NL_EINVAL, "nl_assemble: need 1 <= L_min <= L_max <= %d", lmax_cap);
-  if (qp->rule != 0) return fail(NL_EINVAL, "nl_assemble: only rule 0 is available");
+  if ((qp->rule & ~NL_QUAD_COUNT_BAND) != 0) return fail(NL_EINVAL, "nl_assemble: only rule 0 is available");
   if (prec != NL_PREC_FP64 && prec != NL_PREC_FP32 && prec != NL_PREC_MIXED_TF32 &&
       prec != NL_PREC_MIXED_BF16)
     return fail(NL_EINVAL, "nl_assemble: unknown precision %d", (int)prec);
@@ -802,6 +836,7 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   double R = kp->delta + kp->eps + 2.0 * m->max_ext;
   P.margin = (float)(2e-5 * R);
   P.L_min = qp->L_min;
+  P.count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
   P.L_max = qp->L_max;
   int64_t total = 0, pw = 1;
   for (int k = 1; k < qp->L_max; k++) {
@@ -865,7 +900,8 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
     st->n_exact_checks = (int64_t)hs[3];
     st->ms_assemble = ms;
     st->n_eval_point_pairs = (int64_t)hs[4];
-    st->n_uniform_points = (int64_t)hs[5];
+    st->n_closed_items = (int64_t)hs[5];
+    st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
   }
   return NL_OK;
 }

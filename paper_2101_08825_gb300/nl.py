@@ -43,7 +43,7 @@ class AssembleStats(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_point_pairs", ctypes.c_int64),
                 ("n_items", ctypes.c_int64), ("n_exact_checks", ctypes.c_int64),
                 ("ms_assemble", ctypes.c_double), ("n_eval_point_pairs", ctypes.c_int64),
-                ("n_uniform_points", ctypes.c_int64)]
+                ("n_closed_items", ctypes.c_int64), ("n_band_point_pairs", ctypes.c_int64)]
 
 
 _lib = None
@@ -252,10 +252,14 @@ def nl_pairs_build(mesh: Mesh, delta: float, eps: float) -> Pairs:
     return Pairs(out)
 
 
+NL_QUAD_COUNT_BAND = 0x100
+
+
 def nl_assemble(mesh: Mesh, pairs: Pairs, delta, eps, L_max, L_min=1, kernel=NL_KERNEL_CONST,
-                precision=NL_PREC_FP64, C_override=0.0, kappa=0.0, into: Matrix | None = None):
+                precision=NL_PREC_FP64, C_override=0.0, kappa=0.0, into: Matrix | None = None,
+                count_band=False):
     kp = KernelParams(float(delta), float(eps), float(kappa), int(kernel), float(C_override))
-    qp = QuadParams(int(L_min), int(L_max), 0)
+    qp = QuadParams(int(L_min), int(L_max), NL_QUAD_COUNT_BAND if count_band else 0)
     st = AssembleStats()
     h = ctypes.c_void_p(into.h.value if into is not None else None)
     _check(lib().nl_assemble(mesh.h, pairs.h, ctypes.byref(kp), ctypes.byref(qp), int(precision),
