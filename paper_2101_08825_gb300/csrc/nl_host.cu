@@ -266,7 +266,8 @@ template <int D>
 __global__ void k_mesh_elements(int64_t n_elem, int64_t n_vert, const double* __restrict__ coords,
                                 const int32_t* __restrict__ conn, double* __restrict__ evert,
                                 double* __restrict__ blo, double* __restrict__ bhi,
-                                double* __restrict__ vol, double* __restrict__ jinv) {
+                                double* __restrict__ vol, double* __restrict__ jinv,
+                                float* __restrict__ ef) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n_elem) return;
   double V[D + 1][D];
@@ -319,6 +320,13 @@ __global__ void k_mesh_elements(int64_t n_elem, int64_t n_vert, const double* __
   }
   for (int r = 0; r < D; r++)
     for (int c = 0; c < D; c++) jinv[(e * D + r) * D + c] = inv[r][c];
+  float* f = ef + e * NL_EF_STRIDE(D);
+  for (int a = 1; a <= D; a++)
+    for (int k = 0; k < D; k++) f[(a - 1) * D + k] = (float)(V[a][k] - V[0][k]);
+  for (int r = 0; r < D; r++)
+    for (int c = 0; c < D; c++) f[D * D + r * D + c] = (float)inv[r][c];
+  f[2 * D * D] = (float)vol[e];
+  for (int t = 2 * D * D + 1; t < NL_EF_STRIDE(D); t++) f[t] = 0.f;
 }
 
 __global__ void k_count_n2e(int64_t n_entries, const int32_t* __restrict__ conn,
@@ -352,6 +360,7 @@ void nlx::mesh_release(nl_mesh* m) {
   dev_free(m->bhi, 0, s);
   dev_free(m->vol, 0, s);
   dev_free(m->jinv, 0, s);
+  dev_free(m->ef, 0, s);
   dev_free(m->n2e_off, 0, s);
   dev_free(m->n2e, 0, s);
   cudaStreamSynchronize(s);
@@ -419,6 +428,7 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
     m->bb_hi[k] = k < dim ? bh[k] : 0.0;
   }
   DevBuf<double> dc, ev, lo, hi, vol, jinv;
+  DevBuf<float> efb;
   DevBuf<int32_t> dconn, n2e, cnt;
   DevBuf<uint8_t> deio, dnf;
   DevBuf<int64_t> off;
@@ -433,6 +443,7 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
     if ((st = hi.alloc(dim * n_elem, s)) != NL_OK) break;
     if ((st = vol.alloc(n_elem, s)) != NL_OK) break;
     if ((st = jinv.alloc(dim * dim * n_elem, s)) != NL_OK) break;
+    if ((st = efb.alloc((size_t)NL_EF_STRIDE(dim) * n_elem, s)) != NL_OK) break;
     if ((st = n2e.alloc(nv * n_elem, s)) != NL_OK) break;
     if ((st = cnt.alloc(n_vert, s)) != NL_OK) break;
     if ((st = off.alloc(n_vert + 1, s)) != NL_OK) break;
@@ -455,9 +466,9 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
   int tb = 256;
   int64_t gb = (n_elem + tb - 1) / tb;
   if (dim == 2)
-    k_mesh_elements<2><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p);
+    k_mesh_elements<2><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   else
-    k_mesh_elements<3><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p);
+    k_mesh_elements<3><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   int64_t ne = nv * n_elem;
   k_count_n2e<<<NL_CNT((unsigned)((ne + tb - 1) / tb)), tb, 0, s>>>(ne, dconn.p, cnt.p);
   st = exclusive_scan_i32_to_i64(cnt.p, off.p, n_vert, s);
@@ -475,6 +486,7 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
   m->bhi = hi.release_ownership();
   m->vol = vol.release_ownership();
   m->jinv = jinv.release_ownership();
+  m->ef = efb.release_ownership();
   m->n2e = n2e.release_ownership();
   m->n2e_off = off.release_ownership();
   *out = m;

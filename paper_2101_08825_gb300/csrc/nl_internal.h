@@ -106,6 +106,9 @@ struct nl_mesh {
   double* bhi = nullptr;
   double* vol = nullptr;           // [n_elem]
   double* jinv = nullptr;          // [n_elem][dim][dim]: lambda_{1..dim} = jinv (x - v0)
+  float* ef = nullptr;             // [n_elem][EF_STRIDE(dim)]: FP32 vertex offsets v_a - v_0
+                                   // (a = 1..dim), inverse Jacobian, volume
+  int32_t max_conn_deg = 0;
   int64_t* n2e_off = nullptr;      // [n_vert+1] node -> elements
   int32_t* n2e = nullptr;          // [(dim+1) n_elem]
   double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};
@@ -139,6 +142,9 @@ struct nl_vector {
   int64_t n = 0;
   cudaStream_t stream = nullptr;
 };
+
+// FP32 per-element record: dim*dim offsets, dim*dim inverse Jacobian, volume, padding
+#define NL_EF_STRIDE(dim) ((dim) == 2 ? 12 : 20)
 
 namespace nlx {
 void mesh_release(nl_mesh* m);

@@ -322,7 +322,7 @@ __global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
                        const int64_t* __restrict__ pair_off, const int32_t* __restrict__ pair_l,
                        int eh, int nh, int32_t* __restrict__ row_cnt,
                        const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
-                       int* __restrict__ err) {
+                       int* __restrict__ err, int* __restrict__ max_row) {
   extern __shared__ int32_t smem[];
   int32_t* etab = smem;
   int32_t* ntab = smem + eh;
@@ -352,7 +352,10 @@ __global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
     return;
   }
   if (!FILL) {
-    if (threadIdx.x == 0) row_cnt[i] = ncount;
+    if (threadIdx.x == 0) {
+      row_cnt[i] = ncount;
+      atomicMax(max_row, ncount);
+    }
     return;
   }
   int n = ncount;
@@ -487,14 +490,16 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   DevBuf<int32_t> rcnt;
   NL_TRY(rcnt.alloc(nvv, s));
   k_rows<D, false><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
-                                                     eh, nh, rcnt.p, nullptr, nullptr, err.p);
+                                                     eh, nh, rcnt.p, nullptr, nullptr, err.p,
+                                                     max_cnt.p + 1);
   NL_CUDA(cudaGetLastError());
   DevBuf<int64_t> rp;
   NL_TRY(rp.alloc(nvv + 1, s));
   NL_TRY(exclusive_scan_i32_to_i64(rcnt.p, rp.p, nvv, s));
   int64_t nnz = 0;
-  int e = 0;
+  int e = 0, max_row = 0;
   NL_CUDA(cudaMemcpyAsync(&nnz, rp.p + nvv, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  NL_CUDA(cudaMemcpyAsync(&max_row, max_cnt.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));
   if (e) {
@@ -505,7 +510,7 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   DevBuf<int32_t> col;
   NL_TRY(col.alloc(nnz > 0 ? nnz : 1, s));
   k_rows<D, true><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
-                                                    eh, nh, nullptr, rp.p, col.p, err.p);
+                                                    eh, nh, nullptr, rp.p, col.p, err.p, nullptr);
   NL_CUDA(cudaGetLastError());
   NL_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));
@@ -513,6 +518,7 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   out->n_pairs = n_pairs;
   out->nnz = nnz;
   out->max_pairs_per_elem = mx;
+  out->max_row_nnz = max_row;
   out->pair_off = off.release_ownership();
   out->pair_l = pl.release_ownership();
   out->row_ptr = rp.release_ownership();

@@ -8,29 +8,38 @@
 // Algorithm 1 is applied per pair; this is the same computation as the per-l recursion with
 // the index set J_l, because the tests and the integration act on every m separately.
 //
-// How: a persistent grid; each warp takes chunks of consecutive pairs (m-major) from a
-// global counter.  For one pair the warp runs Algorithm 1 as a LIFO of refined
-// sub-elements ("parent records", vertices + path code) in shared memory: each round pops
+// How (k_quad): a persistent grid; each warp takes chunks of consecutive pairs (m-major)
+// from a global counter.  For one pair the warp runs Algorithm 1 as a LIFO of refined
+// sub-elements ("parent records": vertices + path code) in shared memory: each round pops
 // up to 32/2^N parents and every lane builds one child by midpoints, classifies it with the
-// box distances of Sec. 5.1 and either drops it, pushes it, or appends it to one of two item
-// buffers: INT (max-dist < delta-eps, mu = 1 at every point pair) or FINAL (the sub-element
-// reached L_max with the band in reach).  A full buffer is integrated by the whole warp:
-// each lane owns one outer point x of the buffered items and a set of 7 inner points y kept
-// in registers, and accumulates per y the sums g = sum_x w_x C eta mu and
-// h_k = sum_x w_x C eta mu lambda^l_k(x).  At the end of the pair the lanes reduce these and
-// the cross block is scattered with FP64 atomics; the self block needs only g and is
-// accumulated over the consecutive pairs of the same m before it is scattered.
+// box distances of Sec. 5.1 and drops it, pushes it, or appends it to one of two item
+// buffers: INT (max-dist < delta-eps: mu = 1 at every point pair) or FINAL (the sub-element
+// reached L_max with the band in reach).  With the constant kernel an INT sub-element is
+// summed in closed form (the degree-5 rule integrates its linear integrand exactly).  A full
+// buffer is integrated by the whole warp: each lane owns one outer point x and 7 inner points
+// y kept in registers (3D: two half-warps share x and take y 0-6 and 7-13), and accumulates
+// per y the sums g = sum_x w_x C eta mu and h_k = sum_x w_x C eta mu lambda^l_k(x).  At the
+// end of the pair the warp reduces them through a shared-memory transpose and writes the
+// pair's cross block -2 vol_m sum_y w_y B_a(y) H_c(y) (H_0 = g - sum_k h_k, H_c = h_{c-1})
+// to a block buffer; the self block only needs g, which is accumulated over the consecutive
+// pairs of the same m (compensated FP32 or FP64) and added to a per-element block.
+// k_scatter (one CTA per inner element m, the rows of m's nodes cached in shared memory)
+// then adds every block to the CSR values with FP64 atomics.
 //
-// Precision: R = double evaluates everything in FP64 and classifies in FP64.  R = float
-// evaluates gamma_eps in FP32 on coordinates relative to the first vertex of m, and screens
-// the classification in FP32: a decision whose FP32 distance lies within a proven margin of
-// the threshold is redone in FP64 on vertices rebuilt from E_l by the same midpoint
-// sequence, so the decisions are those of a plain FP64 evaluation in both precisions.
+// Precision: R = double evaluates everything in FP64 on global coordinates and classifies
+// in FP64.  R = float evaluates gamma_eps in FP32 on coordinates relative to the first
+// vertex of m, built from per-element FP32 vertex offsets and one FP64 difference of first
+// vertices per pair; the classification is screened in FP32, and a decision whose FP32
+// distance lies within a proven margin of its threshold is redone in FP64 on vertices
+// rebuilt from E_l by the same midpoint sequence, so the decisions are those of a plain FP64
+// evaluation in both precisions.  No FP64 arithmetic runs per sub-element or per point pair.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "nl_internal.h"
 
@@ -50,28 +59,29 @@ constexpr int KIND_FINAL = 1;
 // farther than delta + eps (mu = 0): counted, not evaluated.
 constexpr int ACT_DROP = 0, ACT_INT = 1, ACT_FINAL = 2, ACT_REFINE = 3, ACT_ZERO = 4;
 constexpr int ERR_STACK = 1, ERR_CSR = 2;
-constexpr int CHUNK = 8;
+constexpr int CHUNK = 32;
 constexpr int IMAX = 64;
 constexpr int LEVEL_SHIFT = 27;
 
 struct QParams {
-  int64_t n_pairs, n_elem;
+  int64_t n_elem, p_begin, p_end;
   const int64_t* pair_off;
   const int32_t* pair_l;
-  const int64_t* row_ptr;
-  const int32_t* col;
   const int32_t* conn;
   const double* evert;
   const double* blo;
   const double* bhi;
   const double* vol;
   const double* jinv;
-  double* values;
+  const float* ef;
+  void* blk;          // [p_end - p_begin][(D+1)^2] cross blocks (R)
+  double* selfblk;    // [n_elem][(D+1)^2]
   unsigned long long* counter;
-  unsigned long long* stats;  // [0] items, [2] exact checks, [3] evaluated pairs, [4] uniform points
+  unsigned long long* stats;  // [0] items, [2] exact checks, [3] evaluated pairs,
+                              // [4] closed-form items, [5] band pairs
   int* err;
   double delta, dme, dpe, C, inv_eps, inv_delta2;
-  float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe;
+  float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
   int L_min, L_max, scap, count_band;
   double B[14][4];
   double W[14];
@@ -87,9 +97,14 @@ struct Geo {
   static constexpr int NYL = 7;                 // inner points per lane
   static constexpr int NVC = NV * D;            // vertex coordinates of a simplex
   static constexpr int BITS = D;                // path bits per level
+  static constexpr int NBLK = NV * NV;          // entries of a local block
+  static constexpr int NRED = NYL * NV + NV;    // per-lane values reduced at pair end
+  static constexpr int RS = NRED | 1;           // odd row stride of the reduction scratch
+  static constexpr int TOTN = NQ * NV + NV;     // pair totals: per inner point, then uniform
+  static constexpr int EFS = NL_EF_STRIDE(D);
 };
 
-// child c, vertex v = midpoint of parent vertices (MA, MB); a corner is mid(P, P) = P exactly
+// child c, vertex v = midpoint of parent vertices (a, b); a corner is mid(P, P) = P exactly
 __constant__ unsigned char c_mid2[4][3][2] = {{{0, 0}, {0, 1}, {0, 2}},
                                               {{0, 1}, {1, 1}, {1, 2}},
                                               {{0, 2}, {1, 2}, {2, 2}},
@@ -113,6 +128,12 @@ __device__ __forceinline__ void mid_pair(int c, int v, int& a, int& b) {
 
 __device__ __forceinline__ double midp(double a, double b) { return __dmul_rn(__dadd_rn(a, b), 0.5); }
 __device__ __forceinline__ float midp(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
+
+// 2^-k as an exact power of two
+__device__ __forceinline__ float pow2m(float, int k) { return __int_as_float((127 - k) << 23); }
+__device__ __forceinline__ double pow2m(double, int k) {
+  return __longlong_as_double((long long)(1023 - k) << 52);
+}
 
 // Exact FP64 box distances of Sec. 5.1 (eqs. maxdist, mindist) between a sub-element with
 // vertices V and the box (lo2, hi2) of E_m, written as in a plain evaluation.
@@ -140,8 +161,8 @@ __device__ void exact_dists(const double (&V)[D + 1][D], const double* lo2, cons
 }
 
 template <int D>
-__device__ void screen_dists(const float (&V)[D + 1][D], const float* lo2, const float* hi2,
-                             float& amax, float& amin) {
+__device__ __forceinline__ void screen_dists(const float (&V)[D + 1][D], const float* lo2,
+                                             const float* hi2, float& amax, float& amin) {
   float s = 0.f, mn = 0.f;
 #pragma unroll
   for (int k = 0; k < D; k++) {
@@ -192,6 +213,31 @@ __device__ void decode_exact(const double (&Vl)[D + 1][D], uint32_t code, double
   }
 }
 
+// FP64 decision of Algorithm 1 for a sub-element below L_max (used by the FP32 path when the
+// screened distance is within the margin of a threshold): ACT_INT, ACT_REFINE or ACT_DROP.
+template <int D>
+__device__ __noinline__ int exact_classify(const double* __restrict__ evert_l,
+                                           const double* __restrict__ lo_m,
+                                           const double* __restrict__ hi_m, uint32_t code,
+                                           double dme, double dpe) {
+  double Vl[D + 1][D], V[D + 1][D], lo2[D], hi2[D];
+#pragma unroll
+  for (int a = 0; a <= D; a++)
+#pragma unroll
+    for (int k = 0; k < D; k++) Vl[a][k] = evert_l[a * D + k];
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    lo2[k] = lo_m[k];
+    hi2[k] = hi_m[k];
+  }
+  decode_exact<D>(Vl, code, V);
+  double amax, amin;
+  exact_dists<D>(V, lo2, hi2, amax, amin);
+  if (amax < dme) return ACT_INT;
+  if (amin < dpe) return ACT_REFINE;
+  return ACT_DROP;
+}
+
 __device__ __forceinline__ double xi_poly(double s) {
   double t = s * s;
   double p = fma(35.0, t, -180.0);
@@ -220,8 +266,35 @@ __device__ __forceinline__ double mollifier(const QParams& P, double r2) {
 __device__ __forceinline__ float mollifier(const QParams& P, float r2) {
   if (r2 < P.fdme2) return 1.f;
   if (r2 > P.fdpe2) return 0.f;
-  float r = r2 * rsqrtf(r2);
+  // r = sqrt(r2): hardware reciprocal square root, then one Newton step on r^2 - r2 = 0
+  // (r <- r + (r2 - r^2) / (2r)), which brings r to about one ulp
+  const float q = rsqrtf(r2);
+  float r = r2 * q;
+  r = fmaf(0.5f * q, fmaf(-r, r, r2), r);
   return xi_poly((P.fdelta - r) * P.finv_eps);
+}
+
+// Sum_j A_ij = 0 for every row of the exact discrete operator (sum_j phi_j = 1 at every
+// point, so every point pair contributes sum_j (phi_j(y) - phi_j(x)) = 0): the diagonal
+// equals minus the sum of the off-diagonal entries.  The FP32 paths rebuild it that way in
+// FP64, which removes the row-sum part of their rounding error (warp per row).
+__global__ void k_diag_from_rows(int64_t n_rows, const int64_t* __restrict__ row_ptr,
+                                 const int32_t* __restrict__ col, double* __restrict__ values) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_rows) return;
+  double s = 0.0;
+  int64_t dpos = -1;
+  for (int64_t t = row_ptr[i] + lane; t < row_ptr[i + 1]; t += 32) {
+    if (col[t] == (int32_t)i) dpos = t;
+    else s += values[t];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    int64_t d = __shfl_xor_sync(0xffffffffu, dpos, o);
+    dpos = d > dpos ? d : dpos;
+  }
+  if (lane == 0 && dpos >= 0) values[dpos] = -s;
 }
 
 template <typename R>
@@ -235,196 +308,201 @@ __device__ __forceinline__ float eta_gauss<float>(const QParams& P, float r2) {
   return __expf(-r2 * P.finv_delta2);
 }
 
-__device__ __forceinline__ int64_t csr_find(const int64_t* __restrict__ row_ptr,
-                                            const int32_t* __restrict__ col, int32_t i, int32_t j) {
-  int64_t lo = row_ptr[i], hi = row_ptr[i + 1] - 1;
-  while (lo <= hi) {
-    int64_t mid = (lo + hi) >> 1;
-    int32_t c = col[mid];
-    if (c == j) return mid;
-    if (c < j) lo = mid + 1;
-    else hi = mid - 1;
-  }
-  return -1;
+// Compensated accumulation (hi + lo) in the working precision (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  float s = hi + v;
+  float bb = s - hi;
+  float e = (hi - (s - bb)) + (v - bb);
+  hi = s;
+  lo += e;
+}
+__device__ __forceinline__ void two_sum_add(double& hi, double& lo, double v) {
+  hi += v;
+  (void)lo;
 }
 
-template <typename R>
-__device__ __forceinline__ R shfl_xor(R v, int o) {
-  return __shfl_xor_sync(0xffffffffu, v, o);
-}
-
-// Per-warp shared memory: stack records and the two item buffers (SoA), sized at launch.
+// Per-warp shared memory: stack records, two item buffers (SoA) and the reduction scratch.
 template <int D, typename R>
 struct WarpMem {
   R* rv;          // [NVC][scap]
   uint32_t* rc;   // [scap]
   R* iv;          // [2][NVC][IMAX]
   R* iw;          // [2][IMAX]
+  R* red;         // [32][RS]
+  R* tot;         // [TOTN] pair totals
   int* ctl;       // [0] sp, [1] n_int, [2] n_final
   static __host__ __device__ size_t bytes(int scap) {
-    size_t b = sizeof(R) * (size_t)Geo<D>::NVC * scap + sizeof(uint32_t) * scap;
+    using G = Geo<D>;
+    size_t b = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
     b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * (size_t)2 * Geo<D>::NVC * IMAX + sizeof(R) * 2 * IMAX;
+    b += sizeof(R) * ((size_t)2 * G::NVC * IMAX + 2 * IMAX + 32 * G::RS + G::TOTN + 16);
     b += 16;
     return (b + 15) & ~size_t(15);
   }
   __device__ void carve(char* base, int scap) {
+    using G = Geo<D>;
     rv = reinterpret_cast<R*>(base);
-    rc = reinterpret_cast<uint32_t*>(rv + (size_t)Geo<D>::NVC * scap);
-    size_t off = sizeof(R) * (size_t)Geo<D>::NVC * scap + sizeof(uint32_t) * scap;
+    rc = reinterpret_cast<uint32_t*>(rv + (size_t)G::NVC * scap);
+    size_t off = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
     off = (off + 15) & ~size_t(15);
     iv = reinterpret_cast<R*>(base + off);
-    iw = iv + (size_t)2 * Geo<D>::NVC * IMAX;
-    ctl = reinterpret_cast<int*>(iw + 2 * IMAX);
+    iw = iv + (size_t)2 * G::NVC * IMAX;
+    red = iw + 2 * IMAX;
+    tot = red + 32 * G::RS;
+    ctl = reinterpret_cast<int*>(tot + G::TOTN + 8);
   }
 };
 
+template <typename R>
+__host__ __device__ constexpr size_t table_bytes() {
+  return (sizeof(R) * (14 * 4 * 2 + 16) + 15) & ~size_t(15);
+}
+
 template <int D, typename R, int KERN>
-__global__ void __launch_bounds__(256) k_quad(const QParams P) {
+__global__ void __launch_bounds__(256, 2) k_quad(const QParams P) {
   using G = Geo<D>;
-  constexpr int NV = G::NV, NQ = G::NQ, NYL = G::NYL, NVC = G::NVC;
+  constexpr int NV = G::NV, NQ = G::NQ, NYL = G::NYL, NVC = G::NVC, NBLK = G::NBLK;
+  constexpr int RS = G::RS;
   constexpr bool F32 = std::is_same<R, float>::value;
   extern __shared__ __align__(16) char smem_raw[];
-  // CTA-shared tables
   R* sB = reinterpret_cast<R*>(smem_raw);  // [NQ][NV]
   R* sW = sB + 14 * 4;                      // [NQ]
   R* sWB = sW + 16;                         // [NQ][NV]: W[q] * B[q][a]
-  const int tid = threadIdx.x;
-  for (int t = tid; t < NQ * NV; t += blockDim.x) {
+  for (int t = threadIdx.x; t < NQ * NV; t += blockDim.x) {
     sB[t] = (R)P.B[t / NV][t % NV];
     sWB[t] = (R)(P.W[t / NV] * P.B[t / NV][t % NV]);
   }
-  for (int t = tid; t < NQ; t += blockDim.x) sW[t] = (R)P.W[t];
+  for (int t = threadIdx.x; t < NQ; t += blockDim.x) sW[t] = (R)P.W[t];
   __syncthreads();
-  const int lane = tid & 31, wid = tid >> 5;
-  size_t tbl = (sizeof(R) * (14 * 4 * 2 + 16) + 15) & ~size_t(15);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem<D, R> wm;
-  wm.carve(smem_raw + tbl + (size_t)wid * WarpMem<D, R>::bytes(P.scap), P.scap);
+  wm.carve(smem_raw + table_bytes<R>() + (size_t)wid * WarpMem<D, R>::bytes(P.scap), P.scap);
 
   const int ybase = (D == 3 && lane >= 16) ? 7 : 0;
   const int xl = (D == 3) ? (lane & 15) : lane;
 
-  // accumulators
-  R gself[NYL];
-#pragma unroll
-  for (int i = 0; i < NYL; i++) gself[i] = 0;
-  unsigned long long st_items = 0, st_exact = 0, st_eval = 0, st_unif = 0, st_band = 0;
+  unsigned long long st_items = 0, st_exact = 0, st_eval = 0, st_closed = 0, st_band = 0;
   int err = 0;
 
+  // state of the current inner element m
   int64_t cur_m = -1;
-  double Vm[NV][D];            // global FP64 vertices of m
-  double lo_m[D], hi_m[D];     // FP64 box of m
-  float flo_m[D], fhi_m[D];    // box of m relative to the origin (FP32 screen)
-  double org[D];               // origin of the local coordinates (vertex 0 of m)
-  R y[NYL][D];                 // inner points (local coordinates if R = float)
+  double v0m[D];      // first vertex of m (origin of the FP32 local coordinates)
+  R lo_m[D], hi_m[D]; // box of m (local FP32 coordinates, or global FP64)
+  R y[NYL][D];        // inner points of m (local if R = float)
   R vol_m = 0;
-  int32_t nodes_m[NV] = {};
+  R gs_hi = 0, gs_lo = 0;  // lane t < NQ: sum of g over the m-run for inner point t
 
   auto flush_self = [&]() {
-    // reduce g over the lanes that share the same inner points
-#pragma unroll
-    for (int i = 0; i < NYL; i++) {
-      R v = gself[i];
-      if (D == 2) v += shfl_xor(v, 16);
-      v += shfl_xor(v, 8);
-      v += shfl_xor(v, 4);
-      v += shfl_xor(v, 2);
-      v += shfl_xor(v, 1);
-      gself[i] = v;
-    }
-    // S[a][b] = 2 vol_m sum_y W B_a B_b g(y)
-    int t = (D == 3) ? (lane & 15) : lane;
-    R s = 0;
-    if (t < NV * NV) {
-      int a = t / NV, b = t % NV;
-#pragma unroll
-      for (int i = 0; i < NYL; i++) {
-        int q = ybase + i;
-        s += sWB[q * NV + a] * sB[q * NV + b] * gself[i];
-      }
-    }
-    if (D == 3) s += shfl_xor(s, 16);
-    if (lane < NV * NV) {
+    // S[a][b] = 2 vol_m sum_y W B_a B_b g(y), in FP64 from the compensated sums
+    double* sd = reinterpret_cast<double*>(wm.red);
+    if (lane < NQ) sd[lane] = (double)gs_hi + (double)gs_lo;
+    __syncwarp();
+    if (lane < NBLK) {
       int a = lane / NV, b = lane % NV;
-      double val = 2.0 * (double)vol_m * (double)s;
-      int64_t pos = csr_find(P.row_ptr, P.col, nodes_m[a], nodes_m[b]);
-      if (pos < 0) err |= ERR_CSR;
-      else atomicAdd(&P.values[pos], val);
-    }
+      double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < NYL; i++) gself[i] = 0;
+      for (int q = 0; q < NQ; q++) s += (double)sWB[q * NV + a] * (double)sB[q * NV + b] * sd[q];
+      atomicAdd(&P.selfblk[cur_m * NBLK + lane], 2.0 * (double)vol_m * s);
+    }
+    __syncwarp();
+    gs_hi = 0;
+    gs_lo = 0;
   };
 
   for (;;) {
     unsigned long long start = 0;
     if (lane == 0) start = atomicAdd(P.counter, (unsigned long long)CHUNK);
     start = __shfl_sync(0xffffffffu, start, 0);
-    if ((int64_t)start >= P.n_pairs) break;
-    int64_t end = min((int64_t)start + CHUNK, P.n_pairs);
-    // element m of the first pair: pair_off[m] <= start < pair_off[m+1]
+    const int64_t p0 = P.p_begin + (int64_t)start;
+    if (p0 >= P.p_end) break;
+    const int64_t p1 = min(p0 + (int64_t)CHUNK, P.p_end);
     int64_t m;
-    if (cur_m >= 0 && P.pair_off[cur_m] <= (int64_t)start && (int64_t)start < P.pair_off[cur_m + 1]) {
+    if (cur_m >= 0 && P.pair_off[cur_m] <= p0 && p0 < P.pair_off[cur_m + 1]) {
       m = cur_m;
     } else {
-      // the last m with pair_off[m] <= start (pair_off[0] = 0 <= start < pair_off[n_elem])
+      // the last m with pair_off[m] <= p0 (pair_off[0] = 0 <= p0 < pair_off[n_elem])
       int64_t lo = 0, hi = P.n_elem;
       while (hi - lo > 1) {
         int64_t mid = (lo + hi) >> 1;
-        if (P.pair_off[mid] <= (int64_t)start) lo = mid;
+        if (P.pair_off[mid] <= p0) lo = mid;
         else hi = mid;
       }
       m = lo;
     }
-    for (int64_t p = (int64_t)start; p < end; p++) {
+    for (int64_t p = p0; p < p1; p++) {
       while (p >= P.pair_off[m + 1]) m++;
       if (m != cur_m) {
         if (cur_m >= 0) flush_self();
         cur_m = m;
 #pragma unroll
-        for (int a = 0; a < NV; a++) {
-          nodes_m[a] = P.conn[m * NV + a];
+        for (int k = 0; k < D; k++) v0m[k] = P.evert[m * NVC + k];
+        R Vm[NV][D];
+        if (F32) {
+          const float* ef = P.ef + m * G::EFS;
 #pragma unroll
-          for (int k = 0; k < D; k++) Vm[a][k] = P.evert[(m * NV + a) * D + k];
+          for (int k = 0; k < D; k++) Vm[0][k] = 0;
+#pragma unroll
+          for (int a = 1; a < NV; a++)
+#pragma unroll
+            for (int k = 0; k < D; k++) Vm[a][k] = (R)ef[(a - 1) * D + k];
+          vol_m = (R)ef[2 * D * D];
+        } else {
+#pragma unroll
+          for (int a = 0; a < NV; a++)
+#pragma unroll
+            for (int k = 0; k < D; k++) Vm[a][k] = (R)P.evert[m * NVC + a * D + k];
+          vol_m = (R)P.vol[m];
         }
 #pragma unroll
         for (int k = 0; k < D; k++) {
-          lo_m[k] = P.blo[m * D + k];
-          hi_m[k] = P.bhi[m * D + k];
-          org[k] = Vm[0][k];
-          flo_m[k] = (float)(lo_m[k] - org[k]);
-          fhi_m[k] = (float)(hi_m[k] - org[k]);
+          R lo = Vm[0][k], hi = Vm[0][k];
+#pragma unroll
+          for (int a = 1; a < NV; a++) {
+            lo = Vm[a][k] < lo ? Vm[a][k] : lo;
+            hi = Vm[a][k] > hi ? Vm[a][k] : hi;
+          }
+          lo_m[k] = lo;
+          hi_m[k] = hi;
         }
-        vol_m = (R)P.vol[m];
 #pragma unroll
         for (int i = 0; i < NYL; i++) {
           int q = ybase + i;
 #pragma unroll
           for (int k = 0; k < D; k++) {
-            double s = 0.0;
+            R s = 0;
 #pragma unroll
-            for (int a = 0; a < NV; a++) s += P.B[q][a] * (F32 ? (Vm[a][k] - org[k]) : Vm[a][k]);
-            y[i][k] = (R)s;
+            for (int a = 0; a < NV; a++) s += sB[q * NV + a] * Vm[a][k];
+            y[i][k] = s;
           }
         }
       }
       const int32_t l = P.pair_l[p];
-      // ---- per-pair set-up --------------------------------------------------------------
-      double Vl[NV][D];
+      // ---- per-pair set-up ------------------------------------------------------------------
+      R Vl[NV][D], Ji[D][D], wl;
+      if (F32) {
+        const float* ef = P.ef + (int64_t)l * G::EFS;
 #pragma unroll
-      for (int a = 0; a < NV; a++)
+        for (int k = 0; k < D; k++) Vl[0][k] = (R)(P.evert[(int64_t)l * NVC + k] - v0m[k]);
 #pragma unroll
-        for (int k = 0; k < D; k++) Vl[a][k] = P.evert[((int64_t)l * NV + a) * D + k];
-      R vl0[D], Ji[D][D];
+        for (int a = 1; a < NV; a++)
 #pragma unroll
-      for (int k = 0; k < D; k++) vl0[k] = (R)(F32 ? Vl[0][k] - org[k] : Vl[0][k]);
+          for (int k = 0; k < D; k++) Vl[a][k] = Vl[0][k] + (R)ef[(a - 1) * D + k];
 #pragma unroll
-      for (int r = 0; r < D; r++)
+        for (int r = 0; r < D; r++)
 #pragma unroll
-        for (int c = 0; c < D; c++) Ji[r][c] = (R)P.jinv[((int64_t)l * D + r) * D + c];
-      const double vol_l = P.vol[l];
-      int32_t nodes_l[NV];
+          for (int c = 0; c < D; c++) Ji[r][c] = (R)ef[D * D + r * D + c];
+        wl = (R)P.fC * (R)ef[2 * D * D];
+      } else {
 #pragma unroll
-      for (int a = 0; a < NV; a++) nodes_l[a] = P.conn[(int64_t)l * NV + a];
+        for (int a = 0; a < NV; a++)
+#pragma unroll
+          for (int k = 0; k < D; k++) Vl[a][k] = (R)P.evert[((int64_t)l * NV + a) * D + k];
+#pragma unroll
+        for (int r = 0; r < D; r++)
+#pragma unroll
+          for (int c = 0; c < D; c++) Ji[r][c] = (R)P.jinv[((int64_t)l * D + r) * D + c];
+        wl = (R)(P.C * P.vol[l]);
+      }
 
       R gp[NYL], hp[D][NYL], ug = 0, uh[D];
 #pragma unroll
@@ -436,13 +514,11 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
 #pragma unroll
       for (int k = 0; k < D; k++) uh[k] = 0;
 
-      // classification of a sub-element (Algorithm 1); V in R coordinates
+      // Algorithm 1 decision for a sub-element (R coordinates)
       auto classify = [&](const R (&V)[NV][D], uint32_t code) -> int {
-        int level = code >> LEVEL_SHIFT;
+        const int level = code >> LEVEL_SHIFT;
         if (level < P.L_min) return ACT_REFINE;
-        bool last = level == P.L_max;
-        double amax, amin;
-        bool certain_int = false, certain_not_int = false, certain_ref = false, certain_out = false;
+        const bool last = level == P.L_max;
         if (F32) {
           float fam, fan;
           float Vf[NV][D];
@@ -450,87 +526,41 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
           for (int a = 0; a < NV; a++)
 #pragma unroll
             for (int k = 0; k < D; k++) Vf[a][k] = (float)V[a][k];
-          screen_dists<D>(Vf, flo_m, fhi_m, fam, fan);
-          certain_int = fam < P.fdme - P.margin;
-          certain_not_int = fam > P.fdme + P.margin;
-          certain_ref = fan < P.fdpe - P.margin;
-          certain_out = fan > P.fdpe + P.margin;
-          if (last) {
-            if (certain_int) return ACT_INT;
-            if (certain_out) return ACT_ZERO;
-            return ACT_FINAL;
+          float flo[D], fhi[D];
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            flo[k] = (float)lo_m[k];
+            fhi[k] = (float)hi_m[k];
           }
-          if (certain_int) return ACT_INT;
-          if (certain_not_int && certain_ref) return ACT_REFINE;
-          if (certain_not_int && certain_out) return ACT_DROP;
-          double Vd[NV][D];
-          decode_exact<D>(Vl, code, Vd);
-          exact_dists<D>(Vd, lo_m, hi_m, amax, amin);
-          st_exact += (code >> LEVEL_SHIFT) == 1 ? (lane == 0) : 1;
+          screen_dists<D>(Vf, flo, fhi, fam, fan);
+          const bool c_int = fam < P.fdme - P.margin;
+          const bool c_notint = fam > P.fdme + P.margin;
+          const bool c_ref = fan < P.fdpe - P.margin;
+          const bool c_out = fan > P.fdpe + P.margin;
+          if (last) return c_int ? ACT_INT : (c_out ? ACT_ZERO : ACT_FINAL);
+          if (c_int) return ACT_INT;
+          if (c_notint && c_ref) return ACT_REFINE;
+          if (c_notint && c_out) return ACT_DROP;
+          st_exact += (level == 1) ? (lane == 0) : 1;
+          return exact_classify<D>(P.evert + (int64_t)l * NVC, P.blo + cur_m * D, P.bhi + cur_m * D,
+                                   code, P.dme, P.dpe);
         } else {
-          double Vd[NV][D];
+          double Vd[NV][D], lo2[D], hi2[D];
 #pragma unroll
           for (int a = 0; a < NV; a++)
 #pragma unroll
             for (int k = 0; k < D; k++) Vd[a][k] = (double)V[a][k];
-          exact_dists<D>(Vd, lo_m, hi_m, amax, amin);
-          if (last) {
-            if (amax < P.dme) return ACT_INT;
-            if (amin > P.dpe) return ACT_ZERO;
-            return ACT_FINAL;
-          }
-        }
-        if (amax < P.dme) return ACT_INT;
-        if (amin < P.dpe) return ACT_REFINE;
-        return ACT_DROP;
-      };
-
-      // integrate the buffered items of one kind (warp-collective)
-      auto integrate = [&](int kind, int n_it) {
-        const R* iv = wm.iv + (size_t)kind * NVC * IMAX;
-        const R* iw = wm.iw + kind * IMAX;
-        const int n_x = n_it * NQ;
-        st_eval += (unsigned long long)n_x * NQ;
-        for (int base = 0; base < n_x; base += G::XPI) {
-          int o = base + xl;
-          bool valid = o < n_x;
-          int it = valid ? o / NQ : 0;
-          int q = valid ? o - it * NQ : 0;
-          R x[D];
 #pragma unroll
           for (int k = 0; k < D; k++) {
-            R s = 0;
-#pragma unroll
-            for (int a = 0; a < NV; a++) s += sB[q * NV + a] * iv[(a * D + k) * IMAX + it];
-            x[k] = s;
+            lo2[k] = (double)lo_m[k];
+            hi2[k] = (double)hi_m[k];
           }
-          R wcx = valid ? sW[q] * iw[it] : (R)0;
-          R lam[D];
-#pragma unroll
-          for (int r = 0; r < D; r++) {
-            R s = 0;
-#pragma unroll
-            for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - vl0[c]);
-            lam[r] = s;
-          }
-#pragma unroll
-          for (int i = 0; i < NYL; i++) {
-            R r2 = 0;
-#pragma unroll
-            for (int k = 0; k < D; k++) {
-              R d = x[k] - y[i][k];
-              r2 += d * d;
-            }
-            R g = wcx;
-            if (kind == KIND_FINAL) {
-              g *= mollifier(P, r2);
-              if (P.count_band) st_band += (r2 >= P.fdme2 && r2 <= P.fdpe2 && valid) ? 1 : 0;
-            }
-            if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
-            gp[i] += g;
-#pragma unroll
-            for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
-          }
+          double amax, amin;
+          exact_dists<D>(Vd, lo2, hi2, amax, amin);
+          if (last) return amax < P.dme ? ACT_INT : (amin > P.dpe ? ACT_ZERO : ACT_FINAL);
+          if (amax < P.dme) return ACT_INT;
+          if (amin < P.dpe) return ACT_REFINE;
+          return ACT_DROP;
         }
       };
 
@@ -546,55 +576,104 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
           for (int a = 0; a < NV; a++) s += V[a][k];
           cen[k] = s * (R)(1.0 / NV);
         }
-        R wv = (R)(P.C * ldexp(vol_l, -D * (level - 1)));
+        const R wv = wl * pow2m(R(0), D * (level - 1));
         ug += wv;
 #pragma unroll
         for (int r = 0; r < D; r++) {
           R s = 0;
 #pragma unroll
-          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - vl0[c]);
+          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - Vl[0][c]);
           uh[r] += wv * s;
         }
-        st_unif++;
+        st_closed++;
       };
 
-      // ---- Algorithm 1 for this pair ----------------------------------------------------------
-      if (lane == 0) {
-        wm.ctl[0] = 0;
-        wm.ctl[1] = 0;
-        wm.ctl[2] = 0;
-      }
-      __syncwarp();
+      // integrate the buffered items of one kind (warp-collective)
+      auto integrate = [&](int kind, int n_it) {
+        const R* iv = wm.iv + (size_t)kind * NVC * IMAX;
+        const R* iw = wm.iw + kind * IMAX;
+        const int n_x = n_it * NQ;
+        st_eval += (unsigned long long)n_x * NQ;
+        for (int base = 0; base < n_x; base += G::XPI) {
+          const int o = base + xl;
+          const bool valid = o < n_x;
+          const int it = valid ? o / NQ : 0;
+          const int q = valid ? o - it * NQ : 0;
+          R x[D];
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            R s = 0;
+#pragma unroll
+            for (int a = 0; a < NV; a++) s += sB[q * NV + a] * iv[(a * D + k) * IMAX + it];
+            x[k] = s;
+          }
+          const R wcx = valid ? sW[q] * iw[it] : (R)0;
+          R lam[D];
+#pragma unroll
+          for (int r = 0; r < D; r++) {
+            R s = 0;
+#pragma unroll
+            for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - Vl[0][c]);
+            lam[r] = s;
+          }
+#pragma unroll
+          for (int i = 0; i < NYL; i++) {
+            R r2 = 0;
+#pragma unroll
+            for (int k = 0; k < D; k++) {
+              const R d = x[k] - y[i][k];
+              r2 += d * d;
+            }
+            R g = wcx;
+            if (kind == KIND_FINAL) {
+              g *= mollifier(P, r2);
+              if (P.count_band)
+                st_band += (valid && r2 >= (R)(P.dme * P.dme) && r2 <= (R)(P.dpe * P.dpe)) ? 1 : 0;
+            }
+            if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
+            gp[i] += g;
+#pragma unroll
+            for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
+          }
+        }
+      };
+
+      // append an item to a buffer slot
+      auto put_item = [&](int kind, int slot, const R (&V)[NV][D], int level) {
+        R* iv = wm.iv + (size_t)kind * NVC * IMAX;
+#pragma unroll
+        for (int t = 0; t < NVC; t++) iv[t * IMAX + slot] = V[t / D][t % D];
+        wm.iw[kind * IMAX + slot] = wl * pow2m(R(0), D * (level - 1));
+      };
+
+      // ---- Algorithm 1 for this pair --------------------------------------------------------
       {
-        R V0[NV][D];
-#pragma unroll
-        for (int a = 0; a < NV; a++)
-#pragma unroll
-          for (int k = 0; k < D; k++) V0[a][k] = (R)(F32 ? Vl[a][k] - org[k] : Vl[a][k]);
         const uint32_t code0 = 1u << LEVEL_SHIFT;
-        int act = classify(V0, code0);
+        const int act = classify(Vl, code0);
         if (lane == 0) {
+          wm.ctl[0] = 0;
+          wm.ctl[1] = 0;
+          wm.ctl[2] = 0;
           if (act == ACT_REFINE) {
 #pragma unroll
-            for (int t = 0; t < NVC; t++) wm.rv[t * P.scap] = V0[t / D][t % D];
+            for (int t = 0; t < NVC; t++) wm.rv[t * P.scap] = Vl[t / D][t % D];
             wm.rc[0] = code0;
             wm.ctl[0] = 1;
           } else if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
-            closed_int(V0, 1);
+            closed_int(Vl, 1);
           } else if (act == ACT_INT || act == ACT_FINAL) {
-            int kind = act == ACT_INT ? KIND_INT : KIND_FINAL;
-            R* iv = wm.iv + (size_t)kind * NVC * IMAX;
-#pragma unroll
-            for (int t = 0; t < NVC; t++) iv[t * IMAX] = V0[t / D][t % D];
-            wm.iw[kind * IMAX] = (R)(P.C * vol_l);
+            const int kind = act == ACT_INT ? KIND_INT : KIND_FINAL;
+            put_item(kind, 0, Vl, 1);
             wm.ctl[1 + kind] = 1;
           }
+          if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
         }
-        if (lane == 0 && (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO)) st_items++;
         __syncwarp();
       }
       for (;;) {
         int n_int = wm.ctl[1], n_fin = wm.ctl[2];
+        const int sp = wm.ctl[0];
+        __syncwarp();
         if (n_fin > IMAX - 32) {
           integrate(KIND_FINAL, n_fin);
           n_fin = 0;
@@ -603,9 +682,7 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
           integrate(KIND_INT, n_int);
           n_int = 0;
         }
-        const int sp = wm.ctl[0];
         if (sp == 0) {
-          __syncwarp();
           if (lane == 0) {
             wm.ctl[1] = n_int;
             wm.ctl[2] = n_fin;
@@ -622,8 +699,8 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
         int act = ACT_DROP;
         if (active) {
           const int slot = base + par;
-          uint32_t pcode = wm.rc[slot];
-          int plevel = pcode >> LEVEL_SHIFT;
+          const uint32_t pcode = wm.rc[slot];
+          const int plevel = pcode >> LEVEL_SHIFT;
 #pragma unroll
           for (int v = 0; v < NV; v++) {
             int ia, ib;
@@ -632,155 +709,283 @@ __global__ void __launch_bounds__(256) k_quad(const QParams P) {
             for (int k = 0; k < D; k++)
               V[v][k] = midp(wm.rv[(ia * D + k) * P.scap + slot], wm.rv[(ib * D + k) * P.scap + slot]);
           }
-          code = (((uint32_t)(plevel + 1)) << LEVEL_SHIFT) |
-                 (pcode & ((1u << LEVEL_SHIFT) - 1)) | ((uint32_t)c << (G::BITS * (plevel - 1)));
+          code = (((uint32_t)(plevel + 1)) << LEVEL_SHIFT) | (pcode & ((1u << LEVEL_SHIFT) - 1)) |
+                 ((uint32_t)c << (G::BITS * (plevel - 1)));
         }
         __syncwarp();
         if (active) act = classify(V, code);
+        const int level = code >> LEVEL_SHIFT;
+        if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
         if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
-          closed_int(V, (int)(code >> LEVEL_SHIFT));
-          st_items++;
+          closed_int(V, level);
           act = ACT_DROP;
         }
-        // append items and push refined sub-elements
         const unsigned m_int = __ballot_sync(0xffffffffu, act == ACT_INT);
         const unsigned m_fin = __ballot_sync(0xffffffffu, act == ACT_FINAL);
         const unsigned m_ref = __ballot_sync(0xffffffffu, act == ACT_REFINE);
         const unsigned below = (1u << lane) - 1u;
-        if (act == ACT_INT || act == ACT_FINAL) {
-          int kind = act == ACT_INT ? KIND_INT : KIND_FINAL;
-          int slot = (kind == KIND_INT ? n_int + __popc(m_int & below) : n_fin + __popc(m_fin & below));
-          R* iv = wm.iv + (size_t)kind * NVC * IMAX;
-#pragma unroll
-          for (int t = 0; t < NVC; t++) iv[t * IMAX + slot] = V[t / D][t % D];
-          int level = code >> LEVEL_SHIFT;
-          wm.iw[kind * IMAX + slot] = (R)(P.C * ldexp(vol_l, -D * (level - 1)));
-          st_items++;
-        }
-        if (act == ACT_ZERO) st_items++;
+        if (act == ACT_INT) put_item(KIND_INT, n_int + __popc(m_int & below), V, level);
+        if (act == ACT_FINAL) put_item(KIND_FINAL, n_fin + __popc(m_fin & below), V, level);
         const int nref = __popc(m_ref);
-        if (base + nref > P.scap) {
+        const bool overflow = base + nref > P.scap;
+        if (overflow) {
           err |= ERR_STACK;
         } else if (act == ACT_REFINE) {
-          int slot = base + __popc(m_ref & below);
+          const int slot = base + __popc(m_ref & below);
 #pragma unroll
           for (int t = 0; t < NVC; t++) wm.rv[t * P.scap + slot] = V[t / D][t % D];
           wm.rc[slot] = code;
         }
         __syncwarp();
         if (lane == 0) {
-          wm.ctl[0] = (base + nref > P.scap) ? base : base + nref;
+          wm.ctl[0] = overflow ? base : base + nref;
           wm.ctl[1] = n_int + __popc(m_int);
           wm.ctl[2] = n_fin + __popc(m_fin);
         }
         __syncwarp();
       }
       {
-        int n_int = wm.ctl[1], n_fin = wm.ctl[2];
+        const int n_int = wm.ctl[1], n_fin = wm.ctl[2];
         if (n_fin > 0) integrate(KIND_FINAL, n_fin);
         if (n_int > 0) integrate(KIND_INT, n_int);
       }
-      __syncwarp();
-      // ---- end of pair: fold, reduce, scatter the cross block --------------------------------
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ug += shfl_xor(ug, o);
-#pragma unroll
-        for (int k = 0; k < D; k++) uh[k] += shfl_xor(uh[k], o);
-      }
-#pragma unroll
-      for (int i = 0; i < NYL; i++) {
-        gself[i] += gp[i];
-        if (xl == 0) gself[i] += ug;  // once per group of lanes that share these inner points
-      }
-#pragma unroll
-      for (int i = 0; i < NYL; i++) {
-        R a0 = gp[i];
-        R ak[D];
-#pragma unroll
-        for (int k = 0; k < D; k++) ak[k] = hp[k][i];
-#pragma unroll
-        for (int o = (D == 2 ? 16 : 8); o > 0; o >>= 1) {
-          a0 += shfl_xor(a0, o);
-#pragma unroll
-          for (int k = 0; k < D; k++) ak[k] += shfl_xor(ak[k], o);
-        }
-        gp[i] = a0 + ug;
-#pragma unroll
-        for (int k = 0; k < D; k++) hp[k][i] = ak[k] + uh[k];
-      }
+      // ---- end of pair: transpose-reduce, cross block, self sums ------------------------------
       {
-        // X[a][c] = vol_m sum_y W B_a(y) H_c(y), H_0 = g - sum_k h_k, H_c = h_{c-1}
-        int t = (D == 3) ? (lane & 15) : lane;
-        R s = 0;
-        if (t < NV * NV) {
-          int a = t / NV, c = t % NV;
+        R* row = wm.red + lane * RS;
 #pragma unroll
-          for (int i = 0; i < NYL; i++) {
-            int q = ybase + i;
+        for (int i = 0; i < NYL; i++) {
+          row[i] = gp[i];
+#pragma unroll
+          for (int k = 0; k < D; k++) row[(k + 1) * NYL + i] = hp[k][i];
+        }
+        row[NYL * NV] = ug;
+#pragma unroll
+        for (int k = 0; k < D; k++) row[NYL * NV + 1 + k] = uh[k];
+      }
+      __syncwarp();
+      // totals: tot[v*NQ + q] for v = 0 (g), 1..D (h_k) over the NQ inner points, then the
+      // D+1 uniform sums at tot[NQ*NV + v]
+      if (D == 2) {
+        if (lane < G::NRED) {
+          R s = 0;
+#pragma unroll 8
+          for (int src = 0; src < 32; src++) s += wm.red[src * RS + lane];
+          wm.tot[lane] = s;
+        }
+      } else {
+        // lanes 0..15 hold inner points 0..6, lanes 16..31 hold 7..13
+        if (lane < NYL * NV) {
+          R s0 = 0, s1 = 0;
+#pragma unroll 8
+          for (int src = 0; src < 16; src++) {
+            s0 += wm.red[src * RS + lane];
+            s1 += wm.red[(src + 16) * RS + lane];
+          }
+          const int v = lane / NYL, i = lane % NYL;
+          wm.tot[v * NQ + i] = s0;
+          wm.tot[v * NQ + 7 + i] = s1;
+        } else if (lane < NYL * NV + NV) {
+          R s = 0;
+#pragma unroll 8
+          for (int src = 0; src < 32; src++) s += wm.red[src * RS + lane];
+          wm.tot[NQ * NV + (lane - NYL * NV)] = s;
+        }
+      }
+      __syncwarp();
+      {
+        const R* tot = wm.tot;
+        if (lane < NBLK) {
+          const int a = lane / NV, c = lane % NV;
+          R s = 0;
+#pragma unroll
+          for (int q = 0; q < NQ; q++) {
             R H;
             if (c == 0) {
-              H = gp[i];
+              H = tot[q] + tot[NQ * NV];
 #pragma unroll
-              for (int k = 0; k < D; k++) H -= hp[k][i];
+              for (int k = 0; k < D; k++) H -= tot[(k + 1) * NQ + q] + tot[NQ * NV + 1 + k];
             } else {
-              H = hp[0][i];
-#pragma unroll
-              for (int k = 1; k < D; k++) H = (c - 1 == k) ? hp[k][i] : H;
+              H = tot[c * NQ + q] + tot[NQ * NV + c];
             }
             s += sWB[q * NV + a] * H;
           }
+          reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + lane] = (R)(-2) * vol_m * s;
         }
-        if (D == 3) s += shfl_xor(s, 16);
-        if (lane < NV * NV) {
-          int a = lane / NV, c = lane % NV;
-          double val = -2.0 * (double)vol_m * (double)s;
-          int64_t pos = csr_find(P.row_ptr, P.col, nodes_m[a], nodes_l[c]);
-          if (pos < 0) err |= ERR_CSR;
-          else atomicAdd(&P.values[pos], val);
-        }
+        if (lane < NQ) two_sum_add(gs_hi, gs_lo, tot[lane] + tot[NQ * NV]);
       }
+      __syncwarp();
     }
   }
   if (cur_m >= 0) flush_self();
-  // statistics and errors
   for (int o = 16; o > 0; o >>= 1) {
     st_items += __shfl_xor_sync(0xffffffffu, st_items, o);
     st_exact += __shfl_xor_sync(0xffffffffu, st_exact, o);
-    st_unif += __shfl_xor_sync(0xffffffffu, st_unif, o);
+    st_closed += __shfl_xor_sync(0xffffffffu, st_closed, o);
     st_band += __shfl_xor_sync(0xffffffffu, st_band, o);
     err |= __shfl_xor_sync(0xffffffffu, err, o);
   }
   if (lane == 0) {
     atomicAdd(&P.stats[0], st_items);
     atomicAdd(&P.stats[2], st_exact);
-    atomicAdd(&P.stats[3], st_eval);
-    atomicAdd(&P.stats[4], st_unif);
+    atomicAdd(&P.stats[3], st_eval);  // every lane counted the same evaluated pairs
+    atomicAdd(&P.stats[4], st_closed);
     atomicAdd(&P.stats[5], st_band);
     if (err) atomicOr(P.err, err);
   }
 }
 
+// ---- scatter of the local blocks into the CSR values ------------------------------------------
+// One CTA per inner element m: the column lists of the rows of m's nodes are cached in shared
+// memory; every cross block of the pairs of m in [p_begin, p_end) is added with FP64 atomics
+// after a binary search in the cached row, and (with_self) the self block of m.
+template <int D, typename R>
+__global__ void __launch_bounds__(128) k_scatter(int64_t m_begin, int64_t p_begin, int64_t p_end,
+                                                 const int64_t* __restrict__ pair_off,
+                                                 const int32_t* __restrict__ pair_l,
+                                                 const int32_t* __restrict__ conn,
+                                                 const int64_t* __restrict__ row_ptr,
+                                                 const int32_t* __restrict__ col,
+                                                 const R* __restrict__ blk,
+                                                 const double* __restrict__ selfblk, int with_self,
+                                                 double* __restrict__ values, int* __restrict__ err) {
+  constexpr int NV = D + 1, NB = NV * NV;
+  extern __shared__ int32_t rows[];
+  __shared__ int64_t rbeg[NV];
+  __shared__ int rlen[NV], roff[NV + 1];
+  __shared__ int32_t nodes[NV];
+  const int64_t m = m_begin + blockIdx.x;
+  if (threadIdx.x < NV) {
+    int32_t i = conn[m * NV + threadIdx.x];
+    nodes[threadIdx.x] = i;
+    rbeg[threadIdx.x] = row_ptr[i];
+    rlen[threadIdx.x] = (int)(row_ptr[i + 1] - row_ptr[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    roff[0] = 0;
+    for (int a = 0; a < NV; a++) roff[a + 1] = roff[a] + rlen[a];
+  }
+  __syncthreads();
+  for (int a = 0; a < NV; a++)
+    for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) rows[roff[a] + t] = col[rbeg[a] + t];
+  __syncthreads();
+  auto find = [&](int a, int32_t j) -> int64_t {
+    int lo = 0, hi = rlen[a] - 1;
+    const int32_t* r = rows + roff[a];
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1;
+      int32_t c = r[mid];
+      if (c == j) return rbeg[a] + mid;
+      if (c < j) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    return -1;
+  };
+  if (!with_self) {
+    const int64_t q0 = max(pair_off[m], p_begin), q1 = min(pair_off[m + 1], p_end);
+    const int64_t n = (q1 - q0) * NB;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+      const int64_t p = q0 + t / NB;
+      const int e = (int)(t % NB);
+      const int a = e / NV, c = e % NV;
+      const int32_t l = pair_l[p];
+      const int64_t pos = find(a, conn[(int64_t)l * NV + c]);
+      if (pos < 0) {
+        atomicOr(err, ERR_CSR);
+        continue;
+      }
+      atomicAdd(&values[pos], (double)blk[(p - p_begin) * NB + e]);
+    }
+  } else if (threadIdx.x < NB) {
+    const int a = threadIdx.x / NV, b = threadIdx.x % NV;
+    const int64_t pos = find(a, nodes[b]);
+    if (pos < 0) atomicOr(err, ERR_CSR);
+    else atomicAdd(&values[pos], selfblk[m * NB + threadIdx.x]);
+  }
+}
+
 template <int D, typename R, int KERN>
-nl_status launch_quad(const QParams& P, cudaStream_t s, int* blocks_out) {
+nl_status launch_quad(const QParams& P, cudaStream_t s) {
   int dev = 0;
   NL_CUDA(cudaGetDevice(&dev));
   int nsm = 0;
   NL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  size_t tbl = (sizeof(R) * (14 * 4 * 2 + 16) + 15) & ~size_t(15);
+  size_t tbl = table_bytes<R>();
   int warps = 8;
-  while (warps > 1 && tbl + warps * WarpMem<D, R>::bytes(P.scap) > (size_t)200 * 1024) warps >>= 1;
+  while (warps > 1 && tbl + warps * WarpMem<D, R>::bytes(P.scap) > (size_t)110 * 1024) warps >>= 1;
   const int threads = warps * 32;
   size_t smem = tbl + warps * WarpMem<D, R>::bytes(P.scap);
-  if (smem > (size_t)220 * 1024) return fail(NL_EINTERNAL, "assembly kernel needs %zu bytes of shared memory", smem);
+  if (smem > (size_t)220 * 1024)
+    return fail(NL_EINTERNAL, "assembly kernel needs %zu bytes of shared memory", smem);
   NL_CUDA(cudaFuncSetAttribute(k_quad<D, R, KERN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quad<D, R, KERN>, threads, smem));
   if (per_sm < 1) return fail(NL_EINTERNAL, "assembly kernel does not fit on an SM (smem %zu)", smem);
-  int blocks = nsm * per_sm;
-  k_quad<D, R, KERN><<<NL_CNT(blocks), threads, smem, s>>>(P);
+  k_quad<D, R, KERN><<<NL_CNT(nsm * per_sm), threads, smem, s>>>(P);
   NL_CUDA(cudaGetLastError());
-  if (blocks_out) *blocks_out = blocks;
+  return NL_OK;
+}
+
+template <int D, typename R>
+nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end, const R* blk,
+                         const double* selfblk, int with_self, double* values, int* err,
+                         cudaStream_t s, const int64_t* h_pair_off) {
+  int64_t m_begin = 0, m_end = m->n_elem;
+  if (!with_self) {
+    // inner elements whose pairs intersect [p_begin, p_end)
+    const int64_t* po = h_pair_off;
+    m_begin = std::upper_bound(po, po + m->n_elem + 1, p_begin) - po - 1;
+    m_end = std::lower_bound(po, po + m->n_elem + 1, p_end) - po;
+    m_begin = std::max<int64_t>(0, m_begin);
+    m_end = std::min<int64_t>(m->n_elem, std::max(m_end, m_begin));
+  }
+  if (m_end <= m_begin) return NL_OK;
+  size_t smem = sizeof(int32_t) * (size_t)(D + 1) * std::max(1, p->max_row_nnz);
+  if (smem > (size_t)200 * 1024)
+    return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
+  NL_CUDA(cudaFuncSetAttribute(k_scatter<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_scatter<D, R><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
+      m_begin, p_begin, p_end, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, blk, selfblk,
+      with_self, values, err);
+  NL_CUDA(cudaGetLastError());
+  return NL_OK;
+}
+
+template <int D, typename R, int KERN>
+nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s,
+                       unsigned long long* scratch, int* err) {
+  const int NB = (D + 1) * (D + 1);
+  // the block buffer holds the cross blocks of one batch of pairs
+  size_t free_b = 0, total_b = 0;
+  NL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
+  int64_t batch = std::max<int64_t>(1 << 20, (int64_t)(budget / (sizeof(R) * NB)));
+  batch = std::min<int64_t>(batch, p->n_pairs);
+  DevBuf<R> blk;
+  DevBuf<double> selfblk;
+  NL_TRY(blk.alloc((size_t)batch * NB, s));
+  NL_TRY(selfblk.alloc((size_t)m->n_elem * NB, s));
+  NL_CUDA(cudaMemsetAsync(selfblk.p, 0, sizeof(double) * m->n_elem * NB, s));
+  std::vector<int64_t> h_off(m->n_elem + 1);
+  NL_CUDA(cudaMemcpyAsync(h_off.data(), p->pair_off, sizeof(int64_t) * (m->n_elem + 1),
+                          cudaMemcpyDeviceToHost, s));
+  NL_CUDA(cudaStreamSynchronize(s));
+  P.blk = blk.p;
+  P.selfblk = selfblk.p;
+  for (int64_t b0 = 0; b0 < p->n_pairs; b0 += batch) {
+    const int64_t b1 = std::min(p->n_pairs, b0 + batch);
+    P.p_begin = b0;
+    P.p_end = b1;
+    NL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s));  // work counter
+    NL_TRY((launch_quad<D, R, KERN>(P, s)));
+    NL_TRY((launch_scatter<D, R>(m, p, b0, b1, blk.p, nullptr, 0, values, err, s, h_off.data())));
+  }
+  NL_TRY((launch_scatter<D, R>(m, p, 0, 0, blk.p, selfblk.p, 1, values, err, s, h_off.data())));
+  if (std::is_same<R, float>::value) {
+    k_diag_from_rows<<<NL_CNT((unsigned)((m->n_vert * 32 + 255) / 256)), 256, 0, s>>>(
+        m->n_vert, p->row_ptr, p->col, values);
+    NL_CUDA(cudaGetLastError());
+  }
   return NL_OK;
 }
 
@@ -803,19 +1008,16 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   cudaStream_t s = m->stream;
   QParams P;
   memset(&P, 0, sizeof P);
-  P.n_pairs = p->n_pairs;
   P.n_elem = m->n_elem;
   P.pair_off = p->pair_off;
   P.pair_l = p->pair_l;
-  P.row_ptr = p->row_ptr;
-  P.col = p->col;
   P.conn = m->conn;
   P.evert = m->evert;
   P.blo = m->blo;
   P.bhi = m->bhi;
   P.vol = m->vol;
   P.jinv = m->jinv;
-  P.values = values;
+  P.ef = m->ef;
   double C = kp->C_override > 0.0 ? kp->C_override
                                   : kernel_constant(D, kp->kernel, kp->delta, kp->eps);
   if (kp->kappa > 0.0) C *= kp->kappa;
@@ -823,6 +1025,7 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   P.dme = kp->delta - kp->eps;
   P.dpe = kp->delta + kp->eps;
   P.C = C;
+  P.fC = (float)C;
   P.inv_eps = 1.0 / kp->eps;
   P.inv_delta2 = 1.0 / (kp->delta * kp->delta);
   P.fdelta = (float)kp->delta;
@@ -833,11 +1036,11 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   P.fdpe2 = (float)(P.dpe * P.dpe);
   P.finv_delta2 = (float)P.inv_delta2;
   // bound on |local coordinates| and on the FP32 error of the screened distances
-  double R = kp->delta + kp->eps + 2.0 * m->max_ext;
-  P.margin = (float)(2e-5 * R);
+  double Rb = kp->delta + kp->eps + 2.0 * m->max_ext;
+  P.margin = (float)(2e-5 * Rb);
   P.L_min = qp->L_min;
-  P.count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
   P.L_max = qp->L_max;
+  P.count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
   int64_t total = 0, pw = 1;
   for (int k = 1; k < qp->L_max; k++) {
     total += pw;
@@ -865,15 +1068,19 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   NL_CUDA(cudaEventCreate(&e1));
   NL_CUDA(cudaEventRecord(e0, s));
   nl_status rc = NL_OK;
-  bool f32 = prec != NL_PREC_FP64;
-  bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
+  const bool f32 = prec != NL_PREC_FP64;
+  const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
   if (p->n_pairs > 0) {
     if (D == 2) {
-      if (f32) rc = gauss ? launch_quad<2, float, 1>(P, s, nullptr) : launch_quad<2, float, 0>(P, s, nullptr);
-      else rc = gauss ? launch_quad<2, double, 1>(P, s, nullptr) : launch_quad<2, double, 0>(P, s, nullptr);
+      if (f32) rc = gauss ? run_assembly<2, float, 1>(m, p, P, values, s, scratch.p, err.p)
+                          : run_assembly<2, float, 0>(m, p, P, values, s, scratch.p, err.p);
+      else rc = gauss ? run_assembly<2, double, 1>(m, p, P, values, s, scratch.p, err.p)
+                      : run_assembly<2, double, 0>(m, p, P, values, s, scratch.p, err.p);
     } else {
-      if (f32) rc = gauss ? launch_quad<3, float, 1>(P, s, nullptr) : launch_quad<3, float, 0>(P, s, nullptr);
-      else rc = gauss ? launch_quad<3, double, 1>(P, s, nullptr) : launch_quad<3, double, 0>(P, s, nullptr);
+      if (f32) rc = gauss ? run_assembly<3, float, 1>(m, p, P, values, s, scratch.p, err.p)
+                          : run_assembly<3, float, 0>(m, p, P, values, s, scratch.p, err.p);
+      else rc = gauss ? run_assembly<3, double, 1>(m, p, P, values, s, scratch.p, err.p)
+                      : run_assembly<3, double, 0>(m, p, P, values, s, scratch.p, err.p);
     }
   }
   cudaEventRecord(e1, s);

@@ -47,9 +47,9 @@ CASES = [
     ("jit2d_Lmin2", lambda: structured_mesh(2, 7, 1 / 7, 0.0, 2, jitter=0.1, seed=4), 0.2, 0.04, 3, 2, 0),
     ("gauss2d", lambda: structured_mesh(2, 8, 1 / 8, 0.0, 2, jitter=0.1, seed=5), 0.2, 0.01, 3, 1, 1),
     ("rect2d", lambda: workload_mesh(table2_tri(2)), 0.2, 0.0125, 3, 1, 0),
-    ("jit3d", lambda: structured_mesh(3, 4, 0.25, 0.0, 2, jitter=0.1, seed=7), 0.4, 0.04, 2, 1, 0),
-    ("gauss3d", lambda: structured_mesh(3, 3, 1 / 3, 0.0, 2, jitter=0.1, seed=8), 0.5, 0.1, 2, 1, 1),
-    ("deep3d", lambda: structured_mesh(3, 2, 0.5, 0.0, 1, jitter=0.05, seed=9), 0.6, 0.05, 3, 1, 0),
+    ("jit3d", lambda: structured_mesh(3, 3, 1 / 3, 0.0, 1, jitter=0.1, seed=7), 0.22, 0.02, 2, 1, 0),
+    ("gauss3d", lambda: structured_mesh(3, 2, 0.5, 0.0, 1, jitter=0.1, seed=8), 0.3, 0.06, 2, 1, 1),
+    ("deep3d", lambda: structured_mesh(3, 2, 0.5, 0.0, 0, jitter=0.05, seed=9), 0.4, 0.05, 3, 1, 0),
 ]
 
 
@@ -83,10 +83,12 @@ def test_deep_refinement_2d():
     # L_max = 7 on a tiny mesh: deep LIFO and many FP32 screens near the thresholds; the
     # decisions must agree exactly (identical Algorithm-1 counts).  Every pair sums ~1.3e5
     # point pairs, so the FP64 values agree only to the rounding of sums that long
-    # (sequential in the oracle, tree-shaped on the GPU): 1e-11 here.
+    # (sequential in the oracle, tree-shaped on the GPU): 1e-11 here.  In FP32 each lane
+    # accumulates ~600 point pairs per inner point and pair, so the FP32 tolerance grows with
+    # that count: 2e-5 here.
     mesh = structured_mesh(2, 2, 0.5, 0.0, 1, jitter=0.1, seed=2)
     *_, ovals, ost = _oracle(mesh, 0.3, 0.02, 7)
-    for prec, tol in ((nl.NL_PREC_FP64, 1e-11), (nl.NL_PREC_FP32, TOL32)):
+    for prec, tol in ((nl.NL_PREC_FP64, 1e-11), (nl.NL_PREC_FP32, 2e-5)):
         *_, vals, st, _ = _gpu(mesh, 0.3, 0.02, 7, precision=prec)
         assert st.n_point_pairs == ost.n_point_pairs
         assert st.n_items == ost.n_integrations
