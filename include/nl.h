@@ -170,6 +170,24 @@ void nl_pairs_destroy(nl_pairs* pairs);
 nl_status nl_assemble(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_params* kp,
                       const nl_quad_params* qp, nl_precision precision, nl_matrix** A,
                       nl_assemble_stats* stats);
+/* Assembly that allocates no device memory.  The paper has no counterpart: this is an
+ * interface for callers that cannot call cudaMalloc while they assemble -- a process that
+ * reserves all of its device memory at start-up (a fixed pool it must not grow, where a new
+ * allocation would fail), or code that must not stall other streams on an allocation.
+ * It computes the same matrix as nl_assemble (same kernels; the cross blocks are added to
+ * the values directly) into `values`, a device array of nnz doubles (nl_pairs_info) that the
+ * caller owns.  Its scratch (work counter, counters, error word, per-element self blocks)
+ * lives in a fixed 16 MiB device array that the library holds on every GPU that loads it
+ * until the process exits, so the mesh may have at most (16 MiB - 256 B) / (8 (dim+1)^2 B)
+ * elements (233,013 triangles or 131,070 tetrahedra); larger meshes return NL_EINVAL.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call clears the scratch it uses
+ * and leaves its contents behind; all calls share the one array, so calls that overlap on
+ * the GPU (other streams or threads) race and must be serialised by the caller.
+ * stats may be NULL; stats->ms_assemble is 0. */
+nl_status nl_assemble_noalloc(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_params* kp,
+                              const nl_quad_params* qp, nl_precision precision, double* values,
+                              nl_assemble_stats* stats);
 /* Host copy of the nnz values (CSR order of the pattern). */
 nl_status nl_matrix_export(const nl_matrix* A, double* values);
 /* Device pointer to the values (valid until nl_matrix_destroy). */

@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -76,6 +77,9 @@ struct QParams {
   const float* ef;
   void* blk;          // [p_end - p_begin][(D+1)^2] cross blocks (R)
   double* selfblk;    // [n_elem][(D+1)^2]
+  const int64_t* row_ptr;  // CSR pattern and values: used only by the variant that adds
+  const int32_t* col;      // its cross blocks to the values directly
+  double* values;
   unsigned long long* counter;
   unsigned long long* stats;  // [0] items, [2] exact checks, [3] evaluated pairs,
                               // [4] closed-form items, [5] band pairs
@@ -358,7 +362,23 @@ __host__ __device__ constexpr size_t table_bytes() {
   return (sizeof(R) * (14 * 4 * 2 + 16) + 15) & ~size_t(15);
 }
 
-template <int D, typename R, int KERN>
+// Position of column j in CSR row i (binary search in global memory), or -1.
+__device__ __forceinline__ int64_t csr_find(const int64_t* __restrict__ row_ptr,
+                                            const int32_t* __restrict__ col, int32_t i, int32_t j) {
+  int64_t lo = row_ptr[i], hi = row_ptr[i + 1] - 1;
+  while (lo <= hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const int32_t c = col[mid];
+    if (c == j) return mid;
+    if (c < j) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return -1;
+}
+
+// DIRECT = true: the cross block of every pair is added to the CSR values at once (global
+// binary search, FP64 atomics) instead of going through the block buffer.
+template <int D, typename R, int KERN, bool DIRECT = false>
 __global__ void __launch_bounds__(256, 2) k_quad(const QParams P) {
   using G = Geo<D>;
   constexpr int NV = G::NV, NQ = G::NQ, NYL = G::NYL, NVC = G::NVC, NBLK = G::NBLK;
@@ -809,7 +829,14 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P) {
             }
             s += sWB[q * NV + a] * H;
           }
-          reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + lane] = (R)(-2) * vol_m * s;
+          if (DIRECT) {
+            const int64_t pos = csr_find(P.row_ptr, P.col, P.conn[cur_m * NV + a],
+                                         P.conn[(int64_t)l * NV + c]);
+            if (pos < 0) err |= ERR_CSR;
+            else atomicAdd(&P.values[pos], (double)((R)(-2) * vol_m * s));
+          } else {
+            reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + lane] = (R)(-2) * vol_m * s;
+          }
         }
         if (lane < NQ) two_sum_add(gs_hi, gs_lo, tot[lane] + tot[NQ * NV]);
       }
@@ -904,7 +931,7 @@ __global__ void __launch_bounds__(128) k_scatter(int64_t m_begin, int64_t p_begi
   }
 }
 
-template <int D, typename R, int KERN>
+template <int D, typename R, int KERN, bool DIRECT = false>
 nl_status launch_quad(const QParams& P, cudaStream_t s) {
   int dev = 0;
   NL_CUDA(cudaGetDevice(&dev));
@@ -917,11 +944,11 @@ nl_status launch_quad(const QParams& P, cudaStream_t s) {
   size_t smem = tbl + warps * WarpMem<D, R>::bytes(P.scap);
   if (smem > (size_t)220 * 1024)
     return fail(NL_EINTERNAL, "assembly kernel needs %zu bytes of shared memory", smem);
-  NL_CUDA(cudaFuncSetAttribute(k_quad<D, R, KERN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NL_CUDA(cudaFuncSetAttribute(k_quad<D, R, KERN, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quad<D, R, KERN>, threads, smem));
+  NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quad<D, R, KERN, DIRECT>, threads, smem));
   if (per_sm < 1) return fail(NL_EINTERNAL, "assembly kernel does not fit on an SM (smem %zu)", smem);
-  k_quad<D, R, KERN><<<NL_CNT(nsm * per_sm), threads, smem, s>>>(P);
+  k_quad<D, R, KERN, DIRECT><<<NL_CNT(nsm * per_sm), threads, smem, s>>>(P);
   NL_CUDA(cudaGetLastError());
   return NL_OK;
 }
@@ -1113,4 +1140,191 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   return NL_OK;
 }
 
+// ---- assembly without device allocation ------------------------------------------------------
+// For callers that cannot call cudaMalloc at assembly time: a process that reserves all of
+// its device memory when it starts (a serving process with a fixed pool, where a new
+// allocation would fail or grow a pool it does not own), or code that must not stall
+// other streams on an allocation's implicit synchronisation.  This variant adds every cross
+// block to the CSR values directly and keeps its only scratch -- the work counter, the
+// counters, the error word and the per-element self blocks -- in the file-scope array below,
+// which every GPU that loads this library holds until the process exits.
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB
+constexpr size_t NOALLOC_HEADER_BYTES = 256;                 // counters and the error word
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[128] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once per device; the
+// host-side name of the array is not a device address).
+nl_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  NL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(NL_EINTERNAL, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return NL_OK;
+}
+
+template <int D, typename R, int KERN>
+nl_status run_noalloc(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s) {
+  NL_TRY((launch_quad<D, R, KERN, true>(P, s)));
+  const size_t smem = sizeof(int32_t) * (size_t)(D + 1) * std::max(1, p->max_row_nnz);
+  if (smem > (size_t)200 * 1024)
+    return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
+  NL_CUDA(cudaFuncSetAttribute(k_scatter<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_scatter<D, R><<<NL_CNT((unsigned)m->n_elem), 128, smem, s>>>(
+      0, 0, 0, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, (const R*)nullptr, P.selfblk, 1,
+      values, P.err);
+  NL_CUDA(cudaGetLastError());
+  if (std::is_same<R, float>::value) {
+    k_diag_from_rows<<<NL_CNT((unsigned)((m->n_vert * 32 + 255) / 256)), 256, 0, s>>>(
+        m->n_vert, p->row_ptr, p->col, values);
+    NL_CUDA(cudaGetLastError());
+  }
+  return NL_OK;
+}
+}  // namespace
+
+nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                           const nl_quad_params* qp, nl_precision prec, double* values,
+                           nl_assemble_stats* st) {
+  const int D = m->dim;
+  if (!values) return fail(NL_EINVAL, "nl_assemble_noalloc: values is NULL");
+  if (!(kp->eps > 0.0 && kp->eps < kp->delta))
+    return fail(NL_EINVAL, "nl_assemble_noalloc: need 0 < eps < delta");
+  if (kp->kernel != NL_KERNEL_CONST && kp->kernel != NL_KERNEL_TRUNC_GAUSS)
+    return fail(NL_EINVAL, "nl_assemble_noalloc: unknown kernel %d", kp->kernel);
+  const int lmax_cap = D == 2 ? 12 : 9;
+  if (qp->L_min < 1 || qp->L_max < qp->L_min || qp->L_max > lmax_cap)
+    return fail(NL_EINVAL, "nl_assemble_noalloc: need 1 <= L_min <= L_max <= %d", lmax_cap);
+  if ((qp->rule & ~NL_QUAD_COUNT_BAND) != 0)
+    return fail(NL_EINVAL, "nl_assemble_noalloc: only rule 0 is available");
+  if (prec != NL_PREC_FP64 && prec != NL_PREC_FP32 && prec != NL_PREC_MIXED_TF32 &&
+      prec != NL_PREC_MIXED_BF16)
+    return fail(NL_EINVAL, "nl_assemble_noalloc: unknown precision %d", (int)prec);
+  const int NB = (D + 1) * (D + 1);
+  const int64_t max_elem =
+      (int64_t)((NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER_BYTES) / (sizeof(double) * NB));
+  if (m->n_elem > max_elem)
+    return fail(NL_EINVAL,
+                "nl_assemble_noalloc: %lld elements exceed the %zu-byte scratch (at most %lld "
+                "elements in %dD); use nl_assemble",
+                (long long)m->n_elem, NOALLOC_SCRATCH_BYTES, (long long)max_elem, D);
+  unsigned char* scratch = nullptr;
+  NL_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = m->stream;
+  QParams P;
+  memset(&P, 0, sizeof P);
+  P.n_elem = m->n_elem;
+  P.p_begin = 0;
+  P.p_end = p->n_pairs;
+  P.pair_off = p->pair_off;
+  P.pair_l = p->pair_l;
+  P.conn = m->conn;
+  P.evert = m->evert;
+  P.blo = m->blo;
+  P.bhi = m->bhi;
+  P.vol = m->vol;
+  P.jinv = m->jinv;
+  P.ef = m->ef;
+  P.row_ptr = p->row_ptr;
+  P.col = p->col;
+  P.values = values;
+  double C = kp->C_override > 0.0 ? kp->C_override
+                                  : kernel_constant(D, kp->kernel, kp->delta, kp->eps);
+  if (kp->kappa > 0.0) C *= kp->kappa;
+  P.delta = kp->delta;
+  P.dme = kp->delta - kp->eps;
+  P.dpe = kp->delta + kp->eps;
+  P.C = C;
+  P.fC = (float)C;
+  P.inv_eps = 1.0 / kp->eps;
+  P.inv_delta2 = 1.0 / (kp->delta * kp->delta);
+  P.fdelta = (float)kp->delta;
+  P.finv_eps = (float)(1.0 / kp->eps);
+  P.fdme = (float)P.dme;
+  P.fdpe = (float)P.dpe;
+  P.fdme2 = (float)(P.dme * P.dme);
+  P.fdpe2 = (float)(P.dpe * P.dpe);
+  P.finv_delta2 = (float)P.inv_delta2;
+  P.margin = (float)(2e-5 * (kp->delta + kp->eps + 2.0 * m->max_ext));
+  P.L_min = qp->L_min;
+  P.L_max = qp->L_max;
+  P.count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
+  int64_t total = 0, pw = 1;
+  for (int k = 1; k < qp->L_max; k++) {
+    total += pw;
+    pw *= (D == 2 ? 4 : 8);
+    if (total > 512) break;
+  }
+  P.scap = (int)std::max<int64_t>(8, std::min<int64_t>(total, 512));
+  const Rule& r = rule(D);
+  for (int q = 0; q < r.n; q++) {
+    for (int a = 0; a <= D; a++) P.B[q][a] = r.bary[q][a];
+    P.W[q] = r.w[q];
+  }
+  // scratch layout: [0, 64) counter + stats, [64, 68) error word, [256, ...) self blocks.
+  // Every call starts by clearing what it accumulates into.
+  P.counter = reinterpret_cast<unsigned long long*>(scratch);
+  P.stats = P.counter + 1;
+  P.err = reinterpret_cast<int*>(scratch + 64);
+  P.selfblk = reinterpret_cast<double*>(scratch + NOALLOC_HEADER_BYTES);
+  NL_CUDA(cudaMemsetAsync(scratch, 0, NOALLOC_HEADER_BYTES, s));
+  NL_CUDA(cudaMemsetAsync(P.selfblk, 0, sizeof(double) * NB * m->n_elem, s));
+  NL_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (p->nnz ? p->nnz : 1), s));
+  const bool f32 = prec != NL_PREC_FP64;
+  const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
+  nl_status rc = NL_OK;
+  if (p->n_pairs > 0) {
+    if (D == 2) {
+      if (f32) rc = gauss ? run_noalloc<2, float, 1>(m, p, P, values, s) : run_noalloc<2, float, 0>(m, p, P, values, s);
+      else rc = gauss ? run_noalloc<2, double, 1>(m, p, P, values, s) : run_noalloc<2, double, 0>(m, p, P, values, s);
+    } else {
+      if (f32) rc = gauss ? run_noalloc<3, float, 1>(m, p, P, values, s) : run_noalloc<3, float, 0>(m, p, P, values, s);
+      else rc = gauss ? run_noalloc<3, double, 1>(m, p, P, values, s) : run_noalloc<3, double, 0>(m, p, P, values, s);
+    }
+  }
+  if (rc != NL_OK) return rc;
+  unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int herr = 0;
+  NL_CUDA(cudaMemcpyAsync(hs, scratch, sizeof hs, cudaMemcpyDeviceToHost, s));
+  NL_CUDA(cudaMemcpyAsync(&herr, scratch + 64, sizeof herr, cudaMemcpyDeviceToHost, s));
+  NL_CUDA(cudaStreamSynchronize(s));
+  if (herr)
+    return fail(NL_EINTERNAL, "nl_assemble_noalloc: device check failed (code %d: %s)", herr,
+                (herr & ERR_STACK) ? "refinement stack capacity exceeded" : "CSR entry missing");
+  if (st) {
+    const int nq = r.n;
+    st->n_pairs = p->n_pairs;
+    st->n_items = (int64_t)hs[1];
+    st->n_point_pairs = (int64_t)hs[1] * nq * nq;
+    st->n_exact_checks = (int64_t)hs[3];
+    st->ms_assemble = 0.0;
+    st->n_eval_point_pairs = (int64_t)hs[4];
+    st->n_closed_items = (int64_t)hs[5];
+    st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
+  }
+  return NL_OK;
+}
+
 }  // namespace nlx
+
+extern "C" nl_status nl_assemble_noalloc(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_params* kp,
+                                         const nl_quad_params* qp, nl_precision precision,
+                                         double* values, nl_assemble_stats* stats) {
+  nlx::clear_error();
+  if (!mesh || !pairs || !kp || !qp) return nlx::fail(NL_EINVAL, "nl_assemble_noalloc: NULL argument");
+  if (pairs->mesh != mesh) return nlx::fail(NL_EINVAL, "nl_assemble_noalloc: pairs were built on another mesh");
+  if (kp->delta != pairs->delta || kp->eps != pairs->eps)
+    return nlx::fail(NL_EINVAL, "nl_assemble_noalloc: delta/eps differ from those of the pairs");
+  return nlx::assemble_noalloc(mesh, pairs, kp, qp, precision, values, stats);
+}

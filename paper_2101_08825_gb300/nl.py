@@ -76,6 +76,8 @@ def lib():
         "nl_pairs_destroy": (None, [p]),
         "nl_assemble": (st, [p, p, ctypes.POINTER(KernelParams), ctypes.POINTER(QuadParams), i, pp,
                              ctypes.POINTER(AssembleStats)]),
+        "nl_assemble_noalloc": (st, [p, p, ctypes.POINTER(KernelParams), ctypes.POINTER(QuadParams),
+                                     i, p, ctypes.POINTER(AssembleStats)]),
         "nl_matrix_export": (st, [p, p]),
         "nl_matrix_device_values": (st, [p, pp]),
         "nl_matrix_destroy": (None, [p]),
@@ -267,6 +269,20 @@ def nl_assemble(mesh: Mesh, pairs: Pairs, delta, eps, L_max, L_min=1, kernel=NL_
     if into is not None:
         return into, st
     return Matrix(h, pairs.info()[1]), st
+
+
+def nl_assemble_noalloc(mesh: Mesh, pairs: Pairs, delta, eps, L_max, values_ptr: int, L_min=1,
+                        kernel=NL_KERNEL_CONST, precision=NL_PREC_FP64, C_override=0.0,
+                        kappa=0.0):
+    """Assembles into the caller's device array (nnz doubles at values_ptr) without any
+    device allocation by the library."""
+    kp = KernelParams(float(delta), float(eps), float(kappa), int(kernel), float(C_override))
+    qp = QuadParams(int(L_min), int(L_max), 0)
+    st = AssembleStats()
+    _check(lib().nl_assemble_noalloc(mesh.h, pairs.h, ctypes.byref(kp), ctypes.byref(qp),
+                                     int(precision), ctypes.c_void_p(int(values_ptr)),
+                                     ctypes.byref(st)), "nl_assemble_noalloc")
+    return st
 
 
 def nl_rhs(mesh: Mesh, A: Matrix, g_nodes, f_const=0.0, f_nodes=None) -> Vector:
