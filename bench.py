@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the seeded 512-request serving stream replayed by the "
+                         "serving leg (0 = skip; 512 = the whole stream)")
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--profile", action="store_true",
                     help="one pair build and one FP32 and one FP64 assembly of the 2D workload "
                          "at h=1/128 (a small case for ncu), then exit")
@@ -148,6 +152,16 @@ def workload(name):
     w = WORKLOADS[name]
     mesh = workload_mesh(w)
     return w, mesh
+
+
+def describe(w, mesh):
+    shape = "triangles" if mesh.dim == 2 else "tetrahedra"
+    n_omega = int(mesh.elem_in_omega.sum())
+    kern = "constant" if w.kernel == 0 else "truncated Gaussian"
+    return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} P1 {shape} "
+            f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
+            f"L_max={w.L_max}, {kern} kernel, jitter {w.jitter:g}h seed {w.seed}; "
+            f"u=sum x_k^2; BiCGStab to 1e-10")
 
 
 def u_exact(mesh):
@@ -265,7 +279,7 @@ def run_ours(args, rank, world, local):
     achieved = flops / (kern_avg / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 1),
             "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
-            "kernel": "k_quad<2,float,0>", "flops_per_launch": flops,
+            "kernel": f"k_quad<{mesh.dim},float,{w.kernel}>", "flops_per_launch": flops,
             "kernel_ms_avg": round(kern_avg, 3)}
 
     out = {
@@ -273,9 +287,7 @@ def run_ours(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"{w.name}: 2D unit square, h=1/256, {mesh.n_elem} P1 triangles "
-                               f"(131072 in Omega), delta=4h, eps=delta/5, L_max=4, constant kernel, "
-                               f"jitter 0.1h seed 0; u=x^2+y^2; BiCGStab to 1e-10",
+        "config": {"workload": describe(w, mesh),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set > L2 and a 256 MB L2 flush between steps"},
         "quad_pt_pairs_per_s": round(world * n_pp / (ms_max / 1e3), 1),
@@ -301,6 +313,8 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(args, mesh, w, g, f_const, stream, world)
+    if args.serve_requests > 0:
+        out["serving"] = run_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(mesh, w, seconds=15.0)
     return out
@@ -354,6 +368,46 @@ def e2e_ours(args, mesh, w, g, f_const, stream, world):
     return {"value": round(world * n_pairs / (ms / 1e3), 1), "unit": "element pairs/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
+
+
+def run_serving(args):
+    """Replays the first N requests of the seeded serving stream (Poisson arrivals at 10/s,
+    mixed 2D/3D meshes, delta in [2h, 6h], constant or truncated-Gaussian kernel) against the
+    library's server: each request is submitted at its arrival time and runs mesh, pairs,
+    FP32 assembly, right-hand side and BiCGStab in FP32 with FP64 refinement to 1e-10.
+    Latency = completion - submission on the server's clock."""
+    from nl_inputs.requests import serving_stream
+    from paper_2101_08825_gb300 import nl
+    reqs = serving_stream(512, seed=0)[: args.serve_requests]
+    budget = 64 << 30
+    lat, pairs, failed = [], 0, 0
+    with nl.Server(budget, args.serve_slots) as S:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            dt = r.arrival_s - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            req = nl.make_request(r.dim, (r.n,) * r.dim, 1.0 / r.n, (0.0,) * r.dim, r.layer,
+                                  r.delta, r.eps, r.L_max, kernel=r.kernel,
+                                  precision=nl.NL_PREC_FP32, ms=1, solver=1, rtol=1e-10,
+                                  jitter=0.1, seed=len(tickets))
+            tickets.append(S.submit(req))
+        results = [S.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        p50, p99, sps = S.stats()
+    for res in results:
+        if res.status != nl.NL_OK:
+            failed += 1
+            continue
+        lat.append(res.t_done_ms - res.t_submit_ms)
+        pairs += res.n_pairs
+    return {"requests": len(reqs), "failed": failed, "slots": args.serve_slots,
+            "budget_bytes": budget, "p50_ms": round(p50, 2), "p99_ms": round(p99, 2),
+            "solves_per_s": round(sps, 3), "element_pairs_per_s": round(pairs / wall, 1),
+            "max_latency_ms": round(max(lat), 2) if lat else None,
+            "sample": f"first {len(reqs)} of the 512-request seeded stream (seed 0), "
+                      f"arrivals at their Poisson times (10/s)"}
 
 
 # ---- the oracle on a bounded sample ------------------------------------------------------------

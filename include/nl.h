@@ -215,6 +215,102 @@ nl_status nl_solve(nl_matrix* A, const nl_vector* rhs, const double* g_nodes, in
                    double rtol, int max_iter, nl_precision precision, double* u_out,
                    int* iters, double* final_rel_res);
 
+/* ---- batched assembly: many problems in one launch -----------------------------------
+ * The paper assembles one problem at a time; a plan is this library's way to keep the GPU
+ * full with many small or uneven ones.  A plan assembles n problems (mesh, pairs, kernel,
+ * Algorithm 1 levels) of one dimension in one precision: a single persistent launch of the
+ * assembly kernel runs over the concatenated pair lists (every warp takes chunks of pairs
+ * from one counter, so pairs of different refinement depth and problems of different sizes
+ * share the grid until the last chunk), then one scatter launch and, for the FP32 paths, one
+ * diagonal launch cover all problems.  Problem k's values equal those of nl_assemble with the
+ * same arguments up to the order of FP64 additions.  Kernels, delta, eps and levels may
+ * differ between problems.  flags:
+ *   NL_PLAN_AUTOTUNE  time candidate launch shapes of the assembly kernel (warps per CTA,
+ *                     CTAs per SM, pairs per grab of the counter) on the plan's problems at
+ *                     creation and keep the fastest (nl_plan_shape reports it);
+ *   NL_PLAN_GRAPH     capture one execution (clears and kernels) into a CUDA graph at
+ *                     creation; every nl_plan_execute replays it.
+ * cuda_stream: the stream the plan runs on (NULL: the plan creates its own non-blocking
+ * stream).  The plan holds references to the pairs (and through them the meshes), owns the
+ * values of all problems, its block buffer ((D+1)^2 values per pair of all problems, FP32 or
+ * FP64) and its counters, and allocates only in nl_plan_create.
+ * Errors: NL_EINVAL for NULL arguments, n < 1, mixed dimensions, pairs of another mesh,
+ * delta/eps that differ from the pairs', or invalid kernel/levels/precision (as nl_assemble);
+ * NL_ENOMEM if the block buffer exceeds half of the free device memory. */
+typedef struct nl_plan nl_plan;
+#define NL_PLAN_AUTOTUNE 1
+#define NL_PLAN_GRAPH 2
+nl_status nl_plan_create(int n, nl_mesh* const* meshes, nl_pairs* const* pairs,
+                         const nl_kernel_params* kps, const nl_quad_params* qps,
+                         nl_precision precision, int flags, void* cuda_stream, nl_plan** out);
+/* Enqueues one execution on the plan's stream and returns (asynchronous). */
+nl_status nl_plan_execute(nl_plan* plan);
+/* Waits for the last execution and checks its device error word (NL_EINTERNAL as in
+ * nl_assemble).  stats: NULL or n entries; ms_assemble is the GPU time of the whole last
+ * execution (all problems). */
+nl_status nl_plan_sync(nl_plan* plan, nl_assemble_stats* stats);
+/* Problem k's values: device pointer (valid until nl_plan_destroy) and count. */
+nl_status nl_plan_values(const nl_plan* plan, int k, double** values, int64_t* nnz);
+/* Host copy of problem k's nnz values (waits for the plan's stream). */
+nl_status nl_plan_export(const nl_plan* plan, int k, double* values);
+/* A matrix handle with a copy of problem k's values, for nl_rhs / nl_solve (*A is created,
+ * or overwritten if it is a matrix of the same pattern). */
+nl_status nl_plan_matrix(const nl_plan* plan, int k, nl_matrix** A);
+/* The launch shape in use (0 = default), the tuned kernel time (0 if not tuned) and whether
+ * executions replay a CUDA graph; any pointer may be NULL. */
+nl_status nl_plan_shape(const nl_plan* plan, int* warps, int* ctas_per_sm, int* chunk,
+                        double* tuned_ms, int* graph);
+void nl_plan_destroy(nl_plan* plan);
+
+/* ---- serving: continuous batching of assemble + solve requests ----------------------
+ * A request is one volume-constrained Poisson problem (Sec. 2) on a structured box mesh,
+ * assembled (Sec. 5) and solved as above, with the manufactured solution u = g on Gamma and
+ * f = -Laplace(u) (= -L_eps u for these polynomials, Sec. 6). */
+typedef struct {
+  int dim;
+  int32_t cells[3];  /* structured box mesh as in nl_mesh_create_box */
+  double h, lo[3];
+  int32_t layer;
+  double jitter;
+  uint64_t seed;
+  nl_kernel_params kernel;
+  nl_quad_params quad;
+  nl_precision precision;
+  int ms;            /* manufactured solution: 0 = 1+sum x, 1 = sum x^2, 2 = sum x^3 */
+  int solver;        /* 0 CG, 1 BiCGStab */
+  double rtol;
+  int max_iter;
+  double* u_out;     /* nullable host array of n_vert values that receives u_h; it must stay
+                        valid until the result has been taken */
+} nl_request;
+
+typedef struct {
+  nl_status status;
+  int iters;
+  double rel_res;
+  double l2_err_omega;   /* ||u - u_h|| over Omega (degree-5 rule per element) */
+  int64_t n_pairs, n_point_pairs, nnz, n_vert;
+  double t_submit_ms, t_start_ms, t_done_ms; /* host clock since nl_serve_create */
+  char message[160];     /* error message when status != NL_OK, "" otherwise */
+} nl_result;
+
+/* device_mem_budget: bytes the server may hold at once (>= 64 MiB); max_slots (1..64):
+ * requests in flight on the device at once, each on its own worker thread and CUDA stream of
+ * the device that is current at creation.  A request is admitted when a slot is free and its
+ * estimated footprint fits in the budget left by the requests in flight (a request larger
+ * than the whole budget runs when nothing else does); requests wait in arrival order.
+ * Requests run concurrently on the device; each keeps its mesh, pattern, matrix and Krylov
+ * vectors on the device while it runs.  nl_serve_destroy lets running requests finish and
+ * drops the ones still waiting. */
+nl_status nl_serve_create(size_t device_mem_budget, int max_slots, nl_server** out);
+nl_status nl_serve_submit(nl_server* s, const nl_request* req, uint64_t* ticket);
+/* NL_EBUSY while the request is not finished; otherwise the result (once). */
+nl_status nl_serve_poll(nl_server* s, uint64_t ticket, nl_result* out);
+/* Waits at most timeout_ms (NL_ETIMEOUT after that). */
+nl_status nl_serve_wait(nl_server* s, uint64_t ticket, double timeout_ms, nl_result* out);
+nl_status nl_serve_stats(nl_server* s, double* p50_ms, double* p99_ms, double* solves_per_s);
+void nl_serve_destroy(nl_server* s);
+
 /* ---- host-side tables (no device work; usable without a GPU) ------------------------- */
 /* The degree-5 simplex rule used by the kernels: bary[npts*(dim+1)], w[npts] (sum 1).
  * Returns the number of points, or -1. */

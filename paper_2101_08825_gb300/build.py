@@ -15,7 +15,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnl.so")
-SOURCES = ["nl_host.cu", "nl_pairs.cu", "nl_quad.cu", "nl_solve.cu"]
+SOURCES = ["nl_host.cu", "nl_pairs.cu", "nl_quad.cu", "nl_batch.cu", "nl_solve.cu", "nl_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,8 +36,8 @@ def _flags(verbose: bool):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "nl_internal.h"), os.path.join(HERE, "..", "include", "nl.h"),
-                   os.path.abspath(__file__)]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
+    deps = srcs + headers + [os.path.join(HERE, "..", "include", "nl.h"), os.path.abspath(__file__)]
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
         return LIB
     bdir = os.path.join(HERE, "_build")

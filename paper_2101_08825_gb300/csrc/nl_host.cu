@@ -25,6 +25,7 @@ nl_status fail(nl_status st, const char* fmt, ...) {
 }
 
 nl_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();  // a failed call also sets the thread's last error; later checks start clean
   return fail(e == cudaErrorMemoryAllocation ? NL_ENOMEM : NL_ECUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }

@@ -29,10 +29,45 @@ void clear_error();
     if (_s != NL_OK) return _s;       \
   } while (0)
 
+// Raises a kernel's dynamic shared-memory ceiling to the most the device allows next to the
+// kernel's static shared memory.  The attribute is global per kernel, so it is only ever set
+// to that one value: launches of the same kernel with different sizes from several threads
+// cannot race on it.
+template <typename F>
+nl_status allow_smem(F* kernel, size_t needed) {
+  int dev = 0, mx = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(NL_ECUDA, "cannot query the shared-memory limit");
+  }
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaFuncGetAttributes");
+  }
+  const size_t dyn_max = (size_t)mx > fa.sharedSizeBytes ? (size_t)mx - fa.sharedSizeBytes : 0;
+  if (needed > dyn_max)
+    return fail(NL_EINTERNAL, "a kernel needs %zu bytes of dynamic shared memory (device limit %zu)",
+                needed, dyn_max);
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  return NL_OK;
+}
+
 // ---- kernel launch counter (every launch site wraps its grid size in NL_CNT) ----------
 void count_launch();
 long long launch_count();
 #define NL_CNT(grid) (::nlx::count_launch(), (grid))
+
+// Upper bound on the assembly's block buffer for the calling thread (0 = default: 8 GiB or
+// a quarter of the free memory).  The serving workers lower it so that concurrent requests
+// stay inside the server's memory budget.
+extern thread_local size_t g_block_budget;
 
 // ---- device memory ---------------------------------------------------------------------
 void* dev_alloc(size_t bytes, cudaStream_t s);

@@ -469,7 +469,7 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   NL_TRY(pl.alloc(n_pairs > 0 ? n_pairs : 1, s));
   int cap = next_pow2(std::max<int64_t>(mx, 1));
   size_t smem = sizeof(int32_t) * cap;
-  NL_CUDA(cudaFuncSetAttribute(k_pairs_fill<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NL_TRY(allow_smem(k_pairs_fill<D>, smem));
   k_pairs_fill<D><<<NL_CNT((unsigned)ne), 256, smem, s>>>(ne, g, reach, m->blo, m->bhi, cell_off.p, items.p,
                                                  off.p, pl.p, cap, err.p);
   NL_CUDA(cudaGetLastError());
@@ -485,8 +485,8 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   int eh = next_pow2(std::max<int64_t>(64, std::min<int64_t>(2 * max_sum, 32768)));
   int nh = std::min(8192, eh);
   size_t rsmem = sizeof(int32_t) * (eh + nh);
-  NL_CUDA(cudaFuncSetAttribute(k_rows<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
-  NL_CUDA(cudaFuncSetAttribute(k_rows<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem));
+  NL_TRY((allow_smem(k_rows<D, false>, rsmem)));
+  NL_TRY((allow_smem(k_rows<D, true>, rsmem)));
   DevBuf<int32_t> rcnt;
   NL_TRY(rcnt.alloc(nvv, s));
   k_rows<D, false><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,

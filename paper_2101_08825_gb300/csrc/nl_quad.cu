@@ -1,38 +1,6 @@
-// nl_quad.cu -- assembly of the mollified nonlocal stiffness matrix on the GPU.
-//
-// What is computed (Sec. 5, Corollary 1, eqs. J21Nr and J22Nr): for every element pair
-// (m, l) of J, with the inner degree-5 rule on E_m (points y, weights w_y, rows = nodes of m)
-// and the outer rule on the sub-elements E' of E_l that Algorithm 1 selects for this m,
-//   A[m_a, m_b] += 2 sum_{x,y} w_x w_y gamma_eps(x,y) phi^m_a(y) phi^m_b(y)
-//   A[m_a, l_c] -= 2 sum_{x,y} w_x w_y gamma_eps(x,y) phi^m_a(y) phi^l_c(x).
-// Algorithm 1 is applied per pair; this is the same computation as the per-l recursion with
-// the index set J_l, because the tests and the integration act on every m separately.
-//
-// How (k_quad): a persistent grid; each warp takes chunks of consecutive pairs (m-major)
-// from a global counter.  For one pair the warp runs Algorithm 1 as a LIFO of refined
-// sub-elements ("parent records": vertices + path code) in shared memory: each round pops
-// up to 32/2^N parents and every lane builds one child by midpoints, classifies it with the
-// box distances of Sec. 5.1 and drops it, pushes it, or appends it to one of two item
-// buffers: INT (max-dist < delta-eps: mu = 1 at every point pair) or FINAL (the sub-element
-// reached L_max with the band in reach).  With the constant kernel an INT sub-element is
-// summed in closed form (the degree-5 rule integrates its linear integrand exactly).  A full
-// buffer is integrated by the whole warp: each lane owns one outer point x and 7 inner points
-// y kept in registers (3D: two half-warps share x and take y 0-6 and 7-13), and accumulates
-// per y the sums g = sum_x w_x C eta mu and h_k = sum_x w_x C eta mu lambda^l_k(x).  At the
-// end of the pair the warp reduces them through a shared-memory transpose and writes the
-// pair's cross block -2 vol_m sum_y w_y B_a(y) H_c(y) (H_0 = g - sum_k h_k, H_c = h_{c-1})
-// to a block buffer; the self block only needs g, which is accumulated over the consecutive
-// pairs of the same m (compensated FP32 or FP64) and added to a per-element block.
-// k_scatter (one CTA per inner element m, the rows of m's nodes cached in shared memory)
-// then adds every block to the CSR values with FP64 atomics.
-//
-// Precision: R = double evaluates everything in FP64 on global coordinates and classifies
-// in FP64.  R = float evaluates gamma_eps in FP32 on coordinates relative to the first
-// vertex of m, built from per-element FP32 vertex offsets and one FP64 difference of first
-// vertices per pair; the classification is screened in FP32, and a decision whose FP32
-// distance lies within a proven margin of its threshold is redone in FP64 on vertices
-// rebuilt from E_l by the same midpoint sequence, so the decisions are those of a plain FP64
-// evaluation in both precisions.  No FP64 arithmetic runs per sub-element or per point pair.
+// nl_quad.cu -- single-problem assembly of the mollified nonlocal stiffness matrix
+// (nl_assemble, nl_assemble_noalloc): the pair batches, the block buffer and the scatter around
+// the kernels of nl_quad_kernel.cuh.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,9 +10,11 @@
 #include <type_traits>
 #include <vector>
 
-#include "nl_internal.h"
+#include "nl_quad_kernel.cuh"
 
 namespace nlx {
+
+thread_local size_t g_block_budget = 0;
 
 nl_status ensure_device_tables() {
   if (rule(2).n != 7 || rule(3).n != 14)
@@ -53,931 +23,6 @@ nl_status ensure_device_tables() {
 }
 
 namespace {
-
-constexpr int KIND_INT = 0;
-constexpr int KIND_FINAL = 1;
-// ACT_ZERO: a sub-element at L_max that Algorithm 1 integrates but whose every point pair is
-// farther than delta + eps (mu = 0): counted, not evaluated.
-constexpr int ACT_DROP = 0, ACT_INT = 1, ACT_FINAL = 2, ACT_REFINE = 3, ACT_ZERO = 4;
-constexpr int ERR_STACK = 1, ERR_CSR = 2;
-constexpr int CHUNK = 32;
-constexpr int IMAX = 64;
-constexpr int LEVEL_SHIFT = 27;
-
-struct QParams {
-  int64_t n_elem, p_begin, p_end;
-  const int64_t* pair_off;
-  const int32_t* pair_l;
-  const int32_t* conn;
-  const double* evert;
-  const double* blo;
-  const double* bhi;
-  const double* vol;
-  const double* jinv;
-  const float* ef;
-  void* blk;          // [p_end - p_begin][(D+1)^2] cross blocks (R)
-  double* selfblk;    // [n_elem][(D+1)^2]
-  const int64_t* row_ptr;  // CSR pattern and values: used only by the variant that adds
-  const int32_t* col;      // its cross blocks to the values directly
-  double* values;
-  unsigned long long* counter;
-  unsigned long long* stats;  // [0] items, [2] exact checks, [3] evaluated pairs,
-                              // [4] closed-form items, [5] band pairs
-  int* err;
-  double delta, dme, dpe, C, inv_eps, inv_delta2;
-  float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
-  int L_min, L_max, scap, count_band;
-  double B[14][4];
-  double W[14];
-};
-
-template <int D>
-struct Geo {
-  static constexpr int NV = D + 1;
-  static constexpr int NQ = D == 2 ? 7 : 14;
-  static constexpr int NCH = 1 << D;
-  static constexpr int NPOP = 32 / NCH;
-  static constexpr int XPI = D == 2 ? 32 : 16;  // distinct outer points per warp iteration
-  static constexpr int NYL = 7;                 // inner points per lane
-  static constexpr int NVC = NV * D;            // vertex coordinates of a simplex
-  static constexpr int BITS = D;                // path bits per level
-  static constexpr int NBLK = NV * NV;          // entries of a local block
-  static constexpr int NRED = NYL * NV + NV;    // per-lane values reduced at pair end
-  static constexpr int RS = NRED | 1;           // odd row stride of the reduction scratch
-  static constexpr int TOTN = NQ * NV + NV;     // pair totals: per inner point, then uniform
-  static constexpr int EFS = NL_EF_STRIDE(D);
-};
-
-// child c, vertex v = midpoint of parent vertices (a, b); a corner is mid(P, P) = P exactly
-__constant__ unsigned char c_mid2[4][3][2] = {{{0, 0}, {0, 1}, {0, 2}},
-                                              {{0, 1}, {1, 1}, {1, 2}},
-                                              {{0, 2}, {1, 2}, {2, 2}},
-                                              {{0, 1}, {1, 2}, {0, 2}}};
-__constant__ unsigned char c_mid3[8][4][2] = {
-    {{0, 0}, {0, 1}, {0, 2}, {0, 3}}, {{0, 1}, {1, 1}, {1, 2}, {1, 3}},
-    {{0, 2}, {1, 2}, {2, 2}, {2, 3}}, {{0, 3}, {1, 3}, {2, 3}, {3, 3}},
-    {{0, 1}, {0, 2}, {0, 3}, {1, 3}}, {{0, 1}, {0, 2}, {1, 2}, {1, 3}},
-    {{0, 2}, {0, 3}, {1, 3}, {2, 3}}, {{0, 2}, {1, 2}, {1, 3}, {2, 3}}};
-
-template <int D>
-__device__ __forceinline__ void mid_pair(int c, int v, int& a, int& b) {
-  if (D == 2) {
-    a = c_mid2[c][v][0];
-    b = c_mid2[c][v][1];
-  } else {
-    a = c_mid3[c][v][0];
-    b = c_mid3[c][v][1];
-  }
-}
-
-__device__ __forceinline__ double midp(double a, double b) { return __dmul_rn(__dadd_rn(a, b), 0.5); }
-__device__ __forceinline__ float midp(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
-
-// 2^-k as an exact power of two
-__device__ __forceinline__ float pow2m(float, int k) { return __int_as_float((127 - k) << 23); }
-__device__ __forceinline__ double pow2m(double, int k) {
-  return __longlong_as_double((long long)(1023 - k) << 52);
-}
-
-// Exact FP64 box distances of Sec. 5.1 (eqs. maxdist, mindist) between a sub-element with
-// vertices V and the box (lo2, hi2) of E_m, written as in a plain evaluation.
-template <int D>
-__device__ void exact_dists(const double (&V)[D + 1][D], const double* lo2, const double* hi2,
-                            double& amax, double& amin) {
-  double s = 0.0, mn = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; k++) {
-    double lo = V[0][k], hi = V[0][k];
-#pragma unroll
-    for (int a = 1; a <= D; a++) {
-      lo = V[a][k] < lo ? V[a][k] : lo;
-      hi = V[a][k] > hi ? V[a][k] : hi;
-    }
-    double d1 = __dsub_rn(lo, hi2[k]);
-    double d2 = __dsub_rn(lo2[k], hi);
-    double p = __dmul_rn(d1, d1), q = __dmul_rn(d2, d2);
-    s = __dadd_rn(s, p > q ? p : q);
-    double t = d1 > d2 ? d1 : d2;
-    mn = t > mn ? t : mn;
-  }
-  amax = __dsqrt_rn(s);
-  amin = mn;
-}
-
-template <int D>
-__device__ __forceinline__ void screen_dists(const float (&V)[D + 1][D], const float* lo2,
-                                             const float* hi2, float& amax, float& amin) {
-  float s = 0.f, mn = 0.f;
-#pragma unroll
-  for (int k = 0; k < D; k++) {
-    float lo = V[0][k], hi = V[0][k];
-#pragma unroll
-    for (int a = 1; a <= D; a++) {
-      lo = fminf(lo, V[a][k]);
-      hi = fmaxf(hi, V[a][k]);
-    }
-    float d1 = lo - hi2[k], d2 = lo2[k] - hi;
-    s += fmaxf(d1 * d1, d2 * d2);
-    mn = fmaxf(mn, fmaxf(d1, d2));
-  }
-  amax = sqrtf(s);
-  amin = mn;
-}
-
-// Rebuilds the FP64 vertices of the sub-element with path `code` from the vertices of E_l.
-template <int D>
-__device__ void decode_exact(const double (&Vl)[D + 1][D], uint32_t code, double (&V)[D + 1][D]) {
-  int level = code >> LEVEL_SHIFT;
-#pragma unroll
-  for (int a = 0; a <= D; a++)
-#pragma unroll
-    for (int k = 0; k < D; k++) V[a][k] = Vl[a][k];
-  for (int lv = 2; lv <= level; lv++) {
-    int c = (code >> (Geo<D>::BITS * (lv - 2))) & (Geo<D>::NCH - 1);
-    double P[D + 1][D];
-#pragma unroll
-    for (int a = 0; a <= D; a++)
-#pragma unroll
-      for (int k = 0; k < D; k++) P[a][k] = V[a][k];
-#pragma unroll
-    for (int v = 0; v <= D; v++) {
-      int ia, ib;
-      mid_pair<D>(c, v, ia, ib);
-#pragma unroll
-      for (int k = 0; k < D; k++) {
-        double pa = P[0][k], pb = P[0][k];
-#pragma unroll
-        for (int a = 1; a <= D; a++) {
-          pa = (ia == a) ? P[a][k] : pa;
-          pb = (ib == a) ? P[a][k] : pb;
-        }
-        V[v][k] = midp(pa, pb);
-      }
-    }
-  }
-}
-
-// FP64 decision of Algorithm 1 for a sub-element below L_max (used by the FP32 path when the
-// screened distance is within the margin of a threshold): ACT_INT, ACT_REFINE or ACT_DROP.
-template <int D>
-__device__ __noinline__ int exact_classify(const double* __restrict__ evert_l,
-                                           const double* __restrict__ lo_m,
-                                           const double* __restrict__ hi_m, uint32_t code,
-                                           double dme, double dpe) {
-  double Vl[D + 1][D], V[D + 1][D], lo2[D], hi2[D];
-#pragma unroll
-  for (int a = 0; a <= D; a++)
-#pragma unroll
-    for (int k = 0; k < D; k++) Vl[a][k] = evert_l[a * D + k];
-#pragma unroll
-  for (int k = 0; k < D; k++) {
-    lo2[k] = lo_m[k];
-    hi2[k] = hi_m[k];
-  }
-  decode_exact<D>(Vl, code, V);
-  double amax, amin;
-  exact_dists<D>(V, lo2, hi2, amax, amin);
-  if (amax < dme) return ACT_INT;
-  if (amin < dpe) return ACT_REFINE;
-  return ACT_DROP;
-}
-
-__device__ __forceinline__ double xi_poly(double s) {
-  double t = s * s;
-  double p = fma(35.0, t, -180.0);
-  p = fma(p, t, 378.0);
-  p = fma(p, t, -420.0);
-  p = fma(p, t, 315.0);
-  return fma(s * p, 1.0 / 256.0, 0.5);
-}
-__device__ __forceinline__ float xi_poly(float s) {
-  float t = s * s;
-  float p = fmaf(35.f, t, -180.f);
-  p = fmaf(p, t, 378.f);
-  p = fmaf(p, t, -420.f);
-  p = fmaf(p, t, 315.f);
-  return fmaf(s * p, 1.f / 256.f, 0.5f);
-}
-
-// mu_{delta,eps}(r) from r^2 (eq. mollifier with argument (delta - r)/eps)
-__device__ __forceinline__ double mollifier(const QParams& P, double r2) {
-  double dme2 = P.dme * P.dme, dpe2 = P.dpe * P.dpe;
-  if (r2 < dme2) return 1.0;
-  if (r2 > dpe2) return 0.0;
-  double r = sqrt(r2);
-  return xi_poly((P.delta - r) * P.inv_eps);
-}
-__device__ __forceinline__ float mollifier(const QParams& P, float r2) {
-  if (r2 < P.fdme2) return 1.f;
-  if (r2 > P.fdpe2) return 0.f;
-  // r = sqrt(r2): hardware reciprocal square root, then one Newton step on r^2 - r2 = 0
-  // (r <- r + (r2 - r^2) / (2r)), which brings r to about one ulp
-  const float q = rsqrtf(r2);
-  float r = r2 * q;
-  r = fmaf(0.5f * q, fmaf(-r, r, r2), r);
-  return xi_poly((P.fdelta - r) * P.finv_eps);
-}
-
-// Sum_j A_ij = 0 for every row of the exact discrete operator (sum_j phi_j = 1 at every
-// point, so every point pair contributes sum_j (phi_j(y) - phi_j(x)) = 0): the diagonal
-// equals minus the sum of the off-diagonal entries.  The FP32 paths rebuild it that way in
-// FP64, which removes the row-sum part of their rounding error (warp per row).
-__global__ void k_diag_from_rows(int64_t n_rows, const int64_t* __restrict__ row_ptr,
-                                 const int32_t* __restrict__ col, double* __restrict__ values) {
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n_rows) return;
-  double s = 0.0;
-  int64_t dpos = -1;
-  for (int64_t t = row_ptr[i] + lane; t < row_ptr[i + 1]; t += 32) {
-    if (col[t] == (int32_t)i) dpos = t;
-    else s += values[t];
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    int64_t d = __shfl_xor_sync(0xffffffffu, dpos, o);
-    dpos = d > dpos ? d : dpos;
-  }
-  if (lane == 0 && dpos >= 0) values[dpos] = -s;
-}
-
-template <typename R>
-__device__ __forceinline__ R eta_gauss(const QParams& P, R r2);
-template <>
-__device__ __forceinline__ double eta_gauss<double>(const QParams& P, double r2) {
-  return exp(-r2 * P.inv_delta2);
-}
-template <>
-__device__ __forceinline__ float eta_gauss<float>(const QParams& P, float r2) {
-  return __expf(-r2 * P.finv_delta2);
-}
-
-// Compensated accumulation (hi + lo) in the working precision (Knuth's TwoSum).
-__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
-  float s = hi + v;
-  float bb = s - hi;
-  float e = (hi - (s - bb)) + (v - bb);
-  hi = s;
-  lo += e;
-}
-__device__ __forceinline__ void two_sum_add(double& hi, double& lo, double v) {
-  hi += v;
-  (void)lo;
-}
-
-// Per-warp shared memory: stack records, two item buffers (SoA) and the reduction scratch.
-template <int D, typename R>
-struct WarpMem {
-  R* rv;          // [NVC][scap]
-  uint32_t* rc;   // [scap]
-  R* iv;          // [2][NVC][IMAX]
-  R* iw;          // [2][IMAX]
-  R* red;         // [32][RS]
-  R* tot;         // [TOTN] pair totals
-  int* ctl;       // [0] sp, [1] n_int, [2] n_final
-  static __host__ __device__ size_t bytes(int scap) {
-    using G = Geo<D>;
-    size_t b = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
-    b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * ((size_t)2 * G::NVC * IMAX + 2 * IMAX + 32 * G::RS + G::TOTN + 16);
-    b += 16;
-    return (b + 15) & ~size_t(15);
-  }
-  __device__ void carve(char* base, int scap) {
-    using G = Geo<D>;
-    rv = reinterpret_cast<R*>(base);
-    rc = reinterpret_cast<uint32_t*>(rv + (size_t)G::NVC * scap);
-    size_t off = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
-    off = (off + 15) & ~size_t(15);
-    iv = reinterpret_cast<R*>(base + off);
-    iw = iv + (size_t)2 * G::NVC * IMAX;
-    red = iw + 2 * IMAX;
-    tot = red + 32 * G::RS;
-    ctl = reinterpret_cast<int*>(tot + G::TOTN + 8);
-  }
-};
-
-template <typename R>
-__host__ __device__ constexpr size_t table_bytes() {
-  return (sizeof(R) * (14 * 4 * 2 + 16) + 15) & ~size_t(15);
-}
-
-// Position of column j in CSR row i (binary search in global memory), or -1.
-__device__ __forceinline__ int64_t csr_find(const int64_t* __restrict__ row_ptr,
-                                            const int32_t* __restrict__ col, int32_t i, int32_t j) {
-  int64_t lo = row_ptr[i], hi = row_ptr[i + 1] - 1;
-  while (lo <= hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    const int32_t c = col[mid];
-    if (c == j) return mid;
-    if (c < j) lo = mid + 1;
-    else hi = mid - 1;
-  }
-  return -1;
-}
-
-// DIRECT = true: the cross block of every pair is added to the CSR values at once (global
-// binary search, FP64 atomics) instead of going through the block buffer.
-template <int D, typename R, int KERN, bool DIRECT = false>
-__global__ void __launch_bounds__(256, 2) k_quad(const QParams P) {
-  using G = Geo<D>;
-  constexpr int NV = G::NV, NQ = G::NQ, NYL = G::NYL, NVC = G::NVC, NBLK = G::NBLK;
-  constexpr int RS = G::RS;
-  constexpr bool F32 = std::is_same<R, float>::value;
-  extern __shared__ __align__(16) char smem_raw[];
-  R* sB = reinterpret_cast<R*>(smem_raw);  // [NQ][NV]
-  R* sW = sB + 14 * 4;                      // [NQ]
-  R* sWB = sW + 16;                         // [NQ][NV]: W[q] * B[q][a]
-  for (int t = threadIdx.x; t < NQ * NV; t += blockDim.x) {
-    sB[t] = (R)P.B[t / NV][t % NV];
-    sWB[t] = (R)(P.W[t / NV] * P.B[t / NV][t % NV]);
-  }
-  for (int t = threadIdx.x; t < NQ; t += blockDim.x) sW[t] = (R)P.W[t];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  WarpMem<D, R> wm;
-  wm.carve(smem_raw + table_bytes<R>() + (size_t)wid * WarpMem<D, R>::bytes(P.scap), P.scap);
-
-  const int ybase = (D == 3 && lane >= 16) ? 7 : 0;
-  const int xl = (D == 3) ? (lane & 15) : lane;
-
-  unsigned long long st_items = 0, st_exact = 0, st_eval = 0, st_closed = 0, st_band = 0;
-  int err = 0;
-
-  // state of the current inner element m
-  int64_t cur_m = -1;
-  double v0m[D];      // first vertex of m (origin of the FP32 local coordinates)
-  R lo_m[D], hi_m[D]; // box of m (local FP32 coordinates, or global FP64)
-  R y[NYL][D];        // inner points of m (local if R = float)
-  R vol_m = 0;
-  R gs_hi = 0, gs_lo = 0;  // lane t < NQ: sum of g over the m-run for inner point t
-
-  auto flush_self = [&]() {
-    // S[a][b] = 2 vol_m sum_y W B_a B_b g(y), in FP64 from the compensated sums
-    double* sd = reinterpret_cast<double*>(wm.red);
-    if (lane < NQ) sd[lane] = (double)gs_hi + (double)gs_lo;
-    __syncwarp();
-    if (lane < NBLK) {
-      int a = lane / NV, b = lane % NV;
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < NQ; q++) s += (double)sWB[q * NV + a] * (double)sB[q * NV + b] * sd[q];
-      atomicAdd(&P.selfblk[cur_m * NBLK + lane], 2.0 * (double)vol_m * s);
-    }
-    __syncwarp();
-    gs_hi = 0;
-    gs_lo = 0;
-  };
-
-  for (;;) {
-    unsigned long long start = 0;
-    if (lane == 0) start = atomicAdd(P.counter, (unsigned long long)CHUNK);
-    start = __shfl_sync(0xffffffffu, start, 0);
-    const int64_t p0 = P.p_begin + (int64_t)start;
-    if (p0 >= P.p_end) break;
-    const int64_t p1 = min(p0 + (int64_t)CHUNK, P.p_end);
-    int64_t m;
-    if (cur_m >= 0 && P.pair_off[cur_m] <= p0 && p0 < P.pair_off[cur_m + 1]) {
-      m = cur_m;
-    } else {
-      // the last m with pair_off[m] <= p0 (pair_off[0] = 0 <= p0 < pair_off[n_elem])
-      int64_t lo = 0, hi = P.n_elem;
-      while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (P.pair_off[mid] <= p0) lo = mid;
-        else hi = mid;
-      }
-      m = lo;
-    }
-    for (int64_t p = p0; p < p1; p++) {
-      while (p >= P.pair_off[m + 1]) m++;
-      if (m != cur_m) {
-        if (cur_m >= 0) flush_self();
-        cur_m = m;
-#pragma unroll
-        for (int k = 0; k < D; k++) v0m[k] = P.evert[m * NVC + k];
-        R Vm[NV][D];
-        if (F32) {
-          const float* ef = P.ef + m * G::EFS;
-#pragma unroll
-          for (int k = 0; k < D; k++) Vm[0][k] = 0;
-#pragma unroll
-          for (int a = 1; a < NV; a++)
-#pragma unroll
-            for (int k = 0; k < D; k++) Vm[a][k] = (R)ef[(a - 1) * D + k];
-          vol_m = (R)ef[2 * D * D];
-        } else {
-#pragma unroll
-          for (int a = 0; a < NV; a++)
-#pragma unroll
-            for (int k = 0; k < D; k++) Vm[a][k] = (R)P.evert[m * NVC + a * D + k];
-          vol_m = (R)P.vol[m];
-        }
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-          R lo = Vm[0][k], hi = Vm[0][k];
-#pragma unroll
-          for (int a = 1; a < NV; a++) {
-            lo = Vm[a][k] < lo ? Vm[a][k] : lo;
-            hi = Vm[a][k] > hi ? Vm[a][k] : hi;
-          }
-          lo_m[k] = lo;
-          hi_m[k] = hi;
-        }
-#pragma unroll
-        for (int i = 0; i < NYL; i++) {
-          int q = ybase + i;
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            R s = 0;
-#pragma unroll
-            for (int a = 0; a < NV; a++) s += sB[q * NV + a] * Vm[a][k];
-            y[i][k] = s;
-          }
-        }
-      }
-      const int32_t l = P.pair_l[p];
-      // ---- per-pair set-up ------------------------------------------------------------------
-      R Vl[NV][D], Ji[D][D], wl;
-      if (F32) {
-        const float* ef = P.ef + (int64_t)l * G::EFS;
-#pragma unroll
-        for (int k = 0; k < D; k++) Vl[0][k] = (R)(P.evert[(int64_t)l * NVC + k] - v0m[k]);
-#pragma unroll
-        for (int a = 1; a < NV; a++)
-#pragma unroll
-          for (int k = 0; k < D; k++) Vl[a][k] = Vl[0][k] + (R)ef[(a - 1) * D + k];
-#pragma unroll
-        for (int r = 0; r < D; r++)
-#pragma unroll
-          for (int c = 0; c < D; c++) Ji[r][c] = (R)ef[D * D + r * D + c];
-        wl = (R)P.fC * (R)ef[2 * D * D];
-      } else {
-#pragma unroll
-        for (int a = 0; a < NV; a++)
-#pragma unroll
-          for (int k = 0; k < D; k++) Vl[a][k] = (R)P.evert[((int64_t)l * NV + a) * D + k];
-#pragma unroll
-        for (int r = 0; r < D; r++)
-#pragma unroll
-          for (int c = 0; c < D; c++) Ji[r][c] = (R)P.jinv[((int64_t)l * D + r) * D + c];
-        wl = (R)(P.C * P.vol[l]);
-      }
-
-      R gp[NYL], hp[D][NYL], ug = 0, uh[D];
-#pragma unroll
-      for (int i = 0; i < NYL; i++) {
-        gp[i] = 0;
-#pragma unroll
-        for (int k = 0; k < D; k++) hp[k][i] = 0;
-      }
-#pragma unroll
-      for (int k = 0; k < D; k++) uh[k] = 0;
-
-      // Algorithm 1 decision for a sub-element (R coordinates)
-      auto classify = [&](const R (&V)[NV][D], uint32_t code) -> int {
-        const int level = code >> LEVEL_SHIFT;
-        if (level < P.L_min) return ACT_REFINE;
-        const bool last = level == P.L_max;
-        if (F32) {
-          float fam, fan;
-          float Vf[NV][D];
-#pragma unroll
-          for (int a = 0; a < NV; a++)
-#pragma unroll
-            for (int k = 0; k < D; k++) Vf[a][k] = (float)V[a][k];
-          float flo[D], fhi[D];
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            flo[k] = (float)lo_m[k];
-            fhi[k] = (float)hi_m[k];
-          }
-          screen_dists<D>(Vf, flo, fhi, fam, fan);
-          const bool c_int = fam < P.fdme - P.margin;
-          const bool c_notint = fam > P.fdme + P.margin;
-          const bool c_ref = fan < P.fdpe - P.margin;
-          const bool c_out = fan > P.fdpe + P.margin;
-          if (last) return c_int ? ACT_INT : (c_out ? ACT_ZERO : ACT_FINAL);
-          if (c_int) return ACT_INT;
-          if (c_notint && c_ref) return ACT_REFINE;
-          if (c_notint && c_out) return ACT_DROP;
-          st_exact += (level == 1) ? (lane == 0) : 1;
-          return exact_classify<D>(P.evert + (int64_t)l * NVC, P.blo + cur_m * D, P.bhi + cur_m * D,
-                                   code, P.dme, P.dpe);
-        } else {
-          double Vd[NV][D], lo2[D], hi2[D];
-#pragma unroll
-          for (int a = 0; a < NV; a++)
-#pragma unroll
-            for (int k = 0; k < D; k++) Vd[a][k] = (double)V[a][k];
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            lo2[k] = (double)lo_m[k];
-            hi2[k] = (double)hi_m[k];
-          }
-          double amax, amin;
-          exact_dists<D>(Vd, lo2, hi2, amax, amin);
-          if (last) return amax < P.dme ? ACT_INT : (amin > P.dpe ? ACT_ZERO : ACT_FINAL);
-          if (amax < P.dme) return ACT_INT;
-          if (amin < P.dpe) return ACT_REFINE;
-          return ACT_DROP;
-        }
-      };
-
-      // A sub-element with max-dist < delta - eps has mu = 1 at every point pair; with the
-      // constant kernel its outer sum is sum_q w_q C [1, lambda^l(x_q)] = C |E'| [1,
-      // lambda^l(centroid)], because the degree-5 rule integrates linear functions exactly.
-      auto closed_int = [&](const R (&V)[NV][D], int level) {
-        R cen[D];
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-          R s = 0;
-#pragma unroll
-          for (int a = 0; a < NV; a++) s += V[a][k];
-          cen[k] = s * (R)(1.0 / NV);
-        }
-        const R wv = wl * pow2m(R(0), D * (level - 1));
-        ug += wv;
-#pragma unroll
-        for (int r = 0; r < D; r++) {
-          R s = 0;
-#pragma unroll
-          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - Vl[0][c]);
-          uh[r] += wv * s;
-        }
-        st_closed++;
-      };
-
-      // integrate the buffered items of one kind (warp-collective)
-      auto integrate = [&](int kind, int n_it) {
-        const R* iv = wm.iv + (size_t)kind * NVC * IMAX;
-        const R* iw = wm.iw + kind * IMAX;
-        const int n_x = n_it * NQ;
-        st_eval += (unsigned long long)n_x * NQ;
-        for (int base = 0; base < n_x; base += G::XPI) {
-          const int o = base + xl;
-          const bool valid = o < n_x;
-          const int it = valid ? o / NQ : 0;
-          const int q = valid ? o - it * NQ : 0;
-          R x[D];
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            R s = 0;
-#pragma unroll
-            for (int a = 0; a < NV; a++) s += sB[q * NV + a] * iv[(a * D + k) * IMAX + it];
-            x[k] = s;
-          }
-          const R wcx = valid ? sW[q] * iw[it] : (R)0;
-          R lam[D];
-#pragma unroll
-          for (int r = 0; r < D; r++) {
-            R s = 0;
-#pragma unroll
-            for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - Vl[0][c]);
-            lam[r] = s;
-          }
-#pragma unroll
-          for (int i = 0; i < NYL; i++) {
-            R r2 = 0;
-#pragma unroll
-            for (int k = 0; k < D; k++) {
-              const R d = x[k] - y[i][k];
-              r2 += d * d;
-            }
-            R g = wcx;
-            if (kind == KIND_FINAL) {
-              g *= mollifier(P, r2);
-              if (P.count_band)
-                st_band += (valid && r2 >= (R)(P.dme * P.dme) && r2 <= (R)(P.dpe * P.dpe)) ? 1 : 0;
-            }
-            if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
-            gp[i] += g;
-#pragma unroll
-            for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
-          }
-        }
-      };
-
-      // append an item to a buffer slot
-      auto put_item = [&](int kind, int slot, const R (&V)[NV][D], int level) {
-        R* iv = wm.iv + (size_t)kind * NVC * IMAX;
-#pragma unroll
-        for (int t = 0; t < NVC; t++) iv[t * IMAX + slot] = V[t / D][t % D];
-        wm.iw[kind * IMAX + slot] = wl * pow2m(R(0), D * (level - 1));
-      };
-
-      // ---- Algorithm 1 for this pair --------------------------------------------------------
-      {
-        const uint32_t code0 = 1u << LEVEL_SHIFT;
-        const int act = classify(Vl, code0);
-        if (lane == 0) {
-          wm.ctl[0] = 0;
-          wm.ctl[1] = 0;
-          wm.ctl[2] = 0;
-          if (act == ACT_REFINE) {
-#pragma unroll
-            for (int t = 0; t < NVC; t++) wm.rv[t * P.scap] = Vl[t / D][t % D];
-            wm.rc[0] = code0;
-            wm.ctl[0] = 1;
-          } else if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
-            closed_int(Vl, 1);
-          } else if (act == ACT_INT || act == ACT_FINAL) {
-            const int kind = act == ACT_INT ? KIND_INT : KIND_FINAL;
-            put_item(kind, 0, Vl, 1);
-            wm.ctl[1 + kind] = 1;
-          }
-          if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
-        }
-        __syncwarp();
-      }
-      for (;;) {
-        int n_int = wm.ctl[1], n_fin = wm.ctl[2];
-        const int sp = wm.ctl[0];
-        __syncwarp();
-        if (n_fin > IMAX - 32) {
-          integrate(KIND_FINAL, n_fin);
-          n_fin = 0;
-        }
-        if (n_int > IMAX - 32) {
-          integrate(KIND_INT, n_int);
-          n_int = 0;
-        }
-        if (sp == 0) {
-          if (lane == 0) {
-            wm.ctl[1] = n_int;
-            wm.ctl[2] = n_fin;
-          }
-          __syncwarp();
-          break;
-        }
-        const int np = min(G::NPOP, sp);
-        const int base = sp - np;
-        const int par = lane / G::NCH, c = lane % G::NCH;
-        const bool active = par < np;
-        R V[NV][D];
-        uint32_t code = 0;
-        int act = ACT_DROP;
-        if (active) {
-          const int slot = base + par;
-          const uint32_t pcode = wm.rc[slot];
-          const int plevel = pcode >> LEVEL_SHIFT;
-#pragma unroll
-          for (int v = 0; v < NV; v++) {
-            int ia, ib;
-            mid_pair<D>(c, v, ia, ib);
-#pragma unroll
-            for (int k = 0; k < D; k++)
-              V[v][k] = midp(wm.rv[(ia * D + k) * P.scap + slot], wm.rv[(ib * D + k) * P.scap + slot]);
-          }
-          code = (((uint32_t)(plevel + 1)) << LEVEL_SHIFT) | (pcode & ((1u << LEVEL_SHIFT) - 1)) |
-                 ((uint32_t)c << (G::BITS * (plevel - 1)));
-        }
-        __syncwarp();
-        if (active) act = classify(V, code);
-        const int level = code >> LEVEL_SHIFT;
-        if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
-        if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
-          closed_int(V, level);
-          act = ACT_DROP;
-        }
-        const unsigned m_int = __ballot_sync(0xffffffffu, act == ACT_INT);
-        const unsigned m_fin = __ballot_sync(0xffffffffu, act == ACT_FINAL);
-        const unsigned m_ref = __ballot_sync(0xffffffffu, act == ACT_REFINE);
-        const unsigned below = (1u << lane) - 1u;
-        if (act == ACT_INT) put_item(KIND_INT, n_int + __popc(m_int & below), V, level);
-        if (act == ACT_FINAL) put_item(KIND_FINAL, n_fin + __popc(m_fin & below), V, level);
-        const int nref = __popc(m_ref);
-        const bool overflow = base + nref > P.scap;
-        if (overflow) {
-          err |= ERR_STACK;
-        } else if (act == ACT_REFINE) {
-          const int slot = base + __popc(m_ref & below);
-#pragma unroll
-          for (int t = 0; t < NVC; t++) wm.rv[t * P.scap + slot] = V[t / D][t % D];
-          wm.rc[slot] = code;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          wm.ctl[0] = overflow ? base : base + nref;
-          wm.ctl[1] = n_int + __popc(m_int);
-          wm.ctl[2] = n_fin + __popc(m_fin);
-        }
-        __syncwarp();
-      }
-      {
-        const int n_int = wm.ctl[1], n_fin = wm.ctl[2];
-        if (n_fin > 0) integrate(KIND_FINAL, n_fin);
-        if (n_int > 0) integrate(KIND_INT, n_int);
-      }
-      // ---- end of pair: transpose-reduce, cross block, self sums ------------------------------
-      {
-        R* row = wm.red + lane * RS;
-#pragma unroll
-        for (int i = 0; i < NYL; i++) {
-          row[i] = gp[i];
-#pragma unroll
-          for (int k = 0; k < D; k++) row[(k + 1) * NYL + i] = hp[k][i];
-        }
-        row[NYL * NV] = ug;
-#pragma unroll
-        for (int k = 0; k < D; k++) row[NYL * NV + 1 + k] = uh[k];
-      }
-      __syncwarp();
-      // totals: tot[v*NQ + q] for v = 0 (g), 1..D (h_k) over the NQ inner points, then the
-      // D+1 uniform sums at tot[NQ*NV + v]
-      if (D == 2) {
-        if (lane < G::NRED) {
-          R s = 0;
-#pragma unroll 8
-          for (int src = 0; src < 32; src++) s += wm.red[src * RS + lane];
-          wm.tot[lane] = s;
-        }
-      } else {
-        // lanes 0..15 hold inner points 0..6, lanes 16..31 hold 7..13
-        if (lane < NYL * NV) {
-          R s0 = 0, s1 = 0;
-#pragma unroll 8
-          for (int src = 0; src < 16; src++) {
-            s0 += wm.red[src * RS + lane];
-            s1 += wm.red[(src + 16) * RS + lane];
-          }
-          const int v = lane / NYL, i = lane % NYL;
-          wm.tot[v * NQ + i] = s0;
-          wm.tot[v * NQ + 7 + i] = s1;
-        } else if (lane < NYL * NV + NV) {
-          R s = 0;
-#pragma unroll 8
-          for (int src = 0; src < 32; src++) s += wm.red[src * RS + lane];
-          wm.tot[NQ * NV + (lane - NYL * NV)] = s;
-        }
-      }
-      __syncwarp();
-      {
-        const R* tot = wm.tot;
-        if (lane < NBLK) {
-          const int a = lane / NV, c = lane % NV;
-          R s = 0;
-#pragma unroll
-          for (int q = 0; q < NQ; q++) {
-            R H;
-            if (c == 0) {
-              H = tot[q] + tot[NQ * NV];
-#pragma unroll
-              for (int k = 0; k < D; k++) H -= tot[(k + 1) * NQ + q] + tot[NQ * NV + 1 + k];
-            } else {
-              H = tot[c * NQ + q] + tot[NQ * NV + c];
-            }
-            s += sWB[q * NV + a] * H;
-          }
-          if (DIRECT) {
-            const int64_t pos = csr_find(P.row_ptr, P.col, P.conn[cur_m * NV + a],
-                                         P.conn[(int64_t)l * NV + c]);
-            if (pos < 0) err |= ERR_CSR;
-            else atomicAdd(&P.values[pos], (double)((R)(-2) * vol_m * s));
-          } else {
-            reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + lane] = (R)(-2) * vol_m * s;
-          }
-        }
-        if (lane < NQ) two_sum_add(gs_hi, gs_lo, tot[lane] + tot[NQ * NV]);
-      }
-      __syncwarp();
-    }
-  }
-  if (cur_m >= 0) flush_self();
-  for (int o = 16; o > 0; o >>= 1) {
-    st_items += __shfl_xor_sync(0xffffffffu, st_items, o);
-    st_exact += __shfl_xor_sync(0xffffffffu, st_exact, o);
-    st_closed += __shfl_xor_sync(0xffffffffu, st_closed, o);
-    st_band += __shfl_xor_sync(0xffffffffu, st_band, o);
-    err |= __shfl_xor_sync(0xffffffffu, err, o);
-  }
-  if (lane == 0) {
-    atomicAdd(&P.stats[0], st_items);
-    atomicAdd(&P.stats[2], st_exact);
-    atomicAdd(&P.stats[3], st_eval);  // every lane counted the same evaluated pairs
-    atomicAdd(&P.stats[4], st_closed);
-    atomicAdd(&P.stats[5], st_band);
-    if (err) atomicOr(P.err, err);
-  }
-}
-
-// ---- scatter of the local blocks into the CSR values ------------------------------------------
-// One CTA per inner element m: the column lists of the rows of m's nodes are cached in shared
-// memory; every cross block of the pairs of m in [p_begin, p_end) is added with FP64 atomics
-// after a binary search in the cached row, and (with_self) the self block of m.
-template <int D, typename R>
-__global__ void __launch_bounds__(128) k_scatter(int64_t m_begin, int64_t p_begin, int64_t p_end,
-                                                 const int64_t* __restrict__ pair_off,
-                                                 const int32_t* __restrict__ pair_l,
-                                                 const int32_t* __restrict__ conn,
-                                                 const int64_t* __restrict__ row_ptr,
-                                                 const int32_t* __restrict__ col,
-                                                 const R* __restrict__ blk,
-                                                 const double* __restrict__ selfblk, int with_self,
-                                                 double* __restrict__ values, int* __restrict__ err) {
-  constexpr int NV = D + 1, NB = NV * NV;
-  extern __shared__ int32_t rows[];
-  __shared__ int64_t rbeg[NV];
-  __shared__ int rlen[NV], roff[NV + 1];
-  __shared__ int32_t nodes[NV];
-  const int64_t m = m_begin + blockIdx.x;
-  if (threadIdx.x < NV) {
-    int32_t i = conn[m * NV + threadIdx.x];
-    nodes[threadIdx.x] = i;
-    rbeg[threadIdx.x] = row_ptr[i];
-    rlen[threadIdx.x] = (int)(row_ptr[i + 1] - row_ptr[i]);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    roff[0] = 0;
-    for (int a = 0; a < NV; a++) roff[a + 1] = roff[a] + rlen[a];
-  }
-  __syncthreads();
-  for (int a = 0; a < NV; a++)
-    for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) rows[roff[a] + t] = col[rbeg[a] + t];
-  __syncthreads();
-  auto find = [&](int a, int32_t j) -> int64_t {
-    int lo = 0, hi = rlen[a] - 1;
-    const int32_t* r = rows + roff[a];
-    while (lo <= hi) {
-      int mid = (lo + hi) >> 1;
-      int32_t c = r[mid];
-      if (c == j) return rbeg[a] + mid;
-      if (c < j) lo = mid + 1;
-      else hi = mid - 1;
-    }
-    return -1;
-  };
-  if (!with_self) {
-    const int64_t q0 = max(pair_off[m], p_begin), q1 = min(pair_off[m + 1], p_end);
-    const int64_t n = (q1 - q0) * NB;
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-      const int64_t p = q0 + t / NB;
-      const int e = (int)(t % NB);
-      const int a = e / NV, c = e % NV;
-      const int32_t l = pair_l[p];
-      const int64_t pos = find(a, conn[(int64_t)l * NV + c]);
-      if (pos < 0) {
-        atomicOr(err, ERR_CSR);
-        continue;
-      }
-      atomicAdd(&values[pos], (double)blk[(p - p_begin) * NB + e]);
-    }
-  } else if (threadIdx.x < NB) {
-    const int a = threadIdx.x / NV, b = threadIdx.x % NV;
-    const int64_t pos = find(a, nodes[b]);
-    if (pos < 0) atomicOr(err, ERR_CSR);
-    else atomicAdd(&values[pos], selfblk[m * NB + threadIdx.x]);
-  }
-}
-
-template <int D, typename R, int KERN, bool DIRECT = false>
-nl_status launch_quad(const QParams& P, cudaStream_t s) {
-  int dev = 0;
-  NL_CUDA(cudaGetDevice(&dev));
-  int nsm = 0;
-  NL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  size_t tbl = table_bytes<R>();
-  int warps = 8;
-  while (warps > 1 && tbl + warps * WarpMem<D, R>::bytes(P.scap) > (size_t)110 * 1024) warps >>= 1;
-  const int threads = warps * 32;
-  size_t smem = tbl + warps * WarpMem<D, R>::bytes(P.scap);
-  if (smem > (size_t)220 * 1024)
-    return fail(NL_EINTERNAL, "assembly kernel needs %zu bytes of shared memory", smem);
-  NL_CUDA(cudaFuncSetAttribute(k_quad<D, R, KERN, DIRECT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quad<D, R, KERN, DIRECT>, threads, smem));
-  if (per_sm < 1) return fail(NL_EINTERNAL, "assembly kernel does not fit on an SM (smem %zu)", smem);
-  k_quad<D, R, KERN, DIRECT><<<NL_CNT(nsm * per_sm), threads, smem, s>>>(P);
-  NL_CUDA(cudaGetLastError());
-  return NL_OK;
-}
-
-template <int D, typename R>
-nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end, const R* blk,
-                         const double* selfblk, int with_self, double* values, int* err,
-                         cudaStream_t s, const int64_t* h_pair_off) {
-  int64_t m_begin = 0, m_end = m->n_elem;
-  if (!with_self) {
-    // inner elements whose pairs intersect [p_begin, p_end)
-    const int64_t* po = h_pair_off;
-    m_begin = std::upper_bound(po, po + m->n_elem + 1, p_begin) - po - 1;
-    m_end = std::lower_bound(po, po + m->n_elem + 1, p_end) - po;
-    m_begin = std::max<int64_t>(0, m_begin);
-    m_end = std::min<int64_t>(m->n_elem, std::max(m_end, m_begin));
-  }
-  if (m_end <= m_begin) return NL_OK;
-  size_t smem = sizeof(int32_t) * (size_t)(D + 1) * std::max(1, p->max_row_nnz);
-  if (smem > (size_t)200 * 1024)
-    return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
-  NL_CUDA(cudaFuncSetAttribute(k_scatter<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_scatter<D, R><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
-      m_begin, p_begin, p_end, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, blk, selfblk,
-      with_self, values, err);
-  NL_CUDA(cudaGetLastError());
-  return NL_OK;
-}
-
 template <int D, typename R, int KERN>
 nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s,
                        unsigned long long* scratch, int* err) {
@@ -986,6 +31,7 @@ nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaS
   size_t free_b = 0, total_b = 0;
   NL_CUDA(cudaMemGetInfo(&free_b, &total_b));
   size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
+  if (g_block_budget) budget = std::min(budget, g_block_budget);
   int64_t batch = std::max<int64_t>(1 << 20, (int64_t)(budget / (sizeof(R) * NB)));
   batch = std::min<int64_t>(batch, p->n_pairs);
   DevBuf<R> blk;
@@ -1021,65 +67,10 @@ nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaS
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st) {
-  const int D = m->dim;
-  if (!(kp->eps > 0.0 && kp->eps < kp->delta)) return fail(NL_EINVAL, "nl_assemble: need 0 < eps < delta");
-  if (kp->kernel != NL_KERNEL_CONST && kp->kernel != NL_KERNEL_TRUNC_GAUSS)
-    return fail(NL_EINVAL, "nl_assemble: unknown kernel %d", kp->kernel);
-  const int lmax_cap = D == 2 ? 12 : 9;
-  if (qp->L_min < 1 || qp->L_max < qp->L_min || qp->L_max > lmax_cap)
-    return fail(NL_EINVAL, "nl_assemble: need 1 <= L_min <= L_max <= %d", lmax_cap);
-  if ((qp->rule & ~NL_QUAD_COUNT_BAND) != 0) return fail(NL_EINVAL, "nl_assemble: only rule 0 is available");
-  if (prec != NL_PREC_FP64 && prec != NL_PREC_FP32 && prec != NL_PREC_MIXED_TF32 &&
-      prec != NL_PREC_MIXED_BF16)
-    return fail(NL_EINVAL, "nl_assemble: unknown precision %d", (int)prec);
-  cudaStream_t s = m->stream;
   QParams P;
-  memset(&P, 0, sizeof P);
-  P.n_elem = m->n_elem;
-  P.pair_off = p->pair_off;
-  P.pair_l = p->pair_l;
-  P.conn = m->conn;
-  P.evert = m->evert;
-  P.blo = m->blo;
-  P.bhi = m->bhi;
-  P.vol = m->vol;
-  P.jinv = m->jinv;
-  P.ef = m->ef;
-  double C = kp->C_override > 0.0 ? kp->C_override
-                                  : kernel_constant(D, kp->kernel, kp->delta, kp->eps);
-  if (kp->kappa > 0.0) C *= kp->kappa;
-  P.delta = kp->delta;
-  P.dme = kp->delta - kp->eps;
-  P.dpe = kp->delta + kp->eps;
-  P.C = C;
-  P.fC = (float)C;
-  P.inv_eps = 1.0 / kp->eps;
-  P.inv_delta2 = 1.0 / (kp->delta * kp->delta);
-  P.fdelta = (float)kp->delta;
-  P.finv_eps = (float)(1.0 / kp->eps);
-  P.fdme = (float)P.dme;
-  P.fdpe = (float)P.dpe;
-  P.fdme2 = (float)(P.dme * P.dme);
-  P.fdpe2 = (float)(P.dpe * P.dpe);
-  P.finv_delta2 = (float)P.inv_delta2;
-  // bound on |local coordinates| and on the FP32 error of the screened distances
-  double Rb = kp->delta + kp->eps + 2.0 * m->max_ext;
-  P.margin = (float)(2e-5 * Rb);
-  P.L_min = qp->L_min;
-  P.L_max = qp->L_max;
-  P.count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
-  int64_t total = 0, pw = 1;
-  for (int k = 1; k < qp->L_max; k++) {
-    total += pw;
-    pw *= (D == 2 ? 4 : 8);
-    if (total > 512) break;
-  }
-  P.scap = (int)std::max<int64_t>(8, std::min<int64_t>(total, 512));
-  const Rule& r = rule(D);
-  for (int q = 0; q < r.n; q++) {
-    for (int a = 0; a <= D; a++) P.B[q][a] = r.bary[q][a];
-    P.W[q] = r.w[q];
-  }
+  NL_TRY(fill_qparams("nl_assemble", m, p, kp, qp, prec, &P));
+  const int D = m->dim;
+  cudaStream_t s = m->stream;
   DevBuf<unsigned long long> scratch;
   DevBuf<int> err;
   NL_TRY(scratch.alloc(8, s));
@@ -1127,7 +118,7 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                 (herr & ERR_STACK) ? "refinement stack capacity exceeded" : "CSR entry missing");
   }
   if (st) {
-    const int nq = r.n;
+    const int nq = D == 2 ? 7 : 14;
     st->n_pairs = p->n_pairs;
     st->n_items = (int64_t)hs[1];
     st->n_point_pairs = (int64_t)hs[1] * nq * nq;
@@ -1180,7 +171,7 @@ nl_status run_noalloc(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaSt
   const size_t smem = sizeof(int32_t) * (size_t)(D + 1) * std::max(1, p->max_row_nnz);
   if (smem > (size_t)200 * 1024)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
-  NL_CUDA(cudaFuncSetAttribute(k_scatter<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NL_TRY((allow_smem(k_scatter<D, R>, smem)));
   k_scatter<D, R><<<NL_CNT((unsigned)m->n_elem), 128, smem, s>>>(
       0, 0, 0, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, (const R*)nullptr, P.selfblk, 1,
       values, P.err);
@@ -1197,20 +188,10 @@ nl_status run_noalloc(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaSt
 nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                            const nl_quad_params* qp, nl_precision prec, double* values,
                            nl_assemble_stats* st) {
-  const int D = m->dim;
   if (!values) return fail(NL_EINVAL, "nl_assemble_noalloc: values is NULL");
-  if (!(kp->eps > 0.0 && kp->eps < kp->delta))
-    return fail(NL_EINVAL, "nl_assemble_noalloc: need 0 < eps < delta");
-  if (kp->kernel != NL_KERNEL_CONST && kp->kernel != NL_KERNEL_TRUNC_GAUSS)
-    return fail(NL_EINVAL, "nl_assemble_noalloc: unknown kernel %d", kp->kernel);
-  const int lmax_cap = D == 2 ? 12 : 9;
-  if (qp->L_min < 1 || qp->L_max < qp->L_min || qp->L_max > lmax_cap)
-    return fail(NL_EINVAL, "nl_assemble_noalloc: need 1 <= L_min <= L_max <= %d", lmax_cap);
-  if ((qp->rule & ~NL_QUAD_COUNT_BAND) != 0)
-    return fail(NL_EINVAL, "nl_assemble_noalloc: only rule 0 is available");
-  if (prec != NL_PREC_FP64 && prec != NL_PREC_FP32 && prec != NL_PREC_MIXED_TF32 &&
-      prec != NL_PREC_MIXED_BF16)
-    return fail(NL_EINVAL, "nl_assemble_noalloc: unknown precision %d", (int)prec);
+  QParams P;
+  NL_TRY(fill_qparams("nl_assemble_noalloc", m, p, kp, qp, prec, &P));
+  const int D = m->dim;
   const int NB = (D + 1) * (D + 1);
   const int64_t max_elem =
       (int64_t)((NOALLOC_SCRATCH_BYTES - NOALLOC_HEADER_BYTES) / (sizeof(double) * NB));
@@ -1222,56 +203,7 @@ nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   unsigned char* scratch = nullptr;
   NL_TRY(noalloc_scratch(&scratch));
   cudaStream_t s = m->stream;
-  QParams P;
-  memset(&P, 0, sizeof P);
-  P.n_elem = m->n_elem;
-  P.p_begin = 0;
-  P.p_end = p->n_pairs;
-  P.pair_off = p->pair_off;
-  P.pair_l = p->pair_l;
-  P.conn = m->conn;
-  P.evert = m->evert;
-  P.blo = m->blo;
-  P.bhi = m->bhi;
-  P.vol = m->vol;
-  P.jinv = m->jinv;
-  P.ef = m->ef;
-  P.row_ptr = p->row_ptr;
-  P.col = p->col;
   P.values = values;
-  double C = kp->C_override > 0.0 ? kp->C_override
-                                  : kernel_constant(D, kp->kernel, kp->delta, kp->eps);
-  if (kp->kappa > 0.0) C *= kp->kappa;
-  P.delta = kp->delta;
-  P.dme = kp->delta - kp->eps;
-  P.dpe = kp->delta + kp->eps;
-  P.C = C;
-  P.fC = (float)C;
-  P.inv_eps = 1.0 / kp->eps;
-  P.inv_delta2 = 1.0 / (kp->delta * kp->delta);
-  P.fdelta = (float)kp->delta;
-  P.finv_eps = (float)(1.0 / kp->eps);
-  P.fdme = (float)P.dme;
-  P.fdpe = (float)P.dpe;
-  P.fdme2 = (float)(P.dme * P.dme);
-  P.fdpe2 = (float)(P.dpe * P.dpe);
-  P.finv_delta2 = (float)P.inv_delta2;
-  P.margin = (float)(2e-5 * (kp->delta + kp->eps + 2.0 * m->max_ext));
-  P.L_min = qp->L_min;
-  P.L_max = qp->L_max;
-  P.count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
-  int64_t total = 0, pw = 1;
-  for (int k = 1; k < qp->L_max; k++) {
-    total += pw;
-    pw *= (D == 2 ? 4 : 8);
-    if (total > 512) break;
-  }
-  P.scap = (int)std::max<int64_t>(8, std::min<int64_t>(total, 512));
-  const Rule& r = rule(D);
-  for (int q = 0; q < r.n; q++) {
-    for (int a = 0; a <= D; a++) P.B[q][a] = r.bary[q][a];
-    P.W[q] = r.w[q];
-  }
   // scratch layout: [0, 64) counter + stats, [64, 68) error word, [256, ...) self blocks.
   // Every call starts by clearing what it accumulates into.
   P.counter = reinterpret_cast<unsigned long long*>(scratch);
@@ -1303,7 +235,7 @@ nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
     return fail(NL_EINTERNAL, "nl_assemble_noalloc: device check failed (code %d: %s)", herr,
                 (herr & ERR_STACK) ? "refinement stack capacity exceeded" : "CSR entry missing");
   if (st) {
-    const int nq = r.n;
+    const int nq = D == 2 ? 7 : 14;
     st->n_pairs = p->n_pairs;
     st->n_items = (int64_t)hs[1];
     st->n_point_pairs = (int64_t)hs[1] * nq * nq;

@@ -5,8 +5,14 @@
 // u = w + g~.  A is nonsymmetric at the quadrature-error level when L_max > 1 (the outer rule
 // of Algorithm 1 depends on the pair), so BiCGStab is offered next to CG.  Vectors span all
 // nodes; constrained entries of the Krylov vectors stay zero and the SpMV skips them.
+//
+// All Krylov scalars live on the device: every dot product is reduced inside the kernel
+// that produces its operands (per-block partial sums; the last block to finish adds them
+// in a fixed order and computes the next scalar), so an iteration is a handful of kernel
+// launches with no host round trip; the host reads the residual every CHECK iterations.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -15,7 +21,14 @@
 namespace nlx {
 namespace {
 
-constexpr int RT = 256;  // reduction / vector kernel block size
+constexpr int RT = 256;    // block size of the vector kernels
+constexpr int CHECK = 8;   // iterations between host convergence checks
+
+// scalar slots (double) shared by the solver kernels
+enum : int {
+  S_RHO_NEW = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_RR, S_BB, S_RR_OLD, S_BREAK, S_NSLOTS = 16
+};
+constexpr int NPARTS = 2;  // dot products that one kernel can reduce
 
 template <int D>
 __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
@@ -61,78 +74,236 @@ __global__ void k_lift(int64_t n, const int64_t* __restrict__ rp, const int32_t*
   if (lane == 0) F[i] -= s;
 }
 
-// y = A_{free,free} x on free rows, 0 on constrained rows (warp per row)
-template <typename V, typename X>
-__global__ void k_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                       const V* __restrict__ val, const uint8_t* __restrict__ free_,
-                       const X* __restrict__ x, X* __restrict__ y) {
-  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  X s = 0;
-  if (free_[i]) {
-    for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += (X)val[t] * x[col[t]];
+// ---- reduction helpers ---------------------------------------------------------------------------
+struct Red {
+  double* part;       // [NPARTS][max_blocks] partial sums
+  unsigned* done;     // blocks finished, reset by the last one
+  double* S;          // scalar slots
+  int max_blocks;
+};
+
+// Block-reduces K values; the last block of the grid sums every block's partials in block
+// order and returns true in thread 0 with the totals in tot[].
+template <int K>
+__device__ bool reduce_last(const Red& R, double (&v)[K], double (&tot)[K]) {
+  __shared__ double ws[K][RT / 32];
+  __shared__ double acc[K][RT];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) ws[k][w] = x;
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[i] = s;
-}
-
-// residual r = b - A u on free rows (FP64), 0 elsewhere; u holds W on free nodes and 0 elsewhere
-__global__ void k_residual(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           const double* __restrict__ val, const uint8_t* __restrict__ free_,
-                           const double* __restrict__ u, const double* __restrict__ b,
-                           double* __restrict__ r) {
-  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  double s = 0.0;
-  if (free_[i])
-    for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += val[t] * u[col[t]];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) r[i] = free_[i] ? b[i] - s : 0.0;
-}
-
-// partial dot products per block; the final sum over blocks is done in fixed order
-template <typename X>
-__global__ void k_dot_partial(int64_t n, const X* __restrict__ a, const X* __restrict__ b,
-                              double* __restrict__ part) {
-  __shared__ double ws[RT / 32];
-  double s = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    s += (double)a[i] * (double)b[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      double t = 0.0;
+      for (int j = 0; j < (int)(blockDim.x >> 5); j++) t += ws[k][j];
+      R.part[k * R.max_blocks + blockIdx.x] = t;
+    }
+    __threadfence();
+    const unsigned ticket = atomicAdd(R.done, 1u);
+    last = ticket == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  // last block: fixed-order sum of the partials
+#pragma unroll
+  for (int k = 0; k < K; k++) {
     double t = 0.0;
-    for (int w = 0; w < RT / 32; w++) t += ws[w];
-    part[blockIdx.x] = t;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
+      t += ((volatile double*)R.part)[k * R.max_blocks + j];
+    acc[k][threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    double t = 0.0;
+    for (int j = 0; j < (int)blockDim.x; j++) t += acc[k][j];
+    tot[k] = t;
+  }
+  *R.done = 0;
+  return true;
+}
+
+__device__ __forceinline__ double safe_div(double a, double b, double* brk) {
+  if (b == 0.0 || !isfinite(b)) {
+    *brk = 1.0;
+    return 0.0;
+  }
+  return a / b;
+}
+
+// y = A x on free rows (0 elsewhere), warp per row, with the dot products of the iteration:
+//   MODE 0 (BiCGStab v = A p): (r^, v) -> alpha = rho_new / (r^, v), rho_old = rho_new
+//   MODE 1 (BiCGStab t = A s): (t, s), (t, t) -> omega = (t, s) / (t, t)
+//   MODE 2 (CG q = A p):       (p, q) -> alpha = rr / (p, q)
+template <typename X, typename V, int MODE>
+__global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int64_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ col,
+                                                 const V* __restrict__ val,
+                                                 const uint8_t* __restrict__ free_,
+                                                 const X* __restrict__ x, X* __restrict__ y,
+                                                 const X* __restrict__ w1, Red R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    X s = 0;
+    if (free_[i])
+      for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += (X)val[t] * x[col[t]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      y[i] = s;
+      if (MODE == 0) d[0] += (double)w1[i] * (double)s;
+      if (MODE == 1) {
+        d[0] += (double)s * (double)x[i];
+        d[1] += (double)s * (double)s;
+      }
+      if (MODE == 2) d[0] += (double)x[i] * (double)s;
+    }
+  }
+  double tot[2];
+  if (reduce_last<2>(R, d, tot)) {
+    double* S = R.S;
+    if (MODE == 0) {
+      S[S_ALPHA] = safe_div(S[S_RHO_NEW], tot[0], &S[S_BREAK]);
+      S[S_RHO_OLD] = S[S_RHO_NEW];
+    } else if (MODE == 1) {
+      S[S_OMEGA] = safe_div(tot[0], tot[1], &S[S_BREAK]);
+    } else {
+      S[S_ALPHA] = safe_div(S[S_RR], tot[0], &S[S_BREAK]);
+    }
   }
 }
 
-__global__ void k_dot_final(int nparts, int nslots, const double* __restrict__ part,
-                            double* __restrict__ out) {
-  // part holds nslots consecutive groups of nparts partial sums
-  int slot = threadIdx.x;
-  if (slot >= nslots) return;
-  double t = 0.0;
-  for (int k = 0; k < nparts; k++) t += part[slot * nparts + k];
-  out[slot] = t;
+// BiCGStab p = r + beta (p - omega v), beta = (rho_new / rho_old) (alpha / omega)
+template <typename X>
+__global__ void __launch_bounds__(RT) k_bicg_p(int64_t n, const X* __restrict__ r,
+                                               const X* __restrict__ v, X* __restrict__ p,
+                                               const double* __restrict__ S) {
+  const double om = S[S_OMEGA];
+  const double beta = (S[S_RHO_OLD] != 0.0 && om != 0.0)
+                          ? (S[S_RHO_NEW] / S[S_RHO_OLD]) * (S[S_ALPHA] / om) : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + (X)beta * (p[i] - (X)om * v[i]);
 }
 
+// BiCGStab s = r - alpha v
 template <typename X>
-__global__ void k_axpby(int64_t n, X a, const X* __restrict__ x, X b, X* __restrict__ y) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = a * x[i] + b * y[i];
+__global__ void __launch_bounds__(RT) k_bicg_s(int64_t n, const X* __restrict__ r,
+                                               const X* __restrict__ v, X* __restrict__ sv,
+                                               const double* __restrict__ S) {
+  const X a = (X)S[S_ALPHA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    sv[i] = r[i] - a * v[i];
 }
 
-// p = r + beta (p - omega v)
+// BiCGStab x += alpha p + omega s; r = s - omega t; (r, r) and (r^, r)
 template <typename X>
-__global__ void k_bicg_p(int64_t n, const X* __restrict__ r, X beta, X omega, const X* __restrict__ v,
-                         X* __restrict__ p) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+__global__ void __launch_bounds__(RT) k_bicg_xr(int64_t n, X* __restrict__ x, const X* __restrict__ p,
+                                                const X* __restrict__ sv, const X* __restrict__ t,
+                                                X* __restrict__ r, const X* __restrict__ rh, Red R) {
+  double d[2] = {0.0, 0.0};
+  const X a = (X)R.S[S_ALPHA], om = (X)R.S[S_OMEGA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += a * p[i] + om * sv[i];
+    const X ri = sv[i] - om * t[i];
+    r[i] = ri;
+    d[0] += (double)ri * (double)ri;
+    d[1] += (double)rh[i] * (double)ri;
+  }
+  double tot[2];
+  if (reduce_last<2>(R, d, tot)) {
+    R.S[S_RR] = tot[0];
+    R.S[S_RHO_NEW] = tot[1];
+  }
+}
+
+// CG x += alpha p; r -= alpha q; (r, r); keeps the previous (r, r) for beta
+template <typename X>
+__global__ void __launch_bounds__(RT) k_cg_xr(int64_t n, X* __restrict__ x, const X* __restrict__ p,
+                                              const X* __restrict__ q, X* __restrict__ r, Red R) {
+  double d[2] = {0.0, 0.0};
+  const X a = (X)R.S[S_ALPHA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += a * p[i];
+    const X ri = r[i] - a * q[i];
+    r[i] = ri;
+    d[0] += (double)ri * (double)ri;
+  }
+  double tot[2];
+  if (reduce_last<2>(R, d, tot)) {
+    R.S[S_RR_OLD] = R.S[S_RR];
+    R.S[S_RR] = tot[0];
+  }
+}
+
+// CG p = r + beta p, beta = (r, r) / (r, r)_old
+template <typename X>
+__global__ void __launch_bounds__(RT) k_cg_p(int64_t n, const X* __restrict__ r, X* __restrict__ p,
+                                             const double* __restrict__ S) {
+  const double beta = S[S_RR_OLD] != 0.0 ? S[S_RR] / S[S_RR_OLD] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = r[i] + (X)beta * p[i];
+}
+
+// r = b - A u (FP64) on free rows, its FP32 copy (optional) and (r, r)
+__global__ void __launch_bounds__(RT) k_residual(int64_t n, const int64_t* __restrict__ rp,
+                                                 const int32_t* __restrict__ col,
+                                                 const double* __restrict__ val,
+                                                 const uint8_t* __restrict__ free_,
+                                                 const double* __restrict__ u,
+                                                 const double* __restrict__ b, double* __restrict__ r,
+                                                 float* __restrict__ r32, Red R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    double s = 0.0;
+    if (free_[i])
+      for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += val[t] * u[col[t]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const double ri = free_[i] ? b[i] - s : 0.0;
+      r[i] = ri;
+      if (r32) r32[i] = (float)ri;
+      d[0] += ri * ri;
+    }
+  }
+  double tot[2];
+  if (reduce_last<2>(R, d, tot)) R.S[S_RR] = tot[0];
+}
+
+// (a, a) of the right-hand side; initialises the scalar slots
+template <typename X>
+__global__ void __launch_bounds__(RT) k_init_dot(int64_t n, const X* __restrict__ a, Red R) {
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[0] += (double)a[i] * (double)a[i];
+  double tot[2];
+  if (reduce_last<2>(R, d, tot)) {
+    double* S = R.S;
+    S[S_BB] = tot[0];
+    S[S_RR] = tot[0];
+    S[S_RHO_NEW] = tot[0];
+    S[S_RHO_OLD] = 1.0;
+    S[S_ALPHA] = 1.0;
+    S[S_OMEGA] = 1.0;
+    S[S_RR_OLD] = 0.0;
+    S[S_BREAK] = 0.0;
+  }
 }
 
 __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -141,8 +312,9 @@ __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ a, float* __r
 }
 
 __global__ void k_add_f32_to_f64(int64_t n, const float* __restrict__ d, double* __restrict__ u) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) u[i] += (double)d[i];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    u[i] += (double)d[i];
 }
 
 struct Ctx {
@@ -151,26 +323,20 @@ struct Ctx {
   const int64_t* rp;
   const int32_t* col;
   const uint8_t* free_;
-  int nparts;
-  double* part;  // [nparts * 4]
-  double* dres;  // [4]
-  unsigned gvec() const { return (unsigned)((n + RT - 1) / RT); }
-  unsigned grow() const { return (unsigned)((n * 32 + RT - 1) / RT); }
+  Red R;
+  int cap = 608;  // 4 CTAs per SM: reductions finish with few partial sums
+  unsigned gvec() const { return (unsigned)std::min<int64_t>(cap, (n + RT - 1) / RT); }
+  unsigned grow() const { return (unsigned)std::min<int64_t>(cap, (n * 32 + RT - 1) / RT); }
 };
 
-// several dot products, one host round trip
-template <typename X>
-nl_status dots(Ctx& c, int k, const X* const* a, const X* const* b, double* out) {
-  for (int j = 0; j < k; j++)
-    k_dot_partial<X><<<NL_CNT(c.nparts), RT, 0, c.s>>>(c.n, a[j], b[j], c.part + j * c.nparts);
-  k_dot_final<<<NL_CNT(1), 32, 0, c.s>>>(c.nparts, k, c.part, c.dres);
-  NL_CUDA(cudaMemcpyAsync(out, c.dres, sizeof(double) * k, cudaMemcpyDeviceToHost, c.s));
+nl_status read_scalars(Ctx& c, double* h) {
+  NL_CUDA(cudaMemcpyAsync(h, c.R.S, sizeof(double) * S_NSLOTS, cudaMemcpyDeviceToHost, c.s));
   NL_CUDA(cudaStreamSynchronize(c.s));
   return NL_OK;
 }
 
-// Krylov solve of A x = b (x starts at 0) to ||b - A x|| <= tol ||b||; X = double or float,
-// V = matrix value type.  Returns iterations in *it; *ok when converged.
+// Krylov solve of A x = b (x starts at 0) to ||b - A x|| <= tol ||b||.  X = double or float
+// (vectors), V = matrix value type.  *it = iterations, *ok when converged.
 template <typename X, typename V>
 nl_status krylov(Ctx& c, const V* val, int solver, const X* b, X* x, double tol, int max_it, int* it,
                  bool* ok, double* relres) {
@@ -181,106 +347,72 @@ nl_status krylov(Ctx& c, const V* val, int solver, const X* b, X* x, double tol,
   NL_TRY(v.alloc(n, c.s));
   NL_CUDA(cudaMemsetAsync(x, 0, sizeof(X) * n, c.s));
   NL_CUDA(cudaMemcpyAsync(r.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
-  NL_CUDA(cudaMemcpyAsync(p.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
-  double bb;
-  {
-    const X* a1[1] = {b};
-    NL_TRY(dots<X>(c, 1, a1, a1, &bb));
-  }
+  k_init_dot<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, b, c.R);
+  NL_CUDA(cudaGetLastError());
+  double h[S_NSLOTS];
+  NL_TRY(read_scalars(c, h));
+  const double bb = h[S_BB];
   *it = 0;
   *ok = false;
+  *relres = 0.0;
   if (bb == 0.0) {
     *ok = true;
-    *relres = 0.0;
     return NL_OK;
   }
   const double stop2 = tol * tol * bb;
-  if (solver == 0) {  // CG
-    double rr = bb;
-    for (int k = 0; k < max_it; k++) {
-      k_spmv<V, X><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p, v.p);
-      double pv;
-      {
-        const X* a1[1] = {p.p};
-        const X* b1[1] = {v.p};
-        NL_TRY(dots<X>(c, 1, a1, b1, &pv));
+  if (solver == 0) {  // CG: p = r = b
+    NL_CUDA(cudaMemcpyAsync(p.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
+    int k = 0;
+    while (k < max_it) {
+      const int batch = std::min(CHECK, max_it - k);
+      for (int j = 0; j < batch; j++) {
+        k_spmv_dot<X, V, 2><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p,
+                                                               v.p, nullptr, c.R);
+        k_cg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, p.p, v.p, r.p, c.R);
+        k_cg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, p.p, c.R.S);
       }
-      if (pv == 0.0) break;
-      X alpha = (X)(rr / pv);
-      k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, alpha, p.p, (X)1, x);
-      k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, -alpha, v.p, (X)1, r.p);
-      double rr_new;
-      {
-        const X* a1[1] = {r.p};
-        NL_TRY(dots<X>(c, 1, a1, a1, &rr_new));
-      }
-      *it = k + 1;
-      *relres = std::sqrt(rr_new / bb);
-      if (rr_new <= stop2) {
+      NL_CUDA(cudaGetLastError());
+      k += batch;
+      NL_TRY(read_scalars(c, h));
+      *it = k;
+      *relres = std::sqrt(std::max(h[S_RR], 0.0) / bb);
+      if (h[S_RR] <= stop2) {
         *ok = true;
         break;
       }
-      X beta = (X)(rr_new / rr);
-      rr = rr_new;
-      k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, (X)1, r.p, beta, p.p);  // p = r + beta p
+      if (h[S_BREAK] != 0.0 || !std::isfinite(h[S_RR])) break;
     }
     return NL_OK;
   }
-  // BiCGStab (van der Vorst)
+  // BiCGStab (van der Vorst): r^ = b, p = v = 0, rho_new = (r^, r)
   NL_TRY(rh.alloc(n, c.s));
   NL_TRY(sv.alloc(n, c.s));
   NL_TRY(t.alloc(n, c.s));
   NL_CUDA(cudaMemcpyAsync(rh.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
   NL_CUDA(cudaMemsetAsync(p.p, 0, sizeof(X) * n, c.s));
   NL_CUDA(cudaMemsetAsync(v.p, 0, sizeof(X) * n, c.s));
-  double rho = 1.0, alpha = 1.0, omega = 1.0;
-  for (int k = 0; k < max_it; k++) {
-    double rho_new;
-    {
-      const X* a1[1] = {rh.p};
-      const X* b1[1] = {r.p};
-      NL_TRY(dots<X>(c, 1, a1, b1, &rho_new));
+  int k = 0;
+  while (k < max_it) {
+    const int batch = std::min(CHECK, max_it - k);
+    for (int j = 0; j < batch; j++) {
+      k_bicg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, v.p, p.p, c.R.S);
+      k_spmv_dot<X, V, 0><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p, v.p,
+                                                             rh.p, c.R);
+      k_bicg_s<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, v.p, sv.p, c.R.S);
+      k_spmv_dot<X, V, 1><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, sv.p, t.p,
+                                                             nullptr, c.R);
+      k_bicg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, p.p, sv.p, t.p, r.p, rh.p, c.R);
     }
-    if (rho_new == 0.0 || omega == 0.0) break;
-    double beta = (rho_new / rho) * (alpha / omega);
-    rho = rho_new;
-    k_bicg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, (X)beta, (X)omega, v.p, p.p);
-    k_spmv<V, X><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p, v.p);
-    double rhv;
-    {
-      const X* a1[1] = {rh.p};
-      const X* b1[1] = {v.p};
-      NL_TRY(dots<X>(c, 1, a1, b1, &rhv));
-    }
-    if (rhv == 0.0) break;
-    alpha = rho / rhv;
-    // s = r - alpha v
-    NL_CUDA(cudaMemcpyAsync(sv.p, r.p, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
-    k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, (X)(-alpha), v.p, (X)1, sv.p);
-    k_spmv<V, X><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, sv.p, t.p);
-    double ts_tt[2];
-    {
-      const X* a2[2] = {t.p, t.p};
-      const X* b2[2] = {sv.p, t.p};
-      NL_TRY(dots<X>(c, 2, a2, b2, ts_tt));
-    }
-    omega = ts_tt[1] > 0.0 ? ts_tt[0] / ts_tt[1] : 0.0;
-    k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, (X)alpha, p.p, (X)1, x);
-    k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, (X)omega, sv.p, (X)1, x);
-    // r = s - omega t
-    NL_CUDA(cudaMemcpyAsync(r.p, sv.p, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
-    k_axpby<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, (X)(-omega), t.p, (X)1, r.p);
-    double rr;
-    {
-      const X* a1[1] = {r.p};
-      NL_TRY(dots<X>(c, 1, a1, a1, &rr));
-    }
-    *it = k + 1;
-    *relres = std::sqrt(rr / bb);
-    if (rr <= stop2) {
+    NL_CUDA(cudaGetLastError());
+    k += batch;
+    NL_TRY(read_scalars(c, h));
+    *it = k;
+    *relres = std::sqrt(std::max(h[S_RR], 0.0) / bb);
+    if (h[S_RR] <= stop2) {
       *ok = true;
       break;
     }
+    if (h[S_BREAK] != 0.0 || !std::isfinite(h[S_RR])) break;
   }
   return NL_OK;
 }
@@ -311,11 +443,11 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   NL_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * m->n_vert, s));
   unsigned ge = (unsigned)((m->n_elem + RT - 1) / RT);
   if (D == 2)
-    k_rhs_elems<2><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free, m->vol,
-                                     fn.p, f_const, B.p, W.p, r.n, F);
+    k_rhs_elems<2><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->vol, fn.p, f_const, B.p, W.p, r.n, F);
   else
-    k_rhs_elems<3><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free, m->vol,
-                                     fn.p, f_const, B.p, W.p, r.n, F);
+    k_rhs_elems<3><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->vol, fn.p, f_const, B.p, W.p, r.n, F);
   k_lift<<<NL_CNT((unsigned)((m->n_vert * 32 + RT - 1) / RT)), RT, 0, s>>>(
       m->n_vert, A->pairs->row_ptr, A->pairs->col, A->values, m->node_free, g.p, F);
   NL_CUDA(cudaGetLastError());
@@ -334,13 +466,19 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
   c.rp = A->pairs->row_ptr;
   c.col = A->pairs->col;
   c.free_ = m->node_free;
-  c.nparts = 120;
-  DevBuf<double> part, dres, x;
-  NL_TRY(part.alloc(c.nparts * 4, s));
-  NL_TRY(dres.alloc(4, s));
+  const int max_blocks = (int)std::max<int64_t>(c.grow(), c.gvec());
+  DevBuf<double> part, S, x;
+  DevBuf<unsigned> done;
+  NL_TRY(part.alloc((size_t)NPARTS * max_blocks, s));
+  NL_TRY(S.alloc(S_NSLOTS, s));
+  NL_TRY(done.alloc(1, s));
   NL_TRY(x.alloc(c.n, s));
-  c.part = part.p;
-  c.dres = dres.p;
+  NL_CUDA(cudaMemsetAsync(done.p, 0, sizeof(unsigned), s));
+  NL_CUDA(cudaMemsetAsync(S.p, 0, sizeof(double) * S_NSLOTS, s));
+  c.R.part = part.p;
+  c.R.done = done.p;
+  c.R.S = S.p;
+  c.R.max_blocks = max_blocks;
   int it = 0;
   bool ok = false;
   double rr = 0.0;
@@ -354,27 +492,23 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
     NL_TRY(r32.alloc(c.n, s));
     NL_TRY(d32.alloc(c.n, s));
     NL_TRY(r64.alloc(c.n, s));
-    k_f64_to_f32<<<NL_CNT((unsigned)((A->pairs->nnz + RT - 1) / RT + 1)), RT, 0, s>>>(A->pairs->nnz, A->values, a32.p);
+    k_f64_to_f32<<<NL_CNT((unsigned)((A->pairs->nnz + RT - 1) / RT + 1)), RT, 0, s>>>(
+        A->pairs->nnz, A->values, a32.p);
     NL_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double) * c.n, s));
-    double bb;
-    {
-      const double* a1[1] = {rhs->v};
-      NL_TRY(dots<double>(c, 1, a1, a1, &bb));
-    }
+    k_init_dot<double><<<NL_CNT(c.gvec()), RT, 0, s>>>(c.n, rhs->v, c.R);
+    double h[S_NSLOTS];
+    NL_TRY(read_scalars(c, h));
+    const double bb = h[S_BB];
     int total = 0;
     for (int outer = 0; outer < 60 && total < max_iter; outer++) {
-      k_residual<<<NL_CNT(c.grow()), RT, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v, r64.p);
-      double r2;
-      {
-        const double* a1[1] = {r64.p};
-        NL_TRY(dots<double>(c, 1, a1, a1, &r2));
-      }
-      rr = bb > 0.0 ? std::sqrt(r2 / bb) : 0.0;
+      k_residual<<<NL_CNT(c.grow()), RT, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v,
+                                                 r64.p, r32.p, c.R);
+      NL_TRY(read_scalars(c, h));
+      rr = bb > 0.0 ? std::sqrt(h[S_RR] / bb) : 0.0;
       if (rr <= rtol) {
         ok = true;
         break;
       }
-      k_f64_to_f32<<<NL_CNT(c.gvec()), RT, 0, s>>>(c.n, r64.p, r32.p);
       int inner = 0;
       bool iok = false;
       double irr = 0.0;
@@ -386,20 +520,19 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
     }
     it = total;
     if (!ok) {
-      k_residual<<<NL_CNT(c.grow()), RT, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v, r64.p);
-      double r2;
-      const double* a1[1] = {r64.p};
-      NL_TRY(dots<double>(c, 1, a1, a1, &r2));
-      rr = bb > 0.0 ? std::sqrt(r2 / bb) : 0.0;
+      k_residual<<<NL_CNT(c.grow()), RT, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v,
+                                                 r64.p, nullptr, c.R);
+      NL_TRY(read_scalars(c, h));
+      rr = bb > 0.0 ? std::sqrt(h[S_RR] / bb) : 0.0;
       ok = rr <= rtol;
     }
   }
-  std::vector<double> h(c.n);
+  std::vector<double> hx(c.n);
   std::vector<uint8_t> fr(c.n);
-  NL_CUDA(cudaMemcpyAsync(h.data(), x.p, sizeof(double) * c.n, cudaMemcpyDeviceToHost, s));
+  NL_CUDA(cudaMemcpyAsync(hx.data(), x.p, sizeof(double) * c.n, cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaMemcpyAsync(fr.data(), m->node_free, c.n, cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));
-  for (int64_t i = 0; i < c.n; i++) u_out[i] = fr[i] ? h[i] : g_nodes[i];
+  for (int64_t i = 0; i < c.n; i++) u_out[i] = fr[i] ? hx[i] : g_nodes[i];
   if (iters) *iters = it;
   if (rel_res) *rel_res = rr;
   if (!ok) return fail(NL_ENOTCONV, "nl_solve: no convergence to %g in %d iterations (%g)", rtol, it, rr);

@@ -46,6 +46,24 @@ class AssembleStats(ctypes.Structure):
                 ("n_closed_items", ctypes.c_int64), ("n_band_point_pairs", ctypes.c_int64)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("cells", ctypes.c_int32 * 3), ("h", ctypes.c_double),
+                ("lo", ctypes.c_double * 3), ("layer", ctypes.c_int32), ("jitter", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("kernel", KernelParams), ("quad", QuadParams),
+                ("precision", ctypes.c_int), ("ms", ctypes.c_int), ("solver", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("u_out", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("l2_err_omega", ctypes.c_double), ("n_pairs", ctypes.c_int64),
+                ("n_point_pairs", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_vert", ctypes.c_int64), ("t_submit_ms", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
+                ("message", ctypes.c_char * 160)]
+
+
 _lib = None
 
 
@@ -86,6 +104,23 @@ def lib():
         "nl_vector_destroy": (None, [p]),
         "nl_solve": (st, [p, p, p, i, d, i, i, p, ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_double)]),
+        "nl_serve_create": (st, [ctypes.c_size_t, i, pp]),
+        "nl_serve_submit": (st, [p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "nl_serve_poll": (st, [p, ctypes.c_uint64, ctypes.POINTER(Result)]),
+        "nl_serve_wait": (st, [p, ctypes.c_uint64, d, ctypes.POINTER(Result)]),
+        "nl_serve_stats": (st, [p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]),
+        "nl_serve_destroy": (None, [p]),
+        "nl_plan_create": (st, [i, p, p, p, p, i, i, p, pp]),
+        "nl_plan_execute": (st, [p]),
+        "nl_plan_sync": (st, [p, p]),
+        "nl_plan_values": (st, [p, i, pp, ctypes.POINTER(ctypes.c_int64)]),
+        "nl_plan_export": (st, [p, i, p]),
+        "nl_plan_matrix": (st, [p, i, pp]),
+        "nl_plan_shape": (st, [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_int)]),
+        "nl_plan_destroy": (None, [p]),
         "nl_quad_rule": (i, [i, p, p]),
         "nl_kernel_constant": (d, [i, i, d, d]),
     }
@@ -335,3 +370,127 @@ def assemble_problem(mesh_in, delta, eps, L_max, L_min=1, kernel=NL_KERNEL_CONST
     p = nl_pairs_build(m, delta, eps)
     A, st = nl_assemble(m, p, delta, eps, L_max, L_min, kernel, precision)
     return Problem(m, p, A, st)
+
+
+# ---- serving ------------------------------------------------------------------------------
+
+def make_request(dim, cells, h, lo, layer, delta, eps, L_max, kernel=NL_KERNEL_CONST,
+                 precision=NL_PREC_FP32, ms=1, solver=1, rtol=1e-10, max_iter=20000, jitter=0.0,
+                 seed=0, L_min=1, u_out=None) -> Request:
+    r = Request()
+    r.dim = dim
+    for k in range(3):
+        r.cells[k] = int(cells[k]) if k < dim else 1
+        r.lo[k] = float(lo[k]) if k < dim else 0.0
+    r.h, r.layer, r.jitter, r.seed = float(h), int(layer), float(jitter), int(seed)
+    r.kernel = KernelParams(float(delta), float(eps), 0.0, int(kernel), 0.0)
+    r.quad = QuadParams(int(L_min), int(L_max), 0)
+    r.precision, r.ms, r.solver, r.rtol, r.max_iter = int(precision), int(ms), int(solver), float(rtol), int(max_iter)
+    r.u_out = None if u_out is None else u_out.ctypes.data
+    return r
+
+
+class Server(_Handle):
+    """nl_serve_*: a continuous-batching server on the current device."""
+    _destroy = "nl_serve_destroy"
+
+    def __init__(self, device_mem_budget: int, max_slots: int):
+        h = ctypes.c_void_p()
+        _check(lib().nl_serve_create(int(device_mem_budget), int(max_slots), ctypes.byref(h)),
+               "nl_serve_create")
+        super().__init__(h)
+        self._keep = {}
+
+    def submit(self, req: Request, u_out=None) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().nl_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)), "nl_serve_submit")
+        self._keep[t.value] = u_out  # keeps the output array alive until the result is taken
+        return t.value
+
+    def poll(self, ticket: int):
+        r = Result()
+        s = lib().nl_serve_poll(self.h, ticket, ctypes.byref(r))
+        if s == NL_EBUSY:
+            return None
+        _check(s, "nl_serve_poll")
+        self._keep.pop(ticket, None)
+        return r
+
+    def wait(self, ticket: int, timeout_ms: float = 600000.0) -> Result:
+        r = Result()
+        _check(lib().nl_serve_wait(self.h, ticket, float(timeout_ms), ctypes.byref(r)), "nl_serve_wait")
+        self._keep.pop(ticket, None)
+        return r
+
+    def stats(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().nl_serve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+
+# ---- batched assembly -----------------------------------------------------------------------
+
+NL_PLAN_AUTOTUNE = 1
+NL_PLAN_GRAPH = 2
+
+
+class Plan(_Handle):
+    """nl_plan_*: n problems of one dimension and precision assembled by one launch.
+
+    problems: sequence of (mesh, pairs, delta, eps, L_max, L_min, kernel) tuples (L_min and
+    kernel may be left out: 1 and NL_KERNEL_CONST)."""
+    _destroy = "nl_plan_destroy"
+
+    def __init__(self, problems, precision=NL_PREC_FP64, flags=0, stream=None):
+        n = len(problems)
+        meshes = (ctypes.c_void_p * n)()
+        pairs = (ctypes.c_void_p * n)()
+        kps = (KernelParams * n)()
+        qps = (QuadParams * n)()
+        self._nnz = []
+        for k, pr in enumerate(problems):
+            mesh, pr_pairs, delta, eps, L_max = pr[:5]
+            L_min = pr[5] if len(pr) > 5 else 1
+            kernel = pr[6] if len(pr) > 6 else NL_KERNEL_CONST
+            meshes[k] = mesh.h.value
+            pairs[k] = pr_pairs.h.value
+            kps[k] = KernelParams(float(delta), float(eps), 0.0, int(kernel), 0.0)
+            qps[k] = QuadParams(int(L_min), int(L_max), 0)
+            self._nnz.append(pr_pairs.info()[1])
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else ctypes.c_void_p(0)
+        _check(lib().nl_plan_create(n, meshes, pairs, kps, qps, int(precision), int(flags), st,
+                                    ctypes.byref(h)), "nl_plan_create")
+        super().__init__(h)
+        self.n = n
+
+    def execute(self):
+        _check(lib().nl_plan_execute(self.h), "nl_plan_execute")
+
+    def sync(self):
+        stats = (AssembleStats * self.n)()
+        _check(lib().nl_plan_sync(self.h, stats), "nl_plan_sync")
+        return list(stats)
+
+    def export(self, k: int) -> np.ndarray:
+        out = np.zeros(self._nnz[k], dtype=np.float64)
+        _check(lib().nl_plan_export(self.h, int(k), _ptr(out)), "nl_plan_export")
+        return out
+
+    def device_values(self, k: int) -> int:
+        v = ctypes.c_void_p()
+        _check(lib().nl_plan_values(self.h, int(k), ctypes.byref(v), None), "nl_plan_values")
+        return v.value or 0
+
+    def matrix(self, k: int) -> Matrix:
+        h = ctypes.c_void_p()
+        _check(lib().nl_plan_matrix(self.h, int(k), ctypes.byref(h)), "nl_plan_matrix")
+        return Matrix(h, self._nnz[k])
+
+    def shape(self):
+        w, c, ch, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(lib().nl_plan_shape(self.h, ctypes.byref(w), ctypes.byref(c), ctypes.byref(ch),
+                                   ctypes.byref(ms), ctypes.byref(g)), "nl_plan_shape")
+        return {"warps": w.value, "ctas_per_sm": c.value, "chunk": ch.value,
+                "tuned_ms": ms.value, "graph": bool(g.value)}

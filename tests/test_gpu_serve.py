@@ -1,0 +1,77 @@
+"""Serving loop: requests admitted by memory and slots, run concurrently, and each result
+equal to the same request run alone (within the solver's tolerance)."""
+import numpy as np
+import pytest
+
+from nl_inputs import structured_mesh
+from paper_2101_08825_gb300 import nl
+
+pytestmark = pytest.mark.gpu
+
+
+def _req(dim, n, delta_h, kernel, prec, u=None, seed=0):
+    h = 1.0 / n
+    delta = delta_h * h
+    eps = delta / 10
+    layer = int(np.ceil((delta + eps) / h - 1e-9))
+    return nl.make_request(dim, (n,) * dim, h, (0.0,) * dim, layer, delta, eps,
+                           3 if dim == 2 else 2, kernel=kernel, precision=prec, ms=1, solver=1,
+                           rtol=1e-11, jitter=0.1, seed=seed, u_out=u)
+
+
+MIX = [(2, 24, 3.0, 0, nl.NL_PREC_FP32), (3, 6, 2.5, 1, nl.NL_PREC_FP32),
+       (2, 40, 4.0, 1, nl.NL_PREC_FP64), (2, 16, 2.0, 0, nl.NL_PREC_FP32),
+       (3, 5, 2.0, 0, nl.NL_PREC_FP64), (2, 32, 5.0, 0, nl.NL_PREC_FP32)]
+
+
+def _nvert(dim, n, delta_h):
+    layer = int(np.ceil(1.1 * delta_h - 1e-9))
+    return (n + 2 * layer + 1) ** dim
+
+
+def test_results_alone_equal_results_in_the_mix():
+    alone = []
+    with nl.Server(8 << 30, 1) as S:
+        for (dim, n, dh, k, prec) in MIX:
+            u = np.zeros(_nvert(dim, n, dh))
+            r = S.wait(S.submit(_req(dim, n, dh, k, prec, u), u))
+            assert r.status == nl.NL_OK, r.message
+            alone.append((u, r))
+    with nl.Server(8 << 30, 4) as S:
+        outs = [np.zeros(_nvert(d, n, dh)) for (d, n, dh, k, p) in MIX]
+        tickets = [S.submit(_req(*spec, u=u), u) for spec, u in zip(MIX, outs)]
+        res = [S.wait(t) for t in tickets]
+        starts = sorted(r.t_start_ms for r in res)
+        dones = sorted(r.t_done_ms for r in res)
+        assert starts[1] < dones[0], "requests did not overlap"
+        for (u0, r0), u1, r1 in zip(alone, outs, res):
+            assert r1.status == nl.NL_OK, r1.message
+            assert r1.n_pairs == r0.n_pairs and r1.n_point_pairs == r0.n_point_pairs
+            assert np.abs(u1 - u0).max() <= 1e-9 * np.abs(u0).max()
+            assert abs(r1.l2_err_omega / r0.l2_err_omega - 1) < 1e-6
+        p50, p99, sps = S.stats()
+        assert 0 < p50 <= p99 and sps > 0
+
+
+def test_admission_by_memory_budget_serialises_large_requests():
+    # a budget below two requests' footprint: the second waits for the first to finish
+    with nl.Server(64 << 20, 4) as S:
+        t = [S.submit(_req(2, 64, 4.0, 0, nl.NL_PREC_FP32)) for _ in range(3)]
+        res = [S.wait(x) for x in t]
+        assert all(r.status == nl.NL_OK for r in res)
+        res.sort(key=lambda r: r.t_start_ms)
+        for a, b in zip(res, res[1:]):
+            assert b.t_start_ms >= a.t_done_ms - 1e-3
+
+
+def test_poll_wait_timeout_and_bad_ticket():
+    with nl.Server(1 << 30, 1) as S:
+        t = S.submit(_req(2, 48, 4.0, 0, nl.NL_PREC_FP64))
+        with pytest.raises(nl.NLError) as e:
+            S.wait(t, timeout_ms=0.01)
+        assert e.value.status == nl.NL_ETIMEOUT
+        r = S.wait(t)
+        assert r.status == nl.NL_OK and r.l2_err_omega > 0
+        with pytest.raises(nl.NLError) as e:
+            S.poll(t)  # a result is taken once
+        assert e.value.status == nl.NL_EINVAL
