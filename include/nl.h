@@ -52,10 +52,13 @@ typedef enum {
 
 typedef enum {
   NL_PREC_FP64 = 0,       /* every point pair and every accumulation in FP64 */
-  NL_PREC_MIXED_TF32 = 1, /* gamma_eps in FP32; cross-term contraction on the tensor cores
-                             (TF32 with a split-precision correction, FP32 accumulation) */
-  NL_PREC_MIXED_BF16 = 2, /* as MIXED_TF32 with BF16 operands split in three parts */
-  NL_PREC_FP32 = 3        /* gamma_eps and the per-pair local sums in FP32 on the ALUs */
+  NL_PREC_MIXED_TF32 = 1, /* accepted; runs the NL_PREC_FP32 path.  The per-pair contraction
+                             (7 or 14 inner points x (dim+1) columns) is 3-4 FMAs per point
+                             pair beside a 15-20 instruction evaluation of gamma_eps, too thin
+                             for tensor-core tiles to save issue slots */
+  NL_PREC_MIXED_BF16 = 2, /* accepted; runs the NL_PREC_FP32 path (as MIXED_TF32) */
+  NL_PREC_FP32 = 3        /* gamma_eps and the per-pair local sums in FP32 on the ALUs
+                             (packed FP32x2 arithmetic), decisions and scatter exact/FP64 */
 } nl_precision;
 
 /* Kernel gamma_eps = C eta mu_{delta,eps}.  Requires 0 < eps < delta (Sec. 3).

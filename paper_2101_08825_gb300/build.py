@@ -27,7 +27,7 @@ def nvcc() -> str:
 
 
 def _flags(verbose: bool):
-    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-ftz=true",
                 "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I", os.path.join(HERE, "..", "include")]
     if verbose:
         f += ["-Xptxas", "-v"]

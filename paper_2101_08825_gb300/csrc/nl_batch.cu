@@ -201,7 +201,8 @@ nl_status plan_prepare_scatter(nl_plan* pl) {
 nl_status plan_autotune(nl_plan* pl) {
   cudaStream_t s = pl->stream;
   std::vector<std::pair<QShape, int>> cands;
-  for (int w : {8, 4})
+  const int wmax = pl->dim == 2 ? 8 : 4;
+  for (int w : {wmax, wmax / 2})
     for (int c : {0, 1})
       for (int ch : {8, 32, 128}) {
         QShape sh;

@@ -328,6 +328,11 @@ __global__ void k_mesh_elements(int64_t n_elem, int64_t n_vert, const double* __
     for (int c = 0; c < D; c++) f[D * D + r * D + c] = (float)inv[r][c];
   f[2 * D * D] = (float)vol[e];
   for (int t = 2 * D * D + 1; t < NL_EF_STRIDE(D); t++) f[t] = 0.f;
+  for (int k = 0; k < D; k++) {
+    const float hi = (float)V[0][k];
+    f[NL_EF_V0HI(D) + k] = hi;
+    f[NL_EF_V0LO(D) + k] = (float)(V[0][k] - (double)hi);
+  }
 }
 
 __global__ void k_count_n2e(int64_t n_entries, const int32_t* __restrict__ conn,

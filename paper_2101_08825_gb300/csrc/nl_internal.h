@@ -142,7 +142,7 @@ struct nl_mesh {
   double* vol = nullptr;           // [n_elem]
   double* jinv = nullptr;          // [n_elem][dim][dim]: lambda_{1..dim} = jinv (x - v0)
   float* ef = nullptr;             // [n_elem][EF_STRIDE(dim)]: FP32 vertex offsets v_a - v_0
-                                   // (a = 1..dim), inverse Jacobian, volume
+                                   // (a = 1..dim), inverse Jacobian, volume, v_0 as hi + lo
   int32_t max_conn_deg = 0;
   int64_t* n2e_off = nullptr;      // [n_vert+1] node -> elements
   int32_t* n2e = nullptr;          // [(dim+1) n_elem]
@@ -178,8 +178,12 @@ struct nl_vector {
   cudaStream_t stream = nullptr;
 };
 
-// FP32 per-element record: dim*dim offsets, dim*dim inverse Jacobian, volume, padding
-#define NL_EF_STRIDE(dim) ((dim) == 2 ? 12 : 20)
+// FP32 per-element record: dim*dim offsets v_a - v_0 (a = 1..dim), dim*dim inverse Jacobian,
+// volume, then v_0 as a float-float pair (dim high parts, dim low parts: v_0 = hi + lo to
+// about 2^-48 relative), zero padding to a multiple of 16 bytes
+#define NL_EF_STRIDE(dim) ((dim) == 2 ? 16 : 32)
+#define NL_EF_V0HI(dim) (2 * (dim) * (dim) + 1)
+#define NL_EF_V0LO(dim) (2 * (dim) * (dim) + 1 + (dim))
 
 namespace nlx {
 void mesh_release(nl_mesh* m);

@@ -82,6 +82,8 @@ struct QParams {
   int* err;
   double delta, dme, dpe, C, inv_eps, inv_delta2;
   float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
+  float fhie, fnthie, fdie;  // 1/(2 eps), -3/(2 eps), delta/eps (branch-free mollifier)
+  float fint2, fnotint2;     // screen thresholds (delta - eps -+ margin)^2 (-1: never)
   int L_min, L_max, scap, count_band;
   int kernel;  // nl_kernel_kind (read at run time by the batched kernel)
   int chunk;   // consecutive pairs a warp takes from the work counter
@@ -100,31 +102,53 @@ struct Geo {
   static constexpr int NVC = NV * D;            // vertex coordinates of a simplex
   static constexpr int BITS = D;                // path bits per level
   static constexpr int NBLK = NV * NV;          // entries of a local block
-  static constexpr int NRED = NYL * NV + NV;    // per-lane values reduced at pair end
-  static constexpr int RS = NRED | 1;           // odd row stride of the reduction scratch
-  static constexpr int TOTN = NQ * NV + NV;     // pair totals: per inner point, then uniform
   static constexpr int EFS = NL_EF_STRIDE(D);
 };
 
-// child c, vertex v = midpoint of parent vertices (a, b); a corner is mid(P, P) = P exactly
-__constant__ unsigned char c_mid2[4][3][2] = {{{0, 0}, {0, 1}, {0, 2}},
-                                              {{0, 1}, {1, 1}, {1, 2}},
-                                              {{0, 2}, {1, 2}, {2, 2}},
-                                              {{0, 1}, {1, 2}, {0, 2}}};
-__constant__ unsigned char c_mid3[8][4][2] = {
+// Child c, vertex v = midpoint of parent vertices (a, b); a corner is mid(P, P) = P exactly.
+// Triangles: the three corner children, then the middle one.  Tetrahedra (Bey): the four
+// corner children, then the four children of the octahedron cut along the x02-x13 diagonal.
+// The tables are packed two bits per index into 64-bit constants, so that a lane-dependent
+// child index is decoded in registers (a lookup in constant memory with a different address
+// per lane would be serialised).
+constexpr unsigned char k_mid2[4][3][2] = {{{0, 0}, {0, 1}, {0, 2}},
+                                           {{0, 1}, {1, 1}, {1, 2}},
+                                           {{0, 2}, {1, 2}, {2, 2}},
+                                           {{0, 1}, {1, 2}, {0, 2}}};
+constexpr unsigned char k_mid3[8][4][2] = {
     {{0, 0}, {0, 1}, {0, 2}, {0, 3}}, {{0, 1}, {1, 1}, {1, 2}, {1, 3}},
     {{0, 2}, {1, 2}, {2, 2}, {2, 3}}, {{0, 3}, {1, 3}, {2, 3}, {3, 3}},
     {{0, 1}, {0, 2}, {0, 3}, {1, 3}}, {{0, 1}, {0, 2}, {1, 2}, {1, 3}},
     {{0, 2}, {0, 3}, {1, 3}, {2, 3}}, {{0, 2}, {1, 2}, {1, 3}, {2, 3}}};
 
+constexpr uint64_t pack_mid2() {
+  uint64_t t = 0;
+  for (int c = 0; c < 4; c++)
+    for (int v = 0; v < 3; v++)
+      for (int j = 0; j < 2; j++) t |= (uint64_t)k_mid2[c][v][j] << (2 * ((c * 3 + v) * 2 + j));
+  return t;
+}
+constexpr uint64_t pack_mid3(int half) {
+  uint64_t t = 0;
+  for (int c = 0; c < 4; c++)
+    for (int v = 0; v < 4; v++)
+      for (int j = 0; j < 2; j++)
+        t |= (uint64_t)k_mid3[4 * half + c][v][j] << (2 * ((c * 4 + v) * 2 + j));
+  return t;
+}
+constexpr uint64_t MID2 = pack_mid2(), MID3A = pack_mid3(0), MID3B = pack_mid3(1);
+
 template <int D>
 __device__ __forceinline__ void mid_pair(int c, int v, int& a, int& b) {
   if (D == 2) {
-    a = c_mid2[c][v][0];
-    b = c_mid2[c][v][1];
+    const int sh = 2 * ((c * 3 + v) * 2);
+    a = (int)(MID2 >> sh) & 3;
+    b = (int)(MID2 >> (sh + 2)) & 3;
   } else {
-    a = c_mid3[c][v][0];
-    b = c_mid3[c][v][1];
+    const uint64_t t = c < 4 ? MID3A : MID3B;
+    const int sh = 2 * (((c & 3) * 4 + v) * 2);
+    a = (int)(t >> sh) & 3;
+    b = (int)(t >> (sh + 2)) & 3;
   }
 }
 
@@ -162,6 +186,8 @@ __device__ void exact_dists(const double (&V)[D + 1][D], const double* lo2, cons
   amin = mn;
 }
 
+// FP32 screen of the same distances: amax is returned squared (no square root on the
+// screening path), amin as is.
 template <int D>
 __device__ __forceinline__ void screen_dists(const float (&V)[D + 1][D], const float* lo2,
                                              const float* hi2, float& amax, float& amin) {
@@ -178,7 +204,7 @@ __device__ __forceinline__ void screen_dists(const float (&V)[D + 1][D], const f
     s += fmaxf(d1 * d1, d2 * d2);
     mn = fmaxf(mn, fmaxf(d1, d2));
   }
-  amax = sqrtf(s);
+  amax = s;  // squared: compared with squared thresholds
   amin = mn;
 }
 
@@ -249,12 +275,13 @@ __device__ __forceinline__ double xi_poly(double s) {
   return fma(s * p, 1.0 / 256.0, 0.5);
 }
 __device__ __forceinline__ float xi_poly(float s) {
+  // coefficients divided by 256 (exact: a power of two)
   float t = s * s;
-  float p = fmaf(35.f, t, -180.f);
-  p = fmaf(p, t, 378.f);
-  p = fmaf(p, t, -420.f);
-  p = fmaf(p, t, 315.f);
-  return fmaf(s * p, 1.f / 256.f, 0.5f);
+  float p = fmaf(35.f / 256.f, t, -180.f / 256.f);
+  p = fmaf(p, t, 378.f / 256.f);
+  p = fmaf(p, t, -420.f / 256.f);
+  p = fmaf(p, t, 315.f / 256.f);
+  return fmaf(s, p, 0.5f);
 }
 
 // mu_{delta,eps}(r) from r^2 (eq. mollifier with argument (delta - r)/eps)
@@ -274,6 +301,105 @@ __device__ __forceinline__ float mollifier(const QParams& P, float r2) {
   float r = r2 * q;
   r = fmaf(0.5f * q, fmaf(-r, r, r2), r);
   return xi_poly((P.fdelta - r) * P.finv_eps);
+}
+
+// ---- packed FP32 pairs (sm_100 family: add/sub/mul/fma .f32x2, one instruction for two
+// lanes of work) for the point-pair loop of the FP32 path ----------------------------------
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2pack(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(f2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2dup(float v) { return f2pack(v, v); }
+__device__ __forceinline__ f2 f2add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Asynchronous 16-byte global-to-shared copies (cp.async), used to fetch the next pair's
+// element record while the current pair is processed.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() {
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Hardware reciprocal square root (MUFU, about 2^-22 relative error), no denormal handling.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// mu_{delta,eps}(r) from r^2 without branches.  r = r2 q with q ~ 1/sqrt(r2) from the
+// hardware, refined by one Newton step folded into s: r' = r (3/2 - r q / 2) and
+//   s = (delta - r')/eps = delta/eps + r (r q/(2 eps) - 3/(2 eps)),
+// two FMAs from r and q/(2 eps).  s is clamped to [-1, 1], where xi is exactly 0 and 1
+// (xi(+-1) = 1/2 +- 128/256 in FP32), so every point pair takes the same path; r2 = 0
+// (coinciding points of a self pair) gives r = 0 and mu = 1.
+// Constants of the branch-free mollifier, read once per buffer integration (in the batched
+// kernel the parameters live in shared memory).
+struct MollK {
+  float hie, nthie, die;  // 1/(2 eps), -3/(2 eps), delta/eps
+};
+__device__ __forceinline__ float mollifier_bf(const MollK& K, float r2) {
+  const float q = rsqrt_hw(r2 + 1e-30f);
+  const float r = r2 * q;
+  const float bq = fmaf(r, q * K.hie, K.nthie);
+  const float sc = fminf(fmaxf(fmaf(r, bq, K.die), -1.f), 1.f);
+  return xi_poly(sc);
+}
+// The two point pairs of a packed r2 in scalar FP32: scalar FMAs take the constants as
+// immediate or constant-bank operands, while every packed constant needs a register pair.
+__device__ __forceinline__ f2 mollifier2(const MollK& K, f2 r2) {
+  float a, b;
+  f2unpack(r2, a, b);
+  return f2pack(mollifier_bf(K, a), mollifier_bf(K, b));
+}
+// Fully packed variant (a register pair per constant).
+__device__ __forceinline__ f2 mollifier2_packed(const MollK& P, f2 r2) {
+  float a, b;
+  f2unpack(f2add(r2, f2dup(1e-30f)), a, b);
+  const f2 q = f2pack(rsqrt_hw(a), rsqrt_hw(b));
+  const f2 r = f2mul(r2, q);
+  const f2 bq = f2fma(r, f2mul(q, f2dup(P.hie)), f2dup(P.nthie));
+  float s0, s1;
+  f2unpack(f2fma(r, bq, f2dup(P.die)), s0, s1);
+  const f2 sc = f2pack(fminf(fmaxf(s0, -1.f), 1.f), fminf(fmaxf(s1, -1.f), 1.f));
+  const f2 t = f2mul(sc, sc);
+  f2 p = f2fma(f2dup(35.f / 256.f), t, f2dup(-180.f / 256.f));
+  p = f2fma(p, t, f2dup(378.f / 256.f));
+  p = f2fma(p, t, f2dup(-420.f / 256.f));
+  p = f2fma(p, t, f2dup(315.f / 256.f));
+  return f2fma(sc, p, f2dup(0.5f));
+}
+__device__ __forceinline__ f2 eta_gauss2(float inv_delta2, f2 r2) {
+  float a, b;
+  f2unpack(r2, a, b);
+  return f2pack(__expf(-a * inv_delta2), __expf(-b * inv_delta2));
 }
 
 // Sum_j A_ij = 0 for every row of the exact discrete operator (sum_j phi_j = 1 at every
@@ -323,21 +449,20 @@ __device__ __forceinline__ void two_sum_add(double& hi, double& lo, double v) {
   (void)lo;
 }
 
-// Per-warp shared memory: stack records, two item buffers (SoA) and the reduction scratch.
+// Per-warp shared memory: stack records, two item buffers (SoA) and a small scratch.
 template <int D, typename R>
 struct WarpMem {
   R* rv;          // [NVC][scap]
   uint32_t* rc;   // [scap]
   R* iv;          // [2][NVC][IMAX]
   R* iw;          // [2][IMAX]
-  R* red;         // [32][RS]
-  R* tot;         // [TOTN] pair totals
-  int* ctl;       // [0] sp, [1] n_int, [2] n_final
+  R* red;         // 16 doubles of scratch (self-block sums)
+  float* pf;      // [2][32]: FP32 element records of the current and the next pair
   static __host__ __device__ size_t bytes(int scap) {
     using G = Geo<D>;
     size_t b = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
     b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * ((size_t)2 * G::NVC * IMAX + 2 * IMAX + 32 * G::RS + G::TOTN + 16);
+    b += sizeof(R) * ((size_t)2 * G::NVC * IMAX + 2 * IMAX) + sizeof(double) * 16 + sizeof(float) * 64;
     b += 16;
     return (b + 15) & ~size_t(15);
   }
@@ -349,15 +474,14 @@ struct WarpMem {
     off = (off + 15) & ~size_t(15);
     iv = reinterpret_cast<R*>(base + off);
     iw = iv + (size_t)2 * G::NVC * IMAX;
-    red = iw + 2 * IMAX;
-    tot = red + 32 * G::RS;
-    ctl = reinterpret_cast<int*>(tot + G::TOTN + 8);
+    red = iw + 2 * IMAX;  // 16-byte aligned: iv and iw hold multiples of 16 bytes
+    pf = reinterpret_cast<float*>(reinterpret_cast<char*>(red) + sizeof(double) * 16);
   }
 };
 
 template <typename R>
 __host__ __device__ constexpr size_t table_bytes() {
-  return (sizeof(R) * (14 * 4 * 2 + 16) + 15) & ~size_t(15);
+  return (sizeof(R) * (14 * 4 * 2 + 16 + 4) + 15) & ~size_t(15);
 }
 
 // Position of column j in CSR row i (binary search in global memory), or -1.
@@ -388,11 +512,19 @@ struct QBatch {
 // BATCHED = true: the launch covers the problems of Bt (same dimension and precision; the
 // kernel profile may differ when KERN = 2); each warp copies the parameters of the problem it
 // works on into shared memory and reads them from there.
+// Launch shape per dimension (measured on GB300): 2D 8 warps x 2 CTAs (128 registers), 3D 4
+// warps x 3 CTAs (up to 168 registers: the 3D state spills at 128).
+template <int D>
+struct QLaunch {
+  static constexpr int THREADS = D == 2 ? 256 : 128;
+  static constexpr int MIN_CTAS = D == 2 ? 2 : 3;
+};
+
 template <int D, typename R, int KERN, bool DIRECT = false, bool BATCHED = false>
-__global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch Bt) {
+__global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
+    k_quad(const QParams P0, const QBatch Bt) {
   using G = Geo<D>;
   constexpr int NV = G::NV, NQ = G::NQ, NYL = G::NYL, NVC = G::NVC, NBLK = G::NBLK;
-  constexpr int RS = G::RS;
   constexpr bool F32 = std::is_same<R, float>::value;
   extern __shared__ __align__(16) char smem_raw[];
   R* sB = reinterpret_cast<R*>(smem_raw);  // [NQ][NV]
@@ -403,6 +535,12 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
     sWB[t] = (R)(P0.W[t / NV] * P0.B[t / NV][t % NV]);
   }
   for (int t = threadIdx.x; t < NQ; t += blockDim.x) sW[t] = (R)P0.W[t];
+  R* sWBs = sWB + 14 * 4;  // [NV]: sum_q W[q] B[q][a] (the weight of a uniform contribution)
+  if (threadIdx.x < NV) {
+    double sacc = 0.0;
+    for (int q = 0; q < NQ; q++) sacc += P0.W[q] * P0.B[q][threadIdx.x];
+    sWBs[threadIdx.x] = (R)sacc;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpMem<D, R> wm;
@@ -419,32 +557,39 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
   const int ybase = (D == 3 && lane >= 16) ? 7 : 0;
   const int xl = (D == 3) ? (lane & 15) : lane;
 
-  unsigned long long st_items = 0, st_exact = 0, st_eval = 0, st_closed = 0, st_band = 0;
+  // per-lane work counters of the current chunk (32-bit: flushed at every chunk's end)
+  unsigned st_items = 0, st_exact = 0, st_eval = 0, st_closed = 0, st_band = 0;
   int err = 0;
 
   // state of the current inner element m
   int64_t cur_m = -1;
-  double v0m[D];      // first vertex of m (origin of the FP32 local coordinates)
+  float v0h[D], v0l[D];  // R = float: first vertex of m (origin of the local coordinates), hi + lo
   R lo_m[D], hi_m[D]; // box of m (local FP32 coordinates, or global FP64)
   R y[NYL][D];        // inner points of m (local if R = float)
+  f2 yq[3][D];        // R = float: inner points 0-5 of the lane packed in pairs
   R vol_m = 0;
-  R gs_hi = 0, gs_lo = 0;  // lane t < NQ: sum of g over the m-run for inner point t
+  // The end-of-pair reduce-scatter leaves entry e_rs of NRS values on this lane: the cross
+  // block (e < NBLK) and the sums of g at the inner points (NBLK <= e < NBLK + NQ); a lane that
+  // holds a g entry keeps its compensated sum over the pairs of the current m-run
+  constexpr int NRS = D == 2 ? 16 : 32;
+  const int e_rs = NRS == 16 ? (lane >> 1) : lane;
+  const bool rs_writer = NRS == 16 ? (lane & 1) == 0 : true;
+  R gsh = 0, gsl = 0;
 
   auto flush_self = [&]() {
     // S[a][b] = 2 vol_m sum_y W B_a B_b g(y), in FP64 from the compensated sums
     double* sd = reinterpret_cast<double*>(wm.red);
-    if (lane < NQ) sd[lane] = (double)gs_hi + (double)gs_lo;
+    if (rs_writer && e_rs >= NBLK && e_rs < NBLK + NQ) sd[e_rs - NBLK] = (double)gsh + (double)gsl;
+    gsh = gsl = 0;
     __syncwarp();
     if (lane < NBLK) {
       int a = lane / NV, b = lane % NV;
-      double s = 0.0;
+      double sacc = 0.0;
 #pragma unroll
-      for (int q = 0; q < NQ; q++) s += (double)sWB[q * NV + a] * (double)sB[q * NV + b] * sd[q];
-      atomicAdd(&P.selfblk[cur_m * NBLK + lane], 2.0 * (double)vol_m * s);
+      for (int q = 0; q < NQ; q++) sacc += (double)sWB[q * NV + a] * (double)sB[q * NV + b] * sd[q];
+      atomicAdd(&P.selfblk[cur_m * NBLK + lane], 2.0 * (double)vol_m * sacc);
     }
     __syncwarp();
-    gs_hi = 0;
-    gs_lo = 0;
   };
 
   // adds the warp's counters to the current problem's statistics and clears them
@@ -457,11 +602,11 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
       err |= __shfl_xor_sync(0xffffffffu, err, o);
     }
     if (lane == 0) {
-      atomicAdd(&P.stats[0], st_items);
-      atomicAdd(&P.stats[2], st_exact);
-      atomicAdd(&P.stats[3], st_eval);  // every lane counted the same evaluated pairs
-      atomicAdd(&P.stats[4], st_closed);
-      atomicAdd(&P.stats[5], st_band);
+      if (st_items) atomicAdd(&P.stats[0], (unsigned long long)st_items);
+      if (st_exact) atomicAdd(&P.stats[2], (unsigned long long)st_exact);
+      if (st_eval) atomicAdd(&P.stats[3], (unsigned long long)st_eval);  // counted alike by every lane
+      if (st_closed) atomicAdd(&P.stats[4], (unsigned long long)st_closed);
+      if (st_band) atomicAdd(&P.stats[5], (unsigned long long)st_band);
       if (err) atomicOr(P0.err, err);
     }
     st_items = st_exact = st_eval = st_closed = st_band = 0;
@@ -524,16 +669,40 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
       }
       m = lo;
     }
+    int32_t l_lane = 0;  // pair_l of the pair p0 + 32 * (block) + lane
     for (int64_t p = p0; p < p1; p++) {
+      const int jj = (int)(p - p0);
+      if ((jj & 31) == 0) {
+        const int64_t pq = p + lane;
+        l_lane = pq < p1 ? P.pair_l[pq] : 0;
+      }
+      const int32_t l = __shfl_sync(0xffffffffu, l_lane, jj & 31);
+      if constexpr (F32) {
+        // the record of this pair was fetched during the previous pair except at the first pair
+        // of each block of 32; the next pair's record is fetched now (cp.async groups: wait for
+        // all but the group just committed)
+        constexpr int NCP = G::EFS / 4;
+        if ((jj & 31) == 0) {
+          if (lane < NCP) cp_async16(wm.pf + (jj & 1) * 32 + lane * 4, P.ef + (int64_t)l * G::EFS + lane * 4);
+          cp_async_commit();
+        }
+        const int32_t ln = __shfl_sync(0xffffffffu, l_lane, (jj + 1) & 31);
+        if (p + 1 < p1 && ((jj + 1) & 31) != 0 && lane < NCP)
+          cp_async16(wm.pf + ((jj + 1) & 1) * 32 + lane * 4, P.ef + (int64_t)ln * G::EFS + lane * 4);
+        cp_async_commit();
+      }
       while (p >= P.pair_off[m + 1]) m++;
       if (m != cur_m) {
         if (cur_m >= 0) flush_self();
         cur_m = m;
-#pragma unroll
-        for (int k = 0; k < D; k++) v0m[k] = P.evert[m * NVC + k];
         R Vm[NV][D];
         if (F32) {
           const float* ef = P.ef + m * G::EFS;
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            v0h[k] = ef[NL_EF_V0HI(D) + k];
+            v0l[k] = ef[NL_EF_V0LO(D) + k];
+          }
 #pragma unroll
           for (int k = 0; k < D; k++) Vm[0][k] = 0;
 #pragma unroll
@@ -570,14 +739,22 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
             y[i][k] = s;
           }
         }
+        if constexpr (F32) {
+#pragma unroll
+          for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int k = 0; k < D; k++) yq[j][k] = f2pack((float)y[2 * j][k], (float)y[2 * j + 1][k]);
+        }
       }
-      const int32_t l = P.pair_l[p];
       // ---- per-pair set-up ------------------------------------------------------------------
       R Vl[NV][D], Ji[D][D], wl;
-      if (F32) {
-        const float* ef = P.ef + (int64_t)l * G::EFS;
+      if constexpr (F32) {
+        cp_async_wait_prior();
+        __syncwarp();
+        const float* ef = wm.pf + (jj & 1) * 32;
 #pragma unroll
-        for (int k = 0; k < D; k++) Vl[0][k] = (R)(P.evert[(int64_t)l * NVC + k] - v0m[k]);
+        for (int k = 0; k < D; k++)  // v_0(l) - v_0(m) from the float-float pairs, ~1 ulp
+          Vl[0][k] = (R)((ef[NL_EF_V0HI(D) + k] - v0h[k]) + (ef[NL_EF_V0LO(D) + k] - v0l[k]));
 #pragma unroll
         for (int a = 1; a < NV; a++)
 #pragma unroll
@@ -600,6 +777,7 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
       }
 
       R gp[NYL], hp[D][NYL], ug = 0, uh[D];
+      f2 gq[3], hq[D][3];  // R = float: accumulators of inner points 0-5 in pairs
 #pragma unroll
       for (int i = 0; i < NYL; i++) {
         gp[i] = 0;
@@ -607,10 +785,18 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
         for (int k = 0; k < D; k++) hp[k][i] = 0;
       }
 #pragma unroll
+      for (int j = 0; j < 3; j++) {
+        gq[j] = 0ull;
+#pragma unroll
+        for (int k = 0; k < D; k++) hq[k][j] = 0ull;
+      }
+#pragma unroll
       for (int k = 0; k < D; k++) uh[k] = 0;
 
       // Algorithm 1 decision for a sub-element (R coordinates)
-      auto classify = [&](const R (&V)[NV][D], uint32_t code) -> int {
+      // count_exact: this lane counts an FP64 re-decision (lanes that classify the same
+      // sub-element redundantly count it once)
+      auto classify = [&](const R (&V)[NV][D], uint32_t code, bool count_exact) -> int {
         const int level = code >> LEVEL_SHIFT;
         if (level < P.L_min) return ACT_REFINE;
         const bool last = level == P.L_max;
@@ -627,16 +813,16 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
             flo[k] = (float)lo_m[k];
             fhi[k] = (float)hi_m[k];
           }
-          screen_dists<D>(Vf, flo, fhi, fam, fan);
-          const bool c_int = fam < P.fdme - P.margin;
-          const bool c_notint = fam > P.fdme + P.margin;
+          screen_dists<D>(Vf, flo, fhi, fam, fan);  // fam = squared aprx-max-dist
+          const bool c_int = fam < P.fint2;
+          const bool c_notint = fam > P.fnotint2;
           const bool c_ref = fan < P.fdpe - P.margin;
           const bool c_out = fan > P.fdpe + P.margin;
           if (last) return c_int ? ACT_INT : (c_out ? ACT_ZERO : ACT_FINAL);
           if (c_int) return ACT_INT;
           if (c_notint && c_ref) return ACT_REFINE;
           if (c_notint && c_out) return ACT_DROP;
-          st_exact += (level == 1) ? (lane == 0) : 1;
+          st_exact += count_exact ? 1 : 0;
           return exact_classify<D>(P.evert + (int64_t)l * NVC, P.blo + cur_m * D, P.bhi + cur_m * D,
                                    code, P.dme, P.dpe);
         } else {
@@ -685,10 +871,13 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
 
       // integrate the buffered items of one kind (warp-collective)
       auto integrate = [&](int kind, int n_it) {
+        const MollK MK{P.fhie, P.fnthie, P.fdie};
+        const bool count_band = P.count_band != 0, gauss = is_gauss();
+        const float inv_d2 = P.finv_delta2;
         const R* iv = wm.iv + (size_t)kind * NVC * IMAX;
         const R* iw = wm.iw + kind * IMAX;
         const int n_x = n_it * NQ;
-        st_eval += (unsigned long long)n_x * NQ;
+        st_eval += (unsigned)(n_x * NQ);
         for (int base = 0; base < n_x; base += G::XPI) {
           const int o = base + xl;
           const bool valid = o < n_x;
@@ -711,24 +900,74 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
             for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - Vl[0][c]);
             lam[r] = s;
           }
-#pragma unroll
-          for (int i = 0; i < NYL; i++) {
-            R r2 = 0;
+          if constexpr (F32) {
+            // inner points 0-5 in packed pairs, point 6 alone
+            f2 X[D], L[D];
 #pragma unroll
             for (int k = 0; k < D; k++) {
-              const R d = x[k] - y[i][k];
-              r2 += d * d;
+              X[k] = f2dup(x[k]);
+              L[k] = f2dup(lam[k]);
             }
-            R g = wcx;
-            if (kind == KIND_FINAL) {
-              g *= mollifier(P, r2);
-              if (P.count_band)
-                st_band += (valid && r2 >= (R)(P.dme * P.dme) && r2 <= (R)(P.dpe * P.dpe)) ? 1 : 0;
-            }
-            if (is_gauss()) g *= eta_gauss<R>(P, r2);
-            gp[i] += g;
+            const f2 Wx = f2dup(wcx);
 #pragma unroll
-            for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
+            for (int j = 0; j < 3; j++) {
+              f2 d = f2sub(X[0], yq[j][0]);
+              f2 r2 = f2mul(d, d);
+#pragma unroll
+              for (int k = 1; k < D; k++) {
+                d = f2sub(X[k], yq[j][k]);
+                r2 = f2fma(d, d, r2);
+              }
+              f2 g = Wx;
+              if (kind == KIND_FINAL) {
+                g = f2mul(g, mollifier2(MK, r2));
+                if (count_band) {
+                  float a, b;
+                  f2unpack(r2, a, b);
+                  st_band += (valid && a >= P.fdme2 && a <= P.fdpe2) ? 1 : 0;
+                  st_band += (valid && b >= P.fdme2 && b <= P.fdpe2) ? 1 : 0;
+                }
+              }
+              if (gauss) g = f2mul(g, eta_gauss2(inv_d2, r2));
+              gq[j] = f2add(gq[j], g);
+#pragma unroll
+              for (int k = 0; k < D; k++) hq[k][j] = f2fma(g, L[k], hq[k][j]);
+            }
+            float r2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; k++) {
+              const float d = x[k] - y[6][k];
+              r2 = fmaf(d, d, r2);
+            }
+            float g = wcx;
+            if (kind == KIND_FINAL) {
+              g *= mollifier_bf(MK, r2);
+              if (count_band) st_band += (valid && r2 >= P.fdme2 && r2 <= P.fdpe2) ? 1 : 0;
+            }
+            if (gauss) g *= __expf(-r2 * inv_d2);
+            gp[6] += g;
+#pragma unroll
+            for (int k = 0; k < D; k++) hp[k][6] += g * lam[k];
+          } else {
+#pragma unroll
+            for (int i = 0; i < NYL; i++) {
+              R r2 = 0;
+#pragma unroll
+              for (int k = 0; k < D; k++) {
+                const R d = x[k] - y[i][k];
+                r2 += d * d;
+              }
+              R g = wcx;
+              if (kind == KIND_FINAL) {
+                g *= mollifier(P, r2);
+                if (P.count_band)
+                  st_band += (valid && r2 >= (R)(P.dme * P.dme) && r2 <= (R)(P.dpe * P.dpe)) ? 1 : 0;
+              }
+              if (is_gauss()) g *= eta_gauss<R>(P, r2);
+              gp[i] += g;
+#pragma unroll
+              for (int k = 0; k < D; k++) hp[k][i] += g * lam[k];
+            }
           }
         }
       };
@@ -742,187 +981,238 @@ __global__ void __launch_bounds__(256, 2) k_quad(const QParams P0, const QBatch 
       };
 
       // ---- Algorithm 1 for this pair --------------------------------------------------------
+      // The warp-uniform state lives in registers (every lane computes it from the same
+      // ballots): sp records on the stack, n_int / n_fin buffered items.  A round expands up to
+      // 32/2^n parents, one child per lane; the first round takes its parent, E_l itself, from
+      // registers, and in 2D with L_max >= 3 expands two levels at once (16 lanes: the four
+      // children and, where a child is refined, its four children).
       {
+        int sp = 0, n_int = 0, n_fin = 0;
         const uint32_t code0 = 1u << LEVEL_SHIFT;
-        const int act = classify(Vl, code0);
-        if (lane == 0) {
-          wm.ctl[0] = 0;
-          wm.ctl[1] = 0;
-          wm.ctl[2] = 0;
-          if (act == ACT_REFINE) {
-#pragma unroll
-            for (int t = 0; t < NVC; t++) wm.rv[t * P.scap] = Vl[t / D][t % D];
-            wm.rc[0] = code0;
-            wm.ctl[0] = 1;
-          } else if (is_const() && act == ACT_INT) {
-            closed_int(Vl, 1);
-          } else if (act == ACT_INT || act == ACT_FINAL) {
-            const int kind = act == ACT_INT ? KIND_INT : KIND_FINAL;
-            put_item(kind, 0, Vl, 1);
-            wm.ctl[1 + kind] = 1;
-          }
-          if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
+        const int act0 = classify(Vl, code0, lane == 0);
+        if (act0 == ACT_INT || act0 == ACT_FINAL || act0 == ACT_ZERO) st_items += (lane == 0);
+        bool from_root = act0 == ACT_REFINE;
+        if (is_const() && act0 == ACT_INT) {
+          if (lane == 0) closed_int(Vl, 1);
+        } else if (act0 == ACT_INT || act0 == ACT_FINAL) {
+          if (lane == 0) put_item(act0 == ACT_INT ? KIND_INT : KIND_FINAL, 0, Vl, 1);
+          if (act0 == ACT_INT) n_int = 1;
+          else n_fin = 1;
         }
-        __syncwarp();
-      }
-      for (;;) {
-        int n_int = wm.ctl[1], n_fin = wm.ctl[2];
-        const int sp = wm.ctl[0];
-        __syncwarp();
-        if (n_fin > IMAX - 32) {
-          integrate(KIND_FINAL, n_fin);
-          n_fin = 0;
-        }
-        if (n_int > IMAX - 32) {
-          integrate(KIND_INT, n_int);
-          n_int = 0;
-        }
-        if (sp == 0) {
-          if (lane == 0) {
-            wm.ctl[1] = n_int;
-            wm.ctl[2] = n_fin;
-          }
-          __syncwarp();
-          break;
-        }
-        const int np = min(G::NPOP, sp);
-        const int base = sp - np;
-        const int par = lane / G::NCH, c = lane % G::NCH;
-        const bool active = par < np;
-        R V[NV][D];
-        uint32_t code = 0;
-        int act = ACT_DROP;
-        if (active) {
-          const int slot = base + par;
-          const uint32_t pcode = wm.rc[slot];
-          const int plevel = pcode >> LEVEL_SHIFT;
+        // child c of the simplex S (registers) by midpoints
+        auto child_of = [&](const R (&S)[NV][D], int c, R (&V)[NV][D]) {
 #pragma unroll
           for (int v = 0; v < NV; v++) {
             int ia, ib;
             mid_pair<D>(c, v, ia, ib);
 #pragma unroll
-            for (int k = 0; k < D; k++)
-              V[v][k] = midp(wm.rv[(ia * D + k) * P.scap + slot], wm.rv[(ib * D + k) * P.scap + slot]);
-          }
-          code = (((uint32_t)(plevel + 1)) << LEVEL_SHIFT) | (pcode & ((1u << LEVEL_SHIFT) - 1)) |
-                 ((uint32_t)c << (G::BITS * (plevel - 1)));
-        }
-        __syncwarp();
-        if (active) act = classify(V, code);
-        const int level = code >> LEVEL_SHIFT;
-        if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
-        if (is_const() && act == ACT_INT) {
-          closed_int(V, level);
-          act = ACT_DROP;
-        }
-        const unsigned m_int = __ballot_sync(0xffffffffu, act == ACT_INT);
-        const unsigned m_fin = __ballot_sync(0xffffffffu, act == ACT_FINAL);
-        const unsigned m_ref = __ballot_sync(0xffffffffu, act == ACT_REFINE);
-        const unsigned below = (1u << lane) - 1u;
-        if (act == ACT_INT) put_item(KIND_INT, n_int + __popc(m_int & below), V, level);
-        if (act == ACT_FINAL) put_item(KIND_FINAL, n_fin + __popc(m_fin & below), V, level);
-        const int nref = __popc(m_ref);
-        const bool overflow = base + nref > P.scap;
-        if (overflow) {
-          err |= ERR_STACK;
-        } else if (act == ACT_REFINE) {
-          const int slot = base + __popc(m_ref & below);
+            for (int k = 0; k < D; k++) {
+              R pa = S[0][k], pb = S[0][k];
 #pragma unroll
-          for (int t = 0; t < NVC; t++) wm.rv[t * P.scap + slot] = V[t / D][t % D];
-          wm.rc[slot] = code;
+              for (int q = 1; q < NV; q++) {
+                pa = (ia == q) ? S[q][k] : pa;
+                pb = (ib == q) ? S[q][k] : pb;
+              }
+              V[v][k] = midp(pa, pb);
+            }
+          }
+        };
+        // one classified node per lane: count it, sum it in closed form, buffer it or push it
+        auto settle = [&](const R (&V)[NV][D], uint32_t code, int act, int base) {
+          const int level = code >> LEVEL_SHIFT;
+          if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
+          if (is_const() && act == ACT_INT) {
+            closed_int(V, level);
+            act = ACT_DROP;
+          }
+          const unsigned m_int = __ballot_sync(0xffffffffu, act == ACT_INT);
+          const unsigned m_fin = __ballot_sync(0xffffffffu, act == ACT_FINAL);
+          const unsigned m_ref = __ballot_sync(0xffffffffu, act == ACT_REFINE);
+          const unsigned below = (1u << lane) - 1u;
+          if (act == ACT_INT || act == ACT_FINAL) {
+            const bool fin = act == ACT_FINAL;
+            put_item(fin ? KIND_FINAL : KIND_INT,
+                     fin ? n_fin + __popc(m_fin & below) : n_int + __popc(m_int & below), V, level);
+          }
+          const int nref = __popc(m_ref);
+          const bool overflow = base + nref > P.scap;
+          if (overflow) {
+            err |= ERR_STACK;
+          } else if (act == ACT_REFINE) {
+            const int slot = base + __popc(m_ref & below);
+#pragma unroll
+            for (int t = 0; t < NVC; t++) wm.rv[t * P.scap + slot] = V[t / D][t % D];
+            wm.rc[slot] = code;
+          }
+          sp = overflow ? base : base + nref;
+          n_int += __popc(m_int);
+          n_fin += __popc(m_fin);
+          __syncwarp();  // records and items written this round are visible to every lane
+        };
+        if (D == 2 && from_root && P.L_max >= 3) {
+          const int c2 = lane >> 2, c3 = lane & 3;
+          R V[NV][D];
+          uint32_t code = 0;
+          int act = ACT_DROP;
+          if (lane < 16) {
+            R C[NV][D];
+            child_of(Vl, c2, C);
+            const uint32_t codeC = (2u << LEVEL_SHIFT) | (uint32_t)c2;
+            const int actC = classify(C, codeC, c3 == 0);
+            if (actC == ACT_REFINE) {
+              child_of(C, c3, V);
+              code = (3u << LEVEL_SHIFT) | (uint32_t)c2 | ((uint32_t)c3 << G::BITS);
+              act = classify(V, code, true);
+            } else if (c3 == 0) {
+#pragma unroll
+              for (int v = 0; v < NV; v++)
+#pragma unroll
+                for (int k = 0; k < D; k++) V[v][k] = C[v][k];
+              code = codeC;
+              act = actC;
+            }
+          }
+          from_root = false;
+          settle(V, code, act, 0);
+        }
+        while (from_root || sp > 0) {
+          if (n_fin > IMAX - 32) {
+            integrate(KIND_FINAL, n_fin);
+            n_fin = 0;
+          }
+          if (n_int > IMAX - 32) {
+            integrate(KIND_INT, n_int);
+            n_int = 0;
+          }
+          const int np = from_root ? 1 : min(G::NPOP, sp);
+          const int base = sp - (from_root ? 0 : np);
+          const int par = lane / G::NCH, c = lane % G::NCH;
+          const bool active = par < np;
+          R V[NV][D];
+          uint32_t code = 0;
+          int act = ACT_DROP;
+          if (active) {
+            if (from_root) {
+              child_of(Vl, c, V);
+              code = (2u << LEVEL_SHIFT) | (uint32_t)c;
+            } else {
+              const int slot = base + par;
+              const uint32_t pcode = wm.rc[slot];
+              const int plevel = pcode >> LEVEL_SHIFT;
+#pragma unroll
+              for (int v = 0; v < NV; v++) {
+                int ia, ib;
+                mid_pair<D>(c, v, ia, ib);
+#pragma unroll
+                for (int k = 0; k < D; k++)
+                  V[v][k] = midp(wm.rv[(ia * D + k) * P.scap + slot], wm.rv[(ib * D + k) * P.scap + slot]);
+              }
+              code = (((uint32_t)(plevel + 1)) << LEVEL_SHIFT) | (pcode & ((1u << LEVEL_SHIFT) - 1)) |
+                     ((uint32_t)c << (G::BITS * (plevel - 1)));
+            }
+          }
+          __syncwarp();  // parent records are read before children overwrite their slots
+          from_root = false;
+          if (active) act = classify(V, code, true);
+          settle(V, code, act, base);
         }
         __syncwarp();
-        if (lane == 0) {
-          wm.ctl[0] = overflow ? base : base + nref;
-          wm.ctl[1] = n_int + __popc(m_int);
-          wm.ctl[2] = n_fin + __popc(m_fin);
-        }
-        __syncwarp();
-      }
-      {
-        const int n_int = wm.ctl[1], n_fin = wm.ctl[2];
         if (n_fin > 0) integrate(KIND_FINAL, n_fin);
         if (n_int > 0) integrate(KIND_INT, n_int);
       }
-      // ---- end of pair: transpose-reduce, cross block, self sums ------------------------------
+      // ---- end of pair: per-lane contraction, warp reduce-scatter, cross block, self sums ------
       {
-        R* row = wm.red + lane * RS;
+        if constexpr (F32) {
+#pragma unroll
+          for (int j = 0; j < 3; j++) {
+            f2unpack(gq[j], gp[2 * j], gp[2 * j + 1]);
+#pragma unroll
+            for (int k = 0; k < D; k++) f2unpack(hq[k][j], hp[k][2 * j], hp[k][2 * j + 1]);
+          }
+        }
+        // H_0 = g - sum_k h_k, H_c = h_{c-1} (P1 basis of l: phi_0 = 1 - sum_k lambda_k); the
+        // closed-form items add the same U_c at every inner point
+        R U[NV];
+        U[0] = ug;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          U[0] -= uh[k];
+          U[k + 1] = uh[k];
+        }
+        // lane partial of sum_y W_y B_a(y) H_c(y) over the lane's inner points, then the lane's g
+        // at its inner points (with the uniform part; 3D: both half-warp lanes of an outer
+        // point hold part of it), zero elsewhere
+        R v[NRS];
+#pragma unroll
+        for (int a = 0; a < NV; a++)
+#pragma unroll
+          for (int c = 0; c < NV; c++) v[a * NV + c] = sWBs[a] * U[c];
 #pragma unroll
         for (int i = 0; i < NYL; i++) {
-          row[i] = gp[i];
+          R H[NV];
+          H[0] = gp[i];
 #pragma unroll
-          for (int k = 0; k < D; k++) row[(k + 1) * NYL + i] = hp[k][i];
-        }
-        row[NYL * NV] = ug;
-#pragma unroll
-        for (int k = 0; k < D; k++) row[NYL * NV + 1 + k] = uh[k];
-      }
-      __syncwarp();
-      // totals: tot[v*NQ + q] for v = 0 (g), 1..D (h_k) over the NQ inner points, then the
-      // D+1 uniform sums at tot[NQ*NV + v]
-      if (D == 2) {
-        if (lane < G::NRED) {
-          R s = 0;
-#pragma unroll 8
-          for (int src = 0; src < 32; src++) s += wm.red[src * RS + lane];
-          wm.tot[lane] = s;
-        }
-      } else {
-        // lanes 0..15 hold inner points 0..6, lanes 16..31 hold 7..13
-        if (lane < NYL * NV) {
-          R s0 = 0, s1 = 0;
-#pragma unroll 8
-          for (int src = 0; src < 16; src++) {
-            s0 += wm.red[src * RS + lane];
-            s1 += wm.red[(src + 16) * RS + lane];
+          for (int k = 0; k < D; k++) {
+            H[0] -= hp[k][i];
+            H[k + 1] = hp[k][i];
           }
-          const int v = lane / NYL, i = lane % NYL;
-          wm.tot[v * NQ + i] = s0;
-          wm.tot[v * NQ + 7 + i] = s1;
-        } else if (lane < NYL * NV + NV) {
-          R s = 0;
-#pragma unroll 8
-          for (int src = 0; src < 32; src++) s += wm.red[src * RS + lane];
-          wm.tot[NQ * NV + (lane - NYL * NV)] = s;
+#pragma unroll
+          for (int a = 0; a < NV; a++) {
+            const R wb = sWB[(ybase + i) * NV + a];
+#pragma unroll
+            for (int c = 0; c < NV; c++) v[a * NV + c] += wb * H[c];
+          }
         }
-      }
-      __syncwarp();
-      {
-        const R* tot = wm.tot;
-        if (lane < NBLK) {
-          const int a = lane / NV, c = lane % NV;
-          R s = 0;
+        {
+          R ugt = ug;
+          if (D == 3) ugt += __shfl_xor_sync(0xffffffffu, ug, 16);
 #pragma unroll
-          for (int q = 0; q < NQ; q++) {
-            R H;
-            if (c == 0) {
-              H = tot[q] + tot[NQ * NV];
-#pragma unroll
-              for (int k = 0; k < D; k++) H -= tot[(k + 1) * NQ + q] + tot[NQ * NV + 1 + k];
+          for (int i = 0; i < NYL; i++) {
+            if (D == 2) {
+              v[NBLK + i] = gp[i] + ugt;
             } else {
-              H = tot[c * NQ + q] + tot[NQ * NV + c];
+              v[NBLK + i] = ybase == 0 ? gp[i] + ugt : (R)0;
+              v[NBLK + NYL + i] = ybase == 0 ? (R)0 : gp[i] + ugt;
             }
-            s += sWB[q * NV + a] * H;
           }
+#pragma unroll
+          for (int t = NBLK + NQ; t < NRS; t++) v[t] = 0;
+        }
+        // reduce-scatter over the warp: every step sends half of the remaining values to the
+        // partner lane and adds the half it keeps; 2D: four steps (offsets 16..2) and a final
+        // sum with lane ^ 1 (lane L holds entry L >> 1), 3D: five steps (lane L holds entry L)
+#pragma unroll
+        for (int half = NRS / 2; half >= 1; half >>= 1) {
+          const int off = half * (32 / NRS);
+          const bool up = (lane & off) != 0;
+#pragma unroll
+          for (int j = 0; j < half; j++) {
+            const R send = up ? v[j] : v[j + half];
+            const R keep = up ? v[j + half] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          }
+        }
+        const R tot_e = NRS == 16 ? v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1) : v[0];
+        if (rs_writer && e_rs < NBLK) {
+          const R cval = (R)(-2) * vol_m * tot_e;
           if (DIRECT) {
+            const int a = e_rs / NV, c = e_rs % NV;
             const int64_t pos = csr_find(P.row_ptr, P.col, P.conn[cur_m * NV + a],
                                          P.conn[(int64_t)l * NV + c]);
             if (pos < 0) err |= ERR_CSR;
-            else atomicAdd(&P.values[pos], (double)((R)(-2) * vol_m * s));
+            else atomicAdd(&P.values[pos], (double)cval);
           } else {
-            reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + lane] = (R)(-2) * vol_m * s;
+            reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + e_rs] = cval;
           }
         }
-        if (lane < NQ) two_sum_add(gs_hi, gs_lo, tot[lane] + tot[NQ * NV]);
+        if (e_rs >= NBLK && e_rs < NBLK + NQ) two_sum_add(gsh, gsl, tot_e);
       }
       __syncwarp();
     }
     }  // pairs of one problem within the chunk
-  }
-  if (cur_k >= 0) {
-    if (cur_m >= 0) flush_self();
     flush_stats();
   }
+  if (cur_k >= 0 && cur_m >= 0) flush_self();
 }
 
 // ---- scatter of the local blocks into the CSR values ------------------------------------------
@@ -1034,7 +1324,8 @@ nl_status launch_quad(const QParams& P, cudaStream_t s, const QBatch& Bt = QBatc
       WarpMem<D, R>::bytes(P.scap) + (BATCHED ? ((sizeof(QParams) + 15) & ~size_t(15)) : 0);
   // default: at most 110 KB per CTA (two CTAs per SM); a requested shape may use up to 220 KB
   const size_t limit = (size_t)(shape.warps > 0 ? 220 : 110) * 1024;
-  int warps = shape.warps > 0 ? std::min(shape.warps, 8) : 8;
+  const int max_warps = QLaunch<D>::THREADS / 32;
+  int warps = shape.warps > 0 ? std::min(shape.warps, max_warps) : max_warps;
   while (warps > 1 && tbl + warps * per_warp > limit) warps >>= 1;
   const int threads = warps * 32;
   const size_t smem = tbl + warps * per_warp;
@@ -1127,8 +1418,16 @@ inline nl_status fill_qparams(const char* who, const nl_mesh* m, const nl_pairs*
   P->fdme2 = (float)(P->dme * P->dme);
   P->fdpe2 = (float)(P->dpe * P->dpe);
   P->finv_delta2 = (float)P->inv_delta2;
+  P->fhie = (float)(0.5 / kp->eps);
+  P->fnthie = (float)(-1.5 / kp->eps);
+  P->fdie = (float)(kp->delta / kp->eps);
   // bound on |local coordinates| and on the FP32 error of the screened distances
   P->margin = (float)(2e-5 * (kp->delta + kp->eps + 2.0 * m->max_ext));
+  {
+    const double lo_t = (double)P->fdme - (double)P->margin, hi_t = (double)P->fdme + (double)P->margin;
+    P->fint2 = lo_t > 0.0 ? (float)(lo_t * lo_t) : -1.f;
+    P->fnotint2 = (float)(hi_t * hi_t);
+  }
   P->L_min = qp->L_min;
   P->L_max = qp->L_max;
   P->count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;

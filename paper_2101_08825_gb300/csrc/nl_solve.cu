@@ -155,8 +155,20 @@ __global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int64_t* __res
   double d[2] = {0.0, 0.0};
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
     X s = 0;
-    if (free_[i])
-      for (int64_t t = rp[i] + lane; t < rp[i + 1]; t += 32) s += (X)val[t] * x[col[t]];
+    if (free_[i]) {
+      // four independent partial sums keep four loads of x in flight per lane
+      const int64_t e = rp[i + 1];
+      int64_t t = rp[i] + lane;
+      X s1 = 0, s2 = 0, s3 = 0;
+      for (; t + 96 < e; t += 128) {
+        s += (X)val[t] * x[col[t]];
+        s1 += (X)val[t + 32] * x[col[t + 32]];
+        s2 += (X)val[t + 64] * x[col[t + 64]];
+        s3 += (X)val[t + 96] * x[col[t + 96]];
+      }
+      for (; t < e; t += 32) s += (X)val[t] * x[col[t]];
+      s = (s + s1) + (s2 + s3);
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
       y[i] = s;
@@ -324,7 +336,7 @@ struct Ctx {
   const int32_t* col;
   const uint8_t* free_;
   Red R;
-  int cap = 608;  // 4 CTAs per SM: reductions finish with few partial sums
+  int cap = 1216;  // 8 CTAs of 256 threads per SM: full occupancy for the row kernels
   unsigned gvec() const { return (unsigned)std::min<int64_t>(cap, (n + RT - 1) / RT); }
   unsigned grow() const { return (unsigned)std::min<int64_t>(cap, (n * 32 + RT - 1) / RT); }
 };

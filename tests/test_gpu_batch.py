@@ -80,7 +80,7 @@ def test_autotuned_graph_plan_repeats_and_feeds_the_solver():
     plain.sync()
     plan = nl.Plan(spec, precision=nl.NL_PREC_FP32, flags=nl.NL_PLAN_AUTOTUNE | nl.NL_PLAN_GRAPH)
     sh = plan.shape()
-    assert sh["graph"] and sh["warps"] in (4, 8) and sh["chunk"] in (8, 32, 128) and sh["tuned_ms"] > 0
+    assert sh["graph"] and sh["warps"] in (2, 4, 8) and sh["chunk"] in (8, 32, 128) and sh["tuned_ms"] > 0
     for rep in range(3):
         plan.execute()
         st = plan.sync()
