@@ -48,6 +48,8 @@ def parse():
                     help="requests of the seeded 512-request serving stream replayed by the "
                          "serving leg (0 = skip; 512 = the whole stream)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--batch-problems", type=int, default=128,
+                    help="small problems of the batching leg (0 = skip)")
     ap.add_argument("--profile", action="store_true",
                     help="one pair build and one FP32 and one FP64 assembly of the 2D workload "
                          "at h=1/128 (a small case for ncu), then exit")
@@ -313,6 +315,8 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(args, mesh, w, g, f_const, stream, world)
+    if args.batch_problems > 0:
+        out["batching"] = run_batching(args)
     if args.serve_requests > 0:
         out["serving"] = run_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -368,6 +372,49 @@ def e2e_ours(args, mesh, w, g, f_const, stream, world):
     return {"value": round(world * n_pairs / (ms / 1e3), 1), "unit": "element pairs/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
+
+
+def run_batching(args):
+    """Batching leg: many small 2D problems (8-24 cells per side, delta in {2,3,4}h,
+    eps = delta/10, L_max = 3, constant and Gaussian kernels alternating, jitter 0.1h), meshes
+    and pair lists resident.  Sequential nl_assemble calls against one plan that assembles
+    all of them in a single launch (autotuned launch shape, replayed CUDA graph); FP32."""
+    import torch
+    from paper_2101_08825_gb300 import nl
+    probs = []
+    for i in range(args.batch_problems):
+        n = 8 + (i * 7) % 17
+        h = 1.0 / n
+        delta = (2 + i % 3) * h
+        eps = delta / 10
+        layer = int(math.ceil((delta + eps) / h - 1e-9))
+        m = nl.nl_mesh_create_box(2, (n, n), h, (0.0, 0.0), layer, 0.1, i)
+        p = nl.nl_pairs_build(m, delta, eps)
+        probs.append((m, p, delta, eps, 3, 1, i % 2))
+    pairs = sum(pr[1].info()[0] for pr in probs)
+
+    def seq():
+        for pr in probs:
+            nl.nl_assemble(*pr[:2], pr[2], pr[3], pr[4], pr[5], pr[6], nl.NL_PREC_FP32)
+        torch.cuda.synchronize()
+
+    seq()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        seq()
+    t_seq = (time.perf_counter() - t0) / 3
+    plan = nl.Plan(probs, precision=nl.NL_PREC_FP32, flags=nl.NL_PLAN_AUTOTUNE | nl.NL_PLAN_GRAPH)
+    plan.execute()
+    plan.sync()
+    t0 = time.perf_counter()
+    for _ in range(10):
+        plan.execute()
+        st = plan.sync()
+    t_plan = (time.perf_counter() - t0) / 10
+    return {"problems": len(probs), "element_pairs": int(pairs),
+            "sequential_pairs_per_s": round(pairs / t_seq, 1),
+            "plan_pairs_per_s": round(pairs / t_plan, 1), "speedup": round(t_seq / t_plan, 2),
+            "plan_gpu_ms": round(st[0].ms_assemble, 3), "shape": plan.shape()}
 
 
 def run_serving(args):

@@ -660,12 +660,19 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
     if (cur_m >= 0 && P.pair_off[cur_m] <= p0 && p0 < P.pair_off[cur_m + 1]) {
       m = cur_m;
     } else {
-      // the last m with pair_off[m] <= p0 (pair_off[0] = 0 <= p0 < pair_off[n_elem])
-      int64_t lo = 0, hi = P.n_elem;
+      // the last m with pair_off[m] <= p0 (pair_off[0] = 0 <= p0 < pair_off[n_elem]): a 32-way
+      // search, every lane probing one position per round (a few dependent loads instead of
+      // log2(n_elem))
+      int64_t lo = 0, hi = P.n_elem;  // pair_off[lo] <= p0 < pair_off[hi]
       while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (P.pair_off[mid] <= p0) lo = mid;
-        else hi = mid;
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t idx = lo + (int64_t)lane * step;
+        const bool le = idx < hi && P.pair_off[idx] <= p0;
+        const unsigned bal = __ballot_sync(0xffffffffu, le);
+        const int last = 31 - __clz(bal);  // lane 0 probes lo itself, so bal != 0
+        const int64_t nlo = lo + (int64_t)last * step;
+        hi = min(hi, nlo + step);
+        lo = nlo;
       }
       m = lo;
     }

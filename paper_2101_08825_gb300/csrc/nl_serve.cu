@@ -104,7 +104,7 @@ void run_request(nl_server* S, cudaStream_t stream, Job& job) {
   nlx::g_block_budget = S->block_budget;
   auto finish = [&](nl_status st) {
     res.status = st;
-    if (st != NL_OK) snprintf(res.message, sizeof res.message, "%s", nl_last_error());
+    if (st != NL_OK && res.message[0] == 0) snprintf(res.message, sizeof res.message, "%s", nl_last_error());
     nl_vector_destroy(rhs);
     nl_matrix_destroy(A);
     nl_pairs_destroy(pairs);
@@ -141,6 +141,7 @@ void run_request(nl_server* S, cudaStream_t stream, Job& job) {
   double rr = 0.0;
   st = nl_solve(A, rhs, g.data(), r.solver, r.rtol, r.max_iter,
                 r.precision == NL_PREC_FP64 ? NL_PREC_FP64 : NL_PREC_FP32, u.data(), &iters, &rr);
+  if (st != NL_OK) snprintf(res.message, sizeof res.message, "%s", nl_last_error());
   res.iters = iters;
   res.rel_res = rr;
   // ||u - u_h|| over Omega with the degree-5 rule on every element of Omega

@@ -22,6 +22,8 @@ namespace nlx {
 namespace {
 
 constexpr int RT = 256;    // block size of the vector kernels
+constexpr int RTR = 1024;  // block size of the row (SpMV) kernels: few large blocks, so that
+                           // the blocks' partial sums serialise on few atomic tickets
 constexpr int CHECK = 8;   // iterations between host convergence checks
 
 // scalar slots (double) shared by the solver kernels
@@ -83,11 +85,11 @@ struct Red {
 };
 
 // Block-reduces K values; the last block of the grid sums every block's partials in block
-// order and returns true in thread 0 with the totals in tot[].
-template <int K>
+// order and returns true in thread 0 with the totals in tot[].  BS: the largest block size
+// the calling kernel is launched with (blockDim.x <= BS).
+template <int K, int BS = RT>
 __device__ bool reduce_last(const Red& R, double (&v)[K], double (&tot)[K]) {
-  __shared__ double ws[K][RT / 32];
-  __shared__ double acc[K][RT];
+  __shared__ double ws[K][BS / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -97,36 +99,33 @@ __device__ bool reduce_last(const Red& R, double (&v)[K], double (&tot)[K]) {
     if (lane == 0) ws[k][w] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (w == 0) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
-      double t = 0.0;
-      for (int j = 0; j < (int)(blockDim.x >> 5); j++) t += ws[k][j];
-      R.part[k * R.max_blocks + blockIdx.x] = t;
+      double t = lane < (int)(blockDim.x >> 5) ? ws[k][lane] : 0.0;  // warps of this launch
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) R.part[k * R.max_blocks + blockIdx.x] = t;
     }
-    __threadfence();
-    const unsigned ticket = atomicAdd(R.done, 1u);
-    last = ticket == gridDim.x - 1;
+    if (lane == 0) {
+      __threadfence();
+      const unsigned ticket = atomicAdd(R.done, 1u);
+      last = ticket == gridDim.x - 1;
+    }
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  // last block: fixed-order sum of the partials
+  // last block: fixed-order sum of the partials (every thread strides over the blocks, then a
+  // fixed tree over the threads)
+  if (w != 0) return false;
 #pragma unroll
   for (int k = 0; k < K; k++) {
     double t = 0.0;
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x)
-      t += ((volatile double*)R.part)[k * R.max_blocks + j];
-    acc[k][threadIdx.x] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return false;
-#pragma unroll
-  for (int k = 0; k < K; k++) {
-    double t = 0.0;
-    for (int j = 0; j < (int)blockDim.x; j++) t += acc[k][j];
+    for (int j = lane; j < (int)gridDim.x; j += 32) t += ((volatile double*)R.part)[k * R.max_blocks + j];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     tot[k] = t;
   }
+  if (lane != 0) return false;
   *R.done = 0;
   return true;
 }
@@ -144,7 +143,7 @@ __device__ __forceinline__ double safe_div(double a, double b, double* brk) {
 //   MODE 1 (BiCGStab t = A s): (t, s), (t, t) -> omega = (t, s) / (t, t)
 //   MODE 2 (CG q = A p):       (p, q) -> alpha = rr / (p, q)
 template <typename X, typename V, int MODE>
-__global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(RTR) k_spmv_dot(int64_t n, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ col,
                                                  const V* __restrict__ val,
                                                  const uint8_t* __restrict__ free_,
@@ -181,7 +180,7 @@ __global__ void __launch_bounds__(RT) k_spmv_dot(int64_t n, const int64_t* __res
     }
   }
   double tot[2];
-  if (reduce_last<2>(R, d, tot)) {
+  if (reduce_last<2, RTR>(R, d, tot)) {
     double* S = R.S;
     if (MODE == 0) {
       S[S_ALPHA] = safe_div(S[S_RHO_NEW], tot[0], &S[S_BREAK]);
@@ -271,7 +270,7 @@ __global__ void __launch_bounds__(RT) k_cg_p(int64_t n, const X* __restrict__ r,
 }
 
 // r = b - A u (FP64) on free rows, its FP32 copy (optional) and (r, r)
-__global__ void __launch_bounds__(RT) k_residual(int64_t n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(RTR) k_residual(int64_t n, const int64_t* __restrict__ rp,
                                                  const int32_t* __restrict__ col,
                                                  const double* __restrict__ val,
                                                  const uint8_t* __restrict__ free_,
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(RT) k_residual(int64_t n, const int64_t* __res
     }
   }
   double tot[2];
-  if (reduce_last<2>(R, d, tot)) R.S[S_RR] = tot[0];
+  if (reduce_last<2, RTR>(R, d, tot)) R.S[S_RR] = tot[0];
 }
 
 // (a, a) of the right-hand side; initialises the scalar slots
@@ -336,9 +335,11 @@ struct Ctx {
   const int32_t* col;
   const uint8_t* free_;
   Red R;
-  int cap = 1216;  // 8 CTAs of 256 threads per SM: full occupancy for the row kernels
-  unsigned gvec() const { return (unsigned)std::min<int64_t>(cap, (n + RT - 1) / RT); }
-  unsigned grow() const { return (unsigned)std::min<int64_t>(cap, (n * 32 + RT - 1) / RT); }
+  // grids: one block per SM at most for the kernels with a reduction (their partial sums
+  // serialise on one atomic ticket); the row kernels use 1024-thread blocks (32 warps per SM)
+  int cap = 152;
+  unsigned gvec() const { return (unsigned)std::min<int64_t>(cap, (n + 4 * RT - 1) / (4 * RT)); }
+  unsigned grow() const { return (unsigned)std::min<int64_t>(cap, (n * 32 + RTR - 1) / RTR); }
 };
 
 nl_status read_scalars(Ctx& c, double* h) {
@@ -378,7 +379,7 @@ nl_status krylov(Ctx& c, const V* val, int solver, const X* b, X* x, double tol,
     while (k < max_it) {
       const int batch = std::min(CHECK, max_it - k);
       for (int j = 0; j < batch; j++) {
-        k_spmv_dot<X, V, 2><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p,
+        k_spmv_dot<X, V, 2><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p,
                                                                v.p, nullptr, c.R);
         k_cg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, p.p, v.p, r.p, c.R);
         k_cg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, p.p, c.R.S);
@@ -408,10 +409,10 @@ nl_status krylov(Ctx& c, const V* val, int solver, const X* b, X* x, double tol,
     const int batch = std::min(CHECK, max_it - k);
     for (int j = 0; j < batch; j++) {
       k_bicg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, v.p, p.p, c.R.S);
-      k_spmv_dot<X, V, 0><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p, v.p,
+      k_spmv_dot<X, V, 0><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p, v.p,
                                                              rh.p, c.R);
       k_bicg_s<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, v.p, sv.p, c.R.S);
-      k_spmv_dot<X, V, 1><<<NL_CNT(c.grow()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, sv.p, t.p,
+      k_spmv_dot<X, V, 1><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, sv.p, t.p,
                                                              nullptr, c.R);
       k_bicg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, p.p, sv.p, t.p, r.p, rh.p, c.R);
     }
@@ -478,6 +479,12 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
   c.rp = A->pairs->row_ptr;
   c.col = A->pairs->col;
   c.free_ = m->node_free;
+  {
+    int dev = 0, nsm = 0;
+    NL_CUDA(cudaGetDevice(&dev));
+    NL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    c.cap = std::max(1, nsm);
+  }
   const int max_blocks = (int)std::max<int64_t>(c.grow(), c.gvec());
   DevBuf<double> part, S, x;
   DevBuf<unsigned> done;
@@ -513,7 +520,7 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
     const double bb = h[S_BB];
     int total = 0;
     for (int outer = 0; outer < 60 && total < max_iter; outer++) {
-      k_residual<<<NL_CNT(c.grow()), RT, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v,
+      k_residual<<<NL_CNT(c.grow()), RTR, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v,
                                                  r64.p, r32.p, c.R);
       NL_TRY(read_scalars(c, h));
       rr = bb > 0.0 ? std::sqrt(h[S_RR] / bb) : 0.0;
@@ -532,7 +539,7 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
     }
     it = total;
     if (!ok) {
-      k_residual<<<NL_CNT(c.grow()), RT, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v,
+      k_residual<<<NL_CNT(c.grow()), RTR, 0, s>>>(c.n, c.rp, c.col, A->values, c.free_, x.p, rhs->v,
                                                  r64.p, nullptr, c.R);
       NL_TRY(read_scalars(c, h));
       rr = bb > 0.0 ? std::sqrt(h[S_RR] / bb) : 0.0;
