@@ -449,31 +449,71 @@ __device__ __forceinline__ void two_sum_add(double& hi, double& lo, double v) {
   (void)lo;
 }
 
-// Per-warp shared memory: stack records, two item buffers (SoA) and a small scratch.
+// A vertex in shared memory: D coordinates padded to 2 (2D) or 4 (3D) values, so that it is
+// read and written with one vector access (float2/float4; double2 or two double2).
+template <int D>
+struct VPad {
+  static constexpr int N = D == 2 ? 2 : 4;
+};
+template <int D, typename R>
+__device__ __forceinline__ void vload(const R* __restrict__ p, R (&v)[D]) {
+  if constexpr (std::is_same<R, float>::value) {
+    if constexpr (D == 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p);
+      v[0] = t.x;
+      v[1] = t.y;
+    } else {
+      const float4 t = *reinterpret_cast<const float4*>(p);
+      v[0] = t.x;
+      v[1] = t.y;
+      v[2] = t.z;
+    }
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    if constexpr (D == 3) v[2] = p[2];
+  }
+}
+template <int D, typename R>
+__device__ __forceinline__ void vstore(R* __restrict__ p, const R (&v)[D]) {
+  if constexpr (std::is_same<R, float>::value) {
+    if constexpr (D == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    else *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], 0.f);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    if constexpr (D == 3) p[2] = v[2];
+  }
+}
+
+// Per-warp shared memory: stack records, two item buffers and a small scratch.  Vertices are
+// stored padded (VPad) so that one vector access moves a vertex.
 template <int D, typename R>
 struct WarpMem {
-  R* rv;          // [NVC][scap]
-  uint32_t* rc;   // [scap]
-  R* iv;          // [2][NVC][IMAX]
+  R* rv;          // [NV][scap][PAD] stacked sub-element vertices
+  uint32_t* rc;   // [scap] path codes
+  R* iv;          // [2][NV][IMAX][PAD] buffered items (INT, FINAL)
   R* iw;          // [2][IMAX]
   R* red;         // 16 doubles of scratch (self-block sums)
   float* pf;      // [2][32]: FP32 element records of the current and the next pair
   static __host__ __device__ size_t bytes(int scap) {
     using G = Geo<D>;
-    size_t b = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
+    constexpr int PAD = VPad<D>::N;
+    size_t b = sizeof(R) * (size_t)G::NV * PAD * scap + sizeof(uint32_t) * scap;
     b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * ((size_t)2 * G::NVC * IMAX + 2 * IMAX) + sizeof(double) * 16 + sizeof(float) * 64;
+    b += sizeof(R) * ((size_t)2 * G::NV * IMAX * PAD + 2 * IMAX) + sizeof(double) * 16 + sizeof(float) * 64;
     b += 16;
     return (b + 15) & ~size_t(15);
   }
   __device__ void carve(char* base, int scap) {
     using G = Geo<D>;
+    constexpr int PAD = VPad<D>::N;
     rv = reinterpret_cast<R*>(base);
-    rc = reinterpret_cast<uint32_t*>(rv + (size_t)G::NVC * scap);
-    size_t off = sizeof(R) * (size_t)G::NVC * scap + sizeof(uint32_t) * scap;
+    rc = reinterpret_cast<uint32_t*>(rv + (size_t)G::NV * PAD * scap);
+    size_t off = sizeof(R) * (size_t)G::NV * PAD * scap + sizeof(uint32_t) * scap;
     off = (off + 15) & ~size_t(15);
     iv = reinterpret_cast<R*>(base + off);
-    iw = iv + (size_t)2 * G::NVC * IMAX;
+    iw = iv + (size_t)2 * G::NV * IMAX * PAD;
     red = iw + 2 * IMAX;  // 16-byte aligned: iv and iw hold multiples of 16 bytes
     pf = reinterpret_cast<float*>(reinterpret_cast<char*>(red) + sizeof(double) * 16);
   }
@@ -881,7 +921,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         const MollK MK{P.fhie, P.fnthie, P.fdie};
         const bool count_band = P.count_band != 0, gauss = is_gauss();
         const float inv_d2 = P.finv_delta2;
-        const R* iv = wm.iv + (size_t)kind * NVC * IMAX;
+        constexpr int PAD = VPad<D>::N;
+        const R* iv = wm.iv + (size_t)kind * NV * IMAX * PAD;
         const R* iw = wm.iw + kind * IMAX;
         const int n_x = n_it * NQ;
         st_eval += (unsigned)(n_x * NQ);
@@ -892,11 +933,14 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           const int q = valid ? o - it * NQ : 0;
           R x[D];
 #pragma unroll
-          for (int k = 0; k < D; k++) {
-            R s = 0;
+          for (int k = 0; k < D; k++) x[k] = 0;
 #pragma unroll
-            for (int a = 0; a < NV; a++) s += sB[q * NV + a] * iv[(a * D + k) * IMAX + it];
-            x[k] = s;
+          for (int a = 0; a < NV; a++) {
+            R va[D];
+            vload<D, R>(iv + ((size_t)a * IMAX + it) * PAD, va);
+            const R b = sB[q * NV + a];
+#pragma unroll
+            for (int k = 0; k < D; k++) x[k] += b * va[k];
           }
           const R wcx = valid ? sW[q] * iw[it] : (R)0;
           R lam[D];
@@ -981,9 +1025,10 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 
       // append an item to a buffer slot
       auto put_item = [&](int kind, int slot, const R (&V)[NV][D], int level) {
-        R* iv = wm.iv + (size_t)kind * NVC * IMAX;
+        constexpr int PAD = VPad<D>::N;
+        R* iv = wm.iv + (size_t)kind * NV * IMAX * PAD;
 #pragma unroll
-        for (int t = 0; t < NVC; t++) iv[t * IMAX + slot] = V[t / D][t % D];
+        for (int a = 0; a < NV; a++) vstore<D, R>(iv + ((size_t)a * IMAX + slot) * PAD, V[a]);
         wm.iw[kind * IMAX + slot] = wl * pow2m(R(0), D * (level - 1));
       };
 
@@ -1048,7 +1093,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           } else if (act == ACT_REFINE) {
             const int slot = base + __popc(m_ref & below);
 #pragma unroll
-            for (int t = 0; t < NVC; t++) wm.rv[t * P.scap + slot] = V[t / D][t % D];
+            for (int a = 0; a < NV; a++)
+              vstore<D, R>(wm.rv + ((size_t)a * P.scap + slot) * VPad<D>::N, V[a]);
             wm.rc[slot] = code;
           }
           sp = overflow ? base : base + nref;
@@ -1110,9 +1156,11 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
               for (int v = 0; v < NV; v++) {
                 int ia, ib;
                 mid_pair<D>(c, v, ia, ib);
+                R pa[D], pb[D];
+                vload<D, R>(wm.rv + ((size_t)ia * P.scap + slot) * VPad<D>::N, pa);
+                vload<D, R>(wm.rv + ((size_t)ib * P.scap + slot) * VPad<D>::N, pb);
 #pragma unroll
-                for (int k = 0; k < D; k++)
-                  V[v][k] = midp(wm.rv[(ia * D + k) * P.scap + slot], wm.rv[(ib * D + k) * P.scap + slot]);
+                for (int k = 0; k < D; k++) V[v][k] = midp(pa[k], pb[k]);
               }
               code = (((uint32_t)(plevel + 1)) << LEVEL_SHIFT) | (pcode & ((1u << LEVEL_SHIFT) - 1)) |
                      ((uint32_t)c << (G::BITS * (plevel - 1)));
