@@ -557,7 +557,12 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
-        out = run_ours(args, rank, world, local)
+        import torch
+        torch.cuda.set_device(local)
+        # all work on one non-default stream (the library captures its Krylov batches into
+        # CUDA graphs on streams that can be captured)
+        with torch.cuda.stream(torch.cuda.Stream()):
+            out = run_ours(args, rank, world, local)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if world > 1:

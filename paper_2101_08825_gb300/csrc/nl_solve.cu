@@ -348,18 +348,95 @@ nl_status read_scalars(Ctx& c, double* h) {
   return NL_OK;
 }
 
+// Krylov vectors of one solve (allocated once, so that every Krylov call of an iterative
+// refinement uses the same pointers) and the CUDA graph of one batch of CHECK iterations,
+// captured at the first full batch and replayed for every later one.  Graphs are used only
+// on a stream that can be captured (not the legacy default stream).
+template <typename X>
+struct KWork {
+  DevBuf<X> r, rh, p, v, sv, t;
+  cudaGraphExec_t exec = nullptr;
+  int exec_solver = -1;
+  bool use_graph = false;
+  ~KWork() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  nl_status alloc(int64_t n, cudaStream_t s) {
+    NL_TRY(r.alloc(n, s));
+    NL_TRY(rh.alloc(n, s));
+    NL_TRY(p.alloc(n, s));
+    NL_TRY(v.alloc(n, s));
+    NL_TRY(sv.alloc(n, s));
+    NL_TRY(t.alloc(n, s));
+    return NL_OK;
+  }
+};
+
+// One iteration of CG (solver 0) or BiCGStab (solver 1).
+template <typename X, typename V>
+void krylov_iteration(Ctx& c, const V* val, int solver, X* x, KWork<X>& W) {
+  const int64_t n = c.n;
+  if (solver == 0) {
+    k_spmv_dot<X, V, 2><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.p.p,
+                                                            W.v.p, nullptr, c.R);
+    k_cg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, W.p.p, W.v.p, W.r.p, c.R);
+    k_cg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.r.p, W.p.p, c.R.S);
+  } else {
+    k_bicg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.r.p, W.v.p, W.p.p, c.R.S);
+    k_spmv_dot<X, V, 0><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.p.p,
+                                                            W.v.p, W.rh.p, c.R);
+    k_bicg_s<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.r.p, W.v.p, W.sv.p, c.R.S);
+    k_spmv_dot<X, V, 1><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.sv.p,
+                                                            W.t.p, nullptr, c.R);
+    k_bicg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, W.p.p, W.sv.p, W.t.p, W.r.p, W.rh.p, c.R);
+  }
+}
+
+// A batch of `batch` iterations: replayed from the captured graph when it is a full batch and
+// graphs are in use, launched kernel by kernel otherwise.
+template <typename X, typename V>
+nl_status krylov_batch(Ctx& c, const V* val, int solver, X* x, KWork<X>& W, int batch) {
+  if (W.use_graph && batch == CHECK) {
+    if (!W.exec || W.exec_solver != solver) {
+      if (W.exec) {
+        cudaGraphExecDestroy(W.exec);
+        W.exec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c.s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int j = 0; j < CHECK; j++) krylov_iteration<X, V>(c, val, solver, x, W);
+        e = cudaStreamEndCapture(c.s, &g);
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&W.exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {  // run without graphs from here on
+        cudaGetLastError();
+        W.exec = nullptr;
+        W.use_graph = false;
+      } else {
+        W.exec_solver = solver;
+      }
+    }
+    if (W.exec) {
+      NL_CUDA(cudaGraphLaunch(W.exec, c.s));
+      for (int j = 0; j < CHECK * (solver == 0 ? 3 : 5); j++) count_launch();
+      return NL_OK;
+    }
+  }
+  for (int j = 0; j < batch; j++) krylov_iteration<X, V>(c, val, solver, x, W);
+  NL_CUDA(cudaGetLastError());
+  return NL_OK;
+}
+
 // Krylov solve of A x = b (x starts at 0) to ||b - A x|| <= tol ||b||.  X = double or float
 // (vectors), V = matrix value type.  *it = iterations, *ok when converged.
 template <typename X, typename V>
 nl_status krylov(Ctx& c, const V* val, int solver, const X* b, X* x, double tol, int max_it, int* it,
-                 bool* ok, double* relres) {
+                 bool* ok, double* relres, KWork<X>& W) {
   const int64_t n = c.n;
-  DevBuf<X> r, rh, p, v, sv, t;
-  NL_TRY(r.alloc(n, c.s));
-  NL_TRY(p.alloc(n, c.s));
-  NL_TRY(v.alloc(n, c.s));
   NL_CUDA(cudaMemsetAsync(x, 0, sizeof(X) * n, c.s));
-  NL_CUDA(cudaMemcpyAsync(r.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
+  NL_CUDA(cudaMemcpyAsync(W.r.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
   k_init_dot<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, b, c.R);
   NL_CUDA(cudaGetLastError());
   double h[S_NSLOTS];
@@ -374,49 +451,16 @@ nl_status krylov(Ctx& c, const V* val, int solver, const X* b, X* x, double tol,
   }
   const double stop2 = tol * tol * bb;
   if (solver == 0) {  // CG: p = r = b
-    NL_CUDA(cudaMemcpyAsync(p.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
-    int k = 0;
-    while (k < max_it) {
-      const int batch = std::min(CHECK, max_it - k);
-      for (int j = 0; j < batch; j++) {
-        k_spmv_dot<X, V, 2><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p,
-                                                               v.p, nullptr, c.R);
-        k_cg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, p.p, v.p, r.p, c.R);
-        k_cg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, p.p, c.R.S);
-      }
-      NL_CUDA(cudaGetLastError());
-      k += batch;
-      NL_TRY(read_scalars(c, h));
-      *it = k;
-      *relres = std::sqrt(std::max(h[S_RR], 0.0) / bb);
-      if (h[S_RR] <= stop2) {
-        *ok = true;
-        break;
-      }
-      if (h[S_BREAK] != 0.0 || !std::isfinite(h[S_RR])) break;
-    }
-    return NL_OK;
+    NL_CUDA(cudaMemcpyAsync(W.p.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
+  } else {  // BiCGStab (van der Vorst): r^ = b, p = v = 0, rho_new = (r^, r)
+    NL_CUDA(cudaMemcpyAsync(W.rh.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
+    NL_CUDA(cudaMemsetAsync(W.p.p, 0, sizeof(X) * n, c.s));
+    NL_CUDA(cudaMemsetAsync(W.v.p, 0, sizeof(X) * n, c.s));
   }
-  // BiCGStab (van der Vorst): r^ = b, p = v = 0, rho_new = (r^, r)
-  NL_TRY(rh.alloc(n, c.s));
-  NL_TRY(sv.alloc(n, c.s));
-  NL_TRY(t.alloc(n, c.s));
-  NL_CUDA(cudaMemcpyAsync(rh.p, b, sizeof(X) * n, cudaMemcpyDeviceToDevice, c.s));
-  NL_CUDA(cudaMemsetAsync(p.p, 0, sizeof(X) * n, c.s));
-  NL_CUDA(cudaMemsetAsync(v.p, 0, sizeof(X) * n, c.s));
   int k = 0;
   while (k < max_it) {
     const int batch = std::min(CHECK, max_it - k);
-    for (int j = 0; j < batch; j++) {
-      k_bicg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, v.p, p.p, c.R.S);
-      k_spmv_dot<X, V, 0><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, p.p, v.p,
-                                                             rh.p, c.R);
-      k_bicg_s<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, r.p, v.p, sv.p, c.R.S);
-      k_spmv_dot<X, V, 1><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, sv.p, t.p,
-                                                             nullptr, c.R);
-      k_bicg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, p.p, sv.p, t.p, r.p, rh.p, c.R);
-    }
-    NL_CUDA(cudaGetLastError());
+    NL_TRY((krylov_batch<X, V>(c, val, solver, x, W, batch)));
     k += batch;
     NL_TRY(read_scalars(c, h));
     *it = k;
@@ -501,8 +545,12 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
   int it = 0;
   bool ok = false;
   double rr = 0.0;
+  const bool graphs = s != nullptr;  // the legacy default stream cannot be captured
   if (prec == NL_PREC_FP64) {
-    NL_TRY((krylov<double, double>(c, A->values, solver, rhs->v, x.p, rtol, max_iter, &it, &ok, &rr)));
+    KWork<double> W;
+    NL_TRY(W.alloc(c.n, s));
+    W.use_graph = graphs;
+    NL_TRY((krylov<double, double>(c, A->values, solver, rhs->v, x.p, rtol, max_iter, &it, &ok, &rr, W)));
   } else {
     // FP32 Krylov inside FP64 iterative refinement: r = F~ - A u in FP64, A d = r in FP32
     DevBuf<float> a32, r32, d32;
@@ -511,6 +559,9 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
     NL_TRY(r32.alloc(c.n, s));
     NL_TRY(d32.alloc(c.n, s));
     NL_TRY(r64.alloc(c.n, s));
+    KWork<float> W;
+    NL_TRY(W.alloc(c.n, s));
+    W.use_graph = graphs;
     k_f64_to_f32<<<NL_CNT((unsigned)((A->pairs->nnz + RT - 1) / RT + 1)), RT, 0, s>>>(
         A->pairs->nnz, A->values, a32.p);
     NL_CUDA(cudaMemsetAsync(x.p, 0, sizeof(double) * c.n, s));
@@ -532,7 +583,7 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
       bool iok = false;
       double irr = 0.0;
       NL_TRY((krylov<float, float>(c, a32.p, solver, r32.p, d32.p, 1e-5, max_iter - total, &inner,
-                                   &iok, &irr)));
+                                   &iok, &irr, W)));
       total += inner;
       k_add_f32_to_f64<<<NL_CNT(c.gvec()), RT, 0, s>>>(c.n, d32.p, x.p);
       if (inner == 0) break;
