@@ -916,6 +916,102 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         st_closed++;
       };
 
+      // A FINAL sub-element E' (L_max reached, the band in reach of the box of m) whose every
+      // point lies, for each inner point y of m, either closer than delta - eps - margin or
+      // farther than delta + eps + margin (ball around the centroid c of radius
+      // R = max |v - c|: |x - y| <= |c - y| + R and >= |c - y| - R) has mu exactly 1 or 0 at
+      // each of its point pairs; with the constant kernel its outer sum for an inner point with
+      // mu = 1 is C |E'| [1, lambda^l(c)] (degree-5 rule, linear integrand), added to that
+      // inner point only.  Returns false (nothing added) unless every inner point is decided.
+      // 2D: every lane holds all inner points of m.
+      auto closed_set = [&](const R (&V)[NV][D], int level) -> bool {
+        if (D != 2) return false;
+        R cen[D];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          R t = 0;
+#pragma unroll
+          for (int a = 0; a < NV; a++) t += V[a][k];
+          cen[k] = t * (R)(1.0 / NV);
+        }
+        R rad2 = 0;
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+          R d2 = 0;
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            const R d = V[a][k] - cen[k];
+            d2 += d * d;
+          }
+          rad2 = rad2 > d2 ? rad2 : d2;
+        }
+        const R rad = sqrt(rad2);
+        const R lo = (R)P.fdme - rad - (R)P.margin, hi = (R)P.fdpe + rad + (R)P.margin;
+        const R lo2 = lo > 0 ? lo * lo : (R)-1, hi2 = hi * hi;
+        unsigned in_mask = 0;
+        bool decided = true;
+#pragma unroll
+        for (int i = 0; i < NYL; i++) {
+          R yi[D];
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            if constexpr (F32) {
+              if (i < 6) {
+                float a, b;
+                f2unpack(yq[i / 2][k], a, b);
+                yi[k] = (i & 1) ? b : a;
+              } else {
+                yi[k] = y[6][k];
+              }
+            } else {
+              yi[k] = y[i][k];
+            }
+          }
+          R d2 = 0;
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            const R d = cen[k] - yi[k];
+            d2 += d * d;
+          }
+          const bool in = d2 < lo2, out = d2 > hi2;
+          in_mask |= in ? (1u << i) : 0u;
+          decided = decided && (in || out);
+        }
+        if (!decided) return false;
+        const R wv = wl * pow2m(R(0), D * (level - 1));
+        R lc[D];  // lambda^l(c)
+#pragma unroll
+        for (int r = 0; r < D; r++) {
+          R t = 0;
+#pragma unroll
+          for (int c = 0; c < D; c++) t += Ji[r][c] * (cen[c] - Vl[0][c]);
+          lc[r] = t;
+        }
+        if constexpr (F32) {
+#pragma unroll
+          for (int j = 0; j < 3; j++) {
+            const f2 w2 = f2pack((in_mask >> (2 * j)) & 1u ? wv : 0.f, (in_mask >> (2 * j + 1)) & 1u ? wv : 0.f);
+            gq[j] = f2add(gq[j], w2);
+#pragma unroll
+            for (int k = 0; k < D; k++) hq[k][j] = f2fma(w2, f2dup(lc[k]), hq[k][j]);
+          }
+          const R w6 = (in_mask >> 6) & 1u ? wv : (R)0;
+          gp[6] += w6;
+#pragma unroll
+          for (int k = 0; k < D; k++) hp[k][6] += w6 * lc[k];
+        } else {
+#pragma unroll
+          for (int i = 0; i < NYL; i++) {
+            const R wi = (in_mask >> i) & 1u ? wv : (R)0;
+            gp[i] += wi;
+#pragma unroll
+            for (int k = 0; k < D; k++) hp[k][i] += wi * lc[k];
+          }
+        }
+        st_closed++;
+        return true;
+      };
+
       // integrate the buffered items of one kind (warp-collective)
       auto integrate = [&](int kind, int n_it) {
         const MollK MK{P.fhie, P.fnthie, P.fdie};
@@ -1077,6 +1173,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             closed_int(V, level);
             act = ACT_DROP;
           }
+          if (is_const() && act == ACT_FINAL && closed_set(V, level)) act = ACT_DROP;
           const unsigned m_int = __ballot_sync(0xffffffffu, act == ACT_INT);
           const unsigned m_fin = __ballot_sync(0xffffffffu, act == ACT_FINAL);
           const unsigned m_ref = __ballot_sync(0xffffffffu, act == ACT_REFINE);
