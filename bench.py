@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed FP64 steps beside the mixed ones (0 = leave the FP64 path out)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
@@ -51,8 +52,12 @@ def parse():
     ap.add_argument("--batch-problems", type=int, default=128,
                     help="small problems of the batching leg (0 = skip)")
     ap.add_argument("--profile", action="store_true",
-                    help="one pair build and one FP32 and one FP64 assembly of the 2D workload "
-                         "at h=1/128 (a small case for ncu), then exit")
+                    help="one pair build and one FP32 and one FP64 assembly of a small workload "
+                         "(--profile-workload, default the 2D workload at h=1/128) for ncu, "
+                         "then exit")
+    ap.add_argument("--profile-workload", default="c2_2d_h128")
+    ap.add_argument("--profile-fp64", type=int, default=1,
+                    help="with --profile: also run the FP64 assembly (0 = FP32 only)")
     return ap.parse_args()
 
 
@@ -260,15 +265,20 @@ def run_ours(args, rank, world, local):
     value = world * n_pairs / (ms_max / 1e3)
     err_mixed = l2_err_omega(mesh, last["u"], rule)
 
-    # FP64 path, same step
-    t64, s64, k64, last64, _ = timed(nl.NL_PREC_FP64, max(1, args.fp64_steps), 1)
-    ms64 = statistics.mean(t64)
-    err64 = l2_err_omega(mesh, last64["u"], rule)
-
-    # matrix difference mixed vs FP64 (one extra untimed assembly each)
-    r32 = step(nl.NL_PREC_FP32, keep=True)["A"]
-    r64 = step(nl.NL_PREC_FP64, keep=True)["A"]
-    a_rel = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
+    # FP64 path, same step (--fp64-steps 0 leaves it out, e.g. for the 3D h = 1/32 workload,
+    # whose FP64 assembly takes minutes)
+    fp64 = None
+    if args.fp64_steps > 0:
+        t64, s64, k64, last64, _ = timed(nl.NL_PREC_FP64, args.fp64_steps, 1)
+        ms64 = statistics.mean(t64)
+        err64 = l2_err_omega(mesh, last64["u"], rule)
+        # matrix difference mixed vs FP64 (one extra untimed assembly each)
+        r32 = step(nl.NL_PREC_FP32, keep=True)["A"]
+        r64 = step(nl.NL_PREC_FP64, keep=True)["A"]
+        a_rel = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
+        fp64 = {"dtype": "f64", "ms_per_step": round(ms64, 3),
+                "value": round(world * n_pairs / (ms64 / 1e3), 1),
+                "assembly_kernel_ms": round(statistics.mean(k64), 3), "l2_err_omega": err64}
 
     # roofline of the dominant kernel (FP32 assembly kernel): algorithmic flops per launch;
     # the band count comes from one extra untimed launch with NL_QUAD_COUNT_BAND
@@ -301,12 +311,11 @@ def run_ours(args, rank, world, local):
                    "evaluated_point_pairs": stb.n_eval_point_pairs,
                    "band_point_pairs": stb.n_band_point_pairs,
                    "closed_form_items": stb.n_closed_items},
-        "fp64": {"dtype": "f64", "ms_per_step": round(ms64, 3),
-                 "value": round(world * n_pairs / (ms64 / 1e3), 1),
-                 "assembly_kernel_ms": round(statistics.mean(k64), 3),
-                 "l2_err_omega": err64},
-        "mixed": {"l2_err_omega": err_mixed, "A_rel_frobenius_vs_fp64": a_rel,
-                  "solve_iters": last["it"], "speedup_vs_fp64": round(ms64 / ms, 2)},
+        "fp64": fp64,
+        "mixed": {"l2_err_omega": err_mixed,
+                  "A_rel_frobenius_vs_fp64": a_rel if fp64 else None,
+                  "solve_iters": last["it"],
+                  "speedup_vs_fp64": round(ms64 / ms, 2) if fp64 else None},
         "solve_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
                      "p99": round(float(np.percentile(solve_ms, 99)), 3)},
         "roofline": roof,
@@ -533,16 +542,17 @@ def run_reference(args, rank, world):
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_profile_case():
+def run_profile_case(args):
     import torch
     from paper_2101_08825_gb300 import nl
     from paper_2101_08825_gb300.build import build
     build()
-    w, mesh = workload("c2_2d_h128")
+    w, mesh = workload(args.profile_workload)
     m = nl.mesh_from(mesh)
     p = nl.nl_pairs_build(m, w.delta, w.eps)
-    for prec in (nl.NL_PREC_FP32, nl.NL_PREC_FP64):
-        A, st = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, precision=prec)
+    precs = (nl.NL_PREC_FP32, nl.NL_PREC_FP64) if args.profile_fp64 else (nl.NL_PREC_FP32,)
+    for prec in precs:
+        A, st = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec)
         print(json.dumps({"profile_case": w.name, "precision": prec, "pairs": st.n_pairs,
                           "point_pairs": st.n_point_pairs, "kernel_ms": st.ms_assemble}))
     torch.cuda.synchronize()
@@ -551,7 +561,7 @@ def run_profile_case():
 def main():
     args = parse()
     if args.profile:
-        run_profile_case()
+        run_profile_case(args)
         return
     rank, world, local = dist_init(args)
     if args.impl == "reference":

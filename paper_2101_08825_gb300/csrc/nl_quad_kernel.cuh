@@ -716,6 +716,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       }
       m = lo;
     }
+    int64_t m_end = P.pair_off[m + 1];  // end of m's pairs, reloaded only when m advances
     int32_t l_lane = 0;  // pair_l of the pair p0 + 32 * (block) + lane
     for (int64_t p = p0; p < p1; p++) {
       const int jj = (int)(p - p0);
@@ -738,7 +739,10 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           cp_async16(wm.pf + ((jj + 1) & 1) * 32 + lane * 4, P.ef + (int64_t)ln * G::EFS + lane * 4);
         cp_async_commit();
       }
-      while (p >= P.pair_off[m + 1]) m++;
+      while (p >= m_end) {
+        m++;
+        m_end = P.pair_off[m + 1];
+      }
       if (m != cur_m) {
         if (cur_m >= 0) flush_self();
         cur_m = m;
