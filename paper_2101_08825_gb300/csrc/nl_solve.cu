@@ -138,24 +138,20 @@ __device__ __forceinline__ double safe_div(double a, double b, double* brk) {
   return a / b;
 }
 
-// y = A x on free rows (0 elsewhere), warp per row, with the dot products of the iteration:
-//   MODE 0 (BiCGStab v = A p): (r^, v) -> alpha = rho_new / (r^, v), rho_old = rho_new
-//   MODE 1 (BiCGStab t = A s): (t, s), (t, t) -> omega = (t, s) / (t, t)
-//   MODE 2 (CG q = A p):       (p, q) -> alpha = rr / (p, q)
-template <typename X, typename V, int MODE>
-__global__ void __launch_bounds__(RTR) k_spmv_dot(int64_t n, const int64_t* __restrict__ rp,
-                                                 const int32_t* __restrict__ col,
-                                                 const V* __restrict__ val,
-                                                 const uint8_t* __restrict__ free_,
-                                                 const X* __restrict__ x, X* __restrict__ y,
-                                                 const X* __restrict__ w1, Red R) {
+// y = A x on free rows (0 elsewhere), warp per row, grid-stride over the rows; four
+// independent partial sums keep four loads of x in flight per lane.  No reduction here, so the
+// grid can fill every SM; the dot products follow in k_spmv_dots.
+template <typename X, typename V>
+__global__ void __launch_bounds__(RT) k_spmv(int64_t n, const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ col,
+                                             const V* __restrict__ val,
+                                             const uint8_t* __restrict__ free_,
+                                             const X* __restrict__ x, X* __restrict__ y) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double d[2] = {0.0, 0.0};
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
     X s = 0;
     if (free_[i]) {
-      // four independent partial sums keep four loads of x in flight per lane
       const int64_t e = rp[i + 1];
       int64_t t = rp[i] + lane;
       X s1 = 0, s2 = 0, s3 = 0;
@@ -169,18 +165,31 @@ __global__ void __launch_bounds__(RTR) k_spmv_dot(int64_t n, const int64_t* __re
       s = (s + s1) + (s2 + s3);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      y[i] = s;
-      if (MODE == 0) d[0] += (double)w1[i] * (double)s;
-      if (MODE == 1) {
-        d[0] += (double)s * (double)x[i];
-        d[1] += (double)s * (double)s;
-      }
-      if (MODE == 2) d[0] += (double)x[i] * (double)s;
+    if (lane == 0) y[i] = s;
+  }
+}
+
+// The dot products that follow y = A x, and the scalar they determine:
+//   MODE 0 (BiCGStab v = A p): (r^, v) -> alpha = rho_new / (r^, v), rho_old = rho_new
+//   MODE 1 (BiCGStab t = A s): (t, s), (t, t) -> omega = (t, s) / (t, t)
+//   MODE 2 (CG q = A p):       (p, q) -> alpha = rr / (p, q)
+template <typename X, int MODE>
+__global__ void __launch_bounds__(RT) k_spmv_dots(int64_t n, const X* __restrict__ x,
+                                                  const X* __restrict__ y,
+                                                  const X* __restrict__ w1, Red R) {
+  double d[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = (double)y[i];
+    if (MODE == 0) d[0] += (double)w1[i] * s;
+    if (MODE == 1) {
+      d[0] += s * (double)x[i];
+      d[1] += s * s;
     }
+    if (MODE == 2) d[0] += (double)x[i] * s;
   }
   double tot[2];
-  if (reduce_last<2, RTR>(R, d, tot)) {
+  if (reduce_last<2>(R, d, tot)) {
     double* S = R.S;
     if (MODE == 0) {
       S[S_ALPHA] = safe_div(S[S_RHO_NEW], tot[0], &S[S_BREAK]);
@@ -340,6 +349,8 @@ struct Ctx {
   int cap = 152;
   unsigned gvec() const { return (unsigned)std::min<int64_t>(cap, (n + 4 * RT - 1) / (4 * RT)); }
   unsigned grow() const { return (unsigned)std::min<int64_t>(cap, (n * 32 + RTR - 1) / RTR); }
+  // SpMV without a reduction: up to 8 blocks of 256 threads per SM
+  unsigned gspmv() const { return (unsigned)std::min<int64_t>(8 * cap, (n * 32 + RT - 1) / RT); }
 };
 
 nl_status read_scalars(Ctx& c, double* h) {
@@ -377,17 +388,17 @@ template <typename X, typename V>
 void krylov_iteration(Ctx& c, const V* val, int solver, X* x, KWork<X>& W) {
   const int64_t n = c.n;
   if (solver == 0) {
-    k_spmv_dot<X, V, 2><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.p.p,
-                                                            W.v.p, nullptr, c.R);
+    k_spmv<X, V><<<NL_CNT(c.gspmv()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.p.p, W.v.p);
+    k_spmv_dots<X, 2><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.p.p, W.v.p, nullptr, c.R);
     k_cg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, W.p.p, W.v.p, W.r.p, c.R);
     k_cg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.r.p, W.p.p, c.R.S);
   } else {
     k_bicg_p<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.r.p, W.v.p, W.p.p, c.R.S);
-    k_spmv_dot<X, V, 0><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.p.p,
-                                                            W.v.p, W.rh.p, c.R);
+    k_spmv<X, V><<<NL_CNT(c.gspmv()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.p.p, W.v.p);
+    k_spmv_dots<X, 0><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.p.p, W.v.p, W.rh.p, c.R);
     k_bicg_s<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.r.p, W.v.p, W.sv.p, c.R.S);
-    k_spmv_dot<X, V, 1><<<NL_CNT(c.grow()), RTR, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.sv.p,
-                                                            W.t.p, nullptr, c.R);
+    k_spmv<X, V><<<NL_CNT(c.gspmv()), RT, 0, c.s>>>(n, c.rp, c.col, val, c.free_, W.sv.p, W.t.p);
+    k_spmv_dots<X, 1><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, W.sv.p, W.t.p, nullptr, c.R);
     k_bicg_xr<X><<<NL_CNT(c.gvec()), RT, 0, c.s>>>(n, x, W.p.p, W.sv.p, W.t.p, W.r.p, W.rh.p, c.R);
   }
 }
@@ -420,7 +431,7 @@ nl_status krylov_batch(Ctx& c, const V* val, int solver, X* x, KWork<X>& W, int 
     }
     if (W.exec) {
       NL_CUDA(cudaGraphLaunch(W.exec, c.s));
-      for (int j = 0; j < CHECK * (solver == 0 ? 3 : 5); j++) count_launch();
+      for (int j = 0; j < CHECK * (solver == 0 ? 4 : 7); j++) count_launch();
       return NL_OK;
     }
   }
