@@ -496,12 +496,14 @@ struct WarpMem {
   R* iw;          // [2][IMAX]
   R* red;         // 16 doubles of scratch (self-block sums)
   float* pf;      // [2][32]: FP32 element records of the current and the next pair
+  R* pc;          // [8]: box of the current inner element m (lo, hi)
   static __host__ __device__ size_t bytes(int scap) {
     using G = Geo<D>;
     constexpr int PAD = VPad<D>::N;
     size_t b = sizeof(R) * (size_t)G::NV * PAD * scap + sizeof(uint32_t) * scap;
     b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * ((size_t)2 * G::NV * IMAX * PAD + 2 * IMAX) + sizeof(double) * 16 + sizeof(float) * 64;
+    b += sizeof(R) * ((size_t)2 * G::NV * IMAX * PAD + 2 * IMAX) + sizeof(double) * 16 + sizeof(float) * 64 +
+         sizeof(R) * 8;
     b += 16;
     return (b + 15) & ~size_t(15);
   }
@@ -516,6 +518,7 @@ struct WarpMem {
     iw = iv + (size_t)2 * G::NV * IMAX * PAD;
     red = iw + 2 * IMAX;  // 16-byte aligned: iv and iw hold multiples of 16 bytes
     pf = reinterpret_cast<float*>(reinterpret_cast<char*>(red) + sizeof(double) * 16);
+    pc = reinterpret_cast<R*>(pf + 64);
   }
 };
 
@@ -604,7 +607,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
   // state of the current inner element m
   int64_t cur_m = -1;
   float v0h[D], v0l[D];  // R = float: first vertex of m (origin of the local coordinates), hi + lo
-  R lo_m[D], hi_m[D]; // box of m (local FP32 coordinates, or global FP64)
+
   R y[NYL][D];        // inner points of m (local if R = float)
   f2 yq[3][D];        // R = float: inner points 0-5 of the lane packed in pairs
   R vol_m = 0;
@@ -776,9 +779,12 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             lo = Vm[a][k] < lo ? Vm[a][k] : lo;
             hi = Vm[a][k] > hi ? Vm[a][k] : hi;
           }
-          lo_m[k] = lo;
-          hi_m[k] = hi;
+          if (lane == 0) {  // box of m (local FP32 coordinates, or global FP64)
+            wm.pc[k] = lo;
+            wm.pc[D + k] = hi;
+          }
         }
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < NYL; i++) {
           int q = ybase + i;
@@ -798,18 +804,17 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         }
       }
       // ---- per-pair set-up ------------------------------------------------------------------
-      R Vl[NV][D], Ji[D][D], wl;
+      // Only the first vertex of E_l stays in registers; the whole simplex is rebuilt when the
+      // traversal needs it (FP32: from this pair's record in shared memory, which stays until the
+      // next pair; FP64: from the element arrays).
+      R Vl0[D], Ji[D][D], wl;
       if constexpr (F32) {
         cp_async_wait_prior();
         __syncwarp();
         const float* ef = wm.pf + (jj & 1) * 32;
 #pragma unroll
         for (int k = 0; k < D; k++)  // v_0(l) - v_0(m) from the float-float pairs, ~1 ulp
-          Vl[0][k] = (R)((ef[NL_EF_V0HI(D) + k] - v0h[k]) + (ef[NL_EF_V0LO(D) + k] - v0l[k]));
-#pragma unroll
-        for (int a = 1; a < NV; a++)
-#pragma unroll
-          for (int k = 0; k < D; k++) Vl[a][k] = Vl[0][k] + (R)ef[(a - 1) * D + k];
+          Vl0[k] = (R)((ef[NL_EF_V0HI(D) + k] - v0h[k]) + (ef[NL_EF_V0LO(D) + k] - v0l[k]));
 #pragma unroll
         for (int r = 0; r < D; r++)
 #pragma unroll
@@ -817,15 +822,29 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         wl = (R)P.fC * (R)ef[2 * D * D];
       } else {
 #pragma unroll
-        for (int a = 0; a < NV; a++)
-#pragma unroll
-          for (int k = 0; k < D; k++) Vl[a][k] = (R)P.evert[((int64_t)l * NV + a) * D + k];
+        for (int k = 0; k < D; k++) Vl0[k] = (R)P.evert[(int64_t)l * NVC + k];
 #pragma unroll
         for (int r = 0; r < D; r++)
 #pragma unroll
           for (int c = 0; c < D; c++) Ji[r][c] = (R)P.jinv[((int64_t)l * D + r) * D + c];
         wl = (R)(P.C * P.vol[l]);
       }
+      auto get_Vl = [&](R (&V)[NV][D]) {
+        if constexpr (F32) {
+          const float* ef = wm.pf + (jj & 1) * 32;
+#pragma unroll
+          for (int k = 0; k < D; k++) V[0][k] = Vl0[k];
+#pragma unroll
+          for (int a = 1; a < NV; a++)
+#pragma unroll
+            for (int k = 0; k < D; k++) V[a][k] = Vl0[k] + (R)ef[(a - 1) * D + k];
+        } else {
+#pragma unroll
+          for (int a = 0; a < NV; a++)
+#pragma unroll
+            for (int k = 0; k < D; k++) V[a][k] = (R)P.evert[((int64_t)l * NV + a) * D + k];
+        }
+      };
 
       R gp[NYL], hp[D][NYL], ug = 0, uh[D];
       f2 gq[3], hq[D][3];  // R = float: accumulators of inner points 0-5 in pairs
@@ -861,8 +880,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           float flo[D], fhi[D];
 #pragma unroll
           for (int k = 0; k < D; k++) {
-            flo[k] = (float)lo_m[k];
-            fhi[k] = (float)hi_m[k];
+            flo[k] = (float)wm.pc[k];
+            fhi[k] = (float)wm.pc[D + k];
           }
           screen_dists<D>(Vf, flo, fhi, fam, fan);  // fam = squared aprx-max-dist
           const bool c_int = fam < P.fint2;
@@ -884,8 +903,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             for (int k = 0; k < D; k++) Vd[a][k] = (double)V[a][k];
 #pragma unroll
           for (int k = 0; k < D; k++) {
-            lo2[k] = (double)lo_m[k];
-            hi2[k] = (double)hi_m[k];
+            lo2[k] = (double)wm.pc[k];
+            hi2[k] = (double)wm.pc[D + k];
           }
           double amax, amin;
           exact_dists<D>(Vd, lo2, hi2, amax, amin);
@@ -914,7 +933,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         for (int r = 0; r < D; r++) {
           R s = 0;
 #pragma unroll
-          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - Vl[0][c]);
+          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - Vl0[c]);
           uh[r] += wv * s;
         }
         st_closed++;
@@ -988,7 +1007,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         for (int r = 0; r < D; r++) {
           R t = 0;
 #pragma unroll
-          for (int c = 0; c < D; c++) t += Ji[r][c] * (cen[c] - Vl[0][c]);
+          for (int c = 0; c < D; c++) t += Ji[r][c] * (cen[c] - Vl0[c]);
           lc[r] = t;
         }
         if constexpr (F32) {
@@ -1048,7 +1067,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           for (int r = 0; r < D; r++) {
             R s = 0;
 #pragma unroll
-            for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - Vl[0][c]);
+            for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - Vl0[c]);
             lam[r] = s;
           }
           if constexpr (F32) {
@@ -1141,13 +1160,20 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       {
         int sp = 0, n_int = 0, n_fin = 0;
         const uint32_t code0 = 1u << LEVEL_SHIFT;
-        const int act0 = classify(Vl, code0, lane == 0);
+        int act0;
+        {
+          R Vl[NV][D];
+          get_Vl(Vl);
+          act0 = classify(Vl, code0, lane == 0);
+          if (is_const() && act0 == ACT_INT) {
+            if (lane == 0) closed_int(Vl, 1);
+          } else if (act0 == ACT_INT || act0 == ACT_FINAL) {
+            if (lane == 0) put_item(act0 == ACT_INT ? KIND_INT : KIND_FINAL, 0, Vl, 1);
+          }
+        }
         if (act0 == ACT_INT || act0 == ACT_FINAL || act0 == ACT_ZERO) st_items += (lane == 0);
         bool from_root = act0 == ACT_REFINE;
-        if (is_const() && act0 == ACT_INT) {
-          if (lane == 0) closed_int(Vl, 1);
-        } else if (act0 == ACT_INT || act0 == ACT_FINAL) {
-          if (lane == 0) put_item(act0 == ACT_INT ? KIND_INT : KIND_FINAL, 0, Vl, 1);
+        if (!(is_const() && act0 == ACT_INT) && (act0 == ACT_INT || act0 == ACT_FINAL)) {
           if (act0 == ACT_INT) n_int = 1;
           else n_fin = 1;
         }
@@ -1210,7 +1236,11 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           int act = ACT_DROP;
           if (lane < 16) {
             R C[NV][D];
-            child_of(Vl, c2, C);
+            {
+              R Vl[NV][D];
+              get_Vl(Vl);
+              child_of(Vl, c2, C);
+            }
             const uint32_t codeC = (2u << LEVEL_SHIFT) | (uint32_t)c2;
             const int actC = classify(C, codeC, c3 == 0);
             if (actC == ACT_REFINE) {
@@ -1247,6 +1277,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           int act = ACT_DROP;
           if (active) {
             if (from_root) {
+              R Vl[NV][D];
+              get_Vl(Vl);
               child_of(Vl, c, V);
               code = (2u << LEVEL_SHIFT) | (uint32_t)c;
             } else {
