@@ -807,7 +807,13 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       // Only the first vertex of E_l stays in registers; the whole simplex is rebuilt when the
       // traversal needs it (FP32: from this pair's record in shared memory, which stays until the
       // next pair; FP64: from the element arrays).
+      // FP32: the inverse Jacobian of E_l is read from the record in shared memory where it is
+      // used (one broadcast load per entry), FP64: registers
       R Vl0[D], Ji[D][D], wl;
+      auto JI = [&](int r, int c) -> R {
+        if constexpr (F32) return wm.pf[(jj & 1) * 32 + D * D + r * D + c];
+        else return Ji[r][c];
+      };
       if constexpr (F32) {
         cp_async_wait_prior();
         __syncwarp();
@@ -815,10 +821,6 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 #pragma unroll
         for (int k = 0; k < D; k++)  // v_0(l) - v_0(m) from the float-float pairs, ~1 ulp
           Vl0[k] = (R)((ef[NL_EF_V0HI(D) + k] - v0h[k]) + (ef[NL_EF_V0LO(D) + k] - v0l[k]));
-#pragma unroll
-        for (int r = 0; r < D; r++)
-#pragma unroll
-          for (int c = 0; c < D; c++) Ji[r][c] = (R)ef[D * D + r * D + c];
         wl = (R)P.fC * (R)ef[2 * D * D];
       } else {
 #pragma unroll
@@ -845,6 +847,26 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             for (int k = 0; k < D; k++) V[a][k] = (R)P.evert[((int64_t)l * NV + a) * D + k];
         }
       };
+      // 2D: largest distance from the centroid of E_l to its vertices (see closed_set)
+      R rad_l = 0;
+      if (D == 2) {
+        R Vt[NV][D], ct[D];
+        get_Vl(Vt);
+#pragma unroll
+        for (int k = 0; k < D; k++) ct[k] = (Vt[0][k] + Vt[1][k] + Vt[D][k]) * (R)(1.0 / NV);
+        R r2 = 0;
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+          R d2 = 0;
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            const R d = Vt[a][k] - ct[k];
+            d2 += d * d;
+          }
+          r2 = r2 > d2 ? r2 : d2;
+        }
+        rad_l = sqrt(r2);
+      }
 
       R gp[NYL], hp[D][NYL], ug = 0, uh[D];
       f2 gq[3], hq[D][3];  // R = float: accumulators of inner points 0-5 in pairs
@@ -933,7 +955,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         for (int r = 0; r < D; r++) {
           R s = 0;
 #pragma unroll
-          for (int c = 0; c < D; c++) s += Ji[r][c] * (cen[c] - Vl0[c]);
+          for (int c = 0; c < D; c++) s += JI(r, c) * (cen[c] - Vl0[c]);
           uh[r] += wv * s;
         }
         st_closed++;
@@ -957,18 +979,9 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           for (int a = 0; a < NV; a++) t += V[a][k];
           cen[k] = t * (R)(1.0 / NV);
         }
-        R rad2 = 0;
-#pragma unroll
-        for (int a = 0; a < NV; a++) {
-          R d2 = 0;
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            const R d = V[a][k] - cen[k];
-            d2 += d * d;
-          }
-          rad2 = rad2 > d2 ? rad2 : d2;
-        }
-        const R rad = sqrt(rad2);
+        // every midpoint child of a triangle is the parent scaled by 1/2, so the radius of a
+        // level-L sub-element is that of E_l times 2^(1-L) (rounding is inside the margin)
+        const R rad = rad_l * pow2m(R(0), level - 1);
         const R lo = (R)P.fdme - rad - (R)P.margin, hi = (R)P.fdpe + rad + (R)P.margin;
         const R lo2 = lo > 0 ? lo * lo : (R)-1, hi2 = hi * hi;
         unsigned in_mask = 0;
@@ -1007,7 +1020,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         for (int r = 0; r < D; r++) {
           R t = 0;
 #pragma unroll
-          for (int c = 0; c < D; c++) t += Ji[r][c] * (cen[c] - Vl0[c]);
+          for (int c = 0; c < D; c++) t += JI(r, c) * (cen[c] - Vl0[c]);
           lc[r] = t;
         }
         if constexpr (F32) {
@@ -1067,7 +1080,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           for (int r = 0; r < D; r++) {
             R s = 0;
 #pragma unroll
-            for (int c = 0; c < D; c++) s += Ji[r][c] * (x[c] - Vl0[c]);
+            for (int c = 0; c < D; c++) s += JI(r, c) * (x[c] - Vl0[c]);
             lam[r] = s;
           }
           if constexpr (F32) {
