@@ -33,6 +33,13 @@ METRIC = ("element pairs/s & quad-pt pairs/s, mixed vs FP64 at equal error; "
           "p50/p99 solve ms")
 WORKLOAD = "c2_2d"
 
+# DRAM traffic of the FP32 assembly kernel per element pair: dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of the current kernel version on a small case of the
+# same dimension (profiles/k_quad_2d_fp32_c2_h128.md, profiles/k_quad_3d_fp32_c3.md) divided by
+# its element pairs.  Almost all of it is the block buffer, written once per pair, so it scales
+# with the pairs of a launch.  None: no capture of the current version.
+TRAFFIC_BYTES_PER_PAIR = {2: 35.47, 3: None}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -69,7 +76,8 @@ def dist_init(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl" if args.impl == "ours" else "gloo"
+        import torch
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
         dist.init_process_group(backend=backend)
     return rank, world, local
 
@@ -290,7 +298,9 @@ def run_ours(args, rank, world, local):
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
     achieved = flops / (kern_avg / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 1),
-            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+            "traffic": (round(TRAFFIC_BYTES_PER_PAIR[mesh.dim] * n_pairs)
+                        if TRAFFIC_BYTES_PER_PAIR.get(mesh.dim) else None),
             "kernel": f"k_quad<{mesh.dim},float,{w.kernel}>", "flops_per_launch": flops,
             "kernel_ms_avg": round(kern_avg, 3)}
 
