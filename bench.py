@@ -38,7 +38,7 @@ WORKLOAD = "c2_2d"
 # same dimension (profiles/k_quad_2d_fp32_c2_h128.md, profiles/k_quad_3d_fp32_c3.md) divided by
 # its element pairs.  Almost all of it is the block buffer, written once per pair, so it scales
 # with the pairs of a launch.  None: no capture of the current version.
-TRAFFIC_BYTES_PER_PAIR = {2: 35.47, 3: None}
+TRAFFIC_BYTES_PER_PAIR = {2: 35.47, 3: 68.73}
 
 
 def parse():
@@ -545,7 +545,9 @@ def run_reference(args, rank, world):
             "unit": "element pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "parallelism": "single CPU core"},
+            "data": "synthetic",
+            "config": {"workload": describe(w, mesh), "parallelism": "single CPU core (oracle)",
+                       "l2": "not applicable (CPU)"},
             "cpu_baseline": {"value": round(value, 1), "unit": "element pairs/s", "cores": 1,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 1), "unit": "element pairs/s",
