@@ -379,23 +379,6 @@ __device__ __forceinline__ f2 mollifier2(const MollK& K, f2 r2) {
   f2unpack(r2, a, b);
   return f2pack(mollifier_bf(K, a), mollifier_bf(K, b));
 }
-// Fully packed variant (a register pair per constant).
-__device__ __forceinline__ f2 mollifier2_packed(const MollK& P, f2 r2) {
-  float a, b;
-  f2unpack(f2add(r2, f2dup(1e-30f)), a, b);
-  const f2 q = f2pack(rsqrt_hw(a), rsqrt_hw(b));
-  const f2 r = f2mul(r2, q);
-  const f2 bq = f2fma(r, f2mul(q, f2dup(P.hie)), f2dup(P.nthie));
-  float s0, s1;
-  f2unpack(f2fma(r, bq, f2dup(P.die)), s0, s1);
-  const f2 sc = f2pack(fminf(fmaxf(s0, -1.f), 1.f), fminf(fmaxf(s1, -1.f), 1.f));
-  const f2 t = f2mul(sc, sc);
-  f2 p = f2fma(f2dup(35.f / 256.f), t, f2dup(-180.f / 256.f));
-  p = f2fma(p, t, f2dup(378.f / 256.f));
-  p = f2fma(p, t, f2dup(-420.f / 256.f));
-  p = f2fma(p, t, f2dup(315.f / 256.f));
-  return f2fma(sc, p, f2dup(0.5f));
-}
 __device__ __forceinline__ f2 eta_gauss2(float inv_delta2, f2 r2) {
   float a, b;
   f2unpack(r2, a, b);
