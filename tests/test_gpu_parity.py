@@ -200,3 +200,22 @@ def test_table2_tri_linear_on_gpu():
         u, *_ = nl.nl_solve(A, b, g, solver=1, rtol=1e-13)
         err = O.l2_error(mesh, u, w.ms, omega_only=False)
         assert abs(err / gold[ml] - 1) < 2e-3, (ml, err)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] in ("c1", "jit2d_L4", "gauss2d", "jit3d")],
+                         ids=lambda c: c[0])
+def test_band_point_pair_counts(case):
+    # the band counter feeds the benchmark's algorithmic flop count: point pairs with
+    # delta - eps <= r <= delta + eps, against the oracle's count (only the rounding of r at
+    # the two band edges may differ)
+    name, mk, delta, eps, L_max, L_min, kernel = case
+    mesh = mk()
+    off, pl = O.pairs(mesh, delta, eps)
+    rp, col = O.csr(mesh, off, pl)
+    _, ost = O.assemble(mesh, off, pl, rp, col, delta, eps, L_max, L_min, kernel)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, delta, eps)
+    for prec, tol in ((nl.NL_PREC_FP64, 1e-9), (nl.NL_PREC_FP32, 1e-4)):
+        _, st = nl.nl_assemble(m, p, delta, eps, L_max, L_min, kernel, prec, count_band=True)
+        assert abs(st.n_band_point_pairs - ost.n_band_pairs) <= tol * ost.n_band_pairs + 2, (
+            name, prec, st.n_band_point_pairs, ost.n_band_pairs)
