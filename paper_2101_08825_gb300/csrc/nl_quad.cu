@@ -168,8 +168,8 @@ nl_status noalloc_scratch(unsigned char** out) {
 template <int D, typename R, int KERN>
 nl_status run_noalloc(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s) {
   NL_TRY((launch_quad<D, R, KERN, true>(P, s)));
-  const size_t smem = sizeof(int32_t) * (size_t)(D + 1) * std::max(1, p->max_row_nnz);
-  if (smem > (size_t)200 * 1024)
+  const size_t smem = scatter_smem_bytes(D, p->max_row_nnz);
+  if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
   NL_TRY((allow_smem(k_scatter<D, R>, smem)));
   k_scatter<D, R><<<NL_CNT((unsigned)m->n_elem), 128, smem, s>>>(

@@ -1445,6 +1445,24 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     }
     return -1;
   };
+  // With enough dynamic shared memory the element's contributions are first summed per CSR
+  // entry in shared memory (an element's pairs hit each column of its rows several times) and
+  // each entry is added to the global values once; otherwise every contribution goes to the
+  // global values directly.
+  const int total = roff[NV];
+  unsigned dyn = 0;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const int acc_off = (total + 3) & ~3;  // ints before the (8-byte aligned) accumulators
+  const bool use_acc = (size_t)acc_off * 4 + (size_t)total * 8 <= (size_t)dyn;
+  double* acc = reinterpret_cast<double*>(rows + acc_off);
+  if (use_acc) {
+    for (int t = threadIdx.x; t < total; t += blockDim.x) acc[t] = 0.0;
+    __syncthreads();
+  }
+  auto add = [&](int a, int64_t pos, double v) {
+    if (use_acc) atomicAdd(&acc[roff[a] + (int)(pos - rbeg[a])], v);
+    else atomicAdd(&values[pos], v);
+  };
   const int64_t n = (q1 > q0 ? q1 - q0 : 0) * NB;
   for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
     const int64_t p = q0 + t / NB;
@@ -1456,14 +1474,33 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
       atomicOr(err, ERR_CSR);
       continue;
     }
-    atomicAdd(&values[pos], (double)blk[(p - p_base) * NB + e]);
+    add(a, pos, (double)blk[(p - p_base) * NB + e]);
   }
   if (with_self && threadIdx.x < NB) {
     const int a = threadIdx.x / NV, b = threadIdx.x % NV;
     const int64_t pos = find(a, nodes[b]);
     if (pos < 0) atomicOr(err, ERR_CSR);
-    else atomicAdd(&values[pos], selfblk[m * NB + threadIdx.x]);
+    else add(a, pos, selfblk[m * NB + threadIdx.x]);
   }
+  if (use_acc) {
+    __syncthreads();
+    for (int a = 0; a < NV; a++)
+      for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) {
+        const double v = acc[roff[a] + t];
+        if (v != 0.0) atomicAdd(&values[rbeg[a] + t], v);
+      }
+  }
+}
+
+// Dynamic shared memory of the scatter kernels for rows of up to max_row columns: the cached
+// column lists plus FP64 accumulators when that fits in 200 KB, else the column lists only
+// (0 if even those do not fit).
+inline size_t scatter_smem_bytes(int dim, int max_row) {
+  const size_t total = (size_t)(dim + 1) * (size_t)std::max(1, max_row);
+  const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
+  if (with_acc <= (size_t)200 * 1024) return with_acc;
+  if (total * 4 <= (size_t)200 * 1024) return total * 4;
+  return 0;
 }
 
 // Single problem: CTA b handles element m_begin + b; with_self = 0 adds the cross blocks of
@@ -1540,8 +1577,8 @@ nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end
     m_end = std::min<int64_t>(m->n_elem, std::max(m_end, m_begin));
   }
   if (m_end <= m_begin) return NL_OK;
-  size_t smem = sizeof(int32_t) * (size_t)(D + 1) * std::max(1, p->max_row_nnz);
-  if (smem > (size_t)200 * 1024)
+  const size_t smem = scatter_smem_bytes(D, p->max_row_nnz);
+  if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
   NL_TRY((allow_smem(k_scatter<D, R>, smem)));
   k_scatter<D, R><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
