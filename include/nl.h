@@ -212,7 +212,9 @@ void nl_vector_destroy(nl_vector* v);
  * method in FP64; any other value runs it in FP32 inside FP64 iterative refinement
  * (residuals r = F~ - A u in FP64).  Stops when ||F~ - A u|| <= rtol ||F~|| (free rows)
  * or after max_iter iterations (total inner iterations).  u_out: host, n_vert values (free
- * nodes: W; constrained nodes: g).  iters, final_rel_res may be NULL.
+ * nodes: W; constrained nodes: g).  iters, final_rel_res may be NULL.  The solve runs on the
+ * stream of the matrix's mesh; when that stream can be captured (any stream but the legacy
+ * default stream), every batch of 8 iterations after the first is replayed from a CUDA graph.
  * Errors: NL_ENOTCONV when max_iter ran out (u_out still written). */
 nl_status nl_solve(nl_matrix* A, const nl_vector* rhs, const double* g_nodes, int solver,
                    double rtol, int max_iter, nl_precision precision, double* u_out,
