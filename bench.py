@@ -9,8 +9,14 @@ with the mesh resident on the device.  The headline runs the FP32 point-pair pat
 solve in FP32 inside FP64 iterative refinement ("mixed"); the same step in FP64 is measured
 next to it with the solution error of both against the manufactured solution.
 
+Beside the headline the JSON line carries: the FP64 step, the roofline of the assembly kernel,
+the public-API end-to-end rate from host buffers (e2e), a batching leg (128 small problems:
+sequential assembly against one plan), a serving leg (the first --serve-requests requests of
+the seeded stream, closed loop and then open loop at 70% load) and the oracle timed on the host
+cores (cpu_baseline).
+
 Output: one JSON line (rank 0).  --impl reference times the plain CPU oracle on a bounded
-sample of the same workload instead.
+sample of the same workload instead.  Under torchrun every rank runs its own replica.
 """
 from __future__ import annotations
 
