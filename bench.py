@@ -303,6 +303,19 @@ def run_ours(args, rank, world, local):
     flops = roofline_flops(mesh.dim, stb)
     peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
     achieved = flops / (kern_avg / 1e3) / 1e12
+    if fp64 is not None:
+        # the FP64 assembly kernel against the FP64 pipe: same algorithmic count with the FP64
+        # launch's own evaluated point pairs (its band pairs: those of the FP32 count launch,
+        # identical up to the rounding of r at the band edges); peak = the measured FP64 FMA
+        # chain of this GPU model, 1.19 TFLOP/s
+        st64 = last64["st"]
+        f64_flops = float(st64.n_eval_point_pairs * ((5 if mesh.dim == 2 else 8) + 2 + 2 * mesh.dim)
+                          + max(0, stb.n_band_point_pairs) * 15)
+        k64_avg = statistics.mean(k64)
+        fp64["roofline"] = {"bound": "fp64 pipe", "achieved": round(f64_flops / (k64_avg / 1e3) / 1e12, 4),
+                            "peak": 1.19, "unit": "TFLOP/s",
+                            "frac": round(f64_flops / (k64_avg / 1e3) / 1.19e12, 4),
+                            "kernel": f"k_quad<{mesh.dim},double,{w.kernel}>"}
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 1),
             "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
             "traffic": (round(TRAFFIC_BYTES_PER_PAIR[mesh.dim] * n_pairs)
