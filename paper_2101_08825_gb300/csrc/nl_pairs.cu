@@ -154,6 +154,48 @@ __device__ __forceinline__ bool in_reach(const double* lo1, const double* hi1, c
   return m < reach;
 }
 
+// The same test screened in FP32 on boxes rounded outwards (fbox: lo rounded down, hi rounded
+// up, so the FP32 box contains the FP64 one): a screened distance below reach - margin or
+// above reach + margin decides; in between the FP64 test of eq. (mindist) decides.  margin
+// bounds the rounding of the FP32 boxes and of the FP32 subtraction, so the result is that of
+// the FP64 test for every pair.
+struct Screen {
+  const float* flo;  // [n_elem][D] lower box corners rounded down
+  const float* fhi;  // [n_elem][D] upper box corners rounded up
+  float lo_t, hi_t;  // reach - margin, reach + margin
+};
+
+template <int D>
+__device__ __forceinline__ bool in_reach_screened(const Screen& S, int64_t l, const float* flo_m,
+                                                  const float* fhi_m, const double* __restrict__ blo,
+                                                  const double* __restrict__ bhi, const double* lo_m,
+                                                  const double* hi_m, double reach) {
+  float mf = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    const float d1 = S.flo[l * D + k] - fhi_m[k];
+    const float d2 = flo_m[k] - S.fhi[l * D + k];
+    mf = fmaxf(mf, fmaxf(d1, d2));
+  }
+  if (mf < S.lo_t) return true;
+  if (mf > S.hi_t) return false;
+  double lo_l[D], hi_l[D];
+#pragma unroll
+  for (int k = 0; k < D; k++) {
+    lo_l[k] = blo[l * D + k];
+    hi_l[k] = bhi[l * D + k];
+  }
+  return in_reach<D>(lo_l, hi_l, lo_m, hi_m, reach);
+}
+
+__global__ void k_round_boxes(int64_t n, const double* __restrict__ blo, const double* __restrict__ bhi,
+                              float* __restrict__ flo, float* __restrict__ fhi) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  flo[i] = __double2float_rd(blo[i]);
+  fhi[i] = __double2float_ru(bhi[i]);
+}
+
 template <int D>
 __global__ void k_bin_count(int64_t n_elem, Grid g, const double* __restrict__ blo,
                             const double* __restrict__ bhi, int32_t* __restrict__ cell_cnt) {
@@ -181,7 +223,7 @@ template <int D>
 __global__ void k_pairs_count(int64_t n_elem, Grid g, double reach, const double* __restrict__ blo,
                               const double* __restrict__ bhi, const int64_t* __restrict__ cell_off,
                               const int32_t* __restrict__ items, int64_t* __restrict__ cnt,
-                              int32_t* __restrict__ max_cnt) {
+                              int32_t* __restrict__ max_cnt, Screen S) {
   int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (m >= n_elem) return;
@@ -189,6 +231,11 @@ __global__ void k_pairs_count(int64_t n_elem, Grid g, double reach, const double
   for (int k = 0; k < D; k++) {
     lo_m[k] = blo[m * D + k];
     hi_m[k] = bhi[m * D + k];
+  }
+  float flo_m[D], fhi_m[D];
+  for (int k = 0; k < D; k++) {
+    flo_m[k] = S.flo[m * D + k];
+    fhi_m[k] = S.fhi[m * D + k];
   }
   int c[3];
   cell_of<D>(g, lo_m, hi_m, c);
@@ -201,13 +248,8 @@ __global__ void k_pairs_count(int64_t n_elem, Grid g, double reach, const double
     if (!ok) continue;
     int id = cell_id<D>(g, cc);
     for (int64_t t = cell_off[id] + lane; t < cell_off[id + 1]; t += 32) {
-      int32_t l = items[t];
-      double lo_l[D], hi_l[D];
-      for (int k = 0; k < D; k++) {
-        lo_l[k] = blo[(int64_t)l * D + k];
-        hi_l[k] = bhi[(int64_t)l * D + k];
-      }
-      count += in_reach<D>(lo_l, hi_l, lo_m, hi_m, reach) ? 1 : 0;
+      const int32_t l = items[t];
+      count += in_reach_screened<D>(S, l, flo_m, fhi_m, blo, bhi, lo_m, hi_m, reach) ? 1 : 0;
     }
   }
   for (int o = 16; o > 0; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
@@ -241,7 +283,7 @@ template <int D>
 __global__ void k_pairs_fill(int64_t n_elem, Grid g, double reach, const double* __restrict__ blo,
                              const double* __restrict__ bhi, const int64_t* __restrict__ cell_off,
                              const int32_t* __restrict__ items, const int64_t* __restrict__ pair_off,
-                             int32_t* __restrict__ pair_l, int cap, int* __restrict__ err) {
+                             int32_t* __restrict__ pair_l, int cap, int* __restrict__ err, Screen S) {
   extern __shared__ int32_t buf[];
   __shared__ int nfound;
   int64_t m = blockIdx.x;
@@ -251,6 +293,11 @@ __global__ void k_pairs_fill(int64_t n_elem, Grid g, double reach, const double*
   for (int k = 0; k < D; k++) {
     lo_m[k] = blo[m * D + k];
     hi_m[k] = bhi[m * D + k];
+  }
+  float flo_m[D], fhi_m[D];
+  for (int k = 0; k < D; k++) {
+    flo_m[k] = S.flo[m * D + k];
+    fhi_m[k] = S.fhi[m * D + k];
   }
   int c[3];
   cell_of<D>(g, lo_m, hi_m, c);
@@ -262,13 +309,8 @@ __global__ void k_pairs_fill(int64_t n_elem, Grid g, double reach, const double*
     if (!ok) continue;
     int id = cell_id<D>(g, cc);
     for (int64_t t = cell_off[id] + threadIdx.x; t < cell_off[id + 1]; t += blockDim.x) {
-      int32_t l = items[t];
-      double lo_l[D], hi_l[D];
-      for (int k = 0; k < D; k++) {
-        lo_l[k] = blo[(int64_t)l * D + k];
-        hi_l[k] = bhi[(int64_t)l * D + k];
-      }
-      if (in_reach<D>(lo_l, hi_l, lo_m, hi_m, reach)) {
+      const int32_t l = items[t];
+      if (in_reach_screened<D>(S, l, flo_m, fhi_m, blo, bhi, lo_m, hi_m, reach)) {
         int pos = atomicAdd(&nfound, 1);
         if (pos < cap) buf[pos] = l;
       }
@@ -446,12 +488,25 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   NL_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int32_t), s));
   const int tb = 256;
   unsigned gb = (unsigned)((ne + tb - 1) / tb);
+  // FP32 boxes for the screened test; margin: 8 FP32 ulps of the largest coordinate magnitude
+  // plus the reach, far above the rounding of the boxes (1 ulp each) and of the subtraction
+  DevBuf<float> fbox;
+  NL_TRY(fbox.alloc((size_t)2 * D * ne, s));
+  {
+    const int64_t nn = (int64_t)D * ne;
+    k_round_boxes<<<NL_CNT((unsigned)((nn + tb - 1) / tb)), tb, 0, s>>>(nn, m->blo, m->bhi, fbox.p,
+                                                                       fbox.p + nn);
+  }
+  double cmax = 0.0;
+  for (int k = 0; k < D; k++) cmax = std::max(cmax, std::max(std::fabs(m->bb_lo[k]), std::fabs(m->bb_hi[k])));
+  const double margin = 8.0 * 1.1920928955078125e-07 * (cmax + reach);
+  Screen S{fbox.p, fbox.p + (size_t)D * ne, (float)(reach - margin), (float)(reach + margin)};
   k_bin_count<D><<<NL_CNT(gb), tb, 0, s>>>(ne, g, m->blo, m->bhi, cell_cnt.p);
   NL_TRY(exclusive_scan_i32_to_i64(cell_cnt.p, cell_off.p, total, s));
   k_bin_fill<D><<<NL_CNT(gb), tb, 0, s>>>(ne, g, m->blo, m->bhi, cell_off.p, cursor.p, items.p);
   unsigned gw = (unsigned)((ne * 32 + tb - 1) / tb);
   k_pairs_count<D><<<NL_CNT(gw), tb, 0, s>>>(ne, g, reach, m->blo, m->bhi, cell_off.p, items.p, cnt.p,
-                                     max_cnt.p);
+                                     max_cnt.p, S);
   NL_CUDA(cudaGetLastError());
   DevBuf<int64_t> off;
   NL_TRY(off.alloc(ne + 1, s));
@@ -471,7 +526,7 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   size_t smem = sizeof(int32_t) * cap;
   NL_TRY(allow_smem(k_pairs_fill<D>, smem));
   k_pairs_fill<D><<<NL_CNT((unsigned)ne), 256, smem, s>>>(ne, g, reach, m->blo, m->bhi, cell_off.p, items.p,
-                                                 off.p, pl.p, cap, err.p);
+                                                 off.p, pl.p, cap, err.p, S);
   NL_CUDA(cudaGetLastError());
 
   // pattern
