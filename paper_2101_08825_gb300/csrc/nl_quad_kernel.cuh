@@ -82,7 +82,7 @@ struct QParams {
   int* err;
   double delta, dme, dpe, C, inv_eps, inv_delta2;
   float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
-  float fhie, fnthie, fdie;  // 1/(2 eps), -3/(2 eps), delta/eps (branch-free mollifier)
+  float fmqe, ftqe, fue;     // -1/(4 eps), 3/(4 eps), (1 - delta/eps)/2 (branch-free mollifier)
   float fint2, fnotint2;     // screen thresholds (delta - eps -+ margin)^2 (-1: never)
   int L_min, L_max, scap, count_band;
   int kernel;  // nl_kernel_kind (read at run time by the batched kernel)
@@ -355,22 +355,25 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
 }
 
 // mu_{delta,eps}(r) from r^2 without branches.  r = r2 q with q ~ 1/sqrt(r2) from the
-// hardware, refined by one Newton step folded into s: r' = r (3/2 - r q / 2) and
-//   s = (delta - r')/eps = delta/eps + r (r q/(2 eps) - 3/(2 eps)),
-// two FMAs from r and q/(2 eps).  s is clamped to [-1, 1], where xi is exactly 0 and 1
-// (xi(+-1) = 1/2 +- 128/256 in FP32), so every point pair takes the same path; r2 = 0
-// (coinciding points of a self pair) gives r = 0 and mu = 1.
+// hardware, refined by one Newton step r' = r (3/2 - r q / 2) folded into the argument
+// u = (1 - s)/2 of s = (delta - r')/eps:
+//   u = (1 - delta/eps)/2 + r (3/(4 eps) - r q/(4 eps)),
+// two FMAs from r and q/(4 eps), the second saturating u to [0, 1] (s to [-1, 1], where xi
+// is exactly 1 and 0: xi(+-1) = 1/2 +- 128/256 in FP32), so every point pair takes the same
+// path.  r2 = 0 (coinciding points of a self pair) gives q = +inf and r = 0 * inf = NaN, which
+// the saturation turns into u = 0: s = 1 and mu = 1, the value at r = 0.
 // Constants of the branch-free mollifier, read once per buffer integration (in the batched
 // kernel the parameters live in shared memory).
 struct MollK {
-  float hie, nthie, die;  // 1/(2 eps), -3/(2 eps), delta/eps
+  float mqe, tqe, ue;  // -1/(4 eps), 3/(4 eps), (1 - delta/eps)/2
 };
 __device__ __forceinline__ float mollifier_bf(const MollK& K, float r2) {
-  const float q = rsqrt_hw(r2 + 1e-30f);
+  const float q = rsqrt_hw(r2);
   const float r = r2 * q;
-  const float bq = fmaf(r, q * K.hie, K.nthie);
-  const float sc = fminf(fmaxf(fmaf(r, bq, K.die), -1.f), 1.f);
-  return xi_poly(sc);
+  const float b = fmaf(r, q * K.mqe, K.tqe);
+  float u;
+  asm("fma.rn.ftz.sat.f32 %0, %1, %2, %3;" : "=f"(u) : "f"(r), "f"(b), "f"(K.ue));
+  return xi_poly(fmaf(-2.f, u, 1.f));
 }
 // The two point pairs of a packed r2 in scalar FP32: scalar FMAs take the constants as
 // immediate or constant-bank operands, while every packed constant needs a register pair.
@@ -1033,7 +1036,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 
       // integrate the buffered items of one kind (warp-collective)
       auto integrate = [&](int kind, int n_it) {
-        const MollK MK{P.fhie, P.fnthie, P.fdie};
+        const MollK MK{P.fmqe, P.ftqe, P.fue};
         const bool count_band = P.count_band != 0, gauss = is_gauss();
         const float inv_d2 = P.finv_delta2;
         constexpr int PAD = VPad<D>::N;
@@ -1068,11 +1071,14 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           }
           if constexpr (F32) {
             // inner points 0-5 in packed pairs, point 6 alone
-            f2 X[D], L[D];
+            // per point pair g = mu (eta): added as w_x g to G and as (w_x lambda_k) g to H_k
+            f2 X[D], WL[D];
+            float wl[D];
 #pragma unroll
             for (int k = 0; k < D; k++) {
               X[k] = f2dup(x[k]);
-              L[k] = f2dup(lam[k]);
+              wl[k] = wcx * lam[k];
+              WL[k] = f2dup(wl[k]);
             }
             const f2 Wx = f2dup(wcx);
 #pragma unroll
@@ -1084,9 +1090,9 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
                 d = f2sub(X[k], yq[j][k]);
                 r2 = f2fma(d, d, r2);
               }
-              f2 g = Wx;
+              f2 g = f2dup(1.f);
               if (kind == KIND_FINAL) {
-                g = f2mul(g, mollifier2(MK, r2));
+                g = mollifier2(MK, r2);
                 if (count_band) {
                   float a, b;
                   f2unpack(r2, a, b);
@@ -1094,10 +1100,10 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
                   st_band += (valid && b >= P.fdme2 && b <= P.fdpe2) ? 1 : 0;
                 }
               }
-              if (gauss) g = f2mul(g, eta_gauss2(inv_d2, r2));
-              gq[j] = f2add(gq[j], g);
+              if (gauss) g = (kind == KIND_FINAL) ? f2mul(g, eta_gauss2(inv_d2, r2)) : eta_gauss2(inv_d2, r2);
+              gq[j] = f2fma(Wx, g, gq[j]);
 #pragma unroll
-              for (int k = 0; k < D; k++) hq[k][j] = f2fma(g, L[k], hq[k][j]);
+              for (int k = 0; k < D; k++) hq[k][j] = f2fma(g, WL[k], hq[k][j]);
             }
             float r2 = 0.f;
 #pragma unroll
@@ -1105,15 +1111,15 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
               const float d = x[k] - y[6][k];
               r2 = fmaf(d, d, r2);
             }
-            float g = wcx;
+            float g = 1.f;
             if (kind == KIND_FINAL) {
-              g *= mollifier_bf(MK, r2);
+              g = mollifier_bf(MK, r2);
               if (count_band) st_band += (valid && r2 >= P.fdme2 && r2 <= P.fdpe2) ? 1 : 0;
             }
             if (gauss) g *= __expf(-r2 * inv_d2);
-            gp[6] += g;
+            gp[6] = fmaf(wcx, g, gp[6]);
 #pragma unroll
-            for (int k = 0; k < D; k++) hp[k][6] += g * lam[k];
+            for (int k = 0; k < D; k++) hp[k][6] = fmaf(g, wl[k], hp[k][6]);
           } else {
 #pragma unroll
             for (int i = 0; i < NYL; i++) {
@@ -1639,9 +1645,9 @@ inline nl_status fill_qparams(const char* who, const nl_mesh* m, const nl_pairs*
   P->fdme2 = (float)(P->dme * P->dme);
   P->fdpe2 = (float)(P->dpe * P->dpe);
   P->finv_delta2 = (float)P->inv_delta2;
-  P->fhie = (float)(0.5 / kp->eps);
-  P->fnthie = (float)(-1.5 / kp->eps);
-  P->fdie = (float)(kp->delta / kp->eps);
+  P->fmqe = (float)(-0.25 / kp->eps);
+  P->ftqe = (float)(0.75 / kp->eps);
+  P->fue = (float)(0.5 * (1.0 - kp->delta / kp->eps));
   // bound on |local coordinates| and on the FP32 error of the screened distances
   P->margin = (float)(2e-5 * (kp->delta + kp->eps + 2.0 * m->max_ext));
   {
