@@ -590,10 +590,16 @@ nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes
         ok = true;
         break;
       }
+      // inner tolerance: 1e-5 (about what one FP32 round reliably gains) while more than that
+      // is still needed; once the remaining factor rtol / rr is within reach, half of it (at
+      // least 1e-6), so that a round that would end just short of rtol is not followed by a
+      // whole extra round
+      const double need = rtol / rr;
+      const double itol = need < 1e-6 ? 1e-5 : std::min(1e-3, std::max(1e-6, 0.5 * need));
       int inner = 0;
       bool iok = false;
       double irr = 0.0;
-      NL_TRY((krylov<float, float>(c, a32.p, solver, r32.p, d32.p, 1e-5, max_iter - total, &inner,
+      NL_TRY((krylov<float, float>(c, a32.p, solver, r32.p, d32.p, itol, max_iter - total, &inner,
                                    &iok, &irr, W)));
       total += inner;
       k_add_f32_to_f64<<<NL_CNT(c.gvec()), RT, 0, s>>>(c.n, d32.p, x.p);
