@@ -356,6 +356,102 @@ def test_algorithm1_equals_uniform_refinement(offset):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), L
 
 
+def _bey_children(T):
+    """Bey's regular refinement of a tetrahedron (x0..x3) into eight children: the four corner
+    tetrahedra and the interior octahedron cut along the diagonal x02-x13."""
+    x0, x1, x2, x3 = T
+    x01, x02, x03 = (x0 + x1) / 2, (x0 + x2) / 2, (x0 + x3) / 2
+    x12, x13, x23 = (x1 + x2) / 2, (x1 + x3) / 2, (x2 + x3) / 2
+    return [np.array(c) for c in ((x0, x01, x02, x03), (x01, x1, x12, x13), (x02, x12, x2, x23),
+                                  (x03, x13, x23, x3), (x01, x02, x03, x13), (x01, x02, x12, x13),
+                                  (x02, x03, x13, x23), (x02, x12, x13, x23))]
+
+
+def _tet_vol(T):
+    return abs(np.linalg.det(np.stack([T[1] - T[0], T[2] - T[0], T[3] - T[0]]))) / 6
+
+
+def test_bey_children_partition_the_tetrahedron():
+    # every child has volume |T|/8, and the 14-point rule (exact to degree 5) summed over the
+    # children reproduces the closed-form integral of every barycentric monomial of T of
+    # degree <= 5: the children cover T without overlap (two levels deep as well)
+    rng = np.random.default_rng(3)
+    T = rng.random((4, 3))
+    vol = _tet_vol(T)
+    b, w = O.quad_rule(3)
+    Tm = np.stack([T[1] - T[0], T[2] - T[0], T[3] - T[0]], axis=1)
+    kids = _bey_children(T)
+    for level_kids in (kids, [g for k in kids for g in _bey_children(k)]):
+        for c in level_kids:
+            assert abs(_tet_vol(c) / vol * len(level_kids) - 1) < 1e-12
+        for alpha in np.ndindex(3, 3, 3, 3):
+            if sum(alpha) > 5:
+                continue
+            tot = 0.0
+            for c in level_kids:
+                X = b @ c
+                l123 = np.linalg.solve(Tm, (X - T[0]).T).T
+                lam = np.column_stack([1 - l123.sum(1), l123])
+                tot += _tet_vol(c) * float(np.sum(w * np.prod(lam ** np.array(alpha), axis=1)))
+            assert abs(tot / vol - _exact_monomial(alpha)) < 1e-13, alpha
+
+
+def _uniform_local_blocks_3d(Vl, Vm, delta, eps, C, depth):
+    """As _uniform_local_blocks, in 3D: E_l split uniformly by Bey's rule `depth` times,
+    14-point rule on every piece and on E_m."""
+    b, w = O.quad_rule(3)
+    tets = [np.array(Vl)]
+    for _ in range(depth):
+        tets = [c for T in tets for c in _bey_children(T)]
+    X = np.concatenate([b @ T for T in tets])
+    WX = np.concatenate([w * _tet_vol(T) for T in tets])
+    Vl = np.array(Vl)
+    Tl = np.stack([Vl[1] - Vl[0], Vl[2] - Vl[0], Vl[3] - Vl[0]], axis=1)
+    l123 = np.linalg.solve(Tl, (X - Vl[0]).T).T
+    PL = np.column_stack([1 - l123.sum(1), l123])
+    Vm = np.array(Vm)
+    Y = b @ Vm
+    WY = w * _tet_vol(Vm)
+    R = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    MU = np.vectorize(lambda r: O.mu(r, delta, eps))(R)
+    G = WX[:, None] * WY[None, :] * C * MU
+    S = np.einsum("xy,ya,yb->ab", G, b, b)
+    Xc = np.einsum("xy,ya,xc->ac", G, b, PL)
+    return 2 * S, -2 * Xc
+
+
+@pytest.mark.parametrize("offset", [0.16, 0.18, 0.2])
+def test_algorithm1_equals_uniform_refinement_3d(offset):
+    # 3D counterpart of the test above: the oracle's Algorithm 1 with Bey's split at L_max = L
+    # against uniform Bey refinement of the outer tetrahedron to level L, brute force.  The
+    # band's point pairs agree only if both produce the same sub-tetrahedra.
+    from nl_inputs.mesh import Mesh
+    Vm = np.array([[0.0, 0.0, 0.0], [0.05, 0.01, 0.0], [0.01, 0.05, 0.01], [0.01, 0.01, 0.05]])
+    Vl = np.array([[offset, 0.02, 0.0], [offset + 0.05, 0.0, 0.01], [offset + 0.02, 0.05, 0.0],
+                   [offset + 0.01, 0.02, 0.05]])
+    coords = np.concatenate([Vm, Vl]).T.copy()
+    mesh = Mesh(dim=3, coords=coords, conn=np.array([[0, 1, 2, 3], [4, 5, 6, 7]], np.int32),
+                elem_in_omega=np.ones(2, np.uint8), node_free=np.ones(8, np.uint8), h=0.05)
+    delta, eps = 0.2, 0.01
+    C = O.kernel_constant(3, O.KERNEL_CONST, delta, eps)
+    off, pl = O.pairs(mesh, delta, eps)
+    assert len(pl) == 4
+    rp, col = O.csr(mesh, off, pl)
+    for L in (1, 2, 3):
+        vals, st = O.assemble(mesh, off, pl, rp, col, delta, eps, L)
+        got = _dense(rp, col, vals, 8)
+        ref = np.zeros((8, 8))
+        for (mi, li) in ((0, 0), (0, 1), (1, 0), (1, 1)):
+            Vmm, Vll = (Vm, Vl)[mi], (Vm, Vl)[li]
+            S2, X2 = _uniform_local_blocks_3d(Vll, Vmm, delta, eps, C, L - 1)
+            nm, nl = np.arange(4) + 4 * mi, np.arange(4) + 4 * li
+            ref[np.ix_(nm, nm)] += S2
+            ref[np.ix_(nm, nl)] += X2
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), L
+        if L == 3:
+            assert st.n_band_pairs > 0  # the band is crossed: mu is not 0/1 everywhere
+
+
 def _dense(rp, col, vals, n):
     A = np.zeros((n, n))
     for i in range(n):
