@@ -1,0 +1,48 @@
+"""The seeded input generators (CPU): the structured meshes of the four workloads have the
+sizes their construction fixes, and the jitter leaves the topology, the inner/outer split and
+the element pairs of the small workload unchanged.
+
+Construction (the structured meshes of Sec. 6): (0,1)^n split into cubes of side h, each cut
+into n! simplices (2 triangles, 6 Kuhn tetrahedra), surrounded by an outer layer of
+ceil((delta + eps)/h) cells, so that every point within delta + eps of Omega is meshed (the
+layer width is this implementation's reading of the interaction domain's extent); unknowns
+are the nodes strictly inside Omega."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from nl_inputs import WORKLOADS, workload_mesh
+
+
+@pytest.mark.parametrize("name", ["c1_2d", "c2_2d", "c3_3d", "c4_3d"])
+def test_workload_mesh_sizes(name):
+    w = WORKLOADS[name]
+    m = workload_mesh(w)
+    n, d = w.cells[0], w.dim
+    assert all(c == n for c in w.cells)
+    assert w.layer * w.h >= w.delta + w.eps - 1e-12 > (w.layer - 1) * w.h
+    N = n + 2 * w.layer
+    assert m.n_vert == (N + 1) ** d
+    assert m.n_elem == math.factorial(d) * N ** d
+    assert int(m.elem_in_omega.sum()) == math.factorial(d) * n ** d
+    assert int(m.node_free.sum()) == (n - 1) ** d
+    # every simplex has positive volume and the volumes fill the meshed box
+    x = m.coords
+    V = np.stack([x[:, m.conn[:, a]].T for a in range(d + 1)], axis=1)  # (elem, d+1, d)
+    vol = np.abs(np.linalg.det(V[:, 1:, :] - V[:, :1, :])) / math.factorial(d)
+    assert vol.min() > 0.2 * w.h ** d / math.factorial(d)
+    assert abs(vol.sum() - (N * w.h) ** d) < 1e-9 * (N * w.h) ** d
+
+
+def test_jitter_keeps_the_small_workload_pairs():
+    # the small 2D workload without and with jitter: same element pairs and CSR pattern
+    w = WORKLOADS["c1_2d"]
+    counts = []
+    for jit in (0.0, w.jitter or 0.1):
+        m = workload_mesh(w.with_(jitter=jit))
+        off, pl = O.pairs(m, w.delta, w.eps)
+        rp, col = O.csr(m, off, pl)
+        counts.append((len(pl), len(col)))
+    assert counts[0] == counts[1] and counts[0][0] > 0
