@@ -151,7 +151,9 @@ void nl_mesh_destroy(nl_mesh* mesh);
 /* Element pairs and sparsity pattern (Sec. 5, eq. k_l; Sec. 5.1 eq. mindist):
  *   J = {(m, l) : aprx-min-dist(E_l, E_m) < delta + eps}, bounding boxes of the vertices,
  * stored m-major with l ascending, and the CSR pattern of A: row i (every node) holds the
- * nodes of every l with (m, l) in J and i a node of m, columns ascending.
+ * nodes of every l with (m, l) in J and i a node of m, columns ascending.  The distance test
+ * runs in FP32 on boxes rounded outwards and is repeated in FP64 within a margin of the
+ * threshold that bounds the FP32 rounding, so J is exactly that of the FP64 test.
  * Errors: NL_EINVAL unless 0 < eps < delta; NL_EINTERNAL if a neighbourhood exceeds the
  * builder's shared-memory capacity (more than 49152 pairs for one element or 8192
  * columns in one row). */
@@ -210,7 +212,9 @@ void nl_vector_destroy(nl_vector* v);
 /* Solves A_{free,free} W = F~_free (A is nonsymmetric at quadrature-error level when
  * L_max > 1, Sec. 5): solver 0 = CG, 1 = BiCGStab.  precision NL_PREC_FP64 runs the Krylov
  * method in FP64; any other value runs it in FP32 inside FP64 iterative refinement
- * (residuals r = F~ - A u in FP64).  Stops when ||F~ - A u|| <= rtol ||F~|| (free rows)
+ * (residuals r = F~ - A u in FP64; each inner FP32 solve stops at 1e-5 of its right-hand
+ * side, or at half the factor rtol / ||r|| that remains once that is within reach, but
+ * not below 1e-6).  Stops when ||F~ - A u|| <= rtol ||F~|| (free rows)
  * or after max_iter iterations (total inner iterations).  u_out: host, n_vert values (free
  * nodes: W; constrained nodes: g).  iters, final_rel_res may be NULL.  The solve runs on the
  * stream of the matrix's mesh; when that stream can be captured (any stream but the legacy
