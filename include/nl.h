@@ -213,8 +213,8 @@ void nl_vector_destroy(nl_vector* v);
  * L_max > 1, Sec. 5): solver 0 = CG, 1 = BiCGStab.  precision NL_PREC_FP64 runs the Krylov
  * method in FP64; any other value runs it in FP32 inside FP64 iterative refinement
  * (residuals r = F~ - A u in FP64; each inner FP32 solve stops at 1e-5 of its right-hand
- * side, or at half the factor rtol / ||r|| that remains once that is within reach, but
- * between 1e-6 and 1e-3).  Stops when ||F~ - A u|| <= rtol ||F~|| (free rows)
+ * side while the remaining factor q = rtol ||F~|| / ||r|| is below 1e-6, else at q / 2
+ * clamped to [1e-6, 1e-3]).  Stops when ||F~ - A u|| <= rtol ||F~|| (free rows)
  * or after max_iter iterations (total inner iterations).  u_out: host, n_vert values (free
  * nodes: W; constrained nodes: g).  iters, final_rel_res may be NULL.  The solve runs on the
  * stream of the matrix's mesh; when that stream can be captured (any stream but the legacy
