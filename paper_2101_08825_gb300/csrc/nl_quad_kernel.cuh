@@ -81,7 +81,7 @@ struct QParams {
                               // [4] closed-form items, [5] band pairs
   int* err;
   double delta, dme, dpe, C, inv_eps, inv_delta2;
-  float fdelta, finv_eps, fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
+  float fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
   float fmqe, ftqe, fue;     // -1/(4 eps), 3/(4 eps), (1 - delta/eps)/2 (branch-free mollifier)
   float fint2, fnotint2;     // screen thresholds (delta - eps -+ margin)^2 (-1: never)
   int L_min, L_max, scap, count_band;
@@ -291,16 +291,6 @@ __device__ __forceinline__ double mollifier(const QParams& P, double r2) {
   if (r2 > dpe2) return 0.0;
   double r = sqrt(r2);
   return xi_poly((P.delta - r) * P.inv_eps);
-}
-__device__ __forceinline__ float mollifier(const QParams& P, float r2) {
-  if (r2 < P.fdme2) return 1.f;
-  if (r2 > P.fdpe2) return 0.f;
-  // r = sqrt(r2): hardware reciprocal square root, then one Newton step on r^2 - r2 = 0
-  // (r <- r + (r2 - r^2) / (2r)), which brings r to about one ulp
-  const float q = rsqrtf(r2);
-  float r = r2 * q;
-  r = fmaf(0.5f * q, fmaf(-r, r, r2), r);
-  return xi_poly((P.fdelta - r) * P.finv_eps);
 }
 
 // ---- packed FP32 pairs (sm_100 family: add/sub/mul/fma .f32x2, one instruction for two
@@ -1638,8 +1628,6 @@ inline nl_status fill_qparams(const char* who, const nl_mesh* m, const nl_pairs*
   P->fC = (float)C;
   P->inv_eps = 1.0 / kp->eps;
   P->inv_delta2 = 1.0 / (kp->delta * kp->delta);
-  P->fdelta = (float)kp->delta;
-  P->finv_eps = (float)(1.0 / kp->eps);
   P->fdme = (float)P->dme;
   P->fdpe = (float)P->dpe;
   P->fdme2 = (float)(P->dme * P->dme);
