@@ -310,7 +310,7 @@ def run_ours(args, rank, world, local):
         # identical up to the rounding of r at the band edges); peak = the measured FP64 FMA
         # chain of this GPU model, 1.19 TFLOP/s
         st64 = last64["st"]
-        f64_flops = float(st64.n_eval_point_pairs * ((5 if mesh.dim == 2 else 8) + 2 + 2 * mesh.dim)
+        f64_flops = float(st64.n_eval_point_pairs * (14 if mesh.dim == 2 else 19)
                           + max(0, stb.n_band_point_pairs) * 15)
         k64_avg = statistics.mean(k64)
         fp64["roofline"] = {"bound": "fp64 pipe", "achieved": round(f64_flops / (k64_avg / 1e3) / 1e12, 4),
@@ -364,14 +364,17 @@ def run_ours(args, rank, world, local):
 
 
 def roofline_flops(dim, st):
-    """Algorithmic FP32 flops of one assembly launch (FMA = 2).  Per point pair evaluated one
-    by one: the squared distance (2D 5, 3D 8), the weight product (1) and the accumulation
-    into g and the dim barycentric moments (1 + 2*dim); per band point pair additionally
-    r = r2*rsqrt(r2) (1), s = (delta - r)/eps (2) and xi(s) by Horner (12).  Sub-elements
-    summed in closed form and the per-item set-up are not counted."""
+    """Algorithmic flops of one assembly launch (FMA = 2), per point pair of the method's
+    double sum as written (eqs. J21Nr, J22Nr): the distance and r^2 (2D 5, 3D 8), the weight
+    w_x w_y C mu (2), the rank-one update of the local block over the nodes of m (2D 6, 3D 8)
+    and the self-term sum (1): 14 (2D) / 19 (3D); per band point pair additionally r (1),
+    s = (delta - r)/eps (2) and xi(s) by Horner (12): 15.  Counted over the point pairs the
+    kernel evaluates one by one; sub-elements summed in closed form are not counted.  (The
+    kernel itself hoists the contraction with m's basis out of the loop over outer points and
+    executes 11 (2D) / 16 (3D) flops per point pair for the same sums.)"""
     ev = max(0, int(getattr(st, "n_eval_point_pairs", 0) or 0))
     band = max(0, int(getattr(st, "n_band_point_pairs", 0) or 0))
-    per_pp = (5 if dim == 2 else 8) + 1 + 1 + 2 * dim
+    per_pp = 14 if dim == 2 else 19
     return float(ev * per_pp + band * 15)
 
 
