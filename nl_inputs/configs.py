@@ -63,6 +63,11 @@ def table2_tri(ml: int) -> Workload:
                     ms=MS_CUBIC, layer_cells=2 * s)
 
 
+def table3_tri(ml: int) -> Workload:
+    """Sec. 6, Table 3: the setting of Table 2 with u = x^4 + y^4."""
+    return table2_tri(ml).with_(name=f"table3_tri_ml{ml}", ms=MS_QUARTIC)
+
+
 _H2 = 1.0 / 256.0
 WORKLOADS = {
     # 2D, h = 1/16, delta = 0.1, eps = delta/10, 3 levels, u = x^2 + y^2

@@ -12,7 +12,7 @@ from scipy import integrate
 
 import oracle as O
 from nl_inputs import structured_mesh, workload_mesh, WORKLOADS
-from nl_inputs.configs import table2_tri
+from nl_inputs.configs import table2_tri, table3_tri
 
 
 # ---- Sec. 3, eq. (mollifier) ----------------------------------------------------------
@@ -515,6 +515,26 @@ def test_table2_tri_linear_errors(ml):
     w = table2_tri(ml)
     r = O.solve_problem(workload_mesh(w), w.delta, w.eps, w.L_max, w.ms)
     # printed with 4 significant digits; the mesh diagonal direction is not stated
+    assert abs(r["err_all"] / gold[ml] - 1) < 2e-3, r["err_all"]
+
+
+def _golden(name):
+    import os
+    rows = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        if line.strip() and not line.startswith("#"):
+            parts = line.split()
+            rows[int(parts[0])] = float(parts[1])
+    return rows
+
+
+@pytest.mark.parametrize("ml", [2, 3])
+def test_table3_tri_linear_quartic_errors(ml):
+    # the quartic solution's forcing carries the kernel's fourth moment (f = -L_eps u), so
+    # the printed errors pin that term as well (without it the error at ml = 2 moves by 34 %)
+    gold = _golden("table3_tri_linear_quartic.txt")
+    w = table3_tri(ml)
+    r = O.solve_problem(workload_mesh(w), w.delta, w.eps, w.L_max, w.ms)
     assert abs(r["err_all"] / gold[ml] - 1) < 2e-3, r["err_all"]
 
 
