@@ -6,8 +6,10 @@
 // aprx-min-dist < delta + eps has centres less than s apart on every axis and lies in
 // neighbouring cells.  A count pass (one warp per inner element m) is followed by a scan
 // and a fill pass (one CTA per m) that collects, sorts (bitonic, in shared memory) and
-// writes the l of every pair of m.  The box test is the exact FP64 expression of
-// eq. (mindist), so the list is bit-identical to a plain evaluation.
+// writes the l of every pair of m.  The box test is screened in FP32 on boxes rounded
+// outwards and decided by the exact FP64 expression of eq. (mindist) wherever the screened
+// distance lies within a margin of the threshold, so the list is bit-identical to a plain
+// FP64 evaluation.
 //
 // Pattern: row i holds the nodes of every l with (m, l) in J and i a node of m.  One CTA
 // per row gathers the union of the l over the elements m around i in a shared-memory hash
