@@ -19,10 +19,12 @@
 // buffer is integrated by the whole warp: each lane owns one outer point x and 7 inner points
 // y kept in registers (3D: two half-warps share x and take y 0-6 and 7-13), and accumulates
 // per y the sums g = sum_x w_x C eta mu and h_k = sum_x w_x C eta mu lambda^l_k(x).  At the
-// end of the pair the warp reduces them through a shared-memory transpose and writes the
-// pair's cross block -2 vol_m sum_y w_y B_a(y) H_c(y) (H_0 = g - sum_k h_k, H_c = h_{c-1})
-// to a block buffer; the self block only needs g, which is accumulated over the consecutive
-// pairs of the same m (compensated FP32 or FP64) and added to a per-element block.
+// end of the pair every lane contracts its own inner points into the pair's cross block
+// -2 vol_m sum_y w_y B_a(y) H_c(y) (H_0 = g - sum_k h_k, H_c = h_{c-1}) and its g per inner
+// point, and one warp reduce-scatter (shuffles; 16 values in 2D, 32 in 3D) leaves each entry
+// summed on one lane; the cross block goes to a block buffer, and the self block, which only
+// needs g, is accumulated over the consecutive pairs of the same m (compensated FP32 or FP64)
+// and added to a per-element block.
 // k_scatter (one CTA per inner element m, the rows of m's nodes cached in shared memory)
 // then adds every block to the CSR values with FP64 atomics.
 //
@@ -32,6 +34,7 @@
 // vertices per pair; the classification is screened in FP32, and a decision whose FP32
 // distance lies within a proven margin of its threshold is redone in FP64 on vertices
 // rebuilt from E_l by the same midpoint sequence, so the decisions are those of a plain FP64
+// evaluation.
 //
 // Included by exactly the translation units that launch these kernels; everything here has
 // internal linkage, so each of them gets its own instantiations.
