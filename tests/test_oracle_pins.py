@@ -291,9 +291,10 @@ def test_fully_interior_pairs_closed_form(dim):
         assert st.n_integrations == k * k and st.n_band_pairs == 0
 
 
-def _uniform_local_blocks(Vl, Vm, delta, eps, C, depth):
+def _uniform_local_blocks(Vl, Vm, delta, eps, C, depth, gauss=False):
     """Outer integral over E_l split uniformly `depth` times (7-point rule on every piece),
-    inner 7-point rule on E_m: the blocks 2*S (m x m) and -2*X (m x l) of eqs. J22Nr, J21Nr."""
+    inner 7-point rule on E_m: the blocks 2*S (m x m) and -2*X (m x l) of eqs. J22Nr, J21Nr.
+    gauss: the truncated Gaussian profile exp(-r^2/delta^2) times the mollifier."""
     b, w = O.quad_rule(2)
     tris = [np.array(Vl)]
     for _ in range(depth):
@@ -318,6 +319,8 @@ def _uniform_local_blocks(Vl, Vm, delta, eps, C, depth):
     WY = w * am
     R = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
     MU = np.vectorize(lambda r: O.mu(r, delta, eps))(R)
+    if gauss:
+        MU = MU * np.exp(-(R / delta) ** 2)
     G = WX[:, None] * WY[None, :] * C * MU  # (x, y)
     S = np.einsum("xy,ya,yb->ab", G, b, b)
     Xc = np.einsum("xy,ya,xc->ac", G, b, PL)
@@ -354,6 +357,37 @@ def test_algorithm1_equals_uniform_refinement(offset):
             ref[np.ix_(nm, nm)] += S2
             ref[np.ix_(nm, nl)] += X2
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), L
+
+
+@pytest.mark.parametrize("offset", [0.252, 0.256])
+def test_algorithm1_gaussian_cross_block_equals_uniform_refinement(offset):
+    # Truncated Gaussian kernel, elements farther apart than delta - eps: no sub-element can
+    # be INT, so Algorithm 1 integrates exactly the level-L sub-elements that reach the band
+    # and drops the rest (mu = 0 there); the cross block (m, l) equals uniform refinement to
+    # level L with the Gaussian profile evaluated at every point pair.
+    from nl_inputs.mesh import Mesh
+    Vm = np.array([[0.0, 0.0], [0.06, 0.01], [0.02, 0.05]])
+    Vl = np.array([[offset, 0.02], [offset + 0.05, 0.0], [offset + 0.03, 0.06]])
+    coords = np.concatenate([Vm, Vl]).T.copy()
+    mesh = Mesh(dim=2, coords=coords, conn=np.array([[0, 1, 2], [3, 4, 5]], np.int32),
+                elem_in_omega=np.ones(2, np.uint8), node_free=np.ones(6, np.uint8), h=0.05)
+    delta, eps = 0.2, 0.01
+    gap = min(np.linalg.norm(a - b) for a in Vm for b in Vl)
+    assert delta - eps < gap < delta + eps
+    C = O.kernel_constant(2, O.KERNEL_GAUSS, delta, eps)
+    off, pl = O.pairs(mesh, delta, eps)
+    assert len(pl) == 4
+    rp, col = O.csr(mesh, off, pl)
+    for L in (1, 3, 5):
+        vals, st = O.assemble(mesh, off, pl, rp, col, delta, eps, L, kernel=O.KERNEL_GAUSS)
+        got = _dense(rp, col, vals, 6)
+        for mi, li in ((0, 1), (1, 0)):
+            _, X2 = _uniform_local_blocks((Vm, Vl)[li], (Vm, Vl)[mi], delta, eps, C, L - 1,
+                                          gauss=True)
+            blk = got[np.ix_(np.arange(3) + 3 * mi, np.arange(3) + 3 * li)]
+            assert np.abs(blk - X2).max() <= 1e-12 * np.abs(X2).max(), (L, mi)
+            if L == 5:  # deep enough for outer points to reach the band
+                assert np.abs(X2).max() > 0 and st.n_band_pairs > 0
 
 
 def _bey_children(T):
