@@ -1,0 +1,119 @@
+"""The FP32 screen of Algorithm 1's decisions in the FP32 assembly path (CPU, numpy float32
+emulation): sub-element vertices relative to the first vertex of E_m (the FP64 offset of the
+first vertices rebuilt from float-float pairs, per-element FP32 vertex offsets, FP32
+midpoints), box distances of Sec. 5.1 (eqs. maxdist, mindist) in FP32, compared against
+delta -/+ eps with the margin 2e-5 (delta + eps + 2 max_ext).  Every decision the screen
+takes must equal the FP64 decision on the exact sub-element, at every refinement level up
+to 12, on the workloads' meshes and on a mesh far from the origin."""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+from nl_inputs import structured_mesh
+
+f32 = np.float32
+
+
+def _children(dim):
+    if dim == 2:
+        # (v0, m01, m02), (m01, v1, m12), (m02, m12, v2), (m01, m12, m02); points 3.. = midpoints
+        # m01, m02, m12
+        return [(0, 3, 4), (3, 1, 5), (4, 5, 2), (3, 5, 4)], [(0, 1), (0, 2), (1, 2)]
+    # Bey: x0..x3, then x01, x02, x03, x12, x13, x23 as points 4..9
+    return ([(0, 4, 5, 6), (4, 1, 7, 8), (5, 7, 2, 9), (6, 8, 9, 3), (4, 5, 6, 8), (4, 5, 7, 8),
+             (5, 6, 8, 9), (5, 7, 8, 9)], [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)])
+
+
+def _refine(V, c, dim, dtype):
+    kids, mids = _children(dim)
+    half = dtype(0.5)
+    pts = [V[:, a, :] for a in range(dim + 1)]
+    pts += [((V[:, i, :] + V[:, j, :]) * half).astype(dtype) for i, j in mids]
+    P = np.stack(pts, axis=1)
+    sel = np.array(kids)[c]  # (n, dim+1)
+    return np.take_along_axis(P, sel[:, :, None].repeat(dim, axis=2), axis=1)
+
+
+def _dists(V, lo2, hi2, dtype):
+    lo, hi = V.min(axis=1), V.max(axis=1)
+    d1 = (lo - hi2).astype(dtype)
+    d2 = (lo2 - hi).astype(dtype)
+    sq = np.maximum(d1 * d1, d2 * d2).astype(dtype)
+    s = np.zeros(len(V), dtype)
+    for k in range(V.shape[2]):
+        s = (s + sq[:, k]).astype(dtype)
+    amin = np.maximum(np.maximum(d1, d2).max(axis=1), dtype(0))
+    return s, amin  # squared max-dist, min-dist
+
+
+@pytest.mark.parametrize("dim,cells,h,lo,delta,eps,jitter", [
+    (2, 256, 1 / 256, (0.0, 0.0), 4 / 256, 4 / 256 / 5, 0.1),
+    (2, 64, 1 / 64, (1000.0, -350.0), 4 / 64, 4 / 64 / 20, 0.1),
+    (3, 16, 1 / 16, (0.0, 0.0, 0.0), 0.125, 0.0125, 0.1),
+])
+def test_fp32_screen_decisions_equal_fp64(dim, cells, h, lo, delta, eps, jitter):
+    layer = int(np.ceil((delta + eps) / h - 1e-9))
+    mesh = structured_mesh(dim, (cells,) * dim, h, lo, layer, jitter=jitter, seed=3)
+    X = mesh.coords.T  # (n_vert, dim)
+    EV = X[mesh.conn]  # (n_elem, dim+1, dim) FP64
+    rng = np.random.default_rng(5)
+    max_ext = float((EV.max(axis=1) - EV.min(axis=1)).max())
+    cen = EV.mean(axis=1)
+    tree = cKDTree(cen)
+    n = 4000
+    ms = rng.integers(0, mesh.n_elem, n)
+    near = tree.query_ball_point(cen[ms], delta + eps + 2 * max_ext)
+    ls = np.array([rng.choice(c) for c in near])
+    # per-element FP32 record: vertex offsets and the first vertex as a float-float pair
+    off = (EV[:, 1:, :] - EV[:, :1, :]).astype(f32)
+    v0 = EV[:, 0, :]
+    v0h = v0.astype(f32)
+    v0l = (v0 - v0h.astype(np.float64)).astype(f32)
+    # E_m relative to its first vertex, and its FP64 box
+    Vm32 = np.concatenate([np.zeros((n, 1, dim), f32), off[ms]], axis=1)
+    lo_m32, hi_m32 = Vm32.min(axis=1), Vm32.max(axis=1)
+    lo_m64, hi_m64 = EV[ms].min(axis=1), EV[ms].max(axis=1)
+    # E_l relative to m's first vertex: (hi_l - hi_m) + (lo_l - lo_m), then the offsets
+    Vl0 = ((v0h[ls] - v0h[ms]).astype(f32) + (v0l[ls] - v0l[ms]).astype(f32)).astype(f32)
+    V32 = np.concatenate([Vl0[:, None, :], (Vl0[:, None, :] + off[ls]).astype(f32)], axis=1)
+    V64 = EV[ls].copy()
+    dme, dpe = delta - eps, delta + eps
+    margin = f32(2e-5 * (delta + eps + 2.0 * max_ext))
+    fdme, fdpe = f32(dme), f32(dpe)
+    lo_t, hi_t = float(fdme) - float(margin), float(fdme) + float(margin)
+    fint2 = f32(lo_t * lo_t) if lo_t > 0 else f32(-1)
+    fnotint2 = f32(hi_t * hi_t)
+    decided = checked = 0
+    for level in range(1, 13):
+        if level > 1:
+            c = rng.integers(0, 2 ** dim, n)
+            V32 = _refine(V32, c, dim, f32)
+            V64 = _refine(V64, c, dim, np.float64)
+        fam, fan = _dists(V32, lo_m32, hi_m32, f32)
+        s64, amin64 = _dists(V64, lo_m64, hi_m64, np.float64)
+        amax64 = np.sqrt(s64)
+        is_int, is_ref = amax64 < dme, amin64 < dpe
+        c_int, c_notint = fam < fint2, fam > fnotint2
+        c_ref, c_out = fan < f32(fdpe - margin), fan > f32(fdpe + margin)
+        assert np.all(is_int[c_int]) and not np.any(is_int[c_notint]), level
+        assert np.all(is_ref[c_ref]) and not np.any(is_ref[c_out]), level
+        decided += int((c_int | c_notint).sum() + (c_ref | c_out).sum())
+        # adversarial thresholds placed at each sub-element's own distances: within a few
+        # margins (the screen's window edges) and within FP32 precision (where only the
+        # FP64 test may decide)
+        for scale in (float(margin), 2.0 ** -20 * (delta + eps)):
+            for dist, is_max in ((amax64, True), (amin64, False)):
+                T = dist + rng.uniform(-3, 3, n) * scale
+                fT = T.astype(f32)
+                exact = dist < T
+                if is_max:
+                    lo_t = fT.astype(np.float64) - float(margin)
+                    t2 = np.where(lo_t > 0, (lo_t * lo_t), -1.0).astype(f32)
+                    hi2 = ((fT.astype(np.float64) + float(margin)) ** 2).astype(f32)
+                    yes, no = fam < t2, fam > hi2
+                else:
+                    yes, no = fan < (fT - margin).astype(f32), fan > (fT + margin).astype(f32)
+                assert np.all(exact[yes]) and not np.any(exact[no]), (level, scale, is_max)
+                checked += int((yes | no).sum())
+    assert decided > 0.9 * 2 * 12 * n  # the FP64 fallback is rare
+    assert checked > 0
