@@ -46,3 +46,32 @@ def test_jitter_keeps_the_small_workload_pairs():
         rp, col = O.csr(m, off, pl)
         counts.append((len(pl), len(col)))
     assert counts[0] == counts[1] and counts[0][0] > 0
+
+
+def test_serving_stream_mix_and_reproducibility():
+    # the seeded request stream: reproducible, both dimensions and kernels, Omega element
+    # counts within 1e3..2e5 (2D) / 1e3..1e5 (3D) up to the rounding to whole cells, delta in
+    # [2h, 6h], eps = delta/10, increasing arrival times
+    from nl_inputs.requests import serving_stream
+    a, b = serving_stream(512, seed=0), serving_stream(512, seed=0)
+    assert a == b and serving_stream(512, seed=1) != a
+    dims = {r.dim for r in a}
+    kernels = {r.kernel for r in a}
+    assert dims == {2, 3} and kernels == {0, 1}
+    for r in a:
+        per_cell = 2 if r.dim == 2 else 6
+        omega = per_cell * r.n ** r.dim
+        hi = 2e5 if r.dim == 2 else 1e5
+        assert 0.5e3 <= omega <= 1.6 * hi, r
+        h = 1.0 / r.n
+        assert 2 * h - 1e-12 <= r.delta <= 6 * h + 1e-12 and abs(r.eps - r.delta / 10) < 1e-15
+        assert r.layer * h >= r.delta + r.eps - 1e-12 > (r.layer - 1) * h
+        assert r.n_elem == per_cell * (r.n + 2 * r.layer) ** r.dim
+    t = np.array([r.arrival_s for r in a])
+    assert np.all(np.diff(t) > 0)
+    # log-uniform sizes: the median Omega element count of each dimension lies near the
+    # geometric mean of its range
+    for dim, hi in ((2, 2e5), (3, 1e5)):
+        sizes = [(2 if dim == 2 else 6) * r.n ** dim for r in a if r.dim == dim]
+        gm = math.sqrt(1e3 * hi)
+        assert gm / 3 < float(np.median(sizes)) < gm * 3
