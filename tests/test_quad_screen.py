@@ -117,3 +117,59 @@ def test_fp32_screen_decisions_equal_fp64(dim, cells, h, lo, delta, eps, jitter)
                 checked += int((yes | no).sum())
     assert decided > 0.9 * 2 * 12 * n  # the FP64 fallback is rare
     assert checked > 0
+
+
+@pytest.mark.parametrize("eps_div", [5, 20])
+def test_closed_form_final_items_have_mu_exactly_0_or_1(eps_div):
+    # 2D FINAL sub-elements taken in closed form: every inner point y of m with
+    # |c - y| < delta - eps - R - margin (or > delta + eps + R + margin), c the centroid and
+    # R = rad(E_l) 2^(1-L) (midpoint children are the parent scaled by 1/2), must have all of
+    # the sub-element's quadrature points x within delta - eps (beyond delta + eps) by a
+    # clear gap, so that the FP32 mollifier clamps to exactly 1 (0) at every point pair.
+    import oracle as O
+    delta = 4 / 256
+    eps = delta / eps_div
+    layer = int(np.ceil((delta + eps) * 256 - 1e-9))
+    mesh = structured_mesh(2, (256, 256), 1 / 256, (0.0, 0.0), layer, jitter=0.1, seed=4)
+    EV = mesh.coords.T[mesh.conn]
+    rng = np.random.default_rng(9)
+    max_ext = float((EV.max(axis=1) - EV.min(axis=1)).max())
+    cen_e = EV.mean(axis=1)
+    tree = cKDTree(cen_e)
+    n = 3000
+    ms = rng.integers(0, mesh.n_elem, n)
+    ls = np.array([rng.choice(c) for c in tree.query_ball_point(cen_e[ms], delta + eps + 2 * max_ext)])
+    b, _ = O.quad_rule(2)
+    bf = b.astype(f32)
+    off = (EV[:, 1:, :] - EV[:, :1, :]).astype(f32)
+    v0 = EV[:, 0, :]
+    v0h = v0.astype(f32)
+    v0l = (v0 - v0h.astype(np.float64)).astype(f32)
+    Vm = np.concatenate([np.zeros((n, 1, 2), f32), off[ms]], axis=1)
+    Y = np.einsum("qa,nak->nqk", bf, Vm).astype(f32)  # inner points of m (FP32, relative)
+    Vl0 = ((v0h[ls] - v0h[ms]).astype(f32) + (v0l[ls] - v0l[ms]).astype(f32)).astype(f32)
+    V = np.concatenate([Vl0[:, None, :], (Vl0[:, None, :] + off[ls]).astype(f32)], axis=1)
+    ct = (V.sum(axis=1) * f32(1 / 3)).astype(f32)
+    rad_l = np.sqrt((((V - ct[:, None, :]) ** 2).sum(-1)).max(axis=1)).astype(f32)
+    margin = f32(2e-5 * (delta + eps + 2.0 * max_ext))
+    dme, dpe = f32(delta - eps), f32(delta + eps)
+    n_in = n_out = 0
+    for level in range(1, 5):
+        if level > 1:
+            V = _refine(V, rng.integers(0, 4, n), 2, f32)
+        cen = (V.sum(axis=1) * f32(1 / 3)).astype(f32)
+        rad = (rad_l * f32(2.0 ** (1 - level))).astype(f32)
+        lo = (dme - rad - margin).astype(f32)
+        hi = (dpe + rad + margin).astype(f32)
+        lo2 = np.where(lo > 0, lo * lo, f32(-1)).astype(f32)
+        hi2 = (hi * hi).astype(f32)
+        d2 = (((cen[:, None, :] - Y) ** 2).sum(-1)).astype(f32)  # (n, 7)
+        inside, outside = d2 < lo2[:, None], d2 > hi2[:, None]
+        X = np.einsum("qa,nak->nqk", bf, V).astype(f32)  # outer points of the sub-element
+        r = np.sqrt(((X[:, :, None, :].astype(np.float64) - Y[:, None, :, :]) ** 2).sum(-1))
+        gap = 0.5 * float(margin)
+        assert np.all(r.max(axis=1)[inside] < float(dme) - gap), level
+        assert np.all(r.min(axis=1)[outside] > float(dpe) + gap), level
+        n_in += int(inside.sum())
+        n_out += int(outside.sum())
+    assert n_in > 0 and n_out > 0
