@@ -75,3 +75,12 @@ def test_serving_stream_mix_and_reproducibility():
         sizes = [(2 if dim == 2 else 6) * r.n ** dim for r in a if r.dim == dim]
         gm = math.sqrt(1e3 * hi)
         assert gm / 3 < float(np.median(sizes)) < gm * 3
+
+
+def test_splitmix64_matches_its_published_sequence():
+    # splitmix64 (Steele, Lea, Flood 2014) from state 0 gives 0xE220A8397B1DCDAF,
+    # 0x6E789E6AA1B965F4, 0x06C45D188009454F; the unit doubles are their top 53 bits / 2^53
+    from nl_inputs.mesh import splitmix64_unit
+    u = splitmix64_unit(0, np.arange(3))
+    for got, z in zip(u, (0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F)):
+        assert got == (z >> 11) / 2.0 ** 53
