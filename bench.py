@@ -1,22 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the nonlocal assembly + solve hot path on one GB300 (or N replicas).
 
-One step = the whole path on the 2D workload at scale (Omega = (0,1)^2, h = 1/256,
-141,512 P1 triangles with the layer, delta = 4h, eps = delta/5, L_max = 4, constant kernel,
-vertices jittered by up to 0.1h, seed 0): element-pair search and CSR pattern, Algorithm 1
-assembly, right-hand side with lifting (u = x^2 + y^2, f = -4) and BiCGStab solve to 1e-10,
-with the mesh resident on the device.  The headline runs the FP32 point-pair path with the
-solve in FP32 inside FP64 iterative refinement ("mixed"); the same step in FP64 is measured
-next to it with the solution error of both against the manufactured solution.
+One step = the whole path on the 3D workload at h = 1/32 (Omega = (0,1)^3 with a 4-cell
+layer, 384,000 Kuhn tetrahedra, delta = 3h, eps = delta/10, L_max = 2, constant kernel;
+1.41e9 element pairs, 2.2e12 quad-pt pairs): element-pair search and CSR pattern,
+Algorithm 1 assembly, right-hand side with lifting (u = x^2 + y^2 + z^2, f = -6) and
+BiCGStab solve to 1e-10, with the mesh resident on the device.  The headline runs the FP32
+point-pair path with the solve in FP32 inside FP64 iterative refinement ("mixed"); the same
+step in FP64 is measured next to it with the solution error of both against the manufactured
+solution and the difference of the two matrices.
 
-Beside the headline the JSON line carries: the FP64 step, the roofline of the assembly kernel,
-the public-API end-to-end rate from host buffers (e2e), a batching leg (128 small problems:
+Beside the headline the JSON line carries: the FP64 step, the roofline of the assembly kernel
+(FP32 and FP64), the achieved bandwidth of the HBM-bound kernels (scatter, SpMV), the
+public-API end-to-end rate from pinned host buffers (e2e), the 2D workload at h = 1/256 in its
+four (eps, kernel) combinations (mixed and FP64 steps), a batching leg (128 small problems:
 sequential assembly against one plan), a serving leg (the first --serve-requests requests of
-the seeded stream, closed loop and then open loop at 70% load) and the oracle timed on the host
-cores (cpu_baseline).
+the seeded stream, closed loop and then open loop at 70% load) and the oracle timed on all
+host cores on a bounded sample (cpu_baseline).
 
-Output: one JSON line (rank 0).  --impl reference times the plain CPU oracle on a bounded
-sample of the same workload instead.  Under torchrun every rank runs its own replica.
+Output: one JSON line (rank 0).  --impl reference times the plain CPU oracle on bounded
+samples of the same workload instead.  Under torchrun every rank runs its own replica.
 """
 from __future__ import annotations
 
@@ -37,14 +40,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("element pairs/s & quad-pt pairs/s, mixed vs FP64 at equal error; "
           "p50/p99 solve ms")
-WORKLOAD = "c2_2d"
+WORKLOAD = "c4_3d"
+C2_BLOCK = ["c2_2d", "c2_2d_eps20", "c2_2d_gauss", "c2_2d_gauss_eps20"]
 
 # DRAM traffic of the FP32 assembly kernel per element pair: dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of the current kernel version on a small case of the
-# same dimension (profiles/k_quad_2d_fp32_c2_h128.md) divided by its element pairs.  Almost all
-# of it is the block buffer, written once per pair, so it scales with the pairs of a launch.
-# None: no capture of the current version (3D: profiles/k_quad_3d_fp32_c3.md holds the counters
-# of the version before the saturating mollifier).
+# same dimension (profiles/k_quad_2d_fp32_c2_h128.md, profiles/k_quad_3d_fp32_c3_h10.md)
+# divided by its element pairs.  Almost all of it is the block buffer, written once per pair,
+# so it scales with the pairs of a launch.  None: no capture of the current version.
 TRAFFIC_BYTES_PER_PAIR = {2: 35.66, 3: None}
 
 
@@ -54,9 +57,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=2,
-                    help="timed FP64 steps beside the mixed ones (0 = leave the FP64 path out)")
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="timed FP64 steps of the headline workload (0 = leave the FP64 path out)")
+    ap.add_argument("--c2-steps", type=int, default=5,
+                    help="timed mixed steps per combination of the 2D block (0 = skip the block)")
+    ap.add_argument("--c2-fp64-steps", type=int, default=1,
+                    help="timed FP64 steps per combination of the 2D block")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="wall seconds of the oracle sample on all host cores")
+    ap.add_argument("--ref-step-seconds", type=float, default=3.0,
+                    help="--impl reference: wall seconds of one step's oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--serve-requests", type=int, default=16,
@@ -66,13 +77,21 @@ def parse():
     ap.add_argument("--batch-problems", type=int, default=128,
                     help="small problems of the batching leg (0 = skip)")
     ap.add_argument("--profile", action="store_true",
-                    help="one pair build and one FP32 and one FP64 assembly of a small workload "
-                         "(--profile-workload, default the 2D workload at h=1/128) for ncu, "
-                         "then exit")
+                    help="one pair build and one FP32 (and FP64) assembly of a small workload "
+                         "(--profile-workload) for ncu, then exit")
     ap.add_argument("--profile-workload", default="c2_2d_h128")
     ap.add_argument("--profile-fp64", type=int, default=1,
                     help="with --profile: also run the FP64 assembly (0 = FP32 only)")
     return ap.parse_args()
+
+
+def measured_peaks():
+    """MEASURED_PEAKS.json (HBM copy GB/s, cuBLAS BF16 TFLOP/s) when present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 # ---- distributed plumbing -------------------------------------------------------------------
@@ -182,7 +201,8 @@ def describe(w, mesh):
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
     return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} P1 {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
-            f"L_max={w.L_max}, {kern} kernel, jitter {w.jitter:g}h seed {w.seed}; "
+            f"layer {w.layer} cells, L_max={w.L_max}, {kern} kernel, jitter {w.jitter:g}h "
+            f"seed {w.seed}; "
             f"u=sum x_k^2; BiCGStab to 1e-10")
 
 
@@ -209,6 +229,119 @@ def l2_err_omega(mesh, u_h, rule):
 
 # ---- our implementation ----------------------------------------------------------------------
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
+FP64_PEAK_TFLOPS = 1.19  # measured FP64 FMA chain of this GPU model
+
+
+def _measure(nl, torch, stream, dmesh, mesh, w, prec, steps, warmup, flush, world,
+             keep_last=False):
+    """Times `steps` whole steps (pairs, pattern, assembly, right-hand side, BiCGStab) after
+    `warmup` untimed ones; the L2 is flushed before every timed step, outside the timing.
+    Returns per-step times, solve times, the last step's stats, solution and (keep_last)
+    the last matrix, and the launches of this library in the timed region."""
+    g = u_exact(mesh)
+    f_const = -2.0 * mesh.dim
+    sprec = nl.NL_PREC_FP64 if prec == nl.NL_PREC_FP64 else nl.NL_PREC_FP32
+
+    def step():
+        p = nl.nl_pairs_build(dmesh, w.delta, w.eps)
+        A, st = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec)
+        b = nl.nl_rhs(dmesh, A, g, f_const=f_const)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        u, it, rr, _ = nl.nl_solve(A, b, g, solver=1, rtol=1e-10, max_iter=20000, precision=sprec)
+        t1.record(stream)
+        t1.synchronize()
+        return dict(st=st, u=u, it=it, rr=rr, solve_ms=t0.elapsed_time(t1), A=A, p=p)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times, solve_ms, stats, last = [], [], [], None
+    launches0 = nl.lib().nl_launch_count()
+    for k in range(steps):
+        if last is not None:
+            last.pop("A", None)
+            last.pop("p", None)
+        flush.zero_()  # L2 flush (256 MB > 129 MB L2) between steps, outside the timing
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step()
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        solve_ms.append(last["solve_ms"])
+        stats.append(last["st"])
+    launches = nl.lib().nl_launch_count() - launches0
+    A = last.pop("A")
+    last.pop("p")
+    if keep_last:
+        last["values"] = A.export()
+    del A
+    return dict(times=times, solve_ms=solve_ms, stats=stats, last=last, launches=launches)
+
+
+def _roofline(nl, dmesh, mesh, w, prec, stats):
+    """Algorithmic flops of the assembly kernel over the measured steps against the FP32 ALU
+    (or FP64 pipe) peak; the band count comes from one extra untimed launch with
+    NL_QUAD_COUNT_BAND."""
+    pb = nl.nl_pairs_build(dmesh, w.delta, w.eps)
+    _, stb = nl.nl_assemble(dmesh, pb, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec,
+                            count_band=True)
+    flops = roofline_flops(mesh.dim, stb)
+    quad_ms = statistics.mean(s.ms_quad for s in stats)
+    f32 = prec != nl.NL_PREC_FP64
+    peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+    achieved = flops / (quad_ms / 1e3) / 1e12
+    rtype = "float" if f32 else "double"
+    return stb, {
+        "bound": "alu" if f32 else "fp64 pipe", "achieved": round(achieved, 3),
+        "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+        "kernel": f"k_quad<{mesh.dim},{rtype},{w.kernel}>", "flops_per_assembly": flops,
+        "kernel_ms_per_assembly": round(quad_ms, 3),
+        "launches_per_assembly": int(stats[-1].n_quad_launches),
+        "peak_source": ("152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)" if f32 else
+                        "FP64 FMA-chain microbenchmark on GB300 (measured)")}
+
+
+def _scatter_bytes(mesh, pairs_info, rp, dim, rsize):
+    """Algorithmic bytes of the scatter over one assembly: every cross block read once (with
+    its pair_l entry and l's nodes), and per inner element the rows of its nodes: their
+    column lists read and their values updated (FP64 read + write) once."""
+    n_pairs = pairs_info[0]
+    nv = dim + 1
+    deg = np.bincount(mesh.conn.ravel(), minlength=mesh.n_vert)
+    rowlen = np.diff(rp)
+    per_elem_rows = int(np.sum(deg.astype(np.int64) * rowlen))
+    return int(n_pairs * (nv * nv * rsize + 4 + 4 * nv) + per_elem_rows * (4 + 16))
+
+
+def _spmv_rate(nl, torch, stream, A, mesh, nnz, reps=20):
+    """nl_matrix_apply (FP64 y = A x over all rows): CUDA-event time per call and achieved
+    HBM bandwidth for the algorithmic bytes (values 8 + col 4 per entry, row_ptr, x and y
+    once)."""
+    x = torch.rand(mesh.n_vert, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    A.apply(x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        A.apply(x.data_ptr(), y.data_ptr())
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    byts = 12 * nnz + 8 * (mesh.n_vert + 1) + 16 * mesh.n_vert
+    return {"kernel": "k_spmv<double,double>", "ms": round(ms, 4), "bytes": int(byts),
+            "achieved_gbs": round(byts / (ms / 1e3) / 1e9, 1)}
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2101_08825_gb300 import nl
@@ -220,109 +353,73 @@ def run_ours(args, rank, world, local):
     barrier(world)
     nl.lib()
     stream = torch.cuda.current_stream()
-    w, mesh = workload(args.workload)
-    delta, eps, L_max = w.delta, w.eps, w.L_max
-    g = u_exact(mesh)
-    f_const = -2.0 * mesh.dim
-    rule = nl.nl_quad_rule(mesh.dim)
     flush = torch.empty(int(256 * 2 ** 20) // 4, dtype=torch.float32, device="cuda")
+    peaks = measured_peaks()
 
+    w, mesh = workload(args.workload)
+    rule = nl.nl_quad_rule(mesh.dim)
     dmesh = nl.mesh_from(mesh)
-
-    def step(prec, keep=False):
-        p = nl.nl_pairs_build(dmesh, delta, eps)
-        A, st = nl.nl_assemble(dmesh, p, delta, eps, L_max, precision=prec)
-        b = nl.nl_rhs(dmesh, A, g, f_const=f_const)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        u, it, rr, _ = nl.nl_solve(A, b, g, solver=1, rtol=1e-10, max_iter=20000,
-                                   precision=nl.NL_PREC_FP32 if prec != nl.NL_PREC_FP64 else nl.NL_PREC_FP64)
-        t1.record(stream)
-        t1.synchronize()
-        res = dict(st=st, u=u, it=it, rr=rr, solve_ms=t0.elapsed_time(t1))
-        if keep:
-            res["A"] = A.export()
-        return res
-
-    def timed(prec, steps, warmup):
-        for _ in range(warmup):
-            step(prec)
-        torch.cuda.synchronize()
-        times, solve_ms, kern_ms, last = [], [], [], None
-        launches0 = nl.lib().nl_launch_count()
-        for _ in range(steps):
-            flush.zero_()  # L2 flush (256 MB > 129 MB L2) between steps, outside the timing
-            barrier(world)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            last = step(prec)
-            e1.record(stream)
-            e1.synchronize()
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-            solve_ms.append(last["solve_ms"])
-            kern_ms.append(last["st"].ms_assemble)
-        launches = nl.lib().nl_launch_count() - launches0
-        return times, solve_ms, kern_ms, last, launches
 
     # mixed headline (timed with clock sampling)
     clk = ClockSampler(local)
     clk.start()
-    times, solve_ms, kern_ms, last, launches = timed(nl.NL_PREC_FP32, args.steps, args.warmup)
+    mx = _measure(nl, torch, stream, dmesh, mesh, w, nl.NL_PREC_FP32, args.steps, args.warmup,
+                  flush, world, keep_last=args.fp64_steps > 0)
     clocks = clk.stop()
-    ms = statistics.mean(times)
+    ms = statistics.mean(mx["times"])
     ms_max = allmax(world, ms)
-    st = last["st"]
+    st = mx["stats"][-1]
     n_pairs, n_pp = st.n_pairs, st.n_point_pairs
     value = world * n_pairs / (ms_max / 1e3)
-    err_mixed = l2_err_omega(mesh, last["u"], rule)
+    err_mixed = l2_err_omega(mesh, mx["last"]["u"], rule)
+    kern_ms = statistics.mean(s.ms_assemble for s in mx["stats"])
+    stb, roof = _roofline(nl, dmesh, mesh, w, nl.NL_PREC_FP32, mx["stats"])
+    tb = TRAFFIC_BYTES_PER_PAIR.get(mesh.dim)
+    roof["traffic"] = round(tb * n_pairs / roof["launches_per_assembly"]) if tb else None
+    roof["traffic_per_launch_note"] = ("DRAM bytes per element pair of the ncu capture of the "
+                                       "current kernel on the small case of this dimension, "
+                                       "times the pairs of one launch")
 
-    # FP64 path, same step (--fp64-steps 0 leaves it out, e.g. for the 3D h = 1/32 workload,
-    # whose FP64 assembly takes minutes)
+    # the FP64 step on the same workload (the FP64 kernels are warmed on a tiny case first)
     fp64 = None
     if args.fp64_steps > 0:
-        t64, s64, k64, last64, _ = timed(nl.NL_PREC_FP64, args.fp64_steps, 1)
-        ms64 = statistics.mean(t64)
-        err64 = l2_err_omega(mesh, last64["u"], rule)
-        # matrix difference mixed vs FP64 (one extra untimed assembly each)
-        r32 = step(nl.NL_PREC_FP32, keep=True)["A"]
-        r64 = step(nl.NL_PREC_FP64, keep=True)["A"]
-        a_rel = float(np.linalg.norm(r32 - r64) / np.linalg.norm(r64))
-        fp64 = {"dtype": "f64", "ms_per_step": round(ms64, 3),
+        wc1, mc1 = workload("c1_2d" if mesh.dim == 2 else "c3_3d_h10")
+        dc1 = nl.mesh_from(mc1)
+        _measure(nl, torch, stream, dc1, mc1, wc1, nl.NL_PREC_FP64, 1, 0, flush, world)
+        del dc1
+        f64 = _measure(nl, torch, stream, dmesh, mesh, w, nl.NL_PREC_FP64, args.fp64_steps, 0,
+                       flush, world, keep_last=True)
+        ms64 = allmax(world, statistics.mean(f64["times"]))
+        err64 = l2_err_omega(mesh, f64["last"]["u"], rule)
+        v32, v64 = mx["last"]["values"], f64["last"]["values"]
+        a_rel = float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64))
+        a_max = float(np.abs(v32 - v64).max() / np.abs(v64).max())
+        _, roof64 = _roofline(nl, dmesh, mesh, w, nl.NL_PREC_FP64, f64["stats"])
+        fp64 = {"dtype": "f64", "ms_per_step": round(ms64, 3), "steps": args.fp64_steps,
                 "value": round(world * n_pairs / (ms64 / 1e3), 1),
-                "assembly_kernel_ms": round(statistics.mean(k64), 3), "l2_err_omega": err64}
+                "assembly_ms": round(statistics.mean(s.ms_assemble for s in f64["stats"]), 3),
+                "l2_err_omega": err64, "roofline": roof64}
+        mx["last"].pop("values", None)
 
-    # roofline of the dominant kernel (FP32 assembly kernel): algorithmic flops per launch;
-    # the band count comes from one extra untimed launch with NL_QUAD_COUNT_BAND
-    kern_avg = statistics.mean(kern_ms)
-    pb = nl.nl_pairs_build(dmesh, delta, eps)
-    _, stb = nl.nl_assemble(dmesh, pb, delta, eps, L_max, precision=nl.NL_PREC_FP32,
-                            count_band=True)
-    flops = roofline_flops(mesh.dim, stb)
-    peak_tflops = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 lanes x 2 flops x max SM clock
-    achieved = flops / (kern_avg / 1e3) / 1e12
-    if fp64 is not None:
-        # the FP64 assembly kernel against the FP64 pipe: same algorithmic count with the FP64
-        # launch's own evaluated point pairs (its band pairs: those of the FP32 count launch,
-        # identical up to the rounding of r at the band edges); peak = the measured FP64 FMA
-        # chain of this GPU model, 1.19 TFLOP/s
-        st64 = last64["st"]
-        f64_flops = float(st64.n_eval_point_pairs * (14 if mesh.dim == 2 else 19)
-                          + max(0, stb.n_band_point_pairs) * 15)
-        k64_avg = statistics.mean(k64)
-        fp64["roofline"] = {"bound": "fp64 pipe", "achieved": round(f64_flops / (k64_avg / 1e3) / 1e12, 4),
-                            "peak": 1.19, "unit": "TFLOP/s",
-                            "frac": round(f64_flops / (k64_avg / 1e3) / 1.19e12, 4),
-                            "kernel": f"k_quad<{mesh.dim},double,{w.kernel}>"}
-    roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 1),
-            "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-            "traffic": (round(TRAFFIC_BYTES_PER_PAIR[mesh.dim] * n_pairs)
-                        if TRAFFIC_BYTES_PER_PAIR.get(mesh.dim) else None),
-            "kernel": f"k_quad<{mesh.dim},float,{w.kernel}>", "flops_per_launch": flops,
-            "kernel_ms_avg": round(kern_avg, 3)}
+    # HBM-bound kernels of the step: the scatter (from the assembly's own CUDA events) and the
+    # SpMV (nl_matrix_apply, FP64)
+    p = nl.nl_pairs_build(dmesh, w.delta, w.eps)
+    pinfo = p.info()
+    rp = p.export(mesh.n_elem, mesh.n_vert)[2]
+    sc_bytes = _scatter_bytes(mesh, pinfo, rp, mesh.dim, 4)
+    sc_ms = statistics.mean(s.ms_scatter for s in mx["stats"])
+    A, _ = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, nl.NL_PREC_FP32)
+    hbm_peak = peaks.get("hbm_gbs", 6746.0)
+    spmv = _spmv_rate(nl, torch, stream, A, mesh, pinfo[1])
+    spmv["frac"] = round(spmv["achieved_gbs"] / hbm_peak, 4)
+    hbm = {"peak_gbs": hbm_peak, "peak_source": "measured STREAM-style copy",
+           "scatter": {"kernel": f"k_scatter<{mesh.dim},float>", "ms_per_assembly": round(sc_ms, 3),
+                       "bytes": sc_bytes,
+                       "achieved_gbs": round(sc_bytes / (sc_ms / 1e3) / 1e9, 1) if sc_ms > 0 else None,
+                       "frac": round(sc_bytes / (sc_ms / 1e3) / 1e9 / hbm_peak, 4) if sc_ms > 0 else None,
+                       "bound": "FP64 atomics (shared, then global)"},
+           "spmv": spmv}
+    del A, p
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": "element pairs/s", "n_gpus": world,
@@ -333,39 +430,82 @@ def run_ours(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "working set > L2 and a 256 MB L2 flush between steps"},
         "quad_pt_pairs_per_s": round(world * n_pp / (ms_max / 1e3), 1),
-        "assembly_kernel": {"ms": round(kern_avg, 3),
-                            "element_pairs_per_s": round(n_pairs / (kern_avg / 1e3), 1),
-                            "quad_pt_pairs_per_s": round(n_pp / (kern_avg / 1e3), 1)},
+        "assembly": {"ms": round(kern_ms, 3), "kernel_ms": roof["kernel_ms_per_assembly"],
+                     "element_pairs_per_s": round(n_pairs / (kern_ms / 1e3), 1),
+                     "quad_pt_pairs_per_s": round(n_pp / (kern_ms / 1e3), 1)},
         "counts": {"element_pairs": n_pairs, "quad_pt_pairs": n_pp, "items": st.n_items,
                    "fp64_rechecks": st.n_exact_checks,
                    "evaluated_point_pairs": stb.n_eval_point_pairs,
                    "band_point_pairs": stb.n_band_point_pairs,
-                   "closed_form_items": stb.n_closed_items},
+                   "closed_form_items": stb.n_closed_items, "nnz": int(pinfo[1])},
         "fp64": fp64,
-        "mixed": {"l2_err_omega": err_mixed,
+        "mixed": {"l2_err_omega": err_mixed, "precision_run": int(st.precision_run),
                   "A_rel_frobenius_vs_fp64": a_rel if fp64 else None,
-                  "solve_iters": last["it"],
+                  "A_max_entry_rel_vs_fp64": a_max if fp64 else None,
+                  "solve_iters": mx["last"]["it"],
                   "speedup_vs_fp64": round(ms64 / ms, 2) if fp64 else None},
-        "solve_ms": {"p50": round(float(np.percentile(solve_ms, 50)), 3),
-                     "p99": round(float(np.percentile(solve_ms, 99)), 3)},
+        "solve_ms": {"p50": round(float(np.percentile(mx["solve_ms"], 50)), 3),
+                     "p99": round(float(np.percentile(mx["solve_ms"], 99)), 3)},
         "roofline": roof,
-        "gpu_launches": int(launches),  # this library's kernels in the whole timed region
-        "gpu_launches_per_step": int(launches / max(1, args.steps)),
+        "hbm_kernels": hbm,
+        "gpu_launches": int(mx["launches"]),  # this library's kernels in the whole timed region
+        "gpu_launches_per_step": int(mx["launches"] / max(1, args.steps)),
         "clocks": clocks,
     }
+    del dmesh
     if not args.no_e2e:
-        out["e2e"] = e2e_ours(args, mesh, w, g, f_const, stream, world)
+        out["e2e"] = e2e_ours(args, mesh, w, stream, world)
+    if args.c2_steps > 0:
+        out["c2_2d"] = run_c2_block(args, nl, torch, stream, flush, world)
     if args.batch_problems > 0:
         out["batching"] = run_batching(args)
     if args.serve_requests > 0:
         out["serving"] = run_serving(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(mesh, w, seconds=15.0)
+        out["cpu_baseline"] = cpu_baseline(mesh, w, seconds=args.cpu_seconds)
+    return out
+
+
+def run_c2_block(args, nl, torch, stream, flush, world):
+    """The 2D workload at h = 1/256 in its four (eps, kernel) combinations: mixed step and
+    FP64 step with the L2 errors of both, and the FP32 kernel's roofline."""
+    out = {}
+    for name in C2_BLOCK:
+        w, mesh = workload(name)
+        rule = nl.nl_quad_rule(2)
+        dm = nl.mesh_from(mesh)
+        mx = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP32, args.c2_steps, 2, flush,
+                      world, keep_last=args.c2_fp64_steps > 0)
+        ms = statistics.mean(mx["times"])
+        st = mx["stats"][-1]
+        _, roof = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP32, mx["stats"])
+        tb = TRAFFIC_BYTES_PER_PAIR.get(2)
+        roof["traffic"] = round(tb * st.n_pairs / roof["launches_per_assembly"]) if tb else None
+        r = {"workload": describe(w, mesh), "element_pairs": st.n_pairs,
+             "quad_pt_pairs": st.n_point_pairs, "ms_per_step": round(ms, 3),
+             "element_pairs_per_s": round(st.n_pairs / (ms / 1e3), 1),
+             "quad_pt_pairs_per_s": round(st.n_point_pairs / (ms / 1e3), 1),
+             "assembly_ms": round(statistics.mean(s.ms_assemble for s in mx["stats"]), 3),
+             "l2_err_omega": l2_err_omega(mesh, mx["last"]["u"], rule),
+             "solve_ms_p50": round(float(np.percentile(mx["solve_ms"], 50)), 3),
+             "roofline": roof}
+        if args.c2_fp64_steps > 0:
+            f64 = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP64, args.c2_fp64_steps, 0,
+                           flush, world, keep_last=True)
+            ms64 = statistics.mean(f64["times"])
+            v32, v64 = mx["last"]["values"], f64["last"]["values"]
+            r["fp64"] = {"ms_per_step": round(ms64, 3),
+                         "element_pairs_per_s": round(st.n_pairs / (ms64 / 1e3), 1),
+                         "l2_err_omega": l2_err_omega(mesh, f64["last"]["u"], rule),
+                         "speedup_of_mixed": round(ms64 / ms, 2),
+                         "A_rel_frobenius": float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64))}
+        out[name] = r
+        del dm
     return out
 
 
 def roofline_flops(dim, st):
-    """Algorithmic flops of one assembly launch (FMA = 2), per point pair of the method's
+    """Algorithmic flops of one assembly (FMA = 2), per point pair of the method's
     double sum as written (eqs. J21Nr, J22Nr): the distance and r^2 (2D 5, 3D 8), the weight
     w_x w_y C mu (2), the rank-one update of the local block over the nodes of m (2D 6, 3D 8)
     and the self-term sum (1): 14 (2D) / 19 (3D); per band point pair additionally r (1),
@@ -379,9 +519,10 @@ def roofline_flops(dim, st):
     return float(ev * per_pp + band * 15)
 
 
-def e2e_ours(args, mesh, w, g, f_const, stream, world):
+def e2e_ours(args, mesh, w, stream, world):
     """Public-API step from pinned host buffers: mesh upload, pairs, assembly, right-hand
-    side, solve and the solution read back, all inside the timed region."""
+    side, solve and the solution read back, all inside the timed region (one warm-up step,
+    then up to three timed ones)."""
     import torch
     from paper_2101_08825_gb300 import nl
 
@@ -390,30 +531,35 @@ def e2e_ours(args, mesh, w, g, f_const, stream, world):
         t.numpy()[...] = a
         return t.numpy()
 
+    g = u_exact(mesh)
+    f_const = -2.0 * mesh.dim
     coords, conn = pinned(mesh.coords), pinned(mesh.conn)
     eio, nf, gp = pinned(mesh.elem_in_omega), pinned(mesh.node_free), pinned(g)
     times = []
-    for k in range(args.warmup + args.steps):
+    steps = max(1, min(args.steps, 3))
+    for k in range(1 + steps):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         dm = nl.nl_mesh_create(mesh.dim, coords, conn, eio, nf)
         p = nl.nl_pairs_build(dm, w.delta, w.eps)
-        A, st = nl.nl_assemble(dm, p, w.delta, w.eps, w.L_max, precision=nl.NL_PREC_FP32)
+        A, st = nl.nl_assemble(dm, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel,
+                               nl.NL_PREC_FP32)
         b = nl.nl_rhs(dm, A, gp, f_const=f_const)
         u, it, rr, _ = nl.nl_solve(A, b, gp, solver=1, rtol=1e-10, max_iter=20000,
                                    precision=nl.NL_PREC_FP32)
         e1.record(stream)
         e1.synchronize()
-        if k >= args.warmup:
+        if k >= 1:
             times.append(e0.elapsed_time(e1))
         n_pairs = st.n_pairs
+        del A, b, p, dm
     ms = allmax(world, statistics.mean(times))
     h2d = coords.nbytes + conn.nbytes + eio.nbytes + nf.nbytes + 2 * gp.nbytes
     d2h = u.nbytes
     return {"value": round(world * n_pairs / (ms / 1e3), 1), "unit": "element pairs/s",
-            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d),
+            "ms_per_step": round(ms, 3), "steps": steps, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h)}
 
 
@@ -515,64 +661,117 @@ def run_serving(args):
                       f"throughput"}
 
 
-# ---- the oracle on a bounded sample ------------------------------------------------------------
+# ---- the oracle on a bounded sample, on all host cores ---------------------------------------
 
-def oracle_sample(mesh, w, n_m, seed=0):
-    """Times the oracle's pair search, pattern and Algorithm 1 assembly for the rows of n_m
-    seeded inner elements of the workload; returns (pairs, point pairs, seconds)."""
+def _oracle_rows(args):
+    """One process of the oracle sample: pairs (brute force), pattern and Algorithm-1
+    assembly restricted to the inner elements `sel` of the workload; returns the pair and
+    point-pair counts."""
+    name, sel = args
     import oracle as O
-    rng = np.random.default_rng(seed)
+    w, mesh = workload(name)
     mask = np.zeros(mesh.n_elem, np.uint8)
-    mask[rng.choice(mesh.n_elem, size=n_m, replace=False)] = 1
+    mask[sel] = 1
     om = O.OMesh(mesh)
-    t0 = time.perf_counter()
     off, pl = O.pairs(om, w.delta, w.eps, m_mask=mask)
     rp, col = O.csr(om, off, pl)
-    vals, st = O.assemble(om, off, pl, rp, col, w.delta, w.eps, w.L_max, w.L_min, w.kernel,
-                          m_mask=mask)
-    dt = time.perf_counter() - t0
-    return len(pl), st.n_point_pairs, dt
+    _, st = O.assemble(om, off, pl, rp, col, w.delta, w.eps, w.L_max, w.L_min, w.kernel,
+                       m_mask=mask)
+    return len(pl), st.n_point_pairs
 
 
-def cpu_baseline(mesh, w, seconds=15.0):
+def _oracle_warm(name):
     import oracle as O
     O.build()
-    n_p, n_pp, dt = oracle_sample(mesh, w, 8)
-    n_m = int(max(8, min(mesh.n_elem, 8 * seconds / max(dt, 1e-3))))
-    n_p, n_pp, dt = oracle_sample(mesh, w, n_m, seed=1)
-    return {"value": round(n_p / dt, 1), "unit": "element pairs/s", "cores": 1, "kind": "oracle",
-            "sample": f"pairs, pattern and Algorithm-1 assembly of the rows of {n_m} seeded "
-                      f"inner elements of the workload ({n_p} element pairs, {n_pp} quad-pt "
-                      f"pairs, {dt:.1f} s single-threaded FP64)",
+    O.lib()
+    workload(name)
+    return os.getpid()
+
+
+class OraclePool:
+    """Spawned worker processes (one per host core) that run the plain single-threaded oracle
+    on disjoint seeded samples of inner elements.  Spawned, never forked: the parent may
+    already hold a CUDA context."""
+
+    def __init__(self, name, procs=None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        import oracle as O
+        O.build()
+        self.name = name
+        self.procs = procs or max(1, os.cpu_count() or 1)
+        self.ex = ProcessPoolExecutor(max_workers=self.procs, mp_context=mp.get_context("spawn"))
+        list(self.ex.map(_oracle_warm, [name] * self.procs))
+        _, mesh = workload(name)
+        self.n_elem = mesh.n_elem
+
+    def run(self, n_m, seed):
+        """Wall time of the oracle on n_m seeded inner elements split over the processes."""
+        rng = np.random.default_rng(seed)
+        sel = np.sort(rng.choice(self.n_elem, size=min(n_m, self.n_elem), replace=False))
+        parts = [p for p in np.array_split(sel, self.procs) if len(p)]
+        t0 = time.perf_counter()
+        res = list(self.ex.map(_oracle_rows, [(self.name, p) for p in parts]))
+        dt = time.perf_counter() - t0
+        return sum(r[0] for r in res), sum(r[1] for r in res), dt, len(parts)
+
+    def calibrate(self, seconds):
+        """Inner elements per call that keep every process busy for about `seconds`."""
+        n_p, n_pp, dt, used = self.run(2 * self.procs, seed=12345)
+        per_m = dt / 2.0
+        return int(max(self.procs, min(self.n_elem, self.procs * seconds / max(per_m, 1e-4))))
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def cpu_baseline(mesh, w, seconds=10.0):
+    pool = OraclePool(w.name)
+    try:
+        n_m = pool.calibrate(seconds)
+        n_p, n_pp, dt, used = pool.run(n_m, seed=1)
+    finally:
+        pool.close()
+    return {"value": round(n_p / dt, 1), "unit": "element pairs/s", "cores": used,
+            "kind": "oracle",
+            "sample": f"pairs (brute force), pattern and Algorithm-1 assembly of the rows of "
+                      f"{n_m} seeded inner elements of {w.name} ({n_p} element pairs, {n_pp} "
+                      f"quad-pt pairs) in {dt:.1f} s wall on {used} processes of the plain "
+                      f"single-threaded FP64 oracle (os.cpu_count() = {os.cpu_count()})",
             "quad_pt_pairs_per_s": round(n_pp / dt, 1)}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    import oracle as O
-    O.build()
     w, mesh = workload(args.workload)
-    n_p, n_pp, dt = oracle_sample(mesh, w, 4)
-    n_m = int(max(4, min(mesh.n_elem, 4 * 6.0 / max(dt, 1e-3))))  # ~6 s per step
-    for _ in range(args.warmup):
-        oracle_sample(mesh, w, max(4, n_m // 8), seed=99)
-    times, pairs = [], []
-    for k in range(args.steps):
-        n_p, n_pp, dt = oracle_sample(mesh, w, n_m, seed=k)
-        times.append(dt)
-        pairs.append(n_p)
+    pool = OraclePool(w.name)
+    try:
+        n_m = pool.calibrate(args.ref_step_seconds)
+        for k in range(args.warmup):
+            pool.run(max(pool.procs, n_m // 8), seed=99 + k)
+        times, pairs, pps = [], [], []
+        for k in range(args.steps):
+            n_p, n_pp, dt, used = pool.run(n_m, seed=k)
+            times.append(dt)
+            pairs.append(n_p)
+            pps.append(n_pp)
+    finally:
+        pool.close()
     value = sum(pairs) / sum(times)
-    sample = (f"each step: pairs, pattern and Algorithm-1 assembly of the rows of {n_m} seeded "
-              f"inner elements of {w.name}")
+    sample = (f"each step: pairs (brute force), pattern and Algorithm-1 assembly of the rows of "
+              f"{n_m} seeded inner elements of {w.name}, split over {used} processes of the "
+              f"plain single-threaded FP64 oracle")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1),
             "unit": "element pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(times), 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": describe(w, mesh), "parallelism": "single CPU core (oracle)",
+            "config": {"workload": describe(w, mesh),
+                       "parallelism": f"{used} host processes (oracle)",
                        "l2": "not applicable (CPU)"},
-            "cpu_baseline": {"value": round(value, 1), "unit": "element pairs/s", "cores": 1,
+            "quad_pt_pairs_per_s": round(sum(pps) / sum(times), 1),
+            "cpu_baseline": {"value": round(value, 1), "unit": "element pairs/s", "cores": used,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 1), "unit": "element pairs/s",
                     "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -96,6 +96,12 @@ typedef struct {
   int64_t n_closed_items;     /* sub-elements summed in closed form (mu = 1, constant kernel) */
   int64_t n_band_point_pairs; /* evaluated point pairs with delta-eps <= r <= delta+eps, when
                                  NL_QUAD_COUNT_BAND was given; -1 otherwise */
+  int32_t precision_run;      /* the nl_precision whose arithmetic ran */
+  int32_t n_quad_launches;    /* launches of the point-pair kernel (the pairs are processed in
+                                 batches that bound the block buffer) */
+  double ms_quad;             /* device time of those launches (CUDA events; 0 in
+                                 nl_assemble_noalloc and nl_plan_sync) */
+  double ms_scatter;          /* device time of the scatter launches (as ms_quad) */
 } nl_assemble_stats;
 
 typedef struct nl_mesh nl_mesh;
@@ -185,8 +191,9 @@ nl_status nl_assemble(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_params* kp
  * lives in a fixed 16 MiB device array that the library holds on every GPU that loads it
  * until the process exits, so the mesh may have at most (16 MiB - 256 B) / (8 (dim+1)^2 B)
  * elements (233,013 triangles or 131,070 tetrahedra); larger meshes return NL_EINVAL.
- * The first call on a device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call clears the scratch it uses
+ * Every call looks up that array's device address in the current context
+ * (cudaGetSymbolAddress); the first lookup in a context may load the library's device code,
+ * so make the first call before any stream capture.  Every call clears the scratch it uses
  * and leaves its contents behind; all calls share the one array, so calls that overlap on
  * the GPU (other streams or threads) race and must be serialised by the caller.
  * stats may be NULL; stats->ms_assemble is 0. */
@@ -195,6 +202,11 @@ nl_status nl_assemble_noalloc(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_pa
                               nl_assemble_stats* stats);
 /* Host copy of the nnz values (CSR order of the pattern). */
 nl_status nl_matrix_export(const nl_matrix* A, double* values);
+/* y = A x over every row, in FP64: the discrete operator of Sec. 2 (eq. A-F) applied to the
+ * nodal vector x.  x and y are device arrays of n_vert doubles owned by the caller (x is read
+ * through the pattern's columns, y written).  Enqueued on the matrix's stream; returns without
+ * waiting.  Errors: NL_EINVAL for NULL arguments or x == y. */
+nl_status nl_matrix_apply(const nl_matrix* A, const double* x, double* y);
 /* Device pointer to the values (valid until nl_matrix_destroy). */
 nl_status nl_matrix_device_values(const nl_matrix* A, double** values);
 void nl_matrix_destroy(nl_matrix* A);

@@ -78,8 +78,13 @@ WORKLOADS = {
     "c2_2d_h128": _unit_box("c2_2d_h128", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1),
     "c2_2d_gauss": _unit_box("c2_2d_gauss", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1,
                              kernel=KERNEL_GAUSS),
+    "c2_2d_gauss_eps20": _unit_box("c2_2d_gauss_eps20", 2, 256, 4 * _H2, 4 * _H2 / 20, 4,
+                                   jitter=0.1, kernel=KERNEL_GAUSS),
     # 3D, h = 1/16, delta = 0.125, eps = delta/10, 2 levels, u = x^2 + y^2 + z^2
     "c3_3d": _unit_box("c3_3d", 3, 16, 0.125, 0.0125, 2),
+    # 3D, h = 1/10, delta = 0.125, eps = delta/10, 2 levels: a small case of the 3D kernel for
+    # profiler captures (12 M pairs, an 0.8 GB block buffer: larger than L2, a few GB at most)
+    "c3_3d_h10": _unit_box("c3_3d_h10", 3, 10, 0.125, 0.0125, 2),
     # 3D, h = 1/32, delta = 3h, eps = delta/10, 2 levels
     "c4_3d": _unit_box("c4_3d", 3, 32, 3.0 / 32, 0.3 / 32, 2),
 }

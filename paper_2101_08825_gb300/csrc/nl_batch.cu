@@ -455,6 +455,10 @@ nl_status nl_plan_sync(nl_plan* pl, nl_assemble_stats* stats) {
       s.n_eval_point_pairs = (int64_t)h[3];
       s.n_closed_items = (int64_t)h[4];
       s.n_band_point_pairs = pl->count_band[k] ? (int64_t)h[5] : -1;
+      s.precision_run = pl->prec != NL_PREC_FP64 ? NL_PREC_FP32 : NL_PREC_FP64;
+      s.n_quad_launches = 1;
+      s.ms_quad = 0.0;
+      s.ms_scatter = 0.0;
     }
   }
   return NL_OK;

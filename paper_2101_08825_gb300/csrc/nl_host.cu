@@ -713,6 +713,13 @@ nl_status nl_assemble(nl_mesh* mesh, nl_pairs* pairs, const nl_kernel_params* kp
   return NL_OK;
 }
 
+nl_status nl_matrix_apply(const nl_matrix* A, const double* x, double* y) {
+  nlx::clear_error();
+  if (!A || !x || !y) return nlx::fail(NL_EINVAL, "nl_matrix_apply: NULL argument");
+  if (x == y) return nlx::fail(NL_EINVAL, "nl_matrix_apply: x and y must not alias");
+  return nlx::apply_matrix(A, x, y);
+}
+
 nl_status nl_matrix_export(const nl_matrix* A, double* values) {
   nlx::clear_error();
   if (!A || !values) return nlx::fail(NL_EINVAL, "nl_matrix_export: NULL argument");

@@ -194,7 +194,8 @@ nl_status build_pairs(nl_mesh* m, double delta, double eps, nl_pairs* out);
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st);
-// Right-hand side and solver kernels (nl_solve.cu).
+// Right-hand side, operator application and solver kernels (nl_solve.cu).
+nl_status apply_matrix(const nl_matrix* A, const double* x, double* y);
 nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_const,
                      const double* g_nodes, double* F);
 nl_status solve_system(nl_matrix* A, const nl_vector* rhs, const double* g_nodes, int solver,

@@ -6,7 +6,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -23,9 +22,36 @@ nl_status ensure_device_tables() {
 }
 
 namespace {
+// CUDA events around every launch of the assembly kernel and of the scatter, read after the
+// assembly's final synchronisation.
+struct PhaseTimer {
+  std::vector<cudaEvent_t> ev[2];
+  ~PhaseTimer() {
+    for (auto& v : ev)
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+  }
+  nl_status mark(int phase, cudaStream_t s) {
+    cudaEvent_t e;
+    NL_CUDA(cudaEventCreate(&e));
+    ev[phase].push_back(e);
+    NL_CUDA(cudaEventRecord(e, s));
+    return NL_OK;
+  }
+  // summed elapsed time of the (start, end) pairs of one phase, after synchronisation
+  double ms(int phase) const {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < ev[phase].size(); i += 2) {
+      float x = 0.f;
+      if (cudaEventElapsedTime(&x, ev[phase][i], ev[phase][i + 1]) == cudaSuccess) t += x;
+    }
+    return t;
+  }
+  int launches(int phase) const { return (int)(ev[phase].size() / 2); }
+};
+
 template <int D, typename R, int KERN>
 nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s,
-                       unsigned long long* scratch, int* err) {
+                       unsigned long long* scratch, int* err, PhaseTimer& T) {
   const int NB = (D + 1) * (D + 1);
   // the block buffer holds the cross blocks of one batch of pairs
   size_t free_b = 0, total_b = 0;
@@ -50,10 +76,16 @@ nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaS
     P.p_begin = b0;
     P.p_end = b1;
     NL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s));  // work counter
+    NL_TRY(T.mark(0, s));
     NL_TRY((launch_quad<D, R, KERN>(P, s)));
+    NL_TRY(T.mark(0, s));
+    NL_TRY(T.mark(1, s));
     NL_TRY((launch_scatter<D, R>(m, p, b0, b1, blk.p, nullptr, 0, values, err, s, h_off.data())));
+    NL_TRY(T.mark(1, s));
   }
+  NL_TRY(T.mark(1, s));
   NL_TRY((launch_scatter<D, R>(m, p, 0, 0, blk.p, selfblk.p, 1, values, err, s, h_off.data())));
+  NL_TRY(T.mark(1, s));
   if (std::is_same<R, float>::value) {
     k_diag_from_rows<<<NL_CNT((unsigned)((m->n_vert * 32 + 255) / 256)), 256, 0, s>>>(
         m->n_vert, p->row_ptr, p->col, values);
@@ -88,17 +120,18 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   nl_status rc = NL_OK;
   const bool f32 = prec != NL_PREC_FP64;
   const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
+  PhaseTimer T;
   if (p->n_pairs > 0) {
     if (D == 2) {
-      if (f32) rc = gauss ? run_assembly<2, float, 1>(m, p, P, values, s, scratch.p, err.p)
-                          : run_assembly<2, float, 0>(m, p, P, values, s, scratch.p, err.p);
-      else rc = gauss ? run_assembly<2, double, 1>(m, p, P, values, s, scratch.p, err.p)
-                      : run_assembly<2, double, 0>(m, p, P, values, s, scratch.p, err.p);
+      if (f32) rc = gauss ? run_assembly<2, float, 1>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly<2, float, 0>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly<2, double, 1>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly<2, double, 0>(m, p, P, values, s, scratch.p, err.p, T);
     } else {
-      if (f32) rc = gauss ? run_assembly<3, float, 1>(m, p, P, values, s, scratch.p, err.p)
-                          : run_assembly<3, float, 0>(m, p, P, values, s, scratch.p, err.p);
-      else rc = gauss ? run_assembly<3, double, 1>(m, p, P, values, s, scratch.p, err.p)
-                      : run_assembly<3, double, 0>(m, p, P, values, s, scratch.p, err.p);
+      if (f32) rc = gauss ? run_assembly<3, float, 1>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly<3, float, 0>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly<3, double, 1>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly<3, double, 0>(m, p, P, values, s, scratch.p, err.p, T);
     }
   }
   cudaEventRecord(e1, s);
@@ -127,6 +160,10 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
     st->n_eval_point_pairs = (int64_t)hs[4];
     st->n_closed_items = (int64_t)hs[5];
     st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
+    st->precision_run = f32 ? NL_PREC_FP32 : NL_PREC_FP64;
+    st->n_quad_launches = T.launches(0);
+    st->ms_quad = T.ms(0);
+    st->ms_scatter = T.ms(1);
   }
   return NL_OK;
 }
@@ -145,23 +182,17 @@ constexpr size_t NOALLOC_HEADER_BYTES = 256;                 // counters and the
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[128] = {};
-
-// Device address of g_noalloc_scratch on the current device (looked up once per device; the
-// host-side name of the array is not a device address).
+// Device address of g_noalloc_scratch in the current context.  The host-side name of the
+// array is not a device address.  The lookup is repeated on every call rather than cached:
+// a cached address would dangle after cudaDeviceReset or a re-created primary context, and
+// the lookup costs far less than the synchronising call around it.  The first lookup in a
+// context can load this library's device code, so the first call belongs before any stream
+// capture.
 nl_status noalloc_scratch(unsigned char** out) {
-  int dev = 0;
-  NL_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return fail(NL_EINTERNAL, "device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-    g_noalloc_addr[dev] = ptr;
-  }
-  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+  *out = static_cast<unsigned char*>(ptr);
   return NL_OK;
 }
 
@@ -244,6 +275,10 @@ nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
     st->n_eval_point_pairs = (int64_t)hs[4];
     st->n_closed_items = (int64_t)hs[5];
     st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
+    st->precision_run = f32 ? NL_PREC_FP32 : NL_PREC_FP64;
+    st->n_quad_launches = 1;
+    st->ms_quad = 0.0;
+    st->ms_scatter = 0.0;
   }
   return NL_OK;
 }

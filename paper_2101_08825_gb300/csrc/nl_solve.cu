@@ -138,7 +138,8 @@ __device__ __forceinline__ double safe_div(double a, double b, double* brk) {
   return a / b;
 }
 
-// y = A x on free rows (0 elsewhere), warp per row, grid-stride over the rows; four
+// y = A x on free rows (0 elsewhere; every row when free_ is NULL), warp per row, grid-stride
+// over the rows; four
 // independent partial sums keep four loads of x in flight per lane.  No reduction here, so the
 // grid can fill every SM; the dot products follow in k_spmv_dots.
 template <typename X, typename V>
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(RT) k_spmv(int64_t n, const int64_t* __restric
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
     X s = 0;
-    if (free_[i]) {
+    if (!free_ || free_[i]) {
       const int64_t e = rp[i + 1];
       int64_t t = rp[i] + lane;
       X s1 = 0, s2 = 0, s3 = 0;
@@ -520,6 +521,22 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
       m->n_vert, A->pairs->row_ptr, A->pairs->col, A->values, m->node_free, g.p, F);
   NL_CUDA(cudaGetLastError());
   NL_CUDA(cudaStreamSynchronize(s));
+  return NL_OK;
+}
+
+nl_status apply_matrix(const nl_matrix* A, const double* x, double* y) {
+  const nl_mesh* m = A->pairs->mesh;
+  Ctx c;
+  c.s = A->stream;
+  c.n = m->n_vert;
+  int dev = 0, nsm = 0;
+  NL_CUDA(cudaGetDevice(&dev));
+  NL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  c.cap = std::max(1, nsm);
+  if (c.n == 0) return NL_OK;
+  k_spmv<double, double><<<NL_CNT(c.gspmv()), RT, 0, c.s>>>(c.n, A->pairs->row_ptr, A->pairs->col,
+                                                           A->values, nullptr, x, y);
+  NL_CUDA(cudaGetLastError());
   return NL_OK;
 }
 

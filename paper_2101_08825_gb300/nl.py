@@ -43,7 +43,9 @@ class AssembleStats(ctypes.Structure):
     _fields_ = [("n_pairs", ctypes.c_int64), ("n_point_pairs", ctypes.c_int64),
                 ("n_items", ctypes.c_int64), ("n_exact_checks", ctypes.c_int64),
                 ("ms_assemble", ctypes.c_double), ("n_eval_point_pairs", ctypes.c_int64),
-                ("n_closed_items", ctypes.c_int64), ("n_band_point_pairs", ctypes.c_int64)]
+                ("n_closed_items", ctypes.c_int64), ("n_band_point_pairs", ctypes.c_int64),
+                ("precision_run", ctypes.c_int32), ("n_quad_launches", ctypes.c_int32),
+                ("ms_quad", ctypes.c_double), ("ms_scatter", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -97,6 +99,7 @@ def lib():
         "nl_assemble_noalloc": (st, [p, p, ctypes.POINTER(KernelParams), ctypes.POINTER(QuadParams),
                                      i, p, ctypes.POINTER(AssembleStats)]),
         "nl_matrix_export": (st, [p, p]),
+        "nl_matrix_apply": (st, [p, p, p]),
         "nl_matrix_device_values": (st, [p, pp]),
         "nl_matrix_destroy": (None, [p]),
         "nl_rhs": (st, [p, p, p, d, p, pp]),
@@ -239,6 +242,11 @@ class Matrix(_Handle):
         p = ctypes.c_void_p()
         _check(lib().nl_matrix_device_values(self.h, ctypes.byref(p)))
         return p.value
+
+    def apply(self, x_ptr: int, y_ptr: int):
+        """nl_matrix_apply: y = A x on the device (x, y: device pointers of n_vert doubles)."""
+        _check(lib().nl_matrix_apply(self.h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr)),
+               "nl_matrix_apply")
 
 
 class Vector(_Handle):

@@ -76,3 +76,36 @@ def test_poll_wait_timeout_and_bad_ticket():
         with pytest.raises(nl.NLError) as e:
             S.poll(t)  # a result is taken once
         assert e.value.status == nl.NL_EINVAL
+
+
+# Served results against the oracle's dense solve of the same problem (pairs, pattern,
+# Algorithm 1, right-hand side with lifting and Gaussian elimination, all in FP64 on the CPU),
+# at the tolerances of the single-problem solver tests: u_h to 1e-9 (FP64 assembly) or 1e-5
+# (FP32 assembly) of max |u_h|, the L2 error over Omega to 1e-8 or 1e-3 relative.
+# (The 3D meshes are small, delta = 0.8h, because the oracle's 3D assembly is slow.)
+ORACLE_MIX = [(2, 16, 3.0, 0, nl.NL_PREC_FP64, 21), (2, 12, 2.5, 1, nl.NL_PREC_FP32, 22),
+              (3, 4, 0.8, 0, nl.NL_PREC_FP32, 23), (3, 3, 0.8, 1, nl.NL_PREC_FP64, 24)]
+
+
+def test_served_results_match_the_oracle():
+    import oracle as O
+    with nl.Server(8 << 30, 4) as S:
+        outs, tickets, specs = [], [], []
+        for (dim, n, dh, kern, prec, seed) in ORACLE_MIX:
+            u = np.zeros(_nvert(dim, n, dh))
+            tickets.append(S.submit(_req(dim, n, dh, kern, prec, u, seed=seed), u))
+            outs.append(u)
+        res = [S.wait(t) for t in tickets]
+    for (dim, n, dh, kern, prec, seed), u, r in zip(ORACLE_MIX, outs, res):
+        assert r.status == nl.NL_OK, r.message
+        h = 1.0 / n
+        delta = dh * h
+        eps = delta / 10
+        layer = int(np.ceil((delta + eps) / h - 1e-9))
+        mesh = structured_mesh(dim, n, h, 0.0, layer, jitter=0.1, seed=seed)
+        ref = O.solve_problem(mesh, delta, eps, 3 if dim == 2 else 2, 1, kernel=kern)
+        assert r.n_pairs == len(ref["pair_l"]) and r.nnz == len(ref["col"])
+        assert r.n_point_pairs == ref["stats"].n_point_pairs
+        tolu, tole = (1e-9, 1e-8) if prec == nl.NL_PREC_FP64 else (1e-5, 1e-3)
+        assert np.abs(u - ref["u_h"]).max() <= tolu * np.abs(ref["u_h"]).max(), (dim, n, prec)
+        assert abs(r.l2_err_omega / ref["err_omega"] - 1) < tole, (dim, n, prec)
