@@ -74,9 +74,18 @@ typedef struct {
 
 /* Algorithm 1 levels, 1 <= L_min <= L_max <= 12 (2D) or 9 (3D).  rule: 0 = the degree-5
  * 7-point triangle rule (Sec. 6) and the degree-5 14-point tetrahedral rule, optionally OR
- * NL_QUAD_COUNT_BAND to count the point pairs in the mollifier band (a measurement aid; it
- * adds an integer add per evaluated point pair). */
+ *   NL_QUAD_COUNT_BAND  count the point pairs in the mollifier band (a measurement aid; it
+ *                       adds an integer add per evaluated point pair);
+ *   NL_QUAD_MINDIST_L2  Algorithm 1's refinement test uses the Euclidean approximate minimum
+ *                       distance sqrt(sum_k max(0, d1^k, d2^k)^2) that Sec. 5.1 gives after
+ *                       eq. mindistin (valid for kernels supported on a Euclidean ball, as
+ *                       both kernels here are) instead of eq. mindist.  It drops sub-elements
+ *                       and pairs whose every point pair lies beyond delta + eps, so the
+ *                       matrix is unchanged (their contributions are exactly zero) while the
+ *                       work counters shrink; the element pairs and the pattern (eq. k_l)
+ *                       keep eq. mindist. */
 #define NL_QUAD_COUNT_BAND 0x100
+#define NL_QUAD_MINDIST_L2 0x200
 typedef struct {
   int L_min, L_max;
   int rule;

@@ -45,7 +45,8 @@ class _Mesh(ctypes.Structure):
 
 class _Params(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("eps", ctypes.c_double), ("C", ctypes.c_double),
-                ("kernel", ctypes.c_int), ("L_min", ctypes.c_int), ("L_max", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("L_min", ctypes.c_int), ("L_max", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -75,6 +76,8 @@ def lib():
         L.or_aprx_max_dist.argtypes = [i, p, p, p, p]
         L.or_aprx_min_dist.restype = d
         L.or_aprx_min_dist.argtypes = [i, p, p, p, p]
+        L.or_aprx_min_dist_l2.restype = d
+        L.or_aprx_min_dist_l2.argtypes = [i, p, p, p, p]
         L.or_pairs.restype = i64
         L.or_pairs.argtypes = [ctypes.POINTER(_Mesh), d, d, p, p, i64, p]
         L.or_csr.restype = i64
@@ -165,6 +168,11 @@ def aprx_min_dist(lo1, hi1, lo2, hi2) -> float:
     return lib().or_aprx_min_dist(len(a[0]), *[_ptr(v) for v in a])
 
 
+def aprx_min_dist_l2(lo1, hi1, lo2, hi2) -> float:
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (lo1, hi1, lo2, hi2)]
+    return lib().or_aprx_min_dist_l2(len(a[0]), *[_ptr(v) for v in a])
+
+
 # ---- pairs, pattern, assembly --------------------------------------------------------
 
 def pairs(mesh, delta: float, eps: float, m_mask=None):
@@ -205,13 +213,17 @@ class Stats:
     n_integrations: int
 
 
+MINDIST_L2 = 1
+
+
 def assemble(mesh, pair_off, pair_l, row_ptr, col, delta, eps, L_max, L_min=1,
-             kernel=KERNEL_CONST, C=None, m_mask=None):
-    """Values of A on the CSR pattern (row_ptr, col) and the work counters."""
+             kernel=KERNEL_CONST, C=None, m_mask=None, mindist_l2=False):
+    """Values of A on the CSR pattern (row_ptr, col) and the work counters.  mindist_l2:
+    Algorithm 1's refinement test uses the Euclidean approximate minimum distance."""
     om = _om(mesh)
     if C is None:
         C = kernel_constant(om.dim, kernel, delta, eps)
-    P = _Params(delta, eps, C, kernel, L_min, L_max)
+    P = _Params(delta, eps, C, kernel, L_min, L_max, MINDIST_L2 if mindist_l2 else 0)
     vals = np.zeros(max(int(row_ptr[-1]), 1), dtype=np.float64)
     st = _Stats()
     mm = None

@@ -368,6 +368,21 @@ double or_aprx_min_dist(int dim, const double* lo1, const double* hi1, const dou
   return m;
 }
 
+/* The sharper variant that Sec. 5.1 states after eq. (mindistin) for kernels supported on a
+ * Euclidean ball: the length of the vector of per-axis gaps max(0, d1^k, d2^k). */
+double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const double* lo2,
+                           const double* hi2) {
+  double s = 0.0;
+  for (int k = 0; k < dim; k++) {
+    double d1 = lo1[k] - hi2[k];
+    double d2 = lo2[k] - hi1[k];
+    double t = (d1 > d2) ? d1 : d2;
+    if (t < 0.0) t = 0.0;
+    s += t * t;
+  }
+  return sqrt(s);
+}
+
 /* ------------------------------------------------------------------------------------
  * Mesh helpers. */
 static void elem_verts(const or_mesh* M, int64_t e, double V[4][3]) {
@@ -692,9 +707,12 @@ static void adaptive_integration(actx* c, int L_cur, const double E[4][3], const
   verts_bbox(dim, E, lo, hi);
   for (int64_t t = 0; t < nJ; t++) {
     int64_t m = J[t];
+    double amin = (P->flags & OR_MINDIST_L2)
+                      ? or_aprx_min_dist_l2(dim, lo, hi, c->lo + 3 * m, c->hi + 3 * m)
+                      : or_aprx_min_dist(dim, lo, hi, c->lo + 3 * m, c->hi + 3 * m);
     if (or_aprx_max_dist(dim, lo, hi, c->lo + 3 * m, c->hi + 3 * m) < P->delta - P->eps)
       Jint[nint++] = (int32_t)m;
-    else if (or_aprx_min_dist(dim, lo, hi, c->lo + 3 * m, c->hi + 3 * m) < P->delta + P->eps)
+    else if (amin < P->delta + P->eps)
       Jref[nref++] = (int32_t)m;
   }
   if (nint > 0) integration(c, E, Jint, nint);

@@ -37,10 +37,16 @@ typedef struct {
   const uint8_t* node_free;     /* 1 = degree of freedom (node inside open Omega) */
 } or_mesh;
 
+/* or_params.flags: the refinement test of Algorithm 1 uses the Euclidean variant of the
+ * approximate minimum distance that Sec. 5.1 gives after eq. (mindistin) instead of eq.
+ * (mindist).  The element pairs (eq. k_l) keep eq. (mindist). */
+#define OR_MINDIST_L2 1
+
 typedef struct {
   double delta, eps, C; /* horizon, mollifier half-width, kernel constant C_{delta,eps} */
   int kernel;           /* OR_KERNEL_* */
   int L_min, L_max;     /* Algorithm 1 refinement levels */
+  int flags;            /* OR_MINDIST_L2 or 0 */
 } or_params;
 
 typedef struct {
@@ -72,6 +78,9 @@ double or_aprx_max_dist(int dim, const double* lo1, const double* hi1, const dou
                         const double* hi2);
 double or_aprx_min_dist(int dim, const double* lo1, const double* hi1, const double* lo2,
                         const double* hi2);
+/* Sec. 5.1, the Euclidean variant after eq. (mindistin): sqrt(sum_k max(0, d1^k, d2^k)^2). */
+double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const double* lo2,
+                           const double* hi2);
 
 /* Eq. (k_l): J = {(m, l) : aprx-min-dist(E_l, E_m) < delta + eps}, m-major, l ascending.
  * pair_off has n_elem+1 entries; pair_l has room for cap entries.  m_mask (nullable) keeps

@@ -87,7 +87,9 @@ struct QParams {
   float fdme2, fdpe2, finv_delta2, margin, fdme, fdpe, fC;
   float fmqe, ftqe, fue;     // -1/(4 eps), 3/(4 eps), (1 - delta/eps)/2 (branch-free mollifier)
   float fint2, fnotint2;     // screen thresholds (delta - eps -+ margin)^2 (-1: never)
+  float fref2, fout2;        // mindist_l2: (delta + eps -+ 2 margin)^2
   int L_min, L_max, scap, count_band;
+  int mindist_l2;            // Algorithm 1's refinement test with the Euclidean minimum distance
   int kernel;  // nl_kernel_kind (read at run time by the batched kernel)
   int chunk;   // consecutive pairs a warp takes from the work counter
   double B[14][4];
@@ -166,10 +168,12 @@ __device__ __forceinline__ double pow2m(double, int k) {
 
 // Exact FP64 box distances of Sec. 5.1 (eqs. maxdist, mindist) between a sub-element with
 // vertices V and the box (lo2, hi2) of E_m, written as in a plain evaluation.
+// With l2, amin is the Euclidean variant that Sec. 5.1 gives after eq. mindistin,
+// sqrt(sum_k max(0, d1^k, d2^k)^2), in the same order of operations as a plain evaluation.
 template <int D>
 __device__ void exact_dists(const double (&V)[D + 1][D], const double* lo2, const double* hi2,
-                            double& amax, double& amin) {
-  double s = 0.0, mn = 0.0;
+                            double& amax, double& amin, bool l2 = false) {
+  double s = 0.0, mn = 0.0, e = 0.0;
 #pragma unroll
   for (int k = 0; k < D; k++) {
     double lo = V[0][k], hi = V[0][k];
@@ -184,17 +188,20 @@ __device__ void exact_dists(const double (&V)[D + 1][D], const double* lo2, cons
     s = __dadd_rn(s, p > q ? p : q);
     double t = d1 > d2 ? d1 : d2;
     mn = t > mn ? t : mn;
+    const double u = t < 0.0 ? 0.0 : t;
+    e = __dadd_rn(e, __dmul_rn(u, u));
   }
   amax = __dsqrt_rn(s);
-  amin = mn;
+  amin = l2 ? __dsqrt_rn(e) : mn;
 }
 
 // FP32 screen of the same distances: amax is returned squared (no square root on the
-// screening path), amin as is.
+// screening path), amin as is, and amin2 the square of the Euclidean variant.
 template <int D>
 __device__ __forceinline__ void screen_dists(const float (&V)[D + 1][D], const float* lo2,
-                                             const float* hi2, float& amax, float& amin) {
-  float s = 0.f, mn = 0.f;
+                                             const float* hi2, float& amax, float& amin,
+                                             float& amin2) {
+  float s = 0.f, mn = 0.f, e = 0.f;
 #pragma unroll
   for (int k = 0; k < D; k++) {
     float lo = V[0][k], hi = V[0][k];
@@ -205,10 +212,14 @@ __device__ __forceinline__ void screen_dists(const float (&V)[D + 1][D], const f
     }
     float d1 = lo - hi2[k], d2 = lo2[k] - hi;
     s += fmaxf(d1 * d1, d2 * d2);
-    mn = fmaxf(mn, fmaxf(d1, d2));
+    const float t = fmaxf(d1, d2);
+    mn = fmaxf(mn, t);
+    const float u = fmaxf(t, 0.f);
+    e = fmaf(u, u, e);
   }
   amax = s;  // squared: compared with squared thresholds
   amin = mn;
+  amin2 = e;
 }
 
 // Rebuilds the FP64 vertices of the sub-element with path `code` from the vertices of E_l.
@@ -250,7 +261,7 @@ template <int D>
 __device__ __noinline__ int exact_classify(const double* __restrict__ evert_l,
                                            const double* __restrict__ lo_m,
                                            const double* __restrict__ hi_m, uint32_t code,
-                                           double dme, double dpe) {
+                                           double dme, double dpe, bool l2) {
   double Vl[D + 1][D], V[D + 1][D], lo2[D], hi2[D];
 #pragma unroll
   for (int a = 0; a <= D; a++)
@@ -263,7 +274,7 @@ __device__ __noinline__ int exact_classify(const double* __restrict__ evert_l,
   }
   decode_exact<D>(Vl, code, V);
   double amax, amin;
-  exact_dists<D>(V, lo2, hi2, amax, amin);
+  exact_dists<D>(V, lo2, hi2, amax, amin, l2);
   if (amax < dme) return ACT_INT;
   if (amin < dpe) return ACT_REFINE;
   return ACT_DROP;
@@ -884,18 +895,20 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             flo[k] = (float)wm.pc[k];
             fhi[k] = (float)wm.pc[D + k];
           }
-          screen_dists<D>(Vf, flo, fhi, fam, fan);  // fam = squared aprx-max-dist
+          float fe2;
+          screen_dists<D>(Vf, flo, fhi, fam, fan, fe2);  // fam = squared aprx-max-dist
           const bool c_int = fam < P.fint2;
           const bool c_notint = fam > P.fnotint2;
-          const bool c_ref = fan < P.fdpe - P.margin;
-          const bool c_out = fan > P.fdpe + P.margin;
+          const bool l2 = P.mindist_l2 != 0;
+          const bool c_ref = l2 ? fe2 < P.fref2 : fan < P.fdpe - P.margin;
+          const bool c_out = l2 ? fe2 > P.fout2 : fan > P.fdpe + P.margin;
           if (last) return c_int ? ACT_INT : (c_out ? ACT_ZERO : ACT_FINAL);
           if (c_int) return ACT_INT;
           if (c_notint && c_ref) return ACT_REFINE;
           if (c_notint && c_out) return ACT_DROP;
           st_exact += count_exact ? 1 : 0;
           return exact_classify<D>(P.evert + (int64_t)l * NVC, P.blo + cur_m * D, P.bhi + cur_m * D,
-                                   code, P.dme, P.dpe);
+                                   code, P.dme, P.dpe, P.mindist_l2 != 0);
         } else {
           double Vd[NV][D], lo2[D], hi2[D];
 #pragma unroll
@@ -908,7 +921,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             hi2[k] = (double)wm.pc[D + k];
           }
           double amax, amin;
-          exact_dists<D>(Vd, lo2, hi2, amax, amin);
+          exact_dists<D>(Vd, lo2, hi2, amax, amin, P.mindist_l2 != 0);
           if (last) return amax < P.dme ? ACT_INT : (amin > P.dpe ? ACT_ZERO : ACT_FINAL);
           if (amax < P.dme) return ACT_INT;
           if (amin < P.dpe) return ACT_REFINE;
@@ -1602,7 +1615,8 @@ inline nl_status fill_qparams(const char* who, const nl_mesh* m, const nl_pairs*
   const int lmax_cap = D == 2 ? 12 : 9;
   if (qp->L_min < 1 || qp->L_max < qp->L_min || qp->L_max > lmax_cap)
     return fail(NL_EINVAL, "%s: need 1 <= L_min <= L_max <= %d", who, lmax_cap);
-  if ((qp->rule & ~NL_QUAD_COUNT_BAND) != 0) return fail(NL_EINVAL, "%s: only rule 0 is available", who);
+  if ((qp->rule & ~(NL_QUAD_COUNT_BAND | NL_QUAD_MINDIST_L2)) != 0)
+    return fail(NL_EINVAL, "%s: only rule 0 is available", who);
   if (prec != NL_PREC_FP64 && prec != NL_PREC_FP32 && prec != NL_PREC_MIXED_TF32 &&
       prec != NL_PREC_MIXED_BF16)
     return fail(NL_EINVAL, "%s: unknown precision %d", who, (int)prec);
@@ -1649,6 +1663,14 @@ inline nl_status fill_qparams(const char* who, const nl_mesh* m, const nl_pairs*
   P->L_min = qp->L_min;
   P->L_max = qp->L_max;
   P->count_band = (qp->rule & NL_QUAD_COUNT_BAND) ? 1 : 0;
+  P->mindist_l2 = (qp->rule & NL_QUAD_MINDIST_L2) ? 1 : 0;
+  {
+    // the Euclidean screen: sqrt(dim) <= 2 times the per-axis error bound, squared
+    const double lo_r = (double)P->fdpe - 2.0 * (double)P->margin;
+    const double hi_r = (double)P->fdpe + 2.0 * (double)P->margin;
+    P->fref2 = lo_r > 0.0 ? (float)(lo_r * lo_r) : -1.f;
+    P->fout2 = (float)(hi_r * hi_r);
+  }
   P->kernel = kp->kernel;
   P->chunk = CHUNK;
   // parent records the LIFO can hold: all sub-elements of levels 1 .. L_max-1 (at most 512)

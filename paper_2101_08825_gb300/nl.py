@@ -298,13 +298,18 @@ def nl_pairs_build(mesh: Mesh, delta: float, eps: float) -> Pairs:
 
 
 NL_QUAD_COUNT_BAND = 0x100
+NL_QUAD_MINDIST_L2 = 0x200
+
+
+def quad_rule_flags(count_band=False, mindist_l2=False) -> int:
+    return (NL_QUAD_COUNT_BAND if count_band else 0) | (NL_QUAD_MINDIST_L2 if mindist_l2 else 0)
 
 
 def nl_assemble(mesh: Mesh, pairs: Pairs, delta, eps, L_max, L_min=1, kernel=NL_KERNEL_CONST,
                 precision=NL_PREC_FP64, C_override=0.0, kappa=0.0, into: Matrix | None = None,
-                count_band=False):
+                count_band=False, mindist_l2=False):
     kp = KernelParams(float(delta), float(eps), float(kappa), int(kernel), float(C_override))
-    qp = QuadParams(int(L_min), int(L_max), NL_QUAD_COUNT_BAND if count_band else 0)
+    qp = QuadParams(int(L_min), int(L_max), quad_rule_flags(count_band, mindist_l2))
     st = AssembleStats()
     h = ctypes.c_void_p(into.h.value if into is not None else None)
     _check(lib().nl_assemble(mesh.h, pairs.h, ctypes.byref(kp), ctypes.byref(qp), int(precision),
@@ -316,11 +321,11 @@ def nl_assemble(mesh: Mesh, pairs: Pairs, delta, eps, L_max, L_min=1, kernel=NL_
 
 def nl_assemble_noalloc(mesh: Mesh, pairs: Pairs, delta, eps, L_max, values_ptr: int, L_min=1,
                         kernel=NL_KERNEL_CONST, precision=NL_PREC_FP64, C_override=0.0,
-                        kappa=0.0):
+                        kappa=0.0, mindist_l2=False):
     """Assembles into the caller's device array (nnz doubles at values_ptr) without any
     device allocation by the library."""
     kp = KernelParams(float(delta), float(eps), float(kappa), int(kernel), float(C_override))
-    qp = QuadParams(int(L_min), int(L_max), 0)
+    qp = QuadParams(int(L_min), int(L_max), quad_rule_flags(False, mindist_l2))
     st = AssembleStats()
     _check(lib().nl_assemble_noalloc(mesh.h, pairs.h, ctypes.byref(kp), ctypes.byref(qp),
                                      int(precision), ctypes.c_void_p(int(values_ptr)),

@@ -227,3 +227,27 @@ def test_band_point_pair_counts(case):
         _, st = nl.nl_assemble(m, p, delta, eps, L_max, L_min, kernel, prec, count_band=True)
         assert abs(st.n_band_point_pairs - ost.n_band_pairs) <= tol * ost.n_band_pairs + 2, (
             name, prec, st.n_band_point_pairs, ost.n_band_pairs)
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[0] in ("c1", "jit2d_L4", "jit2d_Lmin2",
+                                                               "gauss2d", "jit3d", "deep3d")],
+                         ids=lambda c: c[0])
+def test_euclidean_min_dist_counts_and_values(case):
+    # NL_QUAD_MINDIST_L2: Algorithm 1's refinement test with the Euclidean minimum distance of
+    # Sec. 5.1; the work counts equal the oracle's with the same test, bit for bit, in both
+    # precisions (FP32 screen with its own margin, FP64 decision inside it), and the matrix is
+    # the default one (only contributions that are exactly zero are left out)
+    name, mk, delta, eps, L_max, L_min, kernel = case
+    mesh = mk()
+    off, pl = O.pairs(mesh, delta, eps)
+    rp, col = O.csr(mesh, off, pl)
+    ovals, ost = O.assemble(mesh, off, pl, rp, col, delta, eps, L_max, L_min, kernel,
+                            mindist_l2=True)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, delta, eps)
+    for prec, tol in ((nl.NL_PREC_FP64, TOL64), (nl.NL_PREC_FP32, TOL32)):
+        A, st = nl.nl_assemble(m, p, delta, eps, L_max, L_min, kernel, prec, mindist_l2=True)
+        vals = A.export()
+        assert st.n_items == ost.n_integrations, (name, prec)
+        assert st.n_point_pairs == ost.n_point_pairs, (name, prec)
+        assert _rel(vals, ovals) < tol and _maxrel(vals, ovals) < tol, (name, prec)

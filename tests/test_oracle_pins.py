@@ -184,6 +184,41 @@ def test_box_distances_are_conservative():
         amax = O.aprx_max_dist(V1.min(0), V1.max(0), V2.min(0), V2.max(0))
         assert amin <= D.min() + 1e-12  # eq. (mindistin)
         assert amax >= D.max() - 1e-12  # eq. (maxdistin)
+        # the Euclidean variant stated after eq. (mindistin) is sharper and still conservative
+        amin2 = O.aprx_min_dist_l2(V1.min(0), V1.max(0), V2.min(0), V2.max(0))
+        assert amin <= amin2 <= D.min() + 1e-12
+
+
+def test_euclidean_min_dist_hand_cases():
+    lo1, hi1 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 1.0, 1.0])
+    # gaps 3 (x) and 4 (y), overlap in z: Euclidean 5, eq. (mindist) 4
+    lo2, hi2 = np.array([4.0, 5.0, 0.5]), np.array([5.0, 6.0, 2.0])
+    assert O.aprx_min_dist_l2(lo1, hi1, lo2, hi2) == 5.0
+    assert O.aprx_min_dist(lo1, hi1, lo2, hi2) == 4.0
+    # a gap along one axis only: both variants give it
+    lo3, hi3 = np.array([0.2, 2.5, 0.0]), np.array([0.8, 3.0, 1.0])
+    assert O.aprx_min_dist_l2(lo1, hi1, lo3, hi3) == O.aprx_min_dist(lo1, hi1, lo3, hi3) == 1.5
+    assert O.aprx_min_dist_l2(lo1, hi1, lo1, hi1) == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_euclidean_refinement_test_drops_only_zero_contributions(dim):
+    # Algorithm 1 with the Euclidean minimum distance leaves out exactly the sub-elements whose
+    # every point pair lies beyond delta + eps (mu = 0), so A is identical bit for bit while
+    # the work shrinks; a box-shaped (eq. mindist) reach and a ball differ near the corners
+    if dim == 2:
+        mesh = structured_mesh(2, 6, 1 / 6, 0.0, 2, jitter=0.1, seed=13)
+        delta, eps, L_max = 0.3, 0.03, 3
+    else:
+        mesh = structured_mesh(3, 2, 0.5, 0.0, 1, jitter=0.1, seed=14)
+        delta, eps, L_max = 0.45, 0.05, 2
+    off, pl = O.pairs(mesh, delta, eps)
+    rp, col = O.csr(mesh, off, pl)
+    v0, s0 = O.assemble(mesh, off, pl, rp, col, delta, eps, L_max)
+    v1, s1 = O.assemble(mesh, off, pl, rp, col, delta, eps, L_max, mindist_l2=True)
+    assert np.array_equal(v0, v1)
+    assert s1.n_point_pairs < s0.n_point_pairs and s1.n_integrations < s0.n_integrations
+    assert s1.n_band_pairs == s0.n_band_pairs  # no point pair within delta + eps is dropped
 
 
 # ---- eq. (k_l) pairs and the pattern -------------------------------------------------

@@ -1,8 +1,9 @@
 """The FP32 screen of Algorithm 1's decisions in the FP32 assembly path (CPU, numpy float32
 emulation): sub-element vertices relative to the first vertex of E_m (the FP64 offset of the
 first vertices rebuilt from float-float pairs, per-element FP32 vertex offsets, FP32
-midpoints), box distances of Sec. 5.1 (eqs. maxdist, mindist) in FP32, compared against
-delta -/+ eps with the margin 2e-5 (delta + eps + 2 max_ext).  Every decision the screen
+midpoints), box distances of Sec. 5.1 (eqs. maxdist, mindist, and the Euclidean minimum
+distance stated after eq. mindistin) in FP32, compared against delta -/+ eps with the margin
+2e-5 (delta + eps + 2 max_ext) (twice that for the Euclidean distance).  Every decision the screen
 takes must equal the FP64 decision on the exact sub-element, at every refinement level up
 to 12, on the workloads' meshes and on a mesh far from the origin."""
 import numpy as np
@@ -42,8 +43,15 @@ def _dists(V, lo2, hi2, dtype):
     s = np.zeros(len(V), dtype)
     for k in range(V.shape[2]):
         s = (s + sq[:, k]).astype(dtype)
-    amin = np.maximum(np.maximum(d1, d2).max(axis=1), dtype(0))
-    return s, amin  # squared max-dist, min-dist
+    t = np.maximum(np.maximum(d1, d2), dtype(0))
+    amin = t.max(axis=1)
+    # squared Euclidean min-dist (the variant after eq. mindistin), accumulated as the kernel's
+    # fused multiply-adds: the product of two FP32 values is exact in FP64, one rounding per add
+    e = np.zeros(len(V), dtype)
+    for k in range(V.shape[2]):
+        tk = t[:, k].astype(np.float64)
+        e = (e.astype(np.float64) + tk * tk).astype(dtype)
+    return s, amin, e  # squared max-dist, min-dist, squared Euclidean min-dist
 
 
 @pytest.mark.parametrize("dim,cells,h,lo,delta,eps,jitter", [
@@ -89,31 +97,42 @@ def test_fp32_screen_decisions_equal_fp64(dim, cells, h, lo, delta, eps, jitter)
             c = rng.integers(0, 2 ** dim, n)
             V32 = _refine(V32, c, dim, f32)
             V64 = _refine(V64, c, dim, np.float64)
-        fam, fan = _dists(V32, lo_m32, hi_m32, f32)
-        s64, amin64 = _dists(V64, lo_m64, hi_m64, np.float64)
-        amax64 = np.sqrt(s64)
+        fam, fan, fe2 = _dists(V32, lo_m32, hi_m32, f32)
+        s64, amin64, e64 = _dists(V64, lo_m64, hi_m64, np.float64)
+        amax64, aminl2 = np.sqrt(s64), np.sqrt(e64)
         is_int, is_ref = amax64 < dme, amin64 < dpe
         c_int, c_notint = fam < fint2, fam > fnotint2
         c_ref, c_out = fan < f32(fdpe - margin), fan > f32(fdpe + margin)
         assert np.all(is_int[c_int]) and not np.any(is_int[c_notint]), level
         assert np.all(is_ref[c_ref]) and not np.any(is_ref[c_out]), level
+        # the Euclidean refinement test (NL_QUAD_MINDIST_L2) against (delta + eps -+ 2 margin)^2
+        fref2 = f32((float(fdpe) - 2.0 * float(margin)) ** 2)
+        fout2 = f32((float(fdpe) + 2.0 * float(margin)) ** 2)
+        is_ref2 = aminl2 < dpe
+        c_ref2, c_out2 = fe2 < fref2, fe2 > fout2
+        assert np.all(is_ref2[c_ref2]) and not np.any(is_ref2[c_out2]), level
         decided += int((c_int | c_notint).sum() + (c_ref | c_out).sum())
         # adversarial thresholds placed at each sub-element's own distances: within a few
         # margins (the screen's window edges) and within FP32 precision (where only the
         # FP64 test may decide)
         for scale in (float(margin), 2.0 ** -20 * (delta + eps)):
-            for dist, is_max in ((amax64, True), (amin64, False)):
+            for dist, kind in ((amax64, "max"), (amin64, "min"), (aminl2, "l2")):
                 T = dist + rng.uniform(-3, 3, n) * scale
                 fT = T.astype(f32)
                 exact = dist < T
-                if is_max:
+                if kind == "max":
                     lo_t = fT.astype(np.float64) - float(margin)
                     t2 = np.where(lo_t > 0, (lo_t * lo_t), -1.0).astype(f32)
                     hi2 = ((fT.astype(np.float64) + float(margin)) ** 2).astype(f32)
                     yes, no = fam < t2, fam > hi2
+                elif kind == "l2":
+                    lo_t = fT.astype(np.float64) - 2.0 * float(margin)
+                    t2 = np.where(lo_t > 0, (lo_t * lo_t), -1.0).astype(f32)
+                    hi2 = ((fT.astype(np.float64) + 2.0 * float(margin)) ** 2).astype(f32)
+                    yes, no = fe2 < t2, fe2 > hi2
                 else:
                     yes, no = fan < (fT - margin).astype(f32), fan > (fT + margin).astype(f32)
-                assert np.all(exact[yes]) and not np.any(exact[no]), (level, scale, is_max)
+                assert np.all(exact[yes]) and not np.any(exact[no]), (level, scale, kind)
                 checked += int((yes | no).sum())
     assert decided > 0.9 * 2 * 12 * n  # the FP64 fallback is rare
     assert checked > 0
