@@ -52,14 +52,20 @@ typedef enum {
 
 typedef enum {
   NL_PREC_FP64 = 0,       /* every point pair and every accumulation in FP64 */
-  NL_PREC_MIXED_TF32 = 1, /* accepted; runs the NL_PREC_FP32 path.  The per-pair contraction
-                             (7 or 14 inner points x (dim+1) columns) is 3-4 FMAs per point
-                             pair beside a 15-20 instruction evaluation of gamma_eps, too thin
-                             for tensor-core tiles to save issue slots */
-  NL_PREC_MIXED_BF16 = 2, /* accepted; runs the NL_PREC_FP32 path (as MIXED_TF32) */
+  NL_PREC_MIXED_TF32 = 1, /* the NL_PREC_FP32 path with the per-pair contraction over the
+                             outer points, H_c(y) = sum_x gamma_eps(x,y) w_x phi^l_c(x), on the
+                             tensor cores (mma.sync m16n8k8 TF32, FP32 accumulation); both
+                             operands split into two TF32 parts (about 22 significant bits)
+                             and the cross products summed; self blocks, scatter and
+                             decisions as in NL_PREC_FP32 */
+  NL_PREC_MIXED_BF16 = 2, /* as MIXED_TF32 with mma.sync m16n8k16 BF16 and two BF16 parts per
+                             operand (about 16 significant bits) */
   NL_PREC_FP32 = 3        /* gamma_eps and the per-pair local sums in FP32 on the ALUs
                              (packed FP32x2 arithmetic), decisions and scatter exact/FP64 */
 } nl_precision;
+/* nl_assemble runs each precision as named.  nl_assemble_noalloc and batched plans run the
+ * MIXED precisions with the NL_PREC_FP32 arithmetic; every assembly reports the arithmetic
+ * that ran in nl_assemble_stats.precision_run. */
 
 /* Kernel gamma_eps = C eta mu_{delta,eps}.  Requires 0 < eps < delta (Sec. 3).
  * C_override = 0 selects C_{delta,eps}: for NL_KERNEL_CONST the closed form of Sec. 6

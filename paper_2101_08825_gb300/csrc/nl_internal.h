@@ -194,6 +194,10 @@ nl_status build_pairs(nl_mesh* m, double delta, double eps, nl_pairs* out);
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st);
+// The same for NL_PREC_MIXED_TF32 / NL_PREC_MIXED_BF16 (nl_quad_mma.cu).
+nl_status assemble_values_mma(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                              const nl_quad_params* qp, nl_precision prec, double* values,
+                              nl_assemble_stats* st);
 // Right-hand side, operator application and solver kernels (nl_solve.cu).
 nl_status apply_matrix(const nl_matrix* A, const double* x, double* y);
 nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_const,

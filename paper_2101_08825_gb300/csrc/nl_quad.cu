@@ -21,151 +21,13 @@ nl_status ensure_device_tables() {
   return NL_OK;
 }
 
-namespace {
-// CUDA events around every launch of the assembly kernel and of the scatter, read after the
-// assembly's final synchronisation.
-struct PhaseTimer {
-  std::vector<cudaEvent_t> ev[2];
-  ~PhaseTimer() {
-    for (auto& v : ev)
-      for (cudaEvent_t e : v) cudaEventDestroy(e);
-  }
-  nl_status mark(int phase, cudaStream_t s) {
-    cudaEvent_t e;
-    NL_CUDA(cudaEventCreate(&e));
-    ev[phase].push_back(e);
-    NL_CUDA(cudaEventRecord(e, s));
-    return NL_OK;
-  }
-  // summed elapsed time of the (start, end) pairs of one phase, after synchronisation
-  double ms(int phase) const {
-    double t = 0.0;
-    for (size_t i = 0; i + 1 < ev[phase].size(); i += 2) {
-      float x = 0.f;
-      if (cudaEventElapsedTime(&x, ev[phase][i], ev[phase][i + 1]) == cudaSuccess) t += x;
-    }
-    return t;
-  }
-  int launches(int phase) const { return (int)(ev[phase].size() / 2); }
-};
-
-template <int D, typename R, int KERN>
-nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s,
-                       unsigned long long* scratch, int* err, PhaseTimer& T) {
-  const int NB = (D + 1) * (D + 1);
-  // the block buffer holds the cross blocks of one batch of pairs
-  size_t free_b = 0, total_b = 0;
-  NL_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
-  if (g_block_budget) budget = std::min(budget, g_block_budget);
-  int64_t batch = std::max<int64_t>(1 << 20, (int64_t)(budget / (sizeof(R) * NB)));
-  batch = std::min<int64_t>(batch, p->n_pairs);
-  DevBuf<R> blk;
-  DevBuf<double> selfblk;
-  NL_TRY(blk.alloc((size_t)batch * NB, s));
-  NL_TRY(selfblk.alloc((size_t)m->n_elem * NB, s));
-  NL_CUDA(cudaMemsetAsync(selfblk.p, 0, sizeof(double) * m->n_elem * NB, s));
-  std::vector<int64_t> h_off(m->n_elem + 1);
-  NL_CUDA(cudaMemcpyAsync(h_off.data(), p->pair_off, sizeof(int64_t) * (m->n_elem + 1),
-                          cudaMemcpyDeviceToHost, s));
-  NL_CUDA(cudaStreamSynchronize(s));
-  P.blk = blk.p;
-  P.selfblk = selfblk.p;
-  for (int64_t b0 = 0; b0 < p->n_pairs; b0 += batch) {
-    const int64_t b1 = std::min(p->n_pairs, b0 + batch);
-    P.p_begin = b0;
-    P.p_end = b1;
-    NL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s));  // work counter
-    NL_TRY(T.mark(0, s));
-    NL_TRY((launch_quad<D, R, KERN>(P, s)));
-    NL_TRY(T.mark(0, s));
-    NL_TRY(T.mark(1, s));
-    NL_TRY((launch_scatter<D, R>(m, p, b0, b1, blk.p, nullptr, 0, values, err, s, h_off.data())));
-    NL_TRY(T.mark(1, s));
-  }
-  NL_TRY(T.mark(1, s));
-  NL_TRY((launch_scatter<D, R>(m, p, 0, 0, blk.p, selfblk.p, 1, values, err, s, h_off.data())));
-  NL_TRY(T.mark(1, s));
-  if (std::is_same<R, float>::value) {
-    k_diag_from_rows<<<NL_CNT((unsigned)((m->n_vert * 32 + 255) / 256)), 256, 0, s>>>(
-        m->n_vert, p->row_ptr, p->col, values);
-    NL_CUDA(cudaGetLastError());
-  }
-  return NL_OK;
-}
-
-}  // namespace
-
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st) {
-  QParams P;
-  NL_TRY(fill_qparams("nl_assemble", m, p, kp, qp, prec, &P));
-  const int D = m->dim;
-  cudaStream_t s = m->stream;
-  DevBuf<unsigned long long> scratch;
-  DevBuf<int> err;
-  NL_TRY(scratch.alloc(8, s));
-  NL_TRY(err.alloc(1, s));
-  NL_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long) * 8, s));
-  NL_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-  NL_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (p->nnz ? p->nnz : 1), s));
-  P.counter = scratch.p;
-  P.stats = scratch.p + 1;
-  P.err = err.p;
-  cudaEvent_t e0, e1;
-  NL_CUDA(cudaEventCreate(&e0));
-  NL_CUDA(cudaEventCreate(&e1));
-  NL_CUDA(cudaEventRecord(e0, s));
-  nl_status rc = NL_OK;
-  const bool f32 = prec != NL_PREC_FP64;
-  const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
-  PhaseTimer T;
-  if (p->n_pairs > 0) {
-    if (D == 2) {
-      if (f32) rc = gauss ? run_assembly<2, float, 1>(m, p, P, values, s, scratch.p, err.p, T)
-                          : run_assembly<2, float, 0>(m, p, P, values, s, scratch.p, err.p, T);
-      else rc = gauss ? run_assembly<2, double, 1>(m, p, P, values, s, scratch.p, err.p, T)
-                      : run_assembly<2, double, 0>(m, p, P, values, s, scratch.p, err.p, T);
-    } else {
-      if (f32) rc = gauss ? run_assembly<3, float, 1>(m, p, P, values, s, scratch.p, err.p, T)
-                          : run_assembly<3, float, 0>(m, p, P, values, s, scratch.p, err.p, T);
-      else rc = gauss ? run_assembly<3, double, 1>(m, p, P, values, s, scratch.p, err.p, T)
-                      : run_assembly<3, double, 0>(m, p, P, values, s, scratch.p, err.p, T);
-    }
-  }
-  cudaEventRecord(e1, s);
-  unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int herr = 0;
-  cudaMemcpyAsync(hs, scratch.p, sizeof hs, cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s);
-  cudaError_t ce = cudaStreamSynchronize(s);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (rc != NL_OK) return rc;
-  if (ce != cudaSuccess) return cuda_fail(ce, "nl_assemble");
-  if (herr) {
-    return fail(NL_EINTERNAL, "nl_assemble: device check failed (code %d: %s)", herr,
-                (herr & ERR_STACK) ? "refinement stack capacity exceeded" : "CSR entry missing");
-  }
-  if (st) {
-    const int nq = D == 2 ? 7 : 14;
-    st->n_pairs = p->n_pairs;
-    st->n_items = (int64_t)hs[1];
-    st->n_point_pairs = (int64_t)hs[1] * nq * nq;
-    st->n_exact_checks = (int64_t)hs[3];
-    st->ms_assemble = ms;
-    st->n_eval_point_pairs = (int64_t)hs[4];
-    st->n_closed_items = (int64_t)hs[5];
-    st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
-    st->precision_run = f32 ? NL_PREC_FP32 : NL_PREC_FP64;
-    st->n_quad_launches = T.launches(0);
-    st->ms_quad = T.ms(0);
-    st->ms_scatter = T.ms(1);
-  }
-  return NL_OK;
+  // the tensor-core variants are compiled in their own translation unit (nl_quad_mma.cu)
+  if (prec == NL_PREC_MIXED_TF32 || prec == NL_PREC_MIXED_BF16)
+    return assemble_values_mma(m, p, kp, qp, prec, values, st);
+  return assemble_single<0>(m, p, kp, qp, prec, values, st);
 }
 
 // ---- assembly without device allocation ------------------------------------------------------

@@ -96,6 +96,9 @@ struct QParams {
   double W[14];
 };
 
+// Values per padded vertex in shared memory (see VPad)
+__host__ __device__ constexpr int VPadN(int D) { return D == 2 ? 2 : 4; }
+
 template <int D>
 struct Geo {
   static constexpr int NV = D + 1;
@@ -351,6 +354,57 @@ __device__ __forceinline__ void cp_async_wait_prior() {
   asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
 
+// ---- tensor-core pieces of the mixed paths (mma.sync, FP32 accumulation) ------------------
+// TF32: a value x is carried as hi + lo, hi = x rounded to TF32 (10 stored mantissa bits) and lo
+// = the remainder rounded to TF32: about 22 significant bits together.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+// D += A B, A 16x8 (row), B 8x8 (col), TF32 operands, FP32 accumulators
+__device__ __forceinline__ void mma_tf32(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// BF16 pairs: (x0, x1) packed with x0 in the low half (the lower matrix index), and the
+// two-term split hi + lo of each value (about 16 significant bits together).
+__device__ __forceinline__ uint32_t bf16x2(float x0, float x1) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  hi = bf16x2(x0, x1);
+  lo = bf16x2(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xffff0000u));
+}
+// D += A B, A 16x16 (row), B 16x8 (col), BF16 operands, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+// Per-warp staging of one batch of 32 outer points for the tensor-core integration: their
+// coordinates (padded vertices) and the weighted P1 basis of E_l at them, split into two
+// parts (TF32 or BF16), column-major with a row stride of MMA_BS floats (40: the lanes of one
+// fragment load hit distinct banks).
+constexpr int MMA_BS = 40;
+template <int D>
+__host__ __device__ constexpr size_t mma_stage_bytes(int mma) {
+  return mma == 0 ? 0 : sizeof(float) * (32 * VPadN(D) + 2 * (D + 1) * MMA_BS);
+}
+
 // Hardware reciprocal square root (MUFU, about 2^-22 relative error), no denormal handling.
 __device__ __forceinline__ float rsqrt_hw(float x) {
   float y;
@@ -553,7 +607,9 @@ struct QLaunch {
   static constexpr int MIN_CTAS = D == 2 ? 2 : 3;
 };
 
-template <int D, typename R, int KERN, bool DIRECT = false, bool BATCHED = false>
+// MMA = 1 (TF32) or 2 (BF16), R = float only: the per-pair contraction over the outer points
+// runs on the tensor cores (see integrate).
+template <int D, typename R, int KERN, bool DIRECT = false, bool BATCHED = false, int MMA = 0>
 __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
     k_quad(const QParams P0, const QBatch Bt) {
   using G = Geo<D>;
@@ -582,6 +638,10 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       smem_raw + table_bytes<R>() + (size_t)(blockDim.x >> 5) * WarpMem<D, R>::bytes(P0.scap) +
       (size_t)wid * ((sizeof(QParams) + 15) & ~size_t(15)));
   const QParams& P = BATCHED ? *qcopy : P0;
+  static_assert(MMA == 0 || (std::is_same<R, float>::value && !BATCHED), "tensor-core variants: FP32, single problem");
+  float* mstage = reinterpret_cast<float*>(
+      smem_raw + table_bytes<R>() + (size_t)(blockDim.x >> 5) * WarpMem<D, R>::bytes(P0.scap) +
+      (size_t)wid * mma_stage_bytes<D>(MMA));
   auto is_const = [&]() { return KERN == 2 ? P.kernel == NL_KERNEL_CONST : KERN == NL_KERNEL_CONST; };
   auto is_gauss = [&]() {
     return KERN == 2 ? P.kernel == NL_KERNEL_TRUNC_GAUSS : KERN == NL_KERNEL_TRUNC_GAUSS;
@@ -600,6 +660,10 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 
   R y[NYL][D];        // inner points of m (local if R = float)
   f2 yq[3][D];        // R = float: inner points 0-5 of the lane packed in pairs
+  // MMA: the inner points of this thread's fragment rows, q = lane/4 (+ 8 in 3D); rows past
+  // the rule's points are padding
+  constexpr int MROWS = D == 2 ? 1 : 2;
+  float ym[MROWS][D];
   R vol_m = 0;
   // The end-of-pair reduce-scatter leaves entry e_rs of NRS values on this lane: the cross
   // block (e < NBLK) and the sums of g at the inner points (NBLK <= e < NBLK + NQ); a lane that
@@ -792,6 +856,21 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 #pragma unroll
             for (int k = 0; k < D; k++) yq[j][k] = f2pack((float)y[2 * j][k], (float)y[2 * j + 1][k]);
         }
+        if constexpr (MMA != 0) {
+#pragma unroll
+          for (int r = 0; r < MROWS; r++) {
+            const int q = (lane >> 2) + 8 * r;
+#pragma unroll
+            for (int k = 0; k < D; k++) {
+              float s = 0.f;
+              if (q < NQ) {
+#pragma unroll
+                for (int a = 0; a < NV; a++) s += (float)sB[q * NV + a] * (float)Vm[a][k];
+              }
+              ym[r][k] = s;
+            }
+          }
+        }
       }
       // ---- per-pair set-up ------------------------------------------------------------------
       // Only the first vertex of E_l stays in registers; the whole simplex is rebuilt when the
@@ -874,6 +953,9 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       }
 #pragma unroll
       for (int k = 0; k < D; k++) uh[k] = 0;
+      // MMA: the fragment accumulators of the pair's contraction H_c(y) = sum_x G(x, y) w_x
+      // phi^l_c(x) (rows: inner points y, columns: nodes c of l)
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
 
       // Algorithm 1 decision for a sub-element (R coordinates)
       // count_exact: this lane counts an FP64 re-decision (lanes that classify the same
@@ -1050,6 +1132,184 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         const R* iw = wm.iw + kind * IMAX;
         const int n_x = n_it * NQ;
         st_eval += (unsigned)(n_x * NQ);
+        if constexpr (MMA != 0) {
+          // Tensor-core contraction.  For each batch of 32 outer points x, lane i stages point
+          // i: its coordinates and B[x][c] = w_x phi^l_c(x) (the P1 basis of l, c = 0..D),
+          // split into two parts.  Then each thread evaluates G(x, y) = [mu] [eta] at the point
+          // pairs of its A-fragment entries (rows: inner points y = lane/4 (+8), columns: outer
+          // points), and mma.sync adds A B into the accumulators H_c(y).  The split makes the
+          // product accurate to about 2^-22 (TF32) / 2^-16 (BF16): 2D uses fragment rows 8-15
+          // for the low parts of A (7 inner points fit in rows 0-6), 3D its 14 inner points use
+          // all rows and the low part of A takes a third product.
+          float* xs = mstage;              // [32][PAD]
+          float* bs = mstage + 32 * PAD;   // [2][NV][MMA_BS]: high and low parts of B
+          const int g = lane >> 2, t = lane & 3;
+          for (int base = 0; base < n_x; base += 32) {
+            {
+              const int o = base + lane;
+              const bool valid = o < n_x;
+              const int it = valid ? o / NQ : 0;
+              const int q = valid ? o - it * NQ : 0;
+              float x[D];
+#pragma unroll
+              for (int k = 0; k < D; k++) x[k] = 0.f;
+#pragma unroll
+              for (int a = 0; a < NV; a++) {
+                float va[D];
+                vload<D, float>(iv + ((size_t)a * IMAX + it) * PAD, va);
+                const float b = sB[q * NV + a];
+#pragma unroll
+                for (int k = 0; k < D; k++) x[k] += b * va[k];
+              }
+              const float wcx = valid ? sW[q] * iw[it] : 0.f;
+              float ph[NV];
+              ph[0] = 1.f;
+#pragma unroll
+              for (int r = 0; r < D; r++) {
+                float s2 = 0.f;
+#pragma unroll
+                for (int c = 0; c < D; c++) s2 += JI(r, c) * (x[c] - Vl0[c]);
+                ph[r + 1] = s2;
+                ph[0] -= s2;
+              }
+              vstore<D, float>(xs + lane * PAD, x);
+#pragma unroll
+              for (int c = 0; c < NV; c++) {
+                const float bv = wcx * ph[c];
+                if constexpr (MMA == 1) {
+                  uint32_t hi, lo;
+                  split_tf32(bv, hi, lo);
+                  bs[c * MMA_BS + lane] = __uint_as_float(hi);
+                  bs[(NV + c) * MMA_BS + lane] = __uint_as_float(lo);
+                } else {
+                  // the BF16 rounding of bv (exact as a float), and the remainder
+                  const float hi = __uint_as_float(bf16x2(bv, 0.f) << 16);
+                  bs[c * MMA_BS + lane] = hi;
+                  bs[(NV + c) * MMA_BS + lane] = bv - hi;
+                }
+              }
+            }
+            __syncwarp();
+            // G at the thread's point pairs: outer points xa, xb (packed), inner point row r
+            auto geval = [&](const float (&xa)[D], const float (&xb)[D], int r, bool xva, bool xvb,
+                             float& ga, float& gb) {
+              f2 d = f2sub(f2pack(xa[0], xb[0]), f2dup(ym[r][0]));
+              f2 r2 = f2mul(d, d);
+#pragma unroll
+              for (int k = 1; k < D; k++) {
+                d = f2sub(f2pack(xa[k], xb[k]), f2dup(ym[r][k]));
+                r2 = f2fma(d, d, r2);
+              }
+              f2 gg = f2dup(1.f);
+              const bool yv = g + 8 * r < NQ;
+              if (kind == KIND_FINAL) {
+                gg = mollifier2(MK, r2);
+                if (count_band) {
+                  float a, b;
+                  f2unpack(r2, a, b);
+                  st_band += (yv && xva && a >= P.fdme2 && a <= P.fdpe2) ? 1 : 0;
+                  st_band += (yv && xvb && b >= P.fdme2 && b <= P.fdpe2) ? 1 : 0;
+                }
+              }
+              if (gauss) gg = (kind == KIND_FINAL) ? f2mul(gg, eta_gauss2(inv_d2, r2)) : eta_gauss2(inv_d2, r2);
+              f2unpack(gg, ga, gb);
+              ga = yv ? ga : 0.f;
+              gb = yv ? gb : 0.f;
+            };
+            if constexpr (MMA == 1) {
+              // m16n8k8: A columns (outer points) t and t+4 of each group of 8
+#pragma unroll
+              for (int j = 0; j < 4; j++) {
+                if (base + 8 * j >= n_x) break;
+                const int ia = 8 * j + t, ib = ia + 4;
+                float xa[D], xb[D];
+                vload<D, float>(xs + ia * PAD, xa);
+                vload<D, float>(xs + ib * PAD, xb);
+                const bool xva = base + ia < n_x, xvb = base + ib < n_x;
+                uint32_t bh0 = 0, bh1 = 0, bl0 = 0, bl1 = 0;
+                if (g < NV) {
+                  bh0 = __float_as_uint(bs[g * MMA_BS + ia]);
+                  bh1 = __float_as_uint(bs[g * MMA_BS + ib]);
+                  bl0 = __float_as_uint(bs[(NV + g) * MMA_BS + ia]);
+                  bl1 = __float_as_uint(bs[(NV + g) * MMA_BS + ib]);
+                }
+                if constexpr (D == 2) {
+                  float ga, gb;
+                  geval(xa, xb, 0, xva, xvb, ga, gb);
+                  uint32_t ah0, al0, ah1, al1;
+                  split_tf32(ga, ah0, al0);
+                  split_tf32(gb, ah1, al1);
+                  // rows 0-7: high parts, rows 8-15: low parts of the same inner points
+                  mma_tf32(acc, ah0, al0, ah1, al1, bh0, bh1);
+                  mma_tf32(acc, ah0, al0, ah1, al1, bl0, bl1);
+                } else {
+                  float g0a, g0b, g1a, g1b;
+                  geval(xa, xb, 0, xva, xvb, g0a, g0b);
+                  geval(xa, xb, 1, xva, xvb, g1a, g1b);
+                  uint32_t h0a, l0a, h0b, l0b, h1a, l1a, h1b, l1b;
+                  split_tf32(g0a, h0a, l0a);
+                  split_tf32(g0b, h0b, l0b);
+                  split_tf32(g1a, h1a, l1a);
+                  split_tf32(g1b, h1b, l1b);
+                  mma_tf32(acc, h0a, h1a, h0b, h1b, bh0, bh1);
+                  mma_tf32(acc, h0a, h1a, h0b, h1b, bl0, bl1);
+                  mma_tf32(acc, l0a, l1a, l0b, l1b, bh0, bh1);
+                }
+              }
+            } else {
+              // m16n8k16: A columns (outer points) 2t, 2t+1, 2t+8, 2t+9 of each group of 16
+#pragma unroll
+              for (int j = 0; j < 2; j++) {
+                if (base + 16 * j >= n_x) break;
+                const int i0 = 16 * j + 2 * t;
+                float x0[D], x1[D], x8[D], x9[D];
+                vload<D, float>(xs + i0 * PAD, x0);
+                vload<D, float>(xs + (i0 + 1) * PAD, x1);
+                vload<D, float>(xs + (i0 + 8) * PAD, x8);
+                vload<D, float>(xs + (i0 + 9) * PAD, x9);
+                const bool v0 = base + i0 < n_x, v1 = base + i0 + 1 < n_x;
+                const bool v8 = base + i0 + 8 < n_x, v9 = base + i0 + 9 < n_x;
+                uint32_t bh0 = 0, bh1 = 0, bl0 = 0, bl1 = 0;
+                if (g < NV) {
+                  const float2 h01 = *reinterpret_cast<const float2*>(bs + g * MMA_BS + i0);
+                  const float2 h89 = *reinterpret_cast<const float2*>(bs + g * MMA_BS + i0 + 8);
+                  const float2 l01 = *reinterpret_cast<const float2*>(bs + (NV + g) * MMA_BS + i0);
+                  const float2 l89 = *reinterpret_cast<const float2*>(bs + (NV + g) * MMA_BS + i0 + 8);
+                  bh0 = bf16x2(h01.x, h01.y);
+                  bh1 = bf16x2(h89.x, h89.y);
+                  bl0 = bf16x2(l01.x, l01.y);
+                  bl1 = bf16x2(l89.x, l89.y);
+                }
+                if constexpr (D == 2) {
+                  float g0, g1, g8, g9;
+                  geval(x0, x1, 0, v0, v1, g0, g1);
+                  geval(x8, x9, 0, v8, v9, g8, g9);
+                  uint32_t h01, l01, h89, l89;
+                  split_bf16x2(g0, g1, h01, l01);
+                  split_bf16x2(g8, g9, h89, l89);
+                  mma_bf16(acc, h01, l01, h89, l89, bh0, bh1);
+                  mma_bf16(acc, h01, l01, h89, l89, bl0, bl1);
+                } else {
+                  float a0, a1, a8, a9, c0, c1, c8, c9;
+                  geval(x0, x1, 0, v0, v1, a0, a1);
+                  geval(x8, x9, 0, v8, v9, a8, a9);
+                  geval(x0, x1, 1, v0, v1, c0, c1);
+                  geval(x8, x9, 1, v8, v9, c8, c9);
+                  uint32_t ha01, la01, ha89, la89, hc01, lc01, hc89, lc89;
+                  split_bf16x2(a0, a1, ha01, la01);
+                  split_bf16x2(a8, a9, ha89, la89);
+                  split_bf16x2(c0, c1, hc01, lc01);
+                  split_bf16x2(c8, c9, hc89, lc89);
+                  mma_bf16(acc, ha01, hc01, ha89, hc89, bh0, bh1);
+                  mma_bf16(acc, ha01, hc01, ha89, hc89, bl0, bl1);
+                  mma_bf16(acc, la01, lc01, la89, lc89, bh0, bh1);
+                }
+              }
+            }
+            __syncwarp();  // the batch is read before the next one is staged
+          }
+          return;
+        }
         for (int base = 0; base < n_x; base += G::XPI) {
           const int o = base + xl;
           const bool valid = o < n_x;
@@ -1374,6 +1634,29 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 #pragma unroll
           for (int t = NBLK + NQ; t < NRS; t++) v[t] = 0;
         }
+        if constexpr (MMA != 0) {
+          // the tensor-core accumulators: H_c(y) for the thread's fragment entries (rows: inner
+          // points q = lane/4 (+8); columns c = 2 (lane % 4) and the next one; 2D: rows 8-15 hold
+          // the low-part products of the same inner points), contracted like the lane sums above
+          // (the reduce-scatter below adds every thread's share)
+          const int q0 = lane >> 2, c0 = 2 * (lane & 3);
+#pragma unroll
+          for (int r = 0; r < MROWS; r++) {
+            const int q = q0 + 8 * r;
+            const float h0 = D == 2 ? acc[0] + acc[2] : acc[2 * r];
+            const float h1 = D == 2 ? acc[1] + acc[3] : acc[2 * r + 1];
+            if (q < NQ) {
+#pragma unroll
+              for (int c = 0; c < NV; c++) {
+                const float hc = c == c0 ? h0 : (c == c0 + 1 ? h1 : 0.f);
+#pragma unroll
+                for (int a = 0; a < NV; a++) v[a * NV + c] += sWB[q * NV + a] * hc;
+              }
+#pragma unroll
+              for (int qq = 0; qq < NQ; qq++) v[NBLK + qq] += qq == q ? h0 + h1 : 0.f;
+            }
+          }
+        }
         // reduce-scatter over the warp: every step sends half of the remaining values to the
         // partner lane and adds the half it keeps; 2D: four steps (offsets 16..2) and a final
         // sum with lane ^ 1 (lane L holds entry L >> 1), 3D: five steps (lane L holds entry L)
@@ -1545,7 +1828,7 @@ struct QShape {
   int ctas_per_sm = 0;
 };
 
-template <int D, typename R, int KERN, bool DIRECT = false, bool BATCHED = false>
+template <int D, typename R, int KERN, bool DIRECT = false, bool BATCHED = false, int MMA = 0>
 nl_status launch_quad(const QParams& P, cudaStream_t s, const QBatch& Bt = QBatch{nullptr, nullptr, 0, 0},
                       QShape shape = QShape{}) {
   int dev = 0;
@@ -1553,8 +1836,9 @@ nl_status launch_quad(const QParams& P, cudaStream_t s, const QBatch& Bt = QBatc
   int nsm = 0;
   NL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const size_t tbl = table_bytes<R>();
-  const size_t per_warp =
-      WarpMem<D, R>::bytes(P.scap) + (BATCHED ? ((sizeof(QParams) + 15) & ~size_t(15)) : 0);
+  const size_t per_warp = WarpMem<D, R>::bytes(P.scap) +
+                          (BATCHED ? ((sizeof(QParams) + 15) & ~size_t(15)) : 0) +
+                          mma_stage_bytes<D>(MMA);
   // default: at most 110 KB per CTA (two CTAs per SM); a requested shape may use up to 220 KB
   const size_t limit = (size_t)(shape.warps > 0 ? 220 : 110) * 1024;
   const int max_warps = QLaunch<D>::THREADS / 32;
@@ -1564,7 +1848,7 @@ nl_status launch_quad(const QParams& P, cudaStream_t s, const QBatch& Bt = QBatc
   const size_t smem = tbl + warps * per_warp;
   if (smem > (size_t)220 * 1024)
     return fail(NL_EINTERNAL, "assembly kernel needs %zu bytes of shared memory", smem);
-  auto kern = k_quad<D, R, KERN, DIRECT, BATCHED>;
+  auto kern = k_quad<D, R, KERN, DIRECT, BATCHED, MMA>;
   NL_TRY(allow_smem(kern, smem));
   int per_sm = 0;
   NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -1685,6 +1969,163 @@ inline nl_status fill_qparams(const char* who, const nl_mesh* m, const nl_pairs*
   for (int q = 0; q < r.n; q++) {
     for (int a = 0; a <= D; a++) P->B[q][a] = r.bary[q][a];
     P->W[q] = r.w[q];
+  }
+  return NL_OK;
+}
+
+// ---- single-problem assembly (nl_assemble) --------------------------------------------------
+// CUDA events around every launch of the assembly kernel and of the scatter, read after the
+// assembly's final synchronisation.
+struct PhaseTimer {
+  std::vector<cudaEvent_t> ev[2];
+  ~PhaseTimer() {
+    for (auto& v : ev)
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+  }
+  nl_status mark(int phase, cudaStream_t s) {
+    cudaEvent_t e;
+    NL_CUDA(cudaEventCreate(&e));
+    ev[phase].push_back(e);
+    NL_CUDA(cudaEventRecord(e, s));
+    return NL_OK;
+  }
+  // summed elapsed time of the (start, end) pairs of one phase, after synchronisation
+  double ms(int phase) const {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < ev[phase].size(); i += 2) {
+      float x = 0.f;
+      if (cudaEventElapsedTime(&x, ev[phase][i], ev[phase][i + 1]) == cudaSuccess) t += x;
+    }
+    return t;
+  }
+  int launches(int phase) const { return (int)(ev[phase].size() / 2); }
+};
+
+template <int D, typename R, int KERN, int MMA>
+nl_status run_assembly(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s,
+                       unsigned long long* scratch, int* err, PhaseTimer& T) {
+  const int NB = (D + 1) * (D + 1);
+  // the block buffer holds the cross blocks of one batch of pairs
+  size_t free_b = 0, total_b = 0;
+  NL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
+  if (g_block_budget) budget = std::min(budget, g_block_budget);
+  int64_t batch = std::max<int64_t>(1 << 20, (int64_t)(budget / (sizeof(R) * NB)));
+  batch = std::min<int64_t>(batch, p->n_pairs);
+  DevBuf<R> blk;
+  DevBuf<double> selfblk;
+  NL_TRY(blk.alloc((size_t)batch * NB, s));
+  NL_TRY(selfblk.alloc((size_t)m->n_elem * NB, s));
+  NL_CUDA(cudaMemsetAsync(selfblk.p, 0, sizeof(double) * m->n_elem * NB, s));
+  std::vector<int64_t> h_off(m->n_elem + 1);
+  NL_CUDA(cudaMemcpyAsync(h_off.data(), p->pair_off, sizeof(int64_t) * (m->n_elem + 1),
+                          cudaMemcpyDeviceToHost, s));
+  NL_CUDA(cudaStreamSynchronize(s));
+  P.blk = blk.p;
+  P.selfblk = selfblk.p;
+  for (int64_t b0 = 0; b0 < p->n_pairs; b0 += batch) {
+    const int64_t b1 = std::min(p->n_pairs, b0 + batch);
+    P.p_begin = b0;
+    P.p_end = b1;
+    NL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s));  // work counter
+    NL_TRY(T.mark(0, s));
+    NL_TRY((launch_quad<D, R, KERN, false, false, MMA>(P, s)));
+    NL_TRY(T.mark(0, s));
+    NL_TRY(T.mark(1, s));
+    NL_TRY((launch_scatter<D, R>(m, p, b0, b1, blk.p, nullptr, 0, values, err, s, h_off.data())));
+    NL_TRY(T.mark(1, s));
+  }
+  NL_TRY(T.mark(1, s));
+  NL_TRY((launch_scatter<D, R>(m, p, 0, 0, blk.p, selfblk.p, 1, values, err, s, h_off.data())));
+  NL_TRY(T.mark(1, s));
+  if (std::is_same<R, float>::value) {
+    k_diag_from_rows<<<NL_CNT((unsigned)((m->n_vert * 32 + 255) / 256)), 256, 0, s>>>(
+        m->n_vert, p->row_ptr, p->col, values);
+    NL_CUDA(cudaGetLastError());
+  }
+  return NL_OK;
+}
+
+// One problem (nl_assemble): the batches of pairs through the assembly kernel, each followed
+// by the scatter of its cross blocks, then the self blocks (and, in FP32, the diagonals from
+// the row sums).  MMA = 0: FP64 or FP32 point-pair arithmetic by prec; 1 / 2: the FP32 path
+// with the contraction on the tensor cores in TF32 / BF16.
+template <int MMA>
+nl_status assemble_single(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                          const nl_quad_params* qp, nl_precision prec, double* values,
+                          nl_assemble_stats* st) {
+  QParams P;
+  NL_TRY(fill_qparams("nl_assemble", m, p, kp, qp, prec, &P));
+  const int D = m->dim;
+  cudaStream_t s = m->stream;
+  DevBuf<unsigned long long> scratch;
+  DevBuf<int> err;
+  NL_TRY(scratch.alloc(8, s));
+  NL_TRY(err.alloc(1, s));
+  NL_CUDA(cudaMemsetAsync(scratch.p, 0, sizeof(unsigned long long) * 8, s));
+  NL_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+  NL_CUDA(cudaMemsetAsync(values, 0, sizeof(double) * (p->nnz ? p->nnz : 1), s));
+  P.counter = scratch.p;
+  P.stats = scratch.p + 1;
+  P.err = err.p;
+  cudaEvent_t e0, e1;
+  NL_CUDA(cudaEventCreate(&e0));
+  NL_CUDA(cudaEventCreate(&e1));
+  NL_CUDA(cudaEventRecord(e0, s));
+  nl_status rc = NL_OK;
+  const bool f32 = prec != NL_PREC_FP64;
+  const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
+  PhaseTimer T;
+  if (p->n_pairs > 0) {
+    if constexpr (MMA != 0) {
+      if (D == 2) rc = gauss ? run_assembly<2, float, 1, MMA>(m, p, P, values, s, scratch.p, err.p, T)
+                             : run_assembly<2, float, 0, MMA>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly<3, float, 1, MMA>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly<3, float, 0, MMA>(m, p, P, values, s, scratch.p, err.p, T);
+    } else if (D == 2) {
+      if (f32) rc = gauss ? run_assembly<2, float, 1, 0>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly<2, float, 0, 0>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly<2, double, 1, 0>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly<2, double, 0, 0>(m, p, P, values, s, scratch.p, err.p, T);
+    } else {
+      if (f32) rc = gauss ? run_assembly<3, float, 1, 0>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly<3, float, 0, 0>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly<3, double, 1, 0>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly<3, double, 0, 0>(m, p, P, values, s, scratch.p, err.p, T);
+    }
+  }
+  cudaEventRecord(e1, s);
+  unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int herr = 0;
+  cudaMemcpyAsync(hs, scratch.p, sizeof hs, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&herr, err.p, sizeof herr, cudaMemcpyDeviceToHost, s);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != NL_OK) return rc;
+  if (ce != cudaSuccess) return cuda_fail(ce, "nl_assemble");
+  if (herr) {
+    return fail(NL_EINTERNAL, "nl_assemble: device check failed (code %d: %s)", herr,
+                (herr & ERR_STACK) ? "refinement stack capacity exceeded" : "CSR entry missing");
+  }
+  if (st) {
+    const int nq = D == 2 ? 7 : 14;
+    st->n_pairs = p->n_pairs;
+    st->n_items = (int64_t)hs[1];
+    st->n_point_pairs = (int64_t)hs[1] * nq * nq;
+    st->n_exact_checks = (int64_t)hs[3];
+    st->ms_assemble = ms;
+    st->n_eval_point_pairs = (int64_t)hs[4];
+    st->n_closed_items = (int64_t)hs[5];
+    st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
+    st->precision_run = MMA == 1 ? NL_PREC_MIXED_TF32
+                        : MMA == 2 ? NL_PREC_MIXED_BF16
+                        : (f32 ? NL_PREC_FP32 : NL_PREC_FP64);
+    st->n_quad_launches = T.launches(0);
+    st->ms_quad = T.ms(0);
+    st->ms_scatter = T.ms(1);
   }
   return NL_OK;
 }

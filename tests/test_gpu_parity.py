@@ -251,3 +251,38 @@ def test_euclidean_min_dist_counts_and_values(case):
         assert st.n_items == ost.n_integrations, (name, prec)
         assert st.n_point_pairs == ost.n_point_pairs, (name, prec)
         assert _rel(vals, ovals) < tol and _maxrel(vals, ovals) < tol, (name, prec)
+
+
+# The tensor-core paths (NL_PREC_MIXED_TF32 / BF16): the contraction over the outer points on
+# mma.sync with two-part split operands, everything else as in NL_PREC_FP32.  Tolerances
+# against the FP64 oracle, relative Frobenius and per entry: TF32 parts carry about 22
+# significant bits (as FP32: 2e-6); BF16 parts about 16 (2e-5).
+MMA_TOL = {nl.NL_PREC_MIXED_TF32: 2e-6, nl.NL_PREC_MIXED_BF16: 2e-5}
+
+
+@pytest.mark.parametrize("prec", [nl.NL_PREC_MIXED_TF32, nl.NL_PREC_MIXED_BF16],
+                         ids=["tf32", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_tensor_core_values(case, prec):
+    name, mk, delta, eps, L_max, L_min, kernel = case
+    mesh = mk()
+    *_, ovals, ost = _oracle(mesh, delta, eps, L_max, L_min, kernel)
+    off, pl, rp, col, vals, st, _ = _gpu(mesh, delta, eps, L_max, L_min, kernel, prec)
+    assert st.precision_run == prec
+    assert st.n_point_pairs == ost.n_point_pairs and st.n_items == ost.n_integrations
+    tol = MMA_TOL[prec]
+    assert _rel(vals, ovals) < tol, (name, _rel(vals, ovals))
+    assert _maxrel(vals, ovals) < tol, (name, _maxrel(vals, ovals))
+
+
+def test_precision_run_is_reported():
+    mesh = structured_mesh(2, 4, 0.25, 0.0, 2)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, 0.4, 0.05)
+    for prec in (nl.NL_PREC_FP64, nl.NL_PREC_FP32, nl.NL_PREC_MIXED_TF32, nl.NL_PREC_MIXED_BF16):
+        _, st = nl.nl_assemble(m, p, 0.4, 0.05, 2, precision=prec)
+        assert st.precision_run == prec
+    # the no-allocation entry point and plans run the mixed precisions in FP32 and say so
+    pl = nl.Plan([(m, p, 0.4, 0.05, 2, 1, 0)], precision=nl.NL_PREC_MIXED_TF32)
+    pl.execute()
+    assert pl.sync()[0].precision_run == nl.NL_PREC_FP32
