@@ -615,3 +615,30 @@ def test_quadratic_solution_converges_at_rate_two():
         errs.append(r["err_omega"])
     rate = math.log(errs[0] / errs[1], 2)
     assert 1.8 < rate < 2.3, (errs, rate)
+
+
+def test_mollified_solution_converges_at_rate_two_in_eps():
+    # Sec. 6, eps-convergence (Table 4): the mollifier's contribution to the error behaves like
+    # C eps^p2 with p2 about 2.  Fixed P1 mesh, u = x^4 + y^4 with the forcing of the sharp
+    # kernel (eps -> 0), kernel gamma_eps assembled for eps = delta/4 ... delta/32, each with
+    # the band resolved (sub-elements of Algorithm 1 no larger than eps: L_max grows by one
+    # per halving).  The differences between successive discrete solutions must shrink by 4
+    # per halving.  The garbled mollifier argument ((delta - eps) - r)/eps, or a constant that
+    # does not follow eps, would give first order.
+    delta, n = 0.3, 4
+    h = 1.0 / n
+    layer = int(np.ceil((delta + delta / 4) / h - 1e-9))
+    mesh = structured_mesh(2, n, h, 0.0, layer)
+    C0 = O.kernel_constant(2, 0, delta, 1e-9)
+    us = []
+    for div in (4, 8, 16, 32):
+        eps = delta / div
+        L_max = int(np.ceil(np.log2(h / eps))) + 1
+        off, pl = O.pairs(mesh, delta, eps)
+        rp, col = O.csr(mesh, off, pl)
+        vals, _ = O.assemble(mesh, off, pl, rp, col, delta, eps, L_max)
+        F = O.rhs(mesh, rp, col, vals, 3, 0, delta, 1e-9, C0)  # f = -L_0 u (sharp kernel)
+        us.append(O.solve_dense(mesh, rp, col, vals, F, 3))
+    d = [np.abs(us[k + 1] - us[k]).max() for k in range(3)]
+    p2 = [math.log2(d[k] / d[k + 1]) for k in range(2)]
+    assert all(1.8 < p < 2.2 for p in p2), (d, p2)
