@@ -13,7 +13,8 @@ solution and the difference of the two matrices.
 Beside the headline the JSON line carries: the FP64 step, the roofline of the assembly kernel
 (FP32 and FP64), the achieved bandwidth of the HBM-bound kernels (scatter, SpMV), the
 public-API end-to-end rate from pinned host buffers (e2e), the 2D workload at h = 1/256 in its
-four (eps, kernel) combinations (mixed and FP64 steps), a batching leg (128 small problems:
+four (eps, kernel) combinations (mixed and FP64 steps), an eps-convergence study (the P1
+analogue of the paper's Table 4: error against cost over eps and L_max), a batching leg (128 small problems:
 sequential assembly against one plan), a serving leg (the first --serve-requests requests of
 the seeded stream, closed loop and then open loop at 70% load) and the oracle timed on all
 host cores on a bounded sample (cpu_baseline).
@@ -69,11 +70,20 @@ def parse():
     ap.add_argument("--ref-step-seconds", type=float, default=3.0,
                     help="--impl reference: wall seconds of one step's oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mindist-l2", type=int, default=1,
+                    help="Algorithm 1's refinement test with the Euclidean minimum distance "
+                         "(NL_QUAD_MINDIST_L2; the matrix is the same) in the timed steps")
+    ap.add_argument("--eps-study", type=int, default=1,
+                    help="the eps-convergence leg (0 = skip)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests of the seeded 512-request serving stream replayed by the "
                          "serving leg (0 = skip; 512 = the whole stream)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-open-loop", type=int, default=1,
+                    help="also replay the requests open loop at 70%% load (0 = closed loop only)")
+    ap.add_argument("--serve-l2", type=int, default=1,
+                    help="serving requests use NL_QUAD_MINDIST_L2 (same matrices, less work)")
     ap.add_argument("--batch-problems", type=int, default=128,
                     help="small problems of the batching leg (0 = skip)")
     ap.add_argument("--profile", action="store_true",
@@ -234,7 +244,7 @@ FP64_PEAK_TFLOPS = 1.19  # measured FP64 FMA chain of this GPU model
 
 
 def _measure(nl, torch, stream, dmesh, mesh, w, prec, steps, warmup, flush, world,
-             keep_last=False):
+             keep_last=False, l2=False):
     """Times `steps` whole steps (pairs, pattern, assembly, right-hand side, BiCGStab) after
     `warmup` untimed ones; the L2 is flushed before every timed step, outside the timing.
     Returns per-step times, solve times, the last step's stats, solution and (keep_last)
@@ -245,7 +255,8 @@ def _measure(nl, torch, stream, dmesh, mesh, w, prec, steps, warmup, flush, worl
 
     def step():
         p = nl.nl_pairs_build(dmesh, w.delta, w.eps)
-        A, st = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec)
+        A, st = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec,
+                               mindist_l2=l2)
         b = nl.nl_rhs(dmesh, A, g, f_const=f_const)
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -286,13 +297,13 @@ def _measure(nl, torch, stream, dmesh, mesh, w, prec, steps, warmup, flush, worl
     return dict(times=times, solve_ms=solve_ms, stats=stats, last=last, launches=launches)
 
 
-def _roofline(nl, dmesh, mesh, w, prec, stats):
+def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False):
     """Algorithmic flops of the assembly kernel over the measured steps against the FP32 ALU
     (or FP64 pipe) peak; the band count comes from one extra untimed launch with
     NL_QUAD_COUNT_BAND."""
     pb = nl.nl_pairs_build(dmesh, w.delta, w.eps)
     _, stb = nl.nl_assemble(dmesh, pb, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec,
-                            count_band=True)
+                            count_band=True, mindist_l2=l2)
     flops = roofline_flops(mesh.dim, stb)
     quad_ms = statistics.mean(s.ms_quad for s in stats)
     f32 = prec != nl.NL_PREC_FP64
@@ -363,8 +374,9 @@ def run_ours(args, rank, world, local):
     # mixed headline (timed with clock sampling)
     clk = ClockSampler(local)
     clk.start()
+    L2 = bool(args.mindist_l2)
     mx = _measure(nl, torch, stream, dmesh, mesh, w, nl.NL_PREC_FP32, args.steps, args.warmup,
-                  flush, world, keep_last=args.fp64_steps > 0)
+                  flush, world, keep_last=args.fp64_steps > 0, l2=L2)
     clocks = clk.stop()
     ms = statistics.mean(mx["times"])
     ms_max = allmax(world, ms)
@@ -373,7 +385,7 @@ def run_ours(args, rank, world, local):
     value = world * n_pairs / (ms_max / 1e3)
     err_mixed = l2_err_omega(mesh, mx["last"]["u"], rule)
     kern_ms = statistics.mean(s.ms_assemble for s in mx["stats"])
-    stb, roof = _roofline(nl, dmesh, mesh, w, nl.NL_PREC_FP32, mx["stats"])
+    stb, roof = _roofline(nl, dmesh, mesh, w, nl.NL_PREC_FP32, mx["stats"], l2=L2)
     tb = TRAFFIC_BYTES_PER_PAIR.get(mesh.dim)
     roof["traffic"] = round(tb * n_pairs / roof["launches_per_assembly"]) if tb else None
     roof["traffic_per_launch_note"] = ("DRAM bytes per element pair of the ncu capture of the "
@@ -388,13 +400,13 @@ def run_ours(args, rank, world, local):
         _measure(nl, torch, stream, dc1, mc1, wc1, nl.NL_PREC_FP64, 1, 0, flush, world)
         del dc1
         f64 = _measure(nl, torch, stream, dmesh, mesh, w, nl.NL_PREC_FP64, args.fp64_steps, 0,
-                       flush, world, keep_last=True)
+                       flush, world, keep_last=True, l2=L2)
         ms64 = allmax(world, statistics.mean(f64["times"]))
         err64 = l2_err_omega(mesh, f64["last"]["u"], rule)
         v32, v64 = mx["last"]["values"], f64["last"]["values"]
         a_rel = float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64))
         a_max = float(np.abs(v32 - v64).max() / np.abs(v64).max())
-        _, roof64 = _roofline(nl, dmesh, mesh, w, nl.NL_PREC_FP64, f64["stats"])
+        _, roof64 = _roofline(nl, dmesh, mesh, w, nl.NL_PREC_FP64, f64["stats"], l2=L2)
         fp64 = {"dtype": "f64", "ms_per_step": round(ms64, 3), "steps": args.fp64_steps,
                 "value": round(world * n_pairs / (ms64 / 1e3), 1),
                 "assembly_ms": round(statistics.mean(s.ms_assemble for s in f64["stats"]), 3),
@@ -408,7 +420,21 @@ def run_ours(args, rank, world, local):
     rp = p.export(mesh.n_elem, mesh.n_vert)[2]
     sc_bytes = _scatter_bytes(mesh, pinfo, rp, mesh.dim, 4)
     sc_ms = statistics.mean(s.ms_scatter for s in mx["stats"])
-    A, _ = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, nl.NL_PREC_FP32)
+    A, _ = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, nl.NL_PREC_FP32,
+                          mindist_l2=L2)
+    # the same FP32 assembly with the paper's default refinement test (eq. mindist) and with the
+    # tensor-core contraction (TF32, BF16), one timed call each
+    variants = {}
+    for vname, vprec, vl2 in (("fp32_eq_mindist", nl.NL_PREC_FP32, False),
+                              ("mixed_tf32", nl.NL_PREC_MIXED_TF32, L2),
+                              ("mixed_bf16", nl.NL_PREC_MIXED_BF16, L2)):
+        _, vst = nl.nl_assemble(dmesh, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, vprec,
+                                mindist_l2=vl2)
+        variants[vname] = {"assembly_ms": round(vst.ms_assemble, 3),
+                           "kernel_ms": round(vst.ms_quad, 3),
+                           "quad_pt_pairs": vst.n_point_pairs,
+                           "evaluated_point_pairs": vst.n_eval_point_pairs,
+                           "precision_run": int(vst.precision_run)}
     hbm_peak = peaks.get("hbm_gbs", 6746.0)
     spmv = _spmv_rate(nl, torch, stream, A, mesh, pinfo[1])
     spmv["frac"] = round(spmv["achieved_gbs"] / hbm_peak, 4)
@@ -448,6 +474,10 @@ def run_ours(args, rank, world, local):
                      "p99": round(float(np.percentile(mx["solve_ms"], 99)), 3)},
         "roofline": roof,
         "hbm_kernels": hbm,
+        "quad_rule": ("Algorithm 1 with the Euclidean approximate minimum distance of Sec. 5.1 "
+                      "(NL_QUAD_MINDIST_L2; same matrix as eq. mindist)" if L2 else
+                      "Algorithm 1 with eq. mindist"),
+        "assembly_variants": variants,
         "gpu_launches": int(mx["launches"]),  # this library's kernels in the whole timed region
         "gpu_launches_per_step": int(mx["launches"] / max(1, args.steps)),
         "clocks": clocks,
@@ -457,6 +487,8 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e_ours(args, mesh, w, stream, world)
     if args.c2_steps > 0:
         out["c2_2d"] = run_c2_block(args, nl, torch, stream, flush, world)
+    if args.eps_study:
+        out["eps_study"] = run_eps_study(args)
     if args.batch_problems > 0:
         out["batching"] = run_batching(args)
     if args.serve_requests > 0:
@@ -474,11 +506,12 @@ def run_c2_block(args, nl, torch, stream, flush, world):
         w, mesh = workload(name)
         rule = nl.nl_quad_rule(2)
         dm = nl.mesh_from(mesh)
+        L2 = bool(args.mindist_l2)
         mx = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP32, args.c2_steps, 2, flush,
-                      world, keep_last=args.c2_fp64_steps > 0)
+                      world, keep_last=args.c2_fp64_steps > 0, l2=L2)
         ms = statistics.mean(mx["times"])
         st = mx["stats"][-1]
-        _, roof = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP32, mx["stats"])
+        _, roof = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP32, mx["stats"], l2=L2)
         tb = TRAFFIC_BYTES_PER_PAIR.get(2)
         roof["traffic"] = round(tb * st.n_pairs / roof["launches_per_assembly"]) if tb else None
         r = {"workload": describe(w, mesh), "element_pairs": st.n_pairs,
@@ -491,7 +524,7 @@ def run_c2_block(args, nl, torch, stream, flush, world):
              "roofline": roof}
         if args.c2_fp64_steps > 0:
             f64 = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP64, args.c2_fp64_steps, 0,
-                           flush, world, keep_last=True)
+                           flush, world, keep_last=True, l2=L2)
             ms64 = statistics.mean(f64["times"])
             v32, v64 = mx["last"]["values"], f64["last"]["values"]
             r["fp64"] = {"ms_per_step": round(ms64, 3),
@@ -545,7 +578,7 @@ def e2e_ours(args, mesh, w, stream, world):
         dm = nl.nl_mesh_create(mesh.dim, coords, conn, eio, nf)
         p = nl.nl_pairs_build(dm, w.delta, w.eps)
         A, st = nl.nl_assemble(dm, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel,
-                               nl.NL_PREC_FP32)
+                               nl.NL_PREC_FP32, mindist_l2=bool(args.mindist_l2))
         b = nl.nl_rhs(dm, A, gp, f_const=f_const)
         u, it, rr, _ = nl.nl_solve(A, b, gp, solver=1, rtol=1e-10, max_iter=20000,
                                    precision=nl.NL_PREC_FP32)
@@ -606,6 +639,80 @@ def run_batching(args):
             "plan_gpu_ms": round(st[0].ms_assemble, 3), "shape": plan.shape()}
 
 
+def l2_norm_p1(mesh, v, rule):
+    """L2 norm over Omega of the P1 function with nodal values v (degree-5 rule)."""
+    b, w = rule
+    P = mesh.points()
+    conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
+    V = P[conn]
+    if mesh.dim == 2:
+        vol = 0.5 * np.abs((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1]) -
+                           (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
+    else:
+        vol = np.abs(np.linalg.det(V[:, 1:] - V[:, :1])) / 6.0
+    vq = np.einsum("qv,ev->eq", b, v[conn])
+    return float(math.sqrt(np.sum(vol[:, None] * w[None, :] * vq * vq)))
+
+
+def run_eps_study(args):
+    """eps-convergence study (the P1 analogue of the paper's Table 4): Omega = (0,1)^2,
+    h = 1/32, delta = 0.1, u = x^4 + y^4 with the forcing of the sharp kernel
+    (f = -12 (x^2 + y^2) - 2 delta^2, its P1 interpolant), the mollified kernel assembled for
+    eps = delta/4 ... delta/64 at L_max = L0 - 1, L0, L0 + 1, where L0 makes Algorithm 1's
+    smallest sub-elements about eps (L0 = ceil(log2(h / eps)) + 1).  Reports per (eps, L_max)
+    the FP32 assembly time and work, and two differences of discrete solutions in L2(Omega):
+    to the same eps at L_max + 1 (quadrature error) and, at L0, to eps / 2 (the mollifier's
+    contribution, expected to fall like eps^2)."""
+    import torch
+    from paper_2101_08825_gb300 import nl
+    n, delta = 32, 0.1
+    h = 1.0 / n
+    divs = (4, 8, 16, 32, 64)
+    layer = int(math.ceil((delta + delta / divs[0]) / h - 1e-9))
+    from nl_inputs import structured_mesh
+    mesh = structured_mesh(2, n, h, 0.0, layer)
+    rule = nl.nl_quad_rule(2)
+    X = mesh.coords
+    g = (X ** 4).sum(axis=0)
+    f = -12.0 * (X ** 2).sum(axis=0) - 2.0 * delta * delta
+    dm = nl.mesh_from(mesh)
+    rows, sol = [], {}
+    for div in divs:
+        eps = delta / div
+        L0 = int(math.ceil(math.log2(h / eps))) + 1
+        p = nl.nl_pairs_build(dm, delta, eps)
+        for L in (L0 - 1, L0, L0 + 1, L0 + 2):
+            if L < 1:
+                continue
+            nl.nl_assemble(dm, p, delta, eps, L, precision=nl.NL_PREC_FP32)  # warm
+            A, st = nl.nl_assemble(dm, p, delta, eps, L, precision=nl.NL_PREC_FP32)
+            b = nl.nl_rhs(dm, A, g, f_nodes=f)
+            u, it, rr, _ = nl.nl_solve(A, b, g, solver=1, rtol=1e-12, max_iter=20000,
+                                       precision=nl.NL_PREC_FP32)
+            sol[(div, L)] = u
+            rows.append({"eps": f"delta/{div}", "L_max": L, "L0": L0,
+                         "assembly_ms": round(st.ms_assemble, 3),
+                         "point_pairs": st.n_point_pairs, "element_pairs": st.n_pairs})
+            del A, b
+    for r in rows:
+        div, L = int(r["eps"].split("/")[1]), r["L_max"]
+        if (div, L + 1) in sol:
+            r["quad_err_l2"] = l2_norm_p1(mesh, sol[(div, L)] - sol[(div, L + 1)], rule)
+    conv = []
+    for k in range(len(divs) - 1):
+        a, c = divs[k], divs[k + 1]
+        La = int(math.ceil(math.log2(h / (delta / a)))) + 1
+        Lc = int(math.ceil(math.log2(h / (delta / c)))) + 1
+        conv.append({"eps": f"delta/{a}", "diff_to_half_eps_l2":
+                     l2_norm_p1(mesh, sol[(a, La)] - sol[(c, Lc)], rule)})
+    for k in range(len(conv) - 1):
+        conv[k]["p2"] = round(math.log2(conv[k]["diff_to_half_eps_l2"] /
+                                        conv[k + 1]["diff_to_half_eps_l2"]), 3)
+    return {"workload": "Omega=(0,1)^2, h=1/32, delta=0.1, u=x^4+y^4, sharp-kernel forcing; "
+                        "FP32 assembly, FP32-in-FP64 BiCGStab to 1e-12",
+            "runs": rows, "eps_convergence": conv}
+
+
 def run_serving(args):
     """Serving leg: the first N requests of the seeded 512-request stream (mixed 2D/3D
     meshes, delta in [2h, 6h], constant or truncated-Gaussian kernel), each running mesh,
@@ -623,7 +730,7 @@ def run_serving(args):
         return nl.make_request(r.dim, (r.n,) * r.dim, 1.0 / r.n, (0.0,) * r.dim, r.layer,
                                r.delta, r.eps, r.L_max, kernel=r.kernel,
                                precision=nl.NL_PREC_FP32, ms=1, solver=1, rtol=1e-10,
-                               jitter=0.1, seed=i)
+                               jitter=0.1, seed=i, mindist_l2=args.serve_l2)
 
     def replay(times):
         with nl.Server(budget, args.serve_slots) as S:
@@ -639,26 +746,45 @@ def run_serving(args):
             p50, p99, sps = S.stats()
         ok = [r for r in results if r.status == nl.NL_OK]
         lat = [r.t_done_ms - r.t_submit_ms for r in ok]
+        queue = [r.t_start_ms - r.t_submit_ms for r in ok]
+        run = [r.t_done_ms - r.t_start_ms for r in ok]
+        per = [{"dim": rq.dim, "n_elem": rq.n_elem, "pairs": int(r.n_pairs),
+                "queue_ms": round(r.t_start_ms - r.t_submit_ms, 1),
+                "run_ms": round(r.t_done_ms - r.t_start_ms, 1), "group": int(r.group)}
+               for rq, r in zip(reqs, results) if r.status == nl.NL_OK]
         return dict(p50=p50, p99=p99, sps=sps, wall=wall, failed=len(results) - len(ok),
-                    pairs=sum(r.n_pairs for r in ok), lat=lat)
+                    pairs=sum(r.n_pairs for r in ok), lat=lat, queue=queue, run=run, per=per,
+                    grouped=sum(1 for r in ok if r.group >= 0))
 
     sat = replay([0.0] * len(reqs))
     rate = 0.7 * sat["sps"]
     gaps = np.diff([0.0] + [r.arrival_s for r in reqs])
     scale = (1.0 / rate) / max(float(np.mean(gaps)), 1e-9) if rate > 0 else 0.0
     arrivals = np.cumsum(gaps * scale)
-    ol = replay(list(arrivals))
-    return {"requests": len(reqs), "slots": args.serve_slots, "budget_bytes": budget,
-            "saturation": {"solves_per_s": round(sat["sps"], 3),
-                           "element_pairs_per_s": round(sat["pairs"] / sat["wall"], 1),
-                           "failed": sat["failed"]},
-            "open_loop": {"arrival_rate_per_s": round(rate, 3), "p50_ms": round(ol["p50"], 2),
-                          "p99_ms": round(ol["p99"], 2), "solves_per_s": round(ol["sps"], 3),
-                          "max_latency_ms": round(max(ol["lat"]), 2) if ol["lat"] else None,
-                          "failed": ol["failed"]},
+    ol = replay(list(arrivals)) if args.serve_open_loop else None
+
+    def pct(v, q):
+        return round(float(np.percentile(v, q)), 2) if v else None
+
+    out = {"requests": len(reqs), "slots": args.serve_slots, "budget_bytes": budget,
+           "quad_rule": "NL_QUAD_MINDIST_L2" if args.serve_l2 else "eq. mindist",
+           "saturation": {"solves_per_s": round(sat["sps"], 3),
+                          "element_pairs_per_s": round(sat["pairs"] / sat["wall"], 1),
+                          "p50_ms": round(sat["p50"], 2), "p99_ms": round(sat["p99"], 2),
+                          "grouped_requests": sat["grouped"], "failed": sat["failed"]}}
+    if ol is not None:
+        out["open_loop"] = {"arrival_rate_per_s": round(rate, 3), "p50_ms": round(ol["p50"], 2),
+                            "p99_ms": round(ol["p99"], 2), "solves_per_s": round(ol["sps"], 3),
+                            "max_latency_ms": round(max(ol["lat"]), 2) if ol["lat"] else None,
+                            "queue_ms_p50": pct(ol["queue"], 50), "queue_ms_p99": pct(ol["queue"], 99),
+                            "run_ms_p50": pct(ol["run"], 50), "run_ms_p99": pct(ol["run"], 99),
+                            "grouped_requests": ol["grouped"], "failed": ol["failed"],
+                            "per_request": ol["per"] if len(reqs) <= 64 else None}
+    out.update({
             "sample": f"first {len(reqs)} of the 512-request seeded stream (seed 0); phase 2 "
                       f"arrivals = the stream's exponential gaps rescaled to 70% of phase 1's "
-                      f"throughput"}
+                      f"throughput"})
+    return out
 
 
 # ---- the oracle on a bounded sample, on all host cores ---------------------------------------

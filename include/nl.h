@@ -328,16 +328,21 @@ typedef struct {
   int64_t n_pairs, n_point_pairs, nnz, n_vert;
   double t_submit_ms, t_start_ms, t_done_ms; /* host clock since nl_serve_create */
   char message[160];     /* error message when status != NL_OK, "" otherwise */
+  int32_t group;         /* batched group the request was assembled in (-1: alone) */
 } nl_result;
 
 /* device_mem_budget: bytes the server may hold at once (>= 64 MiB); max_slots (1..64):
- * requests in flight on the device at once, each on its own worker thread and CUDA stream of
- * the device that is current at creation.  A request is admitted when a slot is free and its
- * estimated footprint fits in the budget left by the requests in flight (a request larger
- * than the whole budget runs when nothing else does); requests wait in arrival order.
- * Requests run concurrently on the device; each keeps its mesh, pattern, matrix and Krylov
- * vectors on the device while it runs.  nl_serve_destroy lets running requests finish and
- * drops the ones still waiting. */
+ * worker threads, each with its own CUDA stream of the device that is current at creation.
+ * A request is admitted when a slot is free and its estimated footprint fits in the budget
+ * left by the requests in flight (a request larger than the whole budget runs when nothing
+ * else does); requests wait in arrival order.  Continuous batching: when a slot admits a
+ * small request (at most about 4e6 element pairs), later small requests of the same dimension
+ * and precision class (FP64 or not) that are waiting and fit the budget join it, up to 16:
+ * their meshes and patterns are built, one batched plan (nl_plan_*) assembles all of them in a
+ * single launch, and each is solved and completed on its own; the result's `group` says which
+ * requests shared a launch.  Requests on different slots run concurrently on the device; each
+ * keeps its mesh, pattern, matrix and Krylov vectors on the device while it runs.
+ * nl_serve_destroy lets running requests finish and drops the ones still waiting. */
 nl_status nl_serve_create(size_t device_mem_budget, int max_slots, nl_server** out);
 nl_status nl_serve_submit(nl_server* s, const nl_request* req, uint64_t* ticket);
 /* NL_EBUSY while the request is not finished; otherwise the result (once). */

@@ -17,6 +17,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -32,6 +33,7 @@ struct Job {
   nl_request req;
   nl_result res;
   size_t est = 0;
+  bool small = false;  // few enough pairs to be assembled in a batched plan with others
   bool done = false;
 };
 
@@ -61,6 +63,16 @@ size_t estimate_bytes(const nl_request& r, size_t block_budget) {
   return (size_t)(mesh + pairs * 4.0 + nnz * 12.0 + blk + solve) + ((size_t)16 << 20);
 }
 
+// Rough upper estimate of a request's element pairs.
+double estimate_pairs(const nl_request& r) {
+  const int D = r.dim;
+  double cells = 1.0;
+  for (int k = 0; k < D; k++) cells *= r.cells[k] + 2.0 * r.layer;
+  const double epc = D == 2 ? 2.0 : 6.0;
+  const double span = 2.0 * std::ceil((r.kernel.delta + r.kernel.eps) / r.h) + 3.0;
+  return cells * epc * epc * std::pow(span, D);
+}
+
 double ms_u(int ms, int D, const double* x) {
   double s = (ms == 0) ? 1.0 : 0.0;
   for (int k = 0; k < D; k++) {
@@ -77,6 +89,9 @@ struct nl_server {
   int slots = 0;
   int device = 0;
   size_t block_budget = (size_t)256 << 20;
+  double small_pairs = 4.0e6;  // requests below this many (estimated) pairs are batched
+  int max_group = 16;          // requests per batched plan
+  int64_t groups = 0;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> pending;
@@ -93,54 +108,57 @@ struct nl_server {
 
 namespace {
 
-// Runs one request on `stream`; fills res (status, counts, error, timings except submit).
-void run_request(nl_server* S, cudaStream_t stream, Job& job) {
-  const nl_request& r = job.req;
-  nl_result& res = job.res;
+// A request's mesh and pattern on the device, and the host copy of its mesh (for the
+// manufactured solution and the error).
+struct Prepared {
   nl_mesh* mesh = nullptr;
   nl_pairs* pairs = nullptr;
-  nl_matrix* A = nullptr;
-  nl_vector* rhs = nullptr;
-  nlx::g_block_budget = S->block_budget;
-  auto finish = [&](nl_status st) {
-    res.status = st;
-    if (st != NL_OK && res.message[0] == 0) snprintf(res.message, sizeof res.message, "%s", nl_last_error());
-    nl_vector_destroy(rhs);
-    nl_matrix_destroy(A);
-    nl_pairs_destroy(pairs);
-    nl_mesh_destroy(mesh);
-  };
-  nl_status st = nl_mesh_create_box(r.dim, r.cells, r.h, r.lo, r.layer, r.jitter, r.seed, stream, &mesh);
-  if (st != NL_OK) return finish(st);
   int dim = 0;
   int64_t nv = 0, ne = 0;
-  nl_mesh_info(mesh, &dim, &nv, &ne);
-  std::vector<double> coords((size_t)dim * nv);
-  std::vector<int32_t> conn((size_t)(dim + 1) * ne);
-  std::vector<uint8_t> eio(ne), nf(nv);
-  if ((st = nl_mesh_export(mesh, coords.data(), conn.data(), eio.data(), nf.data())) != NL_OK)
-    return finish(st);
-  if ((st = nl_pairs_build(mesh, r.kernel.delta, r.kernel.eps, &pairs)) != NL_OK) return finish(st);
-  nl_assemble_stats ast;
-  memset(&ast, 0, sizeof ast);
-  if ((st = nl_assemble(mesh, pairs, &r.kernel, &r.quad, r.precision, &A, &ast)) != NL_OK)
-    return finish(st);
+  std::vector<double> coords;
+  std::vector<int32_t> conn;
+  std::vector<uint8_t> eio, nf;
+  ~Prepared() {
+    nl_pairs_destroy(pairs);
+    nl_mesh_destroy(mesh);
+  }
+};
+
+nl_status prepare(const nl_request& r, cudaStream_t stream, Prepared& pr) {
+  NL_TRY(nl_mesh_create_box(r.dim, r.cells, r.h, r.lo, r.layer, r.jitter, r.seed, stream, &pr.mesh));
+  nl_mesh_info(pr.mesh, &pr.dim, &pr.nv, &pr.ne);
+  pr.coords.resize((size_t)pr.dim * pr.nv);
+  pr.conn.resize((size_t)(pr.dim + 1) * pr.ne);
+  pr.eio.resize(pr.ne);
+  pr.nf.resize(pr.nv);
+  NL_TRY(nl_mesh_export(pr.mesh, pr.coords.data(), pr.conn.data(), pr.eio.data(), pr.nf.data()));
+  return nl_pairs_build(pr.mesh, r.kernel.delta, r.kernel.eps, &pr.pairs);
+}
+
+// Right-hand side with lifting, solve and error of one request whose matrix is assembled.
+nl_status solve_and_report(const nl_request& r, Prepared& pr, nl_matrix* A,
+                           const nl_assemble_stats& ast, nl_result& res) {
+  const int dim = pr.dim;
+  const int64_t nv = pr.nv, ne = pr.ne;
   // u = g on the layer; f = -L_eps u = -Laplace(u) for the manufactured solutions used here
   std::vector<double> g(nv), f(nv);
   for (int64_t i = 0; i < nv; i++) {
     double x[3] = {0, 0, 0};
-    for (int k = 0; k < dim; k++) x[k] = coords[(size_t)k * nv + i];
+    for (int k = 0; k < dim; k++) x[k] = pr.coords[(size_t)k * nv + i];
     g[i] = ms_u(r.ms, dim, x);
     double lap = 0.0;
     for (int k = 0; k < dim; k++) lap += r.ms == 1 ? 2.0 : r.ms == 2 ? 6.0 * x[k] : 0.0;
     f[i] = -lap;
   }
-  if ((st = nl_rhs(mesh, A, f.data(), 0.0, g.data(), &rhs)) != NL_OK) return finish(st);
+  nl_vector* rhs = nullptr;
+  nl_status st = nl_rhs(pr.mesh, A, f.data(), 0.0, g.data(), &rhs);
+  if (st != NL_OK) return st;
   std::vector<double> u(nv);
   int iters = 0;
   double rr = 0.0;
   st = nl_solve(A, rhs, g.data(), r.solver, r.rtol, r.max_iter,
                 r.precision == NL_PREC_FP64 ? NL_PREC_FP64 : NL_PREC_FP32, u.data(), &iters, &rr);
+  nl_vector_destroy(rhs);
   if (st != NL_OK) snprintf(res.message, sizeof res.message, "%s", nl_last_error());
   res.iters = iters;
   res.rel_res = rr;
@@ -148,12 +166,12 @@ void run_request(nl_server* S, cudaStream_t stream, Job& job) {
   const nlx::Rule& rule = nlx::rule(dim);
   double err2 = 0.0;
   for (int64_t e = 0; e < ne; e++) {
-    if (!eio[e]) continue;
+    if (!pr.eio[e]) continue;
     double V[4][3] = {{0}}, uh[4];
     for (int a = 0; a <= dim; a++) {
-      const int32_t v = conn[(size_t)e * (dim + 1) + a];
+      const int32_t v = pr.conn[(size_t)e * (dim + 1) + a];
       uh[a] = u[v];
-      for (int k = 0; k < dim; k++) V[a][k] = coords[(size_t)k * nv + v];
+      for (int k = 0; k < dim; k++) V[a][k] = pr.coords[(size_t)k * nv + v];
     }
     double vol;
     if (dim == 2) {
@@ -181,19 +199,114 @@ void run_request(nl_server* S, cudaStream_t stream, Job& job) {
   res.l2_err_omega = std::sqrt(err2);
   res.n_pairs = ast.n_pairs;
   res.n_point_pairs = ast.n_point_pairs;
-  nl_pairs_info(pairs, nullptr, &res.nnz);
+  nl_pairs_info(pr.pairs, nullptr, &res.nnz);
   res.n_vert = nv;
   if (r.u_out) memcpy(r.u_out, u.data(), sizeof(double) * nv);
-  finish(st);
+  return st;
+}
+
+void set_status(nl_result& res, nl_status st) {
+  res.status = st;
+  if (st != NL_OK && res.message[0] == 0) snprintf(res.message, sizeof res.message, "%s", nl_last_error());
+}
+
+// Runs one request on `stream`: mesh, pairs, its own assembly, solve.
+void run_request(nl_server* S, cudaStream_t stream, Job& job) {
+  const nl_request& r = job.req;
+  nlx::g_block_budget = S->block_budget;
+  Prepared pr;
+  nl_status st = prepare(r, stream, pr);
+  if (st != NL_OK) return set_status(job.res, st);
+  nl_assemble_stats ast;
+  memset(&ast, 0, sizeof ast);
+  nl_matrix* A = nullptr;
+  st = nl_assemble(pr.mesh, pr.pairs, &r.kernel, &r.quad, r.precision, &A, &ast);
+  if (st == NL_OK) st = solve_and_report(r, pr, A, ast, job.res);
+  nl_matrix_destroy(A);
+  set_status(job.res, st);
+}
+
+// Runs a group of small requests of one dimension and precision class: each request's mesh
+// and pattern on `stream`, then one batched plan assembles all of them in a single launch of
+// the assembly kernel (and one scatter), then every request is solved; complete() is called
+// for each request as soon as its own result is ready.  If the plan cannot be created (device
+// memory), the requests are assembled one by one.
+template <typename F>
+void run_group(nl_server* S, cudaStream_t stream, const std::vector<Job*>& js, F complete) {
+  nlx::g_block_budget = S->block_budget;
+  const int n = (int)js.size();
+  std::vector<std::unique_ptr<Prepared>> prs(n);
+  std::vector<int> idx;
+  for (int k = 0; k < n; k++) {
+    prs[k].reset(new Prepared());
+    const nl_status st = prepare(js[k]->req, stream, *prs[k]);
+    if (st != NL_OK) {
+      set_status(js[k]->res, st);
+      prs[k].reset();
+      complete(*js[k]);
+    } else {
+      idx.push_back(k);
+    }
+  }
+  if (idx.empty()) return;
+  std::vector<nl_mesh*> ms;
+  std::vector<nl_pairs*> ps;
+  std::vector<nl_kernel_params> kps;
+  std::vector<nl_quad_params> qps;
+  for (int k : idx) {
+    ms.push_back(prs[k]->mesh);
+    ps.push_back(prs[k]->pairs);
+    kps.push_back(js[k]->req.kernel);
+    qps.push_back(js[k]->req.quad);
+  }
+  const nl_precision prec = js[idx[0]]->req.precision == NL_PREC_FP64 ? NL_PREC_FP64 : NL_PREC_FP32;
+  nl_plan* plan = nullptr;
+  nl_status pst = nl_plan_create((int)idx.size(), ms.data(), ps.data(), kps.data(), qps.data(),
+                                 prec, 0, stream, &plan);
+  std::vector<nl_assemble_stats> stats(idx.size());
+  if (pst == NL_OK) pst = nl_plan_execute(plan);
+  if (pst == NL_OK) pst = nl_plan_sync(plan, stats.data());
+  for (size_t j = 0; j < idx.size(); j++) {
+    const int k = idx[j];
+    Job& job = *js[k];
+    nl_matrix* A = nullptr;
+    nl_status st;
+    if (pst == NL_OK) {
+      st = nl_plan_matrix(plan, (int)j, &A);
+      if (st == NL_OK) st = solve_and_report(job.req, *prs[k], A, stats[j], job.res);
+    } else {
+      nl_assemble_stats ast;
+      memset(&ast, 0, sizeof ast);
+      st = nl_assemble(prs[k]->mesh, prs[k]->pairs, &job.req.kernel, &job.req.quad,
+                       job.req.precision, &A, &ast);
+      if (st == NL_OK) st = solve_and_report(job.req, *prs[k], A, ast, job.res);
+    }
+    nl_matrix_destroy(A);
+    set_status(job.res, st);
+    complete(job);
+  }
+  nl_plan_destroy(plan);
 }
 
 void worker_main(nl_server* S) {
   cudaSetDevice(S->device);
   cudaStream_t stream = nullptr;
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  auto complete = [&](Job& job) {
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      job.res.t_done_ms = ms_since(S->t0);
+      job.done = true;
+      S->in_use -= job.est;
+      S->running--;
+      S->latencies.push_back(job.res.t_done_ms - job.res.t_submit_ms);
+      S->last_done = job.res.t_done_ms;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  };
   for (;;) {
-    uint64_t ticket = 0;
-    Job* job = nullptr;
+    std::vector<Job*> group;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [&] {
@@ -203,25 +316,40 @@ void worker_main(nl_server* S) {
         return S->in_use + head.est <= S->budget || S->running == 0;
       });
       if (S->stop) break;
-      ticket = S->pending.front();
+      const double now = ms_since(S->t0);
+      Job* head = &S->jobs[S->pending.front()];
       S->pending.pop_front();
-      job = &S->jobs[ticket];
-      S->in_use += job->est;
+      S->in_use += head->est;
       S->running++;
-      job->res.t_start_ms = ms_since(S->t0);
+      head->res.t_start_ms = now;
+      group.push_back(head);
+      if (head->small) {
+        // continuous batching of small requests: later small requests of the same dimension
+        // and precision class that fit the memory left join this one's launch
+        for (auto it = S->pending.begin(); it != S->pending.end() && (int)group.size() < S->max_group;) {
+          Job& o = S->jobs[*it];
+          if (o.small && o.req.dim == head->req.dim &&
+              (o.req.precision == NL_PREC_FP64) == (head->req.precision == NL_PREC_FP64) &&
+              S->in_use + o.est <= S->budget) {
+            S->in_use += o.est;
+            S->running++;
+            o.res.t_start_ms = now;
+            o.res.group = (int32_t)S->groups;
+            group.push_back(&o);
+            it = S->pending.erase(it);
+          } else {
+            ++it;
+          }
+        }
+        if (group.size() > 1) head->res.group = (int32_t)S->groups++;
+      }
     }
-    run_request(S, stream, *job);
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      job->res.t_done_ms = ms_since(S->t0);
-      job->done = true;
-      S->in_use -= job->est;
-      S->running--;
-      S->latencies.push_back(job->res.t_done_ms - job->res.t_submit_ms);
-      S->last_done = job->res.t_done_ms;
+    if (group.size() == 1) {
+      run_request(S, stream, *group[0]);
+      complete(*group[0]);
+    } else {
+      run_group(S, stream, group, complete);
     }
-    S->cv_done.notify_all();
-    S->cv_work.notify_all();
   }
   cudaStreamDestroy(stream);
 }
@@ -267,6 +395,8 @@ nl_status nl_serve_submit(nl_server* S, const nl_request* req, uint64_t* ticket)
   job.res.t_submit_ms = ms_since(S->t0);
   if (S->first_submit < 0) S->first_submit = job.res.t_submit_ms;
   job.est = estimate_bytes(*req, S->block_budget);
+  job.small = estimate_pairs(*req) <= S->small_pairs;
+  job.res.group = -1;
   S->pending.push_back(t);
   *ticket = t;
   S->cv_work.notify_all();

@@ -63,7 +63,7 @@ class Result(ctypes.Structure):
                 ("n_point_pairs", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("n_vert", ctypes.c_int64), ("t_submit_ms", ctypes.c_double),
                 ("t_start_ms", ctypes.c_double), ("t_done_ms", ctypes.c_double),
-                ("message", ctypes.c_char * 160)]
+                ("message", ctypes.c_char * 160), ("group", ctypes.c_int32)]
 
 
 _lib = None
@@ -389,7 +389,7 @@ def assemble_problem(mesh_in, delta, eps, L_max, L_min=1, kernel=NL_KERNEL_CONST
 
 def make_request(dim, cells, h, lo, layer, delta, eps, L_max, kernel=NL_KERNEL_CONST,
                  precision=NL_PREC_FP32, ms=1, solver=1, rtol=1e-10, max_iter=20000, jitter=0.0,
-                 seed=0, L_min=1, u_out=None) -> Request:
+                 seed=0, L_min=1, u_out=None, mindist_l2=False) -> Request:
     r = Request()
     r.dim = dim
     for k in range(3):
@@ -397,7 +397,7 @@ def make_request(dim, cells, h, lo, layer, delta, eps, L_max, kernel=NL_KERNEL_C
         r.lo[k] = float(lo[k]) if k < dim else 0.0
     r.h, r.layer, r.jitter, r.seed = float(h), int(layer), float(jitter), int(seed)
     r.kernel = KernelParams(float(delta), float(eps), 0.0, int(kernel), 0.0)
-    r.quad = QuadParams(int(L_min), int(L_max), 0)
+    r.quad = QuadParams(int(L_min), int(L_max), quad_rule_flags(False, mindist_l2))
     r.precision, r.ms, r.solver, r.rtol, r.max_iter = int(precision), int(ms), int(solver), float(rtol), int(max_iter)
     r.u_out = None if u_out is None else u_out.ctypes.data
     return r

@@ -1,5 +1,11 @@
-"""Serving loop: requests admitted by memory and slots, run concurrently, and each result
-equal to the same request run alone (within the solver's tolerance)."""
+"""Serving loop: requests admitted by memory and slots, run concurrently (small ones batched
+into one plan launch with others), and each result equal to the same request run alone, and to
+the oracle.
+
+Alone vs in the mix: FP64 requests agree to the solver's tolerance (u to 1e-9 relative, the
+L2 error to 1e-6); FP32 requests may be assembled in a batched plan in the mix, whose work
+counter regroups the FP32 sums of the assembly (the matrices differ at the 1e-7 level), so u
+agrees to 1e-6 and the L2 error to 1e-4."""
 import numpy as np
 import pytest
 
@@ -45,11 +51,12 @@ def test_results_alone_equal_results_in_the_mix():
             starts = sorted(r.t_start_ms for r in res)
             dones = sorted(r.t_done_ms for r in res)
             assert starts[1] < dones[0], "requests did not overlap"
-            for (u0, r0), u1, r1 in zip(alone, outs, res):
+            for (u0, r0), u1, r1, spec in zip(alone, outs, res, MIX):
                 assert r1.status == nl.NL_OK, (rep, r1.message)
                 assert r1.n_pairs == r0.n_pairs and r1.n_point_pairs == r0.n_point_pairs
-                assert np.abs(u1 - u0).max() <= 1e-9 * np.abs(u0).max()
-                assert abs(r1.l2_err_omega / r0.l2_err_omega - 1) < 1e-6
+                tu, te = (1e-9, 1e-6) if spec[4] == nl.NL_PREC_FP64 else (1e-6, 1e-4)
+                assert np.abs(u1 - u0).max() <= tu * np.abs(u0).max(), (spec, r1.group)
+                assert abs(r1.l2_err_omega / r0.l2_err_omega - 1) < te, (spec, r1.group)
             p50, p99, sps = S.stats()
             assert 0 < p50 <= p99 and sps > 0
 
@@ -109,3 +116,28 @@ def test_served_results_match_the_oracle():
         tolu, tole = (1e-9, 1e-8) if prec == nl.NL_PREC_FP64 else (1e-5, 1e-3)
         assert np.abs(u - ref["u_h"]).max() <= tolu * np.abs(ref["u_h"]).max(), (dim, n, prec)
         assert abs(r.l2_err_omega / ref["err_omega"] - 1) < tole, (dim, n, prec)
+
+
+def test_small_requests_share_one_launch():
+    # 12 small 2D requests submitted at once to a one-slot server: the first is admitted alone
+    # (nothing else is waiting yet, or a group starts), the rest that wait are batched into
+    # plans; every grouped result matches the oracle-checked single path to the FP32
+    # tolerance, and results of one group share its id
+    specs = [(2, 8 + (i % 4) * 2, 2.0 + (i % 3), i % 2, nl.NL_PREC_FP32) for i in range(12)]
+    alone = []
+    with nl.Server(4 << 30, 1) as S:
+        for sp in specs:
+            u = np.zeros(_nvert(*sp[:3]))
+            r = S.wait(S.submit(_req(*sp, u=u), u))
+            assert r.status == nl.NL_OK and r.group == -1
+            alone.append((u, r))
+    with nl.Server(4 << 30, 1) as S:
+        outs = [np.zeros(_nvert(*sp[:3])) for sp in specs]
+        tickets = [S.submit(_req(*sp, u=u), u) for sp, u in zip(specs, outs)]
+        res = [S.wait(t) for t in tickets]
+    groups = [r.group for r in res]
+    assert sum(g >= 0 for g in groups) >= 8, groups
+    for (u0, r0), u1, r1 in zip(alone, outs, res):
+        assert r1.status == nl.NL_OK, r1.message
+        assert r1.n_pairs == r0.n_pairs and r1.n_point_pairs == r0.n_point_pairs
+        assert np.abs(u1 - u0).max() <= 1e-6 * np.abs(u0).max(), r1.group
