@@ -92,6 +92,9 @@ def parse():
     ap.add_argument("--profile-workload", default="c2_2d_h128")
     ap.add_argument("--profile-fp64", type=int, default=1,
                     help="with --profile: also run the FP64 assembly (0 = FP32 only)")
+    ap.add_argument("--profile-precs", default="",
+                    help="with --profile: comma list of fp64, fp32, tf32, bf16 (overrides "
+                         "--profile-fp64)")
     return ap.parse_args()
 
 
@@ -911,11 +914,18 @@ def run_profile_case(args):
     w, mesh = workload(args.profile_workload)
     m = nl.mesh_from(mesh)
     p = nl.nl_pairs_build(m, w.delta, w.eps)
-    precs = (nl.NL_PREC_FP32, nl.NL_PREC_FP64) if args.profile_fp64 else (nl.NL_PREC_FP32,)
+    names = {"fp64": nl.NL_PREC_FP64, "fp32": nl.NL_PREC_FP32, "tf32": nl.NL_PREC_MIXED_TF32,
+             "bf16": nl.NL_PREC_MIXED_BF16}
+    if args.profile_precs:
+        precs = tuple(names[x] for x in args.profile_precs.split(","))
+    else:
+        precs = (nl.NL_PREC_FP32, nl.NL_PREC_FP64) if args.profile_fp64 else (nl.NL_PREC_FP32,)
     for prec in precs:
-        A, st = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec)
+        A, st = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec,
+                               mindist_l2=bool(args.mindist_l2))
         print(json.dumps({"profile_case": w.name, "precision": prec, "pairs": st.n_pairs,
-                          "point_pairs": st.n_point_pairs, "kernel_ms": st.ms_assemble}))
+                          "point_pairs": st.n_point_pairs, "kernel_ms": st.ms_quad,
+                          "assembly_ms": st.ms_assemble}))
     torch.cuda.synchronize()
 
 
