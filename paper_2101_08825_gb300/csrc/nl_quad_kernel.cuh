@@ -956,6 +956,9 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       // MMA: the fragment accumulators of the pair's contraction H_c(y) = sum_x G(x, y) w_x
       // phi^l_c(x) (rows: inner points y, columns: nodes c of l)
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      // whether anything was summed for this pair (a closed form on this lane, or an
+      // integration by the warp): pairs with no contribution skip the end-of-pair reduction
+      bool contrib = false;
 
       // Algorithm 1 decision for a sub-element (R coordinates)
       // count_exact: this lane counts an FP64 re-decision (lanes that classify the same
@@ -1033,6 +1036,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           uh[r] += wv * s;
         }
         st_closed++;
+        contrib = true;
       };
 
       // A FINAL sub-element E' (L_max reached, the band in reach of the box of m) whose every
@@ -1119,6 +1123,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           }
         }
         st_closed++;
+        contrib = true;
         return true;
       };
 
@@ -1132,6 +1137,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         const R* iw = wm.iw + kind * IMAX;
         const int n_x = n_it * NQ;
         st_eval += (unsigned)(n_x * NQ);
+        contrib = true;
         if constexpr (MMA != 0) {
           // Tensor-core contraction.  For each batch of 32 outer points x, lane i stages point
           // i: its coordinates and B[x][c] = w_x phi^l_c(x) (the P1 basis of l, c = 0..D),
@@ -1216,6 +1222,10 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
               ga = yv ? ga : 0.f;
               gb = yv ? gb : 0.f;
             };
+            // the products of this batch of 32 outer points accumulate from zero in the tensor
+            // cores and are then added to the pair's accumulators in FP32 (at most 32 terms
+            // summed inside the MMA chain)
+            float part[4] = {0.f, 0.f, 0.f, 0.f};
             if constexpr (MMA == 1) {
               // m16n8k8: A columns (outer points) t and t+4 of each group of 8
 #pragma unroll
@@ -1240,8 +1250,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
                   split_tf32(ga, ah0, al0);
                   split_tf32(gb, ah1, al1);
                   // rows 0-7: high parts, rows 8-15: low parts of the same inner points
-                  mma_tf32(acc, ah0, al0, ah1, al1, bh0, bh1);
-                  mma_tf32(acc, ah0, al0, ah1, al1, bl0, bl1);
+                  mma_tf32(part, ah0, al0, ah1, al1, bh0, bh1);
+                  mma_tf32(part, ah0, al0, ah1, al1, bl0, bl1);
                 } else {
                   float g0a, g0b, g1a, g1b;
                   geval(xa, xb, 0, xva, xvb, g0a, g0b);
@@ -1251,9 +1261,9 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
                   split_tf32(g0b, h0b, l0b);
                   split_tf32(g1a, h1a, l1a);
                   split_tf32(g1b, h1b, l1b);
-                  mma_tf32(acc, h0a, h1a, h0b, h1b, bh0, bh1);
-                  mma_tf32(acc, h0a, h1a, h0b, h1b, bl0, bl1);
-                  mma_tf32(acc, l0a, l1a, l0b, l1b, bh0, bh1);
+                  mma_tf32(part, h0a, h1a, h0b, h1b, bh0, bh1);
+                  mma_tf32(part, h0a, h1a, h0b, h1b, bl0, bl1);
+                  mma_tf32(part, l0a, l1a, l0b, l1b, bh0, bh1);
                 }
               }
             } else {
@@ -1287,8 +1297,8 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
                   uint32_t h01, l01, h89, l89;
                   split_bf16x2(g0, g1, h01, l01);
                   split_bf16x2(g8, g9, h89, l89);
-                  mma_bf16(acc, h01, l01, h89, l89, bh0, bh1);
-                  mma_bf16(acc, h01, l01, h89, l89, bl0, bl1);
+                  mma_bf16(part, h01, l01, h89, l89, bh0, bh1);
+                  mma_bf16(part, h01, l01, h89, l89, bl0, bl1);
                 } else {
                   float a0, a1, a8, a9, c0, c1, c8, c9;
                   geval(x0, x1, 0, v0, v1, a0, a1);
@@ -1300,12 +1310,14 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
                   split_bf16x2(a8, a9, ha89, la89);
                   split_bf16x2(c0, c1, hc01, lc01);
                   split_bf16x2(c8, c9, hc89, lc89);
-                  mma_bf16(acc, ha01, hc01, ha89, hc89, bh0, bh1);
-                  mma_bf16(acc, ha01, hc01, ha89, hc89, bl0, bl1);
-                  mma_bf16(acc, la01, lc01, la89, lc89, bh0, bh1);
+                  mma_bf16(part, ha01, hc01, ha89, hc89, bh0, bh1);
+                  mma_bf16(part, ha01, hc01, ha89, hc89, bl0, bl1);
+                  mma_bf16(part, la01, lc01, la89, lc89, bh0, bh1);
                 }
               }
             }
+#pragma unroll
+            for (int r = 0; r < 4; r++) acc[r] += part[r];
             __syncwarp();  // the batch is read before the next one is staged
           }
           return;
@@ -1577,6 +1589,13 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         if (n_int > 0) integrate(KIND_INT, n_int);
       }
       // ---- end of pair: per-lane contraction, warp reduce-scatter, cross block, self sums ------
+      // A pair whose every sub-element was dropped (or lies beyond delta + eps) contributes
+      // nothing: its cross block is zero and the self sums are unchanged.
+      if (!__any_sync(0xffffffffu, contrib)) {
+        if (!DIRECT && lane < NBLK) reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + lane] = (R)0;
+        __syncwarp();
+        continue;
+      }
       {
         if constexpr (F32) {
 #pragma unroll
@@ -1695,10 +1714,29 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 }
 
 // ---- scatter of the local blocks into the CSR values ------------------------------------------
-// One CTA per inner element m: the column lists of the rows of m's nodes are cached in shared
-// memory; every cross block of the pairs p of m in [q0, q1) (stored at blk[p - p_base]) is
-// added with FP64 atomics after a binary search in the cached row, and (with_self) the self
-// block of m.  Needs (D+1) * (longest row) ints of dynamic shared memory.
+// One CTA per inner element m; its contributions (the cross blocks of the pairs p of m in
+// [q0, q1), stored at blk[p - p_base], and with_self the self block of m) are summed per CSR
+// entry in shared-memory FP64 accumulators and each entry is added to the global values once
+// (FP64 atomics: the rows of a node are shared by the elements around it).
+//
+// Where the column of an entry is found: every row of m's nodes holds the nodes of every l
+// paired with m, so a shared-memory hash table keyed by column node gives, for each of m's
+// rows, the entry's position in that row: one lookup per node of l serves all D+1 rows of the
+// block.  The table (open addressing, linear probing, at most half full: its size is the
+// power of two at least twice the longest of the rows) is built from the rows' column lists.
+// If the dynamic shared memory cannot hold it, the columns are cached and each entry is found
+// by binary search in its row instead.
+__host__ __device__ inline int scatter_table_size(int max_row) {
+  int t = 64;
+  while (t < 2 * max_row) t <<= 1;
+  return t;
+}
+__host__ __device__ inline size_t scatter_hash_bytes(int dim, int T, int64_t acc_entries) {
+  size_t b = (size_t)T * 4;                               // keys
+  b += ((size_t)T * (dim + 1) * 2 + 7) & ~size_t(7);      // int16 positions per row
+  return b + (size_t)acc_entries * 8;                     // FP64 accumulators
+}
+
 template <int D, typename R>
 __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, int64_t p_base,
                                              bool with_self, const int32_t* __restrict__ pair_l,
@@ -1709,22 +1747,109 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
                                              const double* __restrict__ selfblk,
                                              double* __restrict__ values, int* __restrict__ err) {
   constexpr int NV = D + 1, NB = NV * NV;
-  extern __shared__ int32_t rows[];
+  extern __shared__ __align__(16) unsigned char sraw[];
   __shared__ int64_t rbeg[NV];
   __shared__ int rlen[NV], roff[NV + 1];
   __shared__ int32_t nodes[NV];
+  __shared__ int overflow;
   if (threadIdx.x < NV) {
     int32_t i = conn[m * NV + threadIdx.x];
     nodes[threadIdx.x] = i;
     rbeg[threadIdx.x] = row_ptr[i];
     rlen[threadIdx.x] = (int)(row_ptr[i + 1] - row_ptr[i]);
   }
+  if (threadIdx.x == 0) overflow = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     roff[0] = 0;
     for (int a = 0; a < NV; a++) roff[a + 1] = roff[a] + rlen[a];
   }
   __syncthreads();
+  const int total = roff[NV];
+  int max_len = 0;
+#pragma unroll
+  for (int a = 0; a < NV; a++) max_len = rlen[a] > max_len ? rlen[a] : max_len;
+  unsigned dyn = 0;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const int T = scatter_table_size(max_len);
+  const int64_t n = (q1 > q0 ? q1 - q0 : 0);
+  if (scatter_hash_bytes(D, T, total) <= (size_t)dyn) {
+    int32_t* keys = reinterpret_cast<int32_t*>(sraw);
+    int16_t* pos = reinterpret_cast<int16_t*>(keys + T);
+    double* acc = reinterpret_cast<double*>(sraw + (((size_t)T * 4 + (size_t)T * NV * 2 + 7) & ~size_t(7)));
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+      keys[t] = -1;
+#pragma unroll
+      for (int a = 0; a < NV; a++) pos[t * NV + a] = -1;
+    }
+    for (int t = threadIdx.x; t < total; t += blockDim.x) acc[t] = 0.0;
+    __syncthreads();
+    const unsigned shift = 32u - (unsigned)(31 - __clz(T));
+    auto h0 = [&](int32_t key) -> int { return (int)(((uint32_t)key * 2654435761u) >> shift); };
+    for (int a = 0; a < NV; a++)
+      for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) {
+        const int32_t key = col[rbeg[a] + t];
+        int slot = h0(key), probe = 0;
+        for (; probe < T; probe++) {
+          const int32_t prev = atomicCAS(&keys[slot], -1, key);
+          if (prev == -1 || prev == key) break;
+          slot = (slot + 1) & (T - 1);
+        }
+        if (probe < T) pos[slot * NV + a] = (int16_t)t;
+        else overflow = 1;  // cannot happen below half load; checked all the same
+      }
+    __syncthreads();
+    if (!overflow) {
+      auto lookup = [&](int32_t key) -> int {
+        int slot = h0(key);
+        for (int probe = 0; probe < T; probe++) {
+          const int32_t k = keys[slot];
+          if (k == key) return slot;
+          if (k == -1) return -1;
+          slot = (slot + 1) & (T - 1);
+        }
+        return -1;
+      };
+      // one thread per (pair, node c of l): the D+1 entries of column c of the block
+      for (int64_t t = threadIdx.x; t < n * NV; t += blockDim.x) {
+        const int64_t p = q0 + t / NV;
+        const int c = (int)(t % NV);
+        const R* bp = blk + (p - p_base) * NB + c;
+        R bv[NV];
+        bool any = false;
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+          bv[a] = bp[a * NV];
+          any = any || bv[a] != (R)0;
+        }
+        if (!any) continue;  // a pair with no contribution (all of it beyond delta + eps)
+        const int32_t l = pair_l[p];
+        const int slot = lookup(conn[(int64_t)l * NV + c]);
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+          const int ps = slot < 0 ? -1 : pos[slot * NV + a];
+          if (ps < 0) atomicOr(err, ERR_CSR);
+          else atomicAdd(&acc[roff[a] + ps], (double)bv[a]);
+        }
+      }
+      if (with_self && threadIdx.x < NB) {
+        const int a = threadIdx.x / NV, b = threadIdx.x % NV;
+        const int slot = lookup(nodes[b]);
+        const int ps = slot < 0 ? -1 : pos[slot * NV + a];
+        if (ps < 0) atomicOr(err, ERR_CSR);
+        else atomicAdd(&acc[roff[a] + ps], selfblk[m * NB + threadIdx.x]);
+      }
+      __syncthreads();
+      for (int a = 0; a < NV; a++)
+        for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) {
+          const double v = acc[roff[a] + t];
+          if (v != 0.0) atomicAdd(&values[rbeg[a] + t], v);
+        }
+      return;
+    }
+    __syncthreads();  // the table is abandoned; its memory is reused below
+  }
+  int32_t* rows = reinterpret_cast<int32_t*>(sraw);
   for (int a = 0; a < NV; a++)
     for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) rows[roff[a] + t] = col[rbeg[a] + t];
   __syncthreads();
@@ -1741,12 +1866,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     return -1;
   };
   // With enough dynamic shared memory the element's contributions are first summed per CSR
-  // entry in shared memory (an element's pairs hit each column of its rows several times) and
-  // each entry is added to the global values once; otherwise every contribution goes to the
-  // global values directly.
-  const int total = roff[NV];
-  unsigned dyn = 0;
-  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  // entry in shared memory; otherwise every contribution goes to the global values directly.
   const int acc_off = (total + 3) & ~3;  // ints before the (8-byte aligned) accumulators
   const bool use_acc = (size_t)acc_off * 4 + (size_t)total * 8 <= (size_t)dyn;
   double* acc = reinterpret_cast<double*>(rows + acc_off);
@@ -1758,8 +1878,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     if (use_acc) atomicAdd(&acc[roff[a] + (int)(pos - rbeg[a])], v);
     else atomicAdd(&values[pos], v);
   };
-  const int64_t n = (q1 > q0 ? q1 - q0 : 0) * NB;
-  for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+  for (int64_t t = threadIdx.x; t < n * NB; t += blockDim.x) {
     const int64_t p = q0 + t / NB;
     const int e = (int)(t % NB);
     const int a = e / NV, c = e % NV;
@@ -1787,11 +1906,13 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   }
 }
 
-// Dynamic shared memory of the scatter kernels for rows of up to max_row columns: the cached
-// column lists plus FP64 accumulators when that fits in 200 KB, else the column lists only
-// (0 if even those do not fit).
+// Dynamic shared memory of the scatter kernels for rows of up to max_row columns: the hash
+// layout when it fits in 200 KB, else the cached column lists plus FP64 accumulators when that
+// fits, else the column lists only (0 if even those do not fit).
 inline size_t scatter_smem_bytes(int dim, int max_row) {
   const size_t total = (size_t)(dim + 1) * (size_t)std::max(1, max_row);
+  const size_t hashed = scatter_hash_bytes(dim, scatter_table_size(std::max(1, max_row)), (int64_t)total);
+  if (hashed <= (size_t)200 * 1024) return hashed;
   const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
   if (with_acc <= (size_t)200 * 1024) return with_acc;
   if (total * 4 <= (size_t)200 * 1024) return total * 4;
