@@ -121,3 +121,33 @@ def structured_mesh(dim: int, cells, h: float, lo, layer: int, jitter: float = 0
     return Mesh(dim=dim, coords=coords, conn=np.ascontiguousarray(conn.astype(np.int32)),
                 elem_in_omega=elem_in_omega, node_free=inside.astype(np.uint8), h=float(h),
                 meta=dict(cells=cells, lo=lo, layer=layer, jitter=jitter, seed=seed))
+
+
+def p2_mesh(mesh: Mesh) -> Mesh:
+    """The P2 (quadratic Lagrange) triangle mesh on the triangles of a structured 2D mesh.
+
+    Nodes: the vertices (same numbers), then one node per edge at its midpoint (a + b) * 0.5,
+    numbered after the vertices in the lexicographic order of the edges' (smaller vertex,
+    larger vertex) pairs.  ``conn`` rows are (v0, v1, v2, m01, m12, m02).  A node is a degree
+    of freedom when it lies strictly inside the open Omega of ``mesh.meta`` (vertices on the
+    boundary of Omega are never moved by the jitter, so midpoints of boundary edges lie
+    exactly on it)."""
+    if mesh.dim != 2 or mesh.conn.shape[1] != 3:
+        raise ValueError("P2 meshes are built from P1 triangle meshes")
+    c = mesh.conn.astype(np.int64)
+    pairs = np.stack([c[:, [0, 1]], c[:, [1, 2]], c[:, [0, 2]]], axis=1)  # (n_elem, 3, 2)
+    lo_hi = np.sort(pairs, axis=2).reshape(-1, 2)
+    key = lo_hi[:, 0] * mesh.n_vert + lo_hi[:, 1]
+    ukey, inv = np.unique(key, return_inverse=True)
+    ea, eb = ukey // mesh.n_vert, ukey % mesh.n_vert
+    mid = (mesh.coords[:, ea] + mesh.coords[:, eb]) * 0.5
+    coords = np.concatenate([mesh.coords, mid], axis=1)
+    edge_node = (mesh.n_vert + inv).reshape(-1, 3)
+    conn = np.concatenate([c, edge_node], axis=1).astype(np.int32)
+    lo = np.array(mesh.meta["lo"], dtype=np.float64)
+    hi = lo + np.array(mesh.meta["cells"], dtype=np.float64) * mesh.h
+    free = np.all((coords > lo[:, None]) & (coords < hi[:, None]), axis=0)
+    free[: mesh.n_vert] = mesh.node_free.astype(bool)
+    meta = dict(mesh.meta, order=2)
+    return Mesh(dim=2, coords=coords, conn=np.ascontiguousarray(conn), elem_in_omega=mesh.elem_in_omega.copy(),
+                node_free=free.astype(np.uint8), h=mesh.h, meta=meta)

@@ -40,7 +40,8 @@ def build(force: bool = False) -> str:
 class _Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n_vert", ctypes.c_int64), ("n_elem", ctypes.c_int64),
                 ("coords", ctypes.c_void_p), ("conn", ctypes.c_void_p),
-                ("elem_in_omega", ctypes.c_void_p), ("node_free", ctypes.c_void_p)]
+                ("elem_in_omega", ctypes.c_void_p), ("node_free", ctypes.c_void_p),
+                ("order", ctypes.c_int)]
 
 
 class _Params(ctypes.Structure):
@@ -110,9 +111,10 @@ class OMesh:
         self.conn = np.ascontiguousarray(mesh.conn, dtype=np.int32)
         self.elem_in_omega = np.ascontiguousarray(mesh.elem_in_omega, dtype=np.uint8)
         self.node_free = np.ascontiguousarray(mesh.node_free, dtype=np.uint8)
+        self.order = 1 if self.conn.shape[1] == self.dim + 1 else 2
         self.c = _Mesh(self.dim, self.coords.shape[1], self.conn.shape[0], _ptr(self.coords).value,
                        _ptr(self.conn).value, _ptr(self.elem_in_omega).value,
-                       _ptr(self.node_free).value)
+                       _ptr(self.node_free).value, self.order)
 
 
 def _om(mesh) -> OMesh:

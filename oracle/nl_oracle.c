@@ -385,10 +385,29 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
 
 /* ------------------------------------------------------------------------------------
  * Mesh helpers. */
+/* Nodes per element: P1 simplices dim+1; P2 triangles 6 (the vertices, then the midpoints of
+ * the edges (0,1), (1,2), (0,2)). */
+static int npe(const or_mesh* M) { return (M->order == 2) ? 6 : M->dim + 1; }
+
+/* The element's Lagrange basis at the point with barycentric coordinates lam: P1 the
+ * barycentric coordinates; P2 (triangles) lam_a (2 lam_a - 1) at the vertices and
+ * 4 lam_a lam_b at the midpoints of the edges (0,1), (1,2), (0,2). */
+static void basis(const or_mesh* M, const double* lam, double* phi) {
+  if (M->order != 2) {
+    for (int a = 0; a <= M->dim; a++) phi[a] = lam[a];
+    return;
+  }
+  for (int a = 0; a < 3; a++) phi[a] = lam[a] * (2.0 * lam[a] - 1.0);
+  phi[3] = 4.0 * lam[0] * lam[1];
+  phi[4] = 4.0 * lam[1] * lam[2];
+  phi[5] = 4.0 * lam[0] * lam[2];
+}
+
+/* The vertices of element e (the first dim+1 of its nodes). */
 static void elem_verts(const or_mesh* M, int64_t e, double V[4][3]) {
-  int nv = M->dim + 1;
+  int nv = M->dim + 1, nb = npe(M);
   for (int a = 0; a < nv; a++) {
-    int64_t v = M->conn[e * nv + a];
+    int64_t v = M->conn[e * nb + a];
     for (int k = 0; k < 3; k++) V[a][k] = (k < M->dim) ? M->coords[k * M->n_vert + v] : 0.0;
   }
 }
@@ -532,7 +551,7 @@ static int cmp_i32(const void* a, const void* b) {
  * of l, (m, l) in J (l = m is in J, so the nodes of m are included). */
 int64_t or_csr(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l, int64_t* row_ptr,
                int32_t* col, int64_t cap) {
-  int nv = M->dim + 1;
+  int nv = npe(M);
   int64_t nV = M->n_vert, nE = M->n_elem;
   /* node -> elements */
   int64_t* deg = (int64_t*)calloc(nV + 1, sizeof(int64_t));
@@ -594,7 +613,7 @@ static double* csr_entry(const int64_t* row_ptr, const int32_t* col, double* val
 typedef struct {
   const or_mesh* M;
   const or_params* P;
-  int dim, nv, nq;
+  int dim, nv, nq, nb; /* nv: vertices (dim+1); nb: nodes (basis functions) per element */
   double qb[16][4], qw[16];
   const double* lo; /* element boxes (3 per element) */
   const double* hi;
@@ -615,10 +634,10 @@ typedef struct {
  * The finite sum over (x, m, y) is accumulated per m into the local blocks S (i, j in m)
  * and X (i in m, j in l) before it is added to A. */
 static void integration(actx* c, const double E[4][3], const int32_t* J, int64_t nJ) {
-  int dim = c->dim, nv = c->nv, nq = c->nq;
+  int dim = c->dim, nv = c->nv, nq = c->nq, nb = c->nb;
   const or_params* P = c->P;
   double vol = simplex_volume(dim, E);
-  double xq[16][3], wx[16], phil[16][4];
+  double xq[16][3], wx[16], phil[16][6], phim[16][6];
   for (int q = 0; q < nq; q++) {
     for (int k = 0; k < 3; k++) {
       double s = 0.0;
@@ -626,14 +645,17 @@ static void integration(actx* c, const double E[4][3], const int32_t* J, int64_t
       xq[q][k] = s;
     }
     wx[q] = c->qw[q] * vol;
-    barycentric(dim, c->Vl, xq[q], phil[q]);
+    double lam[4];
+    barycentric(dim, c->Vl, xq[q], lam);
+    basis(c->M, lam, phil[q]);     /* basis of l at the outer point */
+    basis(c->M, c->qb[q], phim[q]); /* basis of m at its inner point q */
   }
   for (int64_t t = 0; t < nJ; t++) {
     int64_t m = J[t];
     double Vm[4][3];
     elem_verts(c->M, m, Vm);
     double volm = simplex_volume(dim, Vm);
-    double S[4][4] = {{0}}, X[4][4] = {{0}};
+    double S[6][6] = {{0}}, X[6][6] = {{0}};
     for (int q = 0; q < nq; q++) {
       for (int p = 0; p < nq; p++) {
         double y[3];
@@ -649,26 +671,26 @@ static void integration(actx* c, const double E[4][3], const int32_t* J, int64_t
         double G = wx[q] * wy * P->C * or_eta(P->kernel, r, P->delta) * or_mu(r, P->delta, P->eps);
         c->st->n_point_pairs++;
         if (r >= P->delta - P->eps && r <= P->delta + P->eps) c->st->n_band_pairs++;
-        for (int a = 0; a < nv; a++) {
-          double phia = c->qb[p][a]; /* phi^m_a(y_p): barycentric coordinate of y_p in E_m */
-          for (int b = 0; b < nv; b++) S[a][b] += G * phia * c->qb[p][b];
-          for (int d = 0; d < nv; d++) X[a][d] += G * phia * phil[q][d];
+        for (int a = 0; a < nb; a++) {
+          double phia = phim[p][a]; /* phi^m_a(y_p) */
+          for (int b = 0; b < nb; b++) S[a][b] += G * phia * phim[p][b];
+          for (int d = 0; d < nb; d++) X[a][d] += G * phia * phil[q][d];
         }
       }
     }
     c->st->n_integrations++;
-    for (int a = 0; a < nv; a++) {
-      int64_t i = c->M->conn[m * nv + a];
-      for (int b = 0; b < nv; b++) {
-        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * nv + b]);
+    for (int a = 0; a < nb; a++) {
+      int64_t i = c->M->conn[m * nb + a];
+      for (int b = 0; b < nb; b++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * nb + b]);
         if (!e) {
           c->error = 1;
           continue;
         }
         *e += 2.0 * S[a][b];
       }
-      for (int d = 0; d < nv; d++) {
-        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * nv + d]);
+      for (int d = 0; d < nb; d++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * nb + d]);
         if (!e) {
           c->error = 1;
           continue;
@@ -738,6 +760,8 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
   c.P = P;
   c.dim = dim;
   c.nv = nv;
+  c.nb = npe(M);
+  if (M->order == 2 && dim != 2) return -1; /* P2: triangles only */
   double bary[64], w[16];
   c.nq = or_quad_rule(dim, bary, w);
   if (c.nq <= 0) return -1;
@@ -836,7 +860,7 @@ double or_ms_f(int ms, int dim, const double* x, int kernel, double delta, doubl
  * the right-hand side: F~_i = F_i - sum_{k not free} A_ik g(x_k). */
 int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const double* values,
            int ms, int kernel, double delta, double eps, double C, double* F) {
-  int dim = M->dim, nv = dim + 1;
+  int dim = M->dim, nv = dim + 1, nb = npe(M);
   double bary[64], w[16];
   int nq = or_quad_rule(dim, bary, w);
   if (nq <= 0) return -1;
@@ -854,9 +878,11 @@ int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const d
         x[k] = s;
       }
       double f = or_ms_f(ms, dim, x, kernel, delta, eps, C);
-      for (int a = 0; a < nv; a++) {
-        int64_t i = M->conn[e * nv + a];
-        if (M->node_free[i]) F[i] += w[q] * vol * f * bary[q * nv + a];
+      double phi[6];
+      basis(M, bary + q * nv, phi);
+      for (int a = 0; a < nb; a++) {
+        int64_t i = M->conn[e * nb + a];
+        if (M->node_free[i]) F[i] += w[q] * vol * f * phi[a];
       }
     }
   }
@@ -912,14 +938,16 @@ int or_solve_dense(const or_mesh* M, const int64_t* row_ptr, const int32_t* col,
 
 /* ||u - u_h||_{L2}: each element is split twice by midpoints and the degree-5 rule is
  * applied on every piece. */
-static double err_on(int dim, const double V[4][3], const double* nodal, const double bary[][4],
-                     const double* w, int nq, int ms, const double Vroot[4][3], int depth) {
+static double err_on(const or_mesh* M, const double V[4][3], const double* nodal,
+                     const double bary[][4], const double* w, int nq, int ms,
+                     const double Vroot[4][3], int depth) {
+  int dim = M->dim;
   if (depth > 0) {
     double C[8][4][3];
     split(dim, V, C);
     double s = 0.0;
     for (int i = 0; i < ((dim == 2) ? 4 : 8); i++)
-      s += err_on(dim, C[i], nodal, bary, w, nq, ms, Vroot, depth - 1);
+      s += err_on(M, C[i], nodal, bary, w, nq, ms, Vroot, depth - 1);
     return s;
   }
   double vol = simplex_volume(dim, V), s = 0.0;
@@ -930,10 +958,11 @@ static double err_on(int dim, const double V[4][3], const double* nodal, const d
       for (int v = 0; v <= dim; v++) t += bary[q][v] * V[v][k];
       x[k] = t;
     }
-    double lam[4];
+    double lam[4], phi[6];
     barycentric(dim, Vroot, x, lam);
+    basis(M, lam, phi);
     double uh = 0.0;
-    for (int a = 0; a <= dim; a++) uh += lam[a] * nodal[a];
+    for (int a = 0; a < npe(M); a++) uh += phi[a] * nodal[a];
     double d = or_ms_u(ms, dim, x) - uh;
     s += w[q] * vol * d * d;
   }
@@ -950,10 +979,10 @@ double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) 
   double s = 0.0;
   for (int64_t e = 0; e < M->n_elem; e++) {
     if (omega_only && !M->elem_in_omega[e]) continue;
-    double V[4][3], nodal[4];
+    double V[4][3], nodal[6];
     elem_verts(M, e, V);
-    for (int a = 0; a < nv; a++) nodal[a] = u_h[M->conn[e * nv + a]];
-    s += err_on(dim, V, nodal, (const double(*)[4])bary, w, nq, ms, V, 2);
+    for (int a = 0; a < npe(M); a++) nodal[a] = u_h[M->conn[e * npe(M) + a]];
+    s += err_on(M, V, nodal, (const double(*)[4])bary, w, nq, ms, V, 2);
   }
   return sqrt(s);
 }

@@ -30,11 +30,13 @@ extern "C" {
 
 typedef struct {
   int dim;
-  int64_t n_vert, n_elem;
+  int64_t n_vert, n_elem;       /* n_vert: all nodes (P2: vertices and edge midpoints) */
   const double* coords;
-  const int32_t* conn;
+  const int32_t* conn;          /* npe nodes per element: P1 dim+1; P2 triangles 6 */
   const uint8_t* elem_in_omega; /* 1 = element of Omega, 0 = of the layer Gamma */
   const uint8_t* node_free;     /* 1 = degree of freedom (node inside open Omega) */
+  int order;                    /* 1 (or 0): P1; 2: P2 Lagrange triangles (vertices, then the
+                                   midpoints of the edges (0,1), (1,2), (0,2)) */
 } or_mesh;
 
 /* or_params.flags: the refinement test of Algorithm 1 uses the Euclidean variant of the

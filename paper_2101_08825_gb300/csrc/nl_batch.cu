@@ -157,7 +157,7 @@ nl_status plan_enqueue(nl_plan* pl) {
     launches++;
   }
   if (pl->total_elem > 0) {
-    const size_t smem = scatter_smem_bytes(D, pl->max_row_nnz);
+    const size_t smem = scatter_smem_bytes(D, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
     const bool f32 = pl->prec != NL_PREC_FP64;
     const int64_t* ep = pl->d_prefix + (pl->n + 1);
     if (D == 2) {
@@ -188,7 +188,7 @@ nl_status kernel_smem_setup(F* kern, size_t smem) {
 
 // Raises the scatter kernel's shared-memory ceiling before any capture.
 nl_status plan_prepare_scatter(nl_plan* pl) {
-  const size_t smem = scatter_smem_bytes(pl->dim, pl->max_row_nnz);
+  const size_t smem = scatter_smem_bytes(pl->dim, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
   if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", pl->max_row_nnz);
   const bool f32 = pl->prec != NL_PREC_FP64;

@@ -1047,40 +1047,36 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
       // mu = 1 is C |E'| [1, lambda^l(c)] (degree-5 rule, linear integrand), added to that
       // inner point only.  Returns false (nothing added) unless every inner point is decided.
       // 2D: every lane holds all inner points of m.
-      auto closed_set = [&](const R (&V)[NV][D], int level) -> bool {
-        if (D != 2) return false;
-        R cen[D];
+      // The lane's inner point i (of the 7 it holds).
+      auto lane_y = [&](int i, R (&yi)[D]) {
 #pragma unroll
         for (int k = 0; k < D; k++) {
-          R t = 0;
-#pragma unroll
-          for (int a = 0; a < NV; a++) t += V[a][k];
-          cen[k] = t * (R)(1.0 / NV);
+          if constexpr (F32) {
+            if (i < 6) {
+              float a, b;
+              f2unpack(yq[i / 2][k], a, b);
+              yi[k] = (i & 1) ? b : a;
+            } else {
+              yi[k] = y[6][k];
+            }
+          } else {
+            yi[k] = y[i][k];
+          }
         }
-        // every midpoint child of a triangle is the parent scaled by 1/2, so the radius of a
-        // level-L sub-element is that of E_l times 2^(1-L) (rounding is inside the margin)
-        const R rad = rad_l * pow2m(R(0), level - 1);
+      };
+      // Sub-element with centroid cen and radius rad (every point within rad of cen): for each
+      // of the lane's inner points y, mu is exactly 1 at every point pair if |cen - y| is below
+      // delta - eps - rad - margin, exactly 0 if above delta + eps + rad + margin.  Returns
+      // whether every inner point is decided, and the mask of those with mu = 1.
+      auto decide_ball = [&](const R (&cen)[D], R rad, unsigned& in_mask) -> bool {
         const R lo = (R)P.fdme - rad - (R)P.margin, hi = (R)P.fdpe + rad + (R)P.margin;
         const R lo2 = lo > 0 ? lo * lo : (R)-1, hi2 = hi * hi;
-        unsigned in_mask = 0;
+        in_mask = 0;
         bool decided = true;
 #pragma unroll
         for (int i = 0; i < NYL; i++) {
           R yi[D];
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            if constexpr (F32) {
-              if (i < 6) {
-                float a, b;
-                f2unpack(yq[i / 2][k], a, b);
-                yi[k] = (i & 1) ? b : a;
-              } else {
-                yi[k] = y[6][k];
-              }
-            } else {
-              yi[k] = y[i][k];
-            }
-          }
+          lane_y(i, yi);
           R d2 = 0;
 #pragma unroll
           for (int k = 0; k < D; k++) {
@@ -1091,8 +1087,11 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           in_mask |= in ? (1u << i) : 0u;
           decided = decided && (in || out);
         }
-        if (!decided) return false;
-        const R wv = wl * pow2m(R(0), D * (level - 1));
+        return decided;
+      };
+      // Adds the closed-form outer sum C |E'| [1, lambda^l(cen)] (weight wv = C |E'|; the degree-5
+      // rule integrates the linear integrand exactly) to the lane's inner points in in_mask.
+      auto add_closed = [&](const R (&cen)[D], R wv, unsigned in_mask) {
         R lc[D];  // lambda^l(c)
 #pragma unroll
         for (int r = 0; r < D; r++) {
@@ -1122,9 +1121,97 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
             for (int k = 0; k < D; k++) hp[k][i] += wi * lc[k];
           }
         }
-        st_closed++;
         contrib = true;
+      };
+
+      // A FINAL sub-element E' (L_max reached, the band in reach of the box of m) whose every
+      // point pair has mu exactly 1 or 0 (decide_ball) contributes, with the constant kernel,
+      // the closed form to the inner points with mu = 1.  2D, at classification time (every
+      // lane holds all inner points of m; every midpoint child of a triangle is the parent
+      // scaled by 1/2, so the radius of a level-L sub-element is that of E_l times 2^(1-L),
+      // with the rounding inside the margin).  Returns false (nothing added) unless every
+      // inner point is decided.
+      auto closed_set = [&](const R (&V)[NV][D], int level) -> bool {
+        if (D != 2) return false;
+        R cen[D];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+          R t = 0;
+#pragma unroll
+          for (int a = 0; a < NV; a++) t += V[a][k];
+          cen[k] = t * (R)(1.0 / NV);
+        }
+        const R rad = rad_l * pow2m(R(0), level - 1);
+        unsigned in_mask;
+        if (!decide_ball(cen, rad, in_mask)) return false;
+        add_closed(cen, wl * pow2m(R(0), D * (level - 1)), in_mask);
+        st_closed++;
         return true;
+      };
+
+      // 3D: the same closed form, applied to a buffer of FINAL items just before it is
+      // integrated (at classification time most lanes of a 3D round hold no sub-element).  The
+      // two half-warps test each item against their own 7 inner points (16 items per pass, the
+      // radius from the item's vertices: Bey's children are not all similar to their parent);
+      // an item decided for all 14 inner points is summed in closed form by both halves, and
+      // the undecided items are compacted to the front of the buffer.  Returns their number.
+      auto closed_final_3d = [&](int n_it) -> int {
+        constexpr int PAD = VPad<D>::N;
+        R* ivw = wm.iv + (size_t)KIND_FINAL * NV * IMAX * PAD;
+        R* iww = wm.iw + KIND_FINAL * IMAX;
+        const int half = lane >> 4, li = lane & 15;
+        int n_keep = 0;
+        for (int b0 = 0; b0 < n_it; b0 += 16) {
+          const int it = b0 + li;
+          const bool valid = it < n_it;
+          R V[NV][D], wv = 0;
+#pragma unroll
+          for (int a = 0; a < NV; a++) {
+            if (valid) vload<D, R>(ivw + ((size_t)a * IMAX + it) * PAD, V[a]);
+            else {
+#pragma unroll
+              for (int k = 0; k < D; k++) V[a][k] = 0;
+            }
+          }
+          if (valid) wv = iww[it];
+          R cen[D];
+#pragma unroll
+          for (int k = 0; k < D; k++) {
+            R t = 0;
+#pragma unroll
+            for (int a = 0; a < NV; a++) t += V[a][k];
+            cen[k] = t * (R)(1.0 / NV);
+          }
+          R r2 = 0;
+#pragma unroll
+          for (int a = 0; a < NV; a++) {
+            R d2 = 0;
+#pragma unroll
+            for (int k = 0; k < D; k++) {
+              const R d = V[a][k] - cen[k];
+              d2 += d * d;
+            }
+            r2 = r2 > d2 ? r2 : d2;
+          }
+          unsigned in_mask;
+          const bool dec = valid && decide_ball(cen, sqrt(r2), in_mask);
+          const bool both = dec && __shfl_xor_sync(0xffffffffu, dec, 16);
+          if (both) {
+            add_closed(cen, wv, in_mask);
+            st_closed += half == 0 ? 1 : 0;
+          }
+          const unsigned keep = __ballot_sync(0xffffffffu, valid && !both) & 0xffffu;
+          const int pos = n_keep + __popc(keep & ((1u << li) - 1u));
+          __syncwarp();  // every item of this pass is in registers before any is moved
+          if (half == 0 && valid && !both) {
+#pragma unroll
+            for (int a = 0; a < NV; a++) vstore<D, R>(ivw + ((size_t)a * IMAX + pos) * PAD, V[a]);
+            iww[pos] = wv;
+          }
+          n_keep += __popc(keep);
+          __syncwarp();
+        }
+        return n_keep;
       };
 
       // integrate the buffered items of one kind (warp-collective)
@@ -1135,9 +1222,12 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         constexpr int PAD = VPad<D>::N;
         const R* iv = wm.iv + (size_t)kind * NV * IMAX * PAD;
         const R* iw = wm.iw + kind * IMAX;
+        if constexpr (D == 3) {
+          if (kind == KIND_FINAL && is_const()) n_it = closed_final_3d(n_it);
+        }
         const int n_x = n_it * NQ;
         st_eval += (unsigned)(n_x * NQ);
-        contrib = true;
+        contrib = contrib || n_x > 0;
         if constexpr (MMA != 0) {
           // Tensor-core contraction.  For each batch of 32 outer points x, lane i stages point
           // i: its coordinates and B[x][c] = w_x phi^l_c(x) (the P1 basis of l, c = 0..D),
@@ -1716,8 +1806,11 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
 // ---- scatter of the local blocks into the CSR values ------------------------------------------
 // One CTA per inner element m; its contributions (the cross blocks of the pairs p of m in
 // [q0, q1), stored at blk[p - p_base], and with_self the self block of m) are summed per CSR
-// entry in shared-memory FP64 accumulators and each entry is added to the global values once
-// (FP64 atomics: the rows of a node are shared by the elements around it).
+// entry in shared-memory accumulators and each entry is added to the global values once
+// (FP64 atomics: the rows of a node are shared by the elements around it).  The accumulators
+// have the blocks' precision R: FP64 for the FP64 path; FP32 for the FP32 paths, whose blocks
+// are FP32 values already (an entry sums about ten of them; shared-memory FP32 atomics are
+// native, FP64 ones are not).
 //
 // Where the column of an entry is found: every row of m's nodes holds the nodes of every l
 // paired with m, so a shared-memory hash table keyed by column node gives, for each of m's
@@ -1731,10 +1824,11 @@ __host__ __device__ inline int scatter_table_size(int max_row) {
   while (t < 2 * max_row) t <<= 1;
   return t;
 }
-__host__ __device__ inline size_t scatter_hash_bytes(int dim, int T, int64_t acc_entries) {
+__host__ __device__ inline size_t scatter_hash_bytes(int dim, int T, int64_t acc_entries,
+                                                     size_t acc_size) {
   size_t b = (size_t)T * 4;                               // keys
   b += ((size_t)T * (dim + 1) * 2 + 7) & ~size_t(7);      // int16 positions per row
-  return b + (size_t)acc_entries * 8;                     // FP64 accumulators
+  return b + (size_t)acc_entries * acc_size;              // accumulators
 }
 
 template <int D, typename R>
@@ -1773,16 +1867,16 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
   const int T = scatter_table_size(max_len);
   const int64_t n = (q1 > q0 ? q1 - q0 : 0);
-  if (scatter_hash_bytes(D, T, total) <= (size_t)dyn) {
+  if (scatter_hash_bytes(D, T, total, sizeof(R)) <= (size_t)dyn) {
     int32_t* keys = reinterpret_cast<int32_t*>(sraw);
     int16_t* pos = reinterpret_cast<int16_t*>(keys + T);
-    double* acc = reinterpret_cast<double*>(sraw + (((size_t)T * 4 + (size_t)T * NV * 2 + 7) & ~size_t(7)));
+    R* acc = reinterpret_cast<R*>(sraw + (((size_t)T * 4 + (size_t)T * NV * 2 + 7) & ~size_t(7)));
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
       keys[t] = -1;
 #pragma unroll
       for (int a = 0; a < NV; a++) pos[t * NV + a] = -1;
     }
-    for (int t = threadIdx.x; t < total; t += blockDim.x) acc[t] = 0.0;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) acc[t] = (R)0;
     __syncthreads();
     const unsigned shift = 32u - (unsigned)(31 - __clz(T));
     auto h0 = [&](int32_t key) -> int { return (int)(((uint32_t)key * 2654435761u) >> shift); };
@@ -1829,7 +1923,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
         for (int a = 0; a < NV; a++) {
           const int ps = slot < 0 ? -1 : pos[slot * NV + a];
           if (ps < 0) atomicOr(err, ERR_CSR);
-          else atomicAdd(&acc[roff[a] + ps], (double)bv[a]);
+          else atomicAdd(&acc[roff[a] + ps], bv[a]);
         }
       }
       if (with_self && threadIdx.x < NB) {
@@ -1837,12 +1931,12 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
         const int slot = lookup(nodes[b]);
         const int ps = slot < 0 ? -1 : pos[slot * NV + a];
         if (ps < 0) atomicOr(err, ERR_CSR);
-        else atomicAdd(&acc[roff[a] + ps], selfblk[m * NB + threadIdx.x]);
+        else atomicAdd(&acc[roff[a] + ps], (R)selfblk[m * NB + threadIdx.x]);
       }
       __syncthreads();
       for (int a = 0; a < NV; a++)
         for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) {
-          const double v = acc[roff[a] + t];
+          const double v = (double)acc[roff[a] + t];
           if (v != 0.0) atomicAdd(&values[rbeg[a] + t], v);
         }
       return;
@@ -1906,12 +2000,14 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   }
 }
 
-// Dynamic shared memory of the scatter kernels for rows of up to max_row columns: the hash
-// layout when it fits in 200 KB, else the cached column lists plus FP64 accumulators when that
-// fits, else the column lists only (0 if even those do not fit).
-inline size_t scatter_smem_bytes(int dim, int max_row) {
+// Dynamic shared memory of the scatter kernels for rows of up to max_row columns and blocks of
+// acc_size-byte values: the hash layout when it fits in 200 KB, else the cached column lists
+// plus FP64 accumulators when that fits, else the column lists only (0 if even those do not
+// fit).
+inline size_t scatter_smem_bytes(int dim, int max_row, size_t acc_size) {
   const size_t total = (size_t)(dim + 1) * (size_t)std::max(1, max_row);
-  const size_t hashed = scatter_hash_bytes(dim, scatter_table_size(std::max(1, max_row)), (int64_t)total);
+  const size_t hashed =
+      scatter_hash_bytes(dim, scatter_table_size(std::max(1, max_row)), (int64_t)total, acc_size);
   if (hashed <= (size_t)200 * 1024) return hashed;
   const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
   if (with_acc <= (size_t)200 * 1024) return with_acc;
@@ -1994,7 +2090,7 @@ nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end
     m_end = std::min<int64_t>(m->n_elem, std::max(m_end, m_begin));
   }
   if (m_end <= m_begin) return NL_OK;
-  const size_t smem = scatter_smem_bytes(D, p->max_row_nnz);
+  const size_t smem = scatter_smem_bytes(D, p->max_row_nnz, sizeof(R));
   if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
   NL_TRY((allow_smem(k_scatter<D, R>, smem)));
