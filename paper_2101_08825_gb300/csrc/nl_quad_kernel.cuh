@@ -1218,7 +1218,9 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           }
           unsigned in_mask;
           const bool dec = valid && decide_ball(cen, sqrt(r2), in_mask);
-          const bool both = dec && __shfl_xor_sync(0xffffffffu, dec, 16);
+          // every lane takes part in the shuffle (a short-circuit would leave lanes out)
+          const bool partner = __shfl_xor_sync(0xffffffffu, dec ? 1 : 0, 16) != 0;
+          const bool both = dec && partner;
           if (both) {
             add_closed(cen, wv, in_mask);
             st_closed += half == 0 ? 1 : 0;
