@@ -1,8 +1,11 @@
 """nl_assemble_noalloc: assembly into the caller's device array with no device allocation by
 the library (for callers that reserve their device memory up front and cannot call cudaMalloc
 while assembling).  Its output must match nl_assemble on the same mesh and pairs, call after
-call: the file-scope scratch it shares across calls keeps the previous call's contents, so
-each call has to start from a clean state.  This file is collected last on purpose."""
+call, within the parity tolerance of the precision (FP64 1e-12; FP32 2e-6: nl_assemble's
+scatter sums an element's FP32 blocks in FP32 shared memory, the allocation-free variant adds
+each block to the FP64 values directly): the file-scope scratch it shares across calls keeps
+the previous call's contents, so each call has to start from a clean state.  This file is
+collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -38,7 +41,7 @@ def test_noalloc_matches_assemble_on_two_calls(case):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        assert rel < 1e-12, (name, call, rel)
+        assert rel < (1e-12 if prec == nl.NL_PREC_FP64 else 2e-6), (name, call, rel)
         assert st.n_point_pairs == st_ref.n_point_pairs and st.n_items == st_ref.n_items
 
 
