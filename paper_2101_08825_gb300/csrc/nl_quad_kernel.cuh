@@ -541,8 +541,6 @@ struct WarpMem {
   R* red;         // 16 doubles of scratch (self-block sums)
   float* pf;      // [2][32]: FP32 element records of the current and the next pair
   R* pc;          // [8]: box of the current inner element m (lo, hi)
-  R* tr;          // [32][TRS]: the lanes' end-of-pair sums, transposed through shared memory
-  static constexpr int TRS = (D + 1) * 8 + 4;
   static __host__ __device__ size_t bytes(int scap) {
     using G = Geo<D>;
     constexpr int PAD = VPad<D>::N;
@@ -550,8 +548,6 @@ struct WarpMem {
     b = (b + 15) & ~size_t(15);
     b += sizeof(R) * ((size_t)2 * G::NV * IMAX * PAD + 2 * IMAX) + sizeof(double) * 16 + sizeof(float) * 64 +
          sizeof(R) * 8;
-    b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * 32 * TRS;
     b += 16;
     return (b + 15) & ~size_t(15);
   }
@@ -567,8 +563,6 @@ struct WarpMem {
     red = iw + 2 * IMAX;  // 16-byte aligned: iv and iw hold multiples of 16 bytes
     pf = reinterpret_cast<float*>(reinterpret_cast<char*>(red) + sizeof(double) * 16);
     pc = reinterpret_cast<R*>(pf + 64);
-    const size_t toff = ((size_t)(reinterpret_cast<char*>(pc + 8) - base) + 15) & ~size_t(15);
-    tr = reinterpret_cast<R*>(base + toff);
   }
 };
 
@@ -678,29 +672,12 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
   const int e_rs = NRS == 16 ? (lane >> 1) : lane;
   const bool rs_writer = NRS == 16 ? (lane & 1) == 0 : true;
   R gsh = 0, gsl = 0;
-  // The transposed end-of-pair reduction (MMA == 0) leaves the sum of g over the pair at the
-  // inner point q = 7 gi + lane on lanes 0-6, one per group gi of lanes that share inner
-  // points (2D: one group, 3D: the two half-warps); those lanes keep compensated sums over the
-  // pairs of the current m-run
-  constexpr int NG = D == 2 ? 1 : 2;
-  R gsh2[NG], gsl2[NG];
-#pragma unroll
-  for (int gi = 0; gi < NG; gi++) gsh2[gi] = gsl2[gi] = 0;
 
   auto flush_self = [&]() {
     // S[a][b] = 2 vol_m sum_y W B_a B_b g(y), in FP64 from the compensated sums
     double* sd = reinterpret_cast<double*>(wm.red);
-    if constexpr (MMA == 0) {
-      if (lane < NYL) {
-#pragma unroll
-        for (int gi = 0; gi < NG; gi++) sd[NYL * gi + lane] = (double)gsh2[gi] + (double)gsl2[gi];
-      }
-#pragma unroll
-      for (int gi = 0; gi < NG; gi++) gsh2[gi] = gsl2[gi] = 0;
-    } else {
-      if (rs_writer && e_rs >= NBLK && e_rs < NBLK + NQ) sd[e_rs - NBLK] = (double)gsh + (double)gsl;
-      gsh = gsl = 0;
-    }
+    if (rs_writer && e_rs >= NBLK && e_rs < NBLK + NQ) sd[e_rs - NBLK] = (double)gsh + (double)gsl;
+    gsh = gsl = 0;
     __syncwarp();
     if (lane < NBLK) {
       int a = lane / NV, b = lane % NV;
@@ -1172,73 +1149,6 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         return true;
       };
 
-      // 3D: the same closed form, applied to a buffer of FINAL items just before it is
-      // integrated (at classification time most lanes of a 3D round hold no sub-element).  The
-      // two half-warps test each item against their own 7 inner points (16 items per pass, the
-      // radius from the item's vertices: Bey's children are not all similar to their parent);
-      // an item decided for all 14 inner points is summed in closed form by both halves, and
-      // the undecided items are compacted to the front of the buffer.  Returns their number.
-      auto closed_final_3d = [&](int n_it) -> int {
-        constexpr int PAD = VPad<D>::N;
-        R* ivw = wm.iv + (size_t)KIND_FINAL * NV * IMAX * PAD;
-        R* iww = wm.iw + KIND_FINAL * IMAX;
-        const int half = lane >> 4, li = lane & 15;
-        int n_keep = 0;
-        for (int b0 = 0; b0 < n_it; b0 += 16) {
-          const int it = b0 + li;
-          const bool valid = it < n_it;
-          R V[NV][D], wv = 0;
-#pragma unroll
-          for (int a = 0; a < NV; a++) {
-            if (valid) vload<D, R>(ivw + ((size_t)a * IMAX + it) * PAD, V[a]);
-            else {
-#pragma unroll
-              for (int k = 0; k < D; k++) V[a][k] = 0;
-            }
-          }
-          if (valid) wv = iww[it];
-          R cen[D];
-#pragma unroll
-          for (int k = 0; k < D; k++) {
-            R t = 0;
-#pragma unroll
-            for (int a = 0; a < NV; a++) t += V[a][k];
-            cen[k] = t * (R)(1.0 / NV);
-          }
-          R r2 = 0;
-#pragma unroll
-          for (int a = 0; a < NV; a++) {
-            R d2 = 0;
-#pragma unroll
-            for (int k = 0; k < D; k++) {
-              const R d = V[a][k] - cen[k];
-              d2 += d * d;
-            }
-            r2 = r2 > d2 ? r2 : d2;
-          }
-          unsigned in_mask;
-          const bool dec = valid && decide_ball(cen, sqrt(r2), in_mask);
-          // every lane takes part in the shuffle (a short-circuit would leave lanes out)
-          const bool partner = __shfl_xor_sync(0xffffffffu, dec ? 1 : 0, 16) != 0;
-          const bool both = dec && partner;
-          if (both) {
-            add_closed(cen, wv, in_mask);
-            st_closed += half == 0 ? 1 : 0;
-          }
-          const unsigned keep = __ballot_sync(0xffffffffu, valid && !both) & 0xffffu;
-          const int pos = n_keep + __popc(keep & ((1u << li) - 1u));
-          __syncwarp();  // every item of this pass is in registers before any is moved
-          if (half == 0 && valid && !both) {
-#pragma unroll
-            for (int a = 0; a < NV; a++) vstore<D, R>(ivw + ((size_t)a * IMAX + pos) * PAD, V[a]);
-            iww[pos] = wv;
-          }
-          n_keep += __popc(keep);
-          __syncwarp();
-        }
-        return n_keep;
-      };
-
       // integrate the buffered items of one kind (warp-collective)
       auto integrate = [&](int kind, int n_it) {
         const MollK MK{P.fmqe, P.ftqe, P.fue};
@@ -1247,9 +1157,6 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
         constexpr int PAD = VPad<D>::N;
         const R* iv = wm.iv + (size_t)kind * NV * IMAX * PAD;
         const R* iw = wm.iw + kind * IMAX;
-        if constexpr (D == 3) {
-          if (kind == KIND_FINAL && is_const()) n_it = closed_final_3d(n_it);
-        }
         const int n_x = n_it * NQ;
         st_eval += (unsigned)(n_x * NQ);
         contrib = contrib || n_x > 0;
@@ -1729,107 +1636,6 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           U[0] -= uh[k];
           U[k + 1] = uh[k];
         }
-        if constexpr (MMA == 0) {
-          // Transposed reduction.  Every lane writes its row of sums H_c(y_i) (c = 0..D, its 7
-          // inner points i) and U_c into shared memory, column c*8 + i (i = 7: U_c); lane
-          // L = c*8 + i then adds its column over the lanes of each group (3D: the two
-          // half-warps hold different inner points), contracts it with W_y B_a(y) (the U
-          // column with sum_y W_y B_a(y)), and shuffles reduce the contributions to block
-          // entry (a, c) over i (lane c*8 keeps them) and to g(y) over c (lanes 0-6 keep them).
-          constexpr int TRS = WarpMem<D, R>::TRS;
-          R* tr = wm.tr;
-          {
-            R row[NV * 8];
-#pragma unroll
-            for (int i = 0; i < NYL; i++) {
-              R h0 = gp[i];
-#pragma unroll
-              for (int k = 0; k < D; k++) {
-                h0 -= hp[k][i];
-                row[(k + 1) * 8 + i] = hp[k][i];
-              }
-              row[i] = h0;
-            }
-#pragma unroll
-            for (int c = 0; c < NV; c++) row[c * 8 + 7] = U[c];
-            R* dst = tr + lane * TRS;
-            if constexpr (F32) {
-#pragma unroll
-              for (int t = 0; t < NV * 8; t += 4)
-                *reinterpret_cast<float4*>(dst + t) = make_float4(row[t], row[t + 1], row[t + 2], row[t + 3]);
-            } else {
-#pragma unroll
-              for (int t = 0; t < NV * 8; t += 2)
-                *reinterpret_cast<double2*>(dst + t) = make_double2(row[t], row[t + 1]);
-            }
-          }
-          __syncwarp();
-          const int cc = lane >> 3, ii = lane & 7;
-          R tot[NG];
-#pragma unroll
-          for (int gi = 0; gi < NG; gi++) tot[gi] = 0;
-          if (cc < NV) {
-            if (ii < NYL) {
-#pragma unroll
-              for (int gi = 0; gi < NG; gi++) {
-                R t = 0;
-#pragma unroll 8
-                for (int r = gi * (32 / NG); r < (gi + 1) * (32 / NG); r++) t += tr[r * TRS + lane];
-                tot[gi] = t;
-              }
-            } else {
-              R t = 0;
-#pragma unroll 8
-              for (int r = 0; r < 32; r++) t += tr[r * TRS + lane];
-#pragma unroll
-              for (int gi = 0; gi < NG; gi++) tot[gi] = t;
-            }
-          }
-          R part[NV];
-#pragma unroll
-          for (int a = 0; a < NV; a++) part[a] = 0;
-          if (cc < NV) {
-            if (ii < NYL) {
-#pragma unroll
-              for (int gi = 0; gi < NG; gi++)
-#pragma unroll
-                for (int a = 0; a < NV; a++) part[a] += sWB[(NYL * gi + ii) * NV + a] * tot[gi];
-            } else {
-#pragma unroll
-              for (int a = 0; a < NV; a++) part[a] = sWBs[a] * tot[0];
-            }
-          }
-#pragma unroll
-          for (int off = 1; off <= 4; off <<= 1)
-#pragma unroll
-            for (int a = 0; a < NV; a++) part[a] += __shfl_xor_sync(0xffffffffu, part[a], off);
-          if (ii == 0 && cc < NV) {
-#pragma unroll
-            for (int a = 0; a < NV; a++) {
-              const R cval = (R)(-2) * vol_m * part[a];
-              if (DIRECT) {
-                const int64_t pos = csr_find(P.row_ptr, P.col, P.conn[cur_m * NV + a],
-                                             P.conn[(int64_t)l * NV + cc]);
-                if (pos < 0) err |= ERR_CSR;
-                else atomicAdd(&P.values[pos], (double)cval);
-              } else {
-                reinterpret_cast<R*>(P.blk)[(p - P.p_begin) * NBLK + a * NV + cc] = cval;
-              }
-            }
-          }
-          R gs[NG];
-#pragma unroll
-          for (int gi = 0; gi < NG; gi++) {
-            gs[gi] = tot[gi];
-            gs[gi] += __shfl_xor_sync(0xffffffffu, gs[gi], 8);
-            gs[gi] += __shfl_xor_sync(0xffffffffu, gs[gi], 16);
-          }
-          const R ugt = __shfl_sync(0xffffffffu, gs[0], 7);  // sum_c U_c: the closed forms' weight
-          if (lane < NYL) {
-#pragma unroll
-            for (int gi = 0; gi < NG; gi++) two_sum_add(gsh2[gi], gsl2[gi], gs[gi] + ugt);
-          }
-        } else {
         // lane partial of sum_y W_y B_a(y) H_c(y) over the lane's inner points, then the lane's g
         // at its inner points (with the uniform part; 3D: both half-warp lanes of an outer
         // point hold part of it), zero elsewhere
@@ -1920,7 +1726,6 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           }
         }
         if (e_rs >= NBLK && e_rs < NBLK + NQ) two_sum_add(gsh, gsl, tot_e);
-        }  // MMA != 0
       }
       __syncwarp();
     }

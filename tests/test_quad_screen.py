@@ -193,55 +193,3 @@ def test_closed_form_final_items_have_mu_exactly_0_or_1(eps_div):
         n_out += int(outside.sum())
     assert n_in > 0 and n_out > 0
 
-
-def test_closed_form_final_items_3d_have_mu_exactly_0_or_1():
-    # 3D FINAL sub-elements summed in closed form before integration: the centroid c and the
-    # radius R = max |v - c| over the sub-element's own vertices (Bey's children are not all
-    # similar to their parent); an inner point y with |c - y| < delta - eps - R - margin (or
-    # > delta + eps + R + margin) must have every quadrature point x of the sub-element within
-    # delta - eps (beyond delta + eps) by a clear gap, in the FP32 coordinates of the kernel.
-    import oracle as O
-    h = 1 / 16
-    delta, eps = 0.125, 0.0125
-    layer = int(np.ceil((delta + eps) / h - 1e-9))
-    mesh = structured_mesh(3, (16, 16, 16), h, (0.0, 0.0, 0.0), layer, jitter=0.1, seed=6)
-    EV = mesh.coords.T[mesh.conn]
-    rng = np.random.default_rng(10)
-    max_ext = float((EV.max(axis=1) - EV.min(axis=1)).max())
-    cen_e = EV.mean(axis=1)
-    tree = cKDTree(cen_e)
-    n = 2000
-    ms = rng.integers(0, mesh.n_elem, n)
-    ls = np.array([rng.choice(c) for c in tree.query_ball_point(cen_e[ms], delta + eps + 2 * max_ext)])
-    b, _ = O.quad_rule(3)
-    bf = b.astype(f32)
-    off = (EV[:, 1:, :] - EV[:, :1, :]).astype(f32)
-    v0 = EV[:, 0, :]
-    v0h = v0.astype(f32)
-    v0l = (v0 - v0h.astype(np.float64)).astype(f32)
-    Vm = np.concatenate([np.zeros((n, 1, 3), f32), off[ms]], axis=1)
-    Y = np.einsum("qa,nak->nqk", bf, Vm).astype(f32)  # the 14 inner points of m
-    Vl0 = ((v0h[ls] - v0h[ms]).astype(f32) + (v0l[ls] - v0l[ms]).astype(f32)).astype(f32)
-    V = np.concatenate([Vl0[:, None, :], (Vl0[:, None, :] + off[ls]).astype(f32)], axis=1)
-    margin = f32(2e-5 * (delta + eps + 2.0 * max_ext))
-    dme, dpe = f32(delta - eps), f32(delta + eps)
-    n_in = n_out = 0
-    for level in range(1, 4):
-        if level > 1:
-            V = _refine(V, rng.integers(0, 8, n), 3, f32)
-        cen = (V.sum(axis=1) * f32(1 / 4)).astype(f32)
-        rad = np.sqrt((((V - cen[:, None, :]) ** 2).sum(-1)).max(axis=1).astype(f32)).astype(f32)
-        lo = (dme - rad - margin).astype(f32)
-        hi = (dpe + rad + margin).astype(f32)
-        lo2 = np.where(lo > 0, lo * lo, f32(-1)).astype(f32)
-        hi2 = (hi * hi).astype(f32)
-        d2 = (((cen[:, None, :] - Y) ** 2).sum(-1)).astype(f32)  # (n, 14)
-        inside, outside = d2 < lo2[:, None], d2 > hi2[:, None]
-        X = np.einsum("qa,nak->nqk", bf, V).astype(f32)  # outer points of the sub-element
-        r = np.sqrt(((X[:, :, None, :].astype(np.float64) - Y[:, None, :, :]) ** 2).sum(-1))
-        gap = 0.5 * float(margin)
-        assert np.all(r.max(axis=1)[inside] < float(dme) - gap), level
-        assert np.all(r.min(axis=1)[outside] > float(dpe) + gap), level
-        n_in += int(inside.sum())
-        n_out += int(outside.sum())
-    assert n_in > 0 and n_out > 0
