@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--eps-study", type=int, default=1,
                     help="the eps-convergence leg (0 = skip)")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--serve-requests", type=int, default=16,
+    ap.add_argument("--serve-requests", type=int, default=32,
                     help="requests of the seeded 512-request serving stream replayed by the "
                          "serving leg (0 = skip; 512 = the whole stream)")
     ap.add_argument("--serve-slots", type=int, default=4)
