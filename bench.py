@@ -49,7 +49,7 @@ C2_BLOCK = ["c2_2d", "c2_2d_eps20", "c2_2d_gauss", "c2_2d_gauss_eps20"]
 # same dimension (profiles/k_quad_2d_fp32_c2_h128.md, profiles/k_quad_3d_fp32_c3_h10.md)
 # divided by its element pairs.  Almost all of it is the block buffer, written once per pair,
 # so it scales with the pairs of a launch.  None: no capture of the current version.
-TRAFFIC_BYTES_PER_PAIR = {2: 35.66, 3: None}
+TRAFFIC_BYTES_PER_PAIR = {2: 35.37, 3: 63.45}
 
 
 def parse():

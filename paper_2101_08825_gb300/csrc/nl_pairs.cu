@@ -359,14 +359,18 @@ __global__ void k_row_bound(int64_t n_vert, const int64_t* __restrict__ n2e_off,
   atomicMax((unsigned long long*)max_sum, (unsigned long long)s);
 }
 
-// FILL = false: count the columns of row i; FILL = true: write them sorted.
-template <int D, bool FILL>
+// MODE 0: count the columns of row i; MODE 1: write them sorted into col at row_ptr[i];
+// MODE 2: count them and write them sorted into the staging rows tmp[i * rowcap ...] (one pass
+// instead of two; k_copy_rows then packs the staged rows once row_ptr is known).
+template <int D, int MODE>
 __global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
                        const int64_t* __restrict__ n2e_off, const int32_t* __restrict__ n2e,
                        const int64_t* __restrict__ pair_off, const int32_t* __restrict__ pair_l,
                        int eh, int nh, int32_t* __restrict__ row_cnt,
                        const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
-                       int* __restrict__ err, int* __restrict__ max_row) {
+                       int* __restrict__ err, int* __restrict__ max_row, int32_t* __restrict__ tmp,
+                       int rowcap) {
+  constexpr bool FILL = MODE == 1;
   extern __shared__ int32_t smem[];
   int32_t* etab = smem;
   int32_t* ntab = smem + eh;
@@ -395,16 +399,20 @@ __global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
     if (threadIdx.x == 0) atomicOr(err, ERR_HASH_FULL);
     return;
   }
-  if (!FILL) {
+  if (MODE != 1) {
     if (threadIdx.x == 0) {
       row_cnt[i] = ncount;
       atomicMax(max_row, ncount);
     }
-    return;
+    if (MODE == 0) return;
   }
   int n = ncount;
-  if ((int64_t)n != row_ptr[i + 1] - row_ptr[i]) {
+  if (MODE == 1 && (int64_t)n != row_ptr[i + 1] - row_ptr[i]) {
     if (threadIdx.x == 0) atomicOr(err, ERR_ROW_COUNT);
+    return;
+  }
+  if (MODE == 2 && n > rowcap) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_HASH_FULL);
     return;
   }
   // compact the node set into etab[0..n), then sort
@@ -421,7 +429,21 @@ __global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
   for (int t = n + threadIdx.x; t < np2; t += blockDim.x) etab[t] = INT_MAX;
   __syncthreads();
   block_bitonic_sort(etab, np2);
-  for (int t = threadIdx.x; t < n; t += blockDim.x) col[row_ptr[i] + t] = etab[t];
+  if (MODE == 1) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) col[row_ptr[i] + t] = etab[t];
+  } else {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) tmp[i * (int64_t)rowcap + t] = etab[t];
+  }
+}
+
+// Packs the staged sorted rows (k_rows MODE 2) into the CSR column array (warp per row).
+__global__ void k_copy_rows(int64_t n_vert, int rowcap, const int32_t* __restrict__ tmp,
+                            const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_vert) return;
+  const int64_t b = row_ptr[i], n = row_ptr[i + 1] - b;
+  for (int64_t t = lane; t < n; t += 32) col[b + t] = tmp[i * (int64_t)rowcap + t];
 }
 
 int next_pow2(int64_t v) {
@@ -542,13 +564,30 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   int eh = next_pow2(std::max<int64_t>(64, std::min<int64_t>(2 * max_sum, 32768)));
   int nh = std::min(8192, eh);
   size_t rsmem = sizeof(int32_t) * (eh + nh);
-  NL_TRY((allow_smem(k_rows<D, false>, rsmem)));
-  NL_TRY((allow_smem(k_rows<D, true>, rsmem)));
+  NL_TRY((allow_smem(k_rows<D, 0>, rsmem)));
+  NL_TRY((allow_smem(k_rows<D, 1>, rsmem)));
+  NL_TRY((allow_smem(k_rows<D, 2>, rsmem)));
   DevBuf<int32_t> rcnt;
   NL_TRY(rcnt.alloc(nvv, s));
-  k_rows<D, false><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
-                                                     eh, nh, rcnt.p, nullptr, nullptr, err.p,
-                                                     max_cnt.p + 1);
+  // one pass that counts and sorts each row into a staging area of rowcap columns per row (the
+  // row's capacity check keeps every row below 3/4 of the node table), when that area fits in
+  // a quarter of the free memory (and 4 GiB); otherwise a counting pass and a filling pass
+  const int rowcap = nh * 3 / 4;
+  size_t free_b = 0, total_b = 0;
+  NL_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t stage_bytes = (size_t)nvv * (size_t)rowcap * sizeof(int32_t);
+  const bool staged = stage_bytes <= std::min<size_t>(free_b / 4, (size_t)4 << 30);
+  DevBuf<int32_t> stage;
+  if (staged) {
+    NL_TRY(stage.alloc(stage_bytes / sizeof(int32_t), s));
+    k_rows<D, 2><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
+                                                       eh, nh, rcnt.p, nullptr, nullptr, err.p,
+                                                       max_cnt.p + 1, stage.p, rowcap);
+  } else {
+    k_rows<D, 0><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
+                                                       eh, nh, rcnt.p, nullptr, nullptr, err.p,
+                                                       max_cnt.p + 1, nullptr, 0);
+  }
   NL_CUDA(cudaGetLastError());
   DevBuf<int64_t> rp;
   NL_TRY(rp.alloc(nvv + 1, s));
@@ -566,8 +605,13 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   }
   DevBuf<int32_t> col;
   NL_TRY(col.alloc(nnz > 0 ? nnz : 1, s));
-  k_rows<D, true><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
-                                                    eh, nh, nullptr, rp.p, col.p, err.p, nullptr);
+  if (staged) {
+    k_copy_rows<<<NL_CNT((unsigned)((nvv * 32 + 255) / 256)), 256, 0, s>>>(nvv, rowcap, stage.p, rp.p, col.p);
+  } else {
+    k_rows<D, 1><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
+                                                       eh, nh, nullptr, rp.p, col.p, err.p, nullptr,
+                                                       nullptr, 0);
+  }
   NL_CUDA(cudaGetLastError());
   NL_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));
