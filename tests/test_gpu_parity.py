@@ -288,3 +288,26 @@ def test_precision_run_is_reported():
     pl = nl.Plan([(m, p, 0.4, 0.05, 2, 1, 0)], precision=nl.NL_PREC_MIXED_TF32)
     pl.execute()
     assert pl.sync()[0].precision_run == nl.NL_PREC_FP32
+
+
+def test_matrix_apply_equals_csr_product():
+    # nl_matrix_apply: y = A x over every row on the device, against the CSR product of the
+    # exported values (FP64; only the summation order differs)
+    import torch
+    mesh = structured_mesh(3, 3, 1 / 3, 0.0, 1, jitter=0.1, seed=7)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, 0.22, 0.02)
+    A, _ = nl.nl_assemble(m, p, 0.22, 0.02, 2)
+    vals = A.export()
+    _, _, rp, col = p.export(mesh.n_elem, mesh.n_vert)
+    x = np.random.default_rng(3).standard_normal(mesh.n_vert)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    yd = torch.full_like(xd, float("nan"))
+    A.apply(xd.data_ptr(), yd.data_ptr())
+    torch.cuda.synchronize()
+    rows = np.repeat(np.arange(mesh.n_vert), np.diff(rp))
+    ref = np.bincount(rows, weights=vals * x[col], minlength=mesh.n_vert)
+    assert np.abs(yd.cpu().numpy() - ref).max() <= 1e-13 * np.abs(vals).max() * np.abs(x).max() * 64
+    with pytest.raises(nl.NLError) as e:
+        A.apply(xd.data_ptr(), xd.data_ptr())
+    assert e.value.status == nl.NL_EINVAL
