@@ -56,3 +56,38 @@ def test_noalloc_rejects_meshes_beyond_its_scratch():
     with pytest.raises(nl.NLError) as e:
         nl.nl_assemble_noalloc(m, p, 1.5 / 340, 0.1 / 340, 2, out.data_ptr())
     assert e.value.status == nl.NL_EINVAL and "scratch" in str(e.value)
+
+
+def test_noalloc_makes_no_device_allocation():
+    # Every device allocation of the library goes through its allocator hook (nl_set_allocator).
+    # A hook that counts its calls and refuses to allocate is installed around one call of the
+    # allocation-free entry point (the handles are created before and released after, with the
+    # default allocator): it must not be called, and the result must still match.  The ordinary
+    # entry point, under the same hook, asks for memory and fails with NL_ENOMEM.
+    import ctypes
+    import torch
+    w = WORKLOADS["c1_2d"]
+    mesh = workload_mesh(w)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, w.delta, w.eps)
+    A, _ = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max)
+    ref = A.export()
+    out = torch.zeros(p.info()[1], dtype=torch.float64, device="cuda")
+    calls = []
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    alloc_cb = ALLOC(lambda nbytes, stream, ctx: calls.append(int(nbytes)) or None)
+    free_cb = FREE(lambda ptr, nbytes, stream, ctx: calls.append(-1))
+    L = nl.lib()
+    assert L.nl_set_allocator(ctypes.cast(alloc_cb, ctypes.c_void_p), ctypes.cast(free_cb, ctypes.c_void_p), None) == 0
+    try:
+        nl.nl_assemble_noalloc(m, p, w.delta, w.eps, w.L_max, out.data_ptr())
+        torch.cuda.synchronize()
+        assert calls == []
+        with pytest.raises(nl.NLError) as e:
+            nl.nl_assemble(m, p, w.delta, w.eps, w.L_max)
+        assert e.value.status == nl.NL_ENOMEM and calls
+    finally:
+        assert L.nl_set_allocator(None, None, None) == 0
+    got = out.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
