@@ -671,11 +671,12 @@ def run_eps_study(args):
     """eps-convergence study (the P1 analogue of the paper's Table 4): Omega = (0,1)^2,
     h = 1/32, delta = 0.1, u = x^4 + y^4 with the forcing of the sharp kernel
     (f = -12 (x^2 + y^2) - 2 delta^2, its P1 interpolant), the mollified kernel assembled for
-    eps = delta/4 ... delta/64 at L_max = L0 - 1, L0, L0 + 1, where L0 makes Algorithm 1's
+    eps = delta/4 ... delta/64 at L_max = L0 - 1 ... L0 + 2, where L0 makes Algorithm 1's
     smallest sub-elements about eps (L0 = ceil(log2(h / eps)) + 1).  Reports per (eps, L_max)
-    the FP32 assembly time and work, and two differences of discrete solutions in L2(Omega):
-    to the same eps at L_max + 1 (quadrature error) and, at L0, to eps / 2 (the mollifier's
-    contribution, expected to fall like eps^2)."""
+    the FP32 and FP64 assembly times and the work, and two differences of the FP64 discrete
+    solutions in L2(Omega) (FP64, so that no FP32 rounding of sums over up to 1e5 point pairs
+    per element pair enters): to the same eps at L_max + 1 (quadrature error) and, at L0, to
+    eps / 2 (the mollifier's contribution, expected to fall like eps^2)."""
     import torch
     from paper_2101_08825_gb300 import nl
     n, delta = 32, 0.1
@@ -698,13 +699,15 @@ def run_eps_study(args):
             if L < 1:
                 continue
             nl.nl_assemble(dm, p, delta, eps, L, precision=nl.NL_PREC_FP32)  # warm
-            A, st = nl.nl_assemble(dm, p, delta, eps, L, precision=nl.NL_PREC_FP32)
+            _, st32 = nl.nl_assemble(dm, p, delta, eps, L, precision=nl.NL_PREC_FP32)
+            A, st = nl.nl_assemble(dm, p, delta, eps, L, precision=nl.NL_PREC_FP64)
             b = nl.nl_rhs(dm, A, g, f_nodes=f)
             u, it, rr, _ = nl.nl_solve(A, b, g, solver=1, rtol=1e-12, max_iter=20000,
-                                       precision=nl.NL_PREC_FP32)
+                                       precision=nl.NL_PREC_FP64)
             sol[(div, L)] = u
             rows.append({"eps": f"delta/{div}", "L_max": L, "L0": L0,
-                         "assembly_ms": round(st.ms_assemble, 3),
+                         "assembly_ms_fp32": round(st32.ms_assemble, 3),
+                         "assembly_ms_fp64": round(st.ms_assemble, 3),
                          "point_pairs": st.n_point_pairs, "element_pairs": st.n_pairs})
             del A, b
     for r in rows:
@@ -722,7 +725,8 @@ def run_eps_study(args):
         conv[k]["p2"] = round(math.log2(conv[k]["diff_to_half_eps_l2"] /
                                         conv[k + 1]["diff_to_half_eps_l2"]), 3)
     return {"workload": "Omega=(0,1)^2, h=1/32, delta=0.1, u=x^4+y^4, sharp-kernel forcing; "
-                        "FP32 assembly, FP32-in-FP64 BiCGStab to 1e-12",
+                        "FP64 assembly and BiCGStab to 1e-12 for the differences, FP32 "
+                        "assembly timed beside",
             "runs": rows, "eps_convergence": conv}
 
 
