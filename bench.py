@@ -64,6 +64,11 @@ def parse():
                     help="timed mixed steps per combination of the 2D block (0 = skip the block)")
     ap.add_argument("--c2-fp64-steps", type=int, default=1,
                     help="timed FP64 steps per combination of the 2D block")
+    ap.add_argument("--p2-steps", type=int, default=2,
+                    help="timed FP32 steps of the P2 leg (the 2D workload with P2 triangles; "
+                         "0 = skip the leg)")
+    ap.add_argument("--p2-fp64-steps", type=int, default=1,
+                    help="timed FP64 steps of the P2 leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="wall seconds of the oracle sample on all host cores")
@@ -212,7 +217,8 @@ def describe(w, mesh):
     shape = "triangles" if mesh.dim == 2 else "tetrahedra"
     n_omega = int(mesh.elem_in_omega.sum())
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
-    return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} P1 {shape} "
+    order = "P2" if mesh.conn.shape[1] == 6 else "P1"
+    return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} {order} {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
             f"layer {w.layer} cells, L_max={w.L_max}, {kern} kernel, jitter {w.jitter:g}h "
             f"seed {w.seed}; "
@@ -224,18 +230,26 @@ def u_exact(mesh):
 
 
 def l2_err_omega(mesh, u_h, rule):
-    """||u - u_h||_{L2(Omega)} with the degree-5 rule per element (u = sum x_k^2)."""
+    """||u - u_h||_{L2(Omega)} with the degree-5 rule per element (u = sum x_k^2); P1, or P2
+    triangles when the elements have six nodes (basis lambda_a (2 lambda_a - 1) at the
+    vertices, 4 lambda_a lambda_b at the edge nodes (0,1), (1,2), (0,2))."""
     b, w = rule
     P = mesh.points()
     conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
-    V = P[conn]  # (ne, nv, dim)
+    nv = mesh.dim + 1
+    V = P[conn[:, :nv]]  # (ne, nv, dim)
     if mesh.dim == 2:
         vol = 0.5 * np.abs((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1]) -
                            (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
     else:
         vol = np.abs(np.linalg.det(V[:, 1:] - V[:, :1])) / 6.0
     X = np.einsum("qv,evk->eqk", b, V)
-    uh = np.einsum("qv,ev->eq", b, u_h[conn])
+    if conn.shape[1] == 6:
+        phi = np.concatenate([b * (2 * b - 1), 4 * b[:, [0]] * b[:, [1]], 4 * b[:, [1]] * b[:, [2]],
+                              4 * b[:, [0]] * b[:, [2]]], axis=1)
+    else:
+        phi = b
+    uh = np.einsum("qv,ev->eq", phi, u_h[conn])
     d = (X ** 2).sum(-1) - uh
     return float(math.sqrt(np.sum(vol[:, None] * w[None, :] * d * d)))
 
@@ -310,8 +324,9 @@ def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False, stb=None):
         pb = nl.nl_pairs_build(dmesh, w.delta, w.eps)
         _, stb = nl.nl_assemble(dmesh, pb, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec,
                                 count_band=True, mindist_l2=l2)
-    flops = roofline_flops(mesh.dim, stb)
-    flops_ev = roofline_flops(mesh.dim, stb, evaluated_only=True)
+    nb = mesh.conn.shape[1]
+    flops = roofline_flops(mesh.dim, stb, nb=nb)
+    flops_ev = roofline_flops(mesh.dim, stb, evaluated_only=True, nb=nb)
     quad_ms = statistics.mean(s.ms_quad for s in stats)
     f32 = prec != nl.NL_PREC_FP64
     peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
@@ -323,7 +338,8 @@ def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False, stb=None):
         "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
         "units": "Algorithm-1 quadrature point pairs (closed-form ones included)",
         "frac_evaluated_only": round(achieved_ev / peak, 4),
-        "kernel": f"k_quad<{mesh.dim},{rtype},{w.kernel}>", "flops_per_assembly": flops,
+        "kernel": (f"k_quad_p2<{rtype},{w.kernel}>" if nb == 6 else
+                   f"k_quad<{mesh.dim},{rtype},{w.kernel}>"), "flops_per_assembly": flops,
         "kernel_ms_per_assembly": round(quad_ms, 3),
         "launches_per_assembly": int(stats[-1].n_quad_launches),
         "peak_source": ("152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (derived)" if f32 else
@@ -497,6 +513,8 @@ def run_ours(args, rank, world, local):
         out["e2e"] = e2e_ours(args, mesh, w, stream, world)
     if args.c2_steps > 0:
         out["c2_2d"] = run_c2_block(args, nl, torch, stream, flush, world)
+    if args.p2_steps > 0:
+        out["p2"] = run_p2_block(args, nl, torch, stream, flush, world)
     if args.eps_study:
         out["eps_study"] = run_eps_study(args)
     if args.batch_problems > 0:
@@ -547,7 +565,48 @@ def run_c2_block(args, nl, torch, stream, flush, world):
     return out
 
 
-def roofline_flops(dim, st, evaluated_only=False):
+def run_p2_block(args, nl, torch, stream, flush, world):
+    """P2 triangles on the 2D workload's triangulation (h = 1/256, 141,512 triangles, 284,089
+    nodes): the FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
+    BiCGStab), their L2 errors, and the roofline of the P2 assembly kernel in both
+    precisions."""
+    w, mesh = workload("c2_2d_p2")
+    rule = nl.nl_quad_rule(2)
+    dm = nl.mesh_from(mesh)
+    mx = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP32, args.p2_steps, 1, flush, world,
+                  keep_last=args.p2_fp64_steps > 0)
+    ms = statistics.mean(mx["times"])
+    st = mx["stats"][-1]
+    stb, roof = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP32, mx["stats"])
+    roof["traffic"] = None
+    r = {"workload": describe(w, mesh), "element_pairs": st.n_pairs,
+         "quad_pt_pairs": st.n_point_pairs, "ms_per_step": round(ms, 3),
+         "element_pairs_per_s": round(world * st.n_pairs / (ms / 1e3), 1),
+         "quad_pt_pairs_per_s": round(world * st.n_point_pairs / (ms / 1e3), 1),
+         "assembly_ms": round(statistics.mean(s.ms_assemble for s in mx["stats"]), 3),
+         "scatter_ms": round(statistics.mean(s.ms_scatter for s in mx["stats"]), 3),
+         "l2_err_omega": l2_err_omega(mesh, mx["last"]["u"], rule),
+         "solve_ms_p50": round(float(np.percentile(mx["solve_ms"], 50)), 3),
+         "solve_iters": mx["last"]["it"], "gpu_launches_per_step": int(mx["launches"] / max(1, args.p2_steps)),
+         "roofline": roof}
+    if args.p2_fp64_steps > 0:
+        f64 = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP64, args.p2_fp64_steps, 0,
+                       flush, world, keep_last=True)
+        ms64 = statistics.mean(f64["times"])
+        _, roof64 = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP64, f64["stats"], stb=stb)
+        v32, v64 = mx["last"]["values"], f64["last"]["values"]
+        r["fp64"] = {"ms_per_step": round(ms64, 3),
+                     "element_pairs_per_s": round(world * st.n_pairs / (ms64 / 1e3), 1),
+                     "assembly_ms": round(statistics.mean(s.ms_assemble for s in f64["stats"]), 3),
+                     "l2_err_omega": l2_err_omega(mesh, f64["last"]["u"], rule),
+                     "speedup_of_fp32": round(ms64 / ms, 2),
+                     "A_rel_frobenius": float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64)),
+                     "roofline": roof64}
+    del dm
+    return r
+
+
+def roofline_flops(dim, st, evaluated_only=False, nb=None):
     """Algorithmic flops of one assembly (FMA = 2), per quadrature point pair of the method's
     double sum as written (eqs. J21Nr, J22Nr): the distance and r^2 (2D 5, 3D 8), the weight
     w_x w_y C mu (2), the rank-one update of the local block over the nodes of m (2D 6, 3D 8)
@@ -558,10 +617,12 @@ def roofline_flops(dim, st, evaluated_only=False):
     sub-element's point pairs in closed form (mu exactly 1 or 0); evaluated_only counts only
     the point pairs evaluated one by one.  (The kernel itself hoists the contraction with m's
     basis out of the loop over outer points and executes 11 (2D) / 16 (3D) flops per
-    evaluated point pair for the same sums.)"""
+    evaluated point pair for the same sums.)  With nb nodes per element (P2 triangles: 6) the
+    rank-one update costs 2 nb: 20 flops per point pair."""
     pp = int(getattr(st, "n_eval_point_pairs" if evaluated_only else "n_point_pairs", 0) or 0)
     band = max(0, int(getattr(st, "n_band_point_pairs", 0) or 0))
-    per_pp = 14 if dim == 2 else 19
+    nb = nb or dim + 1
+    per_pp = 5 + 2 + 2 * nb + 1 if dim == 2 else 19
     return float(max(0, pp) * per_pp + band * 15)
 
 

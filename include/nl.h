@@ -163,8 +163,27 @@ nl_status nl_mesh_create(int dim, int64_t n_vert, const double* coords, int64_t 
 nl_status nl_mesh_create_box(int dim, const int32_t* cells, double h, const double* lo,
                              int32_t layer, double jitter, uint64_t seed, void* cuda_stream,
                              nl_mesh** out);
+/* Mesh of quadratic (P2) Lagrange triangles (Sec. 6, Tables 1-3, the quadratic columns):
+ * the arguments of nl_mesh_create with dim = 2 and six nodes per element in conn, ordered
+ * (v0, v1, v2, m01, m12, m02): the three vertices, then the nodes at the midpoints of the
+ * edges (v0,v1), (v1,v2), (v0,v2).  n_vert counts every node (vertices and edge nodes);
+ * node_free flags every node.  The elements are straight-sided: each edge node must lie at
+ * the midpoint of its edge.  The basis on an element with barycentric coordinates lambda is
+ * lambda_a (2 lambda_a - 1) at the vertices and 4 lambda_a lambda_b at the edge nodes.
+ * Pairs, pattern, nl_assemble (FP64 and FP32; the MIXED precisions run the FP32 path and
+ * report it in stats->precision_run), nl_rhs and nl_solve accept it; the batched plans and
+ * nl_assemble_noalloc take P1 meshes only.
+ * Errors: those of nl_mesh_create, and NL_EINVAL for an edge node off the midpoint of its
+ * edge (by more than 1e-9 of the edge's length). */
+nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64_t n_elem,
+                            const int32_t* conn, const uint8_t* elem_in_omega,
+                            const uint8_t* node_free, void* cuda_stream, nl_mesh** out);
 nl_status nl_mesh_info(const nl_mesh* mesh, int* dim, int64_t* n_vert, int64_t* n_elem);
-/* Copies the mesh back (host buffers of the sizes of nl_mesh_create; any may be NULL). */
+/* Polynomial order of the mesh's elements (1: P1, 2: P2) and nodes per element (dim+1 or
+ * 6); either pointer may be NULL. */
+nl_status nl_mesh_order(const nl_mesh* mesh, int* order, int* nodes_per_elem);
+/* Copies the mesh back (host buffers of the sizes of nl_mesh_create, conn of
+ * nodes_per_elem*n_elem entries; any may be NULL). */
 nl_status nl_mesh_export(const nl_mesh* mesh, double* coords, int32_t* conn,
                          uint8_t* elem_in_omega, uint8_t* node_free);
 void nl_mesh_destroy(nl_mesh* mesh);
@@ -227,8 +246,9 @@ nl_status nl_matrix_device_values(const nl_matrix* A, double** values);
 void nl_matrix_destroy(nl_matrix* A);
 
 /* Right-hand side with lifting (Sec. 2, eqs. A-F and weak-homo):
- *   F_i = int_Omega f phi_i for free i, f = f_const + the P1 interpolant of f_nodes
- *         (f_nodes may be NULL), integrated with the degree-5 rule per element of Omega;
+ *   F_i = int_Omega f phi_i for free i, f = f_const + the interpolant of f_nodes in the
+ *         mesh's element space (P1 or P2; f_nodes may be NULL), integrated with the
+ *         degree-5 rule per element of Omega;
  *   F~_i = F_i - sum_{k not free} A_ik g_k;  F~_i = 0 for constrained i.
  * f_nodes, g_nodes: host, n_vert values (g_nodes is read at constrained nodes only). */
 nl_status nl_rhs(nl_mesh* mesh, nl_matrix* A, const double* f_nodes, double f_const,

@@ -10,7 +10,7 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, replace
 
-from .mesh import Mesh, structured_mesh
+from .mesh import Mesh, p2_mesh, structured_mesh
 
 KERNEL_CONST = 0
 KERNEL_GAUSS = 1
@@ -37,6 +37,7 @@ class Workload:
     jitter: float = 0.0
     seed: int = 0
     layer_cells: int = 0  # 0: ceil((delta + eps)/h); otherwise the given number of cells
+    order: int = 1        # 1: P1 elements; 2: P2 triangles on the same triangulation
 
     @property
     def layer(self) -> int:
@@ -87,8 +88,14 @@ WORKLOADS = {
     "c3_3d_h10": _unit_box("c3_3d_h10", 3, 10, 0.125, 0.0125, 2),
     # 3D, h = 1/32, delta = 3h, eps = delta/10, 2 levels
     "c4_3d": _unit_box("c4_3d", 3, 32, 3.0 / 32, 0.3 / 32, 2),
+    # the c2_2d triangulation with P2 elements (Sec. 6, the quadratic columns of Tables 1-3)
+    "c2_2d_p2": _unit_box("c2_2d_p2", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1, order=2),
+    # the c2_2d_h128 triangulation with P2 elements: a small case for profiler captures
+    "c2_2d_h128_p2": _unit_box("c2_2d_h128_p2", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1,
+                               order=2),
 }
 
 
 def workload_mesh(w: Workload) -> Mesh:
-    return structured_mesh(w.dim, w.cells, w.h, w.lo, w.layer, jitter=w.jitter, seed=w.seed)
+    m = structured_mesh(w.dim, w.cells, w.h, w.lo, w.layer, jitter=w.jitter, seed=w.seed)
+    return p2_mesh(m) if w.order == 2 else m

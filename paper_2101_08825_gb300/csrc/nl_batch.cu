@@ -157,7 +157,7 @@ nl_status plan_enqueue(nl_plan* pl) {
     launches++;
   }
   if (pl->total_elem > 0) {
-    const size_t smem = scatter_smem_bytes(D, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
+    const size_t smem = scatter_smem_bytes(D + 1, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
     const bool f32 = pl->prec != NL_PREC_FP64;
     const int64_t* ep = pl->d_prefix + (pl->n + 1);
     if (D == 2) {
@@ -188,7 +188,7 @@ nl_status kernel_smem_setup(F* kern, size_t smem) {
 
 // Raises the scatter kernel's shared-memory ceiling before any capture.
 nl_status plan_prepare_scatter(nl_plan* pl) {
-  const size_t smem = scatter_smem_bytes(pl->dim, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
+  const size_t smem = scatter_smem_bytes(pl->dim + 1, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
   if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", pl->max_row_nnz);
   const bool f32 = pl->prec != NL_PREC_FP64;
@@ -276,6 +276,8 @@ nl_status nl_plan_create(int n, nl_mesh* const* meshes, nl_pairs* const* pairs,
     if (!meshes[k] || !pairs[k]) return fail(NL_EINVAL, "nl_plan_create: problem %d has a NULL mesh or pairs", k);
     if (meshes[k]->dim != D) return fail(NL_EINVAL, "nl_plan_create: problem %d is %dD, problem 0 is %dD", k, meshes[k]->dim, D);
     if (pairs[k]->mesh != meshes[k]) return fail(NL_EINVAL, "nl_plan_create: problem %d: pairs of another mesh", k);
+    if (meshes[k]->order != 1)
+      return fail(NL_EINVAL, "nl_plan_create: problem %d: plans take P1 meshes only (use nl_assemble)", k);
     if (kps[k].delta != pairs[k]->delta || kps[k].eps != pairs[k]->eps)
       return fail(NL_EINVAL, "nl_plan_create: problem %d: delta/eps differ from those of its pairs", k);
     NL_TRY(fill_qparams("nl_plan_create", meshes[k], pairs[k], &kps[k], &qps[k], precision, &probs[k]));

@@ -263,9 +263,11 @@ int nl_quad_rule(int dim, double* bary, double* w) {
 // ---- mesh ------------------------------------------------------------------------------------
 namespace {
 
+// Per-element geometry from the first D+1 nodes of each element (its vertices; a P2 element
+// lists its edge nodes after them): nb nodes per element in conn.
 template <int D>
 __global__ void k_mesh_elements(int64_t n_elem, int64_t n_vert, const double* __restrict__ coords,
-                                const int32_t* __restrict__ conn, double* __restrict__ evert,
+                                const int32_t* __restrict__ conn, int nb, double* __restrict__ evert,
                                 double* __restrict__ blo, double* __restrict__ bhi,
                                 double* __restrict__ vol, double* __restrict__ jinv,
                                 float* __restrict__ ef) {
@@ -273,7 +275,7 @@ __global__ void k_mesh_elements(int64_t n_elem, int64_t n_vert, const double* __
   if (e >= n_elem) return;
   double V[D + 1][D];
   for (int a = 0; a <= D; a++) {
-    int32_t v = conn[e * (D + 1) + a];
+    int32_t v = conn[e * nb + a];
     for (int k = 0; k < D; k++) {
       V[a][k] = coords[k * n_vert + v];
       evert[(e * (D + 1) + a) * D + k] = V[a][k];
@@ -373,28 +375,50 @@ void nlx::mesh_release(nl_mesh* m) {
   delete m;
 }
 
-static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords, int64_t n_elem,
-                                  const int32_t* conn, const uint8_t* eio, const uint8_t* nf,
-                                  void* cuda_stream, nl_mesh** out) {
+// order 1: P1 simplices (dim+1 nodes per element); order 2: P2 triangles (6 nodes: the
+// vertices, then the midpoints of the edges (0,1), (1,2), (0,2)).
+static nl_status mesh_create_impl(int dim, int order, int64_t n_vert, const double* coords,
+                                  int64_t n_elem, const int32_t* conn, const uint8_t* eio,
+                                  const uint8_t* nf, void* cuda_stream, nl_mesh** out) {
   using namespace nlx;
   if (!out) return fail(NL_EINVAL, "nl_mesh_create: out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create: dim must be 2 or 3");
+  if (order != 1 && !(order == 2 && dim == 2))
+    return fail(NL_EINVAL, "nl_mesh_create: P2 elements are triangles (dim 2) only");
   if (n_vert <= 0 || n_vert > INT32_MAX || n_elem <= 0 || n_elem > INT32_MAX)
     return fail(NL_EINVAL, "nl_mesh_create: bad sizes n_vert=%lld n_elem=%lld",
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
-  const int nv = dim + 1;
+  const int nv = dim + 1, nb = order == 2 ? 6 : nv;
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
     if (!std::isfinite(coords[i])) return fail(NL_EINVAL, "nl_mesh_create: non-finite coordinate");
   double bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
   double max_ext = 0.0;
   for (int64_t e = 0; e < n_elem; e++) {
     double V[4][3];
-    for (int a = 0; a < nv; a++) {
-      int32_t v = conn[e * nv + a];
+    for (int a = 0; a < nb; a++) {
+      int32_t v = conn[e * nb + a];
       if (v < 0 || v >= n_vert) return fail(NL_EINVAL, "nl_mesh_create: vertex index out of range");
-      for (int k = 0; k < dim; k++) V[a][k] = coords[k * n_vert + v];
+      if (a < nv)
+        for (int k = 0; k < dim; k++) V[a][k] = coords[k * n_vert + v];
+    }
+    if (order == 2) {
+      // straight-sided P2: edge node 3 + j at the midpoint of edge j = (0,1), (1,2), (0,2)
+      static const int ea[3] = {0, 1, 0}, eb[3] = {1, 2, 2};
+      for (int j = 0; j < 3; j++) {
+        const int32_t v = conn[e * nb + 3 + j];
+        double d2 = 0.0, l2 = 0.0;
+        for (int k = 0; k < dim; k++) {
+          const double mid = (V[ea[j]][k] + V[eb[j]][k]) * 0.5;
+          const double d = coords[k * n_vert + v] - mid, ed = V[eb[j]][k] - V[ea[j]][k];
+          d2 += d * d;
+          l2 += ed * ed;
+        }
+        if (!(d2 <= 1e-18 * l2))
+          return fail(NL_EINVAL, "nl_mesh_create_p2: edge node %d of element %lld is not at its edge's midpoint",
+                      3 + j, (long long)e);
+      }
     }
     double det;
     if (dim == 2) {
@@ -425,6 +449,8 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   nl_mesh* m = new nl_mesh();
   m->dim = dim;
+  m->order = order;
+  m->nb = nb;
   m->n_vert = n_vert;
   m->n_elem = n_elem;
   m->stream = s;
@@ -441,7 +467,7 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
   nl_status st = NL_OK;
   do {
     if ((st = dc.alloc(dim * n_vert, s)) != NL_OK) break;
-    if ((st = dconn.alloc(nv * n_elem, s)) != NL_OK) break;
+    if ((st = dconn.alloc(nb * n_elem, s)) != NL_OK) break;
     if ((st = deio.alloc(n_elem, s)) != NL_OK) break;
     if ((st = dnf.alloc(n_vert, s)) != NL_OK) break;
     if ((st = ev.alloc(nv * dim * n_elem, s)) != NL_OK) break;
@@ -450,7 +476,7 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
     if ((st = vol.alloc(n_elem, s)) != NL_OK) break;
     if ((st = jinv.alloc(dim * dim * n_elem, s)) != NL_OK) break;
     if ((st = efb.alloc((size_t)NL_EF_STRIDE(dim) * n_elem, s)) != NL_OK) break;
-    if ((st = n2e.alloc(nv * n_elem, s)) != NL_OK) break;
+    if ((st = n2e.alloc(nb * n_elem, s)) != NL_OK) break;
     if ((st = cnt.alloc(n_vert, s)) != NL_OK) break;
     if ((st = off.alloc(n_vert + 1, s)) != NL_OK) break;
   } while (0);
@@ -464,7 +490,7 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
   };
   cudaError_t ce;
   if ((ce = cudaMemcpyAsync(dc.p, coords, sizeof(double) * dim * n_vert, cudaMemcpyHostToDevice, s)) ||
-      (ce = cudaMemcpyAsync(dconn.p, conn, sizeof(int32_t) * nv * n_elem, cudaMemcpyHostToDevice, s)) ||
+      (ce = cudaMemcpyAsync(dconn.p, conn, sizeof(int32_t) * nb * n_elem, cudaMemcpyHostToDevice, s)) ||
       (ce = cudaMemcpyAsync(deio.p, eio, n_elem, cudaMemcpyHostToDevice, s)) ||
       (ce = cudaMemcpyAsync(dnf.p, nf, n_vert, cudaMemcpyHostToDevice, s)) ||
       (ce = cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * n_vert, s)))
@@ -472,15 +498,15 @@ static nl_status mesh_create_impl(int dim, int64_t n_vert, const double* coords,
   int tb = 256;
   int64_t gb = (n_elem + tb - 1) / tb;
   if (dim == 2)
-    k_mesh_elements<2><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
+    k_mesh_elements<2><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   else
-    k_mesh_elements<3><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
-  int64_t ne = nv * n_elem;
+    k_mesh_elements<3><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
+  int64_t ne = (int64_t)nb * n_elem;
   k_count_n2e<<<NL_CNT((unsigned)((ne + tb - 1) / tb)), tb, 0, s>>>(ne, dconn.p, cnt.p);
   st = exclusive_scan_i32_to_i64(cnt.p, off.p, n_vert, s);
   if (st != NL_OK) return cleanup(st);
   if ((ce = cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * n_vert, s))) return cleanup(cuda_fail(ce, "memset"));
-  k_fill_n2e<<<NL_CNT((unsigned)((ne + tb - 1) / tb)), tb, 0, s>>>(ne, nv, dconn.p, off.p, cnt.p, n2e.p);
+  k_fill_n2e<<<NL_CNT((unsigned)((ne + tb - 1) / tb)), tb, 0, s>>>(ne, nb, dconn.p, off.p, cnt.p, n2e.p);
   if ((ce = cudaGetLastError())) return cleanup(cuda_fail(ce, "nl_mesh_create kernels"));
   if ((ce = cudaStreamSynchronize(s))) return cleanup(cuda_fail(ce, "nl_mesh_create sync"));
   m->coords = dc.release_ownership();
@@ -584,7 +610,7 @@ extern "C" nl_status nl_mesh_create_box(int dim, const int32_t* cells, double h,
       }
     }
   }
-  return mesh_create_impl(dim, n_vert, coords.data(), n_elem, conn.data(), eio.data(), nf.data(),
+  return mesh_create_impl(dim, 1, n_vert, coords.data(), n_elem, conn.data(), eio.data(), nf.data(),
                           cuda_stream, out);
 }
 
@@ -611,8 +637,24 @@ nl_status nl_mesh_create(int dim, int64_t n_vert, const double* coords, int64_t 
                          const int32_t* conn, const uint8_t* elem_in_omega,
                          const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
-  return mesh_create_impl(dim, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+  return mesh_create_impl(dim, 1, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
+}
+
+nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64_t n_elem,
+                            const int32_t* conn, const uint8_t* elem_in_omega,
+                            const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
+  nlx::clear_error();
+  return mesh_create_impl(dim, 2, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+                          cuda_stream, out);
+}
+
+nl_status nl_mesh_order(const nl_mesh* m, int* order, int* nodes_per_elem) {
+  nlx::clear_error();
+  if (!m) return nlx::fail(NL_EINVAL, "nl_mesh_order: NULL mesh");
+  if (order) *order = m->order;
+  if (nodes_per_elem) *nodes_per_elem = m->nb;
+  return NL_OK;
 }
 
 nl_status nl_mesh_info(const nl_mesh* m, int* dim, int64_t* n_vert, int64_t* n_elem) {
@@ -630,7 +672,7 @@ nl_status nl_mesh_export(const nl_mesh* m, double* coords, int32_t* conn, uint8_
   if (!m) return nlx::fail(NL_EINVAL, "nl_mesh_export: NULL mesh");
   cudaStream_t s = m->stream;
   if (coords) NL_CUDA(cudaMemcpyAsync(coords, m->coords, sizeof(double) * m->dim * m->n_vert, cudaMemcpyDeviceToHost, s));
-  if (conn) NL_CUDA(cudaMemcpyAsync(conn, m->conn, sizeof(int32_t) * (m->dim + 1) * m->n_elem, cudaMemcpyDeviceToHost, s));
+  if (conn) NL_CUDA(cudaMemcpyAsync(conn, m->conn, sizeof(int32_t) * m->nb * m->n_elem, cudaMemcpyDeviceToHost, s));
   if (eio) NL_CUDA(cudaMemcpyAsync(eio, m->elem_in_omega, m->n_elem, cudaMemcpyDeviceToHost, s));
   if (nf) NL_CUDA(cudaMemcpyAsync(nf, m->node_free, m->n_vert, cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));

@@ -130,10 +130,12 @@ nl_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, 
 struct nl_mesh {
   std::atomic<int> refs{1};
   int dim = 0;
-  int64_t n_vert = 0, n_elem = 0;
+  int order = 1;                   // 1: P1 simplices, 2: P2 triangles
+  int nb = 0;                      // nodes per element: dim+1 (P1) or 6 (P2)
+  int64_t n_vert = 0, n_elem = 0;  // n_vert counts every node
   cudaStream_t stream = nullptr;
   double* coords = nullptr;        // [dim][n_vert]
-  int32_t* conn = nullptr;         // [n_elem][dim+1]
+  int32_t* conn = nullptr;         // [n_elem][nb]: vertices first, then (P2) edge nodes
   uint8_t* elem_in_omega = nullptr;
   uint8_t* node_free = nullptr;
   double* evert = nullptr;         // [n_elem][dim+1][dim] vertex coordinates per element
@@ -145,7 +147,7 @@ struct nl_mesh {
                                    // (a = 1..dim), inverse Jacobian, volume, v_0 as hi + lo
   int32_t max_conn_deg = 0;
   int64_t* n2e_off = nullptr;      // [n_vert+1] node -> elements
-  int32_t* n2e = nullptr;          // [(dim+1) n_elem]
+  int32_t* n2e = nullptr;          // [nb n_elem]
   double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};
   double max_ext = 0.0;            // largest bounding-box side of an element
   size_t bytes = 0;
@@ -194,6 +196,10 @@ nl_status build_pairs(nl_mesh* m, double delta, double eps, nl_pairs* out);
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st);
+// The same for meshes of P2 triangles (nl_quad_p2.cu).
+nl_status assemble_values_p2(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                             const nl_quad_params* qp, nl_precision prec, double* values,
+                             nl_assemble_stats* st);
 // The same for NL_PREC_MIXED_TF32 / NL_PREC_MIXED_BF16 (nl_quad_mma.cu).
 nl_status assemble_values_mma(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                               const nl_quad_params* qp, nl_precision prec, double* values,

@@ -362,8 +362,9 @@ __global__ void k_row_bound(int64_t n_vert, const int64_t* __restrict__ n2e_off,
 // MODE 0: count the columns of row i; MODE 1: write them sorted into col at row_ptr[i];
 // MODE 2: count them and write them sorted into the staging rows tmp[i * rowcap ...] (one pass
 // instead of two; k_copy_rows then packs the staged rows once row_ptr is known).
+// conn holds nb nodes per element (the vertices, then a P2 element's edge nodes).
 template <int D, int MODE>
-__global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
+__global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn, int nb,
                        const int64_t* __restrict__ n2e_off, const int32_t* __restrict__ n2e,
                        const int64_t* __restrict__ pair_off, const int32_t* __restrict__ pair_l,
                        int eh, int nh, int32_t* __restrict__ row_cnt,
@@ -391,8 +392,8 @@ __global__ void k_rows(int64_t n_vert, const int32_t* __restrict__ conn,
   for (int s = threadIdx.x; s < eh; s += blockDim.x) {
     int32_t l = etab[s];
     if (l < 0) continue;
-    for (int c = 0; c <= D; c++)
-      if (hash_insert(ntab, nh - 1, conn[(int64_t)l * (D + 1) + c], &overflow)) atomicAdd(&ncount, 1);
+    for (int c = 0; c < nb; c++)
+      if (hash_insert(ntab, nh - 1, conn[(int64_t)l * nb + c], &overflow)) atomicAdd(&ncount, 1);
   }
   __syncthreads();
   if (overflow || ncount * 4 > nh * 3) {
@@ -562,7 +563,8 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   NL_CUDA(cudaMemcpyAsync(&max_sum, maxs.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));
   int eh = next_pow2(std::max<int64_t>(64, std::min<int64_t>(2 * max_sum, 32768)));
-  int nh = std::min(8192, eh);
+  // node table: a P2 element brings about four times the nodes of a P1 one into a row
+  int nh = std::min(8192, m->order == 2 ? 2 * eh : eh);
   size_t rsmem = sizeof(int32_t) * (eh + nh);
   NL_TRY((allow_smem(k_rows<D, 0>, rsmem)));
   NL_TRY((allow_smem(k_rows<D, 1>, rsmem)));
@@ -580,11 +582,11 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   DevBuf<int32_t> stage;
   if (staged) {
     NL_TRY(stage.alloc(stage_bytes / sizeof(int32_t), s));
-    k_rows<D, 2><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
+    k_rows<D, 2><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->nb, m->n2e_off, m->n2e, off.p, pl.p,
                                                        eh, nh, rcnt.p, nullptr, nullptr, err.p,
                                                        max_cnt.p + 1, stage.p, rowcap);
   } else {
-    k_rows<D, 0><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
+    k_rows<D, 0><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->nb, m->n2e_off, m->n2e, off.p, pl.p,
                                                        eh, nh, rcnt.p, nullptr, nullptr, err.p,
                                                        max_cnt.p + 1, nullptr, 0);
   }
@@ -608,7 +610,7 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   if (staged) {
     k_copy_rows<<<NL_CNT((unsigned)((nvv * 32 + 255) / 256)), 256, 0, s>>>(nvv, rowcap, stage.p, rp.p, col.p);
   } else {
-    k_rows<D, 1><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->n2e_off, m->n2e, off.p, pl.p,
+    k_rows<D, 1><<<NL_CNT((unsigned)nvv), 256, rsmem, s>>>(nvv, m->conn, m->nb, m->n2e_off, m->n2e, off.p, pl.p,
                                                        eh, nh, nullptr, rp.p, col.p, err.p, nullptr,
                                                        nullptr, 0);
   }

@@ -24,7 +24,9 @@ nl_status ensure_device_tables() {
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st) {
-  // the tensor-core variants are compiled in their own translation unit (nl_quad_mma.cu)
+  // P2 triangles (nl_quad_p2.cu; MIXED precisions run its FP32 path) and the tensor-core
+  // variants are compiled in translation units of their own (nl_quad_mma.cu)
+  if (m->order == 2) return assemble_values_p2(m, p, kp, qp, prec, values, st);
   if (prec == NL_PREC_MIXED_TF32 || prec == NL_PREC_MIXED_BF16)
     return assemble_values_mma(m, p, kp, qp, prec, values, st);
   return assemble_single<0>(m, p, kp, qp, prec, values, st);
@@ -61,7 +63,7 @@ nl_status noalloc_scratch(unsigned char** out) {
 template <int D, typename R, int KERN>
 nl_status run_noalloc(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s) {
   NL_TRY((launch_quad<D, R, KERN, true>(P, s)));
-  const size_t smem = scatter_smem_bytes(D, p->max_row_nnz, sizeof(R));
+  const size_t smem = scatter_smem_bytes(D + 1, p->max_row_nnz, sizeof(R));
   if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
   NL_TRY((allow_smem(k_scatter<D, R>, smem)));
@@ -82,6 +84,7 @@ nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                            const nl_quad_params* qp, nl_precision prec, double* values,
                            nl_assemble_stats* st) {
   if (!values) return fail(NL_EINVAL, "nl_assemble_noalloc: values is NULL");
+  if (m->order != 1) return fail(NL_EINVAL, "nl_assemble_noalloc: P1 meshes only; use nl_assemble");
   QParams P;
   NL_TRY(fill_qparams("nl_assemble_noalloc", m, p, kp, qp, prec, &P));
   const int D = m->dim;

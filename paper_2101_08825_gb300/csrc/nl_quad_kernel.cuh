@@ -1756,14 +1756,16 @@ __host__ __device__ inline int scatter_table_size(int max_row) {
   while (t < 2 * max_row) t <<= 1;
   return t;
 }
-__host__ __device__ inline size_t scatter_hash_bytes(int dim, int T, int64_t acc_entries,
+// nn: nodes per element (rows of the element's blocks)
+__host__ __device__ inline size_t scatter_hash_bytes(int nn, int T, int64_t acc_entries,
                                                      size_t acc_size) {
   size_t b = (size_t)T * 4;                               // keys
-  b += ((size_t)T * (dim + 1) * 2 + 7) & ~size_t(7);      // int16 positions per row
+  b += ((size_t)T * nn * 2 + 7) & ~size_t(7);             // int16 positions per row
   return b + (size_t)acc_entries * acc_size;              // accumulators
 }
 
-template <int D, typename R>
+// NN: nodes per element (D+1 for P1, 6 for P2 triangles); blocks are NN x NN.
+template <int D, typename R, int NN = D + 1>
 __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, int64_t p_base,
                                              bool with_self, const int32_t* __restrict__ pair_l,
                                              const int32_t* __restrict__ conn,
@@ -1772,7 +1774,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
                                              const R* __restrict__ blk,
                                              const double* __restrict__ selfblk,
                                              double* __restrict__ values, int* __restrict__ err) {
-  constexpr int NV = D + 1, NB = NV * NV;
+  constexpr int NV = NN, NB = NV * NV;
   extern __shared__ __align__(16) unsigned char sraw[];
   __shared__ int64_t rbeg[NV];
   __shared__ int rlen[NV], roff[NV + 1];
@@ -1799,7 +1801,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
   const int T = scatter_table_size(max_len);
   const int64_t n = (q1 > q0 ? q1 - q0 : 0);
-  if (scatter_hash_bytes(D, T, total, sizeof(R)) <= (size_t)dyn) {
+  if (scatter_hash_bytes(NV, T, total, sizeof(R)) <= (size_t)dyn) {
     int32_t* keys = reinterpret_cast<int32_t*>(sraw);
     int16_t* pos = reinterpret_cast<int16_t*>(keys + T);
     R* acc = reinterpret_cast<R*>(sraw + (((size_t)T * 4 + (size_t)T * NV * 2 + 7) & ~size_t(7)));
@@ -1932,14 +1934,14 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   }
 }
 
-// Dynamic shared memory of the scatter kernels for rows of up to max_row columns and blocks of
-// acc_size-byte values: the hash layout when it fits in 200 KB, else the cached column lists
+// Dynamic shared memory of the scatter kernels for elements of nn nodes, rows of up to max_row
+// columns and blocks of acc_size-byte values: the hash layout when it fits in 200 KB, else the cached column lists
 // plus FP64 accumulators when that fits, else the column lists only (0 if even those do not
 // fit).
-inline size_t scatter_smem_bytes(int dim, int max_row, size_t acc_size) {
-  const size_t total = (size_t)(dim + 1) * (size_t)std::max(1, max_row);
+inline size_t scatter_smem_bytes(int nn, int max_row, size_t acc_size) {
+  const size_t total = (size_t)nn * (size_t)std::max(1, max_row);
   const size_t hashed =
-      scatter_hash_bytes(dim, scatter_table_size(std::max(1, max_row)), (int64_t)total, acc_size);
+      scatter_hash_bytes(nn, scatter_table_size(std::max(1, max_row)), (int64_t)total, acc_size);
   if (hashed <= (size_t)200 * 1024) return hashed;
   const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
   if (with_acc <= (size_t)200 * 1024) return with_acc;
@@ -1949,7 +1951,7 @@ inline size_t scatter_smem_bytes(int dim, int max_row, size_t acc_size) {
 
 // Single problem: CTA b handles element m_begin + b; with_self = 0 adds the cross blocks of
 // the pairs in [p_begin, p_end), with_self = 1 only the self blocks.
-template <int D, typename R>
+template <int D, typename R, int NN = D + 1>
 __global__ void __launch_bounds__(128) k_scatter(int64_t m_begin, int64_t p_begin, int64_t p_end,
                                                  const int64_t* __restrict__ pair_off,
                                                  const int32_t* __restrict__ pair_l,
@@ -1965,7 +1967,7 @@ __global__ void __launch_bounds__(128) k_scatter(int64_t m_begin, int64_t p_begi
     q0 = max(pair_off[m], p_begin);
     q1 = min(pair_off[m + 1], p_end);
   }
-  scatter_elem<D, R>(m, q0, q1, p_begin, with_self != 0, pair_l, conn, row_ptr, col, blk, selfblk,
+  scatter_elem<D, R, NN>(m, q0, q1, p_begin, with_self != 0, pair_l, conn, row_ptr, col, blk, selfblk,
                      values, err);
 }
 
@@ -2008,7 +2010,7 @@ nl_status launch_quad(const QParams& P, cudaStream_t s, const QBatch& Bt = QBatc
   return NL_OK;
 }
 
-template <int D, typename R>
+template <int D, typename R, int NN = D + 1>
 nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end, const R* blk,
                          const double* selfblk, int with_self, double* values, int* err,
                          cudaStream_t s, const int64_t* h_pair_off) {
@@ -2022,11 +2024,11 @@ nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end
     m_end = std::min<int64_t>(m->n_elem, std::max(m_end, m_begin));
   }
   if (m_end <= m_begin) return NL_OK;
-  const size_t smem = scatter_smem_bytes(D, p->max_row_nnz, sizeof(R));
+  const size_t smem = scatter_smem_bytes(NN, p->max_row_nnz, sizeof(R));
   if (smem == 0)
     return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
-  NL_TRY((allow_smem(k_scatter<D, R>, smem)));
-  k_scatter<D, R><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
+  NL_TRY((allow_smem(k_scatter<D, R, NN>, smem)));
+  k_scatter<D, R, NN><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
       m_begin, p_begin, p_end, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, blk, selfblk,
       with_self, values, err);
   NL_CUDA(cudaGetLastError());

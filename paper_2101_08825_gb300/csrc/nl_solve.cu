@@ -32,7 +32,9 @@ enum : int {
 };
 constexpr int NPARTS = 2;  // dot products that one kernel can reduce
 
-template <int D>
+// F_i += int_E f phi_i per element of Omega with NB nodes (P1: D+1, P2 triangles: 6); B[q][a]
+// (row stride 8) is the element basis phi_a at rule point q.
+template <int NB>
 __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
                             const uint8_t* __restrict__ eio, const uint8_t* __restrict__ free_,
                             const double* __restrict__ vol, const double* __restrict__ fn,
@@ -40,20 +42,20 @@ __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
                             const double* __restrict__ W, int nq, double* __restrict__ F) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n_elem || !eio[e]) return;
-  int32_t nd[D + 1];
-  double fv[D + 1];
-  for (int a = 0; a <= D; a++) {
-    nd[a] = conn[e * (D + 1) + a];
+  int32_t nd[NB];
+  double fv[NB];
+  for (int a = 0; a < NB; a++) {
+    nd[a] = conn[e * NB + a];
     fv[a] = fn ? fn[nd[a]] : 0.0;
   }
-  double acc[D + 1];
-  for (int a = 0; a <= D; a++) acc[a] = 0.0;
+  double acc[NB];
+  for (int a = 0; a < NB; a++) acc[a] = 0.0;
   for (int q = 0; q < nq; q++) {
     double f = f_const;
-    for (int v = 0; v <= D; v++) f += B[q * 4 + v] * fv[v];
-    for (int a = 0; a <= D; a++) acc[a] += W[q] * f * B[q * 4 + a];
+    for (int v = 0; v < NB; v++) f += B[q * 8 + v] * fv[v];
+    for (int a = 0; a < NB; a++) acc[a] += W[q] * f * B[q * 8 + a];
   }
-  for (int a = 0; a <= D; a++)
+  for (int a = 0; a < NB; a++)
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], vol[e] * acc[a]);
 }
 
@@ -493,16 +495,27 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   cudaStream_t s = m->stream;
   const int D = m->dim;
   const Rule& r = rule(D);
-  std::vector<double> hB(16 * 4, 0.0), hW(16, 0.0);
+  // the element basis at the rule points: P1 the barycentric coordinates; P2 (triangles)
+  // lambda_a (2 lambda_a - 1) at the vertices and 4 lambda_a lambda_b at the edge nodes
+  // (0,1), (1,2), (0,2)
+  std::vector<double> hB(16 * 8, 0.0), hW(16, 0.0);
   for (int q = 0; q < r.n; q++) {
-    for (int a = 0; a <= D; a++) hB[q * 4 + a] = r.bary[q][a];
+    const double* lam = r.bary[q];
+    if (m->order == 2) {
+      for (int a = 0; a < 3; a++) hB[q * 8 + a] = lam[a] * (2.0 * lam[a] - 1.0);
+      hB[q * 8 + 3] = 4.0 * lam[0] * lam[1];
+      hB[q * 8 + 4] = 4.0 * lam[1] * lam[2];
+      hB[q * 8 + 5] = 4.0 * lam[0] * lam[2];
+    } else {
+      for (int a = 0; a <= D; a++) hB[q * 8 + a] = lam[a];
+    }
     hW[q] = r.w[q];
   }
   DevBuf<double> B, W, fn, g;
-  NL_TRY(B.alloc(64, s));
+  NL_TRY(B.alloc(128, s));
   NL_TRY(W.alloc(16, s));
   NL_TRY(g.alloc(m->n_vert, s));
-  NL_CUDA(cudaMemcpyAsync(B.p, hB.data(), sizeof(double) * 64, cudaMemcpyHostToDevice, s));
+  NL_CUDA(cudaMemcpyAsync(B.p, hB.data(), sizeof(double) * 128, cudaMemcpyHostToDevice, s));
   NL_CUDA(cudaMemcpyAsync(W.p, hW.data(), sizeof(double) * 16, cudaMemcpyHostToDevice, s));
   NL_CUDA(cudaMemcpyAsync(g.p, g_nodes, sizeof(double) * m->n_vert, cudaMemcpyHostToDevice, s));
   if (f_nodes) {
@@ -511,11 +524,14 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   }
   NL_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * m->n_vert, s));
   unsigned ge = (unsigned)((m->n_elem + RT - 1) / RT);
-  if (D == 2)
-    k_rhs_elems<2><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+  if (m->nb == 6)
+    k_rhs_elems<6><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->vol, fn.p, f_const, B.p, W.p, r.n, F);
+  else if (D == 2)
+    k_rhs_elems<3><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->vol, fn.p, f_const, B.p, W.p, r.n, F);
   else
-    k_rhs_elems<3><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+    k_rhs_elems<4><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->vol, fn.p, f_const, B.p, W.p, r.n, F);
   k_lift<<<NL_CNT((unsigned)((m->n_vert * 32 + RT - 1) / RT)), RT, 0, s>>>(
       m->n_vert, A->pairs->row_ptr, A->pairs->col, A->values, m->node_free, g.p, F);

@@ -85,9 +85,11 @@ def lib():
         "nl_version": (ctypes.c_char_p, []),
         "nl_launch_count": (i64, []),
         "nl_mesh_create": (st, [i, i64, p, i64, p, p, p, p, pp]),
+        "nl_mesh_create_p2": (st, [i, i64, p, i64, p, p, p, p, pp]),
         "nl_mesh_create_box": (st, [i, p, d, p, ctypes.c_int32, d, ctypes.c_uint64, p, pp]),
         "nl_mesh_info": (st, [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64)]),
+        "nl_mesh_order": (st, [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "nl_mesh_export": (st, [p, p, p, p, p]),
         "nl_mesh_destroy": (None, [p]),
         "nl_pairs_build": (st, [p, d, d, pp]),
@@ -198,14 +200,21 @@ class Mesh(_Handle):
         _check(lib().nl_mesh_info(self.h, ctypes.byref(dim), ctypes.byref(nv), ctypes.byref(ne)))
         return dim.value, nv.value, ne.value
 
+    def order(self):
+        """(polynomial order, nodes per element)."""
+        o, nb = ctypes.c_int(), ctypes.c_int()
+        _check(lib().nl_mesh_order(self.h, ctypes.byref(o), ctypes.byref(nb)))
+        return o.value, nb.value
+
     def export(self):
         dim, nv, ne = self.info()
+        nb = self.order()[1]
         coords = np.zeros(dim * nv)
-        conn = np.zeros(ne * (dim + 1), dtype=np.int32)
+        conn = np.zeros(ne * nb, dtype=np.int32)
         eio = np.zeros(ne, dtype=np.uint8)
         nf = np.zeros(nv, dtype=np.uint8)
         _check(lib().nl_mesh_export(self.h, _ptr(coords), _ptr(conn), _ptr(eio), _ptr(nf)))
-        return coords.reshape(dim, nv), conn.reshape(ne, dim + 1), eio, nf
+        return coords.reshape(dim, nv), conn.reshape(ne, nb), eio, nf
 
 
 class Pairs(_Handle):
@@ -276,8 +285,23 @@ def nl_mesh_create(dim, coords, conn, elem_in_omega, node_free, stream=None) -> 
     return Mesh(h)
 
 
+def nl_mesh_create_p2(dim, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
+    """Mesh of P2 triangles: conn rows (v0, v1, v2, m01, m12, m02)."""
+    coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(dim, -1)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 6)
+    eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
+    nf = np.ascontiguousarray(node_free, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib().nl_mesh_create_p2(dim, coords.shape[1], _ptr(coords), conn.shape[0], _ptr(conn),
+                                   _ptr(eio), _ptr(nf), stream if stream is not None else current_stream(),
+                                   ctypes.byref(h)), "nl_mesh_create_p2")
+    return Mesh(h)
+
+
 def mesh_from(mesh, stream=None) -> Mesh:
-    """Uploads an nl_inputs.Mesh."""
+    """Uploads an nl_inputs.Mesh (P1, or P2 triangles when conn has six columns)."""
+    if mesh.conn.shape[1] == 6:
+        return nl_mesh_create_p2(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
     return nl_mesh_create(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
 
 

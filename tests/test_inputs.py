@@ -84,3 +84,24 @@ def test_splitmix64_matches_its_published_sequence():
     u = splitmix64_unit(0, np.arange(3))
     for got, z in zip(u, (0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F)):
         assert got == (z >> 11) / 2.0 ** 53
+
+
+def test_p2_workload_mesh():
+    # the P2 workload: the c2_2d triangulation with one node per edge at its midpoint, so the
+    # nodes are the points of the grid of spacing h/2 over the meshed box ((2N+1)^2 of them,
+    # N cells per side), the free ones the (2n-1)^2 strictly inside Omega; every element's
+    # edge nodes sit at the midpoints of its edges (v0v1, v1v2, v0v2)
+    w = WORKLOADS["c2_2d_p2"]
+    m = workload_mesh(w)
+    n, N = w.cells[0], w.cells[0] + 2 * w.layer
+    assert m.conn.shape == (2 * N * N, 6)
+    assert m.n_vert == (2 * N + 1) ** 2
+    assert int(m.node_free.sum()) == (2 * n - 1) ** 2
+    x = m.coords
+    for j, (a, b) in enumerate(((0, 1), (1, 2), (0, 2))):
+        mid = (x[:, m.conn[:, a]] + x[:, m.conn[:, b]]) * 0.5
+        assert np.array_equal(x[:, m.conn[:, 3 + j]], mid)
+    # the vertices and the P1 mesh are those of c2_2d
+    p1 = workload_mesh(WORKLOADS["c2_2d"])
+    assert np.array_equal(m.conn[:, :3], p1.conn)
+    assert np.array_equal(x[:, :p1.n_vert], p1.coords)
