@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
   P2Mem<R> wm;
   wm.carve(smem_raw + p2_table_bytes<R>() + (size_t)wid * P2Mem<R>::bytes(P.scap), P.scap);
 
-  unsigned st_items = 0, st_exact = 0, st_eval = 0, st_band = 0;
+  unsigned st_items = 0, st_exact = 0, st_eval = 0, st_closed = 0, st_band = 0;
   int err = 0;
   int64_t cur_m = -1;
   // the box of m: FP64 global (exact decisions); R = float also in the local FP32 frame whose
@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
     for (int o = 16; o > 0; o >>= 1) {
       st_items += __shfl_xor_sync(FULL, st_items, o);
       st_exact += __shfl_xor_sync(FULL, st_exact, o);
+      st_closed += __shfl_xor_sync(FULL, st_closed, o);
       st_band += __shfl_xor_sync(FULL, st_band, o);
       err |= __shfl_xor_sync(FULL, err, o);
     }
@@ -167,10 +168,11 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
       if (st_items) atomicAdd(&P.stats[0], (unsigned long long)st_items);
       if (st_exact) atomicAdd(&P.stats[2], (unsigned long long)st_exact);
       if (st_eval) atomicAdd(&P.stats[3], (unsigned long long)st_eval);  // alike on every lane
+      if (st_closed) atomicAdd(&P.stats[4], (unsigned long long)st_closed);
       if (st_band) atomicAdd(&P.stats[5], (unsigned long long)st_band);
       if (err) atomicOr(P.err, err);
     }
-    st_items = st_exact = st_eval = st_band = 0;
+    st_items = st_exact = st_eval = st_closed = st_band = 0;
     err = 0;
     __syncwarp();
   };
@@ -298,7 +300,26 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
       for (int d = 0; d < P2_NN; d++)
 #pragma unroll
         for (int j = 0; j < 3; j++) Hq[d][j] = 0ull;
-      bool contrib = false;  // warp-uniform: set by the warp-collective integration
+      // whether anything was summed for this pair on this lane (a closed form) or by the warp
+      // (an integration): pairs with no contribution anywhere write a zero block
+      bool contrib = false;
+      // the largest distance from the centroid of E_l to its vertices, in the frame of y (the
+      // radius of a level-L sub-element is this times 2^(1-L): every midpoint child of a
+      // triangle is its parent scaled by 1/2)
+      R rad_l = 0;
+      if (KERN == NL_KERNEL_CONST) {
+        R ct[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++) ct[k] = (Vl[0][k] + Vl[1][k] + Vl[2][k]) * (R)(1.0 / 3.0);
+        R r2 = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const R d0 = Vl[a][0] - ct[0], d1 = Vl[a][1] - ct[1];
+          const R d2 = d0 * d0 + d1 * d1;
+          r2 = r2 > d2 ? r2 : d2;
+        }
+        rad_l = sqrt(r2);
+      }
 
       // Algorithm 1 decision for the sub-element with vertices V and path code `code`.
       // R = double: eqs. maxdist and mindist in FP64 on global coordinates.  R = float: the
@@ -335,6 +356,82 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
           if (amin < P.dpe) return ACT_REFINE;
           return ACT_DROP;
         }
+      };
+      // Closed forms (constant kernel).  On a sub-element E' whose point pairs all have mu
+      // exactly 1 (INT) or, per inner point y, all 1 or all 0 (FINAL, decided by the ball
+      // around E''s centroid), the outer sum at y is C sum_x w_x phi^l_d(x) = C |E'| times the
+      // mean of phi^l_d over E' (the degree-5 rule is exact for the quadratic phi^l_d), which
+      // the three edge midpoints give exactly (their rule is exact for quadratics).  Added to
+      // the inner points in `mask` by the lane that classified E'.
+      auto add_closed = [&](const R (&V)[3][2], int level, unsigned mask) {
+        R mean[P2_NN];
+#pragma unroll
+        for (int d = 0; d < P2_NN; d++) mean[d] = 0;
+#pragma unroll
+        for (int e = 0; e < 3; e++) {
+          const int a = e, b = e == 2 ? 0 : e + 1;
+          R dx[2];
+#pragma unroll
+          for (int k = 0; k < 2; k++)
+            dx[k] = (V[a][k] + V[b][k]) * (R)0.5 - (F32 ? (R)0 : (R)v0m[k]) - Vl0[k];
+          const R l1 = JI[0][0] * dx[0] + JI[0][1] * dx[1];
+          const R l2 = JI[1][0] * dx[0] + JI[1][1] * dx[1];
+          const R l0 = (R)1 - l1 - l2;
+          mean[0] += l0 * ((R)2 * l0 - (R)1);
+          mean[1] += l1 * ((R)2 * l1 - (R)1);
+          mean[2] += l2 * ((R)2 * l2 - (R)1);
+          mean[3] += (R)4 * l0 * l1;
+          mean[4] += (R)4 * l1 * l2;
+          mean[5] += (R)4 * l0 * l2;
+        }
+        const R wv = wl * pow2m(R(0), 2 * (level - 1)) * (R)(1.0 / 3.0);
+        if constexpr (F32) {
+#pragma unroll
+          for (int j = 0; j < 3; j++) {
+            const float w0 = (mask >> (2 * j)) & 1u ? wv : 0.f, w1 = (mask >> (2 * j + 1)) & 1u ? wv : 0.f;
+            const f2 W2 = f2pack(w0, w1);
+#pragma unroll
+            for (int d = 0; d < P2_NN; d++) Hq[d][j] = f2fma(W2, f2dup(mean[d]), Hq[d][j]);
+          }
+          const float w6 = (mask >> 6) & 1u ? wv : 0.f;
+#pragma unroll
+          for (int d = 0; d < P2_NN; d++) H[d][6] = fmaf(w6, mean[d], H[d][6]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < P2_NQ; i++) {
+            const R wi = (mask >> i) & 1u ? wv : (R)0;
+#pragma unroll
+            for (int d = 0; d < P2_NN; d++) H[d][i] += wi * mean[d];
+          }
+        }
+        st_closed++;
+        contrib = true;
+      };
+      // FINAL E' at `level`: for each inner point y, mu is exactly 1 at every point pair if
+      // |c - y| < delta - eps - rad - margin, exactly 0 if |c - y| > delta + eps + rad + margin
+      // (c the centroid, rad the radius of E').  Adds the closed form and returns true when
+      // every inner point is decided.
+      auto closed_final = [&](const R (&V)[3][2], int level) -> bool {
+        R cen[2];
+#pragma unroll
+        for (int k = 0; k < 2; k++)
+          cen[k] = (V[0][k] + V[1][k] + V[2][k]) * (R)(1.0 / 3.0) - (F32 ? (R)0 : (R)v0m[k]);
+        const R rad = rad_l * pow2m(R(0), level - 1);
+        const R lo = (R)P.fdme - rad - (R)P.margin, hi = (R)P.fdpe + rad + (R)P.margin;
+        const R lo2 = lo > 0 ? lo * lo : (R)-1, hi2 = hi * hi;
+        unsigned in_mask = 0;
+        bool decided = true;
+#pragma unroll
+        for (int i = 0; i < P2_NQ; i++) {
+          const R d0 = cen[0] - y[i][0], d1 = cen[1] - y[i][1];
+          const R d2 = d0 * d0 + d1 * d1;
+          const bool in = d2 < lo2, out = d2 > hi2;
+          in_mask |= in ? (1u << i) : 0u;
+          decided = decided && (in || out);
+        }
+        if (!decided) return false;
+        add_closed(V, level, in_mask);
+        return true;
       };
       auto put_item = [&](int slot, const R (&V)[3][2], int level, int fin) {
         R* it = wm.iv + slot * 6;
@@ -432,8 +529,12 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
       {
         int sp = 0, n_it = 0;
         const uint32_t code0 = 1u << LEVEL_SHIFT;
-        const int act0 = classify(Vl, code0, lane == 0);
+        int act0 = classify(Vl, code0, lane == 0);
         if (act0 == ACT_INT || act0 == ACT_FINAL || act0 == ACT_ZERO) st_items += (lane == 0);
+        if (KERN == NL_KERNEL_CONST && act0 == ACT_INT) {
+          if (lane == 0) add_closed(Vl, 1, 0x7fu);
+          act0 = ACT_DROP;
+        }
         if (act0 == ACT_INT || act0 == ACT_FINAL) {
           if (lane == 0) put_item(0, Vl, 1, act0 == ACT_FINAL);
           n_it = 1;
@@ -468,8 +569,16 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
             }
           }
           __syncwarp();  // parents are read before children overwrite their slots
-          const int act = active ? classify(V, code, true) : ACT_DROP;
+          int act = active ? classify(V, code, true) : ACT_DROP;
           if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
+          if (KERN == NL_KERNEL_CONST) {
+            if (act == ACT_INT) {
+              add_closed(V, code >> LEVEL_SHIFT, 0x7fu);
+              act = ACT_DROP;
+            } else if (act == ACT_FINAL && closed_final(V, code >> LEVEL_SHIFT)) {
+              act = ACT_DROP;
+            }
+          }
           const unsigned m_it = __ballot_sync(FULL, act == ACT_INT || act == ACT_FINAL);
           const unsigned m_ref = __ballot_sync(FULL, act == ACT_REFINE);
           const unsigned below = (1u << lane) - 1u;
@@ -488,7 +597,7 @@ __global__ void __launch_bounds__(P2_WARPS * 32, std::is_same<R, float>::value ?
 
       // ---- end of pair: sums over the lanes, cross block, self sums ---------------------------
       R* bp = reinterpret_cast<R*>(P.blk) + (p - P.p_begin) * P2_NBLK;
-      if (!contrib) {  // every sub-element dropped or beyond delta + eps
+      if (!__any_sync(FULL, contrib)) {  // every sub-element dropped or beyond delta + eps
         for (int e = lane; e < P2_NBLK; e += 32) bp[e] = (R)0;
         __syncwarp();
         continue;
@@ -657,7 +766,7 @@ nl_status assemble_values_p2(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp
     st->n_exact_checks = (int64_t)hs[3];
     st->ms_assemble = ms;
     st->n_eval_point_pairs = (int64_t)hs[4];
-    st->n_closed_items = 0;
+    st->n_closed_items = (int64_t)hs[5];
     st->n_band_point_pairs = P.count_band ? (int64_t)hs[6] : -1;
     st->precision_run = f32 ? NL_PREC_FP32 : NL_PREC_FP64;
     st->n_quad_launches = T.launches(0);

@@ -68,6 +68,13 @@ def test_p2_pairs_pattern_counts_and_values(case):
         assert st.n_point_pairs == ost.n_point_pairs, (name, prec)
         assert _rel(vals, ovals) < tol, (name, prec, _rel(vals, ovals))
         assert _maxrel(vals, ovals) < tol, (name, prec, _maxrel(vals, ovals))
+        # constant kernel: INT sub-elements and FINAL ones with mu in {0, 1} are summed in
+        # closed form (edge-midpoint means of the quadratic basis), the rest point by point
+        assert st.n_eval_point_pairs + 49 * st.n_closed_items <= st.n_point_pairs
+        if kernel == 0 and L_max > 1:
+            assert st.n_closed_items > 0, name
+        if kernel == 1:
+            assert st.n_closed_items == 0
 
 
 def test_p2_mesh_round_trip_and_validation():
