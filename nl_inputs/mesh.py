@@ -151,3 +151,49 @@ def p2_mesh(mesh: Mesh) -> Mesh:
     meta = dict(mesh.meta, order=2)
     return Mesh(dim=2, coords=coords, conn=np.ascontiguousarray(conn), elem_in_omega=mesh.elem_in_omega.copy(),
                 node_free=free.astype(np.uint8), h=mesh.h, meta=meta)
+
+
+def quad_mesh(mesh: Mesh) -> Mesh:
+    """The quadrilateral (Q1) mesh of the cells of a structured 2D mesh: the same vertices, one
+    element per cell with vertices (v00, v10, v11, v01) counterclockwise (the images of the
+    unit square's corners (0,0), (1,0), (1,1), (0,1)); a cell of Omega is an element of
+    Omega.  With jitter the cells are general convex quadrilaterals."""
+    if mesh.dim != 2 or mesh.conn.shape[1] != 3:
+        raise ValueError("quadrilateral meshes are built from structured P1 triangle meshes")
+    t = mesh.conn.reshape(-1, 2, 3)  # the two triangles (v00, v10, v11), (v00, v11, v01) per cell
+    conn = np.stack([t[:, 0, 0], t[:, 0, 1], t[:, 0, 2], t[:, 1, 2]], axis=1).astype(np.int32)
+    eio = mesh.elem_in_omega.reshape(-1, 2)[:, 0].copy()
+    return Mesh(dim=2, coords=mesh.coords.copy(), conn=np.ascontiguousarray(conn),
+                elem_in_omega=eio, node_free=mesh.node_free.copy(), h=mesh.h,
+                meta=dict(mesh.meta, cell="quad"))
+
+
+def q2_mesh(mesh: Mesh) -> Mesh:
+    """The Q2 (biquadratic Lagrange) mesh on the cells of a quadrilateral mesh: the vertices
+    (same numbers), one node per edge at its midpoint (a + b) * 0.5 (numbered after the
+    vertices in the lexicographic order of the edges' (smaller, larger) vertex pairs), then
+    one node per cell at the image of the unit square's centre ((v0 + v1) * 0.5 + (v2 + v3) *
+    0.5) * 0.5.  ``conn`` rows are (v0, v1, v2, v3, m01, m12, m23, m30, centre).  A node is a
+    degree of freedom when it lies strictly inside the open Omega."""
+    if mesh.dim != 2 or mesh.conn.shape[1] != 4:
+        raise ValueError("Q2 meshes are built from quadrilateral meshes")
+    c = mesh.conn.astype(np.int64)
+    edges = np.stack([c[:, [0, 1]], c[:, [1, 2]], c[:, [2, 3]], c[:, [3, 0]]], axis=1)
+    lo_hi = np.sort(edges, axis=2).reshape(-1, 2)
+    key = lo_hi[:, 0] * mesh.n_vert + lo_hi[:, 1]
+    ukey, inv = np.unique(key, return_inverse=True)
+    ea, eb = ukey // mesh.n_vert, ukey % mesh.n_vert
+    mid = (mesh.coords[:, ea] + mesh.coords[:, eb]) * 0.5
+    x = mesh.coords
+    cen = ((x[:, c[:, 0]] + x[:, c[:, 1]]) * 0.5 + (x[:, c[:, 2]] + x[:, c[:, 3]]) * 0.5) * 0.5
+    coords = np.concatenate([mesh.coords, mid, cen], axis=1)
+    edge_node = (mesh.n_vert + inv).reshape(-1, 4)
+    cen_node = mesh.n_vert + len(ukey) + np.arange(mesh.n_elem)
+    conn = np.concatenate([c, edge_node, cen_node[:, None]], axis=1).astype(np.int32)
+    lo = np.array(mesh.meta["lo"], dtype=np.float64)
+    hi = lo + np.array(mesh.meta["cells"], dtype=np.float64) * mesh.h
+    free = np.all((coords > lo[:, None]) & (coords < hi[:, None]), axis=0)
+    free[: mesh.n_vert] = mesh.node_free.astype(bool)
+    return Mesh(dim=2, coords=coords, conn=np.ascontiguousarray(conn),
+                elem_in_omega=mesh.elem_in_omega.copy(), node_free=free.astype(np.uint8),
+                h=mesh.h, meta=dict(mesh.meta, order=2))

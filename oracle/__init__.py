@@ -41,7 +41,7 @@ class _Mesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n_vert", ctypes.c_int64), ("n_elem", ctypes.c_int64),
                 ("coords", ctypes.c_void_p), ("conn", ctypes.c_void_p),
                 ("elem_in_omega", ctypes.c_void_p), ("node_free", ctypes.c_void_p),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("cell", ctypes.c_int)]
 
 
 class _Params(ctypes.Structure):
@@ -111,10 +111,14 @@ class OMesh:
         self.conn = np.ascontiguousarray(mesh.conn, dtype=np.int32)
         self.elem_in_omega = np.ascontiguousarray(mesh.elem_in_omega, dtype=np.uint8)
         self.node_free = np.ascontiguousarray(mesh.node_free, dtype=np.uint8)
-        self.order = 1 if self.conn.shape[1] == self.dim + 1 else 2
+        # nodes per element -> element kind: 2D 3 P1 / 6 P2 triangles, 4 Q1 / 9 Q2
+        # quadrilaterals; 3D 4 P1 tetrahedra
+        npe = self.conn.shape[1]
+        self.cell = 1 if (self.dim == 2 and npe in (4, 9)) else 0
+        self.order = 2 if npe in (6, 9) else 1
         self.c = _Mesh(self.dim, self.coords.shape[1], self.conn.shape[0], _ptr(self.coords).value,
                        _ptr(self.conn).value, _ptr(self.elem_in_omega).value,
-                       _ptr(self.node_free).value, self.order)
+                       _ptr(self.node_free).value, self.order, self.cell)
 
 
 def _om(mesh) -> OMesh:

@@ -387,7 +387,12 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
  * Mesh helpers. */
 /* Nodes per element: P1 simplices dim+1; P2 triangles 6 (the vertices, then the midpoints of
  * the edges (0,1), (1,2), (0,2)). */
-static int npe(const or_mesh* M) { return (M->order == 2) ? 6 : M->dim + 1; }
+static int npe(const or_mesh* M) {
+  if (M->cell == 1) return (M->order == 2) ? 9 : 4;
+  return (M->order == 2) ? 6 : M->dim + 1;
+}
+/* Vertices per element: simplices dim+1, quadrilaterals 4. */
+static int nverts(const or_mesh* M) { return (M->cell == 1) ? 4 : M->dim + 1; }
 
 /* The element's Lagrange basis at the point with barycentric coordinates lam: P1 the
  * barycentric coordinates; P2 (triangles) lam_a (2 lam_a - 1) at the vertices and
@@ -403,20 +408,21 @@ static void basis(const or_mesh* M, const double* lam, double* phi) {
   phi[5] = 4.0 * lam[0] * lam[2];
 }
 
-/* The vertices of element e (the first dim+1 of its nodes). */
+/* The vertices of element e (the first nverts of its nodes). */
 static void elem_verts(const or_mesh* M, int64_t e, double V[4][3]) {
-  int nv = M->dim + 1, nb = npe(M);
+  int nv = nverts(M), nb = npe(M);
   for (int a = 0; a < nv; a++) {
     int64_t v = M->conn[e * nb + a];
     for (int k = 0; k < 3; k++) V[a][k] = (k < M->dim) ? M->coords[k * M->n_vert + v] : 0.0;
   }
 }
 
-static void verts_bbox(int dim, const double V[4][3], double* lo, double* hi) {
+/* Box of the first nvx vertices of V. */
+static void verts_bbox(int dim, int nvx, const double V[4][3], double* lo, double* hi) {
   for (int k = 0; k < dim; k++) {
     lo[k] = V[0][k];
     hi[k] = V[0][k];
-    for (int a = 1; a <= dim; a++) {
+    for (int a = 1; a < nvx; a++) {
       if (V[a][k] < lo[k]) lo[k] = V[a][k];
       if (V[a][k] > hi[k]) hi[k] = V[a][k];
     }
@@ -522,7 +528,7 @@ int64_t or_pairs(const or_mesh* M, double delta, double eps, int64_t* pair_off, 
   for (int64_t e = 0; e < n; e++) {
     double V[4][3];
     elem_verts(M, e, V);
-    verts_bbox(dim, V, lo + 3 * e, hi + 3 * e);
+    verts_bbox(dim, nverts(M), V, lo + 3 * e, hi + 3 * e);
   }
   double reach = delta + eps;
   int64_t cnt = 0;
@@ -726,7 +732,7 @@ static void adaptive_integration(actx* c, int L_cur, const double E[4][3], const
   }
   int64_t nint = 0, nref = 0;
   double lo[3], hi[3];
-  verts_bbox(dim, E, lo, hi);
+  verts_bbox(dim, dim + 1, E, lo, hi);
   for (int64_t t = 0; t < nJ; t++) {
     int64_t m = J[t];
     double amin = (P->flags & OR_MINDIST_L2)
@@ -747,12 +753,210 @@ static void adaptive_integration(actx* c, int L_cur, const double E[4][3], const
   free(Jref);
 }
 
+/* ------------------------------------------------------------------------------------
+ * Quadrilateral elements (Sec. 6: the QUAD meshes, the Gauss-Legendre 3x3 product rule for
+ * both the inner and the outer integral).  An element is the image of the unit square
+ * under the bilinear map F(s,t) = (1-s)(1-t) v0 + s(1-t) v1 + s t v2 + (1-s) t v3.  A
+ * sub-element of Algorithm 1 is the image of a sub-square [s0, s0+len] x [t0, t0+len] of
+ * l's unit square; its physical vertices (for the box distances of Sec. 5.1) come from the
+ * parent's by midpoints, the centre as the midpoint of the midpoints of the edges (0,1) and
+ * (2,3). */
+typedef struct {
+  double V[4][3];      /* physical vertices */
+  double s0, t0, len;  /* the sub-square of l's unit square */
+} qsub;
+
+/* 1D Lagrange basis of degree 1 or 2 at s (nodes 0, 1 or 0, 1/2, 1). */
+static void lagrange1d(int order, double s, double* L) {
+  if (order == 2) {
+    L[0] = 2.0 * (s - 0.5) * (s - 1.0);
+    L[1] = 4.0 * s * (1.0 - s);
+    L[2] = 2.0 * s * (s - 0.5);
+  } else {
+    L[0] = 1.0 - s;
+    L[1] = s;
+  }
+}
+
+/* Q1 / Q2 basis at (s, t), nodes in the mesh's order: Q1 the vertices (0,0), (1,0), (1,1),
+ * (0,1); Q2 the vertices, the midpoints of the edges (0,1), (1,2), (2,3), (3,0), the centre. */
+static void quad_basis(int order, double s, double t, double* phi) {
+  double Ls[3], Lt[3];
+  lagrange1d(order, s, Ls);
+  lagrange1d(order, t, Lt);
+  if (order != 2) {
+    phi[0] = Ls[0] * Lt[0];
+    phi[1] = Ls[1] * Lt[0];
+    phi[2] = Ls[1] * Lt[1];
+    phi[3] = Ls[0] * Lt[1];
+    return;
+  }
+  static const int ij[9][2] = {{0, 0}, {2, 0}, {2, 2}, {0, 2}, {1, 0}, {2, 1}, {1, 2}, {0, 1}, {1, 1}};
+  for (int a = 0; a < 9; a++) phi[a] = Ls[ij[a][0]] * Lt[ij[a][1]];
+}
+
+/* x = F(s,t) for the quadrilateral V and |det DF(s,t)|. */
+static void quad_map(const double V[4][3], double s, double t, double* x, double* detJ) {
+  double N[4] = {(1.0 - s) * (1.0 - t), s * (1.0 - t), s * t, (1.0 - s) * t};
+  double xs[2], xt[2];
+  for (int k = 0; k < 3; k++) x[k] = N[0] * V[0][k] + N[1] * V[1][k] + N[2] * V[2][k] + N[3] * V[3][k];
+  for (int k = 0; k < 2; k++) {
+    xs[k] = (1.0 - t) * (V[1][k] - V[0][k]) + t * (V[2][k] - V[3][k]);
+    xt[k] = (1.0 - s) * (V[3][k] - V[0][k]) + s * (V[2][k] - V[1][k]);
+  }
+  *detJ = fabs(xs[0] * xt[1] - xs[1] * xt[0]);
+}
+
+/* Gauss-Legendre 3x3 on the unit square: points (g[i], g[j]), weights gw[i] gw[j]. */
+static void gl3_unit(double* g, double* gw) {
+  double x[3], w[3];
+  or_gauss_legendre(3, x, w);
+  for (int i = 0; i < 3; i++) {
+    g[i] = 0.5 * (x[i] + 1.0);
+    gw[i] = 0.5 * w[i];
+  }
+}
+
+/* The four children of a quadrilateral sub-element (Sec. 5, midpoint refinement). */
+static void quad_split(const qsub* E, qsub C[4]) {
+  double m01[3], m12[3], m23[3], m30[3], ce[3];
+  midpoint(E->V[0], E->V[1], m01);
+  midpoint(E->V[1], E->V[2], m12);
+  midpoint(E->V[2], E->V[3], m23);
+  midpoint(E->V[3], E->V[0], m30);
+  midpoint(m01, m23, ce);
+  const double* ch[4][4] = {{E->V[0], m01, ce, m30}, {m01, E->V[1], m12, ce},
+                            {ce, m12, E->V[2], m23}, {m30, ce, m23, E->V[3]}};
+  const double h = 0.5 * E->len;
+  const double org[4][2] = {{0.0, 0.0}, {h, 0.0}, {h, h}, {0.0, h}};
+  for (int c = 0; c < 4; c++) {
+    for (int a = 0; a < 4; a++)
+      for (int k = 0; k < 3; k++) C[c].V[a][k] = ch[c][a][k];
+    C[c].s0 = E->s0 + org[c][0];
+    C[c].t0 = E->t0 + org[c][1];
+    C[c].len = h;
+  }
+}
+
+/* Integration(E', J') on a quadrilateral sub-element: the sums of integration() with the
+ * outer points x = F_l(s0 + len g_i, t0 + len g_j), weights w_i w_j len^2 |det DF_l|, the
+ * basis of l at those reference points, and the inner points y = F_m(g_i, g_j) with weights
+ * w_i w_j |det DF_m| and the basis of m there. */
+static void integration_quad(actx* c, const qsub* E, const int32_t* J, int64_t nJ) {
+  const or_params* P = c->P;
+  int nb = c->nb, order = c->M->order;
+  double g[3], gw[3];
+  gl3_unit(g, gw);
+  double xq[9][3], wx[9], phil[9][9], phim[9][9], gq[9][2], gwq[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      int q = 3 * i + j;
+      gq[q][0] = g[i];
+      gq[q][1] = g[j];
+      gwq[q] = gw[i] * gw[j];
+      double s = E->s0 + E->len * g[i], t = E->t0 + E->len * g[j], det;
+      quad_map(c->Vl, s, t, xq[q], &det);
+      wx[q] = gwq[q] * E->len * E->len * det;
+      quad_basis(order, s, t, phil[q]);
+      quad_basis(order, g[i], g[j], phim[q]);
+    }
+  for (int64_t tt = 0; tt < nJ; tt++) {
+    int64_t m = J[tt];
+    double Vm[4][3];
+    elem_verts(c->M, m, Vm);
+    double S[9][9] = {{0}}, X[9][9] = {{0}};
+    for (int q = 0; q < 9; q++) {
+      for (int p = 0; p < 9; p++) {
+        double y[3], detm;
+        quad_map(Vm, gq[p][0], gq[p][1], y, &detm);
+        double wy = gwq[p] * detm;
+        double r2 = 0.0;
+        for (int k = 0; k < 2; k++) r2 += (xq[q][k] - y[k]) * (xq[q][k] - y[k]);
+        double r = sqrt(r2);
+        double G = wx[q] * wy * P->C * or_eta(P->kernel, r, P->delta) * or_mu(r, P->delta, P->eps);
+        c->st->n_point_pairs++;
+        if (r >= P->delta - P->eps && r <= P->delta + P->eps) c->st->n_band_pairs++;
+        for (int a = 0; a < nb; a++) {
+          double phia = phim[p][a];
+          for (int b = 0; b < nb; b++) S[a][b] += G * phia * phim[p][b];
+          for (int d = 0; d < nb; d++) X[a][d] += G * phia * phil[q][d];
+        }
+      }
+    }
+    c->st->n_integrations++;
+    for (int a = 0; a < nb; a++) {
+      int64_t i = c->M->conn[m * nb + a];
+      for (int b = 0; b < nb; b++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * nb + b]);
+        if (!e) {
+          c->error = 1;
+          continue;
+        }
+        *e += 2.0 * S[a][b];
+      }
+      for (int d = 0; d < nb; d++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * nb + d]);
+        if (!e) {
+          c->error = 1;
+          continue;
+        }
+        *e -= 2.0 * X[a][d];
+      }
+    }
+  }
+}
+
+/* Algorithm 1 on a quadrilateral sub-element (the three branches of adaptive_integration). */
+static void adaptive_integration_quad(actx* c, int L_cur, const qsub* E, const int32_t* J,
+                                      int64_t nJ) {
+  const or_params* P = c->P;
+  if (L_cur < P->L_min) {
+    qsub C[4];
+    quad_split(E, C);
+    for (int i = 0; i < 4; i++) adaptive_integration_quad(c, L_cur + 1, &C[i], J, nJ);
+    return;
+  }
+  if (L_cur == P->L_max) {
+    integration_quad(c, E, J, nJ);
+    return;
+  }
+  int32_t* Jint = (int32_t*)malloc(sizeof(int32_t) * (nJ + 1));
+  int32_t* Jref = (int32_t*)malloc(sizeof(int32_t) * (nJ + 1));
+  if (!Jint || !Jref) {
+    free(Jint), free(Jref);
+    c->error = 1;
+    return;
+  }
+  int64_t nint = 0, nref = 0;
+  double lo[3], hi[3];
+  verts_bbox(2, 4, E->V, lo, hi);
+  for (int64_t t = 0; t < nJ; t++) {
+    int64_t m = J[t];
+    double amin = (P->flags & OR_MINDIST_L2)
+                      ? or_aprx_min_dist_l2(2, lo, hi, c->lo + 3 * m, c->hi + 3 * m)
+                      : or_aprx_min_dist(2, lo, hi, c->lo + 3 * m, c->hi + 3 * m);
+    if (or_aprx_max_dist(2, lo, hi, c->lo + 3 * m, c->hi + 3 * m) < P->delta - P->eps)
+      Jint[nint++] = (int32_t)m;
+    else if (amin < P->delta + P->eps)
+      Jref[nref++] = (int32_t)m;
+  }
+  if (nint > 0) integration_quad(c, E, Jint, nint);
+  if (nref > 0) {
+    qsub C[4];
+    quad_split(E, C);
+    for (int i = 0; i < 4; i++) adaptive_integration_quad(c, L_cur + 1, &C[i], Jref, nref);
+  }
+  free(Jint);
+  free(Jref);
+}
+
 int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l,
                 const or_params* P, const int64_t* row_ptr, const int32_t* col, double* values,
                 const uint8_t* m_mask, or_stats* stats) {
   int dim = M->dim, nv = dim + 1;
   int64_t nE = M->n_elem, nV = M->n_vert;
   if (dim != 2 && dim != 3) return -1;
+  if (M->cell == 1 && dim != 2) return -1; /* quadrilaterals: dim 2 */
   if (!(P->eps > 0.0 && P->eps < P->delta) || P->L_min < 1 || P->L_max < P->L_min) return -1;
   actx c;
   memset(&c, 0, sizeof c);
@@ -783,7 +987,7 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
   for (int64_t e = 0; e < nE; e++) {
     double V[4][3];
     elem_verts(M, e, V);
-    verts_bbox(dim, V, lo + 3 * e, hi + 3 * e);
+    verts_bbox(dim, nverts(M), V, lo + 3 * e, hi + 3 * e);
   }
   for (int64_t m = 0; m < nE; m++) {
     if (m_mask && !m_mask[m]) continue;
@@ -809,7 +1013,16 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
     if (nJ == 0) continue;
     c.l = l;
     elem_verts(M, l, c.Vl);
-    adaptive_integration(&c, 1, c.Vl, tm + toff[l], nJ);
+    if (M->cell == 1) {
+      qsub root;
+      memcpy(root.V, c.Vl, sizeof root.V);
+      root.s0 = 0.0;
+      root.t0 = 0.0;
+      root.len = 1.0;
+      adaptive_integration_quad(&c, 1, &root, tm + toff[l], nJ);
+    } else {
+      adaptive_integration(&c, 1, c.Vl, tm + toff[l], nJ);
+    }
   }
   if (stats) *stats = local;
   free(lo), free(hi), free(toff), free(fillp), free(tm);
@@ -869,6 +1082,22 @@ int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const d
     if (!M->elem_in_omega[e]) continue;
     double V[4][3];
     elem_verts(M, e, V);
+    if (M->cell == 1) { /* Gauss-Legendre 3x3 on the image of the unit square */
+      double g[3], gw[3];
+      gl3_unit(g, gw);
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+          double x[3], det, phi[9];
+          quad_map(V, g[i], g[j], x, &det);
+          double f = or_ms_f(ms, dim, x, kernel, delta, eps, C);
+          quad_basis(M->order, g[i], g[j], phi);
+          for (int a = 0; a < nb; a++) {
+            int64_t n = M->conn[e * nb + a];
+            if (M->node_free[n]) F[n] += gw[i] * gw[j] * det * f * phi[a];
+          }
+        }
+      continue;
+    }
     double vol = simplex_volume(dim, V);
     for (int q = 0; q < nq; q++) {
       double x[3];
@@ -969,6 +1198,26 @@ static double err_on(const or_mesh* M, const double V[4][3], const double* nodal
   return s;
 }
 
+/* The same on a quadrilateral: Gauss-Legendre 3x3 on each of the 4 x 4 sub-squares of the
+ * unit square, mapped by the element's bilinear map. */
+static double err_on_quad(const or_mesh* M, const double V[4][3], const double* nodal, int ms) {
+  double g[3], gw[3], s = 0.0;
+  gl3_unit(g, gw);
+  for (int bi = 0; bi < 4; bi++)
+    for (int bj = 0; bj < 4; bj++)
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+          double u = 0.25 * (bi + g[i]), v = 0.25 * (bj + g[j]), x[3], det, phi[9];
+          quad_map(V, u, v, x, &det);
+          quad_basis(M->order, u, v, phi);
+          double uh = 0.0;
+          for (int a = 0; a < npe(M); a++) uh += phi[a] * nodal[a];
+          double d = or_ms_u(ms, M->dim, x) - uh;
+          s += 0.0625 * gw[i] * gw[j] * det * d * d;
+        }
+  return s;
+}
+
 double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) {
   int dim = M->dim, nv = dim + 1;
   double b[64], w[16], bary[16][4];
@@ -979,10 +1228,11 @@ double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) 
   double s = 0.0;
   for (int64_t e = 0; e < M->n_elem; e++) {
     if (omega_only && !M->elem_in_omega[e]) continue;
-    double V[4][3], nodal[6];
+    double V[4][3], nodal[9];
     elem_verts(M, e, V);
     for (int a = 0; a < npe(M); a++) nodal[a] = u_h[M->conn[e * npe(M) + a]];
-    s += err_on(M, V, nodal, (const double(*)[4])bary, w, nq, ms, V, 2);
+    if (M->cell == 1) s += err_on_quad(M, V, nodal, ms);
+    else s += err_on(M, V, nodal, (const double(*)[4])bary, w, nq, ms, V, 2);
   }
   return sqrt(s);
 }

@@ -9,7 +9,8 @@
  *
  * Conventions
  *   coords : SoA, coords[k*n_vert + v] = k-th coordinate of vertex v (k < dim)
- *   conn   : element-major, conn[e*(dim+1) + a] = a-th vertex of element e (P1)
+ *   conn   : element-major, conn[e*npe + a] = a-th node of element e (npe nodes per
+ *            element: P1 simplices dim+1, P2 triangles 6, quadrilaterals 4 (Q1) or 9 (Q2))
  *   pairs  : m-major lists, pair_off[m]..pair_off[m+1] index pair_l, l ascending
  *   CSR    : row_ptr[n_vert+1] (int64), col (int32), columns sorted ascending
  */
@@ -37,6 +38,12 @@ typedef struct {
   const uint8_t* node_free;     /* 1 = degree of freedom (node inside open Omega) */
   int order;                    /* 1 (or 0): P1; 2: P2 Lagrange triangles (vertices, then the
                                    midpoints of the edges (0,1), (1,2), (0,2)) */
+  int cell;                     /* 0: simplices; 1: quadrilaterals (dim 2), vertices v0..v3
+                                   counterclockwise, the images of the unit square's corners
+                                   (0,0), (1,0), (1,1), (0,1) under the bilinear map; order 1:
+                                   Q1 (the four vertices), order 2: Q2 (the vertices, the
+                                   midpoints of the edges (0,1), (1,2), (2,3), (3,0), then the
+                                   image of the square's centre) */
 } or_mesh;
 
 /* or_params.flags: the refinement test of Algorithm 1 uses the Euclidean variant of the
