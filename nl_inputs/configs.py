@@ -10,7 +10,7 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, replace
 
-from .mesh import Mesh, p2_mesh, structured_mesh
+from .mesh import Mesh, p2_mesh, q2_mesh, quad_mesh, structured_mesh
 
 KERNEL_CONST = 0
 KERNEL_GAUSS = 1
@@ -38,6 +38,7 @@ class Workload:
     seed: int = 0
     layer_cells: int = 0  # 0: ceil((delta + eps)/h); otherwise the given number of cells
     order: int = 1        # 1: P1 elements; 2: P2 triangles on the same triangulation
+    cell: str = "simplex"  # "quad": one quadrilateral per grid cell (2D; Q1, or Q2 with order 2)
 
     @property
     def layer(self) -> int:
@@ -93,9 +94,16 @@ WORKLOADS = {
     # the c2_2d_h128 triangulation with P2 elements: a small case for profiler captures
     "c2_2d_h128_p2": _unit_box("c2_2d_h128_p2", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1,
                                order=2),
+    # the c2_2d grid with one Q1 quadrilateral per cell (Sec. 6, QUAD meshes)
+    "c2_2d_q1": _unit_box("c2_2d_q1", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1, cell="quad"),
+    "c2_2d_h128_q1": _unit_box("c2_2d_h128_q1", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1,
+                               cell="quad"),
 }
 
 
 def workload_mesh(w: Workload) -> Mesh:
     m = structured_mesh(w.dim, w.cells, w.h, w.lo, w.layer, jitter=w.jitter, seed=w.seed)
+    if w.cell == "quad":
+        q = quad_mesh(m)
+        return q2_mesh(q) if w.order == 2 else q
     return p2_mesh(m) if w.order == 2 else m

@@ -276,7 +276,7 @@ nl_status nl_plan_create(int n, nl_mesh* const* meshes, nl_pairs* const* pairs,
     if (!meshes[k] || !pairs[k]) return fail(NL_EINVAL, "nl_plan_create: problem %d has a NULL mesh or pairs", k);
     if (meshes[k]->dim != D) return fail(NL_EINVAL, "nl_plan_create: problem %d is %dD, problem 0 is %dD", k, meshes[k]->dim, D);
     if (pairs[k]->mesh != meshes[k]) return fail(NL_EINVAL, "nl_plan_create: problem %d: pairs of another mesh", k);
-    if (meshes[k]->order != 1)
+    if (meshes[k]->order != 1 || meshes[k]->cell != 0)
       return fail(NL_EINVAL, "nl_plan_create: problem %d: plans take P1 meshes only (use nl_assemble)", k);
     if (kps[k].delta != pairs[k]->delta || kps[k].eps != pairs[k]->eps)
       return fail(NL_EINVAL, "nl_plan_create: problem %d: delta/eps differ from those of its pairs", k);

@@ -188,6 +188,23 @@ const Rule& rule(int dim) {
   return dim == 2 ? tri : tet;
 }
 
+// Gauss-Legendre with 3 points on [0, 1]: the roots of the Legendre polynomial P_3,
+// 0 and +-sqrt(3/5) on [-1, 1], with weights 8/9 and 5/9, mapped by s = (x + 1)/2.
+const GL3& gl3() {
+  static const GL3 r = [] {
+    GL3 t;
+    const double a = std::sqrt(0.6);
+    t.g[0] = 0.5 * (1.0 - a);
+    t.g[1] = 0.5;
+    t.g[2] = 0.5 * (1.0 + a);
+    t.w[0] = 5.0 / 18.0;
+    t.w[1] = 8.0 / 18.0;
+    t.w[2] = 5.0 / 18.0;
+    return t;
+  }();
+  return r;
+}
+
 // ---- kernel constants ------------------------------------------------------------------------
 static double xi_host(double s) {
   double t = s * s;
@@ -337,6 +354,52 @@ __global__ void k_mesh_elements(int64_t n_elem, int64_t n_vert, const double* __
   }
 }
 
+// Quadrilaterals (the bilinear image of the unit square, vertices v0..v3 counterclockwise,
+// the first four of an element's nb nodes): the four vertices, the box, the area
+// |(v2 - v0) x (v3 - v1)| / 2, no inverse Jacobian (zeros), and an FP32 record with the
+// offsets v_a - v_0 (a = 1..3) at [0, 6), the area at [8] and v_0 as a float-float pair at
+// the positions of the P1 record.
+__global__ void k_mesh_quads(int64_t n_elem, int64_t n_vert, const double* __restrict__ coords,
+                             const int32_t* __restrict__ conn, int nb, double* __restrict__ evert,
+                             double* __restrict__ blo, double* __restrict__ bhi,
+                             double* __restrict__ vol, double* __restrict__ jinv,
+                             float* __restrict__ ef) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  double V[4][2];
+  for (int a = 0; a < 4; a++) {
+    int32_t v = conn[e * nb + a];
+    for (int k = 0; k < 2; k++) {
+      V[a][k] = coords[k * n_vert + v];
+      evert[(e * 4 + a) * 2 + k] = V[a][k];
+    }
+  }
+  for (int k = 0; k < 2; k++) {
+    double lo = V[0][k], hi = V[0][k];
+    for (int a = 1; a < 4; a++) {
+      lo = fmin(lo, V[a][k]);
+      hi = fmax(hi, V[a][k]);
+    }
+    blo[e * 2 + k] = lo;
+    bhi[e * 2 + k] = hi;
+  }
+  const double d1x = V[2][0] - V[0][0], d1y = V[2][1] - V[0][1];
+  const double d2x = V[3][0] - V[1][0], d2y = V[3][1] - V[1][1];
+  vol[e] = fabs(d1x * d2y - d1y * d2x) / 2.0;
+  for (int t = 0; t < 4; t++) jinv[e * 4 + t] = 0.0;
+  float* f = ef + e * NL_EF_STRIDE(2);
+  for (int a = 1; a < 4; a++)
+    for (int k = 0; k < 2; k++) f[(a - 1) * 2 + k] = (float)(V[a][k] - V[0][k]);
+  f[6] = f[7] = 0.f;
+  f[8] = (float)vol[e];
+  for (int t = 9; t < NL_EF_STRIDE(2); t++) f[t] = 0.f;
+  for (int k = 0; k < 2; k++) {
+    const float hi = (float)V[0][k];
+    f[NL_EF_V0HI(2) + k] = hi;
+    f[NL_EF_V0LO(2) + k] = (float)(V[0][k] - (double)hi);
+  }
+}
+
 __global__ void k_count_n2e(int64_t n_entries, const int32_t* __restrict__ conn,
                             int32_t* __restrict__ cnt) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -375,22 +438,27 @@ void nlx::mesh_release(nl_mesh* m) {
   delete m;
 }
 
-// order 1: P1 simplices (dim+1 nodes per element); order 2: P2 triangles (6 nodes: the
-// vertices, then the midpoints of the edges (0,1), (1,2), (0,2)).
-static nl_status mesh_create_impl(int dim, int order, int64_t n_vert, const double* coords,
-                                  int64_t n_elem, const int32_t* conn, const uint8_t* eio,
-                                  const uint8_t* nf, void* cuda_stream, nl_mesh** out) {
+// cell 0, order 1: P1 simplices (dim+1 nodes per element); cell 0, order 2: P2 triangles (6
+// nodes: the vertices, then the midpoints of the edges (0,1), (1,2), (0,2)); cell 1:
+// quadrilaterals (dim 2), order 1 Q1 (the 4 vertices, counterclockwise), order 2 Q2 (the
+// vertices, the midpoints of the edges (0,1), (1,2), (2,3), (3,0), the centre).
+static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
+                                  const double* coords, int64_t n_elem, const int32_t* conn,
+                                  const uint8_t* eio, const uint8_t* nf, void* cuda_stream,
+                                  nl_mesh** out) {
   using namespace nlx;
   if (!out) return fail(NL_EINVAL, "nl_mesh_create: out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create: dim must be 2 or 3");
   if (order != 1 && !(order == 2 && dim == 2))
     return fail(NL_EINVAL, "nl_mesh_create: P2 elements are triangles (dim 2) only");
+  if (cell == 1 && dim != 2) return fail(NL_EINVAL, "nl_mesh_create_quad: quadrilaterals are 2D");
   if (n_vert <= 0 || n_vert > INT32_MAX || n_elem <= 0 || n_elem > INT32_MAX)
     return fail(NL_EINVAL, "nl_mesh_create: bad sizes n_vert=%lld n_elem=%lld",
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
-  const int nv = dim + 1, nb = order == 2 ? 6 : nv;
+  const int nv = cell == 1 ? 4 : dim + 1;
+  const int nb = cell == 1 ? (order == 2 ? 9 : 4) : (order == 2 ? 6 : nv);
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
     if (!std::isfinite(coords[i])) return fail(NL_EINVAL, "nl_mesh_create: non-finite coordinate");
   double bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -403,7 +471,37 @@ static nl_status mesh_create_impl(int dim, int order, int64_t n_vert, const doub
       if (a < nv)
         for (int k = 0; k < dim; k++) V[a][k] = coords[k * n_vert + v];
     }
-    if (order == 2) {
+    if (cell == 1) {
+      // a convex, counterclockwise quadrilateral: the cross product at every corner is
+      // positive (the bilinear map's Jacobian is then positive everywhere)
+      for (int a = 0; a < 4; a++) {
+        const double* p = V[a];
+        const double* q = V[(a + 1) & 3];
+        const double* r = V[(a + 3) & 3];
+        const double cr = (q[0] - p[0]) * (r[1] - p[1]) - (q[1] - p[1]) * (r[0] - p[0]);
+        if (!(cr > 0.0))
+          return fail(NL_EINVAL, "nl_mesh_create_quad: element %lld is not a convex counterclockwise quadrilateral",
+                      (long long)e);
+      }
+      if (order == 2) {
+        // Q2: edge node 4 + j at the midpoint of edge j = (0,1), (1,2), (2,3), (3,0), node 8 at
+        // the image of the square's centre, the mean of the four vertices
+        for (int j = 0; j < 5; j++) {
+          const int32_t v = conn[e * nb + 4 + j];
+          double d2 = 0.0, l2 = 0.0;
+          for (int k = 0; k < 2; k++) {
+            const double mid = j < 4 ? (V[j][k] + V[(j + 1) & 3][k]) * 0.5
+                                     : (V[0][k] + V[1][k] + V[2][k] + V[3][k]) * 0.25;
+            const double d = coords[k * n_vert + v] - mid, ed = V[2][k] - V[0][k];
+            d2 += d * d;
+            l2 += ed * ed;
+          }
+          if (!(d2 <= 1e-18 * l2))
+            return fail(NL_EINVAL, "nl_mesh_create_quad: node %d of element %lld is off its position",
+                        4 + j, (long long)e);
+        }
+      }
+    } else if (order == 2) {
       // straight-sided P2: edge node 3 + j at the midpoint of edge j = (0,1), (1,2), (0,2)
       static const int ea[3] = {0, 1, 0}, eb[3] = {1, 2, 2};
       for (int j = 0; j < 3; j++) {
@@ -450,6 +548,7 @@ static nl_status mesh_create_impl(int dim, int order, int64_t n_vert, const doub
   nl_mesh* m = new nl_mesh();
   m->dim = dim;
   m->order = order;
+  m->cell = cell;
   m->nb = nb;
   m->n_vert = n_vert;
   m->n_elem = n_elem;
@@ -470,7 +569,7 @@ static nl_status mesh_create_impl(int dim, int order, int64_t n_vert, const doub
     if ((st = dconn.alloc(nb * n_elem, s)) != NL_OK) break;
     if ((st = deio.alloc(n_elem, s)) != NL_OK) break;
     if ((st = dnf.alloc(n_vert, s)) != NL_OK) break;
-    if ((st = ev.alloc(nv * dim * n_elem, s)) != NL_OK) break;
+    if ((st = ev.alloc((int64_t)nv * dim * n_elem, s)) != NL_OK) break;
     if ((st = lo.alloc(dim * n_elem, s)) != NL_OK) break;
     if ((st = hi.alloc(dim * n_elem, s)) != NL_OK) break;
     if ((st = vol.alloc(n_elem, s)) != NL_OK) break;
@@ -497,7 +596,9 @@ static nl_status mesh_create_impl(int dim, int order, int64_t n_vert, const doub
     return cleanup(cuda_fail(ce, "nl_mesh_create upload"));
   int tb = 256;
   int64_t gb = (n_elem + tb - 1) / tb;
-  if (dim == 2)
+  if (cell == 1)
+    k_mesh_quads<<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
+  else if (dim == 2)
     k_mesh_elements<2><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   else
     k_mesh_elements<3><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
@@ -610,7 +711,7 @@ extern "C" nl_status nl_mesh_create_box(int dim, const int32_t* cells, double h,
       }
     }
   }
-  return mesh_create_impl(dim, 1, n_vert, coords.data(), n_elem, conn.data(), eio.data(), nf.data(),
+  return mesh_create_impl(dim, 1, 0, n_vert, coords.data(), n_elem, conn.data(), eio.data(), nf.data(),
                           cuda_stream, out);
 }
 
@@ -637,7 +738,7 @@ nl_status nl_mesh_create(int dim, int64_t n_vert, const double* coords, int64_t 
                          const int32_t* conn, const uint8_t* elem_in_omega,
                          const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
-  return mesh_create_impl(dim, 1, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+  return mesh_create_impl(dim, 1, 0, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
 }
 
@@ -645,7 +746,16 @@ nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64
                             const int32_t* conn, const uint8_t* elem_in_omega,
                             const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
-  return mesh_create_impl(dim, 2, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+  return mesh_create_impl(dim, 2, 0, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+                          cuda_stream, out);
+}
+
+nl_status nl_mesh_create_quad(int order, int64_t n_vert, const double* coords, int64_t n_elem,
+                              const int32_t* conn, const uint8_t* elem_in_omega,
+                              const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
+  nlx::clear_error();
+  if (order != 1 && order != 2) return nlx::fail(NL_EINVAL, "nl_mesh_create_quad: order must be 1 or 2");
+  return mesh_create_impl(2, order, 1, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
 }
 

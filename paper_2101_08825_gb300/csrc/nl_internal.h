@@ -114,6 +114,35 @@ struct Rule {
   double w[16] = {};
 };
 const Rule& rule(int dim);  // degree-5 simplex rule; weights sum to 1
+// 3-point Gauss-Legendre on [0, 1] (the 3x3 product rule of the quadrilaterals)
+struct GL3 {
+  double g[3], w[3];
+};
+const GL3& gl3();
+// Q1 / Q2 basis on the unit square at (s, t), in the node order of nl_mesh_create_quad: the
+// vertices (0,0), (1,0), (1,1), (0,1), then (Q2) the edge midpoints (0,1), (1,2), (2,3),
+// (3,0) and the centre; products of the 1D Lagrange bases on {0, 1} or {0, 1/2, 1}.
+template <typename T>
+__host__ __device__ inline void quad_basis(int order, T s, T t, T* phi) {
+  if (order == 2) {
+    const T ls[3] = {(T)2 * (s - (T)0.5) * (s - (T)1), (T)4 * s * ((T)1 - s), (T)2 * s * (s - (T)0.5)};
+    const T lt[3] = {(T)2 * (t - (T)0.5) * (t - (T)1), (T)4 * t * ((T)1 - t), (T)2 * t * (t - (T)0.5)};
+    phi[0] = ls[0] * lt[0];
+    phi[1] = ls[2] * lt[0];
+    phi[2] = ls[2] * lt[2];
+    phi[3] = ls[0] * lt[2];
+    phi[4] = ls[1] * lt[0];
+    phi[5] = ls[2] * lt[1];
+    phi[6] = ls[1] * lt[2];
+    phi[7] = ls[0] * lt[1];
+    phi[8] = ls[1] * lt[1];
+  } else {
+    phi[0] = ((T)1 - s) * ((T)1 - t);
+    phi[1] = s * ((T)1 - t);
+    phi[2] = s * t;
+    phi[3] = ((T)1 - s) * t;
+  }
+}
 double kernel_constant(int dim, int kernel, double delta, double eps);
 
 // Uploads the rule tables to the current device once.
@@ -130,7 +159,8 @@ nl_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, 
 struct nl_mesh {
   std::atomic<int> refs{1};
   int dim = 0;
-  int order = 1;                   // 1: P1 simplices, 2: P2 triangles
+  int order = 1;                   // 1: P1 / Q1, 2: P2 triangles / Q2 quadrilaterals
+  int cell = 0;                    // 0: simplices, 1: quadrilaterals (dim 2)
   int nb = 0;                      // nodes per element: dim+1 (P1) or 6 (P2)
   int64_t n_vert = 0, n_elem = 0;  // n_vert counts every node
   cudaStream_t stream = nullptr;
@@ -138,7 +168,7 @@ struct nl_mesh {
   int32_t* conn = nullptr;         // [n_elem][nb]: vertices first, then (P2) edge nodes
   uint8_t* elem_in_omega = nullptr;
   uint8_t* node_free = nullptr;
-  double* evert = nullptr;         // [n_elem][dim+1][dim] vertex coordinates per element
+  double* evert = nullptr;         // [n_elem][dim+1 or 4][dim] vertex coordinates per element
   double* blo = nullptr;           // [n_elem][dim] bounding boxes
   double* bhi = nullptr;
   double* vol = nullptr;           // [n_elem]
@@ -196,6 +226,10 @@ nl_status build_pairs(nl_mesh* m, double delta, double eps, nl_pairs* out);
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st);
+// The same for meshes of quadrilaterals (nl_quad_quad.cu).
+nl_status assemble_values_quad(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                               const nl_quad_params* qp, nl_precision prec, double* values,
+                               nl_assemble_stats* st);
 // The same for meshes of P2 triangles (nl_quad_p2.cu).
 nl_status assemble_values_p2(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                              const nl_quad_params* qp, nl_precision prec, double* values,

@@ -563,8 +563,9 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   NL_CUDA(cudaMemcpyAsync(&max_sum, maxs.p, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   NL_CUDA(cudaStreamSynchronize(s));
   int eh = next_pow2(std::max<int64_t>(64, std::min<int64_t>(2 * max_sum, 32768)));
-  // node table: a P2 element brings about four times the nodes of a P1 one into a row
-  int nh = std::min(8192, m->order == 2 ? 2 * eh : eh);
+  // node table: a P2 (or quadrilateral) element brings about four (two) times the nodes of a
+  // P1 triangle into a row
+  int nh = std::min(8192, (m->order == 2 || m->cell == 1) ? 2 * eh : eh);
   size_t rsmem = sizeof(int32_t) * (eh + nh);
   NL_TRY((allow_smem(k_rows<D, 0>, rsmem)));
   NL_TRY((allow_smem(k_rows<D, 1>, rsmem)));

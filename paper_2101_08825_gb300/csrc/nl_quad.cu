@@ -24,8 +24,10 @@ nl_status ensure_device_tables() {
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st) {
-  // P2 triangles (nl_quad_p2.cu; MIXED precisions run its FP32 path) and the tensor-core
-  // variants are compiled in translation units of their own (nl_quad_mma.cu)
+  // quadrilaterals (nl_quad_quad.cu), P2 triangles (nl_quad_p2.cu; MIXED precisions run
+  // their FP32 paths) and the tensor-core variants (nl_quad_mma.cu) are compiled in
+  // translation units of their own
+  if (m->cell == 1) return assemble_values_quad(m, p, kp, qp, prec, values, st);
   if (m->order == 2) return assemble_values_p2(m, p, kp, qp, prec, values, st);
   if (prec == NL_PREC_MIXED_TF32 || prec == NL_PREC_MIXED_BF16)
     return assemble_values_mma(m, p, kp, qp, prec, values, st);
@@ -84,7 +86,7 @@ nl_status assemble_noalloc(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                            const nl_quad_params* qp, nl_precision prec, double* values,
                            nl_assemble_stats* st) {
   if (!values) return fail(NL_EINVAL, "nl_assemble_noalloc: values is NULL");
-  if (m->order != 1) return fail(NL_EINVAL, "nl_assemble_noalloc: P1 meshes only; use nl_assemble");
+  if (m->order != 1 || m->cell != 0) return fail(NL_EINVAL, "nl_assemble_noalloc: P1 meshes only; use nl_assemble");
   QParams P;
   NL_TRY(fill_qparams("nl_assemble_noalloc", m, p, kp, qp, prec, &P));
   const int D = m->dim;

@@ -59,6 +59,43 @@ __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], vol[e] * acc[a]);
 }
 
+// F_i += int_E f phi_i per quadrilateral of Omega with NB nodes (Q1 4, Q2 9): Gauss-Legendre
+// 3x3 on the unit square mapped by the element's bilinear map; S[q] = (s, t, weight) and
+// B[q][a] (row stride 16) the basis at point q.
+template <int NB>
+__global__ void k_rhs_quads(int64_t n_elem, const int32_t* __restrict__ conn,
+                            const uint8_t* __restrict__ eio, const uint8_t* __restrict__ free_,
+                            const double* __restrict__ evert, const double* __restrict__ fn,
+                            double f_const, const double* __restrict__ B,
+                            const double* __restrict__ S, double* __restrict__ F) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_elem || !eio[e]) return;
+  int32_t nd[NB];
+  double fv[NB], acc[NB];
+  for (int a = 0; a < NB; a++) {
+    nd[a] = conn[e * NB + a];
+    fv[a] = fn ? fn[nd[a]] : 0.0;
+    acc[a] = 0.0;
+  }
+  double V[4][2];
+  for (int a = 0; a < 4; a++)
+    for (int k = 0; k < 2; k++) V[a][k] = evert[(e * 4 + a) * 2 + k];
+  for (int q = 0; q < 9; q++) {
+    const double s = S[q * 3], t = S[q * 3 + 1];
+    double xs[2], xt[2];
+    for (int k = 0; k < 2; k++) {
+      xs[k] = (1.0 - t) * (V[1][k] - V[0][k]) + t * (V[2][k] - V[3][k]);
+      xt[k] = (1.0 - s) * (V[3][k] - V[0][k]) + s * (V[2][k] - V[1][k]);
+    }
+    const double w = S[q * 3 + 2] * fabs(xs[0] * xt[1] - xs[1] * xt[0]);
+    double f = f_const;
+    for (int v = 0; v < NB; v++) f += B[q * 16 + v] * fv[v];
+    for (int a = 0; a < NB; a++) acc[a] += w * f * B[q * 16 + a];
+  }
+  for (int a = 0; a < NB; a++)
+    if (free_[nd[a]]) atomicAdd(&F[nd[a]], acc[a]);
+}
+
 __global__ void k_lift(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                        const double* __restrict__ val, const uint8_t* __restrict__ free_,
                        const double* __restrict__ g, double* __restrict__ F) {
@@ -524,7 +561,31 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   }
   NL_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * m->n_vert, s));
   unsigned ge = (unsigned)((m->n_elem + RT - 1) / RT);
-  if (m->nb == 6)
+  DevBuf<double> QB, QS;
+  if (m->cell == 1) {
+    // Gauss-Legendre 3x3 points (s, t, weight) and the Q1 / Q2 basis there
+    std::vector<double> hq(9 * 16, 0.0), hs(27, 0.0);
+    const GL3& g = gl3();
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) {
+        const int q = 3 * i + j;
+        hs[q * 3] = g.g[i];
+        hs[q * 3 + 1] = g.g[j];
+        hs[q * 3 + 2] = g.w[i] * g.w[j];
+        quad_basis<double>(m->order, g.g[i], g.g[j], &hq[q * 16]);
+      }
+    NL_TRY(QB.alloc(9 * 16, s));
+    NL_TRY(QS.alloc(27, s));
+    NL_CUDA(cudaMemcpyAsync(QB.p, hq.data(), sizeof(double) * 9 * 16, cudaMemcpyHostToDevice, s));
+    NL_CUDA(cudaMemcpyAsync(QS.p, hs.data(), sizeof(double) * 27, cudaMemcpyHostToDevice, s));
+  }
+  if (m->cell == 1 && m->nb == 9)
+    k_rhs_quads<9><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->evert, fn.p, f_const, QB.p, QS.p, F);
+  else if (m->cell == 1)
+    k_rhs_quads<4><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->evert, fn.p, f_const, QB.p, QS.p, F);
+  else if (m->nb == 6)
     k_rhs_elems<6><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->vol, fn.p, f_const, B.p, W.p, r.n, F);
   else if (D == 2)

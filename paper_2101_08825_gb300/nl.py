@@ -86,6 +86,7 @@ def lib():
         "nl_launch_count": (i64, []),
         "nl_mesh_create": (st, [i, i64, p, i64, p, p, p, p, pp]),
         "nl_mesh_create_p2": (st, [i, i64, p, i64, p, p, p, p, pp]),
+        "nl_mesh_create_quad": (st, [i, i64, p, i64, p, p, p, p, pp]),
         "nl_mesh_create_box": (st, [i, p, d, p, ctypes.c_int32, d, ctypes.c_uint64, p, pp]),
         "nl_mesh_info": (st, [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64)]),
@@ -298,8 +299,25 @@ def nl_mesh_create_p2(dim, coords, conn, elem_in_omega, node_free, stream=None) 
     return Mesh(h)
 
 
+def nl_mesh_create_quad(order, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
+    """Mesh of quadrilaterals: conn rows of 4 (Q1) or 9 (Q2) nodes."""
+    coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(2, -1)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 9 if order == 2 else 4)
+    eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
+    nf = np.ascontiguousarray(node_free, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib().nl_mesh_create_quad(int(order), coords.shape[1], _ptr(coords), conn.shape[0], _ptr(conn),
+                                     _ptr(eio), _ptr(nf), stream if stream is not None else current_stream(),
+                                     ctypes.byref(h)), "nl_mesh_create_quad")
+    return Mesh(h)
+
+
 def mesh_from(mesh, stream=None) -> Mesh:
-    """Uploads an nl_inputs.Mesh (P1, or P2 triangles when conn has six columns)."""
+    """Uploads an nl_inputs.Mesh: P1 simplices, P2 triangles (six nodes per element) or
+    quadrilaterals (2D, four or nine nodes per element)."""
+    if mesh.dim == 2 and mesh.conn.shape[1] in (4, 9):
+        return nl_mesh_create_quad(1 if mesh.conn.shape[1] == 4 else 2, mesh.coords, mesh.conn,
+                                   mesh.elem_in_omega, mesh.node_free, stream)
     if mesh.conn.shape[1] == 6:
         return nl_mesh_create_p2(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
     return nl_mesh_create(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
