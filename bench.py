@@ -69,6 +69,11 @@ def parse():
                          "0 = skip the leg)")
     ap.add_argument("--p2-fp64-steps", type=int, default=1,
                     help="timed FP64 steps of the P2 leg")
+    ap.add_argument("--quad-steps", type=int, default=2,
+                    help="timed FP32 steps of each quadrilateral leg (Q1, Q2 on the 2D workload's "
+                         "grid; 0 = skip)")
+    ap.add_argument("--quad-fp64-steps", type=int, default=1,
+                    help="timed FP64 steps of each quadrilateral leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="wall seconds of the oracle sample on all host cores")
@@ -215,9 +220,11 @@ def workload(name):
 
 def describe(w, mesh):
     shape = "triangles" if mesh.dim == 2 else "tetrahedra"
+    if _is_quad(mesh):
+        shape = "quadrilaterals"
     n_omega = int(mesh.elem_in_omega.sum())
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
-    order = "P2" if mesh.conn.shape[1] == 6 else "P1"
+    order = {6: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2"}.get(mesh.conn.shape[1], "P1")
     return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} {order} {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
             f"layer {w.layer} cells, L_max={w.L_max}, {kern} kernel, jitter {w.jitter:g}h "
@@ -229,10 +236,46 @@ def u_exact(mesh):
     return (mesh.coords ** 2).sum(axis=0)  # u = x^2 + y^2 (+ z^2)
 
 
+def _is_quad(mesh):
+    return mesh.dim == 2 and mesh.conn.shape[1] in (4, 9)
+
+
+def l2_err_omega_quads(mesh, u_h):
+    """||u - u_h||_{L2(Omega)} on quadrilaterals (u = sum x_k^2): Gauss-Legendre 3x3 on each
+    element's unit square mapped by its bilinear map; Q1 / Q2 basis (tensor products of the 1D
+    Lagrange bases on {0, 1} or {0, 1/2, 1}, nodes: vertices, edge midpoints, centre)."""
+    x, gw = np.polynomial.legendre.leggauss(3)
+    g, gw = (x + 1) / 2, gw / 2
+    S, T = np.meshgrid(g, g, indexing="ij")
+    W = np.outer(gw, gw).ravel()
+    s, t = S.ravel(), T.ravel()
+    conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
+    V = mesh.points()[conn[:, :4]]  # (ne, 4, 2)
+    N = np.stack([(1 - s) * (1 - t), s * (1 - t), s * t, (1 - s) * t], 1)  # (9, 4)
+    X = np.einsum("qa,eak->eqk", N, V)
+    xs = (1 - t)[None, :, None] * (V[:, 1] - V[:, 0])[:, None] + t[None, :, None] * (V[:, 2] - V[:, 3])[:, None]
+    xt = (1 - s)[None, :, None] * (V[:, 3] - V[:, 0])[:, None] + s[None, :, None] * (V[:, 2] - V[:, 1])[:, None]
+    det = np.abs(xs[..., 0] * xt[..., 1] - xs[..., 1] * xt[..., 0])
+    if conn.shape[1] == 9:
+        def L(v):
+            return np.stack([2 * (v - 0.5) * (v - 1), 4 * v * (1 - v), 2 * v * (v - 0.5)], 1)
+        Ls, Lt = L(s), L(t)
+        ij = [(0, 0), (2, 0), (2, 2), (0, 2), (1, 0), (2, 1), (1, 2), (0, 1), (1, 1)]
+        phi = np.stack([Ls[:, i] * Lt[:, j] for i, j in ij], 1)
+    else:
+        phi = N
+    uh = np.einsum("qa,ea->eq", phi, u_h[conn])
+    d = (X ** 2).sum(-1) - uh
+    return float(math.sqrt(np.sum(det * W[None, :] * d * d)))
+
+
 def l2_err_omega(mesh, u_h, rule):
     """||u - u_h||_{L2(Omega)} with the degree-5 rule per element (u = sum x_k^2); P1, or P2
     triangles when the elements have six nodes (basis lambda_a (2 lambda_a - 1) at the
-    vertices, 4 lambda_a lambda_b at the edge nodes (0,1), (1,2), (0,2))."""
+    vertices, 4 lambda_a lambda_b at the edge nodes (0,1), (1,2), (0,2)); quadrilaterals with
+    l2_err_omega_quads."""
+    if _is_quad(mesh):
+        return l2_err_omega_quads(mesh, u_h)
     b, w = rule
     P = mesh.points()
     conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
@@ -339,6 +382,7 @@ def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False, stb=None):
         "units": "Algorithm-1 quadrature point pairs (closed-form ones included)",
         "frac_evaluated_only": round(achieved_ev / peak, 4),
         "kernel": (f"k_quad_p2<{rtype},{w.kernel}>" if nb == 6 else
+                   f"k_quad_q<{rtype},{w.kernel},{1 if nb == 4 else 2}>" if _is_quad(mesh) else
                    f"k_quad<{mesh.dim},{rtype},{w.kernel}>"), "flops_per_assembly": flops,
         "kernel_ms_per_assembly": round(quad_ms, 3),
         "launches_per_assembly": int(stats[-1].n_quad_launches),
@@ -514,7 +558,12 @@ def run_ours(args, rank, world, local):
     if args.c2_steps > 0:
         out["c2_2d"] = run_c2_block(args, nl, torch, stream, flush, world)
     if args.p2_steps > 0:
-        out["p2"] = run_p2_block(args, nl, torch, stream, flush, world)
+        out["p2"] = run_element_block(args, nl, torch, stream, flush, world, "c2_2d_p2",
+                                      args.p2_steps, args.p2_fp64_steps)
+    if args.quad_steps > 0:
+        for key, name in (("q1", "c2_2d_q1"), ("q2", "c2_2d_q2")):
+            out[key] = run_element_block(args, nl, torch, stream, flush, world, name,
+                                         args.quad_steps, args.quad_fp64_steps)
     if args.eps_study:
         out["eps_study"] = run_eps_study(args)
     if args.batch_problems > 0:
@@ -565,16 +614,17 @@ def run_c2_block(args, nl, torch, stream, flush, world):
     return out
 
 
-def run_p2_block(args, nl, torch, stream, flush, world):
-    """P2 triangles on the 2D workload's triangulation (h = 1/256, 141,512 triangles, 284,089
-    nodes): the FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
-    BiCGStab), their L2 errors, and the roofline of the P2 assembly kernel in both
+def run_element_block(args, nl, torch, stream, flush, world, name, steps, fp64_steps):
+    """Other element families on the 2D workload's grid (h = 1/256): P2 triangles (c2_2d_p2:
+    141,512 triangles, 284,089 nodes), Q1 and Q2 quadrilaterals (c2_2d_q1, c2_2d_q2: 70,756
+    cells).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
+    BiCGStab), their L2 errors, and the roofline of the assembly kernel in both
     precisions."""
-    w, mesh = workload("c2_2d_p2")
+    w, mesh = workload(name)
     rule = nl.nl_quad_rule(2)
     dm = nl.mesh_from(mesh)
-    mx = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP32, args.p2_steps, 1, flush, world,
-                  keep_last=args.p2_fp64_steps > 0)
+    mx = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP32, steps, 1, flush, world,
+                  keep_last=fp64_steps > 0)
     ms = statistics.mean(mx["times"])
     st = mx["stats"][-1]
     stb, roof = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP32, mx["stats"])
@@ -587,10 +637,10 @@ def run_p2_block(args, nl, torch, stream, flush, world):
          "scatter_ms": round(statistics.mean(s.ms_scatter for s in mx["stats"]), 3),
          "l2_err_omega": l2_err_omega(mesh, mx["last"]["u"], rule),
          "solve_ms_p50": round(float(np.percentile(mx["solve_ms"], 50)), 3),
-         "solve_iters": mx["last"]["it"], "gpu_launches_per_step": int(mx["launches"] / max(1, args.p2_steps)),
+         "solve_iters": mx["last"]["it"], "gpu_launches_per_step": int(mx["launches"] / max(1, steps)),
          "roofline": roof}
-    if args.p2_fp64_steps > 0:
-        f64 = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP64, args.p2_fp64_steps, 0,
+    if fp64_steps > 0:
+        f64 = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP64, fp64_steps, 0,
                        flush, world, keep_last=True)
         ms64 = statistics.mean(f64["times"])
         _, roof64 = _roofline(nl, dm, mesh, w, nl.NL_PREC_FP64, f64["stats"], stb=stb)

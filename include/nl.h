@@ -183,21 +183,23 @@ nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64
  * vertices v0..v3 counterclockwise (the images of (0,0), (1,0), (1,1), (0,1)).  order 1: Q1,
  * conn holds the 4 vertices per element; order 2: Q2 (biquadratic Lagrange), 9 nodes per
  * element: the vertices, the nodes at the midpoints of the edges (0,1), (1,2), (2,3), (3,0),
- * then the node at the image of the square's centre (the mean of the vertices).  Algorithm
+ * then the node at the image of the square's centre (the mean of the vertices); order 3: the
+ * 8-node serendipity element, the Q2 nodes without the centre.  Algorithm
  * 1's midpoint refinement splits the square into its four half-size sub-squares (physical
  * vertices: the parent's vertices, edge midpoints (a+b)*0.5 and the centre as the midpoint
  * of the midpoints of the edges (0,1) and (2,3)).  Other arguments as nl_mesh_create.  Pairs,
  * pattern, nl_assemble (FP64, FP32; the MIXED precisions run the FP32 path and report it),
  * nl_rhs and nl_solve accept it; plans and nl_assemble_noalloc take P1 meshes only.
- * Errors: those of nl_mesh_create; NL_EINVAL for order not 1/2, an element that is not a
+ * Errors: those of nl_mesh_create; NL_EINVAL for order not 1/2/3, an element that is not a
  * convex counterclockwise quadrilateral, or a Q2 node off its position (by more than 1e-9
  * of the element's diagonal). */
 nl_status nl_mesh_create_quad(int order, int64_t n_vert, const double* coords, int64_t n_elem,
                               const int32_t* conn, const uint8_t* elem_in_omega,
                               const uint8_t* node_free, void* cuda_stream, nl_mesh** out);
 nl_status nl_mesh_info(const nl_mesh* mesh, int* dim, int64_t* n_vert, int64_t* n_elem);
-/* Polynomial order of the mesh's elements (1: P1 / Q1, 2: P2 / Q2) and nodes per element
- * (simplices dim+1 or 6, quadrilaterals 4 or 9); either pointer may be NULL. */
+/* Polynomial order of the mesh's elements (1: P1 / Q1, 2: P2 / Q2, 3: serendipity
+ * quadrilaterals) and nodes per element (simplices dim+1 or 6, quadrilaterals 4, 8 or 9);
+ * either pointer may be NULL. */
 nl_status nl_mesh_order(const nl_mesh* mesh, int* order, int* nodes_per_elem);
 /* Copies the mesh back (host buffers of the sizes of nl_mesh_create, conn of
  * nodes_per_elem*n_elem entries; any may be NULL). */

@@ -98,6 +98,11 @@ WORKLOADS = {
     "c2_2d_q1": _unit_box("c2_2d_q1", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1, cell="quad"),
     "c2_2d_h128_q1": _unit_box("c2_2d_h128_q1", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1,
                                cell="quad"),
+    # the same grid with Q2 (biquadratic) quadrilaterals
+    "c2_2d_q2": _unit_box("c2_2d_q2", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1, cell="quad",
+                          order=2),
+    "c2_2d_h128_q2": _unit_box("c2_2d_h128_q2", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1,
+                               cell="quad", order=2),
 }
 
 

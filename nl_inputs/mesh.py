@@ -197,3 +197,17 @@ def q2_mesh(mesh: Mesh) -> Mesh:
     return Mesh(dim=2, coords=coords, conn=np.ascontiguousarray(conn),
                 elem_in_omega=mesh.elem_in_omega.copy(), node_free=free.astype(np.uint8),
                 h=mesh.h, meta=dict(mesh.meta, order=2))
+
+
+def s2_mesh(mesh: Mesh) -> Mesh:
+    """The 8-node serendipity mesh of a Q2 mesh: the same nodes and elements without the
+    cells' centre nodes (the last n_elem nodes of q2_mesh); rows (v0, v1, v2, v3, m01, m12,
+    m23, m30)."""
+    if mesh.dim != 2 or mesh.conn.shape[1] != 9:
+        raise ValueError("serendipity meshes are built from Q2 meshes")
+    n_keep = mesh.n_vert - mesh.n_elem
+    if not np.array_equal(mesh.conn[:, 8], np.arange(n_keep, mesh.n_vert)):
+        raise ValueError("the centre nodes must be the last n_elem nodes")
+    return Mesh(dim=2, coords=np.ascontiguousarray(mesh.coords[:, :n_keep]),
+                conn=np.ascontiguousarray(mesh.conn[:, :8]), elem_in_omega=mesh.elem_in_omega.copy(),
+                node_free=mesh.node_free[:n_keep].copy(), h=mesh.h, meta=dict(mesh.meta, order=3))

@@ -388,7 +388,7 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
 /* Nodes per element: P1 simplices dim+1; P2 triangles 6 (the vertices, then the midpoints of
  * the edges (0,1), (1,2), (0,2)). */
 static int npe(const or_mesh* M) {
-  if (M->cell == 1) return (M->order == 2) ? 9 : 4;
+  if (M->cell == 1) return (M->order == 2) ? 9 : (M->order == 3) ? 8 : 4;
   return (M->order == 2) ? 6 : M->dim + 1;
 }
 /* Vertices per element: simplices dim+1, quadrilaterals 4. */
@@ -779,8 +779,26 @@ static void lagrange1d(int order, double s, double* L) {
 }
 
 /* Q1 / Q2 basis at (s, t), nodes in the mesh's order: Q1 the vertices (0,0), (1,0), (1,1),
- * (0,1); Q2 the vertices, the midpoints of the edges (0,1), (1,2), (2,3), (3,0), the centre. */
+ * (0,1); Q2 the vertices, the midpoints of the edges (0,1), (1,2), (2,3), (3,0), the centre.
+ * Order 3, the serendipity element (the Q2 nodes without the centre): with xi = 2s - 1,
+ * eta = 2t - 1 and a node at (xi_a, eta_a), the corner functions
+ * (1 + xi xi_a)(1 + eta eta_a)(xi xi_a + eta eta_a - 1)/4 and the edge functions
+ * (1 - xi^2)(1 + eta eta_a)/2 (xi_a = 0) or (1 + xi xi_a)(1 - eta^2)/2 (eta_a = 0). */
 static void quad_basis(int order, double s, double t, double* phi) {
+  if (order == 3) {
+    static const double nd[8][2] = {{-1, -1}, {1, -1}, {1, 1}, {-1, 1}, {0, -1}, {1, 0}, {0, 1}, {-1, 0}};
+    double xi = 2.0 * s - 1.0, eta = 2.0 * t - 1.0;
+    for (int a = 0; a < 8; a++) {
+      double xa = nd[a][0], ya = nd[a][1];
+      if (a < 4)
+        phi[a] = 0.25 * (1.0 + xi * xa) * (1.0 + eta * ya) * (xi * xa + eta * ya - 1.0);
+      else if (xa == 0.0)
+        phi[a] = 0.5 * (1.0 - xi * xi) * (1.0 + eta * ya);
+      else
+        phi[a] = 0.5 * (1.0 + xi * xa) * (1.0 - eta * eta);
+    }
+    return;
+  }
   double Ls[3], Lt[3];
   lagrange1d(order, s, Ls);
   lagrange1d(order, t, Lt);

@@ -450,7 +450,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
   if (!out) return fail(NL_EINVAL, "nl_mesh_create: out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create: dim must be 2 or 3");
-  if (order != 1 && !(order == 2 && dim == 2))
+  if (order != 1 && !(order == 2 && dim == 2) && !(order == 3 && cell == 1))
     return fail(NL_EINVAL, "nl_mesh_create: P2 elements are triangles (dim 2) only");
   if (cell == 1 && dim != 2) return fail(NL_EINVAL, "nl_mesh_create_quad: quadrilaterals are 2D");
   if (n_vert <= 0 || n_vert > INT32_MAX || n_elem <= 0 || n_elem > INT32_MAX)
@@ -458,7 +458,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
   const int nv = cell == 1 ? 4 : dim + 1;
-  const int nb = cell == 1 ? (order == 2 ? 9 : 4) : (order == 2 ? 6 : nv);
+  const int nb = cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4)) : (order == 2 ? 6 : nv);
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
     if (!std::isfinite(coords[i])) return fail(NL_EINVAL, "nl_mesh_create: non-finite coordinate");
   double bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -483,10 +483,10 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
           return fail(NL_EINVAL, "nl_mesh_create_quad: element %lld is not a convex counterclockwise quadrilateral",
                       (long long)e);
       }
-      if (order == 2) {
-        // Q2: edge node 4 + j at the midpoint of edge j = (0,1), (1,2), (2,3), (3,0), node 8 at
-        // the image of the square's centre, the mean of the four vertices
-        for (int j = 0; j < 5; j++) {
+      if (order >= 2) {
+        // Q2 / serendipity: edge node 4 + j at the midpoint of edge j = (0,1), (1,2), (2,3),
+        // (3,0); Q2 node 8 at the image of the square's centre, the mean of the four vertices
+        for (int j = 0; j < nb - 4; j++) {
           const int32_t v = conn[e * nb + 4 + j];
           double d2 = 0.0, l2 = 0.0;
           for (int k = 0; k < 2; k++) {
@@ -754,7 +754,7 @@ nl_status nl_mesh_create_quad(int order, int64_t n_vert, const double* coords, i
                               const int32_t* conn, const uint8_t* elem_in_omega,
                               const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
-  if (order != 1 && order != 2) return nlx::fail(NL_EINVAL, "nl_mesh_create_quad: order must be 1 or 2");
+  if (order < 1 || order > 3) return nlx::fail(NL_EINVAL, "nl_mesh_create_quad: order must be 1, 2 or 3");
   return mesh_create_impl(2, order, 1, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
 }

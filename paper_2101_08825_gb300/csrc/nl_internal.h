@@ -122,8 +122,25 @@ const GL3& gl3();
 // Q1 / Q2 basis on the unit square at (s, t), in the node order of nl_mesh_create_quad: the
 // vertices (0,0), (1,0), (1,1), (0,1), then (Q2) the edge midpoints (0,1), (1,2), (2,3),
 // (3,0) and the centre; products of the 1D Lagrange bases on {0, 1} or {0, 1/2, 1}.
+// order 3: the 8-node serendipity element (the Q2 nodes without the centre), on
+// (xi, eta) = (2s - 1, 2t - 1) with nodes (xi_a, eta_a): corners
+// (1 + xi xi_a)(1 + eta eta_a)(xi xi_a + eta eta_a - 1)/4, edge nodes
+// (1 - xi^2)(1 + eta eta_a)/2 or (1 + xi xi_a)(1 - eta^2)/2.
 template <typename T>
 __host__ __device__ inline void quad_basis(int order, T s, T t, T* phi) {
+  if (order == 3) {
+    const T x = (T)2 * s - (T)1, y = (T)2 * t - (T)1;
+    const T xm = (T)1 - x, xp = (T)1 + x, ym = (T)1 - y, yp = (T)1 + y;
+    phi[0] = (T)0.25 * xm * ym * (-x - y - (T)1);
+    phi[1] = (T)0.25 * xp * ym * (x - y - (T)1);
+    phi[2] = (T)0.25 * xp * yp * (x + y - (T)1);
+    phi[3] = (T)0.25 * xm * yp * (-x + y - (T)1);
+    phi[4] = (T)0.5 * ((T)1 - x * x) * ym;
+    phi[5] = (T)0.5 * xp * ((T)1 - y * y);
+    phi[6] = (T)0.5 * ((T)1 - x * x) * yp;
+    phi[7] = (T)0.5 * xm * ((T)1 - y * y);
+    return;
+  }
   if (order == 2) {
     const T ls[3] = {(T)2 * (s - (T)0.5) * (s - (T)1), (T)4 * s * ((T)1 - s), (T)2 * s * (s - (T)0.5)};
     const T lt[3] = {(T)2 * (t - (T)0.5) * (t - (T)1), (T)4 * t * ((T)1 - t), (T)2 * t * (t - (T)0.5)};

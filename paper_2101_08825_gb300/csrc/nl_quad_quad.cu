@@ -19,8 +19,8 @@
 // round), decisions in FP64 (FP64 path) or by the FP32 screen with an FP64 re-decision inside
 // the margin (FP32 path), buffered sub-elements integrated by the whole warp.  Q1: each lane
 // owns one outer point per pass and m's 9 inner points (36 sums H_d(y) = sum_x w_x C eta mu
-// phi^l_d(x)); Q2: the two half-warps share the outer points and take inner points 0-4 and
-// 5-8 (45 sums per lane).  The end of a pair sums H over the lanes through shared memory,
+// phi^l_d(x)); Q2 and the 8-node serendipity element: the two half-warps share the outer
+// points and take inner points 0-4 and 5-8 (45 / 40 sums per lane).  The end of a pair sums H over the lanes through shared memory,
 // writes the cross block -2 sum_y w_y |det DF_m| phi^m_a(y) H_d(y) and keeps g(y) = sum_d
 // H_d(y) (the basis sums to one) for m's self block.  With the constant kernel an INT
 // sub-element (mu = 1 at every point pair) adds sum_x w_x C phi^l_d(x), which does not depend
@@ -38,11 +38,12 @@ constexpr int QQ_IMAX = 64;    // buffered sub-elements
 constexpr int QQ_RS = 33;      // row stride of the reduction scratch
 constexpr int QQ_WARPS = 4;
 
+// ORD 1: Q1, 2: Q2, 3: the 8-node serendipity element
 template <int ORD>
 struct QGeo {
-  static constexpr int NN = ORD == 2 ? 9 : 4;       // nodes per element
-  static constexpr int NYL = ORD == 2 ? 5 : 9;      // inner points per lane
-  static constexpr int XPI = ORD == 2 ? 16 : 32;    // outer points per warp pass
+  static constexpr int NN = ORD == 2 ? 9 : (ORD == 3 ? 8 : 4);  // nodes per element
+  static constexpr int NYL = ORD == 1 ? 9 : 5;                  // inner points per lane
+  static constexpr int XPI = ORD == 1 ? 32 : 16;                // outer points per warp pass
   static constexpr int NH = NN * QQ_NQ;             // H_d(y) per pair
   static constexpr int NBLK = NN * NN;
 };
@@ -212,9 +213,11 @@ __device__ __noinline__ int qexact_classify(const double* __restrict__ evert_l,
   return ACT_DROP;
 }
 
-// FP32: 2 CTAs of 4 warps per SM; FP64 1.
+// FP32: 3 CTAs of 4 warps per SM (168 registers; measured on GB300 at the 2D workload's grid,
+// Q1 56.5 / Q2 72.8 ms per assembly kernel against 61.7 / 84.8 ms with 2 CTAs and 222 / 242
+// registers, and 61.9 / 83.9 ms with 4 CTAs at 128 registers); FP64 1.
 template <typename R, int KERN, int ORD>
-__global__ void __launch_bounds__(QQ_WARPS * 32, std::is_same<R, float>::value ? 2 : 1)
+__global__ void __launch_bounds__(QQ_WARPS * 32, std::is_same<R, float>::value ? 3 : 1)
     k_quad_q(const QParams P) {
   using G = QGeo<ORD>;
   constexpr int NN = G::NN, NYL = G::NYL, XPI = G::XPI, NH = G::NH, NBLK = G::NBLK;
@@ -240,8 +243,8 @@ __global__ void __launch_bounds__(QQ_WARPS * 32, std::is_same<R, float>::value ?
   for (int t = threadIdx.x; t < 81; t += blockDim.x) rB[t] = (R)tB[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int ybase = (ORD == 2 && lane >= 16) ? 5 : 0;  // first inner point of this lane
-  const int xl = ORD == 2 ? (lane & 15) : lane;        // outer point slot of this lane
+  const int ybase = (ORD != 1 && lane >= 16) ? 5 : 0;  // first inner point of this lane
+  const int xl = ORD != 1 ? (lane & 15) : lane;        // outer point slot of this lane
   QMem<R, ORD> wm;
   wm.carve(smem_raw + qq_table_bytes<R>() + (size_t)wid * QMem<R, ORD>::bytes(P.scap), P.scap);
 
@@ -447,8 +450,8 @@ __global__ void __launch_bounds__(QQ_WARPS * 32, std::is_same<R, float>::value ?
       auto outer_sum = [&](R s0, R t0, R len, R (&S)[NN]) {
 #pragma unroll
         for (int d = 0; d < NN; d++) S[d] = 0;
-#pragma unroll
-        for (int q = 0; q < QQ_NQ; q++) {
+#pragma unroll 1
+        for (int q = 0; q < QQ_NQ; q++) {  // not unrolled: rare, keeps the code small
           const R s = s0 + len * rS[q * 3], t = t0 + len * rS[q * 3 + 1];
           R x0, x1, det;
           qmap<R>(VL, s, t, x0, x1, det);
@@ -475,7 +478,7 @@ __global__ void __launch_bounds__(QQ_WARPS * 32, std::is_same<R, float>::value ?
       // Q1: a FINAL sub-element whose ball (the vertices' mean c, radius max |v - c|) clears
       // delta - eps - margin or delta + eps + margin at every inner point
       auto closed_final = [&](const R (&V)[4][2], R s0, R t0, R len) -> bool {
-        if (ORD == 2) return false;
+        if (ORD != 1) return false;
         R c[2], r2 = 0;
 #pragma unroll
         for (int k = 0; k < 2; k++)
@@ -806,8 +809,9 @@ nl_status assemble_values_quad(nl_mesh* m, nl_pairs* p, const nl_kernel_params* 
   const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
   PhaseTimer T;
   if (p->n_pairs > 0) {
-    rc = m->order == 2 ? run_q<2>(m, p, P, values, s, scratch.p, err.p, T, f32, gauss)
-                       : run_q<1>(m, p, P, values, s, scratch.p, err.p, T, f32, gauss);
+    rc = m->order == 2   ? run_q<2>(m, p, P, values, s, scratch.p, err.p, T, f32, gauss)
+         : m->order == 3 ? run_q<3>(m, p, P, values, s, scratch.p, err.p, T, f32, gauss)
+                         : run_q<1>(m, p, P, values, s, scratch.p, err.p, T, f32, gauss);
   }
   cudaEventRecord(e1, s);
   unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};

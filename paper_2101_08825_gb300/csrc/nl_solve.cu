@@ -59,7 +59,7 @@ __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], vol[e] * acc[a]);
 }
 
-// F_i += int_E f phi_i per quadrilateral of Omega with NB nodes (Q1 4, Q2 9): Gauss-Legendre
+// F_i += int_E f phi_i per quadrilateral of Omega with NB nodes (Q1 4, serendipity 8, Q2 9): Gauss-Legendre
 // 3x3 on the unit square mapped by the element's bilinear map; S[q] = (s, t, weight) and
 // B[q][a] (row stride 16) the basis at point q.
 template <int NB>
@@ -581,6 +581,9 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   }
   if (m->cell == 1 && m->nb == 9)
     k_rhs_quads<9><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->evert, fn.p, f_const, QB.p, QS.p, F);
+  else if (m->cell == 1 && m->nb == 8)
+    k_rhs_quads<8><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->evert, fn.p, f_const, QB.p, QS.p, F);
   else if (m->cell == 1)
     k_rhs_quads<4><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,

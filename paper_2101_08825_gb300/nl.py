@@ -300,9 +300,10 @@ def nl_mesh_create_p2(dim, coords, conn, elem_in_omega, node_free, stream=None) 
 
 
 def nl_mesh_create_quad(order, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
-    """Mesh of quadrilaterals: conn rows of 4 (Q1) or 9 (Q2) nodes."""
+    """Mesh of quadrilaterals: conn rows of 4 (Q1, order 1), 9 (Q2, order 2) or 8
+    (serendipity, order 3) nodes."""
     coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(2, -1)
-    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 9 if order == 2 else 4)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, {1: 4, 2: 9, 3: 8}[int(order)])
     eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
     nf = np.ascontiguousarray(node_free, dtype=np.uint8)
     h = ctypes.c_void_p()
@@ -314,9 +315,9 @@ def nl_mesh_create_quad(order, coords, conn, elem_in_omega, node_free, stream=No
 
 def mesh_from(mesh, stream=None) -> Mesh:
     """Uploads an nl_inputs.Mesh: P1 simplices, P2 triangles (six nodes per element) or
-    quadrilaterals (2D, four or nine nodes per element)."""
-    if mesh.dim == 2 and mesh.conn.shape[1] in (4, 9):
-        return nl_mesh_create_quad(1 if mesh.conn.shape[1] == 4 else 2, mesh.coords, mesh.conn,
+    quadrilaterals (2D, four, eight or nine nodes per element)."""
+    if mesh.dim == 2 and mesh.conn.shape[1] in (4, 8, 9):
+        return nl_mesh_create_quad({4: 1, 9: 2, 8: 3}[mesh.conn.shape[1]], mesh.coords, mesh.conn,
                                    mesh.elem_in_omega, mesh.node_free, stream)
     if mesh.conn.shape[1] == 6:
         return nl_mesh_create_p2(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)

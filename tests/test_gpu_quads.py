@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from nl_inputs import WORKLOADS, q2_mesh, quad_mesh, structured_mesh, workload_mesh
+from nl_inputs import WORKLOADS, q2_mesh, quad_mesh, s2_mesh, structured_mesh, workload_mesh
 from nl_inputs.configs import table2_tri, table3_tri
 from paper_2101_08825_gb300 import nl
 
@@ -22,8 +22,11 @@ TOL32 = 2e-6
 
 
 def _q(m, order):
+    # order 1: Q1, 2: Q2, 3: the 8-node serendipity element
     qm = quad_mesh(m)
-    return q2_mesh(qm) if order == 2 else qm
+    if order == 1:
+        return qm
+    return q2_mesh(qm) if order == 2 else s2_mesh(q2_mesh(qm))
 
 
 CASES = [
@@ -37,6 +40,9 @@ CASES = [
     ("gauss_q1", lambda: _q(structured_mesh(2, 8, 1 / 8, 0.0, 2, jitter=0.1, seed=5), 1), 0.2, 0.01, 3, 1, 1, False),
     ("gauss_q2", lambda: _q(structured_mesh(2, 6, 1 / 6, 0.0, 2, jitter=0.1, seed=6), 2), 0.25, 0.02, 3, 1, 1, False),
     ("euclid_q1", lambda: _q(structured_mesh(2, 9, 1 / 9, 0.0, 3, jitter=0.1, seed=13), 1), 0.25, 0.03, 4, 1, 0, True),
+    ("t2_s2", lambda: _q(workload_mesh(table2_tri(2)), 3), 0.2, 0.0125, 3, 1, 0, False),
+    ("jit_s2_L4", lambda: _q(structured_mesh(2, 7, 1 / 7, 0.0, 3, jitter=0.15, seed=14), 3), 0.3, 0.03, 4, 1, 0, False),
+    ("gauss_s2", lambda: _q(structured_mesh(2, 6, 1 / 6, 0.0, 2, jitter=0.1, seed=15), 3), 0.25, 0.02, 3, 1, 1, False),
 ]
 
 
@@ -80,6 +86,7 @@ def test_quad_mesh_round_trip_and_validation():
     mesh = _q(structured_mesh(2, 4, 0.25, 0.0, 1, jitter=0.1, seed=2), 2)
     m = nl.mesh_from(mesh)
     assert m.order() == (2, 9)
+    assert nl.mesh_from(_q(structured_mesh(2, 3, 1 / 3, 0.0, 1), 3)).order() == (3, 8)
     coords, conn, eio, nf = m.export()
     assert np.array_equal(coords, mesh.coords) and np.array_equal(conn, mesh.conn)
     assert np.array_equal(eio, mesh.elem_in_omega) and np.array_equal(nf, mesh.node_free)
@@ -95,7 +102,7 @@ def test_quad_mesh_round_trip_and_validation():
         nl.nl_mesh_create_quad(2, moved, mesh.conn, mesh.elem_in_omega, mesh.node_free)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_quad_mixed_precision_runs_fp32(order):
     mesh = _q(structured_mesh(2, 6, 1 / 6, 0.0, 2, jitter=0.1, seed=6), order)
     delta, eps = 0.3, 0.03
@@ -123,11 +130,13 @@ def _gpu_solve(mesh, w, L_max, eps, ms, precision=nl.NL_PREC_FP64):
     return u
 
 
-def test_table1_quad_on_gpu():
-    # Table 1, QUAD (Q2 consistency; the forcing is constant, its Q2 interpolant exact): the
-    # printed errors to 0.2 % at L_max = 3, 4, and the oracle's dense solution to 1e-9
+@pytest.mark.parametrize("order", [2, 3])
+def test_table1_quad_on_gpu(order):
+    # Table 1, QUAD (quadratic consistency, Q2 and the serendipity element; the forcing is
+    # constant, its interpolant exact): the printed errors to 0.2 % at L_max = 3, 4, and the
+    # oracle's dense solution to 1e-9
     w = table2_tri(2)
-    mesh = _q(workload_mesh(w), 2)
+    mesh = _q(workload_mesh(w), order)
     gold = {3: 8.123e-5, 4: 1.278e-5}
     for L in (3, 4):
         eps = 0.0125 * 0.75 ** (L - 3)

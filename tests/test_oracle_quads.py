@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from nl_inputs import q2_mesh, quad_mesh, structured_mesh, workload_mesh
+from nl_inputs import q2_mesh, quad_mesh, s2_mesh, structured_mesh, workload_mesh
 from nl_inputs.configs import table2_tri, table3_tri
 from nl_inputs.mesh import Mesh
 
@@ -26,13 +26,16 @@ def _golden(name, col=1):
 
 
 def _quads(w, order=1):
+    # order 1: Q1, 2: Q2, 3: the 8-node serendipity element
     m = quad_mesh(workload_mesh(w))
-    return q2_mesh(m) if order == 2 else m
+    if order == 1:
+        return m
+    return q2_mesh(m) if order == 2 else s2_mesh(q2_mesh(m))
 
 
 # ---- geometry and rule ------------------------------------------------------------------------
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_l2_norm_of_a_quadratic_over_jittered_quadrilaterals(order):
     # ||x^2 + y^2||_{L2} over the meshed box, through the error routine with u_h = 0: the
     # bilinear maps of the jittered cells tile the box exactly (boundary vertices stay), and
@@ -88,6 +91,18 @@ def _lagrange1d(order, s):
 
 
 def _qbasis(order, s, t):
+    if order == 3:  # serendipity: corners and edge midpoints of [-1, 1]^2
+        xi, eta = 2 * s - 1, 2 * t - 1
+        nd = [(-1, -1), (1, -1), (1, 1), (-1, 1), (0, -1), (1, 0), (0, 1), (-1, 0)]
+        out = []
+        for xa, ya in nd:
+            if xa != 0 and ya != 0:
+                out.append((1 + xi * xa) * (1 + eta * ya) * (xi * xa + eta * ya - 1) / 4)
+            elif xa == 0:
+                out.append((1 - xi * xi) * (1 + eta * ya) / 2)
+            else:
+                out.append((1 + xi * xa) * (1 - eta * eta) / 2)
+        return np.stack(out, -1)
     Ls, Lt = _lagrange1d(order, s), _lagrange1d(order, t)
     ij = [(0, 0), (1, 0), (1, 1), (0, 1)] if order == 1 else \
         [(0, 0), (2, 0), (2, 2), (0, 2), (1, 0), (2, 1), (1, 2), (0, 1), (1, 1)]
@@ -124,7 +139,7 @@ def _uniform_quad_blocks(Vl, Vm, order, delta, eps, C, depth):
     return 2 * np.einsum("xy,ya,yb->ab", G, PM, PM), -2 * np.einsum("xy,ya,xc->ac", G, PM, PL)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("offset", [0.17, 0.205, 0.215])
 def test_algorithm1_quads_equal_uniform_refinement(order, offset):
     # Constant kernel: Algorithm 1 at L_max = L and uniform refinement of l's unit square to
@@ -136,17 +151,16 @@ def test_algorithm1_quads_equal_uniform_refinement(order, offset):
     Vl = np.array([[offset, 0.02], [offset + 0.05, 0.0], [offset + 0.06, 0.055], [offset + 0.01, 0.06]])
     coords = np.concatenate([Vm, Vl]).T.copy()
     conn = np.array([[0, 1, 2, 3], [4, 5, 6, 7]], np.int32)
-    nb = 4
-    if order == 2:
+    if order >= 2:
+        ne = 5 if order == 2 else 4  # Q2: edge midpoints and centre; serendipity: edges only
         extra, cz = [], []
         for e, V in enumerate((Vm, Vl)):
             mids = [(V[0] + V[1]) / 2, (V[1] + V[2]) / 2, (V[2] + V[3]) / 2, (V[3] + V[0]) / 2,
-                    ((V[0] + V[1]) / 2 + (V[2] + V[3]) / 2) / 2]
-            cz.append(list(conn[e]) + [8 + 5 * e + k for k in range(5)])
+                    ((V[0] + V[1]) / 2 + (V[2] + V[3]) / 2) / 2][:ne]
+            cz.append(list(conn[e]) + [8 + ne * e + k for k in range(ne)])
             extra += mids
         coords = np.concatenate([np.concatenate([Vm, Vl]), np.array(extra)]).T.copy()
         conn = np.array(cz, np.int32)
-        nb = 9
     nn = coords.shape[1]
     mesh = Mesh(dim=2, coords=coords, conn=conn, elem_in_omega=np.ones(2, np.uint8),
                 node_free=np.ones(nn, np.uint8), h=0.05)
@@ -168,9 +182,9 @@ def test_algorithm1_quads_equal_uniform_refinement(order, offset):
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (order, L)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_quad_zero_row_sums_symmetry_and_linear_consistency(order):
-    # the Q1 / Q2 basis sums to one, so every row sums to zero; at L_max = 1 the inner and
+    # the Q1 / Q2 / serendipity basis sums to one, so every row sums to zero; at L_max = 1 the inner and
     # outer rules coincide and A is symmetric; u = 1 + x + y (f = 0) is reproduced
     w = table2_tri(2).with_(jitter=0.15, seed=5)
     m = _quads(w, order)
@@ -188,13 +202,16 @@ def test_quad_zero_row_sums_symmetry_and_linear_consistency(order):
 
 # ---- the printed QUAD columns of Sec. 6 ---------------------------------------------------------
 
+@pytest.mark.parametrize("order", [2, 3])
 @pytest.mark.parametrize("L_max", [3, 4])
-def test_table1_quad_consistency(L_max):
-    # Table 1, QUAD (Q2, u = x^2 + y^2 in the FE space, h = 0.1, delta = 0.2, eps = 0.0125
-    # (3/4)^(L_max - 3)): only the integration and mollifier errors remain; printed 8.123e-5,
-    # 1.278e-5 (and 3.453e-7 at L_max = 5, reproduced to 3.4544e-7, 10 s, not in the suite)
+def test_table1_quad_consistency(L_max, order):
+    # Table 1, QUAD (quadratic FE, u = x^2 + y^2 in the FE space, h = 0.1, delta = 0.2,
+    # eps = 0.0125 (3/4)^(L_max - 3)): only the integration and mollifier errors remain;
+    # printed 8.123e-5, 1.278e-5 (and 3.453e-7 at L_max = 5, reproduced by Q2 to 3.4544e-7,
+    # 10 s, not in the suite).  The serendipity element contains u as well and gives the same
+    # errors to 0.02 %.
     gold = _golden("table1_quad_quadratic.txt")
-    m2 = _quads(table2_tri(2), 2)
+    m2 = _quads(table2_tri(2), order)
     eps = 0.0125 * 0.75 ** (L_max - 3)
     err = O.solve_problem(m2, 0.2, eps, L_max, 1)["err_all"]
     assert abs(err / gold[L_max] - 1) < 2e-3, err
