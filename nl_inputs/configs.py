@@ -10,7 +10,7 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, replace
 
-from .mesh import Mesh, p2_mesh, q2_mesh, quad_mesh, structured_mesh
+from .mesh import Mesh, hex_mesh, p2_mesh, q2_mesh, quad_mesh, structured_mesh
 
 KERNEL_CONST = 0
 KERNEL_GAUSS = 1
@@ -65,6 +65,17 @@ def table2_tri(ml: int) -> Workload:
                     ms=MS_CUBIC, layer_cells=2 * s)
 
 
+def table7_hex(ml: int) -> Workload:
+    """Sec. 6, Table 7 (3D h-convergence, u = x^3 + y^3 + z^3): Omega = [-0.6, 0.6] x
+    [-0.4, 0.4] x [-0.4, 0.4], h = 0.2 (1/2)^(ml-1), delta = 0.2, eps = 0.01875 (2/3)^(ml-1),
+    L_min = 1, L_max = 2, one hexahedron per grid cell (Q1); the layer Gamma is meshed delta
+    wide (2^(ml-1) cells), as for the 2D tables."""
+    s = 2 ** (ml - 1)
+    return Workload(name=f"table7_hex_ml{ml}", dim=3, cells=(6 * s, 4 * s, 4 * s), h=0.2 / s,
+                    lo=(-0.6, -0.4, -0.4), delta=0.2, eps=0.01875 * (2.0 / 3.0) ** (ml - 1),
+                    L_max=2, ms=MS_CUBIC, layer_cells=s, cell="hex")
+
+
 def table3_tri(ml: int) -> Workload:
     """Sec. 6, Table 3: the setting of Table 2 with u = x^4 + y^4."""
     return table2_tri(ml).with_(name=f"table3_tri_ml{ml}", ms=MS_QUARTIC)
@@ -111,4 +122,6 @@ def workload_mesh(w: Workload) -> Mesh:
     if w.cell == "quad":
         q = quad_mesh(m)
         return q2_mesh(q) if w.order == 2 else q
+    if w.cell == "hex":
+        return hex_mesh(m)
     return p2_mesh(m) if w.order == 2 else m

@@ -211,3 +211,24 @@ def s2_mesh(mesh: Mesh) -> Mesh:
     return Mesh(dim=2, coords=np.ascontiguousarray(mesh.coords[:, :n_keep]),
                 conn=np.ascontiguousarray(mesh.conn[:, :8]), elem_in_omega=mesh.elem_in_omega.copy(),
                 node_free=mesh.node_free[:n_keep].copy(), h=mesh.h, meta=dict(mesh.meta, order=3))
+
+
+def hex_mesh(mesh: Mesh) -> Mesh:
+    """The hexahedral (Q1) mesh of the cells of a structured 3D mesh: the same vertices, one
+    element per cell with vertices (v000, v100, v110, v010, v001, v101, v111, v011) (the
+    images of the unit cube's corners (0,0,0), (1,0,0), (1,1,0), (0,1,0), (0,0,1), (1,0,1),
+    (1,1,1), (0,1,1)); a cell of Omega is an element of Omega."""
+    if mesh.dim != 3 or mesh.conn.shape[1] != 4:
+        raise ValueError("hexahedral meshes are built from structured P1 tetrahedral meshes")
+    cells, layer = mesh.meta["cells"], mesh.meta["layer"]
+    nc = [c + 2 * layer for c in cells]
+    nl = [c + 1 for c in nc]
+    stride = [1, nl[0], nl[0] * nl[1]]
+    cidx = np.indices(nc[::-1]).reshape(3, -1)[::-1]  # x fastest, the order of the tetrahedra
+    base = sum(cidx[k] * stride[k] for k in range(3))
+    corners = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    conn = np.stack([base + sum(c[k] * stride[k] for k in range(3)) for c in corners], 1).astype(np.int32)
+    assert np.array_equal(conn[:, 0], mesh.conn[::6, 0]) and np.array_equal(conn[:, 6], mesh.conn[::6, 3])
+    eio = mesh.elem_in_omega[::6].copy()
+    return Mesh(dim=3, coords=mesh.coords.copy(), conn=np.ascontiguousarray(conn), elem_in_omega=eio,
+                node_free=mesh.node_free.copy(), h=mesh.h, meta=dict(mesh.meta, cell="hex"))

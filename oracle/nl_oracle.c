@@ -388,11 +388,33 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
 /* Nodes per element: P1 simplices dim+1; P2 triangles 6 (the vertices, then the midpoints of
  * the edges (0,1), (1,2), (0,2)). */
 static int npe(const or_mesh* M) {
+  if (M->cell == 2) return 8;
   if (M->cell == 1) return (M->order == 2) ? 9 : (M->order == 3) ? 8 : 4;
   return (M->order == 2) ? 6 : M->dim + 1;
 }
-/* Vertices per element: simplices dim+1, quadrilaterals 4. */
+/* Vertices per element: simplices dim+1, quadrilaterals 4 (hexahedra 8: hex_verts). */
 static int nverts(const or_mesh* M) { return (M->cell == 1) ? 4 : M->dim + 1; }
+
+/* The 8 vertices of hexahedron e and their box. */
+static void hex_verts(const or_mesh* M, int64_t e, double V[8][3]) {
+  for (int a = 0; a < 8; a++) {
+    int64_t v = M->conn[e * 8 + a];
+    for (int k = 0; k < 3; k++) V[a][k] = M->coords[k * M->n_vert + v];
+  }
+}
+static void hex_bbox(const double V[8][3], double* lo, double* hi) {
+  for (int k = 0; k < 3; k++) {
+    lo[k] = V[0][k];
+    hi[k] = V[0][k];
+    for (int a = 1; a < 8; a++) {
+      if (V[a][k] < lo[k]) lo[k] = V[a][k];
+      if (V[a][k] > hi[k]) hi[k] = V[a][k];
+    }
+  }
+}
+
+/* The box of element e (any cell kind). */
+static void elem_box(const or_mesh* M, int64_t e, double* lo, double* hi);
 
 /* The element's Lagrange basis at the point with barycentric coordinates lam: P1 the
  * barycentric coordinates; P2 (triangles) lam_a (2 lam_a - 1) at the vertices and
@@ -427,6 +449,18 @@ static void verts_bbox(int dim, int nvx, const double V[4][3], double* lo, doubl
       if (V[a][k] > hi[k]) hi[k] = V[a][k];
     }
   }
+}
+
+static void elem_box(const or_mesh* M, int64_t e, double* lo, double* hi) {
+  if (M->cell == 2) {
+    double H[8][3];
+    hex_verts(M, e, H);
+    hex_bbox(H, lo, hi);
+    return;
+  }
+  double V[4][3];
+  elem_verts(M, e, V);
+  verts_bbox(M->dim, nverts(M), V, lo, hi);
 }
 
 /* |det[v1-v0, ..., vn-v0]| / n! */
@@ -525,11 +559,7 @@ int64_t or_pairs(const or_mesh* M, double delta, double eps, int64_t* pair_off, 
     free(hi);
     return -1;
   }
-  for (int64_t e = 0; e < n; e++) {
-    double V[4][3];
-    elem_verts(M, e, V);
-    verts_bbox(dim, nverts(M), V, lo + 3 * e, hi + 3 * e);
-  }
+  for (int64_t e = 0; e < n; e++) elem_box(M, e, lo + 3 * e, hi + 3 * e);
   double reach = delta + eps;
   int64_t cnt = 0;
   for (int64_t m = 0; m < n; m++) {
@@ -968,6 +998,198 @@ static void adaptive_integration_quad(actx* c, int L_cur, const qsub* E, const i
   free(Jref);
 }
 
+/* ------------------------------------------------------------------------------------
+ * Hexahedra (Sec. 6: the HEX meshes of the three-dimensional tests; the Gauss-Legendre
+ * 3x3x3 product rule for both integrals; Q1 trilinear elements).  An element is the image
+ * of the unit cube under the trilinear map F(s,t,u) = sum_a N_a(s,t,u) v_a; a sub-element of
+ * Algorithm 1 is the image of a sub-cube [s0, s0+len] x [t0, t0+len] x [u0, u0+len].  The
+ * physical vertices of the eight children come from the parent's by midpoints on the lattice
+ * of half-steps: a lattice point with a middle index is the midpoint of its two neighbours
+ * along the first such axis (x, then y, then z), so edge midpoints are (a+b)*0.5 of two
+ * vertices, face centres the midpoints of two edge midpoints, the centre the midpoint of
+ * two face centres. */
+typedef struct {
+  double V[8][3];
+  double s0, t0, u0, len;
+} hsub;
+
+static const int hex_corner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                     {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+
+/* Trilinear basis N_a(s,t,u) and x = F(s,t,u), |det DF(s,t,u)|. */
+static void hex_map(const double V[8][3], double s, double t, double u, double* x, double* detJ,
+                    double* N) {
+  double J[3][3] = {{0}};
+  for (int k = 0; k < 3; k++) x[k] = 0.0;
+  for (int a = 0; a < 8; a++) {
+    const int* c = hex_corner[a];
+    double fs = c[0] ? s : 1.0 - s, ft = c[1] ? t : 1.0 - t, fu = c[2] ? u : 1.0 - u;
+    double ds = c[0] ? 1.0 : -1.0, dt = c[1] ? 1.0 : -1.0, du = c[2] ? 1.0 : -1.0;
+    N[a] = fs * ft * fu;
+    for (int k = 0; k < 3; k++) {
+      x[k] += N[a] * V[a][k];
+      J[k][0] += ds * ft * fu * V[a][k];
+      J[k][1] += fs * dt * fu * V[a][k];
+      J[k][2] += fs * ft * du * V[a][k];
+    }
+  }
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  *detJ = fabs(det);
+}
+
+/* The lattice point (i, j, k) in {0, 1, 2}^3 of the hexahedron V (see above). */
+static void hex_lattice(const double V[8][3], int i, int j, int k, double* out) {
+  double a[3], b[3];
+  if (i == 1) {
+    hex_lattice(V, 0, j, k, a);
+    hex_lattice(V, 2, j, k, b);
+    midpoint(a, b, out);
+  } else if (j == 1) {
+    hex_lattice(V, i, 0, k, a);
+    hex_lattice(V, i, 2, k, b);
+    midpoint(a, b, out);
+  } else if (k == 1) {
+    hex_lattice(V, i, j, 0, a);
+    hex_lattice(V, i, j, 2, b);
+    midpoint(a, b, out);
+  } else {
+    for (int v = 0; v < 8; v++)
+      if (2 * hex_corner[v][0] == i && 2 * hex_corner[v][1] == j && 2 * hex_corner[v][2] == k)
+        for (int q = 0; q < 3; q++) out[q] = V[v][q];
+  }
+}
+
+/* The eight children (sub-cubes (cx, cy, cz), child index cx + 2 cy + 4 cz). */
+static void hex_split(const hsub* E, hsub C[8]) {
+  double L[3][3][3][3];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++) hex_lattice(E->V, i, j, k, L[i][j][k]);
+  const double h = 0.5 * E->len;
+  for (int c = 0; c < 8; c++) {
+    int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    for (int a = 0; a < 8; a++)
+      for (int q = 0; q < 3; q++)
+        C[c].V[a][q] = L[cx + hex_corner[a][0]][cy + hex_corner[a][1]][cz + hex_corner[a][2]][q];
+    C[c].s0 = E->s0 + cx * h;
+    C[c].t0 = E->t0 + cy * h;
+    C[c].u0 = E->u0 + cz * h;
+    C[c].len = h;
+  }
+}
+
+/* Integration(E', J') on a hexahedral sub-element (the sums of integration() with the 3x3x3
+ * rule on the sub-cube of l's cube and on m's cube). */
+static void integration_hex(actx* c, const hsub* E, const int32_t* J, int64_t nJ,
+                            const double Vl[8][3]) {
+  const or_params* P = c->P;
+  double g[3], gw[3];
+  gl3_unit(g, gw);
+  double xq[27][3], wx[27], phil[27][8], gq[27][3], gwq[27];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++)
+      for (int k = 0; k < 3; k++) {
+        int q = 9 * i + 3 * j + k;
+        gq[q][0] = g[i];
+        gq[q][1] = g[j];
+        gq[q][2] = g[k];
+        gwq[q] = gw[i] * gw[j] * gw[k];
+        double det;
+        hex_map(Vl, E->s0 + E->len * g[i], E->t0 + E->len * g[j], E->u0 + E->len * g[k], xq[q],
+                &det, phil[q]);
+        wx[q] = gwq[q] * E->len * E->len * E->len * det;
+      }
+  for (int64_t tt = 0; tt < nJ; tt++) {
+    int64_t m = J[tt];
+    double Vm[8][3];
+    hex_verts(c->M, m, Vm);
+    double S[8][8] = {{0}}, X[8][8] = {{0}};
+    for (int p = 0; p < 27; p++) {
+      double y[3], detm, phim[8];
+      hex_map(Vm, gq[p][0], gq[p][1], gq[p][2], y, &detm, phim);
+      double wy = gwq[p] * detm;
+      for (int q = 0; q < 27; q++) {
+        double r2 = 0.0;
+        for (int k = 0; k < 3; k++) r2 += (xq[q][k] - y[k]) * (xq[q][k] - y[k]);
+        double r = sqrt(r2);
+        double G = wx[q] * wy * P->C * or_eta(P->kernel, r, P->delta) * or_mu(r, P->delta, P->eps);
+        c->st->n_point_pairs++;
+        if (r >= P->delta - P->eps && r <= P->delta + P->eps) c->st->n_band_pairs++;
+        for (int a = 0; a < 8; a++) {
+          for (int b = 0; b < 8; b++) S[a][b] += G * phim[a] * phim[b];
+          for (int d = 0; d < 8; d++) X[a][d] += G * phim[a] * phil[q][d];
+        }
+      }
+    }
+    c->st->n_integrations++;
+    for (int a = 0; a < 8; a++) {
+      int64_t i = c->M->conn[m * 8 + a];
+      for (int b = 0; b < 8; b++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * 8 + b]);
+        if (!e) {
+          c->error = 1;
+          continue;
+        }
+        *e += 2.0 * S[a][b];
+      }
+      for (int d = 0; d < 8; d++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * 8 + d]);
+        if (!e) {
+          c->error = 1;
+          continue;
+        }
+        *e -= 2.0 * X[a][d];
+      }
+    }
+  }
+}
+
+/* Algorithm 1 on a hexahedral sub-element. */
+static void adaptive_integration_hex(actx* c, int L_cur, const hsub* E, const int32_t* J,
+                                     int64_t nJ, const double Vl[8][3]) {
+  const or_params* P = c->P;
+  if (L_cur < P->L_min) {
+    hsub C[8];
+    hex_split(E, C);
+    for (int i = 0; i < 8; i++) adaptive_integration_hex(c, L_cur + 1, &C[i], J, nJ, Vl);
+    return;
+  }
+  if (L_cur == P->L_max) {
+    integration_hex(c, E, J, nJ, Vl);
+    return;
+  }
+  int32_t* Jint = (int32_t*)malloc(sizeof(int32_t) * (nJ + 1));
+  int32_t* Jref = (int32_t*)malloc(sizeof(int32_t) * (nJ + 1));
+  if (!Jint || !Jref) {
+    free(Jint), free(Jref);
+    c->error = 1;
+    return;
+  }
+  int64_t nint = 0, nref = 0;
+  double lo[3], hi[3];
+  hex_bbox(E->V, lo, hi);
+  for (int64_t t = 0; t < nJ; t++) {
+    int64_t m = J[t];
+    double amin = (P->flags & OR_MINDIST_L2)
+                      ? or_aprx_min_dist_l2(3, lo, hi, c->lo + 3 * m, c->hi + 3 * m)
+                      : or_aprx_min_dist(3, lo, hi, c->lo + 3 * m, c->hi + 3 * m);
+    if (or_aprx_max_dist(3, lo, hi, c->lo + 3 * m, c->hi + 3 * m) < P->delta - P->eps)
+      Jint[nint++] = (int32_t)m;
+    else if (amin < P->delta + P->eps)
+      Jref[nref++] = (int32_t)m;
+  }
+  if (nint > 0) integration_hex(c, E, Jint, nint, Vl);
+  if (nref > 0) {
+    hsub C[8];
+    hex_split(E, C);
+    for (int i = 0; i < 8; i++) adaptive_integration_hex(c, L_cur + 1, &C[i], Jref, nref, Vl);
+  }
+  free(Jint);
+  free(Jref);
+}
+
 int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l,
                 const or_params* P, const int64_t* row_ptr, const int32_t* col, double* values,
                 const uint8_t* m_mask, or_stats* stats) {
@@ -975,6 +1197,7 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
   int64_t nE = M->n_elem, nV = M->n_vert;
   if (dim != 2 && dim != 3) return -1;
   if (M->cell == 1 && dim != 2) return -1; /* quadrilaterals: dim 2 */
+  if (M->cell == 2 && (dim != 3 || M->order != 1)) return -1; /* hexahedra: Q1, dim 3 */
   if (!(P->eps > 0.0 && P->eps < P->delta) || P->L_min < 1 || P->L_max < P->L_min) return -1;
   actx c;
   memset(&c, 0, sizeof c);
@@ -1002,11 +1225,7 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
     free(lo), free(hi), free(toff), free(fillp), free(tm);
     return -1;
   }
-  for (int64_t e = 0; e < nE; e++) {
-    double V[4][3];
-    elem_verts(M, e, V);
-    verts_bbox(dim, nverts(M), V, lo + 3 * e, hi + 3 * e);
-  }
+  for (int64_t e = 0; e < nE; e++) elem_box(M, e, lo + 3 * e, hi + 3 * e);
   for (int64_t m = 0; m < nE; m++) {
     if (m_mask && !m_mask[m]) continue;
     for (int64_t p = pair_off[m]; p < pair_off[m + 1]; p++) toff[pair_l[p] + 1]++;
@@ -1030,6 +1249,14 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
     int64_t nJ = toff[l + 1] - toff[l];
     if (nJ == 0) continue;
     c.l = l;
+    if (M->cell == 2) {
+      hsub root;
+      hex_verts(M, l, root.V);
+      root.s0 = root.t0 = root.u0 = 0.0;
+      root.len = 1.0;
+      adaptive_integration_hex(&c, 1, &root, tm + toff[l], nJ, root.V);
+      continue;
+    }
     elem_verts(M, l, c.Vl);
     if (M->cell == 1) {
       qsub root;
@@ -1098,6 +1325,23 @@ int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const d
   for (int64_t i = 0; i < M->n_vert; i++) F[i] = 0.0;
   for (int64_t e = 0; e < M->n_elem; e++) {
     if (!M->elem_in_omega[e]) continue;
+    if (M->cell == 2) { /* Gauss-Legendre 3x3x3 on the image of the unit cube */
+      double H[8][3], g[3], gw[3];
+      hex_verts(M, e, H);
+      gl3_unit(g, gw);
+      for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++)
+          for (int k = 0; k < 3; k++) {
+            double x[3], det, phi[8];
+            hex_map(H, g[i], g[j], g[k], x, &det, phi);
+            double f = or_ms_f(ms, dim, x, kernel, delta, eps, C);
+            for (int a = 0; a < 8; a++) {
+              int64_t n = M->conn[e * 8 + a];
+              if (M->node_free[n]) F[n] += gw[i] * gw[j] * gw[k] * det * f * phi[a];
+            }
+          }
+      continue;
+    }
     double V[4][3];
     elem_verts(M, e, V);
     if (M->cell == 1) { /* Gauss-Legendre 3x3 on the image of the unit square */
@@ -1236,6 +1480,26 @@ static double err_on_quad(const or_mesh* M, const double V[4][3], const double* 
   return s;
 }
 
+/* The same on a hexahedron: Gauss-Legendre 3x3x3 on each of the 2 x 2 x 2 sub-cubes of the
+ * unit cube, mapped by the element's trilinear map. */
+static double err_on_hex(const or_mesh* M, const double V[8][3], const double* nodal, int ms) {
+  double g[3], gw[3], s = 0.0;
+  gl3_unit(g, gw);
+  for (int b = 0; b < 8; b++)
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++)
+        for (int k = 0; k < 3; k++) {
+          double u = 0.5 * ((b & 1) + g[i]), v = 0.5 * (((b >> 1) & 1) + g[j]);
+          double w = 0.5 * (((b >> 2) & 1) + g[k]), x[3], det, phi[8];
+          hex_map(V, u, v, w, x, &det, phi);
+          double uh = 0.0;
+          for (int a = 0; a < 8; a++) uh += phi[a] * nodal[a];
+          double d = or_ms_u(ms, M->dim, x) - uh;
+          s += 0.125 * gw[i] * gw[j] * gw[k] * det * d * d;
+        }
+  return s;
+}
+
 double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) {
   int dim = M->dim, nv = dim + 1;
   double b[64], w[16], bary[16][4];
@@ -1246,6 +1510,13 @@ double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) 
   double s = 0.0;
   for (int64_t e = 0; e < M->n_elem; e++) {
     if (omega_only && !M->elem_in_omega[e]) continue;
+    if (M->cell == 2) {
+      double H[8][3], hn[8];
+      hex_verts(M, e, H);
+      for (int a = 0; a < 8; a++) hn[a] = u_h[M->conn[e * 8 + a]];
+      s += err_on_hex(M, H, hn, ms);
+      continue;
+    }
     double V[4][3], nodal[9];
     elem_verts(M, e, V);
     for (int a = 0; a < npe(M); a++) nodal[a] = u_h[M->conn[e * npe(M) + a]];

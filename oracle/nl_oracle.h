@@ -44,7 +44,10 @@ typedef struct {
                                    Q1 (the four vertices), order 2: Q2 (the vertices, the
                                    midpoints of the edges (0,1), (1,2), (2,3), (3,0), then the
                                    image of the square's centre), order 3: the 8-node
-                                   serendipity element (the Q2 nodes without the centre) */
+                                   serendipity element (the Q2 nodes without the centre);
+                                   2: hexahedra (dim 3), Q1 (trilinear), vertices the images of
+                                   the unit cube's corners (0,0,0), (1,0,0), (1,1,0), (0,1,0),
+                                   (0,0,1), (1,0,1), (1,1,1), (0,1,1) */
 } or_mesh;
 
 /* or_params.flags: the refinement test of Algorithm 1 uses the Euclidean variant of the

@@ -1,0 +1,157 @@
+"""The oracle's hexahedra (Sec. 6, the three-dimensional tests: HEX meshes, Q1 trilinear
+elements, the Gauss-Legendre 3x3x3 rule for both integrals) against what the paper and the
+mathematics fix: the printed HEX linear column of Table 7, exact integrals, closed-form local
+matrices of fully-interior pairs, Algorithm 1 against brute-force uniform refinement, zero row
+sums, symmetry at one level and linear consistency.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from nl_inputs import hex_mesh, structured_mesh
+from nl_inputs.configs import table7_hex, workload_mesh
+from nl_inputs.mesh import Mesh
+
+CORNERS = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+
+
+def test_l2_norm_of_a_linear_function_over_jittered_hexahedra():
+    # ||1 + x + y + z||_{L2} over the meshed box through the error routine with u_h = 0: the
+    # trilinear maps of the jittered cells tile the box exactly, and Gauss-Legendre 3x3x3
+    # integrates (1 + x + y + z)^2 |det DF| exactly (degree <= 4 per reference variable)
+    m = hex_mesh(structured_mesh(3, 3, 1 / 3, 0.0, 1, jitter=0.2, seed=4))
+    a, b = -1 / 3, 4 / 3
+
+    def I(p):
+        return (b ** (p + 1) - a ** (p + 1)) / (p + 1)
+    L = b - a
+    # int (1 + x + y + z)^2 = int 1 + 2 sum x_k + sum x_k^2 + 2 sum_{k<j} x_k x_j over the cube
+    exact = L ** 3 + 2 * 3 * I(1) * L ** 2 + 3 * I(2) * L ** 2 + 2 * 3 * I(1) ** 2 * L
+    got = O.l2_error(m, np.zeros(m.n_vert), 0, omega_only=False)
+    assert abs(got ** 2 / exact - 1) < 1e-13
+
+
+def test_fully_interior_hex_pairs_closed_form():
+    # two h-cubes far inside delta - eps of each other: mu = 1 at every point pair and A is
+    # the closed form of the constant kernel with the Q1 mass matrix of a cube,
+    # M(a,b) = (h/6)^3 prod_k (2 if a_k = b_k else 1), and int phi_a = h^3 / 8
+    h, delta, eps = 0.05, 1.0, 0.1
+    cube = np.array(CORNERS, float) * h
+    coords = np.concatenate([cube, cube + [0.3, 0.1, 0.05]]).T.copy()
+    mesh = Mesh(dim=3, coords=coords, conn=np.arange(16, dtype=np.int32).reshape(2, 8),
+                elem_in_omega=np.ones(2, np.uint8), node_free=np.ones(16, np.uint8), h=h)
+    off, pl = O.pairs(mesh, delta, eps)
+    rp, col = O.csr(mesh, off, pl)
+    C = O.kernel_constant(3, O.KERNEL_CONST, delta, eps)
+    M = np.array([[np.prod([2 if CORNERS[a][k] == CORNERS[b][k] else 1 for k in range(3)])
+                   for b in range(8)] for a in range(8)]) * (h / 6) ** 3
+    ref = np.zeros((16, 16))
+    for mm in range(2):
+        for ll in range(2):
+            nm, nl = np.arange(8) + 8 * mm, np.arange(8) + 8 * ll
+            ref[np.ix_(nm, nm)] += 2 * C * h ** 3 * M
+            ref[np.ix_(nm, nl)] -= 2 * C * (h ** 3 / 8) ** 2
+    for L in (1, 2):
+        vals, st = O.assemble(mesh, off, pl, rp, col, delta, eps, L)
+        got = np.zeros((16, 16))
+        for i in range(16):
+            got[i, col[rp[i]:rp[i + 1]]] = vals[rp[i]:rp[i + 1]]
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max(), L
+        assert st.n_integrations == 4 and st.n_point_pairs == 4 * 27 * 27 and st.n_band_pairs == 0
+
+
+def _trilinear(V, s, t, u):
+    """x = F(s,t,u), |det DF| and the Q1 basis at the points (s, t, u) of the hexahedron V."""
+    N, dN = [], []
+    for c in CORNERS:
+        fs, ft, fu = (s if c[0] else 1 - s), (t if c[1] else 1 - t), (u if c[2] else 1 - u)
+        ds, dt, du = (1 if c[0] else -1), (1 if c[1] else -1), (1 if c[2] else -1)
+        N.append(fs * ft * fu)
+        dN.append(np.stack([ds * ft * fu, fs * dt * fu, fs * ft * du], -1))
+    N, dN = np.stack(N, -1), np.stack(dN, -2)  # (n, 8), (n, 8, 3)
+    X = N @ V
+    J = np.einsum("nar,ak->nkr", dN, V)
+    return X, np.abs(np.linalg.det(J)), N
+
+
+def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth):
+    """Outer integral over E_l on the 8^depth sub-cubes of its unit cube (Gauss-Legendre
+    3x3x3 on each), inner 3x3x3 on E_m: the blocks 2 S and -2 X."""
+    x, w = np.polynomial.legendre.leggauss(3)
+    g, gw = (x + 1) / 2, w / 2
+    n = 2 ** depth
+    pts = np.array(list(itertools.product(range(n), range(n), range(n), range(3), range(3), range(3))))
+    s = (pts[:, 0] + g[pts[:, 3]]) / n
+    t = (pts[:, 1] + g[pts[:, 4]]) / n
+    u = (pts[:, 2] + g[pts[:, 5]]) / n
+    X, detl, PL = _trilinear(Vl, s, t, u)
+    WX = gw[pts[:, 3]] * gw[pts[:, 4]] * gw[pts[:, 5]] / n ** 3 * detl
+    q = np.array(list(itertools.product(range(3), range(3), range(3))))
+    Y, detm, PM = _trilinear(Vm, g[q[:, 0]], g[q[:, 1]], g[q[:, 2]])
+    WY = gw[q[:, 0]] * gw[q[:, 1]] * gw[q[:, 2]] * detm
+    R = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    MU = np.vectorize(lambda r: O.mu(r, delta, eps))(R)
+    G = WX[:, None] * WY[None, :] * C * MU
+    return 2 * np.einsum("xy,ya,yb->ab", G, PM, PM), -2 * np.einsum("xy,ya,xc->ac", G, PM, PL)
+
+
+@pytest.mark.parametrize("offset", [0.16, 0.205, 0.215])
+def test_algorithm1_hexes_equal_uniform_refinement(offset):
+    # Constant kernel: Algorithm 1 at L_max = L and uniform refinement of l's cube to level L
+    # give the same sums up to rounding (an INT sub-element's integrand phi^l_d |det DF_l| has
+    # degree <= 3 per reference variable; dropped sub-elements have mu = 0 at every point
+    # pair); general trilinear hexahedra, so the Jacobian varies
+    rng = np.random.default_rng(7)
+    base = np.array(CORNERS, float) * 0.05
+    Vm = base + rng.uniform(-0.006, 0.006, (8, 3))
+    Vl = base + [offset, 0.01, 0.0] + rng.uniform(-0.006, 0.006, (8, 3))
+    coords = np.concatenate([Vm, Vl]).T.copy()
+    mesh = Mesh(dim=3, coords=coords, conn=np.arange(16, dtype=np.int32).reshape(2, 8),
+                elem_in_omega=np.ones(2, np.uint8), node_free=np.ones(16, np.uint8), h=0.05)
+    delta, eps = 0.2, 0.01
+    C = O.kernel_constant(3, O.KERNEL_CONST, delta, eps)
+    off, pl = O.pairs(mesh, delta, eps)
+    assert len(pl) == 4
+    rp, col = O.csr(mesh, off, pl)
+    for L in (1, 2, 3):
+        vals, _ = O.assemble(mesh, off, pl, rp, col, delta, eps, L)
+        got = np.zeros((16, 16))
+        for i in range(16):
+            got[i, col[rp[i]:rp[i + 1]]] = vals[rp[i]:rp[i + 1]]
+        ref = np.zeros((16, 16))
+        for (mi, li) in ((0, 0), (0, 1), (1, 0), (1, 1)):
+            S2, X2 = _uniform_hex_blocks((Vm, Vl)[li], (Vm, Vl)[mi], delta, eps, C, L - 1)
+            nm, nl = np.arange(8) + 8 * mi, np.arange(8) + 8 * li
+            ref[np.ix_(nm, nm)] += S2
+            ref[np.ix_(nm, nl)] += X2
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), L
+
+
+def test_hex_zero_row_sums_symmetry_and_linear_consistency():
+    m = hex_mesh(structured_mesh(3, 3, 1 / 3, 0.0, 1, jitter=0.15, seed=5))
+    off, pl = O.pairs(m, 0.4, 0.04)
+    rp, col = O.csr(m, off, pl)
+    v1, _ = O.assemble(m, off, pl, rp, col, 0.4, 0.04, 1)
+    rows = np.repeat(np.arange(m.n_vert), np.diff(rp))
+    assert np.abs(np.bincount(rows, weights=v1, minlength=m.n_vert)).max() < 1e-12 * np.abs(v1).max()
+    import scipy.sparse as sp
+    A = sp.csr_matrix((v1, col, rp), shape=(m.n_vert, m.n_vert))
+    assert abs(A - A.T).max() < 1e-14 * np.abs(v1).max()
+    r = O.solve_problem(hex_mesh(structured_mesh(3, 3, 1 / 3, 0.0, 2)), 0.4, 0.04, 2, 0)
+    assert r["err_all"] < 1e-9
+
+
+def test_table7_hex_linear():
+    # Table 7, HEX linear, ml = 1 (h = 0.2): the printed error to 0.2 % (the oracle gives
+    # 2.2204e-2; ml = 2 takes minutes on one core and is not in the suite)
+    gold = {}
+    import os
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "table7_hex_linear.txt")):
+        if line.strip() and not line.startswith("#"):
+            parts = line.split()
+            gold[int(parts[0])] = float(parts[1])
+    w = table7_hex(1)
+    err = O.solve_problem(workload_mesh(w), w.delta, w.eps, w.L_max, w.ms)["err_all"]
+    assert abs(err / gold[1] - 1) < 2e-3, err
