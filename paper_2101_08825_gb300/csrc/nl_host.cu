@@ -400,6 +400,70 @@ __global__ void k_mesh_quads(int64_t n_elem, int64_t n_vert, const double* __res
   }
 }
 
+// Hexahedra (the trilinear image of the unit cube, vertices in the order (0,0,0), (1,0,0),
+// (1,1,0), (0,1,0), (0,0,1), (1,0,1), (1,1,1), (0,1,1)): the eight vertices, the box, the
+// volume (Gauss-Legendre 2x2x2 of |det DF|, exact: the determinant is of degree <= 2 in each
+// variable), no inverse Jacobian, and an FP32 record of its own layout: the offsets v_a - v_0
+// (a = 1..7) at [0, 21), v_0 as a float-float pair at [21, 24) and [24, 27), the volume at
+// [27].
+__global__ void k_mesh_hexes(int64_t n_elem, int64_t n_vert, const double* __restrict__ coords,
+                             const int32_t* __restrict__ conn, double* __restrict__ evert,
+                             double* __restrict__ blo, double* __restrict__ bhi,
+                             double* __restrict__ vol, double* __restrict__ jinv,
+                             float* __restrict__ ef) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  double V[8][3];
+  for (int a = 0; a < 8; a++) {
+    int32_t v = conn[e * 8 + a];
+    for (int k = 0; k < 3; k++) {
+      V[a][k] = coords[k * n_vert + v];
+      evert[(e * 8 + a) * 3 + k] = V[a][k];
+    }
+  }
+  for (int k = 0; k < 3; k++) {
+    double lo = V[0][k], hi = V[0][k];
+    for (int a = 1; a < 8; a++) {
+      lo = fmin(lo, V[a][k]);
+      hi = fmax(hi, V[a][k]);
+    }
+    blo[e * 3 + k] = lo;
+    bhi[e * 3 + k] = hi;
+  }
+  const int cc[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0}, {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+  const double g0 = 0.5 - 0.5 / sqrt(3.0), g1 = 0.5 + 0.5 / sqrt(3.0);
+  double v = 0.0;
+  for (int p = 0; p < 8; p++) {
+    const double s = (p & 1) ? g1 : g0, t = (p & 2) ? g1 : g0, u = (p & 4) ? g1 : g0;
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < 8; a++) {
+      const double fs = cc[a][0] ? s : 1.0 - s, ft = cc[a][1] ? t : 1.0 - t, fu = cc[a][2] ? u : 1.0 - u;
+      const double ds = cc[a][0] ? 1.0 : -1.0, dt = cc[a][1] ? 1.0 : -1.0, du = cc[a][2] ? 1.0 : -1.0;
+      for (int k = 0; k < 3; k++) {
+        J[k][0] += ds * ft * fu * V[a][k];
+        J[k][1] += fs * dt * fu * V[a][k];
+        J[k][2] += fs * ft * du * V[a][k];
+      }
+    }
+    const double d = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                     J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                     J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    v += 0.125 * fabs(d);
+  }
+  vol[e] = v;
+  for (int t = 0; t < 9; t++) jinv[e * 9 + t] = 0.0;
+  float* f = ef + e * NL_EF_STRIDE(3);
+  for (int a = 1; a < 8; a++)
+    for (int k = 0; k < 3; k++) f[(a - 1) * 3 + k] = (float)(V[a][k] - V[0][k]);
+  for (int k = 0; k < 3; k++) {
+    const float hi = (float)V[0][k];
+    f[21 + k] = hi;
+    f[24 + k] = (float)(V[0][k] - (double)hi);
+  }
+  f[27] = (float)v;
+  for (int t = 28; t < NL_EF_STRIDE(3); t++) f[t] = 0.f;
+}
+
 __global__ void k_count_n2e(int64_t n_entries, const int32_t* __restrict__ conn,
                             int32_t* __restrict__ cnt) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -453,18 +517,20 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
   if (order != 1 && !(order == 2 && dim == 2) && !(order == 3 && cell == 1))
     return fail(NL_EINVAL, "nl_mesh_create: P2 elements are triangles (dim 2) only");
   if (cell == 1 && dim != 2) return fail(NL_EINVAL, "nl_mesh_create_quad: quadrilaterals are 2D");
+  if (cell == 2 && (dim != 3 || order != 1))
+    return fail(NL_EINVAL, "nl_mesh_create_hex: Q1 hexahedra are 3D");
   if (n_vert <= 0 || n_vert > INT32_MAX || n_elem <= 0 || n_elem > INT32_MAX)
     return fail(NL_EINVAL, "nl_mesh_create: bad sizes n_vert=%lld n_elem=%lld",
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
-  const int nv = cell == 1 ? 4 : dim + 1;
-  const int nb = cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4)) : (order == 2 ? 6 : nv);
+  const int nv = cell == 1 ? 4 : (cell == 2 ? 8 : dim + 1);
+  const int nb = cell == 2 ? 8 : cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4)) : (order == 2 ? 6 : nv);
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
     if (!std::isfinite(coords[i])) return fail(NL_EINVAL, "nl_mesh_create: non-finite coordinate");
   double bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
   double max_ext = 0.0;
   for (int64_t e = 0; e < n_elem; e++) {
-    double V[4][3];
+    double V[8][3];
     for (int a = 0; a < nb; a++) {
       int32_t v = conn[e * nb + a];
       if (v < 0 || v >= n_vert) return fail(NL_EINVAL, "nl_mesh_create: vertex index out of range");
@@ -519,7 +585,33 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
       }
     }
     double det;
-    if (dim == 2) {
+    if (cell == 2) {
+      // the trilinear map keeps its orientation at every corner: the Jacobian there, the
+      // edges from the corner along s, t, u, has a positive determinant
+      static const int cc[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                   {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+      auto idx = [](int i, int j, int k) {
+        for (int a = 0; a < 8; a++)
+          if (cc[a][0] == i && cc[a][1] == j && cc[a][2] == k) return a;
+        return 0;
+      };
+      det = 1.0;
+      for (int a = 0; a < 8; a++) {
+        const int i = cc[a][0], j = cc[a][1], k = cc[a][2];
+        double E[3][3];
+        for (int q = 0; q < 3; q++) {
+          E[0][q] = V[idx(1, j, k)][q] - V[idx(0, j, k)][q];
+          E[1][q] = V[idx(i, 1, k)][q] - V[idx(i, 0, k)][q];
+          E[2][q] = V[idx(i, j, 1)][q] - V[idx(i, j, 0)][q];
+        }
+        const double d = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+                         E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+                         E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+        if (!(d > 0.0))
+          return fail(NL_EINVAL, "nl_mesh_create_hex: element %lld is inverted or degenerate at corner %d",
+                      (long long)e, a);
+      }
+    } else if (dim == 2) {
       det = (V[1][0] - V[0][0]) * (V[2][1] - V[0][1]) - (V[2][0] - V[0][0]) * (V[1][1] - V[0][1]);
     } else {
       double a[3], b[3], c[3];
@@ -596,7 +688,9 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
     return cleanup(cuda_fail(ce, "nl_mesh_create upload"));
   int tb = 256;
   int64_t gb = (n_elem + tb - 1) / tb;
-  if (cell == 1)
+  if (cell == 2)
+    k_mesh_hexes<<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
+  else if (cell == 1)
     k_mesh_quads<<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   else if (dim == 2)
     k_mesh_elements<2><<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
@@ -747,6 +841,14 @@ nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64
                             const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
   return mesh_create_impl(dim, 2, 0, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+                          cuda_stream, out);
+}
+
+nl_status nl_mesh_create_hex(int64_t n_vert, const double* coords, int64_t n_elem,
+                             const int32_t* conn, const uint8_t* elem_in_omega,
+                             const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
+  nlx::clear_error();
+  return mesh_create_impl(3, 1, 2, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
 }
 

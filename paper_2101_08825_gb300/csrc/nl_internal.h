@@ -177,7 +177,7 @@ struct nl_mesh {
   std::atomic<int> refs{1};
   int dim = 0;
   int order = 1;                   // 1: P1 / Q1, 2: P2 triangles / Q2 quadrilaterals
-  int cell = 0;                    // 0: simplices, 1: quadrilaterals (dim 2)
+  int cell = 0;                    // 0: simplices, 1: quadrilaterals (dim 2), 2: hexahedra (dim 3)
   int nb = 0;                      // nodes per element: dim+1 (P1) or 6 (P2)
   int64_t n_vert = 0, n_elem = 0;  // n_vert counts every node
   cudaStream_t stream = nullptr;
@@ -185,7 +185,7 @@ struct nl_mesh {
   int32_t* conn = nullptr;         // [n_elem][nb]: vertices first, then (P2) edge nodes
   uint8_t* elem_in_omega = nullptr;
   uint8_t* node_free = nullptr;
-  double* evert = nullptr;         // [n_elem][dim+1 or 4][dim] vertex coordinates per element
+  double* evert = nullptr;         // [n_elem][dim+1, 4 or 8][dim] vertex coordinates per element
   double* blo = nullptr;           // [n_elem][dim] bounding boxes
   double* bhi = nullptr;
   double* vol = nullptr;           // [n_elem]
@@ -243,6 +243,10 @@ nl_status build_pairs(nl_mesh* m, double delta, double eps, nl_pairs* out);
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st);
+// The same for meshes of hexahedra (nl_quad_hex.cu).
+nl_status assemble_values_hex(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                              const nl_quad_params* qp, nl_precision prec, double* values,
+                              nl_assemble_stats* st);
 // The same for meshes of quadrilaterals (nl_quad_quad.cu).
 nl_status assemble_values_quad(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                                const nl_quad_params* qp, nl_precision prec, double* values,

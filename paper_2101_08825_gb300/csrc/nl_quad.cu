@@ -24,9 +24,10 @@ nl_status ensure_device_tables() {
 nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                           const nl_quad_params* qp, nl_precision prec, double* values,
                           nl_assemble_stats* st) {
-  // quadrilaterals (nl_quad_quad.cu), P2 triangles (nl_quad_p2.cu; MIXED precisions run
+  // hexahedra (nl_quad_hex.cu), quadrilaterals (nl_quad_quad.cu), P2 triangles (nl_quad_p2.cu; MIXED precisions run
   // their FP32 paths) and the tensor-core variants (nl_quad_mma.cu) are compiled in
   // translation units of their own
+  if (m->cell == 2) return assemble_values_hex(m, p, kp, qp, prec, values, st);
   if (m->cell == 1) return assemble_values_quad(m, p, kp, qp, prec, values, st);
   if (m->order == 2) return assemble_values_p2(m, p, kp, qp, prec, values, st);
   if (prec == NL_PREC_MIXED_TF32 || prec == NL_PREC_MIXED_BF16)

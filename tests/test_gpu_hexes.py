@@ -1,0 +1,144 @@
+"""Hexahedra on the GPU (Sec. 6: the HEX meshes of the 3D tests, Q1 trilinear elements,
+Gauss-Legendre 3x3x3), through the C ABI, against the oracle on the same seeded meshes.
+
+Tolerances as for the other elements (test_gpu_parity): pair lists, CSR pattern and
+Algorithm-1 work counts bit-exact; A within 1e-12 relative (Frobenius, and per entry against
+the largest entry) in FP64 and 2e-6 in FP32.  Whole GPU path: Table 7's HEX linear error at
+ml = 1, and the oracle's dense solution to 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from nl_inputs import WORKLOADS, hex_mesh, structured_mesh, workload_mesh
+from nl_inputs.configs import table7_hex
+from paper_2101_08825_gb300 import nl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-6
+
+
+def _h(n, layer, jitter, seed):
+    return hex_mesh(structured_mesh(3, n, 1 / n, 0.0, layer, jitter=jitter, seed=seed))
+
+
+CASES = [
+    # (name, mesh factory, delta, eps, L_max, L_min, kernel, mindist_l2)
+    ("jit_L2", lambda: _h(3, 1, 0.15, 1), 0.4, 0.04, 2, 1, 0, False),
+    ("jit_L3", lambda: _h(3, 1, 0.1, 2), 0.35, 0.035, 3, 1, 0, False),
+    ("jit_L1", lambda: _h(3, 1, 0.1, 3), 0.4, 0.05, 1, 1, 0, False),
+    ("jit_Lmin2", lambda: _h(3, 1, 0.1, 4), 0.4, 0.05, 2, 2, 0, False),
+    ("gauss", lambda: _h(3, 1, 0.1, 5), 0.4, 0.02, 2, 1, 1, False),
+    ("euclid", lambda: _h(3, 1, 0.1, 6), 0.4, 0.04, 2, 1, 0, True),
+    ("t7_ml1", lambda: workload_mesh(table7_hex(1)), 0.2, 0.01875, 2, 1, 0, False),
+]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _maxrel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_hex_pairs_pattern_counts_and_values(case):
+    name, mk, delta, eps, L_max, L_min, kernel, l2 = case
+    mesh = mk()
+    off0, pl0 = O.pairs(mesh, delta, eps)
+    rp0, col0 = O.csr(mesh, off0, pl0)
+    v0, st0 = O.assemble(mesh, off0, pl0, rp0, col0, delta, eps, L_max, L_min, kernel, mindist_l2=l2)
+    m = nl.mesh_from(mesh)
+    assert m.order() == (1, 8)
+    p = nl.nl_pairs_build(m, delta, eps)
+    off, pl, rp, col = p.export(mesh.n_elem, mesh.n_vert)
+    assert np.array_equal(off, off0)
+    assert np.array_equal(pl, pl0)
+    assert np.array_equal(rp, rp0)
+    assert np.array_equal(col, col0)
+    for prec, tol in ((nl.NL_PREC_FP64, TOL64), (nl.NL_PREC_FP32, TOL32)):
+        A, st = nl.nl_assemble(m, p, delta, eps, L_max, L_min, kernel, prec, mindist_l2=l2)
+        vals = A.export()
+        assert st.precision_run == prec
+        assert st.n_items == st0.n_integrations, (name, prec)
+        assert st.n_point_pairs == st0.n_point_pairs, (name, prec)
+        assert st.n_eval_point_pairs + 729 * st.n_closed_items <= st.n_point_pairs
+        if kernel == 1:
+            assert st.n_closed_items == 0
+        assert _rel(vals, v0) < tol, (name, prec, _rel(vals, v0))
+        assert _maxrel(vals, v0) < tol, (name, prec, _maxrel(vals, v0))
+
+
+def test_hex_mesh_round_trip_and_validation():
+    mesh = _h(2, 1, 0.1, 7)
+    m = nl.mesh_from(mesh)
+    coords, conn, eio, nf = m.export()
+    assert np.array_equal(coords, mesh.coords) and np.array_equal(conn, mesh.conn)
+    assert np.array_equal(eio, mesh.elem_in_omega) and np.array_equal(nf, mesh.node_free)
+    bad = mesh.conn.copy()
+    bad[4] = bad[4][[1, 0, 3, 2, 5, 4, 7, 6]]  # mirrored: negative Jacobian
+    with pytest.raises(nl.NLError):
+        nl.nl_mesh_create_hex(mesh.coords, bad, mesh.elem_in_omega, mesh.node_free)
+
+
+def test_table7_hex_linear_on_gpu():
+    # Table 7, HEX linear at ml = 1 (u = x^3 + y^3 + z^3, f = -6(x + y + z) linear: its Q1
+    # interpolant is exact): the whole GPU path gives the printed error to 0.2 % and the
+    # oracle's dense solution to 1e-9; FP32 assembly with FP32 Krylov inside FP64 refinement
+    # the same error to 1e-3
+    w = table7_hex(1)
+    mesh = workload_mesh(w)
+    C = O.kernel_constant(3, 0, w.delta, w.eps)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, w.delta, w.eps)
+    g = np.array([O.ms_u(w.ms, mesh.coords[:, i]) for i in range(mesh.n_vert)])
+    f = np.array([O.ms_f(w.ms, mesh.coords[:, i], 0, w.delta, w.eps, C) for i in range(mesh.n_vert)])
+    errs = {}
+    for prec in (nl.NL_PREC_FP64, nl.NL_PREC_FP32):
+        A, _ = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, precision=prec)
+        b = nl.nl_rhs(m, A, g, f_nodes=f)
+        u, *_ = nl.nl_solve(A, b, g, solver=1, rtol=1e-13 if prec == nl.NL_PREC_FP64 else 1e-12,
+                            precision=prec)
+        errs[prec] = O.l2_error(mesh, u, w.ms, omega_only=False)
+        if prec == nl.NL_PREC_FP64:
+            ref = O.solve_problem(mesh, w.delta, w.eps, w.L_max, w.ms)
+            assert np.abs(u - ref["u_h"]).max() / np.abs(ref["u_h"]).max() < 1e-9
+    assert abs(errs[nl.NL_PREC_FP64] / 2.220e-2 - 1) < 2e-3, errs
+    assert abs(errs[nl.NL_PREC_FP32] / errs[nl.NL_PREC_FP64] - 1) < 1e-3, errs
+
+
+def test_hex_full_size_sampled_rows():
+    # the 3D workload's grid at h = 1/16 with one Q1 hexahedron per cell (10,648 cells): whole
+    # matrix on the GPU, rows of seeded nodes (inside Omega, on its boundary, in the layer)
+    # against the oracle assembling only the elements around them
+    w = WORKLOADS["c3_3d_hex"]
+    mesh = workload_mesh(w)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, w.delta, w.eps)
+    rng = np.random.default_rng(23)
+    x = mesh.coords
+    lo = np.array(w.lo)
+    hi = lo + np.array(w.cells) * w.h
+    inside = np.all((x > lo[:, None] + 1e-9) & (x < hi[:, None] - 1e-9), axis=0)
+    on_bd = np.all((x >= lo[:, None] - 1e-9) & (x <= hi[:, None] + 1e-9), axis=0) & ~inside
+    layer = ~np.all((x >= lo[:, None] - 1e-9) & (x <= hi[:, None] + 1e-9), axis=0)
+    nodes = [int(rng.choice(np.flatnonzero(inside))), int(rng.choice(np.flatnonzero(on_bd))),
+             int(rng.choice(np.flatnonzero(layer)))]
+    mask = np.zeros(mesh.n_elem, np.uint8)
+    for i in nodes:
+        mask[np.any(mesh.conn == i, axis=1)] = 1
+    ooff, opl = O.pairs(mesh, w.delta, w.eps, m_mask=mask)
+    orp, ocol = O.csr(mesh, ooff, opl)
+    ovals, _ = O.assemble(mesh, ooff, opl, orp, ocol, w.delta, w.eps, w.L_max, w.L_min, w.kernel,
+                          m_mask=mask)
+    _, _, rp, col = p.export(mesh.n_elem, mesh.n_vert)
+    for prec, tol in ((nl.NL_PREC_FP64, TOL64), (nl.NL_PREC_FP32, TOL32)):
+        A, _ = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, w.L_min, w.kernel, prec)
+        vals = A.export()
+        for i in nodes:
+            assert np.array_equal(col[rp[i]:rp[i + 1]], ocol[orp[i]:orp[i + 1]]), i
+            g_row, o_row = vals[rp[i]:rp[i + 1]], ovals[orp[i]:orp[i + 1]]
+            assert np.linalg.norm(g_row - o_row) / np.linalg.norm(o_row) < tol, (prec, i)
