@@ -222,9 +222,12 @@ def describe(w, mesh):
     shape = "triangles" if mesh.dim == 2 else "tetrahedra"
     if _is_quad(mesh):
         shape = "quadrilaterals"
+    if _is_hex(mesh):
+        shape = "hexahedra"
     n_omega = int(mesh.elem_in_omega.sum())
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
-    order = {6: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2"}.get(mesh.conn.shape[1], "P1")
+    order = {6: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2",
+             8: "Q1" if mesh.dim == 3 else "serendipity"}.get(mesh.conn.shape[1], "P1")
     return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} {order} {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
             f"layer {w.layer} cells, L_max={w.L_max}, {kern} kernel, jitter {w.jitter:g}h "
@@ -237,7 +240,11 @@ def u_exact(mesh):
 
 
 def _is_quad(mesh):
-    return mesh.dim == 2 and mesh.conn.shape[1] in (4, 9)
+    return mesh.dim == 2 and mesh.conn.shape[1] in (4, 8, 9)
+
+
+def _is_hex(mesh):
+    return mesh.dim == 3 and mesh.conn.shape[1] == 8
 
 
 def l2_err_omega_quads(mesh, u_h):
@@ -269,6 +276,32 @@ def l2_err_omega_quads(mesh, u_h):
     return float(math.sqrt(np.sum(det * W[None, :] * d * d)))
 
 
+def l2_err_omega_hexes(mesh, u_h):
+    """||u - u_h||_{L2(Omega)} on Q1 hexahedra (u = sum x_k^2): Gauss-Legendre 3x3x3 on each
+    element's unit cube mapped by its trilinear map."""
+    x, gw = np.polynomial.legendre.leggauss(3)
+    g, gw = (x + 1) / 2, gw / 2
+    S, T, U = np.meshgrid(g, g, g, indexing="ij")
+    s, t, u = S.ravel(), T.ravel(), U.ravel()
+    W = np.einsum("i,j,k->ijk", gw, gw, gw).ravel()
+    corners = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    N, dN = [], []
+    for c in corners:
+        fs, ft, fu = (s if c[0] else 1 - s), (t if c[1] else 1 - t), (u if c[2] else 1 - u)
+        ds, dt, du = (1 if c[0] else -1), (1 if c[1] else -1), (1 if c[2] else -1)
+        N.append(fs * ft * fu)
+        dN.append(np.stack([ds * ft * fu, fs * dt * fu, fs * ft * du], -1))
+    N, dN = np.stack(N, 1), np.stack(dN, 1)  # (27, 8), (27, 8, 3)
+    conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
+    V = mesh.points()[conn]  # (ne, 8, 3)
+    X = np.einsum("qa,eak->eqk", N, V)
+    J = np.einsum("qar,eak->eqkr", dN, V)
+    det = np.abs(np.linalg.det(J))
+    uh = np.einsum("qa,ea->eq", N, u_h[conn])
+    d = (X ** 2).sum(-1) - uh
+    return float(math.sqrt(np.sum(det * W[None, :] * d * d)))
+
+
 def l2_err_omega(mesh, u_h, rule):
     """||u - u_h||_{L2(Omega)} with the degree-5 rule per element (u = sum x_k^2); P1, or P2
     triangles when the elements have six nodes (basis lambda_a (2 lambda_a - 1) at the
@@ -276,6 +309,8 @@ def l2_err_omega(mesh, u_h, rule):
     l2_err_omega_quads."""
     if _is_quad(mesh):
         return l2_err_omega_quads(mesh, u_h)
+    if _is_hex(mesh):
+        return l2_err_omega_hexes(mesh, u_h)
     b, w = rule
     P = mesh.points()
     conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
@@ -382,7 +417,8 @@ def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False, stb=None):
         "units": "Algorithm-1 quadrature point pairs (closed-form ones included)",
         "frac_evaluated_only": round(achieved_ev / peak, 4),
         "kernel": (f"k_quad_p2<{rtype},{w.kernel}>" if nb == 6 else
-                   f"k_quad_q<{rtype},{w.kernel},{1 if nb == 4 else 2}>" if _is_quad(mesh) else
+                   f"k_quad_h<{rtype},{w.kernel}>" if _is_hex(mesh) else
+                   f"k_quad_q<{rtype},{w.kernel},{ {4: 1, 9: 2, 8: 3}[nb] }>" if _is_quad(mesh) else
                    f"k_quad<{mesh.dim},{rtype},{w.kernel}>"), "flops_per_assembly": flops,
         "kernel_ms_per_assembly": round(quad_ms, 3),
         "launches_per_assembly": int(stats[-1].n_quad_launches),
@@ -561,7 +597,7 @@ def run_ours(args, rank, world, local):
         out["p2"] = run_element_block(args, nl, torch, stream, flush, world, "c2_2d_p2",
                                       args.p2_steps, args.p2_fp64_steps)
     if args.quad_steps > 0:
-        for key, name in (("q1", "c2_2d_q1"), ("q2", "c2_2d_q2")):
+        for key, name in (("q1", "c2_2d_q1"), ("q2", "c2_2d_q2"), ("hex", "c3_3d_hex")):
             out[key] = run_element_block(args, nl, torch, stream, flush, world, name,
                                          args.quad_steps, args.quad_fp64_steps)
     if args.eps_study:
@@ -615,13 +651,13 @@ def run_c2_block(args, nl, torch, stream, flush, world):
 
 
 def run_element_block(args, nl, torch, stream, flush, world, name, steps, fp64_steps):
-    """Other element families on the 2D workload's grid (h = 1/256): P2 triangles (c2_2d_p2:
+    """Other element families: on the 2D workload's grid (h = 1/256) P2 triangles (c2_2d_p2:
     141,512 triangles, 284,089 nodes), Q1 and Q2 quadrilaterals (c2_2d_q1, c2_2d_q2: 70,756
-    cells).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
+    cells); on the 3D grid at h = 1/16 Q1 hexahedra (c3_3d_hex: 10,648 cells).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
     BiCGStab), their L2 errors, and the roofline of the assembly kernel in both
     precisions."""
     w, mesh = workload(name)
-    rule = nl.nl_quad_rule(2)
+    rule = nl.nl_quad_rule(mesh.dim)
     dm = nl.mesh_from(mesh)
     mx = _measure(nl, torch, stream, dm, mesh, w, nl.NL_PREC_FP32, steps, 1, flush, world,
                   keep_last=fp64_steps > 0)
@@ -672,7 +708,7 @@ def roofline_flops(dim, st, evaluated_only=False, nb=None):
     pp = int(getattr(st, "n_eval_point_pairs" if evaluated_only else "n_point_pairs", 0) or 0)
     band = max(0, int(getattr(st, "n_band_point_pairs", 0) or 0))
     nb = nb or dim + 1
-    per_pp = 5 + 2 + 2 * nb + 1 if dim == 2 else 19
+    per_pp = (5 if dim == 2 else 8) + 2 + 2 * nb + 1
     return float(max(0, pp) * per_pp + band * 15)
 
 
