@@ -124,32 +124,35 @@ def structured_mesh(dim: int, cells, h: float, lo, layer: int, jitter: float = 0
 
 
 def p2_mesh(mesh: Mesh) -> Mesh:
-    """The P2 (quadratic Lagrange) triangle mesh on the triangles of a structured 2D mesh.
+    """The P2 (quadratic Lagrange) mesh on the simplices of a structured mesh.
 
     Nodes: the vertices (same numbers), then one node per edge at its midpoint (a + b) * 0.5,
     numbered after the vertices in the lexicographic order of the edges' (smaller vertex,
-    larger vertex) pairs.  ``conn`` rows are (v0, v1, v2, m01, m12, m02).  A node is a degree
-    of freedom when it lies strictly inside the open Omega of ``mesh.meta`` (vertices on the
+    larger vertex) pairs.  ``conn`` rows are (v0, v1, v2, m01, m12, m02) for triangles and
+    (v0, v1, v2, v3, m01, m12, m02, m03, m13, m23) for tetrahedra.  A node is a degree of
+    freedom when it lies strictly inside the open Omega of ``mesh.meta`` (vertices on the
     boundary of Omega are never moved by the jitter, so midpoints of boundary edges lie
     exactly on it)."""
-    if mesh.dim != 2 or mesh.conn.shape[1] != 3:
-        raise ValueError("P2 meshes are built from P1 triangle meshes")
+    if mesh.conn.shape[1] != mesh.dim + 1:
+        raise ValueError("P2 meshes are built from P1 simplex meshes")
     c = mesh.conn.astype(np.int64)
-    pairs = np.stack([c[:, [0, 1]], c[:, [1, 2]], c[:, [0, 2]]], axis=1)  # (n_elem, 3, 2)
+    edges = [(0, 1), (1, 2), (0, 2)] if mesh.dim == 2 else [(0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3)]
+    ne = len(edges)
+    pairs = np.stack([c[:, list(e)] for e in edges], axis=1)  # (n_elem, ne, 2)
     lo_hi = np.sort(pairs, axis=2).reshape(-1, 2)
     key = lo_hi[:, 0] * mesh.n_vert + lo_hi[:, 1]
     ukey, inv = np.unique(key, return_inverse=True)
     ea, eb = ukey // mesh.n_vert, ukey % mesh.n_vert
     mid = (mesh.coords[:, ea] + mesh.coords[:, eb]) * 0.5
     coords = np.concatenate([mesh.coords, mid], axis=1)
-    edge_node = (mesh.n_vert + inv).reshape(-1, 3)
+    edge_node = (mesh.n_vert + inv).reshape(-1, ne)
     conn = np.concatenate([c, edge_node], axis=1).astype(np.int32)
     lo = np.array(mesh.meta["lo"], dtype=np.float64)
     hi = lo + np.array(mesh.meta["cells"], dtype=np.float64) * mesh.h
     free = np.all((coords > lo[:, None]) & (coords < hi[:, None]), axis=0)
     free[: mesh.n_vert] = mesh.node_free.astype(bool)
     meta = dict(mesh.meta, order=2)
-    return Mesh(dim=2, coords=coords, conn=np.ascontiguousarray(conn), elem_in_omega=mesh.elem_in_omega.copy(),
+    return Mesh(dim=mesh.dim, coords=coords, conn=np.ascontiguousarray(conn), elem_in_omega=mesh.elem_in_omega.copy(),
                 node_free=free.astype(np.uint8), h=mesh.h, meta=meta)
 
 

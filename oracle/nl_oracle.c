@@ -386,11 +386,13 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
 /* ------------------------------------------------------------------------------------
  * Mesh helpers. */
 /* Nodes per element: P1 simplices dim+1; P2 triangles 6 (the vertices, then the midpoints of
- * the edges (0,1), (1,2), (0,2)). */
+ * the edges (0,1), (1,2), (0,2)); P2 tetrahedra 10 (the vertices, then the midpoints of the
+ * edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3)). */
 static int npe(const or_mesh* M) {
   if (M->cell == 2) return 8;
   if (M->cell == 1) return (M->order == 2) ? 9 : (M->order == 3) ? 8 : 4;
-  return (M->order == 2) ? 6 : M->dim + 1;
+  if (M->order == 2) return M->dim == 2 ? 6 : 10;
+  return M->dim + 1;
 }
 /* Vertices per element: simplices dim+1, quadrilaterals 4 (hexahedra 8: hex_verts). */
 static int nverts(const or_mesh* M) { return (M->cell == 1) ? 4 : M->dim + 1; }
@@ -417,17 +419,21 @@ static void hex_bbox(const double V[8][3], double* lo, double* hi) {
 static void elem_box(const or_mesh* M, int64_t e, double* lo, double* hi);
 
 /* The element's Lagrange basis at the point with barycentric coordinates lam: P1 the
- * barycentric coordinates; P2 (triangles) lam_a (2 lam_a - 1) at the vertices and
- * 4 lam_a lam_b at the midpoints of the edges (0,1), (1,2), (0,2). */
+ * barycentric coordinates; P2 lam_a (2 lam_a - 1) at the vertices and 4 lam_a lam_b at the
+ * edge midpoints, in the node order of npe(). */
 static void basis(const or_mesh* M, const double* lam, double* phi) {
   if (M->order != 2) {
     for (int a = 0; a <= M->dim; a++) phi[a] = lam[a];
     return;
   }
-  for (int a = 0; a < 3; a++) phi[a] = lam[a] * (2.0 * lam[a] - 1.0);
-  phi[3] = 4.0 * lam[0] * lam[1];
-  phi[4] = 4.0 * lam[1] * lam[2];
-  phi[5] = 4.0 * lam[0] * lam[2];
+  static const int e2[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+  static const int e3[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+  int nv = M->dim + 1, ne = M->dim == 2 ? 3 : 6;
+  for (int a = 0; a < nv; a++) phi[a] = lam[a] * (2.0 * lam[a] - 1.0);
+  for (int j = 0; j < ne; j++) {
+    const int* e = M->dim == 2 ? e2[j] : e3[j];
+    phi[nv + j] = 4.0 * lam[e[0]] * lam[e[1]];
+  }
 }
 
 /* The vertices of element e (the first nverts of its nodes). */
@@ -673,7 +679,7 @@ static void integration(actx* c, const double E[4][3], const int32_t* J, int64_t
   int dim = c->dim, nv = c->nv, nq = c->nq, nb = c->nb;
   const or_params* P = c->P;
   double vol = simplex_volume(dim, E);
-  double xq[16][3], wx[16], phil[16][6], phim[16][6];
+  double xq[16][3], wx[16], phil[16][10], phim[16][10];
   for (int q = 0; q < nq; q++) {
     for (int k = 0; k < 3; k++) {
       double s = 0.0;
@@ -691,7 +697,7 @@ static void integration(actx* c, const double E[4][3], const int32_t* J, int64_t
     double Vm[4][3];
     elem_verts(c->M, m, Vm);
     double volm = simplex_volume(dim, Vm);
-    double S[6][6] = {{0}}, X[6][6] = {{0}};
+    double S[10][10] = {{0}}, X[10][10] = {{0}};
     for (int q = 0; q < nq; q++) {
       for (int p = 0; p < nq; p++) {
         double y[3];
@@ -1206,7 +1212,7 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
   c.dim = dim;
   c.nv = nv;
   c.nb = npe(M);
-  if (M->order == 2 && dim != 2) return -1; /* P2: triangles only */
+
   double bary[64], w[16];
   c.nq = or_quad_rule(dim, bary, w);
   if (c.nq <= 0) return -1;
@@ -1369,7 +1375,7 @@ int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const d
         x[k] = s;
       }
       double f = or_ms_f(ms, dim, x, kernel, delta, eps, C);
-      double phi[6];
+      double phi[10];
       basis(M, bary + q * nv, phi);
       for (int a = 0; a < nb; a++) {
         int64_t i = M->conn[e * nb + a];
@@ -1449,7 +1455,7 @@ static double err_on(const or_mesh* M, const double V[4][3], const double* nodal
       for (int v = 0; v <= dim; v++) t += bary[q][v] * V[v][k];
       x[k] = t;
     }
-    double lam[4], phi[6];
+    double lam[4], phi[10];
     barycentric(dim, Vroot, x, lam);
     basis(M, lam, phi);
     double uh = 0.0;
@@ -1517,7 +1523,7 @@ double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) 
       s += err_on_hex(M, H, hn, ms);
       continue;
     }
-    double V[4][3], nodal[9];
+    double V[4][3], nodal[10];
     elem_verts(M, e, V);
     for (int a = 0; a < npe(M); a++) nodal[a] = u_h[M->conn[e * npe(M) + a]];
     if (M->cell == 1) s += err_on_quad(M, V, nodal, ms);
