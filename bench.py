@@ -226,7 +226,7 @@ def describe(w, mesh):
         shape = "hexahedra"
     n_omega = int(mesh.elem_in_omega.sum())
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
-    order = {6: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2",
+    order = {6: "P2", 10: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2",
              8: "Q1" if mesh.dim == 3 else "serendipity"}.get(mesh.conn.shape[1], "P1")
     return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} {order} {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
@@ -304,9 +304,9 @@ def l2_err_omega_hexes(mesh, u_h):
 
 def l2_err_omega(mesh, u_h, rule):
     """||u - u_h||_{L2(Omega)} with the degree-5 rule per element (u = sum x_k^2); P1, or P2
-    triangles when the elements have six nodes (basis lambda_a (2 lambda_a - 1) at the
-    vertices, 4 lambda_a lambda_b at the edge nodes (0,1), (1,2), (0,2)); quadrilaterals with
-    l2_err_omega_quads."""
+    simplices when the elements have more nodes than vertices (basis lambda_a (2 lambda_a - 1)
+    at the vertices, 4 lambda_a lambda_b at the edge nodes (0,1), (1,2), (0,2) (, (0,3), (1,3),
+    (2,3))); quadrilaterals and hexahedra with their own routines."""
     if _is_quad(mesh):
         return l2_err_omega_quads(mesh, u_h)
     if _is_hex(mesh):
@@ -322,9 +322,9 @@ def l2_err_omega(mesh, u_h, rule):
     else:
         vol = np.abs(np.linalg.det(V[:, 1:] - V[:, :1])) / 6.0
     X = np.einsum("qv,evk->eqk", b, V)
-    if conn.shape[1] == 6:
-        phi = np.concatenate([b * (2 * b - 1), 4 * b[:, [0]] * b[:, [1]], 4 * b[:, [1]] * b[:, [2]],
-                              4 * b[:, [0]] * b[:, [2]]], axis=1)
+    if conn.shape[1] > nv:  # P2: vertices, then the edge nodes in the mesh's edge order
+        edges = [(0, 1), (1, 2), (0, 2)] if mesh.dim == 2 else [(0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3)]
+        phi = np.concatenate([b * (2 * b - 1)] + [4 * b[:, [i]] * b[:, [j]] for i, j in edges], axis=1)
     else:
         phi = b
     uh = np.einsum("qv,ev->eq", phi, u_h[conn])
@@ -417,6 +417,7 @@ def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False, stb=None):
         "units": "Algorithm-1 quadrature point pairs (closed-form ones included)",
         "frac_evaluated_only": round(achieved_ev / peak, 4),
         "kernel": (f"k_quad_p2<{rtype},{w.kernel}>" if nb == 6 else
+                   f"k_quad_p2t<{rtype},{w.kernel}>" if nb == 10 else
                    f"k_quad_h<{rtype},{w.kernel}>" if _is_hex(mesh) else
                    f"k_quad_q<{rtype},{w.kernel},{ {4: 1, 9: 2, 8: 3}[nb] }>" if _is_quad(mesh) else
                    f"k_quad<{mesh.dim},{rtype},{w.kernel}>"), "flops_per_assembly": flops,
@@ -597,7 +598,8 @@ def run_ours(args, rank, world, local):
         out["p2"] = run_element_block(args, nl, torch, stream, flush, world, "c2_2d_p2",
                                       args.p2_steps, args.p2_fp64_steps)
     if args.quad_steps > 0:
-        for key, name in (("q1", "c2_2d_q1"), ("q2", "c2_2d_q2"), ("hex", "c3_3d_hex")):
+        for key, name in (("q1", "c2_2d_q1"), ("q2", "c2_2d_q2"), ("hex", "c3_3d_hex"),
+                          ("p2_tet", "c3_3d_p2")):
             out[key] = run_element_block(args, nl, torch, stream, flush, world, name,
                                          args.quad_steps, args.quad_fp64_steps)
     if args.eps_study:
@@ -653,7 +655,8 @@ def run_c2_block(args, nl, torch, stream, flush, world):
 def run_element_block(args, nl, torch, stream, flush, world, name, steps, fp64_steps):
     """Other element families: on the 2D workload's grid (h = 1/256) P2 triangles (c2_2d_p2:
     141,512 triangles, 284,089 nodes), Q1 and Q2 quadrilaterals (c2_2d_q1, c2_2d_q2: 70,756
-    cells); on the 3D grid at h = 1/16 Q1 hexahedra (c3_3d_hex: 10,648 cells).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
+    cells); on the 3D grid at h = 1/16 Q1 hexahedra (c3_3d_hex: 10,648 cells) and P2
+    tetrahedra (c3_3d_p2: 63,888 tetrahedra, 91,125 nodes).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
     BiCGStab), their L2 errors, and the roofline of the assembly kernel in both
     precisions."""
     w, mesh = workload(name)

@@ -163,11 +163,12 @@ nl_status nl_mesh_create(int dim, int64_t n_vert, const double* coords, int64_t 
 nl_status nl_mesh_create_box(int dim, const int32_t* cells, double h, const double* lo,
                              int32_t layer, double jitter, uint64_t seed, void* cuda_stream,
                              nl_mesh** out);
-/* Mesh of quadratic (P2) Lagrange triangles (Sec. 6, Tables 1-3, the quadratic columns):
- * the arguments of nl_mesh_create with dim = 2 and six nodes per element in conn, ordered
+/* Mesh of quadratic (P2) Lagrange simplices (Sec. 6, Tables 1-3, the quadratic columns):
+ * the arguments of nl_mesh_create; dim = 2: six nodes per element in conn, ordered
  * (v0, v1, v2, m01, m12, m02): the three vertices, then the nodes at the midpoints of the
- * edges (v0,v1), (v1,v2), (v0,v2).  n_vert counts every node (vertices and edge nodes);
- * node_free flags every node.  The elements are straight-sided: each edge node must lie at
+ * edges (v0,v1), (v1,v2), (v0,v2); dim = 3: ten nodes, the four vertices, then the midpoints
+ * of the edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3).  n_vert counts every node (vertices
+ * and edge nodes); node_free flags every node.  The elements are straight-sided: each edge node must lie at
  * the midpoint of its edge.  The basis on an element with barycentric coordinates lambda is
  * lambda_a (2 lambda_a - 1) at the vertices and 4 lambda_a lambda_b at the edge nodes.
  * Pairs, pattern, nl_assemble (FP64 and FP32; the MIXED precisions run the FP32 path and

@@ -109,6 +109,9 @@ WORKLOADS = {
     "c2_2d_q1": _unit_box("c2_2d_q1", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1, cell="quad"),
     "c2_2d_h128_q1": _unit_box("c2_2d_h128_q1", 2, 128, 4 / 128, 4 / 128 / 5, 4, jitter=0.1,
                                cell="quad"),
+    # the c3_3d tetrahedra with P2 elements
+    "c3_3d_p2": _unit_box("c3_3d_p2", 3, 16, 0.125, 0.0125, 2, order=2),
+    "c3_3d_h10_p2": _unit_box("c3_3d_h10_p2", 3, 10, 0.125, 0.0125, 2, order=2),
     # the c3_3d grid with one Q1 hexahedron per cell (Sec. 6, the HEX meshes of the 3D tests)
     "c3_3d_hex": _unit_box("c3_3d_hex", 3, 16, 0.125, 0.0125, 2, cell="hex"),
     "c3_3d_h10_hex": _unit_box("c3_3d_h10_hex", 3, 10, 0.125, 0.0125, 2, cell="hex"),

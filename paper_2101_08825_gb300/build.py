@@ -15,8 +15,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnl.so")
-SOURCES = ["nl_host.cu", "nl_pairs.cu", "nl_quad.cu", "nl_quad_mma.cu", "nl_quad_p2.cu", "nl_quad_quad.cu", "nl_quad_hex.cu",
-           "nl_batch.cu", "nl_solve.cu", "nl_serve.cu"]
+SOURCES = ["nl_host.cu", "nl_pairs.cu", "nl_quad.cu", "nl_quad_mma.cu", "nl_quad_p2.cu",
+           "nl_quad_p2t.cu", "nl_quad_quad.cu", "nl_quad_hex.cu", "nl_batch.cu", "nl_solve.cu",
+           "nl_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

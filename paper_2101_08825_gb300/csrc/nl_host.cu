@@ -514,8 +514,8 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
   if (!out) return fail(NL_EINVAL, "nl_mesh_create: out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create: dim must be 2 or 3");
-  if (order != 1 && !(order == 2 && dim == 2) && !(order == 3 && cell == 1))
-    return fail(NL_EINVAL, "nl_mesh_create: P2 elements are triangles (dim 2) only");
+  if (order != 1 && !(order == 2 && cell != 2) && !(order == 3 && cell == 1))
+    return fail(NL_EINVAL, "nl_mesh_create: unknown element order %d", order);
   if (cell == 1 && dim != 2) return fail(NL_EINVAL, "nl_mesh_create_quad: quadrilaterals are 2D");
   if (cell == 2 && (dim != 3 || order != 1))
     return fail(NL_EINVAL, "nl_mesh_create_hex: Q1 hexahedra are 3D");
@@ -524,7 +524,9 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
   const int nv = cell == 1 ? 4 : (cell == 2 ? 8 : dim + 1);
-  const int nb = cell == 2 ? 8 : cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4)) : (order == 2 ? 6 : nv);
+  const int nb = cell == 2 ? 8
+                 : cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4))
+                             : (order == 2 ? (dim == 2 ? 6 : 10) : nv);
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
     if (!std::isfinite(coords[i])) return fail(NL_EINVAL, "nl_mesh_create: non-finite coordinate");
   double bl[3] = {INFINITY, INFINITY, INFINITY}, bh[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -568,10 +570,11 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
         }
       }
     } else if (order == 2) {
-      // straight-sided P2: edge node 3 + j at the midpoint of edge j = (0,1), (1,2), (0,2)
-      static const int ea[3] = {0, 1, 0}, eb[3] = {1, 2, 2};
-      for (int j = 0; j < 3; j++) {
-        const int32_t v = conn[e * nb + 3 + j];
+      // straight-sided P2: edge node nv + j at the midpoint of edge j = (0,1), (1,2), (0,2)
+      // (and for tetrahedra (0,3), (1,3), (2,3))
+      static const int ea[6] = {0, 1, 0, 0, 1, 2}, eb[6] = {1, 2, 2, 3, 3, 3};
+      for (int j = 0; j < nb - nv; j++) {
+        const int32_t v = conn[e * nb + nv + j];
         double d2 = 0.0, l2 = 0.0;
         for (int k = 0; k < dim; k++) {
           const double mid = (V[ea[j]][k] + V[eb[j]][k]) * 0.5;
@@ -581,7 +584,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
         }
         if (!(d2 <= 1e-18 * l2))
           return fail(NL_EINVAL, "nl_mesh_create_p2: edge node %d of element %lld is not at its edge's midpoint",
-                      3 + j, (long long)e);
+                      nv + j, (long long)e);
       }
     }
     double det;

@@ -251,6 +251,10 @@ nl_status assemble_values_hex(nl_mesh* m, nl_pairs* p, const nl_kernel_params* k
 nl_status assemble_values_quad(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                                const nl_quad_params* qp, nl_precision prec, double* values,
                                nl_assemble_stats* st);
+// The same for meshes of P2 tetrahedra (nl_quad_p2t.cu).
+nl_status assemble_values_p2t(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
+                              const nl_quad_params* qp, nl_precision prec, double* values,
+                              nl_assemble_stats* st);
 // The same for meshes of P2 triangles (nl_quad_p2.cu).
 nl_status assemble_values_p2(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
                              const nl_quad_params* qp, nl_precision prec, double* values,

@@ -29,7 +29,8 @@ nl_status assemble_values(nl_mesh* m, nl_pairs* p, const nl_kernel_params* kp,
   // translation units of their own
   if (m->cell == 2) return assemble_values_hex(m, p, kp, qp, prec, values, st);
   if (m->cell == 1) return assemble_values_quad(m, p, kp, qp, prec, values, st);
-  if (m->order == 2) return assemble_values_p2(m, p, kp, qp, prec, values, st);
+  if (m->order == 2) return m->dim == 2 ? assemble_values_p2(m, p, kp, qp, prec, values, st)
+                                        : assemble_values_p2t(m, p, kp, qp, prec, values, st);
   if (prec == NL_PREC_MIXED_TF32 || prec == NL_PREC_MIXED_BF16)
     return assemble_values_mma(m, p, kp, qp, prec, values, st);
   return assemble_single<0>(m, p, kp, qp, prec, values, st);

@@ -32,8 +32,8 @@ enum : int {
 };
 constexpr int NPARTS = 2;  // dot products that one kernel can reduce
 
-// F_i += int_E f phi_i per element of Omega with NB nodes (P1: D+1, P2 triangles: 6); B[q][a]
-// (row stride 8) is the element basis phi_a at rule point q.
+// F_i += int_E f phi_i per element of Omega with NB nodes (P1: D+1, P2 triangles 6, P2
+// tetrahedra 10); B[q][a] (row stride 16) is the element basis phi_a at rule point q.
 template <int NB>
 __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
                             const uint8_t* __restrict__ eio, const uint8_t* __restrict__ free_,
@@ -52,8 +52,8 @@ __global__ void k_rhs_elems(int64_t n_elem, const int32_t* __restrict__ conn,
   for (int a = 0; a < NB; a++) acc[a] = 0.0;
   for (int q = 0; q < nq; q++) {
     double f = f_const;
-    for (int v = 0; v < NB; v++) f += B[q * 8 + v] * fv[v];
-    for (int a = 0; a < NB; a++) acc[a] += W[q] * f * B[q * 8 + a];
+    for (int v = 0; v < NB; v++) f += B[q * 16 + v] * fv[v];
+    for (int a = 0; a < NB; a++) acc[a] += W[q] * f * B[q * 16 + a];
   }
   for (int a = 0; a < NB; a++)
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], vol[e] * acc[a]);
@@ -577,24 +577,23 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   // the element basis at the rule points: P1 the barycentric coordinates; P2 (triangles)
   // lambda_a (2 lambda_a - 1) at the vertices and 4 lambda_a lambda_b at the edge nodes
   // (0,1), (1,2), (0,2)
-  std::vector<double> hB(16 * 8, 0.0), hW(16, 0.0);
+  std::vector<double> hB(16 * 16, 0.0), hW(16, 0.0);
+  static const int ea[6] = {0, 1, 0, 0, 1, 2}, eb[6] = {1, 2, 2, 3, 3, 3};
   for (int q = 0; q < r.n; q++) {
     const double* lam = r.bary[q];
     if (m->order == 2) {
-      for (int a = 0; a < 3; a++) hB[q * 8 + a] = lam[a] * (2.0 * lam[a] - 1.0);
-      hB[q * 8 + 3] = 4.0 * lam[0] * lam[1];
-      hB[q * 8 + 4] = 4.0 * lam[1] * lam[2];
-      hB[q * 8 + 5] = 4.0 * lam[0] * lam[2];
+      for (int a = 0; a <= D; a++) hB[q * 16 + a] = lam[a] * (2.0 * lam[a] - 1.0);
+      for (int j = 0; j < (D == 2 ? 3 : 6); j++) hB[q * 16 + D + 1 + j] = 4.0 * lam[ea[j]] * lam[eb[j]];
     } else {
-      for (int a = 0; a <= D; a++) hB[q * 8 + a] = lam[a];
+      for (int a = 0; a <= D; a++) hB[q * 16 + a] = lam[a];
     }
     hW[q] = r.w[q];
   }
   DevBuf<double> B, W, fn, g;
-  NL_TRY(B.alloc(128, s));
+  NL_TRY(B.alloc(256, s));
   NL_TRY(W.alloc(16, s));
   NL_TRY(g.alloc(m->n_vert, s));
-  NL_CUDA(cudaMemcpyAsync(B.p, hB.data(), sizeof(double) * 128, cudaMemcpyHostToDevice, s));
+  NL_CUDA(cudaMemcpyAsync(B.p, hB.data(), sizeof(double) * 256, cudaMemcpyHostToDevice, s));
   NL_CUDA(cudaMemcpyAsync(W.p, hW.data(), sizeof(double) * 16, cudaMemcpyHostToDevice, s));
   NL_CUDA(cudaMemcpyAsync(g.p, g_nodes, sizeof(double) * m->n_vert, cudaMemcpyHostToDevice, s));
   if (f_nodes) {
@@ -641,6 +640,9 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   else if (m->cell == 1)
     k_rhs_quads<4><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->evert, fn.p, f_const, QB.p, QS.p, F);
+  else if (m->nb == 10)
+    k_rhs_elems<10><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                              m->vol, fn.p, f_const, B.p, W.p, r.n, F);
   else if (m->nb == 6)
     k_rhs_elems<6><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->vol, fn.p, f_const, B.p, W.p, r.n, F);

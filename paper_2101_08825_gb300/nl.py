@@ -288,9 +288,10 @@ def nl_mesh_create(dim, coords, conn, elem_in_omega, node_free, stream=None) -> 
 
 
 def nl_mesh_create_p2(dim, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
-    """Mesh of P2 triangles: conn rows (v0, v1, v2, m01, m12, m02)."""
+    """Mesh of P2 simplices: conn rows (v0, v1, v2, m01, m12, m02) for triangles, (v0, v1, v2,
+    v3, m01, m12, m02, m03, m13, m23) for tetrahedra."""
     coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(dim, -1)
-    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 6)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 6 if dim == 2 else 10)
     eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
     nf = np.ascontiguousarray(node_free, dtype=np.uint8)
     h = ctypes.c_void_p()
@@ -328,14 +329,14 @@ def nl_mesh_create_hex(coords, conn, elem_in_omega, node_free, stream=None) -> M
 
 
 def mesh_from(mesh, stream=None) -> Mesh:
-    """Uploads an nl_inputs.Mesh: P1 simplices, P2 triangles (six nodes per element) or
+    """Uploads an nl_inputs.Mesh: P1 simplices, P2 simplices (six or ten nodes per element),
     quadrilaterals (2D, four, eight or nine nodes per element) or hexahedra (3D, eight)."""
     if mesh.dim == 3 and mesh.conn.shape[1] == 8:
         return nl_mesh_create_hex(mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
     if mesh.dim == 2 and mesh.conn.shape[1] in (4, 8, 9):
         return nl_mesh_create_quad({4: 1, 9: 2, 8: 3}[mesh.conn.shape[1]], mesh.coords, mesh.conn,
                                    mesh.elem_in_omega, mesh.node_free, stream)
-    if mesh.conn.shape[1] == 6:
+    if mesh.conn.shape[1] == (6 if mesh.dim == 2 else 10):
         return nl_mesh_create_p2(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
     return nl_mesh_create(mesh.dim, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
 
