@@ -5,5 +5,5 @@ This package holds no arithmetic of the method: it only lays out structured P1 m
 optional seeded vertex jitter, and describes the workloads (horizon, mollifier width,
 refinement levels, kernel, manufactured solution) the tests and the benchmark run.
 """
-from .mesh import Mesh, hex_mesh, p2_mesh, q2_mesh, quad_mesh, s2_mesh, structured_mesh, splitmix64_unit  # noqa: F401
+from .mesh import Mesh, hex_mesh, p2_mesh, q2_hex_mesh, q2_mesh, quad_mesh, s2_mesh, structured_mesh, splitmix64_unit  # noqa: F401
 from .configs import WORKLOADS, Workload, workload_mesh  # noqa: F401

@@ -235,3 +235,60 @@ def hex_mesh(mesh: Mesh) -> Mesh:
     eio = mesh.elem_in_omega[::6].copy()
     return Mesh(dim=3, coords=mesh.coords.copy(), conn=np.ascontiguousarray(conn), elem_in_omega=eio,
                 node_free=mesh.node_free.copy(), h=mesh.h, meta=dict(mesh.meta, cell="hex"))
+
+
+# The 27 nodes of the Q2 hexahedron as lattice points (i, j, k) of half steps: the 8 vertices in
+# the Q1 order, then the 12 edge midpoints, the 6 face centres and the centre, each group in
+# the order of (k, j, i) (z slowest)
+HEX27 = [(0, 0, 0), (2, 0, 0), (2, 2, 0), (0, 2, 0), (0, 0, 2), (2, 0, 2), (2, 2, 2), (0, 2, 2),
+         (1, 0, 0), (0, 1, 0), (2, 1, 0), (1, 2, 0), (0, 0, 1), (2, 0, 1), (0, 2, 1), (2, 2, 1),
+         (1, 0, 2), (0, 1, 2), (2, 1, 2), (1, 2, 2), (1, 1, 0), (1, 0, 1), (0, 1, 1), (2, 1, 1),
+         (1, 2, 1), (1, 1, 2), (1, 1, 1)]
+
+
+def q2_hex_mesh(mesh: Mesh) -> Mesh:
+    """The Q2 (triquadratic Lagrange) mesh on the cells of a hexahedral mesh: every node of the
+    cells' lattices of half steps (the vertices keep their numbers; the other points are
+    numbered after them by their position on the grid of half steps, x fastest), placed at
+    the image of its lattice point under the cell's trilinear map.  ``conn`` rows list the 27
+    nodes in the order HEX27.  A node is a degree of freedom when it lies strictly inside the
+    open Omega."""
+    if mesh.dim != 3 or mesh.conn.shape[1] != 8:
+        raise ValueError("Q2 hexahedral meshes are built from Q1 hexahedral meshes")
+    cells, layer = mesh.meta["cells"], mesh.meta["layer"]
+    nc = [c + 2 * layer for c in cells]
+    n2 = [2 * c + 1 for c in nc]  # half-step grid points per axis
+    x = mesh.coords
+    V = x[:, mesh.conn]  # (3, n_elem, 8)
+    cidx = np.indices(nc[::-1]).reshape(3, -1)[::-1]  # cell index per axis, x fastest
+    corners = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    gid = np.zeros((mesh.n_elem, 27), dtype=np.int64)
+    pos = np.zeros((3, mesh.n_elem, 27))
+    for a, (i, j, k) in enumerate(HEX27):
+        g = [2 * cidx[0] + i, 2 * cidx[1] + j, 2 * cidx[2] + k]
+        gid[:, a] = g[0] + n2[0] * (g[1] + n2[1] * g[2])
+        w = [(1 - i / 2 if c[0] == 0 else i / 2) * (1 - j / 2 if c[1] == 0 else j / 2) *
+             (1 - k / 2 if c[2] == 0 else k / 2) for c in corners]
+        pos[:, :, a] = sum(w[b] * V[:, :, b] for b in range(8))
+    # vertices keep their numbers; the other grid points follow in grid order
+    vert_gid = np.unique(gid[:, :8])
+    other = np.setdiff1d(np.unique(gid), vert_gid)
+    number = {}
+    # a vertex's grid id -> its mesh number
+    for a in range(8):
+        for e_gid, v in zip(gid[:, a], mesh.conn[:, a]):
+            number[int(e_gid)] = int(v)
+    base = mesh.n_vert
+    for t, g in enumerate(other):
+        number[int(g)] = base + t
+    conn = np.vectorize(number.get)(gid).astype(np.int32)
+    n_vert = base + len(other)
+    coords = np.zeros((3, n_vert))
+    coords[:, conn.ravel()] = pos.reshape(3, -1)
+    coords[:, :mesh.n_vert] = x
+    lo = np.array(mesh.meta["lo"], dtype=np.float64)
+    hi = lo + np.array(mesh.meta["cells"], dtype=np.float64) * mesh.h
+    free = np.all((coords > lo[:, None] + 1e-12) & (coords < hi[:, None] - 1e-12), axis=0)
+    free[: mesh.n_vert] = mesh.node_free.astype(bool)
+    return Mesh(dim=3, coords=coords, conn=np.ascontiguousarray(conn), elem_in_omega=mesh.elem_in_omega.copy(),
+                node_free=free.astype(np.uint8), h=mesh.h, meta=dict(mesh.meta, order=2))

@@ -114,8 +114,8 @@ class OMesh:
         # nodes per element -> element kind: 2D 3 P1 / 6 P2 triangles, 4 Q1 / 9 Q2 / 8
         # serendipity quadrilaterals (order 3); 3D 4 P1 tetrahedra, 8 Q1 hexahedra (cell 2)
         npe = self.conn.shape[1]
-        self.cell = 1 if (self.dim == 2 and npe in (4, 8, 9)) else (2 if (self.dim == 3 and npe == 8) else 0)
-        self.order = 2 if (npe in (6, 9) or (self.dim == 3 and npe == 10)) else \
+        self.cell = 1 if (self.dim == 2 and npe in (4, 8, 9)) else (2 if (self.dim == 3 and npe in (8, 27)) else 0)
+        self.order = 2 if (npe in (6, 9, 27) or (self.dim == 3 and npe == 10)) else \
             (3 if (self.cell == 1 and npe == 8) else 1)
         self.c = _Mesh(self.dim, self.coords.shape[1], self.conn.shape[0], _ptr(self.coords).value,
                        _ptr(self.conn).value, _ptr(self.elem_in_omega).value,

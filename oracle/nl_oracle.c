@@ -389,7 +389,7 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
  * the edges (0,1), (1,2), (0,2)); P2 tetrahedra 10 (the vertices, then the midpoints of the
  * edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3)). */
 static int npe(const or_mesh* M) {
-  if (M->cell == 2) return 8;
+  if (M->cell == 2) return (M->order == 2) ? 27 : 8;
   if (M->cell == 1) return (M->order == 2) ? 9 : (M->order == 3) ? 8 : 4;
   if (M->order == 2) return M->dim == 2 ? 6 : 10;
   return M->dim + 1;
@@ -397,10 +397,11 @@ static int npe(const or_mesh* M) {
 /* Vertices per element: simplices dim+1, quadrilaterals 4 (hexahedra 8: hex_verts). */
 static int nverts(const or_mesh* M) { return (M->cell == 1) ? 4 : M->dim + 1; }
 
-/* The 8 vertices of hexahedron e and their box. */
+/* The 8 vertices of hexahedron e (its first 8 nodes) and their box. */
 static void hex_verts(const or_mesh* M, int64_t e, double V[8][3]) {
+  int nb = (M->order == 2) ? 27 : 8;
   for (int a = 0; a < 8; a++) {
-    int64_t v = M->conn[e * 8 + a];
+    int64_t v = M->conn[e * nb + a];
     for (int k = 0; k < 3; k++) V[a][k] = M->coords[k * M->n_vert + v];
   }
 }
@@ -1045,6 +1046,32 @@ static void hex_map(const double V[8][3], double s, double t, double u, double* 
   *detJ = fabs(det);
 }
 
+/* The 27 nodes of the Q2 hexahedron as points (i, j, k) of the lattice of half steps: the
+ * eight vertices in the Q1 order, then the twelve edge midpoints, the six face centres and
+ * the centre, each group in the order of (k, j, i) (z slowest, x fastest). */
+static const int hex27[27][3] = {
+    {0, 0, 0}, {2, 0, 0}, {2, 2, 0}, {0, 2, 0}, {0, 0, 2}, {2, 0, 2}, {2, 2, 2}, {0, 2, 2},
+    {1, 0, 0}, {0, 1, 0}, {2, 1, 0}, {1, 2, 0}, {0, 0, 1}, {2, 0, 1}, {0, 2, 1}, {2, 2, 1},
+    {1, 0, 2}, {0, 1, 2}, {2, 1, 2}, {1, 2, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {2, 1, 1},
+    {1, 2, 1}, {1, 1, 2}, {1, 1, 1}};
+
+/* Basis of a hexahedron at (s, t, u): Q1 the trilinear functions (as hex_map); Q2 the
+ * products L_i(s) L_j(t) L_k(u) of the 1D quadratic Lagrange functions on {0, 1/2, 1} for
+ * the node at lattice point (i, j, k). */
+static void hex_basis(int order, double s, double t, double u, double* phi) {
+  if (order != 2) {
+    for (int a = 0; a < 8; a++)
+      phi[a] = (hex_corner[a][0] ? s : 1.0 - s) * (hex_corner[a][1] ? t : 1.0 - t) *
+               (hex_corner[a][2] ? u : 1.0 - u);
+    return;
+  }
+  double L[3][3];
+  lagrange1d(2, s, L[0]);
+  lagrange1d(2, t, L[1]);
+  lagrange1d(2, u, L[2]);
+  for (int a = 0; a < 27; a++) phi[a] = L[0][hex27[a][0]] * L[1][hex27[a][1]] * L[2][hex27[a][2]];
+}
+
 /* The lattice point (i, j, k) in {0, 1, 2}^3 of the hexahedron V (see above). */
 static void hex_lattice(const double V[8][3], int i, int j, int k, double* out) {
   double a[3], b[3];
@@ -1093,7 +1120,8 @@ static void integration_hex(actx* c, const hsub* E, const int32_t* J, int64_t nJ
   const or_params* P = c->P;
   double g[3], gw[3];
   gl3_unit(g, gw);
-  double xq[27][3], wx[27], phil[27][8], gq[27][3], gwq[27];
+  int nb = c->nb, order = c->M->order;
+  double xq[27][3], wx[27], phil[27][27], gq[27][3], gwq[27];
   for (int i = 0; i < 3; i++)
     for (int j = 0; j < 3; j++)
       for (int k = 0; k < 3; k++) {
@@ -1102,19 +1130,21 @@ static void integration_hex(actx* c, const hsub* E, const int32_t* J, int64_t nJ
         gq[q][1] = g[j];
         gq[q][2] = g[k];
         gwq[q] = gw[i] * gw[j] * gw[k];
-        double det;
-        hex_map(Vl, E->s0 + E->len * g[i], E->t0 + E->len * g[j], E->u0 + E->len * g[k], xq[q],
-                &det, phil[q]);
+        double det, N[8];
+        double s = E->s0 + E->len * g[i], t = E->t0 + E->len * g[j], u = E->u0 + E->len * g[k];
+        hex_map(Vl, s, t, u, xq[q], &det, N);
+        hex_basis(order, s, t, u, phil[q]);
         wx[q] = gwq[q] * E->len * E->len * E->len * det;
       }
   for (int64_t tt = 0; tt < nJ; tt++) {
     int64_t m = J[tt];
     double Vm[8][3];
     hex_verts(c->M, m, Vm);
-    double S[8][8] = {{0}}, X[8][8] = {{0}};
+    double S[27][27] = {{0}}, X[27][27] = {{0}};
     for (int p = 0; p < 27; p++) {
-      double y[3], detm, phim[8];
-      hex_map(Vm, gq[p][0], gq[p][1], gq[p][2], y, &detm, phim);
+      double y[3], detm, N[8], phim[27];
+      hex_map(Vm, gq[p][0], gq[p][1], gq[p][2], y, &detm, N);
+      hex_basis(order, gq[p][0], gq[p][1], gq[p][2], phim);
       double wy = gwq[p] * detm;
       for (int q = 0; q < 27; q++) {
         double r2 = 0.0;
@@ -1123,25 +1153,25 @@ static void integration_hex(actx* c, const hsub* E, const int32_t* J, int64_t nJ
         double G = wx[q] * wy * P->C * or_eta(P->kernel, r, P->delta) * or_mu(r, P->delta, P->eps);
         c->st->n_point_pairs++;
         if (r >= P->delta - P->eps && r <= P->delta + P->eps) c->st->n_band_pairs++;
-        for (int a = 0; a < 8; a++) {
-          for (int b = 0; b < 8; b++) S[a][b] += G * phim[a] * phim[b];
-          for (int d = 0; d < 8; d++) X[a][d] += G * phim[a] * phil[q][d];
+        for (int a = 0; a < nb; a++) {
+          for (int b = 0; b < nb; b++) S[a][b] += G * phim[a] * phim[b];
+          for (int d = 0; d < nb; d++) X[a][d] += G * phim[a] * phil[q][d];
         }
       }
     }
     c->st->n_integrations++;
-    for (int a = 0; a < 8; a++) {
-      int64_t i = c->M->conn[m * 8 + a];
-      for (int b = 0; b < 8; b++) {
-        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * 8 + b]);
+    for (int a = 0; a < nb; a++) {
+      int64_t i = c->M->conn[m * nb + a];
+      for (int b = 0; b < nb; b++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[m * nb + b]);
         if (!e) {
           c->error = 1;
           continue;
         }
         *e += 2.0 * S[a][b];
       }
-      for (int d = 0; d < 8; d++) {
-        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * 8 + d]);
+      for (int d = 0; d < nb; d++) {
+        double* e = csr_entry(c->row_ptr, c->col, c->values, i, c->M->conn[c->l * nb + d]);
         if (!e) {
           c->error = 1;
           continue;
@@ -1203,7 +1233,7 @@ int or_assemble(const or_mesh* M, const int64_t* pair_off, const int32_t* pair_l
   int64_t nE = M->n_elem, nV = M->n_vert;
   if (dim != 2 && dim != 3) return -1;
   if (M->cell == 1 && dim != 2) return -1; /* quadrilaterals: dim 2 */
-  if (M->cell == 2 && (dim != 3 || M->order != 1)) return -1; /* hexahedra: Q1, dim 3 */
+  if (M->cell == 2 && dim != 3) return -1; /* hexahedra: dim 3 */
   if (!(P->eps > 0.0 && P->eps < P->delta) || P->L_min < 1 || P->L_max < P->L_min) return -1;
   actx c;
   memset(&c, 0, sizeof c);
@@ -1338,11 +1368,12 @@ int or_rhs(const or_mesh* M, const int64_t* row_ptr, const int32_t* col, const d
       for (int i = 0; i < 3; i++)
         for (int j = 0; j < 3; j++)
           for (int k = 0; k < 3; k++) {
-            double x[3], det, phi[8];
-            hex_map(H, g[i], g[j], g[k], x, &det, phi);
+            double x[3], det, N[8], phi[27];
+            hex_map(H, g[i], g[j], g[k], x, &det, N);
+            hex_basis(M->order, g[i], g[j], g[k], phi);
             double f = or_ms_f(ms, dim, x, kernel, delta, eps, C);
-            for (int a = 0; a < 8; a++) {
-              int64_t n = M->conn[e * 8 + a];
+            for (int a = 0; a < nb; a++) {
+              int64_t n = M->conn[e * nb + a];
               if (M->node_free[n]) F[n] += gw[i] * gw[j] * gw[k] * det * f * phi[a];
             }
           }
@@ -1496,10 +1527,11 @@ static double err_on_hex(const or_mesh* M, const double V[8][3], const double* n
       for (int j = 0; j < 3; j++)
         for (int k = 0; k < 3; k++) {
           double u = 0.5 * ((b & 1) + g[i]), v = 0.5 * (((b >> 1) & 1) + g[j]);
-          double w = 0.5 * (((b >> 2) & 1) + g[k]), x[3], det, phi[8];
-          hex_map(V, u, v, w, x, &det, phi);
+          double w = 0.5 * (((b >> 2) & 1) + g[k]), x[3], det, N[8], phi[27];
+          hex_map(V, u, v, w, x, &det, N);
+          hex_basis(M->order, u, v, w, phi);
           double uh = 0.0;
-          for (int a = 0; a < 8; a++) uh += phi[a] * nodal[a];
+          for (int a = 0; a < npe(M); a++) uh += phi[a] * nodal[a];
           double d = or_ms_u(ms, M->dim, x) - uh;
           s += 0.125 * gw[i] * gw[j] * gw[k] * det * d * d;
         }
@@ -1517,9 +1549,9 @@ double or_l2_error(const or_mesh* M, const double* u_h, int ms, int omega_only) 
   for (int64_t e = 0; e < M->n_elem; e++) {
     if (omega_only && !M->elem_in_omega[e]) continue;
     if (M->cell == 2) {
-      double H[8][3], hn[8];
+      double H[8][3], hn[27];
       hex_verts(M, e, H);
-      for (int a = 0; a < 8; a++) hn[a] = u_h[M->conn[e * 8 + a]];
+      for (int a = 0; a < npe(M); a++) hn[a] = u_h[M->conn[e * npe(M) + a]];
       s += err_on_hex(M, H, hn, ms);
       continue;
     }

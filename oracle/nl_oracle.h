@@ -45,9 +45,11 @@ typedef struct {
                                    midpoints of the edges (0,1), (1,2), (2,3), (3,0), then the
                                    image of the square's centre), order 3: the 8-node
                                    serendipity element (the Q2 nodes without the centre);
-                                   2: hexahedra (dim 3), Q1 (trilinear), vertices the images of
-                                   the unit cube's corners (0,0,0), (1,0,0), (1,1,0), (0,1,0),
-                                   (0,0,1), (1,0,1), (1,1,1), (0,1,1) */
+                                   2: hexahedra (dim 3), vertices the images of the unit cube's
+                                   corners (0,0,0), (1,0,0), (1,1,0), (0,1,0), (0,0,1), (1,0,1),
+                                   (1,1,1), (0,1,1); order 1: Q1 (trilinear), order 2: Q2 (27
+                                   nodes on the lattice of half steps: the vertices, the edge
+                                   midpoints, the face centres, the centre) */
 } or_mesh;
 
 /* or_params.flags: the refinement test of Algorithm 1 uses the Euclidean variant of the

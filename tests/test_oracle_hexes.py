@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle as O
-from nl_inputs import hex_mesh, structured_mesh
+from nl_inputs import hex_mesh, q2_hex_mesh, structured_mesh
+from nl_inputs.mesh import HEX27
 from nl_inputs.configs import table7_hex, workload_mesh
 from nl_inputs.mesh import Mesh
 
@@ -76,7 +77,15 @@ def _trilinear(V, s, t, u):
     return X, np.abs(np.linalg.det(J)), N
 
 
-def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth):
+def _q2_basis(s, t, u):
+    """The 27 triquadratic Lagrange functions (nodes HEX27) at the points (s, t, u)."""
+    def L(v):
+        return np.stack([2 * (v - 0.5) * (v - 1), 4 * v * (1 - v), 2 * v * (v - 0.5)], -1)
+    Ls, Lt, Lu = L(s), L(t), L(u)
+    return np.stack([Ls[:, i] * Lt[:, j] * Lu[:, k] for i, j, k in HEX27], -1)
+
+
+def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth, order=1):
     """Outer integral over E_l on the 8^depth sub-cubes of its unit cube (Gauss-Legendre
     3x3x3 on each), inner 3x3x3 on E_m: the blocks 2 S and -2 X."""
     x, w = np.polynomial.legendre.leggauss(3)
@@ -87,9 +96,13 @@ def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth):
     t = (pts[:, 1] + g[pts[:, 4]]) / n
     u = (pts[:, 2] + g[pts[:, 5]]) / n
     X, detl, PL = _trilinear(Vl, s, t, u)
+    if order == 2:
+        PL = _q2_basis(s, t, u)
     WX = gw[pts[:, 3]] * gw[pts[:, 4]] * gw[pts[:, 5]] / n ** 3 * detl
     q = np.array(list(itertools.product(range(3), range(3), range(3))))
     Y, detm, PM = _trilinear(Vm, g[q[:, 0]], g[q[:, 1]], g[q[:, 2]])
+    if order == 2:
+        PM = _q2_basis(g[q[:, 0]], g[q[:, 1]], g[q[:, 2]])
     WY = gw[q[:, 0]] * gw[q[:, 1]] * gw[q[:, 2]] * detm
     R = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
     MU = np.vectorize(lambda r: O.mu(r, delta, eps))(R)
@@ -97,8 +110,9 @@ def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth):
     return 2 * np.einsum("xy,ya,yb->ab", G, PM, PM), -2 * np.einsum("xy,ya,xc->ac", G, PM, PL)
 
 
+@pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("offset", [0.16, 0.205, 0.215])
-def test_algorithm1_hexes_equal_uniform_refinement(offset):
+def test_algorithm1_hexes_equal_uniform_refinement(offset, order):
     # Constant kernel: Algorithm 1 at L_max = L and uniform refinement of l's cube to level L
     # give the same sums up to rounding (an INT sub-element's integrand phi^l_d |det DF_l| has
     # degree <= 3 per reference variable; dropped sub-elements have mu = 0 at every point
@@ -107,23 +121,34 @@ def test_algorithm1_hexes_equal_uniform_refinement(offset):
     base = np.array(CORNERS, float) * 0.05
     Vm = base + rng.uniform(-0.006, 0.006, (8, 3))
     Vl = base + [offset, 0.01, 0.0] + rng.uniform(-0.006, 0.006, (8, 3))
-    coords = np.concatenate([Vm, Vl]).T.copy()
-    mesh = Mesh(dim=3, coords=coords, conn=np.arange(16, dtype=np.int32).reshape(2, 8),
-                elem_in_omega=np.ones(2, np.uint8), node_free=np.ones(16, np.uint8), h=0.05)
+    nb = 8 if order == 1 else 27
+    pts = []
+    for V in (Vm, Vl):
+        if order == 1:
+            pts += list(V)
+        else:  # the 27 nodes at the trilinear images of the lattice points
+            for i, j, k in HEX27:
+                w = [(1 - i / 2 if c[0] == 0 else i / 2) * (1 - j / 2 if c[1] == 0 else j / 2) *
+                     (1 - k / 2 if c[2] == 0 else k / 2) for c in CORNERS]
+                pts.append(sum(w[b] * V[b] for b in range(8)))
+    coords = np.array(pts).T.copy()
+    nn = 2 * nb
+    mesh = Mesh(dim=3, coords=coords, conn=np.arange(nn, dtype=np.int32).reshape(2, nb),
+                elem_in_omega=np.ones(2, np.uint8), node_free=np.ones(nn, np.uint8), h=0.05)
     delta, eps = 0.2, 0.01
     C = O.kernel_constant(3, O.KERNEL_CONST, delta, eps)
     off, pl = O.pairs(mesh, delta, eps)
     assert len(pl) == 4
     rp, col = O.csr(mesh, off, pl)
-    for L in (1, 2, 3):
+    for L in ((1, 2, 3) if order == 1 else (1, 2)):
         vals, _ = O.assemble(mesh, off, pl, rp, col, delta, eps, L)
-        got = np.zeros((16, 16))
-        for i in range(16):
+        got = np.zeros((nn, nn))
+        for i in range(nn):
             got[i, col[rp[i]:rp[i + 1]]] = vals[rp[i]:rp[i + 1]]
-        ref = np.zeros((16, 16))
+        ref = np.zeros((nn, nn))
         for (mi, li) in ((0, 0), (0, 1), (1, 0), (1, 1)):
-            S2, X2 = _uniform_hex_blocks((Vm, Vl)[li], (Vm, Vl)[mi], delta, eps, C, L - 1)
-            nm, nl = np.arange(8) + 8 * mi, np.arange(8) + 8 * li
+            S2, X2 = _uniform_hex_blocks((Vm, Vl)[li], (Vm, Vl)[mi], delta, eps, C, L - 1, order)
+            nm, nl = np.arange(nb) + nb * mi, np.arange(nb) + nb * li
             ref[np.ix_(nm, nm)] += S2
             ref[np.ix_(nm, nl)] += X2
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), L
@@ -141,6 +166,26 @@ def test_hex_zero_row_sums_symmetry_and_linear_consistency():
     assert abs(A - A.T).max() < 1e-14 * np.abs(v1).max()
     r = O.solve_problem(hex_mesh(structured_mesh(3, 3, 1 / 3, 0.0, 2)), 0.4, 0.04, 2, 0)
     assert r["err_all"] < 1e-9
+
+
+def test_q2_hex_row_sums_symmetry_and_consistency():
+    # Q2 (27-node) hexahedra: the basis sums to one (zero row sums), one level makes the rules
+    # coincide (symmetry), u = 1 + x + y + z is reproduced, and u = x^2 + y^2 + z^2 (in the FE
+    # space) up to the integration and mollifier errors, which fall with L_max
+    m = q2_hex_mesh(hex_mesh(structured_mesh(3, 2, 0.5, 0.0, 1, jitter=0.1, seed=3)))
+    off, pl = O.pairs(m, 0.4, 0.04)
+    rp, col = O.csr(m, off, pl)
+    v1, _ = O.assemble(m, off, pl, rp, col, 0.4, 0.04, 1)
+    rows = np.repeat(np.arange(m.n_vert), np.diff(rp))
+    assert np.abs(np.bincount(rows, weights=v1, minlength=m.n_vert)).max() < 1e-12 * np.abs(v1).max()
+    import scipy.sparse as sp
+    A = sp.csr_matrix((v1, col, rp), shape=(m.n_vert, m.n_vert))
+    assert abs(A - A.T).max() < 1e-14 * np.abs(v1).max()
+    m2 = q2_hex_mesh(hex_mesh(structured_mesh(3, 2, 0.5, 0.0, 1)))
+    assert O.solve_problem(m2, 0.4, 0.04, 1, 0)["err_all"] < 1e-12
+    e1 = O.solve_problem(m2, 0.4, 0.04, 1, 1)["err_all"]
+    e2 = O.solve_problem(m2, 0.4, 0.04, 2, 1)["err_all"]
+    assert e2 < 0.1 * e1, (e1, e2)
 
 
 def test_table7_hex_linear():
