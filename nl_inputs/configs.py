@@ -10,7 +10,7 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, replace
 
-from .mesh import Mesh, hex_mesh, p2_mesh, q2_mesh, quad_mesh, structured_mesh
+from .mesh import Mesh, hex_mesh, p2_mesh, q2_hex_mesh, q2_mesh, quad_mesh, structured_mesh
 
 KERNEL_CONST = 0
 KERNEL_GAUSS = 1
@@ -37,8 +37,10 @@ class Workload:
     jitter: float = 0.0
     seed: int = 0
     layer_cells: int = 0  # 0: ceil((delta + eps)/h); otherwise the given number of cells
-    order: int = 1        # 1: P1 elements; 2: P2 triangles on the same triangulation
-    cell: str = "simplex"  # "quad": one quadrilateral per grid cell (2D; Q1, or Q2 with order 2)
+    order: int = 1        # 1: P1 elements; 2: P2 simplices on the same triangulation
+    # "quad": one quadrilateral per grid cell (2D; Q1, or Q2 with order 2); "hex": one
+    # hexahedron per grid cell (3D; Q1, or Q2 with order 2)
+    cell: str = "simplex"
 
     @property
     def layer(self) -> int:
@@ -74,6 +76,15 @@ def table7_hex(ml: int) -> Workload:
     return Workload(name=f"table7_hex_ml{ml}", dim=3, cells=(6 * s, 4 * s, 4 * s), h=0.2 / s,
                     lo=(-0.6, -0.4, -0.4), delta=0.2, eps=0.01875 * (2.0 / 3.0) ** (ml - 1),
                     L_max=2, ms=MS_CUBIC, layer_cells=s, cell="hex")
+
+
+def table6_hex(L_max: int) -> Workload:
+    """Sec. 6, Table 6 (3D consistency, Q2 hexahedra): Omega = [-0.6, 0.6] x [-0.4, 0.4] x
+    [-0.4, 0.4], h = 0.1, delta = 0.2, eps = 0.0125 (3/4)^(L_max-2), L_min = 1,
+    u = x^2 + y^2 + z^2 (f = -6); the layer Gamma is meshed delta wide (2 cells)."""
+    return Workload(name=f"table6_hex_L{L_max}", dim=3, cells=(12, 8, 8), h=0.1,
+                    lo=(-0.6, -0.4, -0.4), delta=0.2, eps=0.0125 * 0.75 ** (L_max - 2),
+                    L_max=L_max, ms=MS_QUADRATIC, layer_cells=2, cell="hex", order=2)
 
 
 def table3_tri(ml: int) -> Workload:
@@ -115,6 +126,10 @@ WORKLOADS = {
     # the c3_3d grid with one Q1 hexahedron per cell (Sec. 6, the HEX meshes of the 3D tests)
     "c3_3d_hex": _unit_box("c3_3d_hex", 3, 16, 0.125, 0.0125, 2, cell="hex"),
     "c3_3d_h10_hex": _unit_box("c3_3d_h10_hex", 3, 10, 0.125, 0.0125, 2, cell="hex"),
+    # the same grids with Q2 (27-node) hexahedra
+    "c3_3d_hex_q2": _unit_box("c3_3d_hex_q2", 3, 16, 0.125, 0.0125, 2, cell="hex", order=2),
+    "c3_3d_h10_hex_q2": _unit_box("c3_3d_h10_hex_q2", 3, 10, 0.125, 0.0125, 2, cell="hex",
+                                  order=2),
     # the same grid with Q2 (biquadratic) quadrilaterals
     "c2_2d_q2": _unit_box("c2_2d_q2", 2, 256, 4 * _H2, 4 * _H2 / 5, 4, jitter=0.1, cell="quad",
                           order=2),
@@ -129,5 +144,5 @@ def workload_mesh(w: Workload) -> Mesh:
         q = quad_mesh(m)
         return q2_mesh(q) if w.order == 2 else q
     if w.cell == "hex":
-        return hex_mesh(m)
+        return q2_hex_mesh(hex_mesh(m)) if w.order == 2 else hex_mesh(m)
     return p2_mesh(m) if w.order == 2 else m

@@ -189,8 +189,6 @@ nl_status kernel_smem_setup(F* kern, size_t smem) {
 // Raises the scatter kernel's shared-memory ceiling before any capture.
 nl_status plan_prepare_scatter(nl_plan* pl) {
   const size_t smem = scatter_smem_bytes(pl->dim + 1, pl->max_row_nnz, pl->prec != NL_PREC_FP64 ? 4 : 8);
-  if (smem == 0)
-    return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", pl->max_row_nnz);
   const bool f32 = pl->prec != NL_PREC_FP64;
   if (pl->dim == 2) return f32 ? kernel_smem_setup(k_scatter_batched<2, float>, smem) : kernel_smem_setup(k_scatter_batched<2, double>, smem);
   return f32 ? kernel_smem_setup(k_scatter_batched<3, float>, smem) : kernel_smem_setup(k_scatter_batched<3, double>, smem);

@@ -401,13 +401,14 @@ __global__ void k_mesh_quads(int64_t n_elem, int64_t n_vert, const double* __res
 }
 
 // Hexahedra (the trilinear image of the unit cube, vertices in the order (0,0,0), (1,0,0),
-// (1,1,0), (0,1,0), (0,0,1), (1,0,1), (1,1,1), (0,1,1)): the eight vertices, the box, the
+// (1,1,0), (0,1,0), (0,0,1), (1,0,1), (1,1,1), (0,1,1), the first 8 of the nb nodes of an
+// element in conn): the eight vertices, the box, the
 // volume (Gauss-Legendre 2x2x2 of |det DF|, exact: the determinant is of degree <= 2 in each
 // variable), no inverse Jacobian, and an FP32 record of its own layout: the offsets v_a - v_0
 // (a = 1..7) at [0, 21), v_0 as a float-float pair at [21, 24) and [24, 27), the volume at
 // [27].
 __global__ void k_mesh_hexes(int64_t n_elem, int64_t n_vert, const double* __restrict__ coords,
-                             const int32_t* __restrict__ conn, double* __restrict__ evert,
+                             const int32_t* __restrict__ conn, int nb, double* __restrict__ evert,
                              double* __restrict__ blo, double* __restrict__ bhi,
                              double* __restrict__ vol, double* __restrict__ jinv,
                              float* __restrict__ ef) {
@@ -415,7 +416,7 @@ __global__ void k_mesh_hexes(int64_t n_elem, int64_t n_vert, const double* __res
   if (e >= n_elem) return;
   double V[8][3];
   for (int a = 0; a < 8; a++) {
-    int32_t v = conn[e * 8 + a];
+    int32_t v = conn[e * nb + a];
     for (int k = 0; k < 3; k++) {
       V[a][k] = coords[k * n_vert + v];
       evert[(e * 8 + a) * 3 + k] = V[a][k];
@@ -514,17 +515,16 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
   if (!out) return fail(NL_EINVAL, "nl_mesh_create: out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create: dim must be 2 or 3");
-  if (order != 1 && !(order == 2 && cell != 2) && !(order == 3 && cell == 1))
+  if (order != 1 && order != 2 && !(order == 3 && cell == 1))
     return fail(NL_EINVAL, "nl_mesh_create: unknown element order %d", order);
   if (cell == 1 && dim != 2) return fail(NL_EINVAL, "nl_mesh_create_quad: quadrilaterals are 2D");
-  if (cell == 2 && (dim != 3 || order != 1))
-    return fail(NL_EINVAL, "nl_mesh_create_hex: Q1 hexahedra are 3D");
+  if (cell == 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create_hex: hexahedra are 3D");
   if (n_vert <= 0 || n_vert > INT32_MAX || n_elem <= 0 || n_elem > INT32_MAX)
     return fail(NL_EINVAL, "nl_mesh_create: bad sizes n_vert=%lld n_elem=%lld",
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
   const int nv = cell == 1 ? 4 : (cell == 2 ? 8 : dim + 1);
-  const int nb = cell == 2 ? 8
+  const int nb = cell == 2 ? (order == 2 ? 27 : 8)
                  : cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4))
                              : (order == 2 ? (dim == 2 ? 6 : 10) : nv);
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
@@ -614,6 +614,24 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
           return fail(NL_EINVAL, "nl_mesh_create_hex: element %lld is inverted or degenerate at corner %d",
                       (long long)e, a);
       }
+      // Q2: node a >= 8 at the trilinear image of its lattice point (i, j, k) / 2
+      for (int a = 8; a < nb; a++) {
+        const int c = hex27_code(a);
+        double w[8];
+        hex_basis<8, double>(0.5 * (c % 3), 0.5 * ((c / 3) % 3), 0.5 * (c / 9), 1.0, w);
+        const int32_t v = conn[e * nb + a];
+        double d2 = 0.0, l2 = 0.0;
+        for (int q = 0; q < 3; q++) {
+          double x = 0.0;
+          for (int b = 0; b < 8; b++) x += w[b] * V[b][q];
+          const double d = coords[q * n_vert + v] - x, ed = V[6][q] - V[0][q];
+          d2 += d * d;
+          l2 += ed * ed;
+        }
+        if (!(d2 <= 1e-18 * l2))
+          return fail(NL_EINVAL, "nl_mesh_create_hex: node %d of element %lld is off its position",
+                      a, (long long)e);
+      }
     } else if (dim == 2) {
       det = (V[1][0] - V[0][0]) * (V[2][1] - V[0][1]) - (V[2][0] - V[0][0]) * (V[1][1] - V[0][1]);
     } else {
@@ -692,7 +710,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
   int tb = 256;
   int64_t gb = (n_elem + tb - 1) / tb;
   if (cell == 2)
-    k_mesh_hexes<<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
+    k_mesh_hexes<<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   else if (cell == 1)
     k_mesh_quads<<<NL_CNT((unsigned)gb), tb, 0, s>>>(n_elem, n_vert, dc.p, dconn.p, nb, ev.p, lo.p, hi.p, vol.p, jinv.p, efb.p);
   else if (dim == 2)
@@ -847,11 +865,12 @@ nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64
                           cuda_stream, out);
 }
 
-nl_status nl_mesh_create_hex(int64_t n_vert, const double* coords, int64_t n_elem,
+nl_status nl_mesh_create_hex(int order, int64_t n_vert, const double* coords, int64_t n_elem,
                              const int32_t* conn, const uint8_t* elem_in_omega,
                              const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
-  return mesh_create_impl(3, 1, 2, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
+  if (order != 1 && order != 2) return nlx::fail(NL_EINVAL, "nl_mesh_create_hex: order must be 1 or 2");
+  return mesh_create_impl(3, order, 2, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
 }
 

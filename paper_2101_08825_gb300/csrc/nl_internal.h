@@ -160,6 +160,51 @@ __host__ __device__ inline void quad_basis(int order, T s, T t, T* phi) {
     phi[3] = ((T)1 - s) * t;
   }
 }
+
+// Node a of a hexahedron as a point (i, j, k) of the lattice {0, 1, 2}^3 of half steps on the
+// unit cube, coded i + 3 j + 9 k: the eight vertices (0,0,0), (1,0,0), (1,1,0), (0,1,0),
+// (0,0,1), (1,0,1), (1,1,1), (0,1,1) (in half steps, doubled), then the 27-node element's
+// twelve edge midpoints, six face centres and the centre, each group in increasing code.
+__host__ __device__ constexpr int hex27_code(int a) {
+  switch (a) {
+    case 0: return 0;   case 1: return 2;   case 2: return 8;   case 3: return 6;
+    case 4: return 18;  case 5: return 20;  case 6: return 26;  case 7: return 24;
+    case 8: return 1;   case 9: return 3;   case 10: return 5;  case 11: return 7;
+    case 12: return 9;  case 13: return 11; case 14: return 15; case 15: return 17;
+    case 16: return 19; case 17: return 21; case 18: return 23; case 19: return 25;
+    case 20: return 4;  case 21: return 10; case 22: return 12; case 23: return 14;
+    case 24: return 16; case 25: return 22; default: return 13;
+  }
+}
+
+// w times the basis of a hexahedron at (s, t, u) of the unit cube: NB = 8 the trilinear
+// functions of the vertices, NB = 27 (Q2) the products L_i(s) L_j(t) L_k(u) of the quadratic
+// Lagrange functions on {0, 1/2, 1} for the node at lattice point (i, j, k).
+template <int NB, typename T>
+__host__ __device__ inline void hex_basis(T s, T t, T u, T w, T* phi) {
+  if (NB == 8) {
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+      const int c = hex27_code(a);
+      phi[a] = w * ((c % 3) ? s : (T)1 - s) * (((c / 3) % 3) ? t : (T)1 - t) * ((c / 9) ? u : (T)1 - u);
+    }
+    return;
+  }
+  const T h = (T)0.5;
+  const T ls[3] = {(T)2 * (s - h) * (s - (T)1), (T)4 * s * ((T)1 - s), (T)2 * s * (s - h)};
+  const T lt[3] = {(T)2 * (t - h) * (t - (T)1), (T)4 * t * ((T)1 - t), (T)2 * t * (t - h)};
+  const T lu[3] = {(T)2 * w * (u - h) * (u - (T)1), (T)4 * w * u * ((T)1 - u), (T)2 * w * u * (u - h)};
+  T st[9];
+#pragma unroll
+  for (int j = 0; j < 3; j++)
+#pragma unroll
+    for (int i = 0; i < 3; i++) st[i + 3 * j] = ls[i] * lt[j];
+#pragma unroll
+  for (int a = 0; a < 27; a++) {
+    const int c = hex27_code(a);
+    phi[a] = st[c % 9] * lu[c / 9];
+  }
+}
 double kernel_constant(int dim, int kernel, double delta, double eps);
 
 // Uploads the rule tables to the current device once.

@@ -68,8 +68,6 @@ template <int D, typename R, int KERN>
 nl_status run_noalloc(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s) {
   NL_TRY((launch_quad<D, R, KERN, true>(P, s)));
   const size_t smem = scatter_smem_bytes(D + 1, p->max_row_nnz, sizeof(R));
-  if (smem == 0)
-    return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
   NL_TRY((allow_smem(k_scatter<D, R>, smem)));
   k_scatter<D, R><<<NL_CNT((unsigned)m->n_elem), 128, smem, s>>>(
       0, 0, 0, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, (const R*)nullptr, P.selfblk, 1,

@@ -1,13 +1,14 @@
 // nl_quad_hex.cu -- nl_assemble on meshes of hexahedra (Sec. 6: the HEX meshes of the 3D
-// tests, Q1 trilinear elements, the Gauss-Legendre 3x3x3 product rule for the inner and the
-// outer integral).
+// tests, Q1 trilinear or Q2 triquadratic elements, the Gauss-Legendre 3x3x3 product rule for
+// the inner and the outer integral).
 //
 // What is computed (Sec. 5, Corollary 1, eqs. J21Nr and J22Nr): for every element pair
 // (m, l) of J, with the 3x3x3 rule on E_m (points y = F_m(g), weights w_y |det DF_m|, rows =
-// the 8 nodes of m) and on the sub-elements E' of E_l that Algorithm 1 selects for this m,
+// the NN nodes of m) and on the sub-elements E' of E_l that Algorithm 1 selects for this m,
 //   A[m_a, m_b] += 2 sum_{x,y} w_x w_y gamma_eps(x,y) phi^m_a(y) phi^m_b(y)
 //   A[m_a, l_d] -= 2 sum_{x,y} w_x w_y gamma_eps(x,y) phi^m_a(y) phi^l_d(x).
-// An element is the trilinear image F of the unit cube; a sub-element is the image of a
+// An element is the trilinear image F of the unit cube (its 8 vertices; a Q2 element's other
+// 19 nodes sit at the images of the lattice of half steps); a sub-element is the image of a
 // sub-cube of l's cube, its outer points x = F_l(s0 + len g_i, t0 + len g_j, u0 + len g_k) with
 // weights w_i w_j w_k len^3 |det DF_l| and the basis of l at those reference points.
 // Algorithm 1 splits a cube into its eight half-size sub-cubes and decides on the box of the
@@ -18,14 +19,21 @@
 // How (k_quad_h): the structure of the other assembly kernels -- a persistent grid, chunks of
 // consecutive m-major pairs per warp, Algorithm 1 as a warp LIFO (4 parents x 8 children per
 // round), decisions in FP64 (FP64 path) or by the FP32 screen with an FP64 re-decision inside
-// the margin (FP32 path), buffered sub-elements integrated by the whole warp.  The warp is
-// four groups of eight lanes: a pass takes 8 outer points, one per lane of a group, and the
-// groups hold inner points 0-6, 7-13, 14-20 and 21-26 of m (56 sums H_d(y) = sum_x w_x C eta
-// mu phi^l_d(x) per lane).  The end of a pair sums H over the 8 lanes of each group through
-// shared memory, writes the cross block -2 sum_y w_y |det DF_m| phi^m_a(y) H_d(y) and keeps
-// g(y) = sum_d H_d(y) for m's self block.  With the constant kernel an INT sub-element adds
-// sum_x w_x C phi^l_d(x), independent of y, to every inner point without evaluating point
-// pairs.
+// the margin (FP32 path), buffered sub-elements integrated by the whole warp.
+//  Q1 (NN = 8): the warp is four groups of eight lanes: a pass takes 8 outer points, one per
+// lane of a group, and the groups hold inner points 0-6, 7-13, 14-20 and 21-26 of m (56 sums
+// H_d(y) = sum_x w_x C eta mu phi^l_d(x) per lane).  The end of a pair sums H over the 8 lanes
+// of each group through shared memory, writes the cross block -2 sum_y w_y |det DF_m|
+// phi^m_a(y) H_d(y) and keeps g(y) = sum_d H_d(y) for m's self block.  With the constant
+// kernel an INT sub-element adds sum_x w_x C phi^l_d(x), independent of y, to every inner
+// point without evaluating point pairs.
+//  Q2 (NN = 27): lane q < 27 holds inner point q and its 27 sums H_d(y_q).  A pass stages 32
+// outer points in shared memory (one per lane: x, the item's kind and w_x phi^l_d(x) for the
+// 27 d), then every lane runs over the staged points (the same point on every lane, so the
+// mollifier's branch is uniform).  A constant-kernel INT sub-element's points are not paired:
+// lane d sums their w_x C phi^l_d(x).  At the end of a pair the H table is transposed through
+// shared memory so that lane d computes column d of the cross block (27 x 27 products with
+// the broadcast rows w_y phi^m_a(y)).
 #include <cuda_runtime.h>
 
 #include "nl_quad_kernel.cuh"
@@ -34,15 +42,23 @@ namespace nlx {
 namespace {
 
 constexpr int HX_NQ = 27;      // Gauss-Legendre 3x3x3 points
-constexpr int HX_NN = 8;       // nodes per element
-constexpr int HX_NYL = 7;      // inner points per lane (4 groups x 7 >= 27)
-constexpr int HX_XPI = 8;      // outer points per pass (lanes per group)
-constexpr int HX_NH = HX_NN * HX_NQ;
-constexpr int HX_NBLK = HX_NN * HX_NN;
 constexpr int HX_IMAX = 64;    // buffered sub-elements
-constexpr int HX_RS = 9;       // row stride of the reduction scratch
+constexpr int HX_RS = 9;       // row stride of the Q1 reduction scratch
 constexpr int HX_REC = 28;     // LIFO record: 8 vertices x 3, s0, t0, u0, pad
 constexpr int HX_WARPS = 4;
+constexpr int HX_SR = 32;      // Q2 staged outer point: x, y, z, kind, w_x phi^l_d (27), pad
+constexpr int HX_WP = 28;      // Q2 row stride of the tables over the 27 points or nodes
+
+// item kinds
+constexpr int HK_INT = 0, HK_FINAL = 1, HK_CLOSED = 2;
+
+// per-lane layout of the inner points: NYL points per lane, XPI outer points per pass
+template <int NN>
+struct HxLay {
+  static constexpr int NYL = NN == 8 ? 7 : 1;
+  static constexpr int XPI = NN == 8 ? 8 : 32;
+  static constexpr int NBLK = NN * NN;
+};
 
 // hexahedron corner a = (x, y, z) bits of the unit cube
 __host__ __device__ constexpr int hx_c(int a, int k) {
@@ -54,30 +70,35 @@ __host__ __device__ constexpr int hx_c(int a, int k) {
 // and low parts at [21, 24) and [24, 27)
 constexpr int HX_EF_V0HI = 21, HX_EF_V0LO = 24;
 
-template <typename R>
+// block tables: the rule (s, t, u, w) in FP64 and R, the basis at the rule's points in FP64
+template <typename R, int NN>
 __host__ __device__ constexpr size_t hx_table_bytes() {
-  return (sizeof(double) * (HX_NQ * 4 + HX_NQ * 8) + sizeof(R) * (HX_NQ * 4 + HX_NQ * 8) + 15) &
-         ~size_t(15);
+  return (sizeof(double) * (HX_NQ * 4 + HX_NQ * NN) + sizeof(R) * (HX_NQ * 4) + 15) & ~size_t(15);
 }
 
-template <typename R>
+template <typename R, int NN>
 struct HMem {
+  // Q1: wpm [8][27], red [8 * 27][RS] + hs [8 * 27 + 8];
+  // Q2: wpm [27][WP], red = the staged outer points [32][SR], at the end of a pair the
+  //     transposed H table [27][WP]
+  static constexpr size_t WPM_N = NN == 8 ? 8 * HX_NQ : 27 * HX_WP;
+  static constexpr size_t RED_N = NN == 8 ? (size_t)8 * HX_NQ * HX_RS + 8 * HX_NQ + 8 : 32 * HX_SR;
   R* sv;         // [scap][REC]
   uint32_t* sc;  // [scap]
-  R* it;         // [IMAX][8]: s0, t0, u0, len, kind (1 = FINAL)
+  R* it;         // [IMAX][8]: s0, t0, u0, len, kind
+  R* wpm;        // w_y |det DF_m(y)| phi^m_a(y)
   R* vl;         // [32]: E_l's 8 vertices in the frame of the inner points
-  R* wpm;        // [8][27]: w_y |det DF_m(y)| phi^m_a(y)
   double* wd;    // [28]
-  R* red;        // [NH][RS]
-  R* hs;         // [NH + 8]
+  R* red;
+  R* hs;
   double* sd;    // [28]
   static __host__ __device__ size_t bytes(int scap) {
     size_t b = sizeof(R) * HX_REC * (size_t)scap + sizeof(uint32_t) * (size_t)scap;
     b = (b + 15) & ~size_t(15);
-    b += sizeof(R) * ((size_t)HX_IMAX * 8 + HX_NN * HX_NQ + 32);
+    b += sizeof(R) * ((size_t)HX_IMAX * 8 + WPM_N + 32);
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * 28;
-    b += sizeof(R) * ((size_t)HX_NH * HX_RS + HX_NH + 8);
+    b += sizeof(R) * RED_N;
     b = (b + 15) & ~size_t(15);
     b += sizeof(double) * 28;
     return (b + 15) & ~size_t(15);
@@ -89,18 +110,35 @@ struct HMem {
     off = (off + 15) & ~size_t(15);
     it = reinterpret_cast<R*>(base + off);
     wpm = it + (size_t)HX_IMAX * 8;
-    vl = wpm + HX_NN * HX_NQ;
-    off += sizeof(R) * ((size_t)HX_IMAX * 8 + HX_NN * HX_NQ + 32);
+    vl = wpm + WPM_N;
+    off += sizeof(R) * ((size_t)HX_IMAX * 8 + WPM_N + 32);
     off = (off + 15) & ~size_t(15);
     wd = reinterpret_cast<double*>(base + off);
     off += sizeof(double) * 28;
-    red = reinterpret_cast<R*>(base + off);
-    hs = red + (size_t)HX_NH * HX_RS;
-    off += sizeof(R) * ((size_t)HX_NH * HX_RS + HX_NH + 8);
+    red = reinterpret_cast<R*>(base + off);  // 16-byte aligned: 28 doubles after an aligned offset
+    hs = red + (size_t)8 * HX_NQ * HX_RS;    // Q1 only
+    off += sizeof(R) * RED_N;
     off = (off + 15) & ~size_t(15);
     sd = reinterpret_cast<double*>(base + off);
   }
 };
+
+// four consecutive values from 16-byte aligned shared memory
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  o[0] = a.x;
+  o[1] = a.y;
+  o[2] = b.x;
+  o[3] = b.y;
+}
 
 // x = F(s, t, u) of the hexahedron V (8 vertices, x y z each), |det DF(s, t, u)| and the
 // trilinear basis N
@@ -251,16 +289,18 @@ __device__ __noinline__ int hexact_classify(const double* __restrict__ evert_l,
   return ACT_DROP;
 }
 
-template <typename R, int KERN>
-__global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ? 2 : 1)
+template <typename R, int KERN, int NN>
+__global__ void __launch_bounds__(HX_WARPS * 32,
+                                  std::is_same<R, float>::value ? (NN == 8 ? 2 : 3) : 1)
     k_quad_h(const QParams P) {
   constexpr bool F32 = std::is_same<R, float>::value;
+  constexpr bool Q2 = NN == 27;
+  constexpr int NYL = HxLay<NN>::NYL, XPI = HxLay<NN>::XPI, NBLK = HxLay<NN>::NBLK;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) char smem_raw[];
   double* tS = reinterpret_cast<double*>(smem_raw);  // [27][4]: s, t, u, w
-  double* tB = tS + HX_NQ * 4;                        // [27][8]: the basis at point q
-  R* rS = reinterpret_cast<R*>(tB + HX_NQ * 8);
-  R* rB = rS + HX_NQ * 4;
+  double* tB = tS + HX_NQ * 4;                        // [27][NN]: the basis at point q
+  R* rS = reinterpret_cast<R*>(tB + HX_NQ * NN);
   for (int q = threadIdx.x; q < HX_NQ; q += blockDim.x) {
     const int i = q / 9, j = (q / 3) % 3, k = q % 3;
     const double s = P.B[i][0], t = P.B[j][0], u = P.B[k][0];  // the 3-point rule (host-filled)
@@ -268,18 +308,17 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
     tS[q * 4 + 1] = t;
     tS[q * 4 + 2] = u;
     tS[q * 4 + 3] = P.W[i] * P.W[j] * P.W[k];
-    for (int a = 0; a < 8; a++)
-      tB[q * 8 + a] = (hx_c(a, 0) ? s : 1.0 - s) * (hx_c(a, 1) ? t : 1.0 - t) * (hx_c(a, 2) ? u : 1.0 - u);
+    hex_basis<NN, double>(s, t, u, 1.0, tB + q * NN);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < HX_NQ * 4; t += blockDim.x) rS[t] = (R)tS[t];
-  for (int t = threadIdx.x; t < HX_NQ * 8; t += blockDim.x) rB[t] = (R)tB[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int ybase = (lane >> 3) * HX_NYL;  // first inner point of this lane's group
-  const int xl = lane & 7;                  // outer point slot of this lane
-  HMem<R> wm;
-  wm.carve(smem_raw + hx_table_bytes<R>() + (size_t)wid * HMem<R>::bytes(P.scap), P.scap);
+  // Q1: first inner point of this lane's group and its outer point slot; Q2: inner point q
+  const int ybase = Q2 ? lane : (lane >> 3) * NYL;
+  const int xl = Q2 ? lane : lane & 7;
+  HMem<R, NN> wm;
+  wm.carve(smem_raw + hx_table_bytes<R, NN>() + (size_t)wid * HMem<R, NN>::bytes(P.scap), P.scap);
 
   unsigned st_items = 0, st_exact = 0, st_eval = 0, st_closed = 0, st_band = 0;
   int err = 0;
@@ -287,18 +326,18 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
   double v0m[3] = {0.0, 0.0, 0.0}, mlo[3] = {0.0, 0.0, 0.0}, mhi[3] = {0.0, 0.0, 0.0};
   float v0h[3] = {0.f, 0.f, 0.f}, v0l[3] = {0.f, 0.f, 0.f}, flo[3] = {0.f, 0.f, 0.f};
   float fhi[3] = {0.f, 0.f, 0.f};
-  R y[HX_NYL][3];
+  R y[NYL][3];
   R gsh = 0, gsl = 0;  // lane q < 27: sum of g(y_q) over the current m-run
 
   auto flush_self = [&]() {
     if (lane < HX_NQ) wm.sd[lane] = (double)gsh + (double)gsl;
     gsh = gsl = 0;
     __syncwarp();
-    for (int e = lane; e < HX_NBLK; e += 32) {
-      const int a = e / HX_NN, b = e % HX_NN;
+    for (int e = lane; e < NBLK; e += 32) {
+      const int a = e / NN, b = e % NN;
       double s = 0.0;
-      for (int q = 0; q < HX_NQ; q++) s += wm.wd[q] * tB[q * 8 + a] * tB[q * 8 + b] * wm.sd[q];
-      atomicAdd(&P.selfblk[cur_m * HX_NBLK + e], 2.0 * s);
+      for (int q = 0; q < HX_NQ; q++) s += wm.wd[q] * tB[q * NN + a] * tB[q * NN + b] * wm.sd[q];
+      atomicAdd(&P.selfblk[cur_m * NBLK + e], 2.0 * s);
     }
     __syncwarp();
   };
@@ -368,7 +407,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
 #pragma unroll
           for (int k = 0; k < 3; k++) Vmr[a * 3 + k] = P.evert[(m * 8 + a) * 3 + k] - v0m[k];
 #pragma unroll
-        for (int i = 0; i < HX_NYL; i++) {
+        for (int i = 0; i < NYL; i++) {
           const int q = min(ybase + i, HX_NQ - 1);
           double x[3], det, N[8];
           hmap<double>(Vmr, tS[q * 4], tS[q * 4 + 1], tS[q * 4 + 2], x, det, N);
@@ -380,8 +419,15 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
           hmap<double>(Vmr, tS[lane * 4], tS[lane * 4 + 1], tS[lane * 4 + 2], x, det, N);
           const double wy = tS[lane * 4 + 3] * det;
           wm.wd[lane] = wy;
+          if constexpr (Q2) {
+#pragma unroll 1
+            for (int a = 0; a < NN; a++) wm.wpm[a * HX_WP + lane] = (R)(wy * tB[lane * NN + a]);
+          } else {
 #pragma unroll
-          for (int a = 0; a < 8; a++) wm.wpm[a * HX_NQ + lane] = (R)(wy * N[a]);
+            for (int a = 0; a < 8; a++) wm.wpm[a * HX_NQ + lane] = (R)(wy * N[a]);
+          }
+        } else if (Q2 && lane == HX_NQ) {
+          for (int a = 0; a < NN; a++) wm.wpm[a * HX_WP + HX_NQ] = (R)0;  // the rows' pad
         }
         if constexpr (F32) {
           const float* ef = P.ef + m * NL_EF_STRIDE(3);
@@ -420,14 +466,15 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
       }
       __syncwarp();
       const R* VL = wm.vl;
-      R H[HX_NN][HX_NYL];
+      R H[NN][NYL];
 #pragma unroll
-      for (int d = 0; d < HX_NN; d++)
+      for (int d = 0; d < NN; d++)
 #pragma unroll
-        for (int i = 0; i < HX_NYL; i++) H[d][i] = 0;
-      R U[HX_NN];
+        for (int i = 0; i < NYL; i++) H[d][i] = 0;
+      // Q1: the closed forms' sums per node d; Q2: lane d's sum for node d
+      R U[Q2 ? 1 : NN];
 #pragma unroll
-      for (int d = 0; d < HX_NN; d++) U[d] = 0;
+      for (int d = 0; d < (Q2 ? 1 : NN); d++) U[d] = 0;
       bool contrib = false, has_u = false;
 
       auto classify = [&](const R (&V)[8][3], uint32_t code, bool count_exact) -> int {
@@ -458,28 +505,30 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
           return ACT_DROP;
         }
       };
-      // closed form of an INT sub-element (constant kernel): sum_x w_x C phi^l_d(x) over the
-      // sub-cube, the same at every inner point (summed over the warp at the end of the pair)
+      // Q1: closed form of an INT sub-element (constant kernel): sum_x w_x C phi^l_d(x) over
+      // the sub-cube, the same at every inner point (summed over the warp at the end of the pair)
       auto closed_int = [&](R s0, R t0, R u0, R len) {
+        if constexpr (!Q2) {
 #pragma unroll 1
-        for (int q = 0; q < HX_NQ; q++) {  // not unrolled: rare, keeps the code small
-          R x[3], det, N[8];
-          hmap<R>(VL, s0 + len * rS[q * 4], t0 + len * rS[q * 4 + 1], u0 + len * rS[q * 4 + 2], x, det, N);
-          const R w = rS[q * 4 + 3] * det * (wl * len * len * len);
+          for (int q = 0; q < HX_NQ; q++) {  // not unrolled: rare, keeps the code small
+            R x[3], det, N[8];
+            hmap<R>(VL, s0 + len * rS[q * 4], t0 + len * rS[q * 4 + 1], u0 + len * rS[q * 4 + 2], x, det, N);
+            const R w = rS[q * 4 + 3] * det * (wl * len * len * len);
 #pragma unroll
-          for (int d = 0; d < HX_NN; d++) U[d] += w * N[d];
+            for (int d = 0; d < NN; d++) U[d] += w * N[d];
+          }
+          has_u = true;
+          st_closed++;
+          contrib = true;
         }
-        has_u = true;
-        st_closed++;
-        contrib = true;
       };
-      auto put_item = [&](int slot, R s0, R t0, R u0, int level, int fin) {
+      auto put_item = [&](int slot, R s0, R t0, R u0, int level, int kind) {
         R* r = wm.it + slot * 8;
         r[0] = s0;
         r[1] = t0;
         r[2] = u0;
         r[3] = pow2m(R(0), level - 1);  // the sub-cube's side, a power of two
-        r[4] = fin ? (R)1 : (R)0;
+        r[4] = (R)kind;
       };
       auto push = [&](int slot, const R (&V)[8][3], R s0, R t0, R u0, uint32_t code) {
         R* r = wm.sv + slot * HX_REC;
@@ -492,27 +541,28 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
         r[26] = u0;
         wm.sc[slot] = code;
       };
-      auto integrate = [&](int n_it) {
+      // Q1: 8 outer points per pass, each paired with the 7 inner points of the lane's group
+      auto integrate1 = [&](int n_it) {
         const int n_x = n_it * HX_NQ;
         st_eval += (unsigned)(n_x * HX_NQ);
         contrib = true;
         const MollK MK{P.fmqe, P.ftqe, P.fue};
-        for (int base = 0; base < n_x; base += HX_XPI) {
+        for (int base = 0; base < n_x; base += XPI) {
           const int o = base + xl;
           const bool valid = o < n_x;
           const int itx = valid ? o / HX_NQ : 0;
           const int q = valid ? o - itx * HX_NQ : 0;
           const R* r = wm.it + itx * 8;
           const R len = r[3];
-          const bool fin = r[4] != (R)0;
+          const bool fin = r[4] == (R)HK_FINAL;
           R x[3], det, N[8];
           hmap<R>(VL, r[0] + len * rS[q * 4], r[1] + len * rS[q * 4 + 1], r[2] + len * rS[q * 4 + 2], x, det, N);
           const R wx = valid ? rS[q * 4 + 3] * (wl * len * len * len) * det : (R)0;
-          R bw[HX_NN];
+          R bw[8];
 #pragma unroll
-          for (int d = 0; d < HX_NN; d++) bw[d] = wx * N[d];
+          for (int d = 0; d < 8; d++) bw[d] = wx * N[d];
 #pragma unroll
-          for (int i = 0; i < HX_NYL; i++) {
+          for (int i = 0; i < NYL; i++) {
             const bool yv = ybase + i < HX_NQ;
             const R d0 = x[0] - y[i][0], d1 = x[1] - y[i][1], d2 = x[2] - y[i][2];
             const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
@@ -528,9 +578,85 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
             }
             if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
 #pragma unroll
-            for (int d = 0; d < HX_NN; d++) H[d][i] += g * bw[d];
+            for (int d = 0; d < (Q2 ? 1 : NN); d++) H[d][i] += g * bw[d];
           }
         }
+      };
+      // Q2: 32 outer points staged per pass; every lane runs over the staged points
+      auto integrate2 = [&](int n_it) {
+        const int n_x = n_it * HX_NQ;
+        contrib = true;
+        const MollK MK{P.fmqe, P.ftqe, P.fue};
+        for (int base = 0; base < n_x; base += XPI) {
+          const int o = base + lane;
+          const bool valid = o < n_x;
+          const int itx = valid ? o / HX_NQ : 0;
+          const int q = valid ? o - itx * HX_NQ : 0;
+          const R* r = wm.it + itx * 8;
+          const R len = r[3];
+          const R kind = r[4];
+          const R s = r[0] + len * rS[q * 4], t = r[1] + len * rS[q * 4 + 1], u = r[2] + len * rS[q * 4 + 2];
+          R x[3], det, N[8];
+          hmap<R>(VL, s, t, u, x, det, N);
+          const R wx = valid ? rS[q * 4 + 3] * (wl * len * len * len) * det : (R)0;
+          R* sp = wm.red + lane * HX_SR;
+          sp[0] = x[0];
+          sp[1] = x[1];
+          sp[2] = x[2];
+          sp[3] = kind;
+          hex_basis<27, R>(s, t, u, wx, sp + 4);
+          sp[31] = (R)0;
+          __syncwarp();
+          const unsigned vm = __ballot_sync(FULL, valid);
+          const unsigned cm = __ballot_sync(FULL, valid && kind == (R)HK_CLOSED);
+          if (cm != 0u && lane < HX_NQ) {
+            unsigned c = cm;
+            while (c) {
+              const int oo = __ffs(c) - 1;
+              c &= c - 1u;
+              U[0] += wm.red[oo * HX_SR + 4 + lane];
+            }
+          }
+          unsigned em = vm & ~cm;
+          st_eval += (unsigned)(__popc(em) * HX_NQ);
+          while (em) {
+            const int oo = __ffs(em) - 1;
+            em &= em - 1u;
+            const R* op = wm.red + oo * HX_SR;
+            R hd[4];
+            ld4(op, hd);
+            const R d0 = hd[0] - y[0][0], d1 = hd[1] - y[0][1], d2 = hd[2] - y[0][2];
+            const R r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            R g = 1;
+            if (hd[3] == (R)HK_FINAL) {  // the same staged point on every lane: a uniform branch
+              if constexpr (F32) {
+                g = mollifier_bf(MK, r2);
+                if (P.count_band) st_band += (lane < HX_NQ && r2 >= P.fdme2 && r2 <= P.fdpe2) ? 1 : 0;
+              } else {
+                g = mollifier(P, r2);
+                if (P.count_band) st_band += (lane < HX_NQ && r2 >= P.dme * P.dme && r2 <= P.dpe * P.dpe) ? 1 : 0;
+              }
+            }
+            if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
+#pragma unroll
+            for (int j = 0; j < 7; j++) {
+              R b[4];
+              ld4(op + 4 + 4 * j, b);
+#pragma unroll
+              for (int v = 0; v < 4; v++)
+                if (4 * j + v < NN) H[(4 * j + v) % NN][0] += g * b[v];
+            }
+          }
+          __syncwarp();  // the staged points are read before the next pass writes them
+        }
+      };
+      auto integrate = [&](int n_it) {
+        if constexpr (Q2) integrate2(n_it);
+        else integrate1(n_it);
+      };
+      // the kind of a buffered INT or FINAL sub-element
+      auto item_kind = [&](int act) -> int {
+        return act == ACT_FINAL ? HK_FINAL : ((Q2 && KERN == NL_KERNEL_CONST) ? HK_CLOSED : HK_INT);
       };
 
       // ---- Algorithm 1 for this pair ------------------------------------------------------
@@ -550,11 +676,15 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
         }
         if (act0 == ACT_INT || act0 == ACT_FINAL || act0 == ACT_ZERO) st_items += (lane == 0);
         if (KERN == NL_KERNEL_CONST && act0 == ACT_INT) {
-          if (lane == 0) closed_int((R)0, (R)0, (R)0, (R)1);
-          act0 = ACT_DROP;
+          if constexpr (Q2) {
+            st_closed += (lane == 0);
+          } else {
+            if (lane == 0) closed_int((R)0, (R)0, (R)0, (R)1);
+            act0 = ACT_DROP;
+          }
         }
         if (act0 == ACT_INT || act0 == ACT_FINAL) {
-          if (lane == 0) put_item(0, (R)0, (R)0, (R)0, 1, act0 == ACT_FINAL);
+          if (lane == 0) put_item(0, (R)0, (R)0, (R)0, 1, item_kind(act0));
           n_it = 1;
         } else if (act0 == ACT_REFINE) {
           sp = 1;  // pushed above
@@ -588,14 +718,18 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
           const int level = code >> LEVEL_SHIFT;
           if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
           if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
-            closed_int(s0, t0, u0, pow2m(R(0), level - 1));
-            act = ACT_DROP;
+            if constexpr (Q2) {
+              st_closed++;
+            } else {
+              closed_int(s0, t0, u0, pow2m(R(0), level - 1));
+              act = ACT_DROP;
+            }
           }
           const unsigned m_it = __ballot_sync(FULL, act == ACT_INT || act == ACT_FINAL);
           const unsigned m_ref = __ballot_sync(FULL, act == ACT_REFINE);
           const unsigned below = (1u << lane) - 1u;
           if (act == ACT_INT || act == ACT_FINAL)
-            put_item(n_it + __popc(m_it & below), s0, t0, u0, level, act == ACT_FINAL);
+            put_item(n_it + __popc(m_it & below), s0, t0, u0, level, item_kind(act));
           const int nref = __popc(m_ref);
           const bool overflow = base + nref > P.scap;
           if (overflow) err |= ERR_STACK;
@@ -608,42 +742,79 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
       }
 
       // ---- end of pair ---------------------------------------------------------------------
-      R* bp = reinterpret_cast<R*>(P.blk) + (p - P.p_begin) * HX_NBLK;
+      R* bp = reinterpret_cast<R*>(P.blk) + (p - P.p_begin) * NBLK;
       if (!__any_sync(FULL, contrib)) {
-        for (int e = lane; e < HX_NBLK; e += 32) bp[e] = (R)0;
+        for (int e = lane; e < NBLK; e += 32) bp[e] = (R)0;
         __syncwarp();
         continue;
       }
-      if (__any_sync(FULL, has_u)) {
+      if constexpr (Q2) {
+        // lane q writes row q of the H table; lane d then holds column d (+ its closed sum)
+        R usum = U[0];
 #pragma unroll
-        for (int d = 0; d < HX_NN; d++)
+        for (int o = 16; o > 0; o >>= 1) usum += __shfl_xor_sync(FULL, usum, o);
+        if (lane < HX_NQ) {
+          R* row = wm.red + lane * HX_WP;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) U[d] += __shfl_xor_sync(FULL, U[d], o);
-      }
+          for (int d = 0; d < NN; d++) row[d] = H[d][0];
+          row[HX_NQ] = (R)0;
+        }
+        __syncwarp();
+        if (lane < HX_NQ) {
+          R col[HX_WP];
 #pragma unroll
-      for (int d = 0; d < HX_NN; d++)
+          for (int q = 0; q < HX_NQ; q++) col[q] = wm.red[q * HX_WP + lane] + U[0];
+          col[HX_NQ] = (R)0;
+#pragma unroll 1
+          for (int a = 0; a < NN; a++) {
+            const R* wr = wm.wpm + a * HX_WP;
+            R s = 0;
 #pragma unroll
-        for (int i = 0; i < HX_NYL; i++)
-          if (ybase + i < HX_NQ) wm.red[(d * HX_NQ + ybase + i) * HX_RS + xl] = H[d][i];
-      __syncwarp();
-      for (int j = lane; j < HX_NH; j += 32) {
-        R s = 0;
+            for (int j = 0; j < 7; j++) {
+              R w4[4];
+              ld4(wr + 4 * j, w4);
 #pragma unroll
-        for (int t = 0; t < HX_XPI; t++) s += wm.red[j * HX_RS + t];
-        wm.hs[j] = s + U[j / HX_NQ];
-      }
-      __syncwarp();
-      for (int e = lane; e < HX_NBLK; e += 32) {
-        const int a = e / HX_NN, d = e % HX_NN;
-        R s = 0;
-        for (int q = 0; q < HX_NQ; q++) s += wm.wpm[a * HX_NQ + q] * wm.hs[d * HX_NQ + q];
-        bp[e] = (R)(-2) * s;
-      }
-      if (lane < HX_NQ) {
-        R g = 0;
+              for (int v = 0; v < 4; v++) s += w4[v] * col[4 * j + v];
+            }
+            bp[a * NN + lane] = (R)(-2) * s;
+          }
+          R g = usum;
 #pragma unroll
-        for (int d = 0; d < HX_NN; d++) g += wm.hs[d * HX_NQ + lane];
-        two_sum_add(gsh, gsl, g);
+          for (int d = 0; d < NN; d++) g += H[d][0];
+          two_sum_add(gsh, gsl, g);
+        }
+      } else {
+        if (__any_sync(FULL, has_u)) {
+#pragma unroll
+          for (int d = 0; d < NN; d++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) U[d] += __shfl_xor_sync(FULL, U[d], o);
+        }
+#pragma unroll
+        for (int d = 0; d < NN; d++)
+#pragma unroll
+          for (int i = 0; i < NYL; i++)
+            if (ybase + i < HX_NQ) wm.red[(d * HX_NQ + ybase + i) * HX_RS + xl] = H[d][i];
+        __syncwarp();
+        for (int j = lane; j < NN * HX_NQ; j += 32) {
+          R s = 0;
+#pragma unroll
+          for (int t = 0; t < XPI; t++) s += wm.red[j * HX_RS + t];
+          wm.hs[j] = s + U[j / HX_NQ];
+        }
+        __syncwarp();
+        for (int e = lane; e < NBLK; e += 32) {
+          const int a = e / NN, d = e % NN;
+          R s = 0;
+          for (int q = 0; q < HX_NQ; q++) s += wm.wpm[a * HX_NQ + q] * wm.hs[d * HX_NQ + q];
+          bp[e] = (R)(-2) * s;
+        }
+        if (lane < HX_NQ) {
+          R g = 0;
+#pragma unroll
+          for (int d = 0; d < NN; d++) g += wm.hs[d * HX_NQ + lane];
+          two_sum_add(gsh, gsl, g);
+        }
       }
       __syncwarp();  // the scratch and E_l's vertices are read before the next pair writes them
     }
@@ -652,18 +823,18 @@ __global__ void __launch_bounds__(HX_WARPS * 32, std::is_same<R, float>::value ?
   if (cur_m >= 0) flush_self();
 }
 
-template <typename R, int KERN>
+template <typename R, int KERN, int NN>
 nl_status launch_quad_h(const QParams& P, cudaStream_t s) {
   int dev = 0, nsm = 0;
   NL_CUDA(cudaGetDevice(&dev));
   NL_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const size_t per_warp = HMem<R>::bytes(P.scap);
+  const size_t per_warp = HMem<R, NN>::bytes(P.scap);
   int warps = HX_WARPS;
-  while (warps > 1 && hx_table_bytes<R>() + warps * per_warp > (size_t)200 * 1024) warps >>= 1;
-  const size_t smem = hx_table_bytes<R>() + warps * per_warp;
+  while (warps > 1 && hx_table_bytes<R, NN>() + warps * per_warp > (size_t)200 * 1024) warps >>= 1;
+  const size_t smem = hx_table_bytes<R, NN>() + warps * per_warp;
   if (smem > (size_t)220 * 1024)
     return fail(NL_EINTERNAL, "hexahedral assembly kernel needs %zu bytes of shared memory", smem);
-  auto kern = k_quad_h<R, KERN>;
+  auto kern = k_quad_h<R, KERN, NN>;
   NL_TRY(allow_smem(kern, smem));
   int per_sm = 0;
   NL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem));
@@ -673,20 +844,21 @@ nl_status launch_quad_h(const QParams& P, cudaStream_t s) {
   return NL_OK;
 }
 
-template <typename R, int KERN>
+template <typename R, int KERN, int NN>
 nl_status run_assembly_h(nl_mesh* m, nl_pairs* p, QParams P, double* values, cudaStream_t s,
                          unsigned long long* scratch, int* err, PhaseTimer& T) {
   size_t free_b = 0, total_b = 0;
   NL_CUDA(cudaMemGetInfo(&free_b, &total_b));
   size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 4);
   if (g_block_budget) budget = std::min(budget, g_block_budget);
-  int64_t batch = std::max<int64_t>(1 << 20, (int64_t)(budget / (sizeof(R) * HX_NBLK)));
+  constexpr int NBLK = HxLay<NN>::NBLK;
+  int64_t batch = std::max<int64_t>(1 << 20, (int64_t)(budget / (sizeof(R) * NBLK)));
   batch = std::min<int64_t>(batch, p->n_pairs);
   DevBuf<R> blk;
   DevBuf<double> selfblk;
-  NL_TRY(blk.alloc((size_t)batch * HX_NBLK, s));
-  NL_TRY(selfblk.alloc((size_t)m->n_elem * HX_NBLK, s));
-  NL_CUDA(cudaMemsetAsync(selfblk.p, 0, sizeof(double) * m->n_elem * HX_NBLK, s));
+  NL_TRY(blk.alloc((size_t)batch * NBLK, s));
+  NL_TRY(selfblk.alloc((size_t)m->n_elem * NBLK, s));
+  NL_CUDA(cudaMemsetAsync(selfblk.p, 0, sizeof(double) * m->n_elem * NBLK, s));
   std::vector<int64_t> h_off(m->n_elem + 1);
   NL_CUDA(cudaMemcpyAsync(h_off.data(), p->pair_off, sizeof(int64_t) * (m->n_elem + 1),
                           cudaMemcpyDeviceToHost, s));
@@ -699,14 +871,14 @@ nl_status run_assembly_h(nl_mesh* m, nl_pairs* p, QParams P, double* values, cud
     P.p_end = b1;
     NL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s));  // work counter
     NL_TRY(T.mark(0, s));
-    NL_TRY((launch_quad_h<R, KERN>(P, s)));
+    NL_TRY((launch_quad_h<R, KERN, NN>(P, s)));
     NL_TRY(T.mark(0, s));
     NL_TRY(T.mark(1, s));
-    NL_TRY((launch_scatter<3, R, HX_NN>(m, p, b0, b1, blk.p, nullptr, 0, values, err, s, h_off.data())));
+    NL_TRY((launch_scatter<3, R, NN>(m, p, b0, b1, blk.p, nullptr, 0, values, err, s, h_off.data())));
     NL_TRY(T.mark(1, s));
   }
   NL_TRY(T.mark(1, s));
-  NL_TRY((launch_scatter<3, R, HX_NN>(m, p, 0, 0, blk.p, selfblk.p, 1, values, err, s, h_off.data())));
+  NL_TRY((launch_scatter<3, R, NN>(m, p, 0, 0, blk.p, selfblk.p, 1, values, err, s, h_off.data())));
   NL_TRY(T.mark(1, s));
   if (std::is_same<R, float>::value) {
     k_diag_from_rows<<<NL_CNT((unsigned)((m->n_vert * 32 + 255) / 256)), 256, 0, s>>>(
@@ -750,10 +922,17 @@ nl_status assemble_values_hex(nl_mesh* m, nl_pairs* p, const nl_kernel_params* k
   const bool gauss = kp->kernel == NL_KERNEL_TRUNC_GAUSS;
   PhaseTimer T;
   if (p->n_pairs > 0) {
-    if (f32) rc = gauss ? run_assembly_h<float, 1>(m, p, P, values, s, scratch.p, err.p, T)
-                        : run_assembly_h<float, 0>(m, p, P, values, s, scratch.p, err.p, T);
-    else rc = gauss ? run_assembly_h<double, 1>(m, p, P, values, s, scratch.p, err.p, T)
-                    : run_assembly_h<double, 0>(m, p, P, values, s, scratch.p, err.p, T);
+    if (m->nb == 27) {
+      if (f32) rc = gauss ? run_assembly_h<float, 1, 27>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly_h<float, 0, 27>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly_h<double, 1, 27>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly_h<double, 0, 27>(m, p, P, values, s, scratch.p, err.p, T);
+    } else {
+      if (f32) rc = gauss ? run_assembly_h<float, 1, 8>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly_h<float, 0, 8>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly_h<double, 1, 8>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly_h<double, 0, 8>(m, p, P, values, s, scratch.p, err.p, T);
+    }
   }
   cudaEventRecord(e1, s);
   unsigned long long hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};

@@ -1860,13 +1860,14 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
           else atomicAdd(&acc[roff[a] + ps], bv[a]);
         }
       }
-      if (with_self && threadIdx.x < NB) {
-        const int a = threadIdx.x / NV, b = threadIdx.x % NV;
-        const int slot = lookup(nodes[b]);
-        const int ps = slot < 0 ? -1 : pos[slot * NV + a];
-        if (ps < 0) atomicOr(err, ERR_CSR);
-        else atomicAdd(&acc[roff[a] + ps], (R)selfblk[m * NB + threadIdx.x]);
-      }
+      if (with_self)
+        for (int t = threadIdx.x; t < NB; t += blockDim.x) {
+          const int a = t / NV, b = t % NV;
+          const int slot = lookup(nodes[b]);
+          const int ps = slot < 0 ? -1 : pos[slot * NV + a];
+          if (ps < 0) atomicOr(err, ERR_CSR);
+          else atomicAdd(&acc[roff[a] + ps], (R)selfblk[m * NB + t]);
+        }
       __syncthreads();
       for (int a = 0; a < NV; a++)
         for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) {
@@ -1877,13 +1878,17 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     }
     __syncthreads();  // the table is abandoned; its memory is reused below
   }
+  // the rows' column lists cached in shared memory when they fit, else searched in global
+  // memory (elements with very long rows, e.g. 27-node hexahedra)
+  const bool cache_rows = (size_t)total * 4 <= (size_t)dyn;
   int32_t* rows = reinterpret_cast<int32_t*>(sraw);
-  for (int a = 0; a < NV; a++)
-    for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) rows[roff[a] + t] = col[rbeg[a] + t];
+  if (cache_rows)
+    for (int a = 0; a < NV; a++)
+      for (int t = threadIdx.x; t < rlen[a]; t += blockDim.x) rows[roff[a] + t] = col[rbeg[a] + t];
   __syncthreads();
   auto find = [&](int a, int32_t j) -> int64_t {
     int lo = 0, hi = rlen[a] - 1;
-    const int32_t* r = rows + roff[a];
+    const int32_t* r = cache_rows ? rows + roff[a] : col + rbeg[a];
     while (lo <= hi) {
       int mid = (lo + hi) >> 1;
       int32_t c = r[mid];
@@ -1896,7 +1901,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   // With enough dynamic shared memory the element's contributions are first summed per CSR
   // entry in shared memory; otherwise every contribution goes to the global values directly.
   const int acc_off = (total + 3) & ~3;  // ints before the (8-byte aligned) accumulators
-  const bool use_acc = (size_t)acc_off * 4 + (size_t)total * 8 <= (size_t)dyn;
+  const bool use_acc = cache_rows && (size_t)acc_off * 4 + (size_t)total * 8 <= (size_t)dyn;
   double* acc = reinterpret_cast<double*>(rows + acc_off);
   if (use_acc) {
     for (int t = threadIdx.x; t < total; t += blockDim.x) acc[t] = 0.0;
@@ -1918,12 +1923,13 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     }
     add(a, pos, (double)blk[(p - p_base) * NB + e]);
   }
-  if (with_self && threadIdx.x < NB) {
-    const int a = threadIdx.x / NV, b = threadIdx.x % NV;
-    const int64_t pos = find(a, nodes[b]);
-    if (pos < 0) atomicOr(err, ERR_CSR);
-    else add(a, pos, selfblk[m * NB + threadIdx.x]);
-  }
+  if (with_self)
+    for (int t = threadIdx.x; t < NB; t += blockDim.x) {
+      const int a = t / NV, b = t % NV;
+      const int64_t pos = find(a, nodes[b]);
+      if (pos < 0) atomicOr(err, ERR_CSR);
+      else add(a, pos, selfblk[m * NB + t]);
+    }
   if (use_acc) {
     __syncthreads();
     for (int a = 0; a < NV; a++)
@@ -1935,9 +1941,9 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
 }
 
 // Dynamic shared memory of the scatter kernels for elements of nn nodes, rows of up to max_row
-// columns and blocks of acc_size-byte values: the hash layout when it fits in 200 KB, else the cached column lists
-// plus FP64 accumulators when that fits, else the column lists only (0 if even those do not
-// fit).
+// columns and blocks of acc_size-byte values: the hash layout when it fits in 200 KB, else the
+// cached column lists plus FP64 accumulators when that fits, else the column lists only, else
+// 16 bytes (the rows are then searched in global memory).
 inline size_t scatter_smem_bytes(int nn, int max_row, size_t acc_size) {
   const size_t total = (size_t)nn * (size_t)std::max(1, max_row);
   const size_t hashed =
@@ -1946,7 +1952,7 @@ inline size_t scatter_smem_bytes(int nn, int max_row, size_t acc_size) {
   const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
   if (with_acc <= (size_t)200 * 1024) return with_acc;
   if (total * 4 <= (size_t)200 * 1024) return total * 4;
-  return 0;
+  return 16;
 }
 
 // Single problem: CTA b handles element m_begin + b; with_self = 0 adds the cross blocks of
@@ -2025,8 +2031,6 @@ nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end
   }
   if (m_end <= m_begin) return NL_OK;
   const size_t smem = scatter_smem_bytes(NN, p->max_row_nnz, sizeof(R));
-  if (smem == 0)
-    return fail(NL_EINTERNAL, "rows of %d columns exceed the scatter kernel's shared memory", p->max_row_nnz);
   NL_TRY((allow_smem(k_scatter<D, R, NN>, smem)));
   k_scatter<D, R, NN><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
       m_begin, p_begin, p_end, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, blk, selfblk,

@@ -96,31 +96,34 @@ __global__ void k_rhs_quads(int64_t n_elem, const int32_t* __restrict__ conn,
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], acc[a]);
 }
 
-// F_i += int_E f phi_i per hexahedron of Omega (Q1): Gauss-Legendre 3x3x3 on the unit cube
-// mapped by the element's trilinear map; G = the 3 points and weights on [0, 1].
+// F_i += int_E f phi_i per hexahedron of Omega (Q1, NB = 8, or Q2, NB = 27; f interpolated in
+// the element space): Gauss-Legendre 3x3x3 on the unit cube mapped by the element's trilinear
+// map; G = the 3 points and weights on [0, 1].
+template <int NB>
 __global__ void k_rhs_hexes(int64_t n_elem, const int32_t* __restrict__ conn,
                             const uint8_t* __restrict__ eio, const uint8_t* __restrict__ free_,
                             const double* __restrict__ evert, const double* __restrict__ fn,
                             double f_const, const double* __restrict__ G, double* __restrict__ F) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= n_elem || !eio[e]) return;
-  const int cc[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0}, {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
-  int32_t nd[8];
-  double fv[8], acc[8], V[8][3];
-  for (int a = 0; a < 8; a++) {
-    nd[a] = conn[e * 8 + a];
+  int32_t nd[NB];
+  double fv[NB], acc[NB], V[8][3];
+  for (int a = 0; a < NB; a++) {
+    nd[a] = conn[e * NB + a];
     fv[a] = fn ? fn[nd[a]] : 0.0;
     acc[a] = 0.0;
-    for (int k = 0; k < 3; k++) V[a][k] = evert[(e * 8 + a) * 3 + k];
   }
+  for (int a = 0; a < 8; a++)
+    for (int k = 0; k < 3; k++) V[a][k] = evert[(e * 8 + a) * 3 + k];
   for (int q = 0; q < 27; q++) {
     const double s = G[q / 9], t = G[(q / 3) % 3], u = G[q % 3];
     const double w = G[3 + q / 9] * G[3 + (q / 3) % 3] * G[3 + q % 3];
-    double N[8], J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int a = 0; a < 8; a++) {
-      const double fs = cc[a][0] ? s : 1.0 - s, ft = cc[a][1] ? t : 1.0 - t, fu = cc[a][2] ? u : 1.0 - u;
-      const double ds = cc[a][0] ? 1.0 : -1.0, dt = cc[a][1] ? 1.0 : -1.0, du = cc[a][2] ? 1.0 : -1.0;
-      N[a] = fs * ft * fu;
+      const int c = hex27_code(a);
+      const bool bx = c % 3, by = (c / 3) % 3, bz = c / 9;
+      const double fs = bx ? s : 1.0 - s, ft = by ? t : 1.0 - t, fu = bz ? u : 1.0 - u;
+      const double ds = bx ? 1.0 : -1.0, dt = by ? 1.0 : -1.0, du = bz ? 1.0 : -1.0;
       for (int k = 0; k < 3; k++) {
         J[k][0] += ds * ft * fu * V[a][k];
         J[k][1] += fs * dt * fu * V[a][k];
@@ -130,11 +133,13 @@ __global__ void k_rhs_hexes(int64_t n_elem, const int32_t* __restrict__ conn,
     const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                        J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
                        J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double phi[NB];
+    hex_basis<NB, double>(s, t, u, 1.0, phi);
     double f = f_const;
-    for (int a = 0; a < 8; a++) f += N[a] * fv[a];
-    for (int a = 0; a < 8; a++) acc[a] += w * fabs(det) * f * N[a];
+    for (int a = 0; a < NB; a++) f += phi[a] * fv[a];
+    for (int a = 0; a < NB; a++) acc[a] += w * fabs(det) * f * phi[a];
   }
-  for (int a = 0; a < 8; a++)
+  for (int a = 0; a < NB; a++)
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], acc[a]);
 }
 
@@ -628,9 +633,12 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
     NL_CUDA(cudaMemcpyAsync(HG.p, hg, sizeof hg, cudaMemcpyHostToDevice, s));
     NL_CUDA(cudaStreamSynchronize(s));  // hg lives on this stack frame
   }
-  if (m->cell == 2)
-    k_rhs_hexes<<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
-                                          m->evert, fn.p, f_const, HG.p, F);
+  if (m->cell == 2 && m->nb == 27)
+    k_rhs_hexes<27><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                              m->evert, fn.p, f_const, HG.p, F);
+  else if (m->cell == 2)
+    k_rhs_hexes<8><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                             m->evert, fn.p, f_const, HG.p, F);
   else if (m->cell == 1 && m->nb == 9)
     k_rhs_quads<9><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                              m->evert, fn.p, f_const, QB.p, QS.p, F);

@@ -87,7 +87,7 @@ def lib():
         "nl_mesh_create": (st, [i, i64, p, i64, p, p, p, p, pp]),
         "nl_mesh_create_p2": (st, [i, i64, p, i64, p, p, p, p, pp]),
         "nl_mesh_create_quad": (st, [i, i64, p, i64, p, p, p, p, pp]),
-        "nl_mesh_create_hex": (st, [i64, p, i64, p, p, p, p, pp]),
+        "nl_mesh_create_hex": (st, [i, i64, p, i64, p, p, p, p, pp]),
         "nl_mesh_create_box": (st, [i, p, d, p, ctypes.c_int32, d, ctypes.c_uint64, p, pp]),
         "nl_mesh_info": (st, [p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                               ctypes.POINTER(ctypes.c_int64)]),
@@ -315,14 +315,14 @@ def nl_mesh_create_quad(order, coords, conn, elem_in_omega, node_free, stream=No
     return Mesh(h)
 
 
-def nl_mesh_create_hex(coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
-    """Mesh of Q1 hexahedra: conn rows of 8 vertices."""
+def nl_mesh_create_hex(order, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
+    """Mesh of hexahedra: conn rows of 8 vertices (Q1, order 1) or 27 nodes (Q2, order 2)."""
     coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(3, -1)
-    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 8)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, {1: 8, 2: 27}[int(order)])
     eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
     nf = np.ascontiguousarray(node_free, dtype=np.uint8)
     h = ctypes.c_void_p()
-    _check(lib().nl_mesh_create_hex(coords.shape[1], _ptr(coords), conn.shape[0], _ptr(conn), _ptr(eio),
+    _check(lib().nl_mesh_create_hex(int(order), coords.shape[1], _ptr(coords), conn.shape[0], _ptr(conn), _ptr(eio),
                                     _ptr(nf), stream if stream is not None else current_stream(),
                                     ctypes.byref(h)), "nl_mesh_create_hex")
     return Mesh(h)
@@ -330,9 +330,10 @@ def nl_mesh_create_hex(coords, conn, elem_in_omega, node_free, stream=None) -> M
 
 def mesh_from(mesh, stream=None) -> Mesh:
     """Uploads an nl_inputs.Mesh: P1 simplices, P2 simplices (six or ten nodes per element),
-    quadrilaterals (2D, four, eight or nine nodes per element) or hexahedra (3D, eight)."""
-    if mesh.dim == 3 and mesh.conn.shape[1] == 8:
-        return nl_mesh_create_hex(mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
+    quadrilaterals (2D, four, eight or nine nodes per element) or hexahedra (3D, eight or
+    twenty-seven)."""
+    if mesh.dim == 3 and mesh.conn.shape[1] in (8, 27):
+        return nl_mesh_create_hex(1 if mesh.conn.shape[1] == 8 else 2, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
     if mesh.dim == 2 and mesh.conn.shape[1] in (4, 8, 9):
         return nl_mesh_create_quad({4: 1, 9: 2, 8: 3}[mesh.conn.shape[1]], mesh.coords, mesh.conn,
                                    mesh.elem_in_omega, mesh.node_free, stream)

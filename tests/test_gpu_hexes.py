@@ -1,5 +1,6 @@
-"""Hexahedra on the GPU (Sec. 6: the HEX meshes of the 3D tests, Q1 trilinear elements,
-Gauss-Legendre 3x3x3), through the C ABI, against the oracle on the same seeded meshes.
+"""Hexahedra on the GPU (Sec. 6: the HEX meshes of the 3D tests, Q1 trilinear and Q2
+triquadratic elements, Gauss-Legendre 3x3x3), through the C ABI, against the oracle on the
+same seeded meshes.
 
 Tolerances as for the other elements (test_gpu_parity): pair lists, CSR pattern and
 Algorithm-1 work counts bit-exact; A within 1e-12 relative (Frobenius, and per entry against
@@ -10,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from nl_inputs import WORKLOADS, hex_mesh, structured_mesh, workload_mesh
+from nl_inputs import WORKLOADS, hex_mesh, q2_hex_mesh, structured_mesh, workload_mesh
 from nl_inputs.configs import table7_hex
 from paper_2101_08825_gb300 import nl
 
@@ -24,6 +25,11 @@ def _h(n, layer, jitter, seed):
     return hex_mesh(structured_mesh(3, n, 1 / n, 0.0, layer, jitter=jitter, seed=seed))
 
 
+def _q2(seed):
+    # 27 Q2 hexahedra of side 0.2 (one cell of Omega and a layer of one), jittered vertices
+    return q2_hex_mesh(hex_mesh(structured_mesh(3, 1, 0.2, 0.0, 1, jitter=0.1, seed=seed)))
+
+
 CASES = [
     # (name, mesh factory, delta, eps, L_max, L_min, kernel, mindist_l2)
     ("jit_L2", lambda: _h(3, 1, 0.15, 1), 0.4, 0.04, 2, 1, 0, False),
@@ -33,6 +39,14 @@ CASES = [
     ("gauss", lambda: _h(3, 1, 0.1, 5), 0.4, 0.02, 2, 1, 1, False),
     ("euclid", lambda: _h(3, 1, 0.1, 6), 0.4, 0.04, 2, 1, 0, True),
     ("t7_ml1", lambda: workload_mesh(table7_hex(1)), 0.2, 0.01875, 2, 1, 0, False),
+    # Q2: INT (closed form), FINAL and dropped sub-elements at delta = 2h, every level of
+    # refinement at delta < h
+    ("q2_L1", lambda: _q2(3), 0.4, 0.04, 1, 1, 0, False),
+    ("q2_L2", lambda: _q2(3), 0.4, 0.04, 2, 1, 0, False),
+    ("q2_L3", lambda: _q2(4), 0.15, 0.02, 3, 1, 0, False),
+    ("q2_Lmin2", lambda: _q2(5), 0.4, 0.04, 2, 2, 0, False),
+    ("q2_gauss", lambda: _q2(6), 0.4, 0.02, 2, 1, 1, False),
+    ("q2_euclid", lambda: _q2(7), 0.4, 0.04, 2, 1, 0, True),
 ]
 
 
@@ -52,7 +66,7 @@ def test_hex_pairs_pattern_counts_and_values(case):
     rp0, col0 = O.csr(mesh, off0, pl0)
     v0, st0 = O.assemble(mesh, off0, pl0, rp0, col0, delta, eps, L_max, L_min, kernel, mindist_l2=l2)
     m = nl.mesh_from(mesh)
-    assert m.order() == (1, 8)
+    assert m.order() == ((1, 8) if mesh.conn.shape[1] == 8 else (2, 27))
     p = nl.nl_pairs_build(m, delta, eps)
     off, pl, rp, col = p.export(mesh.n_elem, mesh.n_vert)
     assert np.array_equal(off, off0)
@@ -81,7 +95,7 @@ def test_hex_mesh_round_trip_and_validation():
     bad = mesh.conn.copy()
     bad[4] = bad[4][[1, 0, 3, 2, 5, 4, 7, 6]]  # mirrored: negative Jacobian
     with pytest.raises(nl.NLError):
-        nl.nl_mesh_create_hex(mesh.coords, bad, mesh.elem_in_omega, mesh.node_free)
+        nl.nl_mesh_create_hex(1, mesh.coords, bad, mesh.elem_in_omega, mesh.node_free)
 
 
 def test_table7_hex_linear_on_gpu():
@@ -142,3 +156,49 @@ def test_hex_full_size_sampled_rows():
             assert np.array_equal(col[rp[i]:rp[i + 1]], ocol[orp[i]:orp[i + 1]]), i
             g_row, o_row = vals[rp[i]:rp[i + 1]], ovals[orp[i]:orp[i + 1]]
             assert np.linalg.norm(g_row - o_row) / np.linalg.norm(o_row) < tol, (prec, i)
+
+
+def test_q2_hex_mesh_validation():
+    mesh = _q2(8)
+    m = nl.mesh_from(mesh)
+    coords, conn, eio, nf = m.export()
+    assert np.array_equal(coords, mesh.coords) and np.array_equal(conn, mesh.conn)
+    bad = mesh.coords.copy()
+    bad[0, mesh.conn[13, 26]] += 0.01  # the centre node off the image of (1/2, 1/2, 1/2)
+    with pytest.raises(nl.NLError):
+        nl.nl_mesh_create_hex(2, bad, mesh.conn, mesh.elem_in_omega, mesh.node_free)
+    with pytest.raises(nl.NLError):
+        nl.nl_mesh_create_hex(3, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free)
+
+
+def test_q2_hex_rhs_and_solve_against_oracle():
+    # F_i = int f phi_i over the elements of Omega with lifted Dirichlet data (u = x^2 + y^2 +
+    # z^2, f constant, so its Q2 interpolant is exact), from the same matrix: the GPU
+    # right-hand side against the oracle's, the GPU solution against the oracle's dense solve
+    mesh = _q2(9)
+    delta, eps, L = 0.4, 0.04, 2
+    C = O.kernel_constant(3, 0, delta, eps)
+    m = nl.mesh_from(mesh)
+    p = nl.nl_pairs_build(m, delta, eps)
+    _, _, rp, col = p.export(mesh.n_elem, mesh.n_vert)
+    A, _ = nl.nl_assemble(m, p, delta, eps, L)
+    vals = A.export()
+    F0 = O.rhs(mesh, rp, col, vals, 1, 0, delta, eps, C)
+    g = np.array([O.ms_u(1, mesh.coords[:, i]) for i in range(mesh.n_vert)])
+    f = np.array([O.ms_f(1, mesh.coords[:, i], 0, delta, eps, C) for i in range(mesh.n_vert)])
+    b = nl.nl_rhs(m, A, g, f_nodes=f)
+    F = b.export()
+    assert np.abs(F - F0).max() <= 1e-10 * np.abs(F0).max()
+    u, *_ = nl.nl_solve(A, b, g, solver=1, rtol=1e-13)
+    u0 = O.solve_dense(mesh, rp, col, vals, F0, 1)
+    assert np.abs(u - u0).max() <= 1e-9 * np.abs(u0).max()
+
+
+def _golden(name):
+    import os
+    gold = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        if line.strip() and not line.startswith("#"):
+            parts = line.split()
+            gold[int(parts[0])] = float(parts[1])
+    return gold
