@@ -226,7 +226,7 @@ def describe(w, mesh):
         shape = "hexahedra"
     n_omega = int(mesh.elem_in_omega.sum())
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
-    order = {6: "P2", 10: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2",
+    order = {6: "P2", 10: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2", 27: "Q2",
              8: "Q1" if mesh.dim == 3 else "serendipity"}.get(mesh.conn.shape[1], "P1")
     return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} {order} {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
@@ -244,7 +244,7 @@ def _is_quad(mesh):
 
 
 def _is_hex(mesh):
-    return mesh.dim == 3 and mesh.conn.shape[1] == 8
+    return mesh.dim == 3 and mesh.conn.shape[1] in (8, 27)
 
 
 def l2_err_omega_quads(mesh, u_h):
@@ -277,8 +277,9 @@ def l2_err_omega_quads(mesh, u_h):
 
 
 def l2_err_omega_hexes(mesh, u_h):
-    """||u - u_h||_{L2(Omega)} on Q1 hexahedra (u = sum x_k^2): Gauss-Legendre 3x3x3 on each
-    element's unit cube mapped by its trilinear map."""
+    """||u - u_h||_{L2(Omega)} on hexahedra (u = sum x_k^2): Gauss-Legendre 3x3x3 on each
+    element's unit cube mapped by its trilinear map; Q1, or Q2 (products of the 1D Lagrange
+    bases on {0, 1/2, 1}, nodes in the order of nl_inputs.HEX27)."""
     x, gw = np.polynomial.legendre.leggauss(3)
     g, gw = (x + 1) / 2, gw / 2
     S, T, U = np.meshgrid(g, g, g, indexing="ij")
@@ -293,11 +294,19 @@ def l2_err_omega_hexes(mesh, u_h):
         dN.append(np.stack([ds * ft * fu, fs * dt * fu, fs * ft * du], -1))
     N, dN = np.stack(N, 1), np.stack(dN, 1)  # (27, 8), (27, 8, 3)
     conn = mesh.conn[mesh.elem_in_omega.astype(bool)]
-    V = mesh.points()[conn]  # (ne, 8, 3)
+    V = mesh.points()[conn[:, :8]]  # (ne, 8, 3)
     X = np.einsum("qa,eak->eqk", N, V)
     J = np.einsum("qar,eak->eqkr", dN, V)
     det = np.abs(np.linalg.det(J))
-    uh = np.einsum("qa,ea->eq", N, u_h[conn])
+    phi = N
+    if conn.shape[1] == 27:
+        from nl_inputs import HEX27
+
+        def L(v):
+            return np.stack([2 * (v - 0.5) * (v - 1), 4 * v * (1 - v), 2 * v * (v - 0.5)], 1)
+        Ls, Lt, Lu = L(s), L(t), L(u)
+        phi = np.stack([Ls[:, i] * Lt[:, j] * Lu[:, k] for i, j, k in HEX27], 1)
+    uh = np.einsum("qa,ea->eq", phi, u_h[conn])
     d = (X ** 2).sum(-1) - uh
     return float(math.sqrt(np.sum(det * W[None, :] * d * d)))
 
@@ -418,7 +427,7 @@ def _roofline(nl, dmesh, mesh, w, prec, stats, l2=False, stb=None):
         "frac_evaluated_only": round(achieved_ev / peak, 4),
         "kernel": (f"k_quad_p2<{rtype},{w.kernel}>" if nb == 6 else
                    f"k_quad_p2t<{rtype},{w.kernel}>" if nb == 10 else
-                   f"k_quad_h<{rtype},{w.kernel}>" if _is_hex(mesh) else
+                   f"k_quad_h<{rtype},{w.kernel},{nb}>" if _is_hex(mesh) else
                    f"k_quad_q<{rtype},{w.kernel},{ {4: 1, 9: 2, 8: 3}[nb] }>" if _is_quad(mesh) else
                    f"k_quad<{mesh.dim},{rtype},{w.kernel}>"), "flops_per_assembly": flops,
         "kernel_ms_per_assembly": round(quad_ms, 3),
@@ -599,7 +608,7 @@ def run_ours(args, rank, world, local):
                                       args.p2_steps, args.p2_fp64_steps)
     if args.quad_steps > 0:
         for key, name in (("q1", "c2_2d_q1"), ("q2", "c2_2d_q2"), ("hex", "c3_3d_hex"),
-                          ("p2_tet", "c3_3d_p2")):
+                          ("hex_q2", "c3_3d_hex_q2"), ("p2_tet", "c3_3d_p2")):
             out[key] = run_element_block(args, nl, torch, stream, flush, world, name,
                                          args.quad_steps, args.quad_fp64_steps)
     if args.eps_study:

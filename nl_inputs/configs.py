@@ -10,7 +10,7 @@ from __future__ import annotations
 import math
 from dataclasses import dataclass, replace
 
-from .mesh import Mesh, hex_mesh, p2_mesh, q2_hex_mesh, q2_mesh, quad_mesh, structured_mesh
+from .mesh import Mesh, hex_mesh, p2_mesh, q2_hex_mesh, q2_mesh, quad_mesh, s20_hex_mesh, structured_mesh
 
 KERNEL_CONST = 0
 KERNEL_GAUSS = 1
@@ -39,7 +39,8 @@ class Workload:
     layer_cells: int = 0  # 0: ceil((delta + eps)/h); otherwise the given number of cells
     order: int = 1        # 1: P1 elements; 2: P2 simplices on the same triangulation
     # "quad": one quadrilateral per grid cell (2D; Q1, or Q2 with order 2); "hex": one
-    # hexahedron per grid cell (3D; Q1, or Q2 with order 2)
+    # hexahedron per grid cell (3D; Q1, Q2 with order 2, the 20-node serendipity element with
+    # order 3)
     cell: str = "simplex"
 
     @property
@@ -144,5 +145,8 @@ def workload_mesh(w: Workload) -> Mesh:
         q = quad_mesh(m)
         return q2_mesh(q) if w.order == 2 else q
     if w.cell == "hex":
-        return q2_hex_mesh(hex_mesh(m)) if w.order == 2 else hex_mesh(m)
+        if w.order == 1:
+            return hex_mesh(m)
+        q2 = q2_hex_mesh(hex_mesh(m))
+        return s20_hex_mesh(q2) if w.order == 3 else q2
     return p2_mesh(m) if w.order == 2 else m

@@ -292,3 +292,19 @@ def q2_hex_mesh(mesh: Mesh) -> Mesh:
     free[: mesh.n_vert] = mesh.node_free.astype(bool)
     return Mesh(dim=3, coords=coords, conn=np.ascontiguousarray(conn), elem_in_omega=mesh.elem_in_omega.copy(),
                 node_free=free.astype(np.uint8), h=mesh.h, meta=dict(mesh.meta, order=2))
+
+
+def s20_hex_mesh(mesh: Mesh) -> Mesh:
+    """The 20-node serendipity mesh of a Q2 hexahedral mesh: the first 20 nodes of each
+    element (the vertices and the edge midpoints, in the order HEX27), the face-centre and
+    centre nodes dropped and the remaining nodes renumbered in their order (the vertices keep
+    their numbers)."""
+    if mesh.dim != 3 or mesh.conn.shape[1] != 27:
+        raise ValueError("serendipity hexahedral meshes are built from Q2 hexahedral meshes")
+    keep = np.unique(mesh.conn[:, :20])
+    new = np.full(mesh.n_vert, -1, dtype=np.int64)
+    new[keep] = np.arange(len(keep))
+    conn = new[mesh.conn[:, :20]].astype(np.int32)
+    return Mesh(dim=3, coords=np.ascontiguousarray(mesh.coords[:, keep]), conn=np.ascontiguousarray(conn),
+                elem_in_omega=mesh.elem_in_omega.copy(), node_free=mesh.node_free[keep].copy(),
+                h=mesh.h, meta=dict(mesh.meta, order=3))

@@ -112,11 +112,12 @@ class OMesh:
         self.elem_in_omega = np.ascontiguousarray(mesh.elem_in_omega, dtype=np.uint8)
         self.node_free = np.ascontiguousarray(mesh.node_free, dtype=np.uint8)
         # nodes per element -> element kind: 2D 3 P1 / 6 P2 triangles, 4 Q1 / 9 Q2 / 8
-        # serendipity quadrilaterals (order 3); 3D 4 P1 tetrahedra, 8 Q1 hexahedra (cell 2)
+        # serendipity quadrilaterals (order 3); 3D 4 P1 / 10 P2 tetrahedra, 8 Q1 / 27 Q2 / 20
+        # serendipity hexahedra (cell 2)
         npe = self.conn.shape[1]
-        self.cell = 1 if (self.dim == 2 and npe in (4, 8, 9)) else (2 if (self.dim == 3 and npe in (8, 27)) else 0)
+        self.cell = 1 if (self.dim == 2 and npe in (4, 8, 9)) else (2 if (self.dim == 3 and npe in (8, 20, 27)) else 0)
         self.order = 2 if (npe in (6, 9, 27) or (self.dim == 3 and npe == 10)) else \
-            (3 if (self.cell == 1 and npe == 8) else 1)
+            (3 if ((self.cell == 1 and npe == 8) or (self.cell == 2 and npe == 20)) else 1)
         self.c = _Mesh(self.dim, self.coords.shape[1], self.conn.shape[0], _ptr(self.coords).value,
                        _ptr(self.conn).value, _ptr(self.elem_in_omega).value,
                        _ptr(self.node_free).value, self.order, self.cell)

@@ -389,7 +389,7 @@ double or_aprx_min_dist_l2(int dim, const double* lo1, const double* hi1, const 
  * the edges (0,1), (1,2), (0,2)); P2 tetrahedra 10 (the vertices, then the midpoints of the
  * edges (0,1), (1,2), (0,2), (0,3), (1,3), (2,3)). */
 static int npe(const or_mesh* M) {
-  if (M->cell == 2) return (M->order == 2) ? 27 : 8;
+  if (M->cell == 2) return (M->order == 2) ? 27 : (M->order == 3) ? 20 : 8;
   if (M->cell == 1) return (M->order == 2) ? 9 : (M->order == 3) ? 8 : 4;
   if (M->order == 2) return M->dim == 2 ? 6 : 10;
   return M->dim + 1;
@@ -399,7 +399,7 @@ static int nverts(const or_mesh* M) { return (M->cell == 1) ? 4 : M->dim + 1; }
 
 /* The 8 vertices of hexahedron e (its first 8 nodes) and their box. */
 static void hex_verts(const or_mesh* M, int64_t e, double V[8][3]) {
-  int nb = (M->order == 2) ? 27 : 8;
+  int nb = npe(M);
   for (int a = 0; a < 8; a++) {
     int64_t v = M->conn[e * nb + a];
     for (int k = 0; k < 3; k++) V[a][k] = M->coords[k * M->n_vert + v];
@@ -1057,8 +1057,32 @@ static const int hex27[27][3] = {
 
 /* Basis of a hexahedron at (s, t, u): Q1 the trilinear functions (as hex_map); Q2 the
  * products L_i(s) L_j(t) L_k(u) of the 1D quadratic Lagrange functions on {0, 1/2, 1} for
- * the node at lattice point (i, j, k). */
+ * the node at lattice point (i, j, k); order 3 the 20-node serendipity element (the Q2 nodes
+ * without the face centres and the centre, i.e. the first 20 of hex27), written on
+ * (xi, eta, zeta) = (2s-1, 2t-1, 2u-1) with node a at (xi_a, eta_a, zeta_a) = (i-1, j-1, k-1):
+ * a corner has (1/8)(1 + xi xi_a)(1 + eta eta_a)(1 + zeta zeta_a)(xi xi_a + eta eta_a +
+ * zeta zeta_a - 2), an edge node with xi_a = 0 has (1/4)(1 - xi^2)(1 + eta eta_a)(1 + zeta
+ * zeta_a), and likewise along eta and zeta. */
 static void hex_basis(int order, double s, double t, double u, double* phi) {
+  if (order == 3) {
+    double c[3] = {2.0 * s - 1.0, 2.0 * t - 1.0, 2.0 * u - 1.0};
+    for (int a = 0; a < 20; a++) {
+      double f[3], p = 1.0;
+      int mid = -1;
+      for (int k = 0; k < 3; k++) {
+        f[k] = (double)(hex27[a][k] - 1);
+        if (f[k] == 0.0) mid = k;
+      }
+      if (mid < 0) {
+        for (int k = 0; k < 3; k++) p *= 1.0 + c[k] * f[k];
+        phi[a] = 0.125 * p * (c[0] * f[0] + c[1] * f[1] + c[2] * f[2] - 2.0);
+      } else {
+        for (int k = 0; k < 3; k++) p *= (k == mid) ? 1.0 - c[k] * c[k] : 1.0 + c[k] * f[k];
+        phi[a] = 0.25 * p;
+      }
+    }
+    return;
+  }
   if (order != 2) {
     for (int a = 0; a < 8; a++)
       phi[a] = (hex_corner[a][0] ? s : 1.0 - s) * (hex_corner[a][1] ? t : 1.0 - t) *

@@ -569,7 +569,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
                         4 + j, (long long)e);
         }
       }
-    } else if (order == 2) {
+    } else if (order == 2 && cell == 0) {
       // straight-sided P2: edge node nv + j at the midpoint of edge j = (0,1), (1,2), (0,2)
       // (and for tetrahedra (0,3), (1,3), (2,3))
       static const int ea[6] = {0, 1, 0, 0, 1, 2}, eb[6] = {1, 2, 2, 3, 3, 3};

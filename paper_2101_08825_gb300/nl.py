@@ -318,7 +318,7 @@ def nl_mesh_create_quad(order, coords, conn, elem_in_omega, node_free, stream=No
 def nl_mesh_create_hex(order, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
     """Mesh of hexahedra: conn rows of 8 vertices (Q1, order 1) or 27 nodes (Q2, order 2)."""
     coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(3, -1)
-    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, {1: 8, 2: 27}[int(order)])
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 8 if int(order) == 1 else 27)
     eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
     nf = np.ascontiguousarray(node_free, dtype=np.uint8)
     h = ctypes.c_void_p()

@@ -1,5 +1,6 @@
-"""The oracle's hexahedra (Sec. 6, the three-dimensional tests: HEX meshes, Q1 trilinear
-elements, the Gauss-Legendre 3x3x3 rule for both integrals) against what the paper and the
+"""The oracle's hexahedra (Sec. 6, the three-dimensional tests: HEX meshes, Q1 trilinear, Q2
+triquadratic and 20-node serendipity elements, the Gauss-Legendre 3x3x3 rule for both
+integrals) against what the paper and the
 mathematics fix: the printed HEX linear column of Table 7, exact integrals, closed-form local
 matrices of fully-interior pairs, Algorithm 1 against brute-force uniform refinement, zero row
 sums, symmetry at one level and linear consistency.
@@ -10,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from nl_inputs import hex_mesh, q2_hex_mesh, structured_mesh
+from nl_inputs import hex_mesh, q2_hex_mesh, s20_hex_mesh, structured_mesh
 from nl_inputs.mesh import HEX27
 from nl_inputs.configs import table7_hex, workload_mesh
 from nl_inputs.mesh import Mesh
@@ -85,6 +86,21 @@ def _q2_basis(s, t, u):
     return np.stack([Ls[:, i] * Lt[:, j] * Lu[:, k] for i, j, k in HEX27], -1)
 
 
+def _s20_basis(s, t, u):
+    """The 20-node serendipity functions (nodes: the first 20 of HEX27) at (s, t, u), as the
+    interpolation basis of the serendipity space span{1, x, y, z, x^2, y^2, z^2, xy, yz, zx,
+    x^2 y, x^2 z, y^2 x, y^2 z, z^2 x, z^2 y, xyz, x^2 yz, x y^2 z, x y z^2} on [-1, 1]^3:
+    the Vandermonde matrix at the nodes, inverted."""
+    def mono(x, y, z):
+        return np.stack([np.ones_like(x), x, y, z, x * x, y * y, z * z, x * y, y * z, z * x,
+                         x * x * y, x * x * z, y * y * x, y * y * z, z * z * x, z * z * y, x * y * z,
+                         x * x * y * z, x * y * y * z, x * y * z * z], -1)
+    nodes = np.array(HEX27[:20], float) - 1.0
+    V = mono(nodes[:, 0], nodes[:, 1], nodes[:, 2])  # (20 nodes, 20 monomials)
+    coef = np.linalg.inv(V)  # column a: the coefficients of phi_a
+    return mono(2 * s - 1, 2 * t - 1, 2 * u - 1) @ coef
+
+
 def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth, order=1):
     """Outer integral over E_l on the 8^depth sub-cubes of its unit cube (Gauss-Legendre
     3x3x3 on each), inner 3x3x3 on E_m: the blocks 2 S and -2 X."""
@@ -98,11 +114,15 @@ def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth, order=1):
     X, detl, PL = _trilinear(Vl, s, t, u)
     if order == 2:
         PL = _q2_basis(s, t, u)
+    elif order == 3:
+        PL = _s20_basis(s, t, u)
     WX = gw[pts[:, 3]] * gw[pts[:, 4]] * gw[pts[:, 5]] / n ** 3 * detl
     q = np.array(list(itertools.product(range(3), range(3), range(3))))
     Y, detm, PM = _trilinear(Vm, g[q[:, 0]], g[q[:, 1]], g[q[:, 2]])
     if order == 2:
         PM = _q2_basis(g[q[:, 0]], g[q[:, 1]], g[q[:, 2]])
+    elif order == 3:
+        PM = _s20_basis(g[q[:, 0]], g[q[:, 1]], g[q[:, 2]])
     WY = gw[q[:, 0]] * gw[q[:, 1]] * gw[q[:, 2]] * detm
     R = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
     MU = np.vectorize(lambda r: O.mu(r, delta, eps))(R)
@@ -110,7 +130,7 @@ def _uniform_hex_blocks(Vl, Vm, delta, eps, C, depth, order=1):
     return 2 * np.einsum("xy,ya,yb->ab", G, PM, PM), -2 * np.einsum("xy,ya,xc->ac", G, PM, PL)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("offset", [0.16, 0.205, 0.215])
 def test_algorithm1_hexes_equal_uniform_refinement(offset, order):
     # Constant kernel: Algorithm 1 at L_max = L and uniform refinement of l's cube to level L
@@ -121,13 +141,13 @@ def test_algorithm1_hexes_equal_uniform_refinement(offset, order):
     base = np.array(CORNERS, float) * 0.05
     Vm = base + rng.uniform(-0.006, 0.006, (8, 3))
     Vl = base + [offset, 0.01, 0.0] + rng.uniform(-0.006, 0.006, (8, 3))
-    nb = 8 if order == 1 else 27
+    nb = {1: 8, 2: 27, 3: 20}[order]
     pts = []
     for V in (Vm, Vl):
         if order == 1:
             pts += list(V)
-        else:  # the 27 nodes at the trilinear images of the lattice points
-            for i, j, k in HEX27:
+        else:  # the 27 (or first 20) nodes at the trilinear images of the lattice points
+            for i, j, k in HEX27[:nb]:
                 w = [(1 - i / 2 if c[0] == 0 else i / 2) * (1 - j / 2 if c[1] == 0 else j / 2) *
                      (1 - k / 2 if c[2] == 0 else k / 2) for c in CORNERS]
                 pts.append(sum(w[b] * V[b] for b in range(8)))
@@ -182,6 +202,28 @@ def test_q2_hex_row_sums_symmetry_and_consistency():
     A = sp.csr_matrix((v1, col, rp), shape=(m.n_vert, m.n_vert))
     assert abs(A - A.T).max() < 1e-14 * np.abs(v1).max()
     m2 = q2_hex_mesh(hex_mesh(structured_mesh(3, 2, 0.5, 0.0, 1)))
+    assert O.solve_problem(m2, 0.4, 0.04, 1, 0)["err_all"] < 1e-12
+    e1 = O.solve_problem(m2, 0.4, 0.04, 1, 1)["err_all"]
+    e2 = O.solve_problem(m2, 0.4, 0.04, 2, 1)["err_all"]
+    assert e2 < 0.1 * e1, (e1, e2)
+
+
+def test_s20_hex_row_sums_symmetry_and_consistency():
+    # 20-node serendipity hexahedra: the basis sums to one (zero row sums), one level makes
+    # the rules coincide (symmetry), u = 1 + x + y + z is reproduced, and u = x^2 + y^2 + z^2
+    # (in the serendipity space) up to the integration and mollifier errors, which fall with
+    # L_max
+    m = s20_hex_mesh(q2_hex_mesh(hex_mesh(structured_mesh(3, 2, 0.5, 0.0, 1, jitter=0.1, seed=3))))
+    assert m.conn.shape[1] == 20
+    off, pl = O.pairs(m, 0.4, 0.04)
+    rp, col = O.csr(m, off, pl)
+    v1, _ = O.assemble(m, off, pl, rp, col, 0.4, 0.04, 1)
+    rows = np.repeat(np.arange(m.n_vert), np.diff(rp))
+    assert np.abs(np.bincount(rows, weights=v1, minlength=m.n_vert)).max() < 1e-12 * np.abs(v1).max()
+    import scipy.sparse as sp
+    A = sp.csr_matrix((v1, col, rp), shape=(m.n_vert, m.n_vert))
+    assert abs(A - A.T).max() < 1e-14 * np.abs(v1).max()
+    m2 = s20_hex_mesh(q2_hex_mesh(hex_mesh(structured_mesh(3, 2, 0.5, 0.0, 1))))
     assert O.solve_problem(m2, 0.4, 0.04, 1, 0)["err_all"] < 1e-12
     e1 = O.solve_problem(m2, 0.4, 0.04, 1, 1)["err_all"]
     e2 = O.solve_problem(m2, 0.4, 0.04, 2, 1)["err_all"]
