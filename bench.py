@@ -226,7 +226,7 @@ def describe(w, mesh):
         shape = "hexahedra"
     n_omega = int(mesh.elem_in_omega.sum())
     kern = "constant" if w.kernel == 0 else "truncated Gaussian"
-    order = {6: "P2", 10: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2", 27: "Q2",
+    order = {6: "P2", 10: "P2", 4: "Q1" if mesh.dim == 2 else "P1", 9: "Q2", 27: "Q2", 20: "serendipity",
              8: "Q1" if mesh.dim == 3 else "serendipity"}.get(mesh.conn.shape[1], "P1")
     return (f"{w.name}: Omega=(0,1)^{mesh.dim}, h=1/{round(1 / w.h)}, {mesh.n_elem} {order} {shape} "
             f"({n_omega} in Omega), delta={w.delta / w.h:g}h, eps=delta/{w.delta / w.eps:g}, "
@@ -244,7 +244,7 @@ def _is_quad(mesh):
 
 
 def _is_hex(mesh):
-    return mesh.dim == 3 and mesh.conn.shape[1] in (8, 27)
+    return mesh.dim == 3 and mesh.conn.shape[1] in (8, 20, 27)
 
 
 def l2_err_omega_quads(mesh, u_h):
@@ -278,8 +278,9 @@ def l2_err_omega_quads(mesh, u_h):
 
 def l2_err_omega_hexes(mesh, u_h):
     """||u - u_h||_{L2(Omega)} on hexahedra (u = sum x_k^2): Gauss-Legendre 3x3x3 on each
-    element's unit cube mapped by its trilinear map; Q1, or Q2 (products of the 1D Lagrange
-    bases on {0, 1/2, 1}, nodes in the order of nl_inputs.HEX27)."""
+    element's unit cube mapped by its trilinear map; Q1, Q2 (products of the 1D Lagrange
+    bases on {0, 1/2, 1}, nodes in the order of nl_inputs.HEX27) or the 20-node serendipity
+    element (the first 20 of those nodes)."""
     x, gw = np.polynomial.legendre.leggauss(3)
     g, gw = (x + 1) / 2, gw / 2
     S, T, U = np.meshgrid(g, g, g, indexing="ij")
@@ -306,6 +307,16 @@ def l2_err_omega_hexes(mesh, u_h):
             return np.stack([2 * (v - 0.5) * (v - 1), 4 * v * (1 - v), 2 * v * (v - 0.5)], 1)
         Ls, Lt, Lu = L(s), L(t), L(u)
         phi = np.stack([Ls[:, i] * Lt[:, j] * Lu[:, k] for i, j, k in HEX27], 1)
+    elif conn.shape[1] == 20:
+        from nl_inputs import HEX27
+        c = np.stack([2 * s - 1, 2 * t - 1, 2 * u - 1], 1)
+        cols = []
+        for a, node in enumerate(HEX27[:20]):
+            f = np.array(node, float) - 1
+            lin = [1 - c[:, k] ** 2 if f[k] == 0 else 1 + f[k] * c[:, k] for k in range(3)]
+            p = lin[0] * lin[1] * lin[2]
+            cols.append(p * (c @ f - 2) / 8 if a < 8 else p / 4)
+        phi = np.stack(cols, 1)
     uh = np.einsum("qa,ea->eq", phi, u_h[conn])
     d = (X ** 2).sum(-1) - uh
     return float(math.sqrt(np.sum(det * W[None, :] * d * d)))

@@ -197,30 +197,32 @@ nl_status nl_mesh_create_p2(int dim, int64_t n_vert, const double* coords, int64
 nl_status nl_mesh_create_quad(int order, int64_t n_vert, const double* coords, int64_t n_elem,
                               const int32_t* conn, const uint8_t* elem_in_omega,
                               const uint8_t* node_free, void* cuda_stream, nl_mesh** out);
-/* Mesh of hexahedra (Sec. 6: the HEX meshes of the 3D tests; Q1 trilinear or Q2 triquadratic
- * elements, the Gauss-Legendre 3x3x3 product rule for the inner and the outer integral): dim
+/* Mesh of hexahedra (Sec. 6: the HEX meshes of the 3D tests; Q1 trilinear, Q2 triquadratic
+ * or 20-node serendipity elements, the Gauss-Legendre 3x3x3 product rule for the inner and the outer integral): dim
  * 3, each element the trilinear image of the unit cube of its first 8 nodes, the images of the
  * corners (0,0,0), (1,0,0), (1,1,0), (0,1,0), (0,0,1), (1,0,1), (1,1,1), (0,1,1).  order 1:
  * conn holds those 8 vertices per element; order 2: 27 nodes per element, the 8 vertices,
  * then the images of the cube's lattice of half steps (i, j, k)/2 that are not corners: the
  * twelve edge midpoints, the six face centres and the centre, each group ordered by
  * i + 3 j + 9 k; the basis is the products of the 1D quadratic Lagrange functions on
- * {0, 1/2, 1}.  Algorithm 1's midpoint refinement splits the cube into its eight half-size
+ * {0, 1/2, 1}; order 3: the 20-node serendipity element, the first 20 of those nodes (the
+ * vertices and the edge midpoints; the quadratic FE of Sec. 6's 3D tests, whose mesh figure
+ * counts vertices and edge midpoints).  Algorithm 1's midpoint refinement splits the cube into its eight half-size
  * sub-cubes; their physical vertices lie on the lattice of half steps, a lattice point with a
  * middle index being the midpoint (a+b)*0.5 of its two neighbours along the first such axis
  * (x, then y, then z).  Other arguments as nl_mesh_create; pairs, pattern, nl_assemble
  * (FP64, FP32; MIXED runs FP32), nl_rhs and nl_solve accept it; plans and
  * nl_assemble_noalloc take P1 meshes only.
- * Errors: those of nl_mesh_create; NL_EINVAL for order not 1 or 2, an element whose trilinear
- * map has a non-positive Jacobian determinant at a corner, or a Q2 node off the image of its
- * lattice point (by more than 1e-9 of the element's diagonal). */
+ * Errors: those of nl_mesh_create; NL_EINVAL for order not 1, 2 or 3, an element whose
+ * trilinear map has a non-positive Jacobian determinant at a corner, or a node off the image
+ * of its lattice point (by more than 1e-9 of the element's diagonal). */
 nl_status nl_mesh_create_hex(int order, int64_t n_vert, const double* coords, int64_t n_elem,
                              const int32_t* conn, const uint8_t* elem_in_omega,
                              const uint8_t* node_free, void* cuda_stream, nl_mesh** out);
 nl_status nl_mesh_info(const nl_mesh* mesh, int* dim, int64_t* n_vert, int64_t* n_elem);
 /* Polynomial order of the mesh's elements (1: P1 / Q1, 2: P2 / Q2, 3: serendipity
  * quadrilaterals) and nodes per element (simplices dim+1, 6 or 10, quadrilaterals 4, 8 or 9,
- * hexahedra 8 or 27); either pointer may be NULL. */
+ * hexahedra 8, 27 or 20 (serendipity, order 3)); either pointer may be NULL. */
 nl_status nl_mesh_order(const nl_mesh* mesh, int* order, int* nodes_per_elem);
 /* Copies the mesh back (host buffers of the sizes of nl_mesh_create, conn of
  * nodes_per_elem*n_elem entries; any may be NULL). */

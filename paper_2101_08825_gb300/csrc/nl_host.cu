@@ -515,7 +515,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
   if (!out) return fail(NL_EINVAL, "nl_mesh_create: out is NULL");
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create: dim must be 2 or 3");
-  if (order != 1 && order != 2 && !(order == 3 && cell == 1))
+  if (order != 1 && order != 2 && !(order == 3 && cell != 0))
     return fail(NL_EINVAL, "nl_mesh_create: unknown element order %d", order);
   if (cell == 1 && dim != 2) return fail(NL_EINVAL, "nl_mesh_create_quad: quadrilaterals are 2D");
   if (cell == 2 && dim != 3) return fail(NL_EINVAL, "nl_mesh_create_hex: hexahedra are 3D");
@@ -524,7 +524,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
                 (long long)n_vert, (long long)n_elem);
   if (!coords || !conn || !eio || !nf) return fail(NL_EINVAL, "nl_mesh_create: NULL array");
   const int nv = cell == 1 ? 4 : (cell == 2 ? 8 : dim + 1);
-  const int nb = cell == 2 ? (order == 2 ? 27 : 8)
+  const int nb = cell == 2 ? (order == 2 ? 27 : (order == 3 ? 20 : 8))
                  : cell == 1 ? (order == 2 ? 9 : (order == 3 ? 8 : 4))
                              : (order == 2 ? (dim == 2 ? 6 : 10) : nv);
   for (int64_t i = 0; i < (int64_t)dim * n_vert; i++)
@@ -614,7 +614,7 @@ static nl_status mesh_create_impl(int dim, int order, int cell, int64_t n_vert,
           return fail(NL_EINVAL, "nl_mesh_create_hex: element %lld is inverted or degenerate at corner %d",
                       (long long)e, a);
       }
-      // Q2: node a >= 8 at the trilinear image of its lattice point (i, j, k) / 2
+      // Q2, serendipity: node a >= 8 at the trilinear image of its lattice point (i, j, k) / 2
       for (int a = 8; a < nb; a++) {
         const int c = hex27_code(a);
         double w[8];
@@ -869,7 +869,7 @@ nl_status nl_mesh_create_hex(int order, int64_t n_vert, const double* coords, in
                              const int32_t* conn, const uint8_t* elem_in_omega,
                              const uint8_t* node_free, void* cuda_stream, nl_mesh** out) {
   nlx::clear_error();
-  if (order != 1 && order != 2) return nlx::fail(NL_EINVAL, "nl_mesh_create_hex: order must be 1 or 2");
+  if (order < 1 || order > 3) return nlx::fail(NL_EINVAL, "nl_mesh_create_hex: order must be 1, 2 or 3");
   return mesh_create_impl(3, order, 2, n_vert, coords, n_elem, conn, elem_in_omega, node_free,
                           cuda_stream, out);
 }

@@ -179,9 +179,28 @@ __host__ __device__ constexpr int hex27_code(int a) {
 
 // w times the basis of a hexahedron at (s, t, u) of the unit cube: NB = 8 the trilinear
 // functions of the vertices, NB = 27 (Q2) the products L_i(s) L_j(t) L_k(u) of the quadratic
-// Lagrange functions on {0, 1/2, 1} for the node at lattice point (i, j, k).
+// Lagrange functions on {0, 1/2, 1} for the node at lattice point (i, j, k), NB = 20 the
+// serendipity element on (x, y, z) = (2s-1, 2t-1, 2u-1) with node a at (x_a, y_a, z_a) =
+// (i-1, j-1, k-1): a vertex (1/8)(1 + x x_a)(1 + y y_a)(1 + z z_a)(x x_a + y y_a + z z_a - 2),
+// an edge node with x_a = 0 (1/4)(1 - x^2)(1 + y y_a)(1 + z z_a), likewise along y and z.
 template <int NB, typename T>
 __host__ __device__ inline void hex_basis(T s, T t, T u, T w, T* phi) {
+  if (NB == 20) {
+    const T x = (T)2 * s - (T)1, y = (T)2 * t - (T)1, z = (T)2 * u - (T)1;
+#pragma unroll
+    for (int a = 0; a < 20; a++) {
+      const int c = hex27_code(a);
+      const int xa = c % 3 - 1, ya = (c / 3) % 3 - 1, za = c / 9 - 1;
+      const T fx = xa == 0 ? (T)1 - x * x : (T)1 + (T)xa * x;
+      const T fy = ya == 0 ? (T)1 - y * y : (T)1 + (T)ya * y;
+      const T fz = za == 0 ? (T)1 - z * z : (T)1 + (T)za * z;
+      if (a < 8)
+        phi[a] = (T)0.125 * w * fx * fy * fz * ((T)xa * x + (T)ya * y + (T)za * z - (T)2);
+      else
+        phi[a] = (T)0.25 * w * fx * fy * fz;
+    }
+    return;
+  }
   if (NB == 8) {
 #pragma unroll
     for (int a = 0; a < 8; a++) {

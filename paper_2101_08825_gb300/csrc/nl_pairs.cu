@@ -564,9 +564,9 @@ static nl_status build_pairs_dim(nl_mesh* m, double delta, double eps, nl_pairs*
   NL_CUDA(cudaStreamSynchronize(s));
   int eh = next_pow2(std::max<int64_t>(64, std::min<int64_t>(2 * max_sum, 32768)));
   // node table: a P2 (or quadrilateral) element brings about four (two) times the nodes of a
-  // P1 triangle into a row, a Q2 hexahedron about eight times those of a Q1 one; the element
-  // table is at least as large, as the sorted row is staged in it
-  int nh = std::min(8192, (m->cell == 2 && m->order == 2) ? 8 * eh
+  // P1 triangle into a row, a Q2 or serendipity hexahedron up to eight times those of a Q1
+  // one; the element table is at least as large, as the sorted row is staged in it
+  int nh = std::min(8192, (m->cell == 2 && m->order >= 2) ? 8 * eh
                           : (m->order == 2 || m->cell == 1) ? 2 * eh : eh);
   eh = std::max(eh, nh);
   size_t rsmem = sizeof(int32_t) * (eh + nh);

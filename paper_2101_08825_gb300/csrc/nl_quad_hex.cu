@@ -1,16 +1,17 @@
 // nl_quad_hex.cu -- nl_assemble on meshes of hexahedra (Sec. 6: the HEX meshes of the 3D
-// tests, Q1 trilinear or Q2 triquadratic elements, the Gauss-Legendre 3x3x3 product rule for
-// the inner and the outer integral).
+// tests, Q1 trilinear, Q2 triquadratic or 20-node serendipity elements, the Gauss-Legendre
+// 3x3x3 product rule for the inner and the outer integral).
 //
 // What is computed (Sec. 5, Corollary 1, eqs. J21Nr and J22Nr): for every element pair
 // (m, l) of J, with the 3x3x3 rule on E_m (points y = F_m(g), weights w_y |det DF_m|, rows =
 // the NN nodes of m) and on the sub-elements E' of E_l that Algorithm 1 selects for this m,
 //   A[m_a, m_b] += 2 sum_{x,y} w_x w_y gamma_eps(x,y) phi^m_a(y) phi^m_b(y)
 //   A[m_a, l_d] -= 2 sum_{x,y} w_x w_y gamma_eps(x,y) phi^m_a(y) phi^l_d(x).
-// An element is the trilinear image F of the unit cube (its 8 vertices; a Q2 element's other
-// 19 nodes sit at the images of the lattice of half steps); a sub-element is the image of a
-// sub-cube of l's cube, its outer points x = F_l(s0 + len g_i, t0 + len g_j, u0 + len g_k) with
-// weights w_i w_j w_k len^3 |det DF_l| and the basis of l at those reference points.
+// An element is the trilinear image F of the unit cube (its 8 vertices; the other nodes of a
+// Q2 or serendipity element sit at the images of the lattice of half steps); a sub-element
+// is the image of a sub-cube of l's cube, its outer points x = F_l(s0 + len g_i, t0 + len g_j,
+// u0 + len g_k) with weights w_i w_j w_k len^3 |det DF_l| and the basis of l at those
+// reference points.
 // Algorithm 1 splits a cube into its eight half-size sub-cubes and decides on the box of the
 // sub-element's physical vertices, which lie on the lattice of half steps: a lattice point
 // with a middle index is the midpoint (a+b)*0.5 of its two neighbours along the first such
@@ -27,13 +28,13 @@
 // phi^m_a(y) H_d(y) and keeps g(y) = sum_d H_d(y) for m's self block.  With the constant
 // kernel an INT sub-element adds sum_x w_x C phi^l_d(x), independent of y, to every inner
 // point without evaluating point pairs.
-//  Q2 (NN = 27): lane q < 27 holds inner point q and its 27 sums H_d(y_q).  A pass stages 32
-// outer points in shared memory (one per lane: x, the item's kind and w_x phi^l_d(x) for the
-// 27 d), then every lane runs over the staged points (the same point on every lane, so the
-// mollifier's branch is uniform).  A constant-kernel INT sub-element's points are not paired:
-// lane d sums their w_x C phi^l_d(x).  At the end of a pair the H table is transposed through
-// shared memory so that lane d computes column d of the cross block (27 x 27 products with
-// the broadcast rows w_y phi^m_a(y)).
+//  Q2 and serendipity (NN = 27, 20; the wide layout): lane q < 27 holds inner point q and its
+// NN sums H_d(y_q).  A pass stages 32 outer points in shared memory (one per lane: x, the
+// item's kind and w_x phi^l_d(x) for the NN d), then every lane runs over the staged points
+// (the same point on every lane, so the mollifier's branch is uniform).  A constant-kernel
+// INT sub-element's points are not paired: lane d sums their w_x C phi^l_d(x).  At the end of
+// a pair the H table is transposed through shared memory so that lane d computes column d of
+// the cross block (NN x 27 products with the broadcast rows w_y phi^m_a(y)).
 #include <cuda_runtime.h>
 
 #include "nl_quad_kernel.cuh"
@@ -46,8 +47,8 @@ constexpr int HX_IMAX = 64;    // buffered sub-elements
 constexpr int HX_RS = 9;       // row stride of the Q1 reduction scratch
 constexpr int HX_REC = 28;     // LIFO record: 8 vertices x 3, s0, t0, u0, pad
 constexpr int HX_WARPS = 4;
-constexpr int HX_SR = 32;      // Q2 staged outer point: x, y, z, kind, w_x phi^l_d (27), pad
-constexpr int HX_WP = 28;      // Q2 row stride of the tables over the 27 points or nodes
+constexpr int HX_SR = 32;      // wide layout: staged outer point: x, y, z, kind, w_x phi^l_d, pad
+constexpr int HX_WP = 28;      // wide layout: row stride of the tables over the points or nodes
 
 // item kinds
 constexpr int HK_INT = 0, HK_FINAL = 1, HK_CLOSED = 2;
@@ -79,8 +80,8 @@ __host__ __device__ constexpr size_t hx_table_bytes() {
 template <typename R, int NN>
 struct HMem {
   // Q1: wpm [8][27], red [8 * 27][RS] + hs [8 * 27 + 8];
-  // Q2: wpm [27][WP], red = the staged outer points [32][SR], at the end of a pair the
-  //     transposed H table [27][WP]
+  // wide: wpm [NN][WP], red = the staged outer points [32][SR], at the end of a pair the
+  //       transposed H table [27][WP]
   static constexpr size_t WPM_N = NN == 8 ? 8 * HX_NQ : 27 * HX_WP;
   static constexpr size_t RED_N = NN == 8 ? (size_t)8 * HX_NQ * HX_RS + 8 * HX_NQ + 8 : 32 * HX_SR;
   R* sv;         // [scap][REC]
@@ -294,7 +295,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
                                   std::is_same<R, float>::value ? (NN == 8 ? 2 : 3) : 1)
     k_quad_h(const QParams P) {
   constexpr bool F32 = std::is_same<R, float>::value;
-  constexpr bool Q2 = NN == 27;
+  constexpr bool WIDE = NN != 8;  // Q2 or serendipity: one inner point per lane
   constexpr int NYL = HxLay<NN>::NYL, XPI = HxLay<NN>::XPI, NBLK = HxLay<NN>::NBLK;
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) char smem_raw[];
@@ -314,9 +315,9 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
   for (int t = threadIdx.x; t < HX_NQ * 4; t += blockDim.x) rS[t] = (R)tS[t];
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // Q1: first inner point of this lane's group and its outer point slot; Q2: inner point q
-  const int ybase = Q2 ? lane : (lane >> 3) * NYL;
-  const int xl = Q2 ? lane : lane & 7;
+  // Q1: first inner point of this lane's group and its outer point slot; wide: inner point q
+  const int ybase = WIDE ? lane : (lane >> 3) * NYL;
+  const int xl = WIDE ? lane : lane & 7;
   HMem<R, NN> wm;
   wm.carve(smem_raw + hx_table_bytes<R, NN>() + (size_t)wid * HMem<R, NN>::bytes(P.scap), P.scap);
 
@@ -419,14 +420,14 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
           hmap<double>(Vmr, tS[lane * 4], tS[lane * 4 + 1], tS[lane * 4 + 2], x, det, N);
           const double wy = tS[lane * 4 + 3] * det;
           wm.wd[lane] = wy;
-          if constexpr (Q2) {
+          if constexpr (WIDE) {
 #pragma unroll 1
             for (int a = 0; a < NN; a++) wm.wpm[a * HX_WP + lane] = (R)(wy * tB[lane * NN + a]);
           } else {
 #pragma unroll
             for (int a = 0; a < 8; a++) wm.wpm[a * HX_NQ + lane] = (R)(wy * N[a]);
           }
-        } else if (Q2 && lane == HX_NQ) {
+        } else if (WIDE && lane == HX_NQ) {
           for (int a = 0; a < NN; a++) wm.wpm[a * HX_WP + HX_NQ] = (R)0;  // the rows' pad
         }
         if constexpr (F32) {
@@ -471,10 +472,10 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
       for (int d = 0; d < NN; d++)
 #pragma unroll
         for (int i = 0; i < NYL; i++) H[d][i] = 0;
-      // Q1: the closed forms' sums per node d; Q2: lane d's sum for node d
-      R U[Q2 ? 1 : NN];
+      // Q1: the closed forms' sums per node d; wide: lane d's sum for node d
+      R U[WIDE ? 1 : NN];
 #pragma unroll
-      for (int d = 0; d < (Q2 ? 1 : NN); d++) U[d] = 0;
+      for (int d = 0; d < (WIDE ? 1 : NN); d++) U[d] = 0;
       bool contrib = false, has_u = false;
 
       auto classify = [&](const R (&V)[8][3], uint32_t code, bool count_exact) -> int {
@@ -508,7 +509,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
       // Q1: closed form of an INT sub-element (constant kernel): sum_x w_x C phi^l_d(x) over
       // the sub-cube, the same at every inner point (summed over the warp at the end of the pair)
       auto closed_int = [&](R s0, R t0, R u0, R len) {
-        if constexpr (!Q2) {
+        if constexpr (!WIDE) {
 #pragma unroll 1
           for (int q = 0; q < HX_NQ; q++) {  // not unrolled: rare, keeps the code small
             R x[3], det, N[8];
@@ -578,11 +579,11 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
             }
             if (KERN == NL_KERNEL_TRUNC_GAUSS) g *= eta_gauss<R>(P, r2);
 #pragma unroll
-            for (int d = 0; d < (Q2 ? 1 : NN); d++) H[d][i] += g * bw[d];
+            for (int d = 0; d < (WIDE ? 1 : NN); d++) H[d][i] += g * bw[d];
           }
         }
       };
-      // Q2: 32 outer points staged per pass; every lane runs over the staged points
+      // wide layout: 32 outer points staged per pass; every lane runs over the staged points
       auto integrate2 = [&](int n_it) {
         const int n_x = n_it * HX_NQ;
         contrib = true;
@@ -604,12 +605,12 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
           sp[1] = x[1];
           sp[2] = x[2];
           sp[3] = kind;
-          hex_basis<27, R>(s, t, u, wx, sp + 4);
+          hex_basis<NN, R>(s, t, u, wx, sp + 4);
           sp[31] = (R)0;
           __syncwarp();
           const unsigned vm = __ballot_sync(FULL, valid);
           const unsigned cm = __ballot_sync(FULL, valid && kind == (R)HK_CLOSED);
-          if (cm != 0u && lane < HX_NQ) {
+          if (cm != 0u && lane < NN) {
             unsigned c = cm;
             while (c) {
               const int oo = __ffs(c) - 1;
@@ -651,12 +652,12 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
         }
       };
       auto integrate = [&](int n_it) {
-        if constexpr (Q2) integrate2(n_it);
+        if constexpr (WIDE) integrate2(n_it);
         else integrate1(n_it);
       };
       // the kind of a buffered INT or FINAL sub-element
       auto item_kind = [&](int act) -> int {
-        return act == ACT_FINAL ? HK_FINAL : ((Q2 && KERN == NL_KERNEL_CONST) ? HK_CLOSED : HK_INT);
+        return act == ACT_FINAL ? HK_FINAL : ((WIDE && KERN == NL_KERNEL_CONST) ? HK_CLOSED : HK_INT);
       };
 
       // ---- Algorithm 1 for this pair ------------------------------------------------------
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
         }
         if (act0 == ACT_INT || act0 == ACT_FINAL || act0 == ACT_ZERO) st_items += (lane == 0);
         if (KERN == NL_KERNEL_CONST && act0 == ACT_INT) {
-          if constexpr (Q2) {
+          if constexpr (WIDE) {
             st_closed += (lane == 0);
           } else {
             if (lane == 0) closed_int((R)0, (R)0, (R)0, (R)1);
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
           const int level = code >> LEVEL_SHIFT;
           if (act == ACT_INT || act == ACT_FINAL || act == ACT_ZERO) st_items++;
           if (KERN == NL_KERNEL_CONST && act == ACT_INT) {
-            if constexpr (Q2) {
+            if constexpr (WIDE) {
               st_closed++;
             } else {
               closed_int(s0, t0, u0, pow2m(R(0), level - 1));
@@ -748,7 +749,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
         __syncwarp();
         continue;
       }
-      if constexpr (Q2) {
+      if constexpr (WIDE) {
         // lane q writes row q of the H table; lane d then holds column d (+ its closed sum)
         R usum = U[0];
 #pragma unroll
@@ -760,7 +761,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
           row[HX_NQ] = (R)0;
         }
         __syncwarp();
-        if (lane < HX_NQ) {
+        if (lane < NN) {
           R col[HX_WP];
 #pragma unroll
           for (int q = 0; q < HX_NQ; q++) col[q] = wm.red[q * HX_WP + lane] + U[0];
@@ -778,6 +779,8 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
             }
             bp[a * NN + lane] = (R)(-2) * s;
           }
+        }
+        if (lane < HX_NQ) {
           R g = usum;
 #pragma unroll
           for (int d = 0; d < NN; d++) g += H[d][0];
@@ -927,6 +930,11 @@ nl_status assemble_values_hex(nl_mesh* m, nl_pairs* p, const nl_kernel_params* k
                           : run_assembly_h<float, 0, 27>(m, p, P, values, s, scratch.p, err.p, T);
       else rc = gauss ? run_assembly_h<double, 1, 27>(m, p, P, values, s, scratch.p, err.p, T)
                       : run_assembly_h<double, 0, 27>(m, p, P, values, s, scratch.p, err.p, T);
+    } else if (m->nb == 20) {
+      if (f32) rc = gauss ? run_assembly_h<float, 1, 20>(m, p, P, values, s, scratch.p, err.p, T)
+                          : run_assembly_h<float, 0, 20>(m, p, P, values, s, scratch.p, err.p, T);
+      else rc = gauss ? run_assembly_h<double, 1, 20>(m, p, P, values, s, scratch.p, err.p, T)
+                      : run_assembly_h<double, 0, 20>(m, p, P, values, s, scratch.p, err.p, T);
     } else {
       if (f32) rc = gauss ? run_assembly_h<float, 1, 8>(m, p, P, values, s, scratch.p, err.p, T)
                           : run_assembly_h<float, 0, 8>(m, p, P, values, s, scratch.p, err.p, T);

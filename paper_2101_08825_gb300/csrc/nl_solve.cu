@@ -96,8 +96,8 @@ __global__ void k_rhs_quads(int64_t n_elem, const int32_t* __restrict__ conn,
     if (free_[nd[a]]) atomicAdd(&F[nd[a]], acc[a]);
 }
 
-// F_i += int_E f phi_i per hexahedron of Omega (Q1, NB = 8, or Q2, NB = 27; f interpolated in
-// the element space): Gauss-Legendre 3x3x3 on the unit cube mapped by the element's trilinear
+// F_i += int_E f phi_i per hexahedron of Omega (Q1, NB = 8, Q2, NB = 27, or serendipity,
+// NB = 20; f interpolated in the element space): Gauss-Legendre 3x3x3 on the unit cube mapped by the element's trilinear
 // map; G = the 3 points and weights on [0, 1].
 template <int NB>
 __global__ void k_rhs_hexes(int64_t n_elem, const int32_t* __restrict__ conn,
@@ -635,6 +635,9 @@ nl_status rhs_values(nl_mesh* m, nl_matrix* A, const double* f_nodes, double f_c
   }
   if (m->cell == 2 && m->nb == 27)
     k_rhs_hexes<27><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
+                                              m->evert, fn.p, f_const, HG.p, F);
+  else if (m->cell == 2 && m->nb == 20)
+    k_rhs_hexes<20><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,
                                               m->evert, fn.p, f_const, HG.p, F);
   else if (m->cell == 2)
     k_rhs_hexes<8><<<NL_CNT(ge), RT, 0, s>>>(m->n_elem, m->conn, m->elem_in_omega, m->node_free,

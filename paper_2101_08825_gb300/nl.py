@@ -316,9 +316,10 @@ def nl_mesh_create_quad(order, coords, conn, elem_in_omega, node_free, stream=No
 
 
 def nl_mesh_create_hex(order, coords, conn, elem_in_omega, node_free, stream=None) -> Mesh:
-    """Mesh of hexahedra: conn rows of 8 vertices (Q1, order 1) or 27 nodes (Q2, order 2)."""
+    """Mesh of hexahedra: conn rows of 8 vertices (Q1, order 1), 27 nodes (Q2, order 2) or
+    20 nodes (serendipity, order 3)."""
     coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(3, -1)
-    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, 8 if int(order) == 1 else 27)
+    conn = np.ascontiguousarray(conn, dtype=np.int32).reshape(-1, {1: 8, 3: 20}.get(int(order), 27))
     eio = np.ascontiguousarray(elem_in_omega, dtype=np.uint8)
     nf = np.ascontiguousarray(node_free, dtype=np.uint8)
     h = ctypes.c_void_p()
@@ -331,9 +332,9 @@ def nl_mesh_create_hex(order, coords, conn, elem_in_omega, node_free, stream=Non
 def mesh_from(mesh, stream=None) -> Mesh:
     """Uploads an nl_inputs.Mesh: P1 simplices, P2 simplices (six or ten nodes per element),
     quadrilaterals (2D, four, eight or nine nodes per element) or hexahedra (3D, eight or
-    twenty-seven)."""
-    if mesh.dim == 3 and mesh.conn.shape[1] in (8, 27):
-        return nl_mesh_create_hex(1 if mesh.conn.shape[1] == 8 else 2, mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
+    twenty-seven or twenty)."""
+    if mesh.dim == 3 and mesh.conn.shape[1] in (8, 20, 27):
+        return nl_mesh_create_hex({8: 1, 27: 2, 20: 3}[mesh.conn.shape[1]], mesh.coords, mesh.conn, mesh.elem_in_omega, mesh.node_free, stream)
     if mesh.dim == 2 and mesh.conn.shape[1] in (4, 8, 9):
         return nl_mesh_create_quad({4: 1, 9: 2, 8: 3}[mesh.conn.shape[1]], mesh.coords, mesh.conn,
                                    mesh.elem_in_omega, mesh.node_free, stream)
