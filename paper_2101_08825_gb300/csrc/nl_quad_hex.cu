@@ -330,15 +330,24 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
   R y[NYL][3];
   R gsh = 0, gsl = 0;  // lane q < 27: sum of g(y_q) over the current m-run
 
+  // m's self block from g(y_q) summed over the m-run: 2 sum_q w_q phi_a(y_q) phi_b(y_q) g(y_q),
+  // symmetric, so only the NN (NN + 1) / 2 entries a <= b are summed, then mirrored
   auto flush_self = [&]() {
-    if (lane < HX_NQ) wm.sd[lane] = (double)gsh + (double)gsl;
+    if (lane < HX_NQ) wm.sd[lane] = ((double)gsh + (double)gsl) * wm.wd[lane];
     gsh = gsl = 0;
     __syncwarp();
-    for (int e = lane; e < NBLK; e += 32) {
-      const int a = e / NN, b = e % NN;
+    constexpr int NTRI = NN * (NN + 1) / 2;
+    for (int t = lane; t < NTRI; t += 32) {
+      int a = 0, r = t;
+      while (r >= NN - a) {  // row a of the upper triangle holds NN - a entries
+        r -= NN - a;
+        a++;
+      }
+      const int b = a + r;
       double s = 0.0;
-      for (int q = 0; q < HX_NQ; q++) s += wm.wd[q] * tB[q * NN + a] * tB[q * NN + b] * wm.sd[q];
-      atomicAdd(&P.selfblk[cur_m * NBLK + e], 2.0 * s);
+      for (int q = 0; q < HX_NQ; q++) s = fma(tB[q * NN + a] * tB[q * NN + b], wm.sd[q], s);
+      atomicAdd(&P.selfblk[cur_m * NBLK + a * NN + b], 2.0 * s);
+      if (b != a) atomicAdd(&P.selfblk[cur_m * NBLK + b * NN + a], 2.0 * s);
     }
     __syncwarp();
   };
