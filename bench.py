@@ -675,8 +675,9 @@ def run_c2_block(args, nl, torch, stream, flush, world):
 def run_element_block(args, nl, torch, stream, flush, world, name, steps, fp64_steps):
     """Other element families: on the 2D workload's grid (h = 1/256) P2 triangles (c2_2d_p2:
     141,512 triangles, 284,089 nodes), Q1 and Q2 quadrilaterals (c2_2d_q1, c2_2d_q2: 70,756
-    cells); on the 3D grid at h = 1/16 Q1 hexahedra (c3_3d_hex: 10,648 cells) and P2
-    tetrahedra (c3_3d_p2: 63,888 tetrahedra, 91,125 nodes).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
+    cells); on the 3D grid at h = 1/16 Q1 and Q2 hexahedra (c3_3d_hex, c3_3d_hex_q2: 10,648
+    cells, the latter 91,125 nodes) and P2 tetrahedra (c3_3d_p2: 63,888 tetrahedra, 91,125
+    nodes).  The FP32 step and the FP64 step (pairs, pattern, assembly, right-hand side,
     BiCGStab), their L2 errors, and the roofline of the assembly kernel in both
     precisions."""
     w, mesh = workload(name)
