@@ -1779,7 +1779,7 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
   __shared__ int64_t rbeg[NV];
   __shared__ int rlen[NV], roff[NV + 1];
   __shared__ int32_t nodes[NV];
-  __shared__ int overflow;
+  __shared__ int overflow, n_keys;
   if (threadIdx.x < NV) {
     int32_t i = conn[m * NV + threadIdx.x];
     nodes[threadIdx.x] = i;
@@ -1878,6 +1878,106 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     }
     __syncthreads();  // the table is abandoned; its memory is reused below
   }
+  // P2 tetrahedra whose rows are too long for the table above: a table of the columns the
+  // element's blocks touch (the nodes of its pairs' l, and its own nodes for the self block)
+  // with R accumulators for a group of G rows at a time.  Each group is added to its rows by
+  // one pass over their column lists in order (coalesced), an entry taking its column's sum.
+  // (Q2 and serendipity hexahedra, whose touched columns need six or four passes at one CTA
+  // per SM, are faster with the global-memory search below at full occupancy.)
+  if constexpr (NV == 10) {
+    constexpr int TT = 8192;  // table slots; the touched columns may fill at most half
+    constexpr size_t KEY_B = (size_t)TT * 4;
+    const int G = (size_t)dyn > KEY_B
+                      ? (int)min((size_t)NV, ((size_t)dyn - KEY_B) / ((size_t)TT * sizeof(R)))
+                      : 0;
+    if (G >= 1) {
+      int32_t* keys = reinterpret_cast<int32_t*>(sraw);
+      R* acc = reinterpret_cast<R*>(sraw + KEY_B);  // [TT][G]
+      for (int t = threadIdx.x; t < TT; t += blockDim.x) keys[t] = -1;
+      if (threadIdx.x == 0) {
+        overflow = 0;
+        n_keys = 0;
+      }
+      __syncthreads();
+      auto h0 = [](int32_t key) -> int { return (int)(((uint32_t)key * 2654435761u) >> 19); };
+      auto insert = [&](int32_t key) {
+        int slot = h0(key);
+        for (int probe = 0; probe < TT; probe++) {
+          const int32_t prev = atomicCAS(&keys[slot], -1, key);
+          if (prev == -1) {
+            atomicAdd(&n_keys, 1);
+            return;
+          }
+          if (prev == key) return;
+          slot = (slot + 1) & (TT - 1);
+        }
+        overflow = 1;
+      };
+      for (int64_t t = threadIdx.x; t < n * NV; t += blockDim.x)
+        insert(conn[(int64_t)pair_l[q0 + t / NV] * NV + (int)(t % NV)]);
+      if (with_self && threadIdx.x < NV) insert(nodes[threadIdx.x]);
+      __syncthreads();
+      if (!overflow && 2 * n_keys <= TT) {
+        auto lookup = [&](int32_t key) -> int {
+          int slot = h0(key);
+          for (int probe = 0; probe < TT; probe++) {
+            const int32_t k = keys[slot];
+            if (k == key) return slot;
+            if (k == -1) return -1;
+            slot = (slot + 1) & (TT - 1);
+          }
+          return -1;
+        };
+        for (int a0 = 0; a0 < NV; a0 += G) {
+          const int g = min(G, NV - a0);
+          for (int t = threadIdx.x; t < TT * G; t += blockDim.x) acc[t] = (R)0;
+          __syncthreads();
+          // one thread per (pair, node c of l): the g entries of column c in rows a0, a0+1, ...
+          for (int64_t t = threadIdx.x; t < n * NV; t += blockDim.x) {
+            const int64_t p = q0 + t / NV;
+            const int c = (int)(t % NV);
+            const R* bp = blk + (p - p_base) * NB + (size_t)a0 * NV + c;
+            const int slot = lookup(conn[(int64_t)pair_l[p] * NV + c]);  // inserted above
+            if (slot < 0) {
+              atomicOr(err, ERR_CSR);
+              continue;
+            }
+            for (int a = 0; a < g; a++) {
+              const R v = bp[a * NV];
+              if (v != (R)0) atomicAdd(&acc[slot * G + a], v);
+            }
+          }
+          if (with_self)
+            for (int t = threadIdx.x; t < g * NV; t += blockDim.x) {
+              const int a = t / NV, b = t % NV;
+              const int slot = lookup(nodes[b]);
+              if (slot < 0) atomicOr(err, ERR_CSR);
+              else atomicAdd(&acc[slot * G + a], (R)selfblk[m * NB + (a0 + a) * NV + b]);
+            }
+          __syncthreads();
+          for (int a = 0; a < g; a++) {
+            const int64_t rb = rbeg[a0 + a];
+            for (int t = threadIdx.x; t < rlen[a0 + a]; t += blockDim.x) {
+              const int slot = lookup(col[rb + t]);
+              if (slot < 0) continue;
+              const R v = acc[slot * G + a];
+              if (v != (R)0) {
+                atomicAdd(&values[rb + t], (double)v);
+                acc[slot * G + a] = (R)0;  // taken: each column appears once in a row
+              }
+            }
+          }
+          __syncthreads();
+          // a sum still left had no entry in its row
+          for (int t = threadIdx.x; t < TT * G; t += blockDim.x)
+            if (t % G < g && acc[t] != (R)0) atomicOr(err, ERR_CSR);
+          __syncthreads();
+        }
+        return;
+      }
+      __syncthreads();  // the table is abandoned; its memory is reused below
+    }
+  }
   // the rows' column lists cached in shared memory when they fit, else searched in global
   // memory (elements with very long rows, e.g. 27-node hexahedra)
   const bool cache_rows = (size_t)total * 4 <= (size_t)dyn;
@@ -1941,14 +2041,16 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
 }
 
 // Dynamic shared memory of the scatter kernels for elements of nn nodes, rows of up to max_row
-// columns and blocks of acc_size-byte values: the hash layout when it fits in 200 KB, else the
-// cached column lists plus FP64 accumulators when that fits, else the column lists only, else
-// 16 bytes (the rows are then searched in global memory).
+// columns and blocks of acc_size-byte values: the hash layout when it fits in 200 KB, else
+// (P2 tetrahedra, ten nodes) 200 KB for the table of touched columns, else the cached column
+// lists plus FP64 accumulators when that fits, else the column lists only, else 16 bytes (the
+// rows are then searched in global memory).
 inline size_t scatter_smem_bytes(int nn, int max_row, size_t acc_size) {
   const size_t total = (size_t)nn * (size_t)std::max(1, max_row);
   const size_t hashed =
       scatter_hash_bytes(nn, scatter_table_size(std::max(1, max_row)), (int64_t)total, acc_size);
   if (hashed <= (size_t)200 * 1024) return hashed;
+  if (nn == 10) return (size_t)200 * 1024;  // the table of touched columns (scatter_elem)
   const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
   if (with_acc <= (size_t)200 * 1024) return with_acc;
   if (total * 4 <= (size_t)200 * 1024) return total * 4;
