@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(HX_WARPS * 32,
           else if (act == ACT_REFINE) push(base + __popc(m_ref & below), V, s0, t0, u0, code);
           sp = overflow ? base : base + nref;
           n_it += __popc(m_it);
-          __syncwarp();  // records and items of this round are visible to every lane
+          __syncwarp();  // records and items of this LIFO step are visible to every lane
         }
         if (n_it > 0) integrate(n_it);
       }

@@ -1529,7 +1529,7 @@ __global__ void __launch_bounds__(QLaunch<D>::THREADS, QLaunch<D>::MIN_CTAS)
           sp = overflow ? base : base + nref;
           n_int += __popc(m_int);
           n_fin += __popc(m_fin);
-          __syncwarp();  // records and items written this round are visible to every lane
+          __syncwarp();  // records and items written in this LIFO step are visible to every lane
         };
         if (D == 2 && from_root && P.L_max >= 3) {
           const int c2 = lane >> 2, c3 = lane & 3;

@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(PT_WARPS * 32, std::is_same<R, float>::value ?
           else if (act == ACT_REFINE) push(base + __popc(m_ref & below), V, code);
           sp = overflow ? base : base + nref;
           n_it += __popc(m_it);
-          __syncwarp();  // records and items of this round are visible to every lane
+          __syncwarp();  // records and items of this LIFO step are visible to every lane
         }
         if (n_it > 0) integrate(n_it);
       }
