@@ -7,6 +7,8 @@ Algorithm-1 work counts bit-exact; A within 1e-12 relative (Frobenius, and per e
 the largest entry) in FP64 and 2e-6 in FP32.  Whole GPU path: Table 7's HEX linear error at
 ml = 1, and the oracle's dense solution to 1e-9.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -252,3 +254,28 @@ def test_table6_q2_hex_consistency_on_gpu():
             errs[(L, prec)] = O.l2_error(mesh, u, w.ms, omega_only=False)
             assert abs(errs[(L, prec)] / gold[L] - 1) < 5e-3, (L, errs)
     assert abs(errs[(3, nl.NL_PREC_FP64)] / errs[(3, nl.NL_PREC_FP32)] - 1) < 5e-3, errs
+
+
+def test_table7_q2_hex_quadratic_order_on_gpu():
+    # Table 7, HEX quadratic at ml = 1, 2 (u = x^3 + y^3 + z^3, f = -6(x + y + z) linear: its
+    # Q2 interpolant is exact): third order (printed 2.972) and the printed errors within 20 %
+    # (7.50e-4 and 9.92e-5 against 6.739e-4 and 8.587e-5; like the 2D quadratic h-convergence
+    # columns, the runs differ in a detail the text leaves open, while the consistency test of
+    # Table 6 on the same elements matches to 0.2 %)
+    errs = {}
+    for ml, gold in ((1, 6.739e-4), (2, 8.587e-5)):
+        w = table7_hex(ml).with_(order=2)
+        mesh = workload_mesh(w)
+        assert mesh.conn.shape[1] == 27
+        C = O.kernel_constant(3, 0, w.delta, w.eps)
+        m = nl.mesh_from(mesh)
+        p = nl.nl_pairs_build(m, w.delta, w.eps)
+        g = np.array([O.ms_u(w.ms, mesh.coords[:, i]) for i in range(mesh.n_vert)])
+        f = np.array([O.ms_f(w.ms, mesh.coords[:, i], 0, w.delta, w.eps, C) for i in range(mesh.n_vert)])
+        A, _ = nl.nl_assemble(m, p, w.delta, w.eps, w.L_max, precision=nl.NL_PREC_FP32)
+        b = nl.nl_rhs(m, A, g, f_nodes=f)
+        u, *_ = nl.nl_solve(A, b, g, solver=1, rtol=1e-12, precision=nl.NL_PREC_FP32)
+        errs[ml] = O.l2_error(mesh, u, w.ms, omega_only=False)
+        assert abs(errs[ml] / gold - 1) < 0.2, (ml, errs)
+    rate = math.log2(errs[1] / errs[2])
+    assert 2.8 < rate < 3.1, (rate, errs)
