@@ -1878,13 +1878,13 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
     }
     __syncthreads();  // the table is abandoned; its memory is reused below
   }
-  // P2 tetrahedra whose rows are too long for the table above: a table of the columns the
-  // element's blocks touch (the nodes of its pairs' l, and its own nodes for the self block)
-  // with R accumulators for a group of G rows at a time.  Each group is added to its rows by
-  // one pass over their column lists in order (coalesced), an entry taking its column's sum.
-  // (Q2 and serendipity hexahedra, whose touched columns need six or four passes at one CTA
-  // per SM, are faster with the global-memory search below at full occupancy.)
-  if constexpr (NV == 10) {
+  // Elements of ten or more nodes (P2 tetrahedra, Q2 and serendipity hexahedra) whose rows
+  // are too long for the table above: a table of the columns the element's blocks touch (the
+  // nodes of its pairs' l, and its own nodes for the self block) with R accumulators for a
+  // group of G rows at a time.  Each group is added to its rows by one pass over their column
+  // lists in order (coalesced), an entry taking its column's sum.  The table fills the
+  // shared memory (one CTA per SM), so these elements run 512 threads per CTA.
+  if constexpr (NV >= 10) {
     constexpr int TT = 8192;  // table slots; the touched columns may fill at most half
     constexpr size_t KEY_B = (size_t)TT * 4;
     const int G = (size_t)dyn > KEY_B
@@ -2042,15 +2042,15 @@ __device__ __forceinline__ void scatter_elem(int64_t m, int64_t q0, int64_t q1, 
 
 // Dynamic shared memory of the scatter kernels for elements of nn nodes, rows of up to max_row
 // columns and blocks of acc_size-byte values: the hash layout when it fits in 200 KB, else
-// (P2 tetrahedra, ten nodes) 200 KB for the table of touched columns, else the cached column
-// lists plus FP64 accumulators when that fits, else the column lists only, else 16 bytes (the
-// rows are then searched in global memory).
+// (ten or more nodes) 200 KB for the table of touched columns, else the cached column lists
+// plus FP64 accumulators when that fits, else the column lists only, else 16 bytes (the rows
+// are then searched in global memory).
 inline size_t scatter_smem_bytes(int nn, int max_row, size_t acc_size) {
   const size_t total = (size_t)nn * (size_t)std::max(1, max_row);
   const size_t hashed =
       scatter_hash_bytes(nn, scatter_table_size(std::max(1, max_row)), (int64_t)total, acc_size);
   if (hashed <= (size_t)200 * 1024) return hashed;
-  if (nn == 10) return (size_t)200 * 1024;  // the table of touched columns (scatter_elem)
+  if (nn >= 10) return (size_t)200 * 1024;  // the table of touched columns (scatter_elem)
   const size_t with_acc = ((total + 3) & ~size_t(3)) * 4 + total * 8;
   if (with_acc <= (size_t)200 * 1024) return with_acc;
   if (total * 4 <= (size_t)200 * 1024) return total * 4;
@@ -2059,16 +2059,20 @@ inline size_t scatter_smem_bytes(int nn, int max_row, size_t acc_size) {
 
 // Single problem: CTA b handles element m_begin + b; with_self = 0 adds the cross blocks of
 // the pairs in [p_begin, p_end), with_self = 1 only the self blocks.
+// threads per CTA of k_scatter: elements of ten or more nodes (one CTA per SM when their
+// tables fill the shared memory) take 512
+template <int NN>
+struct ScatterThreads {
+  static constexpr int N = NN >= 10 ? 512 : 128;
+};
+
 template <int D, typename R, int NN = D + 1>
-__global__ void __launch_bounds__(128) k_scatter(int64_t m_begin, int64_t p_begin, int64_t p_end,
-                                                 const int64_t* __restrict__ pair_off,
-                                                 const int32_t* __restrict__ pair_l,
-                                                 const int32_t* __restrict__ conn,
-                                                 const int64_t* __restrict__ row_ptr,
-                                                 const int32_t* __restrict__ col,
-                                                 const R* __restrict__ blk,
-                                                 const double* __restrict__ selfblk, int with_self,
-                                                 double* __restrict__ values, int* __restrict__ err) {
+__global__ void __launch_bounds__(ScatterThreads<NN>::N)
+    k_scatter(int64_t m_begin, int64_t p_begin, int64_t p_end, const int64_t* __restrict__ pair_off,
+              const int32_t* __restrict__ pair_l, const int32_t* __restrict__ conn,
+              const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+              const R* __restrict__ blk, const double* __restrict__ selfblk, int with_self,
+              double* __restrict__ values, int* __restrict__ err) {
   const int64_t m = m_begin + blockIdx.x;
   int64_t q0 = 0, q1 = 0;
   if (!with_self) {
@@ -2134,7 +2138,7 @@ nl_status launch_scatter(nl_mesh* m, nl_pairs* p, int64_t p_begin, int64_t p_end
   if (m_end <= m_begin) return NL_OK;
   const size_t smem = scatter_smem_bytes(NN, p->max_row_nnz, sizeof(R));
   NL_TRY((allow_smem(k_scatter<D, R, NN>, smem)));
-  k_scatter<D, R, NN><<<NL_CNT((unsigned)(m_end - m_begin)), 128, smem, s>>>(
+  k_scatter<D, R, NN><<<NL_CNT((unsigned)(m_end - m_begin)), ScatterThreads<NN>::N, smem, s>>>(
       m_begin, p_begin, p_end, p->pair_off, p->pair_l, m->conn, p->row_ptr, p->col, blk, selfblk,
       with_self, values, err);
   NL_CUDA(cudaGetLastError());
