@@ -105,3 +105,42 @@ def test_p2_workload_mesh():
     p1 = workload_mesh(WORKLOADS["c2_2d"])
     assert np.array_equal(m.conn[:, :3], p1.conn)
     assert np.array_equal(x[:, :p1.n_vert], p1.coords)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+def test_quadratic_hex_workload_meshes(order):
+    # Table 6's grid (12 x 8 x 8 cells of Omega and a 2-cell layer) with Q2 (27-node) or
+    # serendipity (20-node) hexahedra: the Q2 nodes are the points of the grid of spacing h/2
+    # over the meshed box, the serendipity nodes those with at most one odd half-step index
+    # (vertices and edge midpoints); node a of every element sits at the trilinear image of
+    # its lattice point HEX27[a] / 2, and the free nodes are those strictly inside Omega
+    from nl_inputs import HEX27
+    from nl_inputs.configs import table6_hex
+    w = table6_hex(3).with_(order=order)
+    m = workload_mesh(w)
+    nb = 27 if order == 2 else 20
+    cells = [c + 2 * w.layer for c in w.cells]
+    assert m.conn.shape == (int(np.prod(cells)), nb)
+    pts = [2 * c + 1 for c in cells]
+    inner = [2 * c - 1 for c in w.cells]
+    if order == 2:
+        assert m.n_vert == int(np.prod(pts))
+        assert int(m.node_free.sum()) == int(np.prod(inner))
+    else:
+        def count(even, odd):  # half-step grid points with at most one odd index
+            return (even[0] * even[1] * even[2] + odd[0] * even[1] * even[2] +
+                    even[0] * odd[1] * even[2] + even[0] * even[1] * odd[2])
+        # the whole box: c + 1 even and c odd indices per axis; strictly inside Omega: n - 1
+        # even and n odd
+        assert m.n_vert == count([c + 1 for c in cells], cells)
+        assert int(m.node_free.sum()) == count([c - 1 for c in w.cells], list(w.cells))
+    assert len(np.unique(m.conn)) == m.n_vert
+    x = m.coords
+    V = x[:, m.conn[:, :8]]  # (3, elem, 8)
+    corners = HEX27[:8]
+    for a in range(8, nb):
+        i, j, k = HEX27[a]
+        w8 = [(1 - i / 2 if c[0] == 0 else i / 2) * (1 - j / 2 if c[1] == 0 else j / 2) *
+              (1 - k / 2 if c[2] == 0 else k / 2) for c in [(p // 2, q // 2, r // 2) for p, q, r in corners]]
+        pos = sum(w8[b] * V[:, :, b] for b in range(8))
+        assert np.abs(x[:, m.conn[:, a]] - pos).max() < 1e-12, a
