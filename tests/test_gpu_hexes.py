@@ -140,8 +140,8 @@ def test_table7_hex_linear_on_gpu():
 @pytest.mark.parametrize("name", ["c3_3d_hex", "c3_3d_hex_q2"])
 def test_hex_full_size_sampled_rows(name):
     # the 3D workload's grid at h = 1/16 with one Q1 or Q2 hexahedron per cell (10,648 cells;
-    # Q2: 91,125 nodes, rows of up to 4,913 columns, too long for the scatter's shared-memory
-    # tables): whole matrix on the GPU in the benchmark's launch configuration, rows of seeded
+    # Q2: 91,125 nodes, rows of up to 4,913 columns, too long for the scatter's table of row
+    # positions): whole matrix on the GPU in the benchmark's launch configuration, rows of seeded
     # nodes (inside Omega, on its boundary, in the layer) against the oracle assembling only
     # the elements around them
     w = WORKLOADS[name]
