@@ -5,7 +5,9 @@ midpoints), box distances of Sec. 5.1 (eqs. maxdist, mindist, and the Euclidean 
 distance stated after eq. mindistin) in FP32, compared against delta -/+ eps with the margin
 2e-5 (delta + eps + 2 max_ext) (twice that for the Euclidean distance).  Every decision the screen
 takes must equal the FP64 decision on the exact sub-element, at every refinement level up
-to 12, on the workloads' meshes and on a mesh far from the origin."""
+to 12, on the workloads' meshes and on a mesh far from the origin; likewise for the
+quadrilaterals and hexahedra (sub-squares and sub-cubes on the lattice of half steps, to
+level 10), on the 2D grids, the 3D workload's grid and Table 6's grid."""
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
@@ -193,3 +195,115 @@ def test_closed_form_final_items_have_mu_exactly_0_or_1(eps_div):
         n_out += int(outside.sum())
     assert n_in > 0 and n_out > 0
 
+
+
+def _tensor_child(V, c, dim, dtype):
+    """Children of quadrilaterals (dim 2: vertices (0,0), (1,0), (1,1), (0,1); child c = 0..3
+    the sub-squares (0,0), (1,0), (1,1), (0,1)) and hexahedra (dim 3: the Q1 vertex order,
+    child c with bits (x, y, z)), their vertices on the lattice of half steps: a lattice point
+    with a middle index is the midpoint of its two neighbours along the first such axis (x,
+    then y, then z); the quadrilateral's centre is the midpoint of the midpoints of its edges
+    (0,1) and (2,3)."""
+    half = dtype(0.5)
+
+    def mid(a, b):
+        return ((a + b) * half).astype(dtype)
+    n = len(V)
+    idx = np.arange(n)
+    if dim == 2:
+        P = [V[:, a, :] for a in range(4)]
+        m01, m12, m23, m30 = mid(P[0], P[1]), mid(P[1], P[2]), mid(P[2], P[3]), mid(P[3], P[0])
+        ce = mid(m01, m23)
+        kids = np.stack([np.stack([P[0], m01, ce, m30], 1), np.stack([m01, P[1], m12, ce], 1),
+                         np.stack([ce, m12, P[2], m23], 1), np.stack([m30, ce, m23, P[3]], 1)], 1)
+        return kids[idx, c]
+    corner = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]
+    L = {}
+    for a, (i, j, k) in enumerate(corner):
+        L[(2 * i, 2 * j, 2 * k)] = V[:, a, :]
+    for i in (0, 2):
+        for j in (0, 2):
+            L[(i, j, 1)] = mid(L[(i, j, 0)], L[(i, j, 2)])
+        for k in range(3):
+            L[(i, 1, k)] = mid(L[(i, 0, k)], L[(i, 2, k)])
+    for j in range(3):
+        for k in range(3):
+            L[(1, j, k)] = mid(L[(0, j, k)], L[(2, j, k)])
+    kids = np.stack([np.stack([L[(cx + i, cy + j, cz + k)] for i, j, k in corner], 1)
+                     for cx, cy, cz in [(q & 1, (q >> 1) & 1, (q >> 2) & 1) for q in range(8)]], 1)
+    return kids[idx, c]
+
+
+@pytest.mark.parametrize("dim,cells,h,lo,delta,eps", [
+    (2, 128, 1 / 128, (0.0, 0.0), 4 / 128, 4 / 128 / 5),
+    (2, 64, 1 / 64, (1000.0, -350.0), 4 / 64, 4 / 64 / 20),
+    (3, 16, 1 / 16, (0.0, 0.0, 0.0), 0.125, 0.0125),
+    (3, 12, 0.1, (-0.6, -0.4, -0.4), 0.2, 0.0125),
+])
+def test_fp32_screen_of_quadrilaterals_and_hexahedra(dim, cells, h, lo, delta, eps):
+    # the same screen on the tensor-product elements: the FP32 record holds the vertex offsets
+    # and the float-float first vertex; sub-elements come from the lattice midpoints in FP32
+    # (the kernels' child rule) and are compared with the FP64 ones built the same way
+    from nl_inputs import hex_mesh, quad_mesh
+    layer = int(np.ceil((delta + eps) / h - 1e-9))
+    base = structured_mesh(dim, (cells,) * dim, h, lo, layer, jitter=0.1, seed=4)
+    mesh = quad_mesh(base) if dim == 2 else hex_mesh(base)
+    nv = 4 if dim == 2 else 8
+    X = mesh.coords.T
+    EV = X[mesh.conn[:, :nv]]  # (n_elem, nv, dim)
+    rng = np.random.default_rng(6)
+    max_ext = float((EV.max(axis=1) - EV.min(axis=1)).max())
+    cen = EV.mean(axis=1)
+    tree = cKDTree(cen)
+    n = 3000
+    ms = rng.integers(0, mesh.n_elem, n)
+    near = tree.query_ball_point(cen[ms], delta + eps + 2 * max_ext)
+    ls = np.array([rng.choice(c) for c in near])
+    off = (EV[:, 1:, :] - EV[:, :1, :]).astype(f32)
+    v0 = EV[:, 0, :]
+    v0h = v0.astype(f32)
+    v0l = (v0 - v0h.astype(np.float64)).astype(f32)
+    Vm32 = np.concatenate([np.zeros((n, 1, dim), f32), off[ms]], axis=1)
+    lo_m32, hi_m32 = Vm32.min(axis=1), Vm32.max(axis=1)
+    lo_m64, hi_m64 = EV[ms].min(axis=1), EV[ms].max(axis=1)
+    Vl0 = ((v0h[ls] - v0h[ms]).astype(f32) + (v0l[ls] - v0l[ms]).astype(f32)).astype(f32)
+    V32 = np.concatenate([Vl0[:, None, :], (Vl0[:, None, :] + off[ls]).astype(f32)], axis=1)
+    V64 = EV[ls].copy()
+    dme, dpe = delta - eps, delta + eps
+    margin = f32(2e-5 * (delta + eps + 2.0 * max_ext))
+    fdme, fdpe = f32(dme), f32(dpe)
+    lo_t, hi_t = float(fdme) - float(margin), float(fdme) + float(margin)
+    fint2 = f32(lo_t * lo_t) if lo_t > 0 else f32(-1)
+    fnotint2 = f32(hi_t * hi_t)
+    fref2 = f32((float(fdpe) - 2.0 * float(margin)) ** 2)
+    fout2 = f32((float(fdpe) + 2.0 * float(margin)) ** 2)
+    decided = 0
+    for level in range(1, 11):
+        if level > 1:
+            c = rng.integers(0, 2 ** dim, n)
+            V32 = _tensor_child(V32, c, dim, f32)
+            V64 = _tensor_child(V64, c, dim, np.float64)
+        fam, fan, fe2 = _dists(V32, lo_m32, hi_m32, f32)
+        s64, amin64, e64 = _dists(V64, lo_m64, hi_m64, np.float64)
+        amax64, aminl2 = np.sqrt(s64), np.sqrt(e64)
+        is_int, is_ref, is_ref2 = amax64 < dme, amin64 < dpe, aminl2 < dpe
+        c_int, c_notint = fam < fint2, fam > fnotint2
+        c_ref, c_out = fan < f32(fdpe - margin), fan > f32(fdpe + margin)
+        c_ref2, c_out2 = fe2 < fref2, fe2 > fout2
+        assert np.all(is_int[c_int]) and not np.any(is_int[c_notint]), level
+        assert np.all(is_ref[c_ref]) and not np.any(is_ref[c_out]), level
+        assert np.all(is_ref2[c_ref2]) and not np.any(is_ref2[c_out2]), level
+        decided += int((c_int | c_notint).sum() + (c_ref | c_out).sum())
+        # thresholds at the sub-elements' own distances, a few margins away
+        for dist, kind in ((amax64, "max"), (amin64, "min")):
+            T = dist + rng.uniform(-3, 3, n) * float(margin)
+            fT = T.astype(f32)
+            exact = dist < T
+            if kind == "max":
+                lt = fT.astype(np.float64) - float(margin)
+                t2 = np.where(lt > 0, lt * lt, -1.0).astype(f32)
+                yes, no = fam < t2, fam > ((fT.astype(np.float64) + float(margin)) ** 2).astype(f32)
+            else:
+                yes, no = fan < (fT - margin).astype(f32), fan > (fT + margin).astype(f32)
+            assert np.all(exact[yes]) and not np.any(exact[no]), (level, kind)
+    assert decided > 0.9 * 2 * 10 * n
