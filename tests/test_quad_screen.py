@@ -7,7 +7,9 @@ distance stated after eq. mindistin) in FP32, compared against delta -/+ eps wit
 takes must equal the FP64 decision on the exact sub-element, at every refinement level up
 to 12, on the workloads' meshes and on a mesh far from the origin; likewise for the
 quadrilaterals and hexahedra (sub-squares and sub-cubes on the lattice of half steps, to
-level 10), on the 2D grids, the 3D workload's grid and Table 6's grid."""
+level 10), on the 2D grids, the 3D workload's grid and Table 6's grid.  The closed forms of
+FINAL items (simplices, Q1 quadrilaterals) are taken only where every point pair clears
+delta - eps or delta + eps by half a margin."""
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
@@ -307,3 +309,62 @@ def test_fp32_screen_of_quadrilaterals_and_hexahedra(dim, cells, h, lo, delta, e
                 yes, no = fan < (fT - margin).astype(f32), fan > (fT + margin).astype(f32)
             assert np.all(exact[yes]) and not np.any(exact[no]), (level, kind)
     assert decided > 0.9 * 2 * 10 * n
+
+
+@pytest.mark.parametrize("eps_div", [5, 20])
+def test_closed_form_final_quadrilaterals_have_mu_exactly_0_or_1(eps_div):
+    # Q1 quadrilaterals: a FINAL sub-square is taken in closed form at inner point y when
+    # |c - y| < delta - eps - R - margin (or > delta + eps + R + margin), c the mean of its
+    # four FP32 vertices and R = max |v - c| (the bilinear image lies in the vertices' convex
+    # hull, inside that ball); every Gauss-Legendre 3x3 point x of the exact sub-square must
+    # then lie within delta - eps of y (beyond delta + eps) by a clear gap
+    from nl_inputs import quad_mesh
+    delta = 4 / 128
+    eps = delta / eps_div
+    layer = int(np.ceil((delta + eps) * 128 - 1e-9))
+    mesh = quad_mesh(structured_mesh(2, (128, 128), 1 / 128, (0.0, 0.0), layer, jitter=0.1, seed=4))
+    EV = mesh.coords.T[mesh.conn]  # (n_elem, 4, 2)
+    rng = np.random.default_rng(11)
+    max_ext = float((EV.max(axis=1) - EV.min(axis=1)).max())
+    cen_e = EV.mean(axis=1)
+    tree = cKDTree(cen_e)
+    n = 3000
+    ms = rng.integers(0, mesh.n_elem, n)
+    ls = np.array([rng.choice(c) for c in tree.query_ball_point(cen_e[ms], delta + eps + 2 * max_ext)])
+    g = (np.polynomial.legendre.leggauss(3)[0] + 1) / 2
+    S, T = np.meshgrid(g, g, indexing="ij")
+    s, t = S.ravel(), T.ravel()
+    N = np.stack([(1 - s) * (1 - t), s * (1 - t), s * t, (1 - s) * t], 1)  # (9, 4)
+    off = (EV[:, 1:, :] - EV[:, :1, :]).astype(f32)
+    v0 = EV[:, 0, :]
+    v0h = v0.astype(f32)
+    v0l = (v0 - v0h.astype(np.float64)).astype(f32)
+    # inner points of m in FP64 relative to m's first vertex, rounded to FP32
+    Y = np.einsum("qa,nak->nqk", N, EV[ms] - EV[ms][:, :1, :]).astype(f32)
+    Vl0 = ((v0h[ls] - v0h[ms]).astype(f32) + (v0l[ls] - v0l[ms]).astype(f32)).astype(f32)
+    V = np.concatenate([Vl0[:, None, :], (Vl0[:, None, :] + off[ls]).astype(f32)], axis=1)
+    V64 = EV[ls] - EV[ms][:, :1, :]  # the exact sub-square in the same frame
+    margin = f32(2e-5 * (delta + eps + 2.0 * max_ext))
+    dme, dpe = f32(delta - eps), f32(delta + eps)
+    n_in = n_out = 0
+    for level in range(1, 6):
+        if level > 1:
+            c = rng.integers(0, 4, n)
+            V = _tensor_child(V, c, 2, f32)
+            V64 = _tensor_child(V64, c, 2, np.float64)
+        cen = (V.sum(axis=1) * f32(0.25)).astype(f32)
+        rad = np.sqrt((((V - cen[:, None, :]) ** 2).sum(-1)).max(axis=1).astype(f32)).astype(f32)
+        lo = (dme - rad - margin).astype(f32)
+        hi = (dpe + rad + margin).astype(f32)
+        lo2 = np.where(lo > 0, lo * lo, f32(-1)).astype(f32)
+        hi2 = (hi * hi).astype(f32)
+        d2 = (((cen[:, None, :] - Y) ** 2).sum(-1)).astype(f32)  # (n, 9)
+        inside, outside = d2 < lo2[:, None], d2 > hi2[:, None]
+        X = np.einsum("qa,nak->nqk", N, V64)  # outer points of the exact sub-square
+        r = np.sqrt(((X[:, :, None, :] - Y[:, None, :, :].astype(np.float64)) ** 2).sum(-1))
+        gap = 0.5 * float(margin)
+        assert np.all(r.max(axis=1)[inside] < float(dme) - gap), level
+        assert np.all(r.min(axis=1)[outside] > float(dpe) + gap), level
+        n_in += int(inside.sum())
+        n_out += int(outside.sum())
+    assert n_in > 0 and n_out > 0
